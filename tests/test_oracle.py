@@ -1,0 +1,356 @@
+"""Pins for the FP64 CPU oracle: each check ties it to something other than
+itself -- values the paper prints, library routines, closed forms, brute-force
+d-separation, and invariants of PC-stable (no GPU needed)."""
+import itertools
+import math
+import os
+import statistics
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2109_04626_gb300 import sem
+from tests.dsep import d_separated
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --------------------------------------------------------------------------- Phi^-1
+def test_norm_ppf_matches_library():
+    nd = statistics.NormalDist()
+    for p in [1e-12, 1e-8, 1e-5, 0.001, 0.02425, 0.1, 0.3, 0.5, 0.7, 0.9, 0.975, 0.995,
+              0.9995, 0.99995, 1 - 5e-7, 1 - 1e-10]:
+        assert oracle.norm_ppf(p) == pytest.approx(nd.inv_cdf(p), rel=1e-14, abs=1e-14)
+
+
+def test_threshold_known_values():
+    # Phi^{-1}(1 - alpha/2) for the alphas the paper uses (Sec. 6: 1e-3, 1e-4, 1e-6)
+    # and the workloads' 0.01; cross-checked against the error function: Phi(q) = 1 - alpha/2.
+    for a in [0.01, 1e-3, 1e-4, 1e-6]:
+        q = oracle.threshold(a)
+        assert 0.5 * math.erfc(q / math.sqrt(2.0)) == pytest.approx(a / 2, rel=1e-12)
+
+
+def test_paper_printed_threshold():
+    rows = [ln.split() for ln in open(os.path.join(GOLDEN, "fisher_threshold.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    for N, alpha, K, thr, tol in rows:
+        val = oracle.threshold(float(alpha)) / math.sqrt(int(N) - int(K) - 3)
+        assert abs(val - float(thr)) <= float(tol)
+
+
+# --------------------------------------------------------------------------- corr
+def test_pearson_matches_numpy():
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((777, 13)) * rng.uniform(0.1, 30, 13) + rng.uniform(-5, 5, 13)
+    X[:, 4] += 3.0 * X[:, 2]
+    C = oracle.pearson(X)
+    np.testing.assert_allclose(C, np.corrcoef(X.T), atol=1e-13)
+    assert np.all(np.diag(C) == 1.0)
+
+
+# --------------------------------------------------------------------------- partial corr
+def _rand_corr(rng, p, cond_boost=0.0):
+    A = rng.standard_normal((p + 5, p))
+    A[:, 1:] += cond_boost * A[:, :-1]
+    S = A.T @ A
+    d = np.sqrt(np.diag(S))
+    C = S / np.outer(d, d)
+    np.fill_diagonal(C, 1.0)
+    return C
+
+
+def _pc_inverse(C, u, v, S):
+    idx = [u, v] + list(S)
+    P = np.linalg.inv(C[np.ix_(idx, idx)])
+    return -P[0, 1] / math.sqrt(P[0, 0] * P[1, 1])
+
+
+def _pc_recursive(C, u, v, S):
+    # r_{uv.S u k} = (r_{uv.S} - r_{uk.S} r_{vk.S}) / sqrt((1-r_{uk.S}^2)(1-r_{vk.S}^2))
+    S = list(S)
+    if not S:
+        return C[u, v]
+    k, rest = S[-1], S[:-1]
+    ruv = _pc_recursive(C, u, v, rest)
+    ruk = _pc_recursive(C, u, k, rest)
+    rvk = _pc_recursive(C, v, k, rest)
+    return (ruv - ruk * rvk) / math.sqrt((1 - ruk ** 2) * (1 - rvk ** 2))
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_partial_corr_three_formulas(seed):
+    rng = np.random.default_rng(100 + seed)
+    p = 12
+    C = _rand_corr(rng, p, cond_boost=0.7 * (seed % 3))
+    for l in range(0, 7):
+        for _ in range(4):
+            nodes = rng.choice(p, size=l + 2, replace=False)
+            u, v, S = int(nodes[0]), int(nodes[1]), sorted(int(x) for x in nodes[2:])
+            r, h11, h22, dg = oracle.partial_corr(C, u, v, S)
+            assert not dg
+            assert r == pytest.approx(_pc_inverse(C, u, v, S), abs=1e-12)
+            assert r == pytest.approx(_pc_recursive(C, u, v, S), abs=1e-12)
+            # h11 is the conditional variance of u given S (1 / [C_T^{-1}]_uu with T = S u {u})
+            Tu = [u] + S
+            assert h11 == pytest.approx(1.0 / np.linalg.inv(C[np.ix_(Tu, Tu)])[0, 0], rel=1e-10)
+
+
+def test_partial_corr_special_cases():
+    rng = np.random.default_rng(7)
+    C = _rand_corr(rng, 8)
+    # l = 0 reduces to the marginal correlation
+    assert oracle.partial_corr(C, 2, 5, [])[0] == C[2, 5]
+    # a conditioning block uncorrelated with u and v leaves r unchanged
+    B = np.eye(6)
+    B[0, 1] = B[1, 0] = 0.4
+    B[2, 3] = B[3, 2] = 0.3
+    assert oracle.partial_corr(B, 0, 1, [2, 3, 5])[0] == pytest.approx(0.4, abs=1e-15)
+    # u duplicated inside S: u is determined by S -> degenerate, r := 0, independent
+    D = np.array([[1.0, 0.5, 1.0], [0.5, 1.0, 0.5], [1.0, 0.5, 1.0]])
+    r, h11, h22, dg = oracle.partial_corr(D, 0, 1, [2])
+    assert dg and r == 0.0
+    ind, r, z, dg = oracle.ci_test(D, 100, 0.01, 0, 1, [2])
+    assert ind and dg
+    # two identical members of S: singular H2 -> degenerate
+    E = np.eye(4)
+    E[2, 3] = E[3, 2] = 1.0
+    assert oracle.partial_corr(E, 0, 1, [2, 3])[3]
+
+
+def test_ci_decision_rule():
+    # z = sqrt(n-l-3)|atanh r| <= q  <=>  independent; both signs of r; equality independent
+    n, alpha = 1003, 0.01
+    q = oracle.threshold(alpha)
+    rt = math.tanh(q / math.sqrt(n - 0 - 3))
+    for sgn in (1, -1):
+        C = np.array([[1.0, sgn * rt * (1 - 1e-9)], [sgn * rt * (1 - 1e-9), 1.0]])
+        assert oracle.ci_test(C, n, alpha, 0, 1, [])[0]
+        C = np.array([[1.0, sgn * rt * (1 + 1e-9)], [sgn * rt * (1 + 1e-9), 1.0]])
+        assert not oracle.ci_test(C, n, alpha, 0, 1, [])[0]
+    # |S| = l > 0 with S uncorrelated to u, v: r_{uv.S} = r_uv and the dof is n - l - 3
+    for l in (1, 3):
+        rt = math.tanh(q / math.sqrt(n - l - 3))
+        for f, want in ((1 - 1e-9, True), (1 + 1e-9, False)):
+            B = np.eye(l + 2)
+            B[0, 1] = B[1, 0] = rt * f
+            assert oracle.ci_test(B, n, alpha, 0, 1, list(range(2, l + 2)))[0] == want
+
+
+def test_precision_matches_numpy():
+    rng = np.random.default_rng(11)
+    C = _rand_corr(rng, 30, cond_boost=0.8)
+    P, sing = oracle.precision(C)
+    assert not sing
+    np.testing.assert_allclose(P, np.linalg.inv(C), rtol=1e-9, atol=1e-9)
+
+
+# --------------------------------------------------------------------------- population mode
+def _tiny_sems():
+    out = []
+    for seed in range(12):
+        rng = np.random.Generator(np.random.PCG64(9000 + seed))
+        p = int(rng.integers(4, 8))
+        dag, W, order = sem.er_dag(p, float(rng.uniform(0.25, 0.6)), rng)
+        out.append((dag, W))
+    return out
+
+
+def test_population_zero_partial_corr_iff_dsep():
+    for dag, W in _tiny_sems():
+        p = dag.shape[0]
+        C = sem.population_corr(W)
+        for u, v in itertools.combinations(range(p), 2):
+            others = [w for w in range(p) if w not in (u, v)]
+            for l in range(len(others) + 1):
+                for S in itertools.combinations(others, l):
+                    r = oracle.partial_corr(C, u, v, list(S))[0]
+                    assert (abs(r) < 1e-10) == d_separated(dag, u, v, S), (u, v, S, r)
+
+
+@pytest.mark.parametrize("rev", [False, True])
+def test_population_skeleton_recovery(rev):
+    for dag, W in _tiny_sems():
+        p = dag.shape[0]
+        C = sem.population_corr(W)
+        R = oracle.skeleton(C, 10 ** 9, 0.01, -1, reversed_order=rev, tol=1e-10)
+        true = ((dag + dag.T) > 0).astype(np.uint8)
+        np.testing.assert_array_equal(R["adj"], true)
+        for (a, b), (lv, side, rank, nodes) in R["sepsets"].items():
+            assert len(nodes) == lv
+            assert d_separated(dag, a, b, nodes)      # every recorded sepset separates
+        # Prop. "whichstage": true edges are never removed, every non-edge is removed
+        for a, b in itertools.combinations(range(p), 2):
+            assert ((a, b) in R["sepsets"]) == (not true[a, b])
+
+
+def _four_node():
+    lines = [ln.split() for ln in open(os.path.join(GOLDEN, "four_node_example.txt"))
+             if ln.strip() and not ln.startswith("#")]
+    spec = {ln[0]: ln[1:] for ln in lines if ln[0] != "indep"}
+    indeps = [ln[1:] for ln in lines if ln[0] == "indep"]
+    dag = np.zeros((4, 4), dtype=np.uint8)
+    W = np.zeros((4, 4))
+    wts = [0.8, -0.6, 0.7, 0.5]
+    for e, w in zip(spec["dag"], wts):
+        a, b = (int(x) - 1 for x in e.split(">"))
+        dag[a, b] = 1
+        W[a, b] = w
+    return spec, indeps, dag, W
+
+
+def test_four_node_example():
+    spec, indeps, dag, W = _four_node()
+    C = sem.population_corr(W)
+    skel = np.zeros((4, 4), dtype=np.uint8)
+    for e in spec["skeleton"]:
+        a, b = (int(x) - 1 for x in e.split("-"))
+        skel[a, b] = skel[b, a] = 1
+    for it in indeps:
+        bar = it.index("|")
+        i, j = int(it[0]) - 1, int(it[1]) - 1
+        S = [int(x) - 1 for x in it[bar + 1:]]
+        assert abs(oracle.partial_corr(C, i, j, S)[0]) < 1e-12
+        assert d_separated(dag, i, j, S)
+    # every convention recovers the stated skeleton
+    for rev in (False, True):
+        for flags in (0, oracle.NONSTABLE, oracle.ONESIDED_I, oracle.ONESIDED_J,
+                      oracle.STAGEA_GENERIC, oracle.NONSTABLE | oracle.ONESIDED_J):
+            R = oracle.skeleton(C, 10 ** 9, 0.01, -1, reversed_order=rev, flags=flags, tol=1e-10)
+            np.testing.assert_array_equal(R["adj"], skel)
+    # reversed order finds every independence at stage 2
+    R = oracle.skeleton(C, 10 ** 9, 0.01, -1, True, flags=oracle.STAGEA_GENERIC, tol=1e-10)
+    assert {v[0] for v in R["sepsets"].values()} == {int(spec["reverse_stage"][0])}
+    # stated counts (Reading R12: conventional non-stable one-sided PC; reversed stable
+    # PC with S drawn from adj(j)\{i}, i<j, the stage l=p-2 run by enumeration)
+    Rc = oracle.skeleton(C, 10 ** 9, 0.01, -1, False,
+                         flags=oracle.NONSTABLE | oracle.ONESIDED_J, tol=1e-10)
+    Rr = oracle.skeleton(C, 10 ** 9, 0.01, -1, True,
+                         flags=oracle.ONESIDED_J | oracle.STAGEA_GENERIC, tol=1e-10)
+    assert Rc["tests_total"] == int(spec["count_pc"][0])
+    assert Rr["tests_total"] == int(spec["count_pc_reverse"][0])
+
+
+# --------------------------------------------------------------------------- sample mode
+def _sample_case(seed, p=16, n=600, prob=0.3):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    dag, W, order = sem.er_dag(p, prob, rng)
+    X = sem.sample(W, order, n, rng)
+    return X, oracle.pearson(X)
+
+
+@pytest.mark.parametrize("rev", [False, True])
+def test_label_permutation_invariance(rev):
+    # PC-stable skeletons do not depend on the order of the variables (Sec. 2.2.2, Thm 3)
+    for seed in range(4):
+        X, C = _sample_case(500 + seed)
+        n, p = X.shape
+        R = oracle.skeleton(C, n, 0.01, -1, rev)
+        perm = np.random.default_rng(seed).permutation(p)
+        Cp = C[np.ix_(perm, perm)]
+        Rp = oracle.skeleton(Cp, n, 0.01, -1, rev)
+        np.testing.assert_array_equal(Rp["adj"], R["adj"][np.ix_(perm, perm)])
+
+
+def test_nonstable_is_order_dependent_somewhere():
+    # the original PC (stable = False) is order dependent; PC-stable is not -- at least
+    # one seeded case must show a difference, otherwise the switch is not doing anything
+    diff = 0
+    for seed in range(30):
+        X, C = _sample_case(700 + seed, p=14, n=300, prob=0.4)
+        n, p = X.shape
+        perm = np.random.default_rng(seed).permutation(p)
+        R = oracle.skeleton(C, n, 0.05, -1, False, flags=oracle.NONSTABLE)
+        Rp = oracle.skeleton(C[np.ix_(perm, perm)], n, 0.05, -1, False, flags=oracle.NONSTABLE)
+        diff += int((Rp["adj"] != R["adj"][np.ix_(perm, perm)]).any())
+    assert diff > 0
+
+
+@pytest.mark.parametrize("rev", [False, True])
+def test_sepsets_retest_independent_and_counts(rev):
+    for seed in range(3):
+        X, C = _sample_case(800 + seed, p=18, n=800, prob=0.35)
+        n, p = X.shape
+        R = oracle.skeleton(C, n, 0.01, -1, rev)
+        for (a, b), (lv, side, rank, nodes) in R["sepsets"].items():
+            assert list(nodes) == sorted(nodes) and len(nodes) == lv
+            assert oracle.ci_test(C, n, 0.01, a, b, list(nodes))[0]
+            # the sepset lies in the candidate set of its side
+            assert a not in nodes and b not in nodes
+        # eq. (2): tests of one stage l are bounded by 2 C(p,2) C(p-2,l) (two sides each)
+        for l in R["levels"]:
+            assert R["tests_level"][l] <= 2 * math.comb(p, 2) * math.comb(p - 2, l)
+        kmax = p - 1
+        assert R["tests_total"] <= 2 * p * (p - 1) ** (kmax + 1) / 2
+
+
+def test_sepset_is_first_in_canonical_order():
+    # the recorded (side, rank) is the first independent set in lexicographic order:
+    # re-enumerate with the oracle's own CI test and compare
+    X, C = _sample_case(901, p=12, n=500, prob=0.4)
+    n, p = X.shape
+    R = oracle.skeleton(C, n, 0.01, -1, False)
+    # rebuild frozen adjacency per level
+    adj = np.ones((p, p), dtype=np.uint8)
+    np.fill_diagonal(adj, 0)
+    for l in R["levels"]:
+        frozen = adj.copy()
+        for (a, b), (lv, side, rank, nodes) in R["sepsets"].items():
+            if lv != l:
+                continue
+            found = None
+            for s, (u, v) in enumerate(((a, b), (b, a))):
+                cand = [w for w in np.nonzero(frozen[u])[0] if w != v]
+                for k, S in enumerate(itertools.combinations(cand, l)):
+                    if oracle.ci_test(C, n, 0.01, u, v, list(S))[0]:
+                        found = (s, k, tuple(int(x) for x in S))
+                        break
+                if found:
+                    break
+            assert found == (side, rank, nodes)
+            adj[a, b] = adj[b, a] = 0
+
+
+def test_stage_a_closed_form_equals_generic_stage():
+    # the closed-form l = p-2 stage (precision matrix) removes the same pairs as running
+    # that stage by enumeration (one set per side, S = V minus the pair)
+    for seed in range(3):
+        X, C = _sample_case(950 + seed, p=14, n=400, prob=0.3)
+        n, p = X.shape
+        Ra = oracle.skeleton(C, n, 0.01, -1, True)
+        Rg = oracle.skeleton(C, n, 0.01, -1, True, flags=oracle.STAGEA_GENERIC)
+        assert Ra["stageA_ran"]
+        A = {k for k, v in Ra["sepsets"].items() if v[0] == p - 2}
+        G = {k for k, v in Rg["sepsets"].items() if v[0] == p - 2}
+        assert A == G
+        np.testing.assert_array_equal(Ra["adj"], Rg["adj"])
+
+
+def test_null_calibration():
+    # under H0 (independent columns) level-0 rejections occur at rate ~ alpha (Sec. 2.2.2)
+    rng = np.random.default_rng(1234)
+    n, p, alpha = 400, 60, 0.05
+    rej = 0
+    tot = 0
+    for _ in range(3):
+        X = rng.standard_normal((n, p))
+        C = oracle.pearson(X)
+        R = oracle.skeleton(C, n, alpha, 0, False)
+        rej += int(R["adj"].sum() // 2)
+        tot += p * (p - 1) // 2
+    rate = rej / tot
+    sd = math.sqrt(alpha * (1 - alpha) / tot)
+    assert abs(rate - alpha) < 5 * sd
+
+
+def test_levels_schedule():
+    X, C = _sample_case(990, p=20, n=1000, prob=0.25)
+    n, p = X.shape
+    Rc = oracle.skeleton(C, n, 0.01, -1, False)
+    assert Rc["levels"] == list(range(len(Rc["levels"])))
+    Rr = oracle.skeleton(C, n, 0.01, -1, True)
+    assert Rr["levels"][0] == p - 2 and Rr["levels"][-1] == 0
+    assert all(a > b for a, b in zip(Rr["levels"], Rr["levels"][1:]))
+    Rm = oracle.skeleton(C, n, 0.01, 2, True)
+    assert Rm["levels"][0] == p - 2 and max(Rm["levels"][1:]) <= 2
