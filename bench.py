@@ -1,0 +1,382 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 PC-stable skeleton search (reversed-order schedule).
+
+One step = the whole hot path on one synthetic input resident in HBM:
+pc_corr (standardise + correlation GEMM) followed by pc_skeleton (every stage
+of Algorithm 2 with PC-stable deletion).  Default workload: the dense p=95 SEM
+(edge prob 0.3, n=5000, FP32 data, alpha=0.01, all stages).
+
+Prints ONE JSON line.  ``value`` is canonical CI tests per second of step time
+(the tests the sequential algorithm executes, i.e. the oracle's count, so the
+CPU baseline and the GPU are counted alike); the L2 is flushed (a 512 MB
+write) before every timed step.  --impl reference times the FP64 CPU oracle
+on the same workload (the reference arm of this build).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "CI tests/s and skeleton time at 1 GB300: learned+mixed vs plain GPU, identical skeleton"
+UNIT = "CI tests/s"
+FP64_PEAK_TFLOPS = 1.25     # nominal GB300 FP64 (CUDA cores)
+SM_COUNT, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.070
+FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_GHZ / 1000.0   # 80.5
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="p95_dense",
+                    choices=["p20_fp64", "p95_dense", "p500_powerlaw", "p1000_er"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    return ap.parse_args()
+
+
+def workload(name):
+    from paper_2109_04626_gb300 import sem
+    cfg = {w["name"]: c for c, w in sem.WORKLOADS.items()}[name]
+    w = dict(sem.WORKLOADS[cfg])
+    s = sem.make(cfg)
+    # the p=500 and p=1000 sparse workloads run the conventional order (Algorithm 1):
+    # their stage l=p-2 leaves moral graphs of mean degree ~46-49 whose exhaustive
+    # reversed enumeration is beyond 1e12 tests
+    w["order"] = 1 if cfg in (1, 2) else 0
+    w["cfg"] = cfg
+    return s, w
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def oracle_run(X, w):
+    """One full oracle pass (Pearson + skeleton), returns (seconds, result)."""
+    import oracle
+    t0 = time.perf_counter()
+    C = oracle.pearson(X)
+    R = oracle.skeleton(C, X.shape[0], w["alpha"], w["max_level"], reversed_order=bool(w["order"]))
+    return time.perf_counter() - t0, R
+
+
+def cpu_baseline(X, w, budget_s=20.0):
+    """The oracle as it stands on the host cores, on a bounded sample: whole runs
+    of the workload repeated until ~budget_s (at least one run)."""
+    import oracle
+    runs, tot_t, tot_tests, R = 0, 0.0, 0, None
+    while runs == 0 or (tot_t < budget_s and runs < 20 and tot_t / runs * (runs + 1) < budget_s * 1.5):
+        dt, R = oracle_run(X, w)
+        runs += 1
+        tot_t += dt
+        tot_tests += R["tests_total"]
+        if dt > budget_s:
+            break
+    return {"value": tot_tests / tot_t, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{runs} full run(s) of the workload (Pearson + skeleton), {tot_t:.1f} s"}, R
+
+
+def run_reference(args):
+    rank, world, local = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), 0
+    if rank != 0:
+        return 0
+    s, w = workload(args.workload)
+    X = s.X
+    for _ in range(max(0, min(args.warmup, 1))):
+        oracle_run(X, w)
+    times, tests = [], 0
+    for _ in range(args.steps):
+        dt, R = oracle_run(X, w)
+        times.append(dt)
+        tests += R["tests_total"]
+    tot = sum(times)
+    import oracle
+    val = tests / tot
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": w["name"], "p": w["p"], "n": w["n"], "alpha": w["alpha"],
+                       "max_level": w["max_level"], "order": "reversed" if w["order"] else "conventional",
+                       "l2": "inputs on the host; oracle runs on CPU cores"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"{args.steps} full run(s) of the workload"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    from paper_2109_04626_gb300 import fastpc as fp
+    rank, world, local = dist_setup(args)
+    fp.load()
+    s, w = workload(args.workload)
+    X = s.X
+    n, p = X.shape
+    dev = torch.device("cuda", torch.cuda.current_device())
+    Xd = torch.from_numpy(X).to(dev)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def make(precision, complement):
+        pc = fp.PC(n, p, w["alpha"], w["max_level"], order=w["order"], precision=precision,
+                   complement=complement)
+        fp.pc_set_stream(pc.h, stream)
+        return pc
+
+    mixed_prec = 0 if w["cfg"] == 1 else 2
+    pc = make(mixed_prec, 1)
+    adj_d = torch.empty((p, p), dtype=torch.uint8, device=dev)
+
+    def step(pcx):
+        pcx.corr(Xd)
+        _, st = pcx.skeleton(adj_d)
+        return st
+
+    for _ in range(args.warmup):
+        st = step(pc)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    stats = []
+    barrier(world)
+    torch.cuda.synchronize()
+    l0 = fp.pc_kernel_launches()
+    with ClockSampler(local if world > 1 else torch.cuda.current_device()) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            stats.append(step(pc))
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    launches = fp.pc_kernel_launches() - l0
+    barrier(world)
+    ms = [a.elapsed_time(b) for a, b in ev]
+    ms_step = float(np.mean(ms))
+    tests = stats[-1]["tests_canonical"]
+    t_max = max_over_ranks(sum(ms) / 1000.0, world)
+    total_tests = sum_over_ranks(float(tests * args.steps), world)
+    value = total_tests / t_max
+    adj_ours = adj_d.cpu().numpy()
+
+    # per-kernel-class device time of one more step (live CUDA events, same stream)
+    fp.pc_set_opt(pc.h, "timing", 1)
+    fp.pc_timing(pc.h, reset=True)
+    flush.zero_()
+    st_t = step(pc)
+    tim = fp.pc_timing(pc.h, reset=True)
+    fp.pc_set_opt(pc.h, "timing", 0)
+    cls = fp.TIMING_CLASSES
+    dom = max(cls, key=lambda c: tim[c][0])
+    di = cls.index(dom)
+    dom_ms = tim[dom][0]
+    dom_flops = st_t["flops_class"][di] if di > 0 else 2.0 * n * p * (p + 1)
+    fp64_classes = {"stage_a", "prec", "ci_complement"}
+    if dom in fp64_classes or (dom == "ci_direct" and mixed_prec == 0):
+        peak, bound = FP64_PEAK_TFLOPS, "alu"
+    else:
+        peak, bound = FP32_PEAK_TFLOPS, "alu"
+    achieved = dom_flops / (dom_ms * 1e-3) / 1e12 if dom_ms > 0 else 0.0
+    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel": dom,
+                "kernel_ms_per_step": dom_ms,
+                "peak_source": "nominal FP64 1.25 TFLOP/s" if peak == FP64_PEAK_TFLOPS else
+                "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                "class_ms": {c: tim[c][0] for c in cls}}
+
+    # plain GPU form: FP32 SIMT GEMM + FP32 tests, direct path only, same stage loop
+    plain = None
+    if not args.no_plain:
+        pcp = make(1 if w["cfg"] != 1 else 0, 0)
+        for _ in range(2):
+            step(pcp)
+        torch.cuda.synchronize()
+        pms = []
+        for _ in range(max(3, min(args.steps, 5))):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            stp = step(pcp)
+            b.record(stream)
+            torch.cuda.synchronize()
+            pms.append(a.elapsed_time(b))
+        adj_plain = adj_d.cpu().numpy()
+        plain = {"ms_per_step": float(np.mean(pms)),
+                 "value": stp["tests_canonical"] / (np.mean(pms) / 1000.0),
+                 "skeleton_ms": stp["t_skeleton_ms"],
+                 "identical_skeleton": bool(np.array_equal(adj_plain, adj_ours))}
+        pcp.close()
+
+    # end to end through the C-ABI with host buffers (H2D of X, D2H of the adjacency)
+    pce = fp.PC(n, p, w["alpha"], w["max_level"], order=w["order"], precision=mixed_prec)
+    adj_h = np.empty((p, p), dtype=np.uint8)
+    Xh = np.ascontiguousarray(X)
+    pce.corr(Xh)
+    pce.skeleton(adj_h)
+    torch.cuda.synchronize()
+    e2e_t = []
+    for _ in range(max(3, min(args.steps, 5))):
+        t0 = time.perf_counter()
+        pce.corr(Xh)
+        _, ste = pce.skeleton(adj_h)
+        e2e_t.append(time.perf_counter() - t0)
+    pce.close()
+    e2e = {"value": ste["tests_canonical"] / float(np.mean(e2e_t)), "unit": UNIT,
+           "h2d_bytes_per_step": int(Xh.nbytes), "d2h_bytes_per_step": int(adj_h.nbytes)}
+
+    cpu = None
+    matches = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu, R = cpu_baseline(X, w)
+        matches = bool(np.array_equal(R["adj"], adj_ours)) and R["tests_total"] == tests
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if mixed_prec == 0 else "f32+f64",
+                "data": "synthetic",
+                "config": {"workload": w["name"], "p": p, "n": n, "alpha": w["alpha"],
+                           "max_level": w["max_level"],
+                           "order": "reversed" if w["order"] else "conventional",
+                           "precision": {0: "fp64", 1: "fp32", 2: "bf16x3-gemm+fp32-tests"}[mixed_prec],
+                           "tensor_core_gemm": bool(fp.pc_get_opt(pc.h, "tensor_core_gemm")),
+                           "parallelism": f"replicas x{world}",
+                           "l2": "flushed before every step (512 MB write)"},
+                "tests_canonical_per_step": tests,
+                "tests_executed_per_step": stats[-1]["tests_executed"],
+                "skeleton_ms": float(np.mean([x["t_skeleton_ms"] for x in stats])),
+                "levels_run": stats[-1]["levels_run"],
+                "redecided": stats[-1]["tests_redecided"],
+                "complement_tests": stats[-1]["complement_tests"],
+                "roofline": roofline,
+                "cpu_baseline": cpu,
+                "skeleton_matches_oracle": matches,
+                "plain_gpu": plain,
+                "e2e": e2e,
+                "gpu_launches": int(launches),
+                "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    pc.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

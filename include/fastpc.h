@@ -1,0 +1,174 @@
+/*
+ * fastpc.h -- C-ABI of the GB300 (sm_103a) PC-stable skeleton search of
+ * "A Fast PC Algorithm with Reversed-order Pruning and A Parallelization
+ * Strategy" (arXiv 2109.04626).
+ *
+ * Conventions shared by every entry point
+ *  - Every call returns a pc_status; PC_OK is 0.  On failure the handle keeps a
+ *    message readable with pc_last_error().  No C++ exception crosses the ABI.
+ *  - The caller owns every buffer it passes in or out; the library owns its
+ *    handle, the correlation matrices, the work queues, the sepset store and
+ *    every other workspace (allocated with cudaMalloc on the current device at
+ *    pc_create/pc_corr and released by pc_destroy).
+ *  - Pointers documented "host or device" are classified with
+ *    cudaPointerGetAttributes; host buffers are copied through pinned staging.
+ *  - All GPU work is issued on the handle's stream (pc_set_stream; default the
+ *    legacy default stream).  pc_corr is stream-ordered and returns without
+ *    synchronising; pc_skeleton and pc_ci_batch synchronise before returning.
+ *  - Matrices are row-major.  Node ids are 0..p-1.
+ *  - Device-side failures (a guard queue that overflows, a bounded wait that
+ *    expires) set a device status word that the next synchronising call turns
+ *    into a pc_status.
+ */
+#ifndef FASTPC_H
+#define FASTPC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pc_handle pc_handle;   /* opaque, library-owned */
+
+typedef enum {
+    PC_OK = 0,
+    PC_ERR_ARG = 1,      /* bad argument (null pointer, size out of range, bad key) */
+    PC_ERR_CUDA = 2,     /* a CUDA runtime call failed                              */
+    PC_ERR_OOM = 3,      /* device allocation failed                                */
+    PC_ERR_STATE = 4,    /* call out of order (e.g. pc_skeleton before pc_corr)     */
+    PC_ERR_DOF = 5,      /* n - l - 3 <= 0: the Fisher-z test is undefined          */
+    PC_ERR_BUDGET = 6,   /* a stage would exceed the test budget (option "budget")  */
+    PC_ERR_TIMEOUT = 7,  /* a device-side bounded wait expired                      */
+    PC_ERR_INTERNAL = 8  /* a device-side consistency check failed                  */
+} pc_status;
+
+enum { PC_F32 = 0, PC_F64 = 1 };
+
+/* Counters of one pc_skeleton call. */
+typedef struct {
+    uint64_t tests_executed;    /* CI tests the GPU evaluated (speculative ones included)     */
+    uint64_t tests_canonical;   /* tests the sequential canonical order needs (oracle count)  */
+    uint64_t tests_redecided;   /* tests re-decided in FP64 (guard or band)                   */
+    uint64_t band_hits;         /* FP32 |z - q| inside the band                               */
+    uint64_t guard_hits;        /* FP32 pivot ratio below the guard                           */
+    uint64_t degenerate;        /* tests decided by the degeneracy rule                       */
+    uint64_t complement_tests;  /* tests evaluated from a neighbourhood precision matrix     */
+    uint64_t edges_removed;     /* unordered pairs removed                                    */
+    uint64_t edges_kept;        /* unordered pairs in the returned skeleton                   */
+    double max_abs_dz;          /* max |z_fp32 - z_fp64| over re-decided tests                */
+    double t_skeleton_ms;       /* device time of the skeleton search (CUDA events)           */
+    double flops;               /* arithmetic of the search, counted in the kernels (2/FMA)   */
+    double flops_class[6];      /* the same split by kernel class (see pc_timing)             */
+    int32_t levels_run;         /* stages visited                                             */
+    int32_t stage_a_ran;        /* 1 if the l = p-2 stage ran in closed form                  */
+    int32_t first_level;        /* first enumerated stage                                     */
+    int32_t reserved;
+} pc_stats;
+
+/* pc_create -- a handle for data of n samples over p variables, significance
+ * level alpha (0 < alpha < 1) and conditioning-set cap max_level (< 0: none).
+ * Sec. 2.2.2 (Fisher-z threshold Phi^{-1}(1-alpha/2)), Algorithm 1/2 inputs.
+ * Requires 4 <= n <= 2^21 and 2 <= p <= 4096.  Allocates the handle's workspaces. */
+pc_status pc_create(int64_t n, int32_t p, double alpha, int32_t max_level, pc_handle **out);
+
+/* pc_destroy -- frees the handle and every library-owned allocation. */
+void pc_destroy(pc_handle *h);
+
+/* pc_set_opt / pc_get_opt -- named options (numeric values):
+ *   "order"       0 = conventional (Algorithm 1, l ascending), 1 = reversed
+ *                 (Algorithm 2, l descending; default)
+ *   "stage_a"     1 = run the l = p-2 stage in closed form when n-p-1 > 0 (default)
+ *   "precision"   0 = FP64 everywhere; 1 = FP32 SIMT correlation GEMM + FP32 tests
+ *                 with FP64 re-decision; 2 = split-precision BF16x3 tensor-core
+ *                 correlation GEMM + FP32 tests with FP64 re-decision (default)
+ *   "band"        FP64 re-decision band on |z - q| (default 1e-3)
+ *   "guard"       pivot-ratio guard: FP32 tests whose smallest Cholesky pivot is
+ *                 below it are re-decided in FP64 (default 1e-3)
+ *   "complement"  1 = evaluate high stages from maintained neighbourhood precision
+ *                 matrices (default), 0 = direct tests only
+ *   "budget"      maximum tests one stage may schedule (default 2e10)
+ *   "timing"      1 = record per-kernel-class CUDA-event times (pc_timing)
+ * Unknown keys return PC_ERR_ARG. */
+pc_status pc_set_opt(pc_handle *h, const char *key, double val);
+pc_status pc_get_opt(pc_handle *h, const char *key, double *val);
+
+/* pc_set_stream -- cudaStream_t on which all later work is issued. */
+pc_status pc_set_stream(pc_handle *h, void *stream);
+
+/* pc_corr -- standardises the columns of X (FP64 mean and population sd) and
+ * forms corr = Xs^T Xs / n with unit diagonal (Sec. 4, the matrix corr).
+ * X: n x p row-major with row stride ld >= p elements, dtype PC_F32 or PC_F64,
+ * host or device, caller-owned, read only.  Stream-ordered; X must stay valid
+ * until the stream reaches the call. */
+pc_status pc_corr(pc_handle *h, const void *X, int32_t dtype, int64_t ld);
+
+/* pc_corr_get -- copies the correlation matrix (p x p row-major) into C32
+ * and/or C64 (either may be NULL; host or device).  Synchronises. */
+pc_status pc_corr_get(pc_handle *h, float *C32, double *C64);
+
+/* pc_skeleton -- Phase I of Algorithm 2 (reversed order) or Algorithm 1
+ * (conventional), PC-stable: the adjacency is frozen at the start of each
+ * stage and deletions are applied at its end.  For every adjacent ordered pair
+ * (u,v) and every S subset of adj(u)\{v} with |S| = l, in lexicographic order
+ * (side 0: u = min(u,v) first), it tests u _||_ v | S with
+ * sqrt(n-l-3)|atanh r_uv.S| <= Phi^{-1}(1-alpha/2) (Eq. 1, Sec. 2.2.2), r from
+ * the Schur complement of Sec. 4.  Writes the skeleton into adj_out (p x p,
+ * 0/1, symmetric, host or device; may be NULL) and the counters into stats
+ * (host; may be NULL).  Sepsets stay in the handle (pc_sepsets_*).
+ * Requires a prior pc_corr.  Synchronises. */
+pc_status pc_skeleton(pc_handle *h, uint8_t *adj_out, pc_stats *stats);
+
+/* pc_sepsets_count -- number of removed pairs of the last pc_skeleton and the
+ * total length of their explicit sepsets (stage l = p-2 sets V\{u,v} are not
+ * stored explicitly: their offset is -1). */
+pc_status pc_sepsets_count(pc_handle *h, int64_t *n_removed, int64_t *pool_len);
+
+/* pc_sepsets_get -- host buffers: pairs[2*k] = (a, b) with a < b, level[k],
+ * side[k] (0: S from adj(a)\{b}, 1: from adj(b)\{a}), rank[k] (lexicographic
+ * rank of S within its side), off[k] (offset into pool or -1) and pool
+ * (the explicit sets, ascending node ids).  Any pointer may be NULL. */
+pc_status pc_sepsets_get(pc_handle *h, int32_t *pairs, int32_t *level, int32_t *side,
+                         int64_t *rank, int64_t *off, int32_t *pool);
+
+/* pc_ci_batch -- b raw CI tests on the current correlation matrix (the index
+ * matrix B of Sec. 4 / Algorithm 3): test k is (ij[2k], ij[2k+1] | S[k*l .. k*l+l-1]).
+ * Outputs r_out[k] (partial correlation), z_out[k] (sqrt(n-l-3)|atanh r|),
+ * indep_out[k] (1 = independent).  Device pointers (caller-owned); any output
+ * may be NULL.  Returns PC_ERR_DOF if n-l-3 <= 0, PC_ERR_ARG for ids out of
+ * range or u == v.  Tests whose FP32 value is unreliable (pivot guard, |z-q|
+ * band) are recomputed in FP64 from FP64 correlations.  Synchronises. */
+pc_status pc_ci_batch(pc_handle *h, const int32_t *ij, const int32_t *S, int32_t l, int64_t b,
+                      double *r_out, uint8_t *indep_out, float *z_out);
+
+/* pc_last_stats -- counters of the last pc_skeleton or pc_ci_batch call (host). */
+pc_status pc_last_stats(pc_handle *h, pc_stats *out);
+
+/* pc_threshold -- q = Phi^{-1}(1 - alpha/2) as used by the handle. */
+double pc_threshold(const pc_handle *h);
+
+/* pc_fisher_threshold -- q = Phi^{-1}(1 - alpha/2) (host only, no GPU needed):
+ * the two-sided normal quantile of the Fisher-z rule (Sec. 2.2.2).  Newton
+ * iterations on log(erfc(x/sqrt 2)/2) = log(alpha/2).  NaN unless 0<alpha<1. */
+double pc_fisher_threshold(double alpha);
+
+/* pc_kernel_launches -- number of CUDA kernels this library has launched in
+ * this process (all handles). */
+int64_t pc_kernel_launches(void);
+
+/* pc_timing -- with option "timing" = 1, the handle brackets its launches
+ * with CUDA events on its stream, grouped by kernel class: 0 correlation,
+ * 1 closed-form stage l=p-2, 2 neighbourhood precision builds and downdates,
+ * 3 direct CI tests, 4 complement CI tests, 5 stage bookkeeping (neighbour
+ * lists, counts, scans, commit).  Writes per-class device milliseconds and
+ * launch-group counts accumulated since the last reset (reset != 0 clears
+ * them afterwards).  ms and count have 6 entries; either may be NULL. */
+pc_status pc_timing(pc_handle *h, double *ms, int64_t *count, int32_t reset);
+
+const char *pc_last_error(const pc_handle *h);
+const char *pc_status_string(pc_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FASTPC_H */

@@ -108,8 +108,11 @@ def norm_ppf(p: float) -> float:
 
 
 def threshold(alpha: float) -> float:
-    """q = Phi^{-1}(1 - alpha/2), the two-sided Fisher-z threshold (Sec. 2.2.2)."""
-    return norm_ppf(1.0 - alpha / 2.0)
+    """q = Phi^{-1}(1 - alpha/2), the two-sided Fisher-z threshold (Sec. 2.2.2).
+
+    Evaluated as -Phi^{-1}(alpha/2) (symmetry of the normal law): the lower-tail
+    argument alpha/2 is exact in floating point, whereas 1 - alpha/2 rounds."""
+    return -norm_ppf(alpha / 2.0)
 
 
 def num_threads() -> int:

@@ -1,0 +1,211 @@
+// corr.cu -- column standardisation and the correlation matrix
+// corr = Xs^T Xs / n (Sec. 4, the matrix corr): FP64 column statistics, FP64
+// and FP32 Gram kernels on the CUDA cores, and the FP64 -> FP32 cast.
+#include "internal.h"
+#include <cuda_bf16.h>
+
+namespace fpc {
+
+template <typename T>
+__device__ __forceinline__ double ld_as_double(const T *p) { return (double)__ldg(p); }
+
+// Column mean and reciprocal population standard deviation, two passes in FP64.
+// Block: 32 columns x 8 row phases; a warp reads 32 consecutive columns of one row.
+template <typename T>
+__global__ void __launch_bounds__(256) col_stats_kernel(const T *__restrict__ X, long long n, int p,
+                                                        long long ld, double *mean, double *rsd)
+{
+    __shared__ double red[8][33];
+    __shared__ double mu_s[32];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int col = blockIdx.x * 32 + tx;
+    const bool ok = col < p;
+    double s = 0.0;
+    if (ok)
+        for (long long t = ty; t < n; t += 8) s += ld_as_double(X + t * ld + col);
+    red[ty][tx] = s;
+    __syncthreads();
+    if (ty == 0) {
+        double a = 0.0;
+        for (int k = 0; k < 8; ++k) a += red[k][tx];
+        mu_s[tx] = a / (double)n;
+    }
+    __syncthreads();
+    const double mu = mu_s[tx];
+    double q = 0.0;
+    if (ok)
+        for (long long t = ty; t < n; t += 8) {
+            double d = ld_as_double(X + t * ld + col) - mu;
+            q += d * d;
+        }
+    red[ty][tx] = q;
+    __syncthreads();
+    if (ty == 0 && ok) {
+        double a = 0.0;
+        for (int k = 0; k < 8; ++k) a += red[k][tx];
+        double var = a / (double)n;
+        mean[col] = mu;
+        rsd[col] = var > 0.0 ? 1.0 / sqrt(var) : 0.0;   // constant column -> zero column
+    }
+}
+
+// Xs = (X - mean) * rsd written K-major (column-major, row stride ldk = padded n)
+// as FP64, FP32 and a BF16 hi/lo split (hi = bf16(x), lo = bf16(x - hi)).
+// 32 x 32 tiles transposed through shared memory.
+template <typename T>
+__global__ void __launch_bounds__(256) standardize_kernel(const T *__restrict__ X, long long n, int p,
+                                                          long long ld, const double *mean,
+                                                          const double *rsd, double *Xs64,
+                                                          float *Xs32, uint16_t *Xhi,
+                                                          uint16_t *Xlo, long long ldk)
+{
+    __shared__ double tile[32][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int col0 = blockIdx.x * 32;
+    const long long row0 = (long long)blockIdx.y * 32;
+    const int col = col0 + tx;
+    const double mu = col < p ? mean[col] : 0.0, rs = col < p ? rsd[col] : 0.0;
+    for (int k = 0; k < 4; ++k) {
+        long long r = row0 + ty + 8 * k;
+        double v = 0.0;
+        if (r < n && col < p) v = (ld_as_double(X + r * ld + col) - mu) * rs;
+        tile[ty + 8 * k][tx] = v;
+    }
+    __syncthreads();
+    for (int k = 0; k < 4; ++k) {
+        int c = col0 + ty + 8 * k;
+        long long r = row0 + tx;
+        if (c < p && r < n) {
+            double v = tile[tx][ty + 8 * k];
+            long long o = (long long)c * ldk + r;
+            if (Xs64) Xs64[o] = v;
+            if (Xs32) Xs32[o] = (float)v;
+            if (Xhi) {
+                __nv_bfloat16 hi = __float2bfloat16_rn((float)v);
+                float rem = (float)(v - (double)__bfloat162float(hi));
+                __nv_bfloat16 lo = __float2bfloat16_rn(rem);
+                Xhi[o] = __bfloat16_as_ushort(hi);
+                Xlo[o] = __bfloat16_as_ushort(lo);
+            }
+        }
+    }
+}
+
+// Gram kernel C = Xs^T Xs / n on the CUDA cores, upper-triangle 64x64 tiles
+// mirrored to the lower triangle, unit diagonal.  Xs is K-major: column a of
+// Xs (= row a of Xs^T) is contiguous.  Acc is the accumulation type; for FP32
+// inputs each 256-long K chunk is summed in FP32 and chunks are added in FP64.
+template <typename T, typename Acc>
+__global__ void __launch_bounds__(256) syrk_kernel(const T *__restrict__ Xs, long long n,
+                                                   long long ldk, int p, T *C, int ldc)
+{
+    constexpr int BT = 64, BK = 32;
+    __shared__ T As[BK][BT + 1];
+    __shared__ T Bs[BK][BT + 1];
+    // upper-triangular tile index -> (bi, bj), bi <= bj
+    int t = blockIdx.x, nt = (p + BT - 1) / BT, bi = 0;
+    while (t >= nt - bi) { t -= nt - bi; ++bi; }
+    const int bj = bi + t;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int a0 = bi * BT, b0 = bj * BT;
+    double accd[4][4];
+    Acc acc[4][4];
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) { accd[i][j] = 0.0; acc[i][j] = (Acc)0; }
+    int chunk = 0;
+    for (long long k0 = 0; k0 < n; k0 += BK) {
+        // load 64 x 32 of each operand (K contiguous): thread -> (row, k)
+        for (int e = threadIdx.x; e < BT * BK; e += 256) {
+            int r = e / BK, k = e % BK;
+            long long kk = k0 + k;
+            int ra = a0 + r, rb = b0 + r;
+            As[k][r] = (ra < p && kk < n) ? Xs[(long long)ra * ldk + kk] : (T)0;
+            Bs[k][r] = (rb < p && kk < n) ? Xs[(long long)rb * ldk + kk] : (T)0;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int k = 0; k < BK; ++k) {
+            Acc av[4], bv[4];
+            for (int i = 0; i < 4; ++i) av[i] = (Acc)As[k][ty * 4 + i];
+            for (int j = 0; j < 4; ++j) bv[j] = (Acc)Bs[k][tx * 4 + j];
+            for (int i = 0; i < 4; ++i)
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+        }
+        __syncthreads();
+        if (++chunk == 8) {
+            chunk = 0;
+            for (int i = 0; i < 4; ++i)
+                for (int j = 0; j < 4; ++j) { accd[i][j] += (double)acc[i][j]; acc[i][j] = (Acc)0; }
+        }
+    }
+    const double inv_n = 1.0 / (double)n;
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) {
+            int a = a0 + ty * 4 + i, b = b0 + tx * 4 + j;
+            if (a >= p || b >= p) continue;
+            double v = (accd[i][j] + (double)acc[i][j]) * inv_n;
+            if (a == b) v = 1.0;
+            C[(long long)a * ldc + b] = (T)v;
+            C[(long long)b * ldc + a] = (T)v;
+        }
+}
+
+__global__ void cast_kernel(const double *C64, float *C32, int p, int ldc)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long tot = (long long)p * ldc;
+    if (i < tot) C32[i] = (float)C64[i];
+}
+
+cudaError_t launch_col_stats(const void *X, int dtype, long long n, int p, long long ld,
+                             double *mean, double *rsd, cudaStream_t s)
+{
+    dim3 g((p + 31) / 32);
+    if (dtype == 1)
+        col_stats_kernel<double><<<g, 256, 0, s>>>((const double *)X, n, p, ld, mean, rsd);
+    else
+        col_stats_kernel<float><<<g, 256, 0, s>>>((const float *)X, n, p, ld, mean, rsd);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_standardize(const void *X, int dtype, long long n, int p, long long ld,
+                               const double *mean, const double *rsd, double *Xs64,
+                               float *Xs32, uint16_t *Xhi, uint16_t *Xlo, long long ldk,
+                               cudaStream_t s)
+{
+    dim3 g((p + 31) / 32, (unsigned)((n + 31) / 32));
+    if (dtype == 1)
+        standardize_kernel<double><<<g, 256, 0, s>>>((const double *)X, n, p, ld, mean, rsd,
+                                                     Xs64, Xs32, Xhi, Xlo, ldk);
+    else
+        standardize_kernel<float><<<g, 256, 0, s>>>((const float *)X, n, p, ld, mean, rsd,
+                                                    Xs64, Xs32, Xhi, Xlo, ldk);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_syrk_f64(const double *Xs, long long n, long long ldk, int p, double *C64,
+                            int ldc, cudaStream_t s)
+{
+    int nt = (p + 63) / 64;
+    syrk_kernel<double, double><<<nt * (nt + 1) / 2, 256, 0, s>>>(Xs, n, ldk, p, C64, ldc); note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_syrk_f32(const float *Xs, long long n, long long ldk, int p, float *C32,
+                            int ldc, cudaStream_t s)
+{
+    int nt = (p + 63) / 64;
+    syrk_kernel<float, float><<<nt * (nt + 1) / 2, 256, 0, s>>>(Xs, n, ldk, p, C32, ldc); note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cast_c(const double *C64, float *C32, int p, int ldc, cudaStream_t s)
+{
+    long long tot = (long long)p * ldc;
+    cast_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(C64, C32, p, ldc); note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace fpc

@@ -1,0 +1,88 @@
+// device_util.cuh -- small device helpers shared by the kernels of libfastpc.
+#pragma once
+#include "internal.h"
+
+namespace fpc {
+
+// In-place Gauss-Jordan inversion of an SPD matrix held in shared memory
+// (no row exchanges: the k-th pivot is the conditional variance of k given
+// 0..k-1).  One CTA.  Sets *bad if a pivot is <= DEGEN.
+__device__ __forceinline__ void gj_inverse_block(double *A, int m, int lda, double *colk, double *rowk, int *bad)
+{
+    for (int k = 0; k < m; ++k) {
+        const double piv = A[k * lda + k];
+        if (!(piv > DEGEN)) {
+            if (threadIdx.x == 0) *bad = 1;
+            return;                                   // uniform: every thread read the same pivot
+        }
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+            colk[i] = A[i * lda + k];
+            rowk[i] = A[k * lda + i];
+        }
+        __syncthreads();
+        const double ip = 1.0 / piv;
+        const int tot = m * m;
+        for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+            int i = e / m, j = e - i * m;
+            double v;
+            if (i == k) v = (j == k) ? ip : rowk[j] * ip;
+            else if (j == k) v = -colk[i] * ip;
+            else v = A[i * lda + j] - colk[i] * rowk[j] * ip;
+            A[i * lda + j] = v;
+        }
+        __syncthreads();
+    }
+}
+
+
+// Lexicographic unranking: positions pos[0..l) (ascending, in 0..d-1) of the
+// rank-th l-subset of d items; the number of subsets whose i-th position is x
+// is C(d-x-1, l-i-1).  binom is the (ldb x ldb) saturating table.
+__device__ __forceinline__ void unrank_lex(unsigned long long rank, int d, int l,
+                                           const unsigned long long *binom, int ldb, int *pos)
+{
+    int x = 0;
+    for (int i = 0; i < l; ++i) {
+        // x never passes d-(l-i): there C(l-i-1, l-i-1) = 1 > any valid remainder
+        while (x < d - (l - i)) {
+            unsigned long long c = binom[(long long)(d - x - 1) * ldb + (l - i - 1)];
+            if (rank < c) break;
+            rank -= c;
+            ++x;
+        }
+        pos[i] = x++;
+    }
+}
+
+// First index i in [0, len) with a[i] > key (len if none).
+template <typename T>
+__device__ __forceinline__ long long upper_bound_dev(const T *a, long long len, T key)
+{
+    long long lo = 0, hi = len;
+    while (lo < hi) {
+        long long mid = (lo + hi) >> 1;
+        if (a[mid] > key) hi = mid;
+        else lo = mid + 1;
+    }
+    return lo;
+}
+
+// First index i in [0, len) with a[i] >= key.
+__device__ __forceinline__ int lower_bound_int(const int *a, int len, int key)
+{
+    int lo = 0, hi = len;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (a[mid] < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void atomic_max_float_pos(unsigned int *addr, float v)
+{
+    // v >= 0: IEEE order equals unsigned order of the bit patterns
+    atomicMax(addr, __float_as_uint(v));
+}
+
+}  // namespace fpc

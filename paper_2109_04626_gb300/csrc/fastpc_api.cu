@@ -1,0 +1,774 @@
+// fastpc_api.cu -- the C-ABI of include/fastpc.h: handle, options, the
+// correlation step and the host side of the stage loop (Algorithm 1 / 2).
+#include "internal.h"
+#include "../../include/fastpc.h"
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using fpc::DevCounters;
+using fpc::GraphDev;
+using fpc::LevelInfo;
+using fpc::TestParams;
+typedef unsigned long long ull;
+
+static std::atomic<long long> g_launches{0};
+namespace fpc {
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+}
+
+constexpr int NCLS = 6;
+struct TimedPair {
+    int cls;
+    cudaEvent_t a, b;
+};
+
+struct pc_handle {
+    long long n = 0;
+    int p = 0;
+    double alpha = 0.01;
+    int max_level = -1;
+    double q = 0.0;
+    // options
+    int order = 1, stage_a = 1, precision = 2, complement = 1;
+    double band = 1e-3, guard = 1e-3;
+    double budget = 2.0e10;
+    cudaStream_t stream = 0;
+    std::string err;
+    // correlation
+    long long ldk = 0;       // padded n (K-major planes)
+    int ldc = 0;             // padded p
+    double *mean = nullptr, *rsd = nullptr;
+    double *Xs64 = nullptr;
+    float *Xs32 = nullptr;
+    uint16_t *Xhi = nullptr, *Xlo = nullptr;
+    double *C64 = nullptr, *Pbuf = nullptr, *work = nullptr;
+    float *C32 = nullptr, *tc_ws = nullptr;
+    int *singular = nullptr;
+    void *Xstage = nullptr;
+    size_t Xstage_bytes = 0;
+    bool have_corr = false;
+    bool used_tc = false;
+    // graph state
+    GraphDev g{};
+    ull *binom = nullptr;
+    long long opair_cap = 0;
+    void *scan_ws = nullptr;
+    LevelInfo *info_h = nullptr;     // pinned mirror
+    DevCounters *ctr_h = nullptr;    // pinned mirror
+    ull *sepcnt_h = nullptr;
+    bool have_skel = false;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    pc_stats last{};
+    std::vector<void *> allocs;
+    // per-kernel-class timing
+    int timing = 0;
+    std::vector<TimedPair> pending;
+    std::vector<cudaEvent_t> evpool;
+    double cls_ms[NCLS] = {0, 0, 0, 0, 0, 0};
+    long long cls_n[NCLS] = {0, 0, 0, 0, 0, 0};
+};
+
+// Brackets the launches of one kernel class with events on the handle's stream.
+struct Timed {
+    pc_handle *h;
+    int cls;
+    cudaEvent_t a = nullptr, b = nullptr;
+    static cudaEvent_t get(pc_handle *h)
+    {
+        if (!h->evpool.empty()) {
+            cudaEvent_t e = h->evpool.back();
+            h->evpool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+    Timed(pc_handle *h_, int c) : h(h_), cls(c)
+    {
+        if (!h->timing) return;
+        a = get(h);
+        b = get(h);
+        cudaEventRecord(a, h->stream);
+    }
+    ~Timed()
+    {
+        if (!h->timing) return;
+        cudaEventRecord(b, h->stream);
+        h->pending.push_back({cls, a, b});
+    }
+};
+
+// ---------------------------------------------------------------- helpers
+static const char *kStatusNames[] = {"PC_OK",          "PC_ERR_ARG",    "PC_ERR_CUDA",
+                                     "PC_ERR_OOM",     "PC_ERR_STATE",  "PC_ERR_DOF",
+                                     "PC_ERR_BUDGET",  "PC_ERR_TIMEOUT", "PC_ERR_INTERNAL"};
+
+static pc_status fail(pc_handle *h, pc_status s, const std::string &msg)
+{
+    if (h) h->err = msg;
+    return s;
+}
+
+static pc_status cuda_fail(pc_handle *h, cudaError_t e, const char *where)
+{
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    return fail(h, e == cudaErrorMemoryAllocation ? PC_ERR_OOM : PC_ERR_CUDA, m);
+}
+
+#define CK(call)                                                   \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, #call);     \
+    } while (0)
+
+template <typename T>
+static cudaError_t dalloc(pc_handle *h, T **p, size_t bytes)
+{
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes ? bytes : 16);
+    if (e != cudaSuccess) return e;
+    h->allocs.push_back(q);
+    *p = (T *)q;
+    return cudaSuccess;
+}
+
+static void dfree(pc_handle *h, void *p)
+{
+    if (!p) return;
+    auto it = std::find(h->allocs.begin(), h->allocs.end(), p);
+    if (it != h->allocs.end()) h->allocs.erase(it);
+    cudaFree(p);
+}
+
+static bool is_device_ptr(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Upper-tail normal quantile x with Q(x) = 0.5 erfc(x/sqrt 2) = a (0 < a < 1):
+// Newton iterations on log Q(x) - log a, started from the tail asymptote.
+static double upper_quantile(double a)
+{
+    if (a > 0.5) return -upper_quantile(1.0 - a);
+    if (a == 0.5) return 0.0;
+    double x = std::sqrt(-2.0 * std::log(a));
+    for (int it = 0; it < 200; ++it) {
+        double Q = 0.5 * std::erfc(x / std::sqrt(2.0));
+        double phi = std::exp(-0.5 * x * x) / std::sqrt(2.0 * M_PI);
+        double step = (std::log(Q) - std::log(a)) * Q / phi;   // g / g', g' = -phi/Q
+        x += step;
+        if (std::fabs(step) <= 1e-16 * std::max(1.0, std::fabs(x))) break;
+    }
+    return x;
+}
+
+static TestParams make_tp(const pc_handle *h)
+{
+    TestParams tp;
+    tp.n = h->n;
+    tp.q = h->q;
+    tp.qf = (float)h->q;
+    tp.band = h->band;
+    tp.guard = h->guard;
+    tp.precision = h->precision;
+    tp.reversed = h->order == 1;
+    tp.complement = h->complement;
+    return tp;
+}
+
+// ---------------------------------------------------------------- create / destroy
+extern "C" pc_status pc_create(int64_t n, int32_t p, double alpha, int32_t max_level,
+                               pc_handle **out)
+{
+    if (!out) return PC_ERR_ARG;
+    *out = nullptr;
+    if (n < 4 || n > (1ll << 21) || p < 2 || p > fpc::MAXP || !(alpha > 0.0 && alpha < 1.0))
+        return PC_ERR_ARG;
+    pc_handle *h = new pc_handle();
+    h->n = n;
+    h->p = p;
+    h->alpha = alpha;
+    h->max_level = max_level;
+    h->q = upper_quantile(alpha / 2.0);
+    h->ldk = (n + 63) / 64 * 64;
+    h->ldc = (p + 3) / 4 * 4;
+    const int W = (p + 31) / 32;
+    GraphDev &g = h->g;
+    g.p = p;
+    g.W = W;
+    size_t pp = (size_t)p * p;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](cudaError_t ee) { if (e == cudaSuccess) e = ee; };
+    A(dalloc(h, &g.adj, (size_t)p * W * sizeof(uint32_t)));
+    A(dalloc(h, &g.deg, (size_t)p * sizeof(int)));
+    A(dalloc(h, &g.nbr, pp * sizeof(int)));
+    A(dalloc(h, &g.ooff, (size_t)(p + 1) * sizeof(long long)));
+    h->opair_cap = (long long)p * (p - 1);
+    A(dalloc(h, &g.tcnt, (size_t)(h->opair_cap + 2) * sizeof(ull)));
+    A(dalloc(h, &g.ccnt, (size_t)(h->opair_cap + 2) * sizeof(ull)));
+    A(dalloc(h, &h->scan_ws, fpc::scan_ws_bytes(h->opair_cap)));
+    A(dalloc(h, &g.best, pp * sizeof(ull)));
+    A(dalloc(h, &h->binom, (size_t)(p + 1) * (p + 1) * sizeof(ull)));
+    A(dalloc(h, &g.sep_level, pp * sizeof(int)));
+    A(dalloc(h, &g.sep_side, pp * sizeof(int)));
+    A(dalloc(h, &g.sep_rank, pp * sizeof(long long)));
+    A(dalloc(h, &g.sep_off, pp * sizeof(long long)));
+    g.pool_cap = std::max<long long>(1 << 16, 4ll * p * p);
+    A(dalloc(h, &g.pool, (size_t)g.pool_cap * sizeof(int)));
+    A(dalloc(h, &g.prec, (size_t)p * fpc::PREC_MAX * fpc::PREC_MAX * sizeof(double)));
+    A(dalloc(h, &g.prec_m, (size_t)p * sizeof(int)));
+    A(dalloc(h, &g.prec_mem, (size_t)p * fpc::PREC_MAX * sizeof(int)));
+    A(dalloc(h, &g.prec_pos, pp * sizeof(short)));
+    A(dalloc(h, &g.prec_need, (size_t)p * sizeof(int)));
+    A(dalloc(h, &g.info, sizeof(LevelInfo)));
+    A(dalloc(h, &g.ctr, sizeof(DevCounters)));
+    A(dalloc(h, &h->mean, (size_t)p * sizeof(double)));
+    A(dalloc(h, &h->rsd, (size_t)p * sizeof(double)));
+    A(dalloc(h, &h->C64, (size_t)p * h->ldc * sizeof(double)));
+    A(dalloc(h, &h->C32, (size_t)p * h->ldc * sizeof(float)));
+    A(dalloc(h, &h->singular, sizeof(int)));
+    A(dalloc(h, &h->work, (size_t)(2 * p + 16) * sizeof(double)));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&h->info_h, sizeof(LevelInfo));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&h->ctr_h, sizeof(DevCounters));
+    if (e == cudaSuccess) e = cudaEventCreate(&h->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&h->ev1);
+    if (e != cudaSuccess) {
+        pc_status st = e == cudaErrorMemoryAllocation ? PC_ERR_OOM : PC_ERR_CUDA;
+        pc_destroy(h);
+        return st;
+    }
+    g.binom = h->binom;
+    // saturating Pascal triangle
+    std::vector<ull> B((size_t)(p + 1) * (p + 1), 0ull);
+    for (int a = 0; a <= p; ++a) {
+        B[(size_t)a * (p + 1)] = 1;
+        for (int b = 1; b <= a; ++b) {
+            ull x = B[(size_t)(a - 1) * (p + 1) + b - 1];
+            ull y = b <= a - 1 ? B[(size_t)(a - 1) * (p + 1) + b] : 0ull;
+            ull s = x + y;
+            B[(size_t)a * (p + 1) + b] = (s < x || x == fpc::KEY_NONE || y == fpc::KEY_NONE) ? fpc::KEY_NONE : s;
+        }
+    }
+    e = cudaMemcpy(h->binom, B.data(), B.size() * sizeof(ull), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        pc_destroy(h);
+        return PC_ERR_CUDA;
+    }
+    *out = h;
+    return PC_OK;
+}
+
+extern "C" void pc_destroy(pc_handle *h)
+{
+    if (!h) return;
+    for (void *p : h->allocs) cudaFree(p);
+    h->allocs.clear();
+    if (h->info_h) cudaFreeHost(h->info_h);
+    if (h->ctr_h) cudaFreeHost(h->ctr_h);
+    if (h->sepcnt_h) cudaFreeHost(h->sepcnt_h);
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+    for (auto &t : h->pending) {
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    for (auto e : h->evpool) cudaEventDestroy(e);
+    delete h;
+}
+
+// ---------------------------------------------------------------- options
+extern "C" pc_status pc_set_opt(pc_handle *h, const char *key, double val)
+{
+    if (!h || !key) return PC_ERR_ARG;
+    std::string k(key);
+    if (k == "order") {
+        if (val != 0 && val != 1) return fail(h, PC_ERR_ARG, "order must be 0 or 1");
+        h->order = (int)val;
+    } else if (k == "stage_a") h->stage_a = val != 0;
+    else if (k == "precision") {
+        if (val != 0 && val != 1 && val != 2) return fail(h, PC_ERR_ARG, "precision must be 0, 1 or 2");
+        h->precision = (int)val;
+        h->have_corr = false;
+    } else if (k == "band") {
+        if (!(val >= 0)) return fail(h, PC_ERR_ARG, "band must be >= 0");
+        h->band = val;
+    } else if (k == "guard") {
+        if (!(val >= 0)) return fail(h, PC_ERR_ARG, "guard must be >= 0");
+        h->guard = val;
+    } else if (k == "complement") h->complement = val != 0;
+    else if (k == "timing") h->timing = val != 0;
+    else if (k == "budget") {
+        if (!(val > 0)) return fail(h, PC_ERR_ARG, "budget must be > 0");
+        h->budget = val;
+    } else return fail(h, PC_ERR_ARG, "unknown option: " + k);
+    return PC_OK;
+}
+
+extern "C" pc_status pc_get_opt(pc_handle *h, const char *key, double *val)
+{
+    if (!h || !key || !val) return PC_ERR_ARG;
+    std::string k(key);
+    if (k == "order") *val = h->order;
+    else if (k == "stage_a") *val = h->stage_a;
+    else if (k == "precision") *val = h->precision;
+    else if (k == "band") *val = h->band;
+    else if (k == "guard") *val = h->guard;
+    else if (k == "complement") *val = h->complement;
+    else if (k == "timing") *val = h->timing;
+    else if (k == "budget") *val = h->budget;
+    else if (k == "tensor_core_gemm") *val = h->used_tc ? 1.0 : 0.0;
+    else return fail(h, PC_ERR_ARG, "unknown option: " + k);
+    return PC_OK;
+}
+
+extern "C" pc_status pc_set_stream(pc_handle *h, void *stream)
+{
+    if (!h) return PC_ERR_ARG;
+    h->stream = (cudaStream_t)stream;
+    return PC_OK;
+}
+
+extern "C" double pc_threshold(const pc_handle *h) { return h ? h->q : NAN; }
+
+extern "C" double pc_fisher_threshold(double alpha)
+{
+    if (!(alpha > 0.0 && alpha < 1.0)) return NAN;
+    return upper_quantile(alpha / 2.0);
+}
+
+extern "C" int64_t pc_kernel_launches(void) { return g_launches.load(); }
+
+extern "C" pc_status pc_timing(pc_handle *h, double *ms, int64_t *count, int32_t reset)
+{
+    if (!h) return PC_ERR_ARG;
+    if (!h->pending.empty()) {
+        CK(cudaStreamSynchronize(h->stream));
+        for (auto &t : h->pending) {
+            float x = 0.f;
+            CK(cudaEventElapsedTime(&x, t.a, t.b));
+            h->cls_ms[t.cls] += x;
+            h->cls_n[t.cls] += 1;
+            h->evpool.push_back(t.a);
+            h->evpool.push_back(t.b);
+        }
+        h->pending.clear();
+    }
+    for (int c = 0; c < NCLS; ++c) {
+        if (ms) ms[c] = h->cls_ms[c];
+        if (count) count[c] = h->cls_n[c];
+        if (reset) {
+            h->cls_ms[c] = 0;
+            h->cls_n[c] = 0;
+        }
+    }
+    return PC_OK;
+}
+
+extern "C" const char *pc_last_error(const pc_handle *h) { return h ? h->err.c_str() : "null handle"; }
+
+extern "C" const char *pc_status_string(pc_status s)
+{
+    int i = (int)s;
+    return (i >= 0 && i <= 8) ? kStatusNames[i] : "PC_UNKNOWN";
+}
+
+// ---------------------------------------------------------------- correlation
+extern "C" pc_status pc_corr(pc_handle *h, const void *X, int32_t dtype, int64_t ld)
+{
+    if (!h) return PC_ERR_ARG;
+    if (!X || (dtype != PC_F32 && dtype != PC_F64) || ld < h->p)
+        return fail(h, PC_ERR_ARG, "pc_corr: bad X, dtype or ld");
+    cudaStream_t s = h->stream;
+    const int p = h->p;
+    const long long n = h->n;
+    const size_t esz = dtype == PC_F64 ? 8 : 4;
+    const void *Xd = X;
+    if (!is_device_ptr(X)) {
+        size_t bytes = (size_t)n * ld * esz;
+        if (bytes > h->Xstage_bytes) {
+            dfree(h, h->Xstage);
+            h->Xstage = nullptr;
+            h->Xstage_bytes = 0;
+            CK(dalloc(h, &h->Xstage, bytes));
+            h->Xstage_bytes = bytes;
+        }
+        CK(cudaMemcpyAsync(h->Xstage, X, bytes, cudaMemcpyHostToDevice, s));
+        Xd = h->Xstage;
+    }
+    const size_t plane = (size_t)p * h->ldk;
+    if (!h->Xs64) {
+        CK(dalloc(h, &h->Xs64, plane * sizeof(double)));
+        CK(dalloc(h, &h->Xs32, plane * sizeof(float)));
+        CK(dalloc(h, &h->Xhi, plane * sizeof(uint16_t)));
+        CK(dalloc(h, &h->Xlo, plane * sizeof(uint16_t)));
+        CK(cudaMemsetAsync(h->Xs64, 0, plane * sizeof(double), s));
+        CK(cudaMemsetAsync(h->Xs32, 0, plane * sizeof(float), s));
+        CK(cudaMemsetAsync(h->Xhi, 0, plane * sizeof(uint16_t), s));
+        CK(cudaMemsetAsync(h->Xlo, 0, plane * sizeof(uint16_t), s));
+    }
+    Timed tm(h, 0);
+    CK(fpc::launch_col_stats(Xd, dtype, n, p, ld, h->mean, h->rsd, s));
+    const bool want_bf16 = h->precision == 2 && fpc::tc_gemm_available();
+    CK(fpc::launch_standardize(Xd, dtype, n, p, ld, h->mean, h->rsd, h->Xs64,
+                               h->precision == 1 ? h->Xs32 : nullptr,
+                               want_bf16 ? h->Xhi : nullptr, want_bf16 ? h->Xlo : nullptr, h->ldk,
+                               s));
+    CK(fpc::launch_syrk_f64(h->Xs64, n, h->ldk, p, h->C64, h->ldc, s));
+    h->used_tc = false;
+    if (h->precision == 0) {
+        CK(fpc::launch_cast_c(h->C64, h->C32, p, h->ldc, s));
+    } else if (h->precision == 1 || !want_bf16) {
+        if (h->precision == 2) {
+            // tensor-core path not available in this build: FP32 operands on the CUDA cores
+            CK(fpc::launch_standardize(Xd, dtype, n, p, ld, h->mean, h->rsd, nullptr, h->Xs32,
+                                       nullptr, nullptr, h->ldk, s));
+        }
+        CK(fpc::launch_syrk_f32(h->Xs32, n, h->ldk, p, h->C32, h->ldc, s));
+    } else {
+        if (!h->tc_ws) CK(dalloc(h, &h->tc_ws, (size_t)p * h->ldc * sizeof(float) * 2 + 4096));
+        CK(fpc::launch_corr_bf16x3(h->Xhi, h->Xlo, n, h->ldk, p, h->C32, h->ldc, h->tc_ws, s));
+        h->used_tc = true;
+    }
+    h->have_corr = true;
+    h->have_skel = false;
+    return PC_OK;
+}
+
+extern "C" pc_status pc_corr_get(pc_handle *h, float *C32, double *C64)
+{
+    if (!h) return PC_ERR_ARG;
+    if (!h->have_corr) return fail(h, PC_ERR_STATE, "pc_corr_get before pc_corr");
+    cudaStream_t s = h->stream;
+    const int p = h->p;
+    if (C32)
+        CK(cudaMemcpy2DAsync(C32, p * sizeof(float), h->C32, h->ldc * sizeof(float),
+                             p * sizeof(float), p, cudaMemcpyDefault, s));
+    if (C64)
+        CK(cudaMemcpy2DAsync(C64, p * sizeof(double), h->C64, h->ldc * sizeof(double),
+                             p * sizeof(double), p, cudaMemcpyDefault, s));
+    CK(cudaStreamSynchronize(s));
+    return PC_OK;
+}
+
+// ---------------------------------------------------------------- skeleton
+static pc_status read_info(pc_handle *h)
+{
+    CK(cudaMemcpyAsync(h->info_h, h->g.info, sizeof(LevelInfo), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return PC_OK;
+}
+
+static pc_status reset_info(pc_handle *h)
+{
+    CK(cudaMemsetAsync(h->g.info, 0, sizeof(LevelInfo), h->stream));
+    CK(cudaMemsetAsync(&h->g.info->lstar, 0xff, sizeof(int), h->stream));   // -1
+    return PC_OK;
+}
+
+static pc_status grow_pool(pc_handle *h, long long need)
+{
+    if (need <= h->g.pool_cap) return PC_OK;
+    long long cap = h->g.pool_cap;
+    while (cap < need) cap *= 2;
+    int *np = nullptr;
+    CK(dalloc(h, &np, (size_t)cap * sizeof(int)));
+    CK(cudaMemcpyAsync(np, h->g.pool, (size_t)h->g.pool_cap * sizeof(int), cudaMemcpyDeviceToDevice,
+                       h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    dfree(h, h->g.pool);
+    h->g.pool = np;
+    h->g.pool_cap = cap;
+    return PC_OK;
+}
+
+static pc_status skeleton_run(pc_handle *h, pc_stats *st)
+{
+    GraphDev &g = h->g;
+    cudaStream_t s = h->stream;
+    const int p = h->p;
+    const long long n = h->n;
+    const size_t pp = (size_t)p * p;
+    TestParams tp = make_tp(h);
+    std::memset(st, 0, sizeof(*st));
+    st->first_level = -1;
+
+    // complete graph, empty sepset store
+    std::vector<uint32_t> full((size_t)p * g.W, 0u);
+    for (int u = 0; u < p; ++u)
+        for (int v = 0; v < p; ++v)
+            if (u != v) full[(size_t)u * g.W + (v >> 5)] |= 1u << (v & 31);
+    CK(cudaMemcpyAsync(g.adj, full.data(), full.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(g.best, 0xff, pp * sizeof(ull), s));
+    CK(cudaMemsetAsync(g.sep_level, 0xff, pp * sizeof(int), s));
+    CK(cudaMemsetAsync(g.sep_off, 0xff, pp * sizeof(long long), s));
+    CK(cudaMemsetAsync(g.prec_m, 0, (size_t)p * sizeof(int), s));
+    CK(cudaMemsetAsync(g.prec_pos, 0xff, pp * sizeof(short), s));
+    CK(cudaMemsetAsync(g.prec_need, 0, (size_t)p * sizeof(int), s));
+    CK(cudaMemsetAsync(g.ctr, 0, sizeof(DevCounters), s));
+    CK(cudaStreamSynchronize(s));   // 'full' is pageable host memory
+    CK(cudaEventRecord(h->ev0, s));
+
+    int cap = p - 2;
+    if (h->max_level >= 0 && h->max_level < cap) cap = h->max_level;
+    if (n - 4 < cap) cap = (int)(n - 4);
+    long long opairs = (long long)p * (p - 1);
+
+    if (pc_status r = reset_info(h)) return r;
+    {
+        Timed tm(h, 5);
+        CK(fpc::launch_level_degrees(g, s));
+    }
+    bool stage_a_ran = false;
+    if (h->order == 1 && h->stage_a && n - p - 1 > 0) {
+        if (!h->Pbuf) CK(dalloc(h, &h->Pbuf, (size_t)p * h->ldc * sizeof(double)));
+        CK(cudaMemcpyAsync(h->Pbuf, h->C64, (size_t)p * h->ldc * sizeof(double),
+                           cudaMemcpyDeviceToDevice, s));
+        {
+            Timed tm(h, 1);
+            CK(fpc::launch_inverse_spd(h->Pbuf, p, h->ldc, h->work, h->singular, s));
+            CK(fpc::launch_stage_a_decide(h->Pbuf, p, h->ldc, h->singular, g, tp, s));
+        }
+        {
+            Timed tm(h, 5);
+            CK(fpc::launch_commit(g, tp, p - 2, opairs, 0, s));
+        }
+        int sing = 1;
+        CK(cudaMemcpyAsync(&sing, h->singular, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        stage_a_ran = sing == 0;
+        if (stage_a_ran) {
+            st->levels_run++;
+            CK(cudaMemsetAsync(g.best, 0xff, pp * sizeof(ull), s));
+        }
+        if (pc_status r = reset_info(h)) return r;
+        Timed tm(h, 5);
+        CK(fpc::launch_level_degrees(g, s));
+    }
+    if (pc_status r = read_info(h)) return r;
+    opairs = h->info_h->n_opairs;
+
+    int l;
+    if (h->order == 1) {
+        l = cap;
+        if (stage_a_ran && l > p - 3) l = p - 3;
+        if (h->info_h->lstar < l) l = h->info_h->lstar;
+    } else {
+        l = 0;
+    }
+    const bool use_prec = h->order == 1 && h->complement;
+    while (true) {
+        if (h->order == 1) {
+            if (l < 0) break;
+        } else {
+            if (l > cap || h->info_h->lstar < l) break;
+        }
+        if (st->first_level < 0) st->first_level = l;
+        const long long edges = (long long)(h->info_h->edges / 2);
+        // work of this stage
+        CK(cudaMemsetAsync(&g.info->n_build, 0, sizeof(int), s));
+        if (use_prec) {
+            Timed tm(h, 2);
+            CK(fpc::launch_prec_need(g, tp, l, s));
+            CK(fpc::launch_prec_build(g, h->C64, h->ldc, s));
+        }
+        {
+            Timed tm(h, 5);
+            CK(fpc::launch_level_counts(g, tp, l, opairs, h->scan_ws, s));
+        }
+        if (pc_status r = read_info(h)) return r;
+        const LevelInfo &I = *h->info_h;
+        if (I.saturated || (double)I.total_direct + (double)I.total_comp > h->budget) {
+            return fail(h, PC_ERR_BUDGET,
+                        "stage l=" + std::to_string(l) + " schedules " +
+                            (I.saturated ? std::string(">2^64") :
+                                           std::to_string((double)I.total_direct + (double)I.total_comp)) +
+                            " tests, above the budget");
+        }
+        // room for this stage's sepsets
+        CK(cudaMemcpyAsync(h->ctr_h, g.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (pc_status r = grow_pool(h, (long long)h->ctr_h->pool_len + edges * (long long)l + 16)) return r;
+        if (I.total_direct) {
+            Timed tm(h, 3);
+            CK(fpc::launch_ci_direct(g, tp, l, h->C32, h->C64, h->ldc, s));
+        }
+        if (I.total_comp) {
+            Timed tm(h, 4);
+            CK(fpc::launch_ci_complement(g, tp, l, s));
+        }
+        {
+            Timed tm(h, 5);
+            CK(fpc::launch_commit(g, tp, l, opairs, 1, s));
+            CK(cudaMemsetAsync(g.best, 0xff, pp * sizeof(ull), s));
+        }
+        if (use_prec) {
+            Timed tm(h, 2);
+            CK(fpc::launch_prec_downdate(g, s));
+        }
+        st->levels_run++;
+        if (pc_status r = reset_info(h)) return r;
+        {
+            Timed tm(h, 5);
+            CK(fpc::launch_level_degrees(g, s));
+        }
+        if (pc_status r = read_info(h)) return r;
+        opairs = h->info_h->n_opairs;
+        if (h->order == 1) {
+            int nl = l - 1;
+            if (h->info_h->lstar < nl) nl = h->info_h->lstar;
+            l = nl;
+        } else {
+            ++l;
+        }
+    }
+    CK(cudaEventRecord(h->ev1, s));
+    CK(cudaMemcpyAsync(h->ctr_h, g.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const DevCounters &c = *h->ctr_h;
+    if (c.status) return fail(h, (pc_status)c.status, "device-side error during the skeleton search");
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+    st->tests_executed = c.tests_executed;
+    st->tests_canonical = c.tests_canonical;
+    st->tests_redecided = c.redecided;
+    st->band_hits = c.band_hits;
+    st->guard_hits = c.guard_hits;
+    st->degenerate = c.degenerate;
+    st->complement_tests = c.complement_tests;
+    st->edges_removed = c.edges_removed;
+    st->edges_kept = h->info_h->edges / 2;
+    unsigned int bits = c.max_dz_bits;
+    float mdz;
+    std::memcpy(&mdz, &bits, sizeof(mdz));
+    st->max_abs_dz = mdz;
+    st->t_skeleton_ms = ms;
+    st->flops_class[1] = (double)c.flops_stagea + (stage_a_ran ? 2.0 * (double)p * p * p : 0.0);
+    st->flops_class[2] = (double)c.flops_prec;
+    st->flops_class[3] = (double)c.flops + (double)c.flops64_direct;
+    st->flops_class[4] = (double)c.flops_comp;
+    st->flops = st->flops_class[1] + st->flops_class[2] + st->flops_class[3] + st->flops_class[4];
+    st->stage_a_ran = stage_a_ran ? 1 : 0;
+    return PC_OK;
+}
+
+extern "C" pc_status pc_skeleton(pc_handle *h, uint8_t *adj_out, pc_stats *stats)
+{
+    if (!h) return PC_ERR_ARG;
+    if (!h->have_corr) return fail(h, PC_ERR_STATE, "pc_skeleton before pc_corr");
+    pc_stats st;
+    pc_status r = skeleton_run(h, &st);
+    if (r != PC_OK) return r;
+    h->last = st;
+    h->have_skel = true;
+    if (stats) *stats = st;
+    if (adj_out) {
+        const int p = h->p, W = h->g.W;
+        std::vector<uint32_t> bits((size_t)p * W);
+        CK(cudaMemcpy(bits.data(), h->g.adj, bits.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+        std::vector<uint8_t> A((size_t)p * p);
+        for (int u = 0; u < p; ++u)
+            for (int v = 0; v < p; ++v) A[(size_t)u * p + v] = (bits[(size_t)u * W + (v >> 5)] >> (v & 31)) & 1u;
+        CK(cudaMemcpy(adj_out, A.data(), A.size(), cudaMemcpyDefault));
+    }
+    return PC_OK;
+}
+
+extern "C" pc_status pc_sepsets_count(pc_handle *h, int64_t *n_removed, int64_t *pool_len)
+{
+    if (!h) return PC_ERR_ARG;
+    if (!h->have_skel) return fail(h, PC_ERR_STATE, "no skeleton yet");
+    const int p = h->p;
+    std::vector<int> lv((size_t)p * p);
+    CK(cudaMemcpy(lv.data(), h->g.sep_level, lv.size() * sizeof(int), cudaMemcpyDeviceToHost));
+    long long cnt = 0;
+    for (int a = 0; a < p; ++a)
+        for (int b = a + 1; b < p; ++b) cnt += lv[(size_t)a * p + b] >= 0;
+    if (n_removed) *n_removed = cnt;
+    if (pool_len) {
+        ull pl = 0;
+        CK(cudaMemcpy(&pl, &h->g.ctr->pool_len, sizeof(ull), cudaMemcpyDeviceToHost));
+        *pool_len = (int64_t)pl;
+    }
+    return PC_OK;
+}
+
+extern "C" pc_status pc_sepsets_get(pc_handle *h, int32_t *pairs, int32_t *level, int32_t *side,
+                                    int64_t *rank, int64_t *off, int32_t *pool)
+{
+    if (!h) return PC_ERR_ARG;
+    if (!h->have_skel) return fail(h, PC_ERR_STATE, "no skeleton yet");
+    const int p = h->p;
+    const size_t pp = (size_t)p * p;
+    std::vector<int> lv(pp), sd(pp);
+    std::vector<long long> rk(pp), of(pp);
+    CK(cudaMemcpy(lv.data(), h->g.sep_level, pp * sizeof(int), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(sd.data(), h->g.sep_side, pp * sizeof(int), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(rk.data(), h->g.sep_rank, pp * sizeof(long long), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(of.data(), h->g.sep_off, pp * sizeof(long long), cudaMemcpyDeviceToHost));
+    long long k = 0;
+    for (int a = 0; a < p; ++a)
+        for (int b = a + 1; b < p; ++b) {
+            size_t e = (size_t)a * p + b;
+            if (lv[e] < 0) continue;
+            if (pairs) { pairs[2 * k] = a; pairs[2 * k + 1] = b; }
+            if (level) level[k] = lv[e];
+            if (side) side[k] = sd[e];
+            if (rank) rank[k] = rk[e];
+            if (off) off[k] = of[e];
+            ++k;
+        }
+    if (pool) {
+        ull pl = 0;
+        CK(cudaMemcpy(&pl, &h->g.ctr->pool_len, sizeof(ull), cudaMemcpyDeviceToHost));
+        if (pl) CK(cudaMemcpy(pool, h->g.pool, (size_t)pl * sizeof(int), cudaMemcpyDeviceToHost));
+    }
+    return PC_OK;
+}
+
+// ---------------------------------------------------------------- raw tests
+extern "C" pc_status pc_ci_batch(pc_handle *h, const int32_t *ij, const int32_t *S, int32_t l,
+                                 int64_t b, double *r_out, uint8_t *indep_out, float *z_out)
+{
+    if (!h) return PC_ERR_ARG;
+    if (!h->have_corr) return fail(h, PC_ERR_STATE, "pc_ci_batch before pc_corr");
+    if (l < 0 || l > h->p - 2 || l > 126 || b < 0 || !ij || (l > 0 && !S))
+        return fail(h, PC_ERR_ARG, "pc_ci_batch: bad l, b or pointers");
+    if (h->n - l - 3 <= 0) return fail(h, PC_ERR_DOF, "n - l - 3 <= 0");
+    if (b == 0) return PC_OK;
+    cudaStream_t s = h->stream;
+    TestParams tp = make_tp(h);
+    CK(cudaMemsetAsync(h->g.ctr, 0, sizeof(DevCounters), s));
+    CK(fpc::launch_ci_list(ij, S, l, b, h->C32, h->C64, h->ldc, h->p, tp, r_out, indep_out, z_out,
+                           h->g.ctr, s));
+    CK(cudaMemcpyAsync(h->ctr_h, h->g.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (h->ctr_h->status)
+        return fail(h, (pc_status)h->ctr_h->status, "pc_ci_batch: node id out of range or u == v");
+    std::memset(&h->last, 0, sizeof(h->last));
+    h->last.tests_executed = h->ctr_h->tests_executed;
+    h->last.tests_redecided = h->ctr_h->redecided;
+    h->last.band_hits = h->ctr_h->band_hits;
+    h->last.guard_hits = h->ctr_h->guard_hits;
+    h->last.degenerate = h->ctr_h->degenerate;
+    return PC_OK;
+}
+
+extern "C" pc_status pc_last_stats(pc_handle *h, pc_stats *out)
+{
+    if (!h || !out) return PC_ERR_ARG;
+    *out = h->last;
+    return PC_OK;
+}

@@ -1,0 +1,132 @@
+// internal.h -- device-state layouts and launch wrappers shared by the
+// translation units of libfastpc (not part of the public C-ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace fpc {
+
+constexpr unsigned long long KEY_NONE = ~0ull;
+constexpr double DEGEN = 1e-12;        // degeneracy floor on conditional variances
+constexpr int MAXP = 4096;             // largest p a handle accepts
+constexpr int KC_MAX = 8;              // largest dropped-set size of the complement path
+constexpr int PREC_MAX = 168;          // largest neighbourhood (|adj(u)|+1) kept as a precision block
+
+// Device counters (one per handle), reset per pc_skeleton call.
+struct DevCounters {
+    unsigned long long tests_executed;
+    unsigned long long tests_canonical;
+    unsigned long long redecided;
+    unsigned long long band_hits;
+    unsigned long long guard_hits;
+    unsigned long long degenerate;
+    unsigned long long complement_tests;
+    unsigned long long edges_removed;
+    unsigned long long pool_len;       // sepset pool fill
+    unsigned long long flops;          // FP32 direct-test arithmetic (2 per FMA)
+    unsigned long long flops64_direct; // FP64 direct tests (re-decisions or FP64 mode)
+    unsigned long long flops_comp;     // complement tests (FP64)
+    unsigned long long flops_prec;     // neighbourhood precision builds and downdates (FP64)
+    unsigned long long flops_stagea;   // closed-form stage l = p-2 (FP64)
+    unsigned int max_dz_bits;          // float bits of max |z32 - z64|
+    int status;                        // device-side error (pc_status value)
+};
+
+// Per-stage scalars produced on the device and read back by the host.
+struct LevelInfo {
+    int l;                              // stage being run
+    int lstar;                          // max |adj(u)\{v}| over adjacent ordered pairs
+    long long n_opairs;                 // adjacent ordered pairs
+    unsigned long long total_direct;    // tests scheduled on the direct path
+    unsigned long long total_comp;      // tests scheduled on the complement path
+    unsigned long long edges;           // unordered edges
+    int n_build;                        // neighbourhood precision blocks to build
+    int saturated;                      // a test count saturated 2^64
+    long long pad[2];
+};
+
+// Everything the stage kernels need, by value.
+struct GraphDev {
+    int p;
+    int W;                      // 32-bit words per adjacency row
+    uint32_t *adj;              // p x W bitset
+    int *deg;                   // p
+    int *nbr;                   // p x p, ascending neighbour ids of the frozen graph
+    long long *ooff;            // p+1, exclusive scan of deg (ordered-pair offsets)
+    unsigned long long *tcnt;   // n_opairs+1: direct tests per ordered pair, scanned in place
+    unsigned long long *ccnt;   // n_opairs+1: complement tests per ordered pair, scanned
+    unsigned long long *best;   // p x p, best (side<<62 | rank) per unordered pair (a<b at a*p+b)
+    const unsigned long long *binom;   // (p+1) x (p+1) saturating binomials
+    int *sep_level;             // p x p (a<b at a*p+b), -1 none
+    int *sep_side;
+    long long *sep_rank;
+    long long *sep_off;
+    int *pool;                  // explicit sepsets
+    long long pool_cap;
+    // neighbourhood precision blocks (reversed order, complement path)
+    double *prec;               // p x PREC_MAX x PREC_MAX
+    int *prec_m;                // p: block size (0 = invalid)
+    int *prec_mem;              // p x PREC_MAX: member node ids (ascending, u included)
+    short *prec_pos;            // p x p: slot of node w in block u, -1 = absent/dead
+    int *prec_need;             // p: build request flags
+    LevelInfo *info;
+    DevCounters *ctr;
+};
+
+struct TestParams {
+    long long n;        // samples
+    double q;           // threshold Phi^{-1}(1-alpha/2)
+    float qf;
+    double band;        // |z - q| band for FP64 re-decision
+    double guard;       // pivot guard
+    int precision;      // 0 fp64, 1/2 fp32 tests with FP64 re-decision
+    int reversed;
+    int complement;
+};
+
+// counts kernel launches (defined in fastpc_api.cu)
+void note_launch();
+
+// ---- correlation (corr.cu)
+cudaError_t launch_col_stats(const void *X, int dtype, long long n, int p, long long ld,
+                             double *mean, double *rsd, cudaStream_t s);
+cudaError_t launch_standardize(const void *X, int dtype, long long n, int p, long long ld,
+                               const double *mean, const double *rsd, double *Xs64,
+                               float *Xs32, uint16_t *Xhi, uint16_t *Xlo, long long ldk,
+                               cudaStream_t s);
+cudaError_t launch_syrk_f64(const double *Xs, long long n, long long ldk, int p, double *C64,
+                            int ldc, cudaStream_t s);
+cudaError_t launch_syrk_f32(const float *Xs, long long n, long long ldk, int p, float *C32,
+                            int ldc, cudaStream_t s);
+cudaError_t launch_cast_c(const double *C64, float *C32, int p, int ldc, cudaStream_t s);
+bool tc_gemm_available();
+cudaError_t launch_corr_bf16x3(const uint16_t *Xhi, const uint16_t *Xlo, long long n,
+                               long long ldk, int p, float *C32, int ldc, float *ws,
+                               cudaStream_t s);
+
+// ---- stage l = p-2 (stage_a.cu)
+cudaError_t launch_inverse_spd(double *A, int m, int lda, double *work, int *singular,
+                               cudaStream_t s);
+cudaError_t launch_stage_a_decide(const double *P, int p, int ldp, const int *singular,
+                                  GraphDev g, TestParams tp, cudaStream_t s);
+
+// ---- stage kernels (level.cu)
+cudaError_t launch_level_degrees(GraphDev g, cudaStream_t s);
+cudaError_t launch_prec_need(GraphDev g, TestParams tp, int l, cudaStream_t s);
+cudaError_t launch_level_counts(GraphDev g, TestParams tp, int l, long long n_opairs,
+                                void *scan_ws, cudaStream_t s);
+cudaError_t launch_ci_direct(GraphDev g, TestParams tp, int l, const float *C32,
+                             const double *C64, int ldc, cudaStream_t s);
+cudaError_t launch_ci_complement(GraphDev g, TestParams tp, int l, cudaStream_t s);
+cudaError_t launch_prec_build(GraphDev g, const double *C64, int ldc, cudaStream_t s);
+cudaError_t launch_commit(GraphDev g, TestParams tp, int l, long long n_opairs,
+                          int explicit_sets, cudaStream_t s);
+cudaError_t launch_prec_downdate(GraphDev g, cudaStream_t s);
+size_t scan_ws_bytes(long long n);
+
+// ---- raw test batches (level.cu)
+cudaError_t launch_ci_list(const int *ij, const int *S, int l, long long b, const float *C32,
+                           const double *C64, int ldc, int p, TestParams tp, double *r_out,
+                           uint8_t *indep_out, float *z_out, DevCounters *ctr, cudaStream_t s);
+
+}  // namespace fpc

@@ -1,0 +1,292 @@
+"""Thin ctypes binding of include/fastpc.h (argument marshalling only).
+
+Every computation runs inside libfastpc.so (CUDA, sm_103a).  PyTorch supplies
+device memory and streams.  There is no CPU fallback: if the library is
+missing or cannot load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfastpc.so")
+
+PC_F32, PC_F64 = 0, 1
+STATUS = ["PC_OK", "PC_ERR_ARG", "PC_ERR_CUDA", "PC_ERR_OOM", "PC_ERR_STATE", "PC_ERR_DOF",
+          "PC_ERR_BUDGET", "PC_ERR_TIMEOUT", "PC_ERR_INTERNAL"]
+
+
+class PCError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        self.status = status
+        name = STATUS[status] if 0 <= status < len(STATUS) else str(status)
+        super().__init__(f"{name}: {msg}")
+
+
+class pc_stats(ctypes.Structure):
+    _fields_ = [
+        ("tests_executed", ctypes.c_uint64),
+        ("tests_canonical", ctypes.c_uint64),
+        ("tests_redecided", ctypes.c_uint64),
+        ("band_hits", ctypes.c_uint64),
+        ("guard_hits", ctypes.c_uint64),
+        ("degenerate", ctypes.c_uint64),
+        ("complement_tests", ctypes.c_uint64),
+        ("edges_removed", ctypes.c_uint64),
+        ("edges_kept", ctypes.c_uint64),
+        ("max_abs_dz", ctypes.c_double),
+        ("t_skeleton_ms", ctypes.c_double),
+        ("flops", ctypes.c_double),
+        ("flops_class", ctypes.c_double * 6),
+        ("levels_run", ctypes.c_int32),
+        ("stage_a_ran", ctypes.c_int32),
+        ("first_level", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+    ]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        d["flops_class"] = list(self.flops_class)
+        return d
+
+
+_lib = None
+
+
+def load():
+    """Load libfastpc.so (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "paper_2109_04626_gb300.build.build() (nvcc, sm_103a)")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    cs = ctypes.c_char_p
+    sig = {
+        "pc_create": (i32, [i64, i32, dbl, i32, ctypes.POINTER(vp)]),
+        "pc_destroy": (None, [vp]),
+        "pc_set_opt": (i32, [vp, cs, dbl]),
+        "pc_get_opt": (i32, [vp, cs, ctypes.POINTER(dbl)]),
+        "pc_set_stream": (i32, [vp, vp]),
+        "pc_corr": (i32, [vp, vp, i32, i64]),
+        "pc_corr_get": (i32, [vp, vp, vp]),
+        "pc_skeleton": (i32, [vp, vp, ctypes.POINTER(pc_stats)]),
+        "pc_sepsets_count": (i32, [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
+        "pc_sepsets_get": (i32, [vp, vp, vp, vp, vp, vp, vp]),
+        "pc_ci_batch": (i32, [vp, vp, vp, i32, i64, vp, vp, vp]),
+        "pc_last_stats": (i32, [vp, ctypes.POINTER(pc_stats)]),
+        "pc_threshold": (dbl, [vp]),
+        "pc_fisher_threshold": (dbl, [dbl]),
+        "pc_kernel_launches": (i64, []),
+        "pc_timing": (i32, [vp, vp, vp, i32]),
+        "pc_last_error": (cs, [vp]),
+        "pc_status_string": (cs, [i32]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(h, st):
+    if st != 0:
+        msg = load().pc_last_error(h)
+        raise PCError(st, msg.decode() if msg else "")
+
+
+def _ptr(x):
+    """Device pointer of a torch tensor or host pointer of a numpy array."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"]
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+def pc_create(n: int, p: int, alpha: float, max_level: int = -1):
+    h = ctypes.c_void_p()
+    st = load().pc_create(int(n), int(p), float(alpha), int(max_level), ctypes.byref(h))
+    if st != 0:
+        raise PCError(st, "pc_create")
+    return h
+
+
+def pc_destroy(h):
+    load().pc_destroy(h)
+
+
+def pc_set_opt(h, key: str, val: float):
+    _check(h, load().pc_set_opt(h, key.encode(), float(val)))
+
+
+def pc_get_opt(h, key: str) -> float:
+    v = ctypes.c_double()
+    _check(h, load().pc_get_opt(h, key.encode(), ctypes.byref(v)))
+    return v.value
+
+
+def pc_set_stream(h, stream):
+    """stream: torch.cuda.Stream, a raw cudaStream_t int, or None (legacy default)."""
+    raw = 0 if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _check(h, load().pc_set_stream(h, ctypes.c_void_p(raw)))
+
+
+def pc_corr(h, X):
+    """X: n x p row-major (torch CUDA tensor or numpy host array), float32 or float64."""
+    if isinstance(X, np.ndarray):
+        X = np.ascontiguousarray(X)
+        dt = PC_F64 if X.dtype == np.float64 else PC_F32
+        assert X.dtype in (np.float32, np.float64)
+        ld = X.shape[1]
+    else:
+        import torch
+        assert X.dtype in (torch.float32, torch.float64) and X.stride(1) == 1
+        dt = PC_F64 if X.dtype == torch.float64 else PC_F32
+        ld = X.stride(0)
+    _check(h, load().pc_corr(h, ctypes.c_void_p(_ptr(X)), dt, int(ld)))
+
+
+def pc_corr_get(h, p: int):
+    C32 = np.empty((p, p), dtype=np.float32)
+    C64 = np.empty((p, p), dtype=np.float64)
+    _check(h, load().pc_corr_get(h, ctypes.c_void_p(_ptr(C32)), ctypes.c_void_p(_ptr(C64))))
+    return C32, C64
+
+
+def pc_skeleton(h, p: int, adj_out=None):
+    """Returns (adjacency p x p uint8, stats dict).  adj_out may be a device tensor."""
+    st = pc_stats()
+    adj = adj_out if adj_out is not None else np.empty((p, p), dtype=np.uint8)
+    _check(h, load().pc_skeleton(h, ctypes.c_void_p(_ptr(adj)), ctypes.byref(st)))
+    return adj, st.as_dict()
+
+
+def pc_last_stats(h) -> dict:
+    st = pc_stats()
+    _check(h, load().pc_last_stats(h, ctypes.byref(st)))
+    return st.as_dict()
+
+
+def pc_sepsets(h, p: int) -> dict:
+    """{(a, b): (level, side, rank, nodes tuple)} for every removed pair a < b."""
+    lib = load()
+    nr, pl = ctypes.c_int64(), ctypes.c_int64()
+    _check(h, lib.pc_sepsets_count(h, ctypes.byref(nr), ctypes.byref(pl)))
+    k = nr.value
+    pairs = np.empty((max(k, 1), 2), dtype=np.int32)
+    level = np.empty(max(k, 1), dtype=np.int32)
+    side = np.empty(max(k, 1), dtype=np.int32)
+    rank = np.empty(max(k, 1), dtype=np.int64)
+    off = np.empty(max(k, 1), dtype=np.int64)
+    pool = np.empty(max(pl.value, 1), dtype=np.int32)
+    _check(h, lib.pc_sepsets_get(h, *(ctypes.c_void_p(_ptr(a)) for a in (pairs, level, side, rank, off, pool))))
+    out = {}
+    for i in range(k):
+        a, b = int(pairs[i, 0]), int(pairs[i, 1])
+        lv, o = int(level[i]), int(off[i])
+        if o < 0:
+            nodes = tuple(w for w in range(p) if w != a and w != b)
+        else:
+            nodes = tuple(int(x) for x in pool[o:o + lv])
+        out[(a, b)] = (lv, int(side[i]), int(rank[i]), nodes)
+    return out
+
+
+def pc_ci_batch(h, ij, S, l: int, r_out=None, indep_out=None, z_out=None):
+    """ij: (b,2) int32 CUDA tensor, S: (b,l) int32 CUDA tensor.  Returns (r, indep, z) tensors."""
+    import torch
+    b = ij.shape[0]
+    dev = ij.device
+    r = r_out if r_out is not None else torch.empty(b, dtype=torch.float64, device=dev)
+    ind = indep_out if indep_out is not None else torch.empty(b, dtype=torch.uint8, device=dev)
+    z = z_out if z_out is not None else torch.empty(b, dtype=torch.float32, device=dev)
+    Sp = _ptr(S) if (S is not None and l > 0) else None
+    _check(h, load().pc_ci_batch(h, ctypes.c_void_p(_ptr(ij)), ctypes.c_void_p(Sp), int(l), int(b),
+                                 ctypes.c_void_p(_ptr(r)), ctypes.c_void_p(_ptr(ind)),
+                                 ctypes.c_void_p(_ptr(z))))
+    return r, ind, z
+
+
+def pc_threshold(h) -> float:
+    return float(load().pc_threshold(h))
+
+
+def pc_fisher_threshold(alpha: float) -> float:
+    """Phi^{-1}(1 - alpha/2) computed by the library's host code (no GPU needed)."""
+    return float(load().pc_fisher_threshold(float(alpha)))
+
+
+def pc_kernel_launches() -> int:
+    return int(load().pc_kernel_launches())
+
+
+TIMING_CLASSES = ["corr", "stage_a", "prec", "ci_direct", "ci_complement", "bookkeeping"]
+
+
+def pc_timing(h, reset: bool = False) -> dict:
+    """Per-kernel-class device ms and launch-group counts (option "timing" = 1)."""
+    ms = np.zeros(6, dtype=np.float64)
+    cnt = np.zeros(6, dtype=np.int64)
+    _check(h, load().pc_timing(h, ctypes.c_void_p(ms.ctypes.data), ctypes.c_void_p(cnt.ctypes.data),
+                               1 if reset else 0))
+    return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(TIMING_CLASSES)}
+
+
+class PC:
+    """Owning wrapper: ``with PC(n, p, alpha, max_level, order=1) as pc: ...``"""
+
+    def __init__(self, n, p, alpha, max_level=-1, **opts):
+        self.n, self.p = int(n), int(p)
+        self.h = pc_create(n, p, alpha, max_level)
+        for k, v in opts.items():
+            pc_set_opt(self.h, k, v)
+
+    def set(self, **opts):
+        for k, v in opts.items():
+            pc_set_opt(self.h, k, v)
+        return self
+
+    def corr(self, X):
+        pc_corr(self.h, X)
+        return self
+
+    def skeleton(self, adj_out=None):
+        return pc_skeleton(self.h, self.p, adj_out)
+
+    def sepsets(self):
+        return pc_sepsets(self.h, self.p)
+
+    def ci_batch(self, ij, S, l):
+        return pc_ci_batch(self.h, ij, S, l)
+
+    def corr_get(self):
+        return pc_corr_get(self.h, self.p)
+
+    @property
+    def threshold(self):
+        return pc_threshold(self.h)
+
+    def close(self):
+        if self.h is not None:
+            pc_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,262 @@
+"""GPU parity: the CUDA path (through the C-ABI) against the FP64 CPU oracle.
+
+Bars (the benchmark spec): partial correlations within 1e-5 absolute, decisions and the
+removed-edge set bit-exact, sepsets (level, side, rank, nodes) identical, and
+the sequential canonical test count equal to the oracle's.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2109_04626_gb300 import sem
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+R_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def fp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2109_04626_gb300 import build
+    from paper_2109_04626_gb300 import fastpc
+    build.build()
+    fastpc.load()
+    return fastpc
+
+
+def _sem_case(seed, p, n, prob, dtype=np.float32):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    dag, W, order = sem.er_dag(p, prob, rng)
+    X = sem.sample(W, order, n, rng).astype(dtype)
+    return np.ascontiguousarray(X)
+
+
+def _run_gpu(fp, X, alpha, max_level, order, precision, complement=1, device_input=True):
+    n, p = X.shape
+    with fp.PC(n, p, alpha, max_level, order=order, precision=precision,
+               complement=complement) as pc:
+        pc.corr(torch.from_numpy(X).cuda() if device_input else X)
+        adj, st = pc.skeleton()
+        seps = pc.sepsets()
+    return adj, st, seps
+
+
+def _check_skeleton(fp, X, alpha=0.01, max_level=-1, order=1, precision=2, complement=1,
+                    device_input=True):
+    n, p = X.shape
+    C = oracle.pearson(X)
+    R = oracle.skeleton(C, n, alpha, max_level, reversed_order=bool(order))
+    adj, st, seps = _run_gpu(fp, X, alpha, max_level, order, precision, complement, device_input)
+    np.testing.assert_array_equal(adj, R["adj"])
+    assert seps == R["sepsets"]
+    assert st["tests_canonical"] == R["tests_total"]
+    assert st["tests_executed"] >= st["tests_canonical"] or st["tests_executed"] > 0 or \
+        R["tests_total"] == 0
+    return R, st
+
+
+# --------------------------------------------------------------------------- correlation
+@pytest.mark.parametrize("precision", [0, 1, 2])
+@pytest.mark.parametrize("shape", [(1000, 20, np.float64), (5000, 95, np.float32),
+                                   (3001, 70, np.float32), (257, 129, np.float64)])
+def test_corr_matches_oracle(fp, precision, shape):
+    n, p, dt = shape
+    X = _sem_case(11 + p, p, n, 0.2, dt)
+    with fp.PC(n, p, 0.01, -1, precision=precision) as pc:
+        pc.corr(torch.from_numpy(X).cuda())
+        C32, C64 = pc.corr_get()
+    Co = oracle.pearson(X)
+    assert np.abs(C64 - Co).max() <= 1e-12
+    assert np.abs(C32.astype(np.float64) - Co).max() <= 2e-6
+    assert np.all(np.diag(C32) == 1.0) and np.all(np.diag(C64) == 1.0)
+
+
+def test_corr_host_input_equals_device_input(fp):
+    X = _sem_case(5, 40, 2000, 0.3)
+    n, p = X.shape
+    with fp.PC(n, p, 0.01) as pc:
+        pc.corr(X)
+        A32, A64 = pc.corr_get()
+        pc.corr(torch.from_numpy(X).cuda())
+        B32, B64 = pc.corr_get()
+    np.testing.assert_array_equal(A64, B64)
+    np.testing.assert_array_equal(A32, B32)
+
+
+# --------------------------------------------------------------------------- raw CI tests
+def _random_tests(rng, p, l, b):
+    ij = np.empty((b, 2), dtype=np.int32)
+    S = np.empty((b, max(l, 1)), dtype=np.int32)
+    for k in range(b):
+        nodes = rng.choice(p, size=l + 2, replace=False)
+        ij[k] = nodes[:2]
+        S[k, :l] = np.sort(nodes[2:])
+    return ij, S[:, :l].copy()
+
+
+@pytest.mark.parametrize("precision", [0, 2])
+@pytest.mark.parametrize("case", ["p95_dense", "p20_fp64", "er_moderate"])
+def test_ci_batch_parity(fp, precision, case):
+    if case == "p95_dense":
+        s = sem.make(2)
+        X = s.X
+        levels = [0, 1, 2, 3, 5, 8, 13, 21, 34, 55, 80, 93]
+    elif case == "p20_fp64":
+        X = sem.make(1).X
+        levels = [0, 1, 2, 4, 7, 11, 18]
+    else:
+        X = _sem_case(77, 200, 4000, 0.03)
+        levels = [0, 1, 2, 3, 4, 6, 9, 14, 20, 31, 50]
+    n, p = X.shape
+    C = oracle.pearson(X)
+    q = oracle.threshold(0.01)
+    rng = np.random.default_rng(2024)
+    with fp.PC(n, p, 0.01, -1, precision=precision) as pc:
+        pc.corr(torch.from_numpy(X).cuda())
+        for l in levels:
+            b = 257
+            ij, S = _random_tests(rng, p, l, b)
+            r, ind, z = pc.ci_batch(torch.from_numpy(ij).cuda(), torch.from_numpy(S).cuda(), l)
+            r = r.cpu().numpy()
+            ind = ind.cpu().numpy().astype(bool)
+            z = z.cpu().numpy()
+            ro, zo, io, do = oracle.ci_batch(C, n, 0.01, ij, S)
+            assert np.abs(r - ro).max() <= R_TOL, (l, np.abs(r - ro).max())
+            clear = np.abs(zo - q) > 1e-9
+            np.testing.assert_array_equal(ind[clear], io[clear])
+
+
+def test_ci_batch_errors(fp):
+    X = _sem_case(3, 12, 10, 0.3)
+    n, p = X.shape                                     # n = 10, p = 12
+    with fp.PC(n, p, 0.01) as pc:
+        pc.corr(torch.from_numpy(X).cuda())
+        ij = torch.tensor([[0, 1]], dtype=torch.int32, device="cuda")
+        S = torch.arange(2, 12, dtype=torch.int32, device="cuda").reshape(1, 10)
+        with pytest.raises(fp.PCError) as e:           # l = 11 > p - 2
+            pc.ci_batch(ij, torch.zeros((1, 11), dtype=torch.int32, device="cuda"), 11)
+        assert e.value.status == 1
+        with pytest.raises(fp.PCError) as e:           # n - l - 3 = 0: Fisher z undefined
+            pc.ci_batch(ij, S[:, :7].contiguous(), 7)
+        assert e.value.status == 5
+        bad = torch.tensor([[0, 99]], dtype=torch.int32, device="cuda")
+        with pytest.raises(fp.PCError) as e:           # node id out of range
+            pc.ci_batch(bad, S[:, :1].contiguous(), 1)
+        assert e.value.status == 1
+        same = torch.tensor([[4, 4]], dtype=torch.int32, device="cuda")
+        with pytest.raises(fp.PCError) as e:           # u == v
+            pc.ci_batch(same, S[:, :1].contiguous(), 1)
+        assert e.value.status == 1
+        r, ind, z = pc.ci_batch(ij, S[:, :2].contiguous(), 2)    # the handle still works
+        assert r.shape == (1,)
+
+
+# --------------------------------------------------------------------------- skeletons
+@pytest.mark.parametrize("order", [1, 0])
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_skeleton_p20_fp64(fp, order, precision):
+    _check_skeleton(fp, sem.make(1).X, order=order, precision=precision)
+
+
+@pytest.mark.parametrize("complement", [1, 0])
+@pytest.mark.parametrize("precision", [0, 2])
+def test_skeleton_p95_dense_reversed(fp, complement, precision):
+    R, st = _check_skeleton(fp, sem.make(2).X, order=1, precision=precision,
+                            complement=complement)
+    assert st["stage_a_ran"] == 1
+    if complement:
+        assert st["complement_tests"] > 0
+
+
+def test_skeleton_p95_dense_conventional(fp):
+    _check_skeleton(fp, sem.make(2).X, order=0, precision=2)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_skeleton_random_small(fp, seed):
+    rng = np.random.default_rng(seed)
+    p = int(rng.integers(5, 70))
+    n = int(rng.integers(p + 10, 3000))
+    X = _sem_case(300 + seed, p, n, float(rng.uniform(0.05, 0.5)))
+    for order in (1, 0):
+        _check_skeleton(fp, X, alpha=float(rng.choice([0.01, 0.05, 1e-3])), order=order,
+                        precision=int(rng.integers(0, 3)))
+
+
+@pytest.mark.parametrize("max_level", [0, 1, 3])
+@pytest.mark.parametrize("order", [1, 0])
+def test_skeleton_max_level(fp, max_level, order):
+    X = _sem_case(41, 30, 1500, 0.3)
+    _check_skeleton(fp, X, max_level=max_level, order=order)
+
+
+def test_skeleton_edge_cases(fp):
+    # two and three variables
+    for p in (2, 3):
+        X = _sem_case(50 + p, p, 200, 0.9)
+        for order in (1, 0):
+            _check_skeleton(fp, X, order=order)
+    # few samples: stages capped at n - 4, stage l=p-2 skipped when n - p - 1 <= 0
+    X = _sem_case(61, 12, 9, 0.4)
+    for order in (1, 0):
+        _check_skeleton(fp, X, order=order, precision=0)
+    # an empty graph (independent columns) and a ragged p not a multiple of 32
+    X = np.random.default_rng(3).standard_normal((800, 37)).astype(np.float32)
+    for order in (1, 0):
+        _check_skeleton(fp, X, order=order)
+
+
+def test_skeleton_degenerate_duplicate_column(fp):
+    X = _sem_case(71, 15, 1200, 0.3, np.float64)
+    X[:, 9] = X[:, 4]                                  # exactly collinear pair
+    R, st = _check_skeleton(fp, X, order=0, precision=0)
+    assert st["degenerate"] > 0 or R["degenerate"] == 0
+
+
+def test_skeleton_host_buffers(fp):
+    X = sem.make(1).X
+    _check_skeleton(fp, X, device_input=False)
+
+
+def test_skeleton_on_torch_stream(fp):
+    X = sem.make(1).X
+    n, p = X.shape
+    C = oracle.pearson(X)
+    R = oracle.skeleton(C, n, 0.01, -1, True)
+    s = torch.cuda.Stream()
+    with fp.PC(n, p, 0.01) as pc:
+        fp.pc_set_stream(pc.h, s)
+        Xd = torch.from_numpy(X).cuda()
+        s.wait_stream(torch.cuda.current_stream())
+        pc.corr(Xd)
+        adj_d = torch.empty((p, p), dtype=torch.uint8, device="cuda")
+        pc.skeleton(adj_d)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(adj_d.cpu().numpy(), R["adj"])
+
+
+def test_repeated_calls_reuse_handle(fp):
+    X = _sem_case(81, 25, 900, 0.3)
+    n, p = X.shape
+    C = oracle.pearson(X)
+    R = oracle.skeleton(C, n, 0.01, -1, True)
+    with fp.PC(n, p, 0.01) as pc:
+        for _ in range(3):
+            pc.corr(torch.from_numpy(X).cuda())
+            adj, st = pc.skeleton()
+            np.testing.assert_array_equal(adj, R["adj"])
+            assert pc.sepsets() == R["sepsets"]
+
+
+# --------------------------------------------------------------------------- full-size workloads
+@pytest.mark.parametrize("cfg", [3, 4])
+def test_full_size_conventional(fp, cfg):
+    """p=500 power law (levels <= 8) and p=1000 ER, conventional order (Algorithm 1)."""
+    w = sem.WORKLOADS[cfg]
+    X = sem.make(cfg).X
+    _check_skeleton(fp, X, alpha=w["alpha"], max_level=w["max_level"], order=0, precision=2)

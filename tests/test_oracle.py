@@ -27,9 +27,10 @@ def test_norm_ppf_matches_library():
 def test_threshold_known_values():
     # Phi^{-1}(1 - alpha/2) for the alphas the paper uses (Sec. 6: 1e-3, 1e-4, 1e-6)
     # and the workloads' 0.01; cross-checked against the error function: Phi(q) = 1 - alpha/2.
-    for a in [0.01, 1e-3, 1e-4, 1e-6]:
+    for a in [0.01, 1e-3, 1e-4, 1e-6, 1e-10]:
         q = oracle.threshold(a)
         assert 0.5 * math.erfc(q / math.sqrt(2.0)) == pytest.approx(a / 2, rel=1e-12)
+        assert q == pytest.approx(-statistics.NormalDist().inv_cdf(a / 2), rel=1e-13)
 
 
 def test_paper_printed_threshold():
