@@ -150,6 +150,113 @@ __global__ void __launch_bounds__(256) syrk_kernel(const T *__restrict__ Xs, lon
         }
 }
 
+// Split-K FP64 Gram: CTA (tile, split) accumulates K range
+// [split*kchunk, min(n, (split+1)*kchunk)) of an upper-triangle 64x64 tile into
+// ws[(split*ntiles + tile)][64][64]; syrk_reduce_kernel then adds the splits
+// in a fixed order (deterministic), scales by 1/n, mirrors, sets the diagonal.
+__global__ void __launch_bounds__(256) syrk_f64_split_kernel(const double *__restrict__ Xs, long long n,
+                                                             long long ldk, int p, long long kchunk,
+                                                             double *ws)
+{
+    constexpr int BT = 64, BK = 32;
+    __shared__ double As[BK][BT + 1];
+    __shared__ double Bs[BK][BT + 1];
+    const int tile = blockIdx.x, nt = (p + BT - 1) / BT;
+    int t = tile, bi = 0;
+    while (t >= nt - bi) { t -= nt - bi; ++bi; }
+    const int bj = bi + t;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int a0 = bi * BT, b0 = bj * BT;
+    const long long kb = (long long)blockIdx.y * kchunk;
+    const long long ke = kb + kchunk < n ? kb + kchunk : n;
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (long long k0 = kb; k0 < ke; k0 += BK) {
+        for (int e = threadIdx.x; e < BT * BK; e += 256) {
+            int r = e / BK, k = e % BK;
+            long long kk = k0 + k;
+            int ra = a0 + r, rb = b0 + r;
+            As[k][r] = (ra < p && kk < ke) ? Xs[(long long)ra * ldk + kk] : 0.0;
+            Bs[k][r] = (rb < p && kk < ke) ? Xs[(long long)rb * ldk + kk] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int k = 0; k < BK; ++k) {
+            double av[4], bv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) av[i] = As[k][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) bv[j] = Bs[k][tx * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+    double *out = ws + ((size_t)blockIdx.y * gridDim.x + tile) * (BT * BT);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) out[(ty * 4 + i) * BT + tx * 4 + j] = acc[i][j];
+}
+
+__global__ void __launch_bounds__(256) syrk_reduce_kernel(const double *ws, int p, int ntiles_total,
+                                                          int splits, long long n, double *C, int ldc)
+{
+    constexpr int BT = 64;
+    const int tile = blockIdx.x, nt = (p + BT - 1) / BT;
+    int t = tile, bi = 0;
+    while (t >= nt - bi) { t -= nt - bi; ++bi; }
+    const int bj = bi + t;
+    const double inv_n = 1.0 / (double)n;
+    for (int e = threadIdx.x; e < BT * BT; e += blockDim.x) {
+        const int r = e / BT, c = e % BT;
+        const int a = bi * BT + r, b = bj * BT + c;
+        if (a >= p || b >= p || (bi == bj && r > c)) continue;
+        double sum = 0.0;
+        for (int sp = 0; sp < splits; ++sp) sum += ws[((size_t)sp * ntiles_total + tile) * (BT * BT) + e];
+        const double v = a == b ? 1.0 : sum * inv_n;
+        C[(long long)a * ldc + b] = v;
+        C[(long long)b * ldc + a] = v;
+    }
+}
+
+static int g_sms = 0;
+static int sm_count()
+{
+    if (!g_sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_sms <= 0) g_sms = 148;
+    }
+    return g_sms;
+}
+
+static void syrk_split_shape(long long n, int p, int &ntiles, int &splits, long long &kchunk)
+{
+    const int nt = (p + 63) / 64;
+    ntiles = nt * (nt + 1) / 2;
+    const long long kt = (n + 31) / 32;                   // 32-wide K steps
+    long long sp = (2LL * sm_count() + ntiles - 1) / ntiles;
+    if (sp > kt / 2) sp = kt / 2;
+    if (sp < 1) sp = 1;
+    kchunk = ((kt + sp - 1) / sp) * 32;
+    splits = (int)((n + kchunk - 1) / kchunk);
+}
+
+size_t syrk_f64_ws_bytes(long long n, int p)
+{
+    int ntiles, splits;
+    long long kchunk;
+    syrk_split_shape(n, p, ntiles, splits, kchunk);
+    return (size_t)ntiles * splits * 64 * 64 * sizeof(double);
+}
+
 __global__ void cast_kernel(const double *C64, float *C32, int p, int ldc)
 {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -186,10 +293,14 @@ cudaError_t launch_standardize(const void *X, int dtype, long long n, int p, lon
 }
 
 cudaError_t launch_syrk_f64(const double *Xs, long long n, long long ldk, int p, double *C64,
-                            int ldc, cudaStream_t s)
+                            int ldc, double *ws, size_t ws_bytes, cudaStream_t s)
 {
-    int nt = (p + 63) / 64;
-    syrk_kernel<double, double><<<nt * (nt + 1) / 2, 256, 0, s>>>(Xs, n, ldk, p, C64, ldc); note_launch();
+    int ntiles, splits;
+    long long kchunk;
+    syrk_split_shape(n, p, ntiles, splits, kchunk);
+    if (ws_bytes < (size_t)ntiles * splits * 64 * 64 * sizeof(double)) return cudaErrorInvalidValue;
+    syrk_f64_split_kernel<<<dim3(ntiles, splits), 256, 0, s>>>(Xs, n, ldk, p, kchunk, ws); note_launch();
+    syrk_reduce_kernel<<<ntiles, 256, 0, s>>>(ws, p, ntiles, splits, n, C64, ldc); note_launch();
     return cudaGetLastError();
 }
 

@@ -4,36 +4,39 @@
 
 namespace fpc {
 
-// In-place Gauss-Jordan inversion of an SPD matrix held in shared memory
-// (no row exchanges: the k-th pivot is the conditional variance of k given
-// 0..k-1).  One CTA.  Sets *bad if a pivot is <= DEGEN.
-__device__ __forceinline__ void gj_inverse_block(double *A, int m, int lda, double *colk, double *rowk, int *bad)
+// Symmetric sweep of every pivot of an SPD matrix in shared memory:
+// A <- -A^{-1}.  Pivot k is used without row exchanges, so it equals the
+// conditional variance of k given 0..k-1 (the degeneracy test of the oracle's
+// elimination).  Step k: D = A_kk, A_ij -= A_ik A_kj / D (i, j != k),
+// A_ik = A_ki = A_ik / D, A_kk = -1/D.  The matrix stays symmetric, so each
+// thread updates one upper-triangle entry and mirrors it (m^3/2 FMAs).
+// One CTA, blockDim.x a multiple of 32.  Sets *bad if a pivot is <= DEGEN.
+__device__ __forceinline__ void sweep_inverse_block(double *A, int m, int lda, double *colk, int *bad)
 {
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, ny = blockDim.x >> 5;
     for (int k = 0; k < m; ++k) {
-        const double piv = A[k * lda + k];
-        if (!(piv > DEGEN)) {
+        const double D = A[k * lda + k];
+        if (!(D > DEGEN)) {
             if (threadIdx.x == 0) *bad = 1;
-            return;                                   // uniform: every thread read the same pivot
+            return;                                   // uniform: all threads read the same pivot
         }
-        for (int i = threadIdx.x; i < m; i += blockDim.x) {
-            colk[i] = A[i * lda + k];
-            rowk[i] = A[k * lda + i];
-        }
+        for (int i = threadIdx.x; i < m; i += blockDim.x) colk[i] = A[i * lda + k];
         __syncthreads();
-        const double ip = 1.0 / piv;
-        const int tot = m * m;
-        for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-            int i = e / m, j = e - i * m;
-            double v;
-            if (i == k) v = (j == k) ? ip : rowk[j] * ip;
-            else if (j == k) v = -colk[i] * ip;
-            else v = A[i * lda + j] - colk[i] * rowk[j] * ip;
-            A[i * lda + j] = v;
+        const double iD = 1.0 / D;
+        for (int i = ty; i < m; i += ny) {
+            const double ci = colk[i] * iD;
+            for (int j = i + tx; j < m; j += 32) {
+                double v;
+                if (i == k) v = (j == k) ? -iD : colk[j] * iD;
+                else if (j == k) v = ci;
+                else v = fma(-ci, colk[j], A[i * lda + j]);
+                A[i * lda + j] = v;
+                A[j * lda + i] = v;
+            }
         }
         __syncthreads();
     }
 }
-
 
 // Lexicographic unranking: positions pos[0..l) (ascending, in 0..d-1) of the
 // rank-th l-subset of d items; the number of subsets whose i-th position is x

@@ -50,6 +50,8 @@ struct pc_handle {
     uint16_t *Xhi = nullptr, *Xlo = nullptr;
     double *C64 = nullptr, *Pbuf = nullptr, *work = nullptr;
     float *C32 = nullptr, *tc_ws = nullptr;
+    size_t tc_ws_bytes = 0;
+    int *tc_err = nullptr;
     int *singular = nullptr;
     void *Xstage = nullptr;
     size_t Xstage_bytes = 0;
@@ -59,7 +61,6 @@ struct pc_handle {
     GraphDev g{};
     ull *binom = nullptr;
     long long opair_cap = 0;
-    void *scan_ws = nullptr;
     LevelInfo *info_h = nullptr;     // pinned mirror
     DevCounters *ctr_h = nullptr;    // pinned mirror
     ull *sepcnt_h = nullptr;
@@ -67,6 +68,16 @@ struct pc_handle {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     pc_stats last{};
     std::vector<void *> allocs;
+    // captured stage loop (CUDA graph with a conditional WHILE node)
+    int use_graph = 1;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    cudaGraphConditionalHandle hcond = 0;
+    std::vector<double> graph_key;
+    long long body_kernels = 0;      // kernel nodes in the captured stage body
+    double *syrk_ws = nullptr;
+    size_t syrk_ws_bytes = 0;
     // per-kernel-class timing
     int timing = 0;
     std::vector<TimedPair> pending;
@@ -93,14 +104,14 @@ struct Timed {
     }
     Timed(pc_handle *h_, int c) : h(h_), cls(c)
     {
-        if (!h->timing) return;
+        if (!h->timing || cls < 0) return;
         a = get(h);
         b = get(h);
         cudaEventRecord(a, h->stream);
     }
     ~Timed()
     {
-        if (!h->timing) return;
+        if (!h->timing || cls < 0) return;
         cudaEventRecord(b, h->stream);
         h->pending.push_back({cls, a, b});
     }
@@ -183,6 +194,7 @@ static TestParams make_tp(const pc_handle *h)
     tp.qf = (float)h->q;
     tp.band = h->band;
     tp.guard = h->guard;
+    tp.eps_c = h->used_tc ? 1.0e-6f : 1.2e-7f;
     tp.precision = h->precision;
     tp.reversed = h->order == 1;
     tp.complement = h->complement;
@@ -217,16 +229,15 @@ extern "C" pc_status pc_create(int64_t n, int32_t p, double alpha, int32_t max_l
     A(dalloc(h, &g.nbr, pp * sizeof(int)));
     A(dalloc(h, &g.ooff, (size_t)(p + 1) * sizeof(long long)));
     h->opair_cap = (long long)p * (p - 1);
-    A(dalloc(h, &g.tcnt, (size_t)(h->opair_cap + 2) * sizeof(ull)));
-    A(dalloc(h, &g.ccnt, (size_t)(h->opair_cap + 2) * sizeof(ull)));
-    A(dalloc(h, &h->scan_ws, fpc::scan_ws_bytes(h->opair_cap)));
+    A(dalloc(h, &g.tn_off, (size_t)(p + 2) * sizeof(ull)));
+    A(dalloc(h, &g.cn_off, (size_t)(p + 2) * sizeof(ull)));
     A(dalloc(h, &g.best, pp * sizeof(ull)));
     A(dalloc(h, &h->binom, (size_t)(p + 1) * (p + 1) * sizeof(ull)));
     A(dalloc(h, &g.sep_level, pp * sizeof(int)));
     A(dalloc(h, &g.sep_side, pp * sizeof(int)));
     A(dalloc(h, &g.sep_rank, pp * sizeof(long long)));
     A(dalloc(h, &g.sep_off, pp * sizeof(long long)));
-    g.pool_cap = std::max<long long>(1 << 16, 4ll * p * p);
+    g.pool_cap = std::max<long long>(1 << 20, 16ll * p * p);
     A(dalloc(h, &g.pool, (size_t)g.pool_cap * sizeof(int)));
     A(dalloc(h, &g.prec, (size_t)p * fpc::PREC_MAX * fpc::PREC_MAX * sizeof(double)));
     A(dalloc(h, &g.prec_m, (size_t)p * sizeof(int)));
@@ -240,9 +251,11 @@ extern "C" pc_status pc_create(int64_t n, int32_t p, double alpha, int32_t max_l
     A(dalloc(h, &h->C64, (size_t)p * h->ldc * sizeof(double)));
     A(dalloc(h, &h->C32, (size_t)p * h->ldc * sizeof(float)));
     A(dalloc(h, &h->singular, sizeof(int)));
+    A(dalloc(h, &h->tc_err, sizeof(int)));
     A(dalloc(h, &h->work, (size_t)(2 * p + 16) * sizeof(double)));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&h->info_h, sizeof(LevelInfo));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&h->ctr_h, sizeof(DevCounters));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreate(&h->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&h->ev1);
     if (e != cudaSuccess) {
@@ -286,6 +299,9 @@ extern "C" void pc_destroy(pc_handle *h)
         cudaEventDestroy(t.b);
     }
     for (auto e : h->evpool) cudaEventDestroy(e);
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     delete h;
 }
 
@@ -310,6 +326,7 @@ extern "C" pc_status pc_set_opt(pc_handle *h, const char *key, double val)
         h->guard = val;
     } else if (k == "complement") h->complement = val != 0;
     else if (k == "timing") h->timing = val != 0;
+    else if (k == "graph") h->use_graph = val != 0;
     else if (k == "budget") {
         if (!(val > 0)) return fail(h, PC_ERR_ARG, "budget must be > 0");
         h->budget = val;
@@ -328,6 +345,7 @@ extern "C" pc_status pc_get_opt(pc_handle *h, const char *key, double *val)
     else if (k == "guard") *val = h->guard;
     else if (k == "complement") *val = h->complement;
     else if (k == "timing") *val = h->timing;
+    else if (k == "graph") *val = h->use_graph;
     else if (k == "budget") *val = h->budget;
     else if (k == "tensor_core_gemm") *val = h->used_tc ? 1.0 : 0.0;
     else return fail(h, PC_ERR_ARG, "unknown option: " + k);
@@ -386,6 +404,17 @@ extern "C" const char *pc_status_string(pc_status s)
 }
 
 // ---------------------------------------------------------------- correlation
+// a bounded wait inside the tensor-core GEMM expired (device-side error word)
+static pc_status check_tc(pc_handle *h)
+{
+    if (!h->used_tc) return PC_OK;
+    int e = 0;
+    CK(cudaMemcpyAsync(&e, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (e) return fail(h, (pc_status)e, "tensor-core correlation GEMM: a bounded wait expired");
+    return PC_OK;
+}
+
 extern "C" pc_status pc_corr(pc_handle *h, const void *X, int32_t dtype, int64_t ld)
 {
     if (!h) return PC_ERR_ARG;
@@ -426,7 +455,14 @@ extern "C" pc_status pc_corr(pc_handle *h, const void *X, int32_t dtype, int64_t
                                h->precision == 1 ? h->Xs32 : nullptr,
                                want_bf16 ? h->Xhi : nullptr, want_bf16 ? h->Xlo : nullptr, h->ldk,
                                s));
-    CK(fpc::launch_syrk_f64(h->Xs64, n, h->ldk, p, h->C64, h->ldc, s));
+    const size_t wsb = fpc::syrk_f64_ws_bytes(n, p);
+    if (wsb > h->syrk_ws_bytes) {
+        dfree(h, h->syrk_ws);
+        h->syrk_ws = nullptr;
+        CK(dalloc(h, &h->syrk_ws, wsb));
+        h->syrk_ws_bytes = wsb;
+    }
+    CK(fpc::launch_syrk_f64(h->Xs64, n, h->ldk, p, h->C64, h->ldc, h->syrk_ws, h->syrk_ws_bytes, s));
     h->used_tc = false;
     if (h->precision == 0) {
         CK(fpc::launch_cast_c(h->C64, h->C32, p, h->ldc, s));
@@ -438,8 +474,16 @@ extern "C" pc_status pc_corr(pc_handle *h, const void *X, int32_t dtype, int64_t
         }
         CK(fpc::launch_syrk_f32(h->Xs32, n, h->ldk, p, h->C32, h->ldc, s));
     } else {
-        if (!h->tc_ws) CK(dalloc(h, &h->tc_ws, (size_t)p * h->ldc * sizeof(float) * 2 + 4096));
-        CK(fpc::launch_corr_bf16x3(h->Xhi, h->Xlo, n, h->ldk, p, h->C32, h->ldc, h->tc_ws, s));
+        const size_t need = fpc::corr_bf16x3_ws_bytes(n, p);
+        if (need > h->tc_ws_bytes) {
+            dfree(h, h->tc_ws);
+            h->tc_ws = nullptr;
+            CK(dalloc(h, &h->tc_ws, need));
+            h->tc_ws_bytes = need;
+        }
+        CK(cudaMemsetAsync(h->tc_err, 0, sizeof(int), s));
+        CK(fpc::launch_corr_bf16x3(h->Xhi, h->Xlo, n, h->ldk, p, h->C32, h->ldc, h->tc_ws,
+                                   h->tc_ws_bytes, h->tc_err, s));
         h->used_tc = true;
     }
     h->have_corr = true;
@@ -460,7 +504,7 @@ extern "C" pc_status pc_corr_get(pc_handle *h, float *C32, double *C64)
         CK(cudaMemcpy2DAsync(C64, p * sizeof(double), h->C64, h->ldc * sizeof(double),
                              p * sizeof(double), p, cudaMemcpyDefault, s));
     CK(cudaStreamSynchronize(s));
-    return PC_OK;
+    return check_tc(h);
 }
 
 // ---------------------------------------------------------------- skeleton
@@ -471,30 +515,115 @@ static pc_status read_info(pc_handle *h)
     return PC_OK;
 }
 
-static pc_status reset_info(pc_handle *h)
+static int level_cap(const pc_handle *h)
 {
-    CK(cudaMemsetAsync(h->g.info, 0, sizeof(LevelInfo), h->stream));
-    CK(cudaMemsetAsync(&h->g.info->lstar, 0xff, sizeof(int), h->stream));   // -1
+    int cap = h->p - 2;
+    if (h->max_level >= 0 && h->max_level < cap) cap = h->max_level;
+    if (h->n - 4 < cap) cap = (int)(h->n - 4);
+    return cap;
+}
+
+// One stage of the loop (every kernel reads l from the device): counts, scan
+// and gate, the CI tests, the PC-stable commit, the next frozen graph, the
+// next l and the loop condition, then the precision blocks of the next stage.
+static pc_status enqueue_level(pc_handle *h, cudaStream_t s, int mmax, bool use_cond, bool timed)
+{
+    GraphDev &g = h->g;
+    TestParams tp = make_tp(h);
+    const bool use_prec = h->order == 1 && h->complement;
+    auto T = [&](int cls) { return Timed(h, timed ? cls : -1); };
+    {
+        auto t = T(5);
+        CK(fpc::launch_head(g, tp, h->budget, mmax, s));
+    }
+    {
+        auto t = T(3);
+        CK(fpc::launch_ci_direct(g, tp, mmax, h->C32, h->C64, h->ldc, s));
+    }
+    if (use_prec) {
+        auto t = T(4);
+        CK(fpc::launch_ci_complement(g, tp, s));
+    }
+    {
+        auto t = T(5);
+        CK(fpc::launch_commit(g, h->opair_cap, -1, 1, s));
+        CK(fpc::launch_level_degrees(g, s));
+        CK(fpc::launch_tail(g, tp, level_cap(h), 0, h->singular, 0, h->hcond, use_cond ? 1 : 0, s));
+    }
+    if (use_prec) {
+        auto t = T(2);
+        CK(fpc::launch_prec_update(g, h->C64, h->ldc, s));
+    }
     return PC_OK;
 }
 
-static pc_status grow_pool(pc_handle *h, long long need)
+static std::vector<double> graph_key(const pc_handle *h)
 {
-    if (need <= h->g.pool_cap) return PC_OK;
-    long long cap = h->g.pool_cap;
-    while (cap < need) cap *= 2;
-    int *np = nullptr;
-    CK(dalloc(h, &np, (size_t)cap * sizeof(int)));
-    CK(cudaMemcpyAsync(np, h->g.pool, (size_t)h->g.pool_cap * sizeof(int), cudaMemcpyDeviceToDevice,
-                       h->stream));
-    CK(cudaStreamSynchronize(h->stream));
-    dfree(h, h->g.pool);
-    h->g.pool = np;
-    h->g.pool_cap = cap;
+    return {(double)h->order, (double)h->complement, (double)h->precision, h->band, h->guard,
+            (double)h->used_tc,
+            h->budget, (double)level_cap(h), (double)(uintptr_t)h->g.pool, (double)h->g.pool_cap,
+            (double)(uintptr_t)h->C32, (double)(uintptr_t)h->C64};
+}
+
+static void drop_graph(pc_handle *h)
+{
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    h->gexec = nullptr;
+    h->graph = nullptr;
+    h->graph_key.clear();
+}
+
+// Capture the stage body once into the body of a conditional WHILE node.
+static pc_status ensure_graph(pc_handle *h)
+{
+    std::vector<double> key = graph_key(h);
+    if (h->gexec && key == h->graph_key) return PC_OK;
+    drop_graph(h);
+    CK(cudaGraphCreate(&h->graph, 0));
+    CK(cudaGraphConditionalHandleCreate(&h->hcond, h->graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h->hcond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, h->graph, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    CK(cudaStreamBeginCaptureToGraph(h->cap_stream, body, nullptr, nullptr, 0,
+                                     cudaStreamCaptureModeRelaxed));
+    const long long l0 = g_launches.load();
+    pc_status st = enqueue_level(h, h->cap_stream, fpc::LG_DIRECT + 2, true, false);
+    h->body_kernels = g_launches.load() - l0;
+    g_launches.fetch_sub(h->body_kernels);         // counted when the body executes
+    cudaGraph_t out = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->cap_stream, &out);
+    if (st != PC_OK) {
+        drop_graph(h);
+        return st;
+    }
+    if (e != cudaSuccess) {
+        drop_graph(h);
+        return cuda_fail(h, e, "cudaStreamEndCapture");
+    }
+    e = cudaGraphInstantiate(&h->gexec, h->graph, 0);
+    if (e != cudaSuccess) {
+        drop_graph(h);
+        return cuda_fail(h, e, "cudaGraphInstantiate");
+    }
+    h->graph_key = key;
     return PC_OK;
 }
 
-static pc_status skeleton_run(pc_handle *h, pc_stats *st)
+static pc_status clear_halt(pc_handle *h)
+{
+    // need_host and halt are adjacent ints after 'done'
+    CK(cudaMemsetAsync(&h->g.info->halt, 0, sizeof(int), h->stream));
+    CK(cudaMemsetAsync(&h->g.info->need_host, 0, sizeof(int), h->stream));
+    return PC_OK;
+}
+
+static pc_status skeleton_once(pc_handle *h, pc_stats *st, bool *overflow)
 {
     GraphDev &g = h->g;
     cudaStream_t s = h->stream;
@@ -503,7 +632,12 @@ static pc_status skeleton_run(pc_handle *h, pc_stats *st)
     const size_t pp = (size_t)p * p;
     TestParams tp = make_tp(h);
     std::memset(st, 0, sizeof(*st));
-    st->first_level = -1;
+    *overflow = false;
+    const bool timed = h->timing != 0;
+    const bool graph = h->use_graph && !timed;
+    if (graph) {
+        if (pc_status r = ensure_graph(h)) return r;
+    }
 
     // complete graph, empty sepset store
     std::vector<uint32_t> full((size_t)p * g.W, 0u);
@@ -518,126 +652,85 @@ static pc_status skeleton_run(pc_handle *h, pc_stats *st)
     CK(cudaMemsetAsync(g.prec_pos, 0xff, pp * sizeof(short), s));
     CK(cudaMemsetAsync(g.prec_need, 0, (size_t)p * sizeof(int), s));
     CK(cudaMemsetAsync(g.ctr, 0, sizeof(DevCounters), s));
+    CK(cudaMemsetAsync(g.info, 0, sizeof(LevelInfo), s));
+    CK(cudaMemsetAsync(&g.info->lstar, 0xff, sizeof(int), s));
+    CK(cudaMemsetAsync(h->singular, 0, sizeof(int), s));
     CK(cudaStreamSynchronize(s));   // 'full' is pageable host memory
     CK(cudaEventRecord(h->ev0, s));
 
-    int cap = p - 2;
-    if (h->max_level >= 0 && h->max_level < cap) cap = h->max_level;
-    if (n - 4 < cap) cap = (int)(n - 4);
-    long long opairs = (long long)p * (p - 1);
-
-    if (pc_status r = reset_info(h)) return r;
+    int stage_a_launched = 0;
     {
-        Timed tm(h, 5);
+        Timed t(h, 5);
         CK(fpc::launch_level_degrees(g, s));
+        CK(fpc::launch_tail(g, tp, level_cap(h), 2, h->singular, 0, h->hcond, 0, s));
     }
-    bool stage_a_ran = false;
     if (h->order == 1 && h->stage_a && n - p - 1 > 0) {
+        stage_a_launched = 1;
         if (!h->Pbuf) CK(dalloc(h, &h->Pbuf, (size_t)p * h->ldc * sizeof(double)));
-        CK(cudaMemcpyAsync(h->Pbuf, h->C64, (size_t)p * h->ldc * sizeof(double),
-                           cudaMemcpyDeviceToDevice, s));
         {
-            Timed tm(h, 1);
+            Timed t(h, 1);
+            CK(cudaMemcpyAsync(h->Pbuf, h->C64, (size_t)p * h->ldc * sizeof(double),
+                               cudaMemcpyDeviceToDevice, s));
             CK(fpc::launch_inverse_spd(h->Pbuf, p, h->ldc, h->work, h->singular, s));
             CK(fpc::launch_stage_a_decide(h->Pbuf, p, h->ldc, h->singular, g, tp, s));
         }
         {
-            Timed tm(h, 5);
-            CK(fpc::launch_commit(g, tp, p - 2, opairs, 0, s));
+            Timed t(h, 5);
+            CK(fpc::launch_commit(g, h->opair_cap, p - 2, 0, s));
+            CK(fpc::launch_level_degrees(g, s));
         }
-        int sing = 1;
-        CK(cudaMemcpyAsync(&sing, h->singular, sizeof(int), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        stage_a_ran = sing == 0;
-        if (stage_a_ran) {
-            st->levels_run++;
-            CK(cudaMemsetAsync(g.best, 0xff, pp * sizeof(ull), s));
-        }
-        if (pc_status r = reset_info(h)) return r;
-        Timed tm(h, 5);
-        CK(fpc::launch_level_degrees(g, s));
     }
-    if (pc_status r = read_info(h)) return r;
-    opairs = h->info_h->n_opairs;
+    {
+        Timed t(h, 5);
+        CK(fpc::launch_tail(g, tp, level_cap(h), 1, h->singular, stage_a_launched, h->hcond, 0, s));
+    }
+    if (h->order == 1 && h->complement) {
+        Timed t(h, 2);
+        CK(fpc::launch_prec_update(g, h->C64, h->ldc, s));
+    }
 
-    int l;
-    if (h->order == 1) {
-        l = cap;
-        if (stage_a_ran && l > p - 3) l = p - 3;
-        if (h->info_h->lstar < l) l = h->info_h->lstar;
-    } else {
-        l = 0;
-    }
-    const bool use_prec = h->order == 1 && h->complement;
-    while (true) {
-        if (h->order == 1) {
-            if (l < 0) break;
+    // the stage loop
+    for (int guard_iter = 0; guard_iter < 4 * p + 16; ++guard_iter) {
+        if (graph) {
+            CK(cudaGraphLaunch(h->gexec, s));
+            if (pc_status r = read_info(h)) return r;
         } else {
-            if (l > cap || h->info_h->lstar < l) break;
+            if (pc_status r = read_info(h)) return r;
+            if (h->info_h->done || h->info_h->halt) {
+                // fall through to the checks below
+            } else {
+                int mmax = std::max(fpc::LG_DIRECT + 2, h->info_h->l + 2);
+                if (pc_status r = enqueue_level(h, s, mmax, false, timed)) return r;
+                continue;
+            }
         }
-        if (st->first_level < 0) st->first_level = l;
-        const long long edges = (long long)(h->info_h->edges / 2);
-        // work of this stage
-        CK(cudaMemsetAsync(&g.info->n_build, 0, sizeof(int), s));
-        if (use_prec) {
-            Timed tm(h, 2);
-            CK(fpc::launch_prec_need(g, tp, l, s));
-            CK(fpc::launch_prec_build(g, h->C64, h->ldc, s));
-        }
-        {
-            Timed tm(h, 5);
-            CK(fpc::launch_level_counts(g, tp, l, opairs, h->scan_ws, s));
-        }
-        if (pc_status r = read_info(h)) return r;
         const LevelInfo &I = *h->info_h;
-        if (I.saturated || (double)I.total_direct + (double)I.total_comp > h->budget) {
-            return fail(h, PC_ERR_BUDGET,
-                        "stage l=" + std::to_string(l) + " schedules " +
+        if (I.pool_overflow) {
+            *overflow = true;
+            return PC_OK;
+        }
+        if (I.error) {
+            return fail(h, (pc_status)I.error,
+                        "stage l=" + std::to_string(I.l) + " schedules " +
                             (I.saturated ? std::string(">2^64") :
                                            std::to_string((double)I.total_direct + (double)I.total_comp)) +
                             " tests, above the budget");
         }
-        // room for this stage's sepsets
-        CK(cudaMemcpyAsync(h->ctr_h, g.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        if (pc_status r = grow_pool(h, (long long)h->ctr_h->pool_len + edges * (long long)l + 16)) return r;
-        if (I.total_direct) {
-            Timed tm(h, 3);
-            CK(fpc::launch_ci_direct(g, tp, l, h->C32, h->C64, h->ldc, s));
-        }
-        if (I.total_comp) {
-            Timed tm(h, 4);
-            CK(fpc::launch_ci_complement(g, tp, l, s));
-        }
-        {
-            Timed tm(h, 5);
-            CK(fpc::launch_commit(g, tp, l, opairs, 1, s));
-            CK(cudaMemsetAsync(g.best, 0xff, pp * sizeof(ull), s));
-        }
-        if (use_prec) {
-            Timed tm(h, 2);
-            CK(fpc::launch_prec_downdate(g, s));
-        }
-        st->levels_run++;
-        if (pc_status r = reset_info(h)) return r;
-        {
-            Timed tm(h, 5);
-            CK(fpc::launch_level_degrees(g, s));
-        }
-        if (pc_status r = read_info(h)) return r;
-        opairs = h->info_h->n_opairs;
-        if (h->order == 1) {
-            int nl = l - 1;
-            if (h->info_h->lstar < nl) nl = h->info_h->lstar;
-            l = nl;
-        } else {
-            ++l;
+        if (I.done) break;
+        if (I.need_host) {
+            // a direct-path stage too large for the captured layout: run it here
+            if (pc_status r = clear_halt(h)) return r;
+            if (pc_status r = enqueue_level(h, s, I.l + 2, false, timed)) return r;
         }
     }
     CK(cudaEventRecord(h->ev1, s));
+    if (pc_status r = read_info(h)) return r;
+    if (!h->info_h->done) return fail(h, PC_ERR_INTERNAL, "stage loop did not finish");
     CK(cudaMemcpyAsync(h->ctr_h, g.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     const DevCounters &c = *h->ctr_h;
+    const LevelInfo &I = *h->info_h;
+    if (graph) g_launches.fetch_add((long long)I.body_runs * h->body_kernels);
     if (c.status) return fail(h, (pc_status)c.status, "device-side error during the skeleton search");
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
@@ -649,25 +742,45 @@ static pc_status skeleton_run(pc_handle *h, pc_stats *st)
     st->degenerate = c.degenerate;
     st->complement_tests = c.complement_tests;
     st->edges_removed = c.edges_removed;
-    st->edges_kept = h->info_h->edges / 2;
+    st->edges_kept = I.edges / 2;
     unsigned int bits = c.max_dz_bits;
     float mdz;
     std::memcpy(&mdz, &bits, sizeof(mdz));
     st->max_abs_dz = mdz;
     st->t_skeleton_ms = ms;
-    st->flops_class[1] = (double)c.flops_stagea + (stage_a_ran ? 2.0 * (double)p * p * p : 0.0);
+    st->stage_a_ran = I.stage_a_ran;
+    st->levels_run = I.levels_run;
+    st->first_level = I.first_level;
+    st->flops_class[1] = (double)c.flops_stagea + (I.stage_a_ran ? (double)p * p * p : 0.0);
     st->flops_class[2] = (double)c.flops_prec;
     st->flops_class[3] = (double)c.flops + (double)c.flops64_direct;
     st->flops_class[4] = (double)c.flops_comp;
     st->flops = st->flops_class[1] + st->flops_class[2] + st->flops_class[3] + st->flops_class[4];
-    st->stage_a_ran = stage_a_ran ? 1 : 0;
     return PC_OK;
+}
+
+static pc_status skeleton_run(pc_handle *h, pc_stats *st)
+{
+    for (int attempt = 0; attempt < 6; ++attempt) {
+        bool overflow = false;
+        if (pc_status r = skeleton_once(h, st, &overflow)) return r;
+        if (!overflow) return PC_OK;
+        // the sepset pool was too small: enlarge it and run again (deterministic)
+        int *np = nullptr;
+        long long cap = h->g.pool_cap * 4;
+        CK(dalloc(h, &np, (size_t)cap * sizeof(int)));
+        dfree(h, h->g.pool);
+        h->g.pool = np;
+        h->g.pool_cap = cap;
+    }
+    return fail(h, PC_ERR_INTERNAL, "sepset pool could not be sized");
 }
 
 extern "C" pc_status pc_skeleton(pc_handle *h, uint8_t *adj_out, pc_stats *stats)
 {
     if (!h) return PC_ERR_ARG;
     if (!h->have_corr) return fail(h, PC_ERR_STATE, "pc_skeleton before pc_corr");
+    if (pc_status r = check_tc(h)) return r;
     pc_stats st;
     pc_status r = skeleton_run(h, &st);
     if (r != PC_OK) return r;

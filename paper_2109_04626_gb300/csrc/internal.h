@@ -32,17 +32,26 @@ struct DevCounters {
     int status;                        // device-side error (pc_status value)
 };
 
-// Per-stage scalars produced on the device and read back by the host.
+// Per-stage scalars: the stage index lives on the device so that the whole
+// stage loop can run without host round trips (CUDA graph, conditional WHILE).
 struct LevelInfo {
     int l;                              // stage being run
     int lstar;                          // max |adj(u)\{v}| over adjacent ordered pairs
     long long n_opairs;                 // adjacent ordered pairs
     unsigned long long total_direct;    // tests scheduled on the direct path
     unsigned long long total_comp;      // tests scheduled on the complement path
-    unsigned long long edges;           // unordered edges
+    unsigned long long edges;           // sum of degrees (2 x unordered edges)
     int n_build;                        // neighbourhood precision blocks to build
     int saturated;                      // a test count saturated 2^64
-    long long pad[2];
+    int done;                           // the stage schedule has finished
+    int halt;                           // stop the device loop (need_host | error | overflow)
+    int need_host;                      // this stage needs a direct launch sized by the host
+    int error;                          // pc_status of a device-detected error
+    int pool_overflow;                  // the sepset pool was too small
+    int levels_run;                     // stages visited (the closed-form l = p-2 included)
+    int first_level;                    // first enumerated stage (-1: none)
+    int stage_a_ran;                    // the closed-form stage l = p-2 ran
+    int body_runs;                      // executions of the stage body (kernel accounting)
 };
 
 // Everything the stage kernels need, by value.
@@ -53,8 +62,8 @@ struct GraphDev {
     int *deg;                   // p
     int *nbr;                   // p x p, ascending neighbour ids of the frozen graph
     long long *ooff;            // p+1, exclusive scan of deg (ordered-pair offsets)
-    unsigned long long *tcnt;   // n_opairs+1: direct tests per ordered pair, scanned in place
-    unsigned long long *ccnt;   // n_opairs+1: complement tests per ordered pair, scanned
+    unsigned long long *tn_off; // p+1: first direct test of each node (exclusive scan)
+    unsigned long long *cn_off; // p+1: first complement test of each node
     unsigned long long *best;   // p x p, best (side<<62 | rank) per unordered pair (a<b at a*p+b)
     const unsigned long long *binom;   // (p+1) x (p+1) saturating binomials
     int *sep_level;             // p x p (a<b at a*p+b), -1 none
@@ -79,12 +88,14 @@ struct TestParams {
     float qf;
     double band;        // |z - q| band for FP64 re-decision
     double guard;       // pivot guard
+    float eps_c;        // bound on |C32 - corr| (FP32 GEMM or cast: 2^-23; BF16x3 tensor cores: 1e-6)
     int precision;      // 0 fp64, 1/2 fp32 tests with FP64 re-decision
     int reversed;
     int complement;
 };
 
-// counts kernel launches (defined in fastpc_api.cu)
+// counts kernel launches (defined in fastpc_api.cu); inside a stream capture the
+// count is remembered per captured body instead
 void note_launch();
 
 // ---- correlation (corr.cu)
@@ -95,14 +106,16 @@ cudaError_t launch_standardize(const void *X, int dtype, long long n, int p, lon
                                float *Xs32, uint16_t *Xhi, uint16_t *Xlo, long long ldk,
                                cudaStream_t s);
 cudaError_t launch_syrk_f64(const double *Xs, long long n, long long ldk, int p, double *C64,
-                            int ldc, cudaStream_t s);
+                            int ldc, double *ws, size_t ws_bytes, cudaStream_t s);
+size_t syrk_f64_ws_bytes(long long n, int p);
 cudaError_t launch_syrk_f32(const float *Xs, long long n, long long ldk, int p, float *C32,
                             int ldc, cudaStream_t s);
 cudaError_t launch_cast_c(const double *C64, float *C32, int p, int ldc, cudaStream_t s);
 bool tc_gemm_available();
-cudaError_t launch_corr_bf16x3(const uint16_t *Xhi, const uint16_t *Xlo, long long n,
-                               long long ldk, int p, float *C32, int ldc, float *ws,
+cudaError_t launch_corr_bf16x3(const uint16_t *Xhi, const uint16_t *Xlo, long long n, long long ldk,
+                               int p, float *C32, int ldc, float *ws, size_t ws_bytes, int *err,
                                cudaStream_t s);
+size_t corr_bf16x3_ws_bytes(long long n, int p);
 
 // ---- stage l = p-2 (stage_a.cu)
 cudaError_t launch_inverse_spd(double *A, int m, int lda, double *work, int *singular,
@@ -110,18 +123,19 @@ cudaError_t launch_inverse_spd(double *A, int m, int lda, double *work, int *sin
 cudaError_t launch_stage_a_decide(const double *P, int p, int ldp, const int *singular,
                                   GraphDev g, TestParams tp, cudaStream_t s);
 
-// ---- stage kernels (level.cu)
+// ---- stage kernels (level.cu); they read the stage index from info->l and
+// return at once when info->done or info->halt is set
+constexpr int LG_DIRECT = 24;          // direct-path stages a captured stage loop can run
 cudaError_t launch_level_degrees(GraphDev g, cudaStream_t s);
-cudaError_t launch_prec_need(GraphDev g, TestParams tp, int l, cudaStream_t s);
-cudaError_t launch_level_counts(GraphDev g, TestParams tp, int l, long long n_opairs,
-                                void *scan_ws, cudaStream_t s);
-cudaError_t launch_ci_direct(GraphDev g, TestParams tp, int l, const float *C32,
+cudaError_t launch_tail(GraphDev g, TestParams tp, int cap, int mode, const int *stagea_singular,
+                        int stagea_launched, cudaGraphConditionalHandle hc, int use_cond, cudaStream_t s);
+cudaError_t launch_head(GraphDev g, TestParams tp, double budget, int mmax_direct, cudaStream_t s);
+cudaError_t launch_ci_direct(GraphDev g, TestParams tp, int mmax, const float *C32,
                              const double *C64, int ldc, cudaStream_t s);
-cudaError_t launch_ci_complement(GraphDev g, TestParams tp, int l, cudaStream_t s);
-cudaError_t launch_prec_build(GraphDev g, const double *C64, int ldc, cudaStream_t s);
-cudaError_t launch_commit(GraphDev g, TestParams tp, int l, long long n_opairs,
-                          int explicit_sets, cudaStream_t s);
-cudaError_t launch_prec_downdate(GraphDev g, cudaStream_t s);
+cudaError_t launch_ci_complement(GraphDev g, TestParams tp, cudaStream_t s);
+cudaError_t launch_prec_update(GraphDev g, const double *C64, int ldc, cudaStream_t s);
+cudaError_t launch_commit(GraphDev g, long long n_opairs_cap, int l_fixed, int explicit_sets,
+                          cudaStream_t s);
 size_t scan_ws_bytes(long long n);
 
 // ---- raw test batches (level.cu)

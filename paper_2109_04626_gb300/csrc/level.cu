@@ -30,12 +30,16 @@ __device__ __forceinline__ ull sat_add(ull a, ull b)
     return c < a ? KEY_NONE : c;
 }
 
-// ---------------------------------------------------------------- degrees
+// the stage loop has finished or has been halted: nothing to do
+__device__ __forceinline__ bool stopped(const LevelInfo *I) { return I->done || I->halt; }
+
+// ---------------------------------------------------------------- frozen graph
+// Degrees and ascending neighbour lists of the current graph, one warp per node.
 __global__ void degrees_kernel(GraphDev g)
 {
     const int lane = threadIdx.x & 31;
     const int u = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
-    if (u >= g.p) return;
+    if (u >= g.p || stopped(g.info)) return;
     const uint32_t *row = g.adj + (long long)u * g.W;
     int base = 0;
     for (int w0 = 0; w0 < g.W; w0 += 32) {
@@ -55,28 +59,53 @@ __global__ void degrees_kernel(GraphDev g)
         }
         base += __shfl_sync(0xffffffffu, incl, 31);
     }
-    if (lane == 0) {
-        g.deg[u] = base;
-        if (base > 0) atomicMax(&g.info->lstar, base - 1);
-        atomicAdd(&g.info->edges, (ull)base);
-    }
+    if (lane == 0) g.deg[u] = base;
 }
 
-// exclusive scan of deg -> ooff[0..p], single CTA (p <= 4096)
-__global__ void __launch_bounds__(1024) ooff_kernel(GraphDev g)
+__device__ __forceinline__ bool comp_eligible(int d, int l, const TestParams &tp)
 {
+    const int k = d - l;
+    return tp.reversed && tp.complement && d >= l && k <= KC_MAX && k < l && d + 2 <= PREC_MAX;
+}
+
+// One CTA after the degrees: ordered-pair offsets, L* = max |adj(u)\{v}|, edge
+// count; then (mode 1) the first stage or (mode 0) the next stage, the loop
+// condition, and the precision-block requests of that stage.  Mode 2 only
+// scans (the complete graph before the closed-form stage).
+//   Algorithm 1: l = 0, 1, ... while some pair has |adj(u)\{v}| >= l and l <= cap.
+//   Algorithm 2: l = min(cap, L*) (below p-2 once the closed-form stage ran),
+//                then l <- min(l-1, L*) while l >= 0.
+__global__ void __launch_bounds__(1024) tail_kernel(GraphDev g, TestParams tp, int cap, int mode,
+                                                    const int *stagea_singular, int stagea_launched,
+                                                    cudaGraphConditionalHandle hc, int use_cond)
+{
+    LevelInfo *I = g.info;
     __shared__ long long part[1024];
+    __shared__ int smax[1024];
+    __shared__ int sh_l, sh_go;
     const int p = g.p, t = threadIdx.x;
+    if (mode == 0 && t == 0) I->body_runs++;
+    if (stopped(I)) {
+        if (use_cond && t == 0) cudaGraphSetConditional(hc, 0u);
+        return;
+    }
     const int per = (p + 1023) / 1024;
-    const int s0 = t * per, s1 = min(p, s0 + per);
+    const int s0 = min(p, t * per), s1 = min(p, s0 + per);
     long long sum = 0;
-    for (int i = s0; i < s1; ++i) sum += g.deg[i];
+    int mx = 0;
+    for (int i = s0; i < s1; ++i) {
+        sum += g.deg[i];
+        mx = max(mx, g.deg[i]);
+    }
     part[t] = sum;
+    smax[t] = mx;
     __syncthreads();
     for (int off = 1; off < 1024; off <<= 1) {
         long long v = (t >= off) ? part[t - off] : 0;
+        int m2 = (t >= off) ? smax[t - off] : 0;
         __syncthreads();
         part[t] += v;
+        smax[t] = max(smax[t], m2);
         __syncthreads();
     }
     long long run = part[t] - sum;
@@ -84,163 +113,153 @@ __global__ void __launch_bounds__(1024) ooff_kernel(GraphDev g)
         g.ooff[i] = run;
         run += g.deg[i];
     }
-    if (t == 1023) {
-        g.ooff[p] = part[1023];
-        g.info->n_opairs = part[1023];
-    }
-}
-
-// ---------------------------------------------------------------- complement eligibility
-__device__ __forceinline__ bool comp_eligible(int d, int l, const TestParams &tp)
-{
-    const int k = d - l;
-    return tp.reversed && tp.complement && d >= l && k <= KC_MAX && k < l && d + 2 <= PREC_MAX;
-}
-
-__global__ void prec_need_kernel(GraphDev g, TestParams tp, int l)
-{
-    const int u = blockIdx.x * blockDim.x + threadIdx.x;
-    if (u >= g.p) return;
-    const int dg = g.deg[u];
-    const bool need = dg > 0 && comp_eligible(dg - 1, l, tp) && g.prec_m[u] == 0;
-    g.prec_need[u] = need;
-    if (need) atomicAdd(&g.info->n_build, 1);
-}
-
-__global__ void counts_kernel(GraphDev g, TestParams tp, int l)
-{
-    const long long nop = g.info->n_opairs;
-    const int p = g.p;
-    for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < nop;
-         o += (long long)gridDim.x * blockDim.x) {
-        const int u = (int)(upper_bound_dev(g.ooff, (long long)p + 1, o) - 1);
-        const int d = g.deg[u] - 1;
-        const ull T = d >= l ? g.binom[(long long)d * (p + 1) + l] : 0ull;
-        const bool comp = d >= l && comp_eligible(d, l, tp) && g.prec_m[u] > 0;
-        g.tcnt[o] = comp ? 0ull : T;
-        g.ccnt[o] = comp ? T : 0ull;
-        if (T == KEY_NONE) g.info->saturated = 1;
-    }
-}
-
-// ---------------------------------------------------------------- u64 saturating scan
-constexpr int SCAN_T = 256, SCAN_PER = 16, SCAN_TILE = SCAN_T * SCAN_PER;
-
-size_t scan_ws_bytes(long long n) { return (size_t)((n + SCAN_TILE - 1) / SCAN_TILE + 2) * sizeof(ull); }
-
-__device__ __forceinline__ ull block_reduce_sat(ull v, ull *sh)
-{
-    const int t = threadIdx.x;
-    sh[t] = v;
-    __syncthreads();
-    for (int s = SCAN_T / 2; s > 0; s >>= 1) {
-        if (t < s) sh[t] = sat_add(sh[t], sh[t + s]);
-        __syncthreads();
-    }
-    ull r = sh[0];
-    __syncthreads();
-    return r;
-}
-
-__global__ void __launch_bounds__(SCAN_T) scan_reduce_kernel(const ull *a, const long long *nptr,
-                                                             ull *part)
-{
-    __shared__ ull sh[SCAN_T];
-    const long long n = *nptr;
-    const long long start = (long long)blockIdx.x * SCAN_TILE;
-    ull s = 0;
-    for (int i = 0; i < SCAN_PER; ++i) {
-        long long idx = start + (long long)i * SCAN_T + threadIdx.x;
-        if (idx < n) s = sat_add(s, a[idx]);
-    }
-    s = block_reduce_sat(s, sh);
-    if (threadIdx.x == 0) part[blockIdx.x] = s;
-}
-
-__global__ void __launch_bounds__(1024) scan_part_kernel(ull *part, int nb, ull *total)
-{
-    __shared__ ull sh[1024];
-    const int t = threadIdx.x;
-    ull carry = 0;
-    for (int c0 = 0; c0 < nb; c0 += 1024) {
-        const int i = c0 + t;
-        sh[t] = i < nb ? part[i] : 0ull;
-        __syncthreads();
-        for (int off = 1; off < 1024; off <<= 1) {
-            ull x = t >= off ? sh[t - off] : 0ull;
-            __syncthreads();
-            sh[t] = sat_add(sh[t], x);
-            __syncthreads();
+    if (t == 0) {
+        const long long tot = part[1023];
+        const int lstar = smax[1023] - 1;              // -1 when no edge is left
+        g.ooff[p] = tot;
+        I->n_opairs = tot;
+        I->edges = (unsigned long long)tot;
+        I->lstar = lstar;
+        if (mode == 1) {
+            const int ran = stagea_launched && !*stagea_singular;
+            I->stage_a_ran = ran;
+            I->levels_run = ran;
+            int l;
+            bool go;
+            if (tp.reversed) {
+                l = cap;
+                if (ran && l > p - 3) l = p - 3;
+                if (lstar < l) l = lstar;
+                go = l >= 0;
+            } else {
+                l = 0;
+                go = cap >= 0 && lstar >= 0;
+            }
+            I->l = l;
+            I->first_level = go ? l : -1;
+            I->done = !go;
+        } else if (mode == 0) {
+            I->levels_run++;
+            const int l = I->l;
+            int nl;
+            bool go;
+            if (tp.reversed) {
+                nl = min(l - 1, lstar);
+                go = nl >= 0;
+            } else {
+                nl = l + 1;
+                go = nl <= cap && lstar >= nl;
+            }
+            I->l = nl;
+            I->done = !go;
         }
-        const ull excl = t ? sh[t - 1] : 0ull;
-        if (i < nb) part[i] = sat_add(carry, excl);
-        const ull blk = sh[1023];
-        __syncthreads();
-        carry = sat_add(carry, blk);
+        sh_l = I->l;
+        sh_go = !I->done;
     }
-    if (t == 0) *total = carry;
+    __syncthreads();
+    if (mode != 2 && sh_go && tp.reversed && tp.complement) {
+        // precision blocks: all nodes that fit at the first stage, then the nodes
+        // that have become small enough for the complement path at this stage
+        for (int u = t; u < p; u += blockDim.x) {
+            const int dg = g.deg[u];
+            bool need;
+            if (mode == 1) need = dg >= 2 && dg + 1 <= PREC_MAX && g.prec_m[u] == 0;
+            else need = dg > 0 && comp_eligible(dg - 1, sh_l, tp) && g.prec_m[u] == 0;
+            g.prec_need[u] = need;
+        }
+    }
+    if (use_cond && t == 0) cudaGraphSetConditional(hc, sh_go ? 1u : 0u);
 }
 
-__global__ void __launch_bounds__(SCAN_T) scan_down_kernel(ull *a, const long long *nptr,
-                                                           const ull *part, const ull *total)
+__device__ __forceinline__ ull sat_mul(ull a, ull b)
 {
-    __shared__ ull tile[SCAN_TILE + SCAN_T];
-    __shared__ ull sh[SCAN_T];
-    const long long n = *nptr;
-    const long long start = (long long)blockIdx.x * SCAN_TILE;
-    if (start > n) return;
-    for (int i = 0; i < SCAN_PER; ++i) {
-        int li = i * SCAN_T + threadIdx.x;
-        long long idx = start + li;
-        tile[li + li / SCAN_PER] = idx < n ? a[idx] : 0ull;
-    }
-    __syncthreads();
-    // thread t owns tile elements [t*PER, (t+1)*PER)
-    const int t = threadIdx.x;
-    ull s = 0;
-    for (int i = 0; i < SCAN_PER; ++i) {
-        int li = t * SCAN_PER + i;
-        s = sat_add(s, tile[li + li / SCAN_PER]);
-    }
-    sh[t] = s;
-    __syncthreads();
-    for (int off = 1; off < SCAN_T; off <<= 1) {
-        ull x = t >= off ? sh[t - off] : 0ull;
-        __syncthreads();
-        sh[t] = sat_add(sh[t], x);
-        __syncthreads();
-    }
-    ull run = sat_add(part[blockIdx.x], t ? sh[t - 1] : 0ull);
-    for (int i = 0; i < SCAN_PER; ++i) {
-        int li = t * SCAN_PER + i;
-        ull v = tile[li + li / SCAN_PER];
-        tile[li + li / SCAN_PER] = run;
-        run = sat_add(run, v);
-    }
-    __syncthreads();
-    for (int i = 0; i < SCAN_PER; ++i) {
-        int li = i * SCAN_T + threadIdx.x;
-        long long idx = start + li;
-        if (idx < n) a[idx] = tile[li + li / SCAN_PER];
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) a[n] = *total;
+    if (a == 0 || b == 0) return 0;
+    if (a == KEY_NONE || b == KEY_NONE || a > KEY_NONE / b) return KEY_NONE;
+    return a * b;
 }
 
-// exclusive scan of a[0..n) in place, a[n] = total (n read from device)
-static cudaError_t scan_u64(ull *a, const long long *nptr, long long ncap, void *ws, ull *total_out,
-                            cudaStream_t s)
+// Work of stage l per node u: every ordered pair (u, v) has C(d, l) tests,
+// d = |adj(u)| - 1, all on the direct path or all on the complement path.
+// One CTA scans the per-node totals into tn_off / cn_off and gates the stage:
+// budget and saturation (PC_ERR_BUDGET), or direct tests at an l larger than
+// the direct kernel's shared-memory layout (the host runs that stage).
+__global__ void __launch_bounds__(1024) head_kernel(GraphDev g, TestParams tp, double budget,
+                                                    int mmax_direct)
 {
-    int nb = (int)((ncap + SCAN_TILE - 1) / SCAN_TILE);
-    if (nb < 1) nb = 1;
-    ull *part = (ull *)ws;
-    ull *total = part + nb;
-    scan_reduce_kernel<<<nb, SCAN_T, 0, s>>>(a, nptr, part); note_launch();
-    scan_part_kernel<<<1, 1024, 0, s>>>(part, nb, total); note_launch();
-    scan_down_kernel<<<nb, SCAN_T, 0, s>>>(a, nptr, part, total); note_launch();
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    return cudaMemcpyAsync(total_out, total, sizeof(ull), cudaMemcpyDeviceToDevice, s);
+    LevelInfo *I = g.info;
+    if (stopped(I)) return;
+    __shared__ ull pd[1024], pc[1024];
+    __shared__ int ssat;
+    const int p = g.p, l = I->l, t = threadIdx.x;
+    if (t == 0) ssat = 0;
+    __syncthreads();
+    const int per = (p + 1023) / 1024;
+    const int s0 = min(p, t * per), s1 = min(p, s0 + per);
+    ull sd = 0, sc = 0;
+    for (int u = s0; u < s1; ++u) {
+        const int dg = g.deg[u], d = dg - 1;
+        const ull T = (dg > 0 && d >= l) ? g.binom[(long long)d * (p + 1) + l] : 0ull;
+        const ull tot = sat_mul(T, (ull)dg);
+        if (tot == KEY_NONE) ssat = 1;
+        const bool comp = T && comp_eligible(d, l, tp) && g.prec_m[u] > 0;
+        if (comp) sc = sat_add(sc, tot);
+        else sd = sat_add(sd, tot);
+    }
+    pd[t] = sd;
+    pc[t] = sc;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        ull a = t >= off ? pd[t - off] : 0ull, b = t >= off ? pc[t - off] : 0ull;
+        __syncthreads();
+        pd[t] = sat_add(pd[t], a);
+        pc[t] = sat_add(pc[t], b);
+        __syncthreads();
+    }
+    ull rd = t ? pd[t - 1] : 0ull, rc = t ? pc[t - 1] : 0ull;
+    for (int u = s0; u < s1; ++u) {
+        const int dg = g.deg[u], d = dg - 1;
+        const ull T = (dg > 0 && d >= l) ? g.binom[(long long)d * (p + 1) + l] : 0ull;
+        const ull tot = sat_mul(T, (ull)dg);
+        const bool comp = T && comp_eligible(d, l, tp) && g.prec_m[u] > 0;
+        g.tn_off[u] = rd;
+        g.cn_off[u] = rc;
+        if (comp) rc = sat_add(rc, tot);
+        else rd = sat_add(rd, tot);
+    }
+    __syncthreads();
+    if (t == 0) {
+        const ull td = pd[1023], tc = pc[1023];
+        g.tn_off[p] = td;
+        g.cn_off[p] = tc;
+        I->total_direct = td;
+        I->total_comp = tc;
+        I->saturated = ssat || td == KEY_NONE || tc == KEY_NONE;
+        if (I->saturated || (double)td + (double)tc > budget) {
+            I->error = 6;                                // PC_ERR_BUDGET
+            I->halt = 1;
+        } else if (td > 0 && l + 2 > mmax_direct) {
+            I->need_host = 1;
+            I->halt = 1;
+        }
+    }
 }
+
+// test index t of the stage -> (u, j, rank): node by the per-node offsets,
+// then j = (t - off[u]) / C(d,l) and rank = (t - off[u]) mod C(d,l)
+__device__ __forceinline__ void locate_test(const GraphDev &g, const ull *noff, int l, ull t, int &u,
+                                            int &j, int &d, ull &rank)
+{
+    const int p = g.p;
+    u = (int)(upper_bound_dev(noff, (long long)p + 1, t) - 1);
+    d = g.deg[u] - 1;
+    const ull T = g.binom[(long long)d * (p + 1) + l];
+    const ull w = t - noff[u];
+    const ull jj = w / T;
+    j = (int)jj;
+    rank = w - jj * T;
+}
+
+size_t scan_ws_bytes(long long n) { return 64 + 0 * n; }
 
 // ---------------------------------------------------------------- warp test
 // Cholesky of the leading l x l block of the (l+2) x (l+2) lower triangle M
@@ -323,7 +342,7 @@ __device__ __forceinline__ bool warp_test(const int *nd, int m, int l, const flo
             ++acc.guard;
         } else {
             // error model of the FP32 evaluation: dr ~ (m eps32 + eps_C) / pmin
-            const float dr = 2.0f * ((float)m * 5.96e-8f + 1.2e-7f) / pmin;
+            const float dr = 2.0f * ((float)m * 5.96e-8f + tp.eps_c) / pmin;
             const float omr = fmaxf(1.0f - rf * rf, 1e-3f);
             zf = fabsf(rf) < 1.0f ? sqf * fabsf(atanhf(rf)) : INFINITY;
             const float dz = sqf * dr / omr;
@@ -384,31 +403,31 @@ __device__ __forceinline__ void flush_acc(const WarpAcc &acc, DevCounters *ctr)
 
 // ---------------------------------------------------------------- direct path (skeleton)
 template <bool F64>
-__global__ void __launch_bounds__(256) ci_direct_kernel(GraphDev g, TestParams tp, int l,
+__global__ void __launch_bounds__(256) ci_direct_kernel(GraphDev g, TestParams tp, int mmax,
                                                         const float *C32, const double *C64,
                                                         int ldc, int ms, int per_warp_bytes)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (stopped(g.info)) return;
+    const int l = g.info->l;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int m = l + 2, p = g.p;
+    if (m > mmax) return;
     unsigned char *mine = smem_raw + (size_t)wib * per_warp_bytes;
     double *Mbuf = (double *)mine;
-    int *nd = (int *)(mine + (size_t)m * ms * sizeof(double));
-    int *pos = nd + m;
+    int *nd = (int *)(mine + (size_t)mmax * ms * sizeof(double));
+    int *pos = nd + mmax;
     const ull total = g.info->total_direct;
-    const long long nop = g.info->n_opairs;
     const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     const double sq = sqrt((double)(tp.n - l - 3));
     const float sqf = (float)sq;
     WarpAcc acc = {0, 0, 0, 0, 0, 0, 0, 0.f};
     for (ull t = gw; t < total; t += nw) {
-        const long long o = upper_bound_dev(g.tcnt, nop + 1, t) - 1;
-        const ull rank = t - g.tcnt[o];
-        const int u = (int)(upper_bound_dev(g.ooff, (long long)p + 1, o) - 1);
-        const int j = (int)(o - g.ooff[u]);
+        int u, j, d;
+        ull rank;
+        locate_test(g, g.tn_off, l, t, u, j, d, rank);
         const int v = g.nbr[(long long)u * p + j];
-        const int d = g.deg[u] - 1;
         const int side = u > v;
         const int a = min(u, v), b = max(u, v);
         const ull key = ((ull)side << 62) | rank;
@@ -435,21 +454,25 @@ __global__ void __launch_bounds__(256) ci_direct_kernel(GraphDev g, TestParams t
 }
 
 // ---------------------------------------------------------------- complement path
-__global__ void __launch_bounds__(128) ci_complement_kernel(GraphDev g, TestParams tp, int l)
+// With P = corr[F,F]^{-1}, F = adj(u) u {u}, and the dropped set R
+// (S = adj(u)\{v}\R, |R| = k = d - l), the {u,v} block of corr[T,T]^{-1},
+// T = S u {u,v}, is Q = P_TT - P_TR P_RR^{-1} P_RT restricted to {u,v}
+// (inverse of a principal submatrix); r = -Q_uv / sqrt(Q_uu Q_vv), and the
+// Schur complement H of Sec. 4 is Q^{-1}: h11 = Q_vv/det, h22 = Q_uu/det.
+__global__ void __launch_bounds__(128) ci_complement_kernel(GraphDev g, TestParams tp)
 {
+    if (stopped(g.info)) return;
+    const int l = g.info->l;
     const ull total = g.info->total_comp;
-    const long long nop = g.info->n_opairs;
     const int p = g.p;
     const double sq = sqrt((double)(tp.n - l - 3));
     ull nt = 0, ndg = 0, nfl = 0;
     for (ull t = blockIdx.x * (ull)blockDim.x + threadIdx.x; t < total;
          t += (ull)gridDim.x * blockDim.x) {
-        const long long o = upper_bound_dev(g.ccnt, nop + 1, t) - 1;
-        const ull rank = t - g.ccnt[o];
-        const int u = (int)(upper_bound_dev(g.ooff, (long long)p + 1, o) - 1);
-        const int j = (int)(o - g.ooff[u]);
+        int u, j, d;
+        ull rank;
+        locate_test(g, g.cn_off, l, t, u, j, d, rank);
         const int v = g.nbr[(long long)u * p + j];
-        const int d = g.deg[u] - 1;
         const int k = d - l;
         const int side = u > v;
         const int a = min(u, v), b = max(u, v);
@@ -519,22 +542,56 @@ __global__ void __launch_bounds__(128) ci_complement_kernel(GraphDev g, TestPara
 }
 
 // ---------------------------------------------------------------- neighbourhood precision blocks
-__global__ void __launch_bounds__(512) prec_build_kernel(GraphDev g, const double *C64, int ldc)
+// One CTA per node.  A maintained block drops the neighbours the last commit
+// deleted (P <- P - P[:,w] P[w,:] / P_ww: the inverse of a principal
+// submatrix); a requested block is built by a symmetric sweep of corr[F,F],
+// F = adj(u) u {u} (ascending ids).
+__global__ void __launch_bounds__(512) prec_update_kernel(GraphDev g, const double *C64, int ldc)
 {
     const int u = blockIdx.x;
-    if (!g.prec_need[u]) return;
+    if (stopped(g.info)) return;
     extern __shared__ double smd[];
     __shared__ int mem[PREC_MAX];
     __shared__ int bad;
     const int p = g.p;
+    const int m0 = g.prec_m[u];
+    if (m0 > 0) {
+        double *colw = smd;
+        double *P = g.prec + (long long)u * PREC_MAX * PREC_MAX;
+        const int *pm = g.prec_mem + (long long)u * PREC_MAX;
+        short *pos = g.prec_pos + (long long)u * p;
+        const uint32_t *row = g.adj + (long long)u * g.W;
+        ull fl = 0;
+        for (int s = 0; s < m0; ++s) {
+            const int w = pm[s];
+            if (w == u || pos[w] < 0) continue;
+            if ((row[w >> 5] >> (w & 31)) & 1u) continue;   // still adjacent
+            for (int i = threadIdx.x; i < m0; i += blockDim.x) colw[i] = P[i * PREC_MAX + s];
+            __syncthreads();
+            const double ipww = 1.0 / colw[s];
+            for (int i = threadIdx.x >> 5; i < m0; i += blockDim.x >> 5) {
+                if (i == s) continue;
+                const double ci = colw[i] * ipww;
+                for (int c = threadIdx.x & 31; c < m0; c += 32)
+                    if (c != s) P[i * PREC_MAX + c] = fma(-ci, colw[c], P[i * PREC_MAX + c]);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) pos[w] = -1;
+            fl += 2ull * m0 * m0;
+            __syncthreads();
+        }
+        if (threadIdx.x == 0 && fl) atomicAdd(&g.ctr->flops_prec, fl);
+        return;
+    }
+    if (!g.prec_need[u]) return;
     const int m = g.deg[u] + 1;
     if (threadIdx.x == 0) {
         bad = 0;
-        int i = 0, o = 0;
+        int o = 0;
         const int *nb = g.nbr + (long long)u * p;
         const int dg = g.deg[u];
         bool placed = false;
-        for (; i < dg; ++i) {
+        for (int i = 0; i < dg; ++i) {
             if (!placed && nb[i] > u) {
                 mem[o++] = u;
                 placed = true;
@@ -544,13 +601,11 @@ __global__ void __launch_bounds__(512) prec_build_kernel(GraphDev g, const doubl
         if (!placed) mem[o++] = u;
     }
     __syncthreads();
-    double *A = smd, *colk = A + m * m, *rowk = colk + m;
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-        int i = e / m, c = e - i * m;
-        A[e] = C64[(long long)mem[i] * ldc + mem[c]];
-    }
+    double *A = smd, *colk = A + m * m;
+    for (int i = threadIdx.x >> 5; i < m; i += blockDim.x >> 5)
+        for (int c = threadIdx.x & 31; c < m; c += 32) A[i * m + c] = C64[(long long)mem[i] * ldc + mem[c]];
     __syncthreads();
-    gj_inverse_block(A, m, m, colk, rowk, &bad);
+    sweep_inverse_block(A, m, m, colk, &bad);     // A = -corr[F,F]^{-1}
     __syncthreads();
     if (bad) {
         if (threadIdx.x == 0) {
@@ -560,10 +615,8 @@ __global__ void __launch_bounds__(512) prec_build_kernel(GraphDev g, const doubl
         return;
     }
     double *P = g.prec + (long long)u * PREC_MAX * PREC_MAX;
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-        int i = e / m, c = e - i * m;
-        P[i * PREC_MAX + c] = A[e];
-    }
+    for (int i = threadIdx.x >> 5; i < m; i += blockDim.x >> 5)
+        for (int c = threadIdx.x & 31; c < m; c += 32) P[i * PREC_MAX + c] = -A[i * m + c];
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
         g.prec_mem[(long long)u * PREC_MAX + i] = mem[i];
         g.prec_pos[(long long)u * p + mem[i]] = (short)i;
@@ -571,46 +624,19 @@ __global__ void __launch_bounds__(512) prec_build_kernel(GraphDev g, const doubl
     if (threadIdx.x == 0) {
         g.prec_m[u] = m;
         g.prec_need[u] = 0;
-        atomicAdd(&g.ctr->flops_prec, 2ull * (ull)m * m * m);
+        atomicAdd(&g.ctr->flops_prec, (ull)m * m * m);
     }
-}
-
-// Remove the neighbours a stage deleted from each maintained block:
-// P <- P - P[:,w] P[w,:] / P_ww drops w (inverse of a principal submatrix).
-__global__ void __launch_bounds__(512) prec_downdate_kernel(GraphDev g)
-{
-    const int u = blockIdx.x;
-    const int m = g.prec_m[u];
-    if (m <= 0) return;
-    __shared__ double colw[PREC_MAX];
-    const int p = g.p;
-    double *P = g.prec + (long long)u * PREC_MAX * PREC_MAX;
-    const int *mem = g.prec_mem + (long long)u * PREC_MAX;
-    short *pos = g.prec_pos + (long long)u * p;
-    const uint32_t *row = g.adj + (long long)u * g.W;
-    ull fl = 0;
-    for (int s = 0; s < m; ++s) {
-        const int w = mem[s];
-        if (w == u || pos[w] < 0) continue;
-        if ((row[w >> 5] >> (w & 31)) & 1u) continue;   // still adjacent
-        for (int i = threadIdx.x; i < m; i += blockDim.x) colw[i] = P[i * PREC_MAX + s];
-        __syncthreads();
-        const double ipww = 1.0 / colw[s];
-        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-            int i = e / m, c = e - i * m;
-            if (i != s && c != s) P[i * PREC_MAX + c] -= colw[i] * colw[c] * ipww;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) pos[w] = -1;
-        fl += 2ull * m * m;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0 && fl) atomicAdd(&g.ctr->flops_prec, fl);
 }
 
 // ---------------------------------------------------------------- commit
-__global__ void commit_kernel(GraphDev g, int l, int explicit_sets, int count_canonical)
+// End of stage l (PC-stable): delete every pair with a recorded key, store its
+// first separating set (side, rank, and the expanded node list), reset the
+// key, and count the tests of the sequential canonical order:
+// key (0, rank) -> rank+1; key (1, rank) -> C(d_u,l) + rank+1; none -> both sides.
+__global__ void commit_kernel(GraphDev g, int l_fixed, int explicit_sets, int count_canonical)
 {
+    if (stopped(g.info)) return;
+    const int l = l_fixed >= 0 ? l_fixed : g.info->l;
     const long long nop = g.info->n_opairs;
     const int p = g.p;
     ull removed = 0, canon = 0;
@@ -622,11 +648,11 @@ __global__ void commit_kernel(GraphDev g, int l, int explicit_sets, int count_ca
         if (u > v) continue;
         const long long e = (long long)u * p + v;
         const ull key = g.best[e];
-        const int jv = lower_bound_int(g.nbr + (long long)v * p, g.deg[v], u);
-        const long long o2 = g.ooff[v] + jv;
+        g.best[e] = KEY_NONE;                         // ready for the next stage
         if (count_canonical) {
-            const ull T0 = (g.tcnt[o + 1] - g.tcnt[o]) + (g.ccnt[o + 1] - g.ccnt[o]);
-            const ull T1 = (g.tcnt[o2 + 1] - g.tcnt[o2]) + (g.ccnt[o2 + 1] - g.ccnt[o2]);
+            const int du = g.deg[u] - 1, dv = g.deg[v] - 1;
+            const ull T0 = du >= l ? g.binom[(long long)du * (p + 1) + l] : 0ull;
+            const ull T1 = dv >= l ? g.binom[(long long)dv * (p + 1) + l] : 0ull;
             ull c;
             if (key == KEY_NONE) c = sat_add(T0, T1);
             else if ((key >> 62) == 0) c = key + 1;
@@ -646,11 +672,12 @@ __global__ void commit_kernel(GraphDev g, int l, int explicit_sets, int count_ca
             const ull off = atomicAdd(&g.ctr->pool_len, (ull)l);
             g.sep_off[e] = (long long)off;
             if ((long long)(off + l) > g.pool_cap) {
-                g.ctr->status = 8;
+                g.info->pool_overflow = 1;           // the host enlarges the pool and reruns
+                g.info->halt = 1;
                 continue;
             }
             const int su = side ? v : u;
-            const int jj = side ? jv : j;
+            const int jj = side ? lower_bound_int(g.nbr + (long long)v * p, g.deg[v], u) : j;
             const int dd = g.deg[su] - 1;
             const int *nb = g.nbr + (long long)su * p;
             ull r = rank;
@@ -737,91 +764,79 @@ static int num_sms()
 cudaError_t launch_level_degrees(GraphDev g, cudaStream_t s)
 {
     degrees_kernel<<<(g.p * 32 + 255) / 256, 256, 0, s>>>(g); note_launch();
-    ooff_kernel<<<1, 1024, 0, s>>>(g); note_launch();
     return cudaGetLastError();
 }
 
-cudaError_t launch_prec_need(GraphDev g, TestParams tp, int l, cudaStream_t s)
+cudaError_t launch_tail(GraphDev g, TestParams tp, int cap, int mode, const int *stagea_singular,
+                        int stagea_launched, cudaGraphConditionalHandle hc, int use_cond, cudaStream_t s)
 {
-    prec_need_kernel<<<(g.p + 255) / 256, 256, 0, s>>>(g, tp, l); note_launch();
+    tail_kernel<<<1, 1024, 0, s>>>(g, tp, cap, mode, stagea_singular, stagea_launched, hc, use_cond); note_launch();
     return cudaGetLastError();
 }
 
-cudaError_t launch_level_counts(GraphDev g, TestParams tp, int l, long long n_opairs_cap,
-                                void *scan_ws, cudaStream_t s)
+cudaError_t launch_head(GraphDev g, TestParams tp, double budget, int mmax_direct, cudaStream_t s)
 {
-    long long cap = n_opairs_cap > 0 ? n_opairs_cap : 1;
-    int blocks = (int)std::min<long long>((cap + 255) / 256, (long long)num_sms() * 16);
-    counts_kernel<<<blocks, 256, 0, s>>>(g, tp, l); note_launch();
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    e = scan_u64(g.tcnt, &g.info->n_opairs, cap, scan_ws, &g.info->total_direct, s);
-    if (e != cudaSuccess) return e;
-    return scan_u64(g.ccnt, &g.info->n_opairs, cap, scan_ws, &g.info->total_comp, s);
+    head_kernel<<<1, 1024, 0, s>>>(g, tp, budget, mmax_direct); note_launch();
+    return cudaGetLastError();
 }
 
-static void direct_shape(int l, int &ms, int &per_warp, int &wpc)
+static void direct_shape(int mmax, int &ms, int &per_warp, int &wpc)
 {
-    const int m = l + 2;
+    const int m = mmax;
     ms = m + 1;
     per_warp = (int)(((size_t)m * ms * sizeof(double) + 2 * (size_t)m * sizeof(int) + 15) / 16 * 16);
     wpc = 8;
     while (wpc > 1 && (size_t)wpc * per_warp > 96 * 1024) wpc >>= 1;
 }
 
-cudaError_t launch_ci_direct(GraphDev g, TestParams tp, int l, const float *C32,
+cudaError_t launch_ci_direct(GraphDev g, TestParams tp, int mmax, const float *C32,
                              const double *C64, int ldc, cudaStream_t s)
 {
     int ms, per_warp, wpc;
-    direct_shape(l, ms, per_warp, wpc);
+    direct_shape(mmax, ms, per_warp, wpc);
     size_t smem = (size_t)wpc * per_warp;
     if (smem > 220 * 1024) return cudaErrorInvalidValue;
-    int blocks = num_sms() * (wpc >= 8 ? 8 : 16 / wpc + 1);
+    // persistent grid: as many CTAs as can be resident (shared memory bound)
+    int per_sm = (int)std::max<size_t>(1, std::min<size_t>(2048 / (wpc * 32), (200 * 1024) / smem));
+    int blocks = num_sms() * per_sm;
     cudaError_t e;
     if (tp.precision == 0) {
         e = cudaFuncSetAttribute(ci_direct_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e != cudaSuccess) return e;
-        ci_direct_kernel<true><<<blocks, wpc * 32, smem, s>>>(g, tp, l, C32, C64, ldc, ms, per_warp); note_launch();
+        ci_direct_kernel<true><<<blocks, wpc * 32, smem, s>>>(g, tp, mmax, C32, C64, ldc, ms, per_warp); note_launch();
     } else {
         e = cudaFuncSetAttribute(ci_direct_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e != cudaSuccess) return e;
-        ci_direct_kernel<false><<<blocks, wpc * 32, smem, s>>>(g, tp, l, C32, C64, ldc, ms, per_warp); note_launch();
+        ci_direct_kernel<false><<<blocks, wpc * 32, smem, s>>>(g, tp, mmax, C32, C64, ldc, ms, per_warp); note_launch();
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_ci_complement(GraphDev g, TestParams tp, int l, cudaStream_t s)
+cudaError_t launch_ci_complement(GraphDev g, TestParams tp, cudaStream_t s)
 {
-    ci_complement_kernel<<<num_sms() * 8, 128, 0, s>>>(g, tp, l); note_launch();
+    ci_complement_kernel<<<num_sms() * 2, 128, 0, s>>>(g, tp); note_launch();
     return cudaGetLastError();
 }
 
-cudaError_t launch_prec_build(GraphDev g, const double *C64, int ldc, cudaStream_t s)
+cudaError_t launch_prec_update(GraphDev g, const double *C64, int ldc, cudaStream_t s)
 {
     int mmax = std::min(g.p + 1, PREC_MAX);
-    size_t smem = ((size_t)mmax * mmax + 2 * (size_t)mmax) * sizeof(double);
-    cudaError_t e = cudaFuncSetAttribute(prec_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    size_t smem = ((size_t)mmax * mmax + (size_t)mmax) * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(prec_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    prec_build_kernel<<<g.p, 512, smem, s>>>(g, C64, ldc); note_launch();
+    prec_update_kernel<<<g.p, 512, smem, s>>>(g, C64, ldc); note_launch();
     return cudaGetLastError();
 }
 
-cudaError_t launch_prec_downdate(GraphDev g, cudaStream_t s)
+cudaError_t launch_commit(GraphDev g, long long n_opairs_cap, int l_fixed, int explicit_sets,
+                          cudaStream_t s)
 {
-    prec_downdate_kernel<<<g.p, 512, 0, s>>>(g); note_launch();
-    return cudaGetLastError();
-}
-
-cudaError_t launch_commit(GraphDev g, TestParams tp, int l, long long n_opairs_cap,
-                          int explicit_sets, cudaStream_t s)
-{
-    (void)tp;
     long long cap = n_opairs_cap > 0 ? n_opairs_cap : 1;
-    int blocks = (int)std::min<long long>((cap + 255) / 256, (long long)num_sms() * 16);
-    commit_kernel<<<blocks, 256, 0, s>>>(g, l, explicit_sets, explicit_sets); note_launch();
+    int blocks = (int)std::min<long long>((cap + 255) / 256, (long long)num_sms() * 8);
+    commit_kernel<<<blocks, 256, 0, s>>>(g, l_fixed, explicit_sets, explicit_sets); note_launch();
     return cudaGetLastError();
 }
 
@@ -830,7 +845,7 @@ cudaError_t launch_ci_list(const int *ij, const int *S, int l, long long b, cons
                            uint8_t *indep_out, float *z_out, DevCounters *ctr, cudaStream_t s)
 {
     int ms, per_warp, wpc;
-    direct_shape(l, ms, per_warp, wpc);
+    direct_shape(l + 2, ms, per_warp, wpc);
     size_t smem = (size_t)wpc * per_warp;
     if (smem > 220 * 1024) return cudaErrorInvalidValue;
     long long warps = b;

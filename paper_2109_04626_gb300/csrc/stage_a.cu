@@ -12,18 +12,18 @@ __global__ void __launch_bounds__(1024) inverse_smem_kernel(double *A, int m, in
 {
     extern __shared__ double sm[];
     double *S = sm;                       // m x m
-    double *colk = S + m * m, *rowk = colk + m;
+    double *colk = S + m * m;
     __shared__ int bad;
     if (threadIdx.x == 0) bad = 0;
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) S[e] = A[(e / m) * (long long)lda + e % m];
     __syncthreads();
-    gj_inverse_block(S, m, m, colk, rowk, &bad);
+    sweep_inverse_block(S, m, m, colk, &bad);     // S = -A^{-1}
     __syncthreads();
     if (bad) {
         if (threadIdx.x == 0) *singular = 1;
         return;
     }
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) A[(e / m) * (long long)lda + e % m] = S[e];
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) A[(e / m) * (long long)lda + e % m] = -S[e];
 }
 
 // Large m: one pivot per pair of launches, A in global memory.
@@ -58,7 +58,7 @@ cudaError_t launch_inverse_spd(double *A, int m, int lda, double *work, int *sin
 {
     cudaError_t e = cudaMemsetAsync(singular, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
-    size_t smem = ((size_t)m * m + 2 * (size_t)m) * sizeof(double);
+    size_t smem = ((size_t)m * m + (size_t)m) * sizeof(double);
     if (smem <= 220 * 1024) {
         e = cudaFuncSetAttribute(inverse_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);

@@ -260,3 +260,39 @@ def test_full_size_conventional(fp, cfg):
     w = sem.WORKLOADS[cfg]
     X = sem.make(cfg).X
     _check_skeleton(fp, X, alpha=w["alpha"], max_level=w["max_level"], order=0, precision=2)
+
+
+@pytest.mark.parametrize("mode", ["host_loop", "timed"])
+def test_stage_loop_drivers_agree(fp, mode):
+    """The captured stage loop (CUDA graph, conditional WHILE) and the
+    host-driven loop (used for per-kernel timing) give the same result."""
+    for cfg, order in ((2, 1), (1, 0), (1, 1)):
+        X = sem.make(cfg).X
+        n, p = X.shape
+        C = oracle.pearson(X)
+        R = oracle.skeleton(C, n, 0.01, -1, reversed_order=bool(order))
+        opts = {"graph": 0} if mode == "host_loop" else {"timing": 1}
+        with fp.PC(n, p, 0.01, -1, order=order, **opts) as pc:
+            pc.corr(torch.from_numpy(X).cuda())
+            adj, st = pc.skeleton()
+            np.testing.assert_array_equal(adj, R["adj"])
+            assert pc.sepsets() == R["sepsets"]
+            assert st["tests_canonical"] == R["tests_total"]
+            assert st["levels_run"] == len(R["levels"])
+            if mode == "timed":
+                tm = fp.pc_timing(pc.h)
+                assert tm["bookkeeping"][1] > 0 and tm["corr"][1] > 0
+
+
+def test_levels_run_and_first_level_match_schedule(fp):
+    X = sem.make(2).X
+    n, p = X.shape
+    C = oracle.pearson(X)
+    for order in (1, 0):
+        R = oracle.skeleton(C, n, 0.01, -1, reversed_order=bool(order))
+        with fp.PC(n, p, 0.01, -1, order=order) as pc:
+            pc.corr(torch.from_numpy(X).cuda())
+            adj, st = pc.skeleton()
+        assert st["levels_run"] == len(R["levels"])
+        lv = R["levels"][1:] if order else R["levels"]
+        assert st["first_level"] == lv[0]
