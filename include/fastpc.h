@@ -165,6 +165,31 @@ int64_t pc_kernel_launches(void);
  * them afterwards).  ms and count have 6 entries; either may be NULL. */
 pc_status pc_timing(pc_handle *h, double *ms, int64_t *count, int32_t reset);
 
+/* pc_corr_noalloc -- the correlation matrix without any allocation, for
+ * callers that cannot call cudaMalloc: applications whose device memory is
+ * reserved up front by their own pool or budget, and latency-critical loops
+ * in which a cudaMalloc would synchronise the device.  The paper has no
+ * counterpart; it computes what pc_corr computes in FP64 (corr = Xs^T Xs / n
+ * of the FP64-standardised columns, unit diagonal), with no handle.
+ *   X      device pointer, n x p row-major, row stride ld >= p, dtype PC_F32 or
+ *          PC_F64 (caller-owned, read only)
+ *   C_out  device pointer, p x p row-major FP64, row stride ldc >= p
+ *          (caller-owned, fully written)
+ *   stream cudaStream_t to issue on (NULL: legacy default stream); returns
+ *          without synchronising
+ * Its scratch (column means and 1/sd) is a file-scope __device__ array sized
+ * for p <= 4096 (64 KiB on every GPU that loads the library, held until the
+ * process exits); p > 4096, n < 2, host pointers or a bad dtype/stride return
+ * PC_ERR_ARG before anything is launched.  It calls no cudaMalloc, cudaFree
+ * or other allocating routine.  The first call on each device looks up the
+ * array's device address with that device current (cudaGetSymbolAddress) and
+ * caches it; make that first call before any stream capture.  All calls share
+ * the one array: calls that overlap on the GPU (other streams, other host
+ * threads) race on it and must be serialised by the caller.  Each call
+ * overwrites the statistics it uses, so nothing needs clearing between calls. */
+pc_status pc_corr_noalloc(const void *X, int32_t dtype, int64_t n, int32_t p, int64_t ld,
+                          double *C_out, int64_t ldc, void *stream);
+
 const char *pc_last_error(const pc_handle *h);
 const char *pc_status_string(pc_status s);
 

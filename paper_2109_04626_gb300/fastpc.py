@@ -84,6 +84,7 @@ def load():
         "pc_fisher_threshold": (dbl, [dbl]),
         "pc_kernel_launches": (i64, []),
         "pc_timing": (i32, [vp, vp, vp, i32]),
+        "pc_corr_noalloc": (i32, [vp, i32, i64, i32, i64, vp, i64, vp]),
         "pc_last_error": (cs, [vp]),
         "pc_status_string": (cs, [i32]),
     }
@@ -238,6 +239,23 @@ def pc_timing(h, reset: bool = False) -> dict:
     _check(h, load().pc_timing(h, ctypes.c_void_p(ms.ctypes.data), ctypes.c_void_p(cnt.ctypes.data),
                                1 if reset else 0))
     return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(TIMING_CLASSES)}
+
+
+def pc_corr_noalloc(X, C_out, stream=None):
+    """FP64 correlation of X (n x p CUDA tensor, float32/float64, row-major)
+    into C_out (p x p float64 CUDA tensor) with no device allocation; see
+    include/fastpc.h.  Issued on ``stream`` (torch stream, raw handle or None)."""
+    import torch
+    assert X.dtype in (torch.float32, torch.float64) and X.stride(1) == 1
+    assert C_out.dtype == torch.float64 and C_out.stride(1) == 1
+    n, p = X.shape
+    dt = PC_F64 if X.dtype == torch.float64 else PC_F32
+    raw = 0 if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    st = load().pc_corr_noalloc(ctypes.c_void_p(X.data_ptr()), dt, int(n), int(p), int(X.stride(0)),
+                                ctypes.c_void_p(C_out.data_ptr()), int(C_out.stride(0)),
+                                ctypes.c_void_p(raw))
+    if st != 0:
+        raise PCError(st, "pc_corr_noalloc: p must be <= 4096, n >= 2, device pointers, valid dtype/strides")
 
 
 class PC:
