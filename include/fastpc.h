@@ -88,7 +88,15 @@ void pc_destroy(pc_handle *h);
  *   "complement"  1 = evaluate high stages from maintained neighbourhood precision
  *                 matrices (default), 0 = direct tests only
  *   "budget"      maximum tests one stage may schedule (default 2e10)
- *   "timing"      1 = record per-kernel-class CUDA-event times (pc_timing)
+ *   "timing"      1 = record per-kernel-class CUDA-event times (pc_timing); the
+ *                 stage loop is then driven from the host, one launch per kernel
+ *   "graph"       1 = run the stage loop as one CUDA graph whose conditional
+ *                 WHILE node is driven by the device (default); 0 = host loop
+ *   "learned"     1 = enumerate the conditioning sets of every ordered pair in
+ *                 the order proposed by the scoring network (needs parameters:
+ *                 pc_mlp_set_params or pc_mlp_train); 0 = lexicographic (default)
+ *   "learned_rows" capacity of the per-stage score buffer in rows (default 2^24);
+ *                 a stage with more candidate rows runs in lexicographic order
  * Unknown keys return PC_ERR_ARG. */
 pc_status pc_set_opt(pc_handle *h, const char *key, double val);
 pc_status pc_get_opt(pc_handle *h, const char *key, double *val);
@@ -160,9 +168,10 @@ int64_t pc_kernel_launches(void);
  * with CUDA events on its stream, grouped by kernel class: 0 correlation,
  * 1 closed-form stage l=p-2, 2 neighbourhood precision builds and downdates,
  * 3 direct CI tests, 4 complement CI tests, 5 stage bookkeeping (neighbour
- * lists, counts, scans, commit).  Writes per-class device milliseconds and
- * launch-group counts accumulated since the last reset (reset != 0 clears
- * them afterwards).  ms and count have 6 entries; either may be NULL. */
+ * lists, counts, scans, commit), 6 proposal scoring and ordering.  Writes
+ * per-class device milliseconds and launch-group counts accumulated since the
+ * last reset (reset != 0 clears them afterwards).  ms and count have 7
+ * entries; either may be NULL. */
 pc_status pc_timing(pc_handle *h, double *ms, int64_t *count, int32_t reset);
 
 /* pc_corr_noalloc -- the correlation matrix without any allocation, for
@@ -189,6 +198,35 @@ pc_status pc_timing(pc_handle *h, double *ms, int64_t *count, int32_t reset);
  * overwrites the statistics it uses, so nothing needs clearing between calls. */
 pc_status pc_corr_noalloc(const void *X, int32_t dtype, int64_t n, int32_t p, int64_t ld,
                           double *C_out, int64_t ldc, void *stream);
+
+/* ---- conditioning-set proposal network (no counterpart in the paper; it only
+ * changes the order in which Algorithm 1/2 enumerate the sets of an edge, so
+ * the skeleton is unchanged; every proposed sepset is re-verified in FP64).
+ * A member score s(u,v,k) for candidate k of the ordered pair (u,v):
+ *   h1 = relu(W1 x + b1) (16->128), h2 = relu(W2 h1 + b2) (128->128),
+ *   s = w3 . h2 + b3; training loss mean BCE(sigmoid(s), y).
+ * Parameters: one FP32 vector W1 (128x16 row-major), b1, W2 (128x128), b2, w3,
+ * b3 -- pc_mlp_nparam() values.  Forward on the tensor cores in BF16 with FP32
+ * accumulation; backward and Adam in FP32. */
+int32_t pc_mlp_nparam(void);
+/* theta: host or device, pc_mlp_nparam() floats; resets the Adam state. */
+pc_status pc_mlp_set_params(pc_handle *h, const float *theta, int64_t count);
+pc_status pc_mlp_get_params(pc_handle *h, float *theta, int64_t count);
+/* Features (16 floats per row, device) of R candidate rows given as device
+ * quadruples (u, v, k, l | d << 16): candidate k of the ordered pair (u, v) at
+ * stage l with candidate-set size d = |adj(u)\{v}|.  Needs pc_corr. */
+pc_status pc_mlp_features(pc_handle *h, const int32_t *quads, int64_t R, float *feats);
+/* Scores of R feature rows (device in, device out). */
+pc_status pc_mlp_forward(pc_handle *h, const float *feats, int64_t R, float *scores);
+/* Full-batch gradient of the mean BCE loss at the current parameters
+ * (grad_out: host or device, pc_mlp_nparam() floats; loss may be NULL). */
+pc_status pc_mlp_grad(pc_handle *h, const float *feats, const float *labels, int64_t R, float *grad_out,
+                      double *loss);
+/* Adam (lr, beta1 0.9, beta2 0.999, eps 1e-8) over contiguous mini-batches of
+ * the given rows (device), `epochs` passes; final_loss = mean loss of the last
+ * pass (may be NULL).  The caller shuffles the rows. */
+pc_status pc_mlp_train(pc_handle *h, const float *feats, const float *labels, int64_t R, int32_t epochs,
+                       int64_t batch, double lr, double *final_loss);
 
 const char *pc_last_error(const pc_handle *h);
 const char *pc_status_string(pc_status s);

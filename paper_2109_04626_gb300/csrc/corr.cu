@@ -49,6 +49,72 @@ __global__ void __launch_bounds__(256) col_stats_kernel(const T *__restrict__ X,
     }
 }
 
+// Column statistics over row chunks: CTA (column tile, chunk) computes the
+// chunk's count, mean and sum of squared deviations (two passes over the
+// chunk); col_stats_merge adds the chunks in a fixed order with Chan's update
+// M2 = M2a + M2b + (mb - ma)^2 na nb / (na + nb).  Population sd (1/n).
+template <typename T>
+__global__ void __launch_bounds__(256) col_stats_part_kernel(const T *__restrict__ X, long long n, int p,
+                                                             long long ld, long long rows_per,
+                                                             double *ws)
+{
+    __shared__ double red[8][33];
+    __shared__ double mu_s[32];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int col = blockIdx.x * 32 + tx;
+    const bool ok = col < p;
+    const long long r0 = (long long)blockIdx.y * rows_per;
+    const long long r1 = r0 + rows_per < n ? r0 + rows_per : n;
+    const double cnt = (double)(r1 - r0);
+    double s = 0.0;
+    if (ok)
+        for (long long t = r0 + ty; t < r1; t += 8) s += ld_as_double(X + t * ld + col);
+    red[ty][tx] = s;
+    __syncthreads();
+    if (ty == 0) {
+        double a = 0.0;
+        for (int k = 0; k < 8; ++k) a += red[k][tx];
+        mu_s[tx] = cnt > 0 ? a / cnt : 0.0;
+    }
+    __syncthreads();
+    const double mu = mu_s[tx];
+    double q = 0.0;
+    if (ok)
+        for (long long t = r0 + ty; t < r1; t += 8) {
+            double d = ld_as_double(X + t * ld + col) - mu;
+            q += d * d;
+        }
+    red[ty][tx] = q;
+    __syncthreads();
+    if (ty == 0 && ok) {
+        double a = 0.0;
+        for (int k = 0; k < 8; ++k) a += red[k][tx];
+        double *w = ws + (size_t)blockIdx.y * 3 * p;
+        w[col] = cnt;
+        w[p + col] = mu;
+        w[2 * p + col] = a;
+    }
+}
+
+__global__ void col_stats_merge_kernel(const double *ws, int chunks, int p, double *mean, double *rsd)
+{
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= p) return;
+    double na = 0.0, ma = 0.0, Ma = 0.0;
+    for (int c = 0; c < chunks; ++c) {
+        const double *w = ws + (size_t)c * 3 * p;
+        const double nb = w[col], mb = w[p + col], Mb = w[2 * p + col];
+        if (nb == 0.0) continue;
+        const double nn = na + nb, dl = mb - ma;
+        ma += dl * (nb / nn);
+        Ma += Mb + dl * dl * (na * nb / nn);
+        na = nn;
+    }
+    const double var = Ma / na;
+    mean[col] = ma;
+    rsd[col] = var > 0.0 ? 1.0 / sqrt(var) : 0.0;   // constant column -> zero column
+}
+
 // Xs = (X - mean) * rsd written K-major (column-major, row stride ldk = padded n)
 // as FP64, FP32 and a BF16 hi/lo split (hi = bf16(x), lo = bf16(x - hi)).
 // 32 x 32 tiles transposed through shared memory.
@@ -209,11 +275,12 @@ __global__ void __launch_bounds__(256) syrk_reduce_kernel(const double *ws, int 
 {
     constexpr int BT = 64;
     const int tile = blockIdx.x, nt = (p + BT - 1) / BT;
+    const int e0 = blockIdx.y * (BT * BT / 8), e1 = e0 + BT * BT / 8;
     int t = tile, bi = 0;
     while (t >= nt - bi) { t -= nt - bi; ++bi; }
     const int bj = bi + t;
     const double inv_n = 1.0 / (double)n;
-    for (int e = threadIdx.x; e < BT * BT; e += blockDim.x) {
+    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
         const int r = e / BT, c = e % BT;
         const int a = bi * BT + r, b = bj * BT + c;
         if (a >= p || b >= p || (bi == bj && r > c)) continue;
@@ -276,6 +343,39 @@ cudaError_t launch_col_stats(const void *X, int dtype, long long n, int p, long 
     return cudaGetLastError();
 }
 
+static void stats_shape(long long n, int &chunks, long long &rows_per)
+{
+    long long c = (n + 511) / 512;
+    if (c > 128) c = 128;
+    if (c < 1) c = 1;
+    rows_per = (n + c - 1) / c;
+    chunks = (int)((n + rows_per - 1) / rows_per);
+}
+
+size_t col_stats_ws_bytes(long long n, int p)
+{
+    int chunks;
+    long long rows_per;
+    stats_shape(n, chunks, rows_per);
+    return (size_t)chunks * 3 * p * sizeof(double);
+}
+
+cudaError_t launch_col_stats_split(const void *X, int dtype, long long n, int p, long long ld,
+                                   double *mean, double *rsd, double *ws, cudaStream_t s)
+{
+    int chunks;
+    long long rows_per;
+    stats_shape(n, chunks, rows_per);
+    dim3 g((p + 31) / 32, chunks);
+    if (dtype == 1)
+        col_stats_part_kernel<double><<<g, 256, 0, s>>>((const double *)X, n, p, ld, rows_per, ws);
+    else
+        col_stats_part_kernel<float><<<g, 256, 0, s>>>((const float *)X, n, p, ld, rows_per, ws);
+    note_launch();
+    col_stats_merge_kernel<<<(p + 127) / 128, 128, 0, s>>>(ws, chunks, p, mean, rsd); note_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_standardize(const void *X, int dtype, long long n, int p, long long ld,
                                const double *mean, const double *rsd, double *Xs64,
                                float *Xs32, uint16_t *Xhi, uint16_t *Xlo, long long ldk,
@@ -300,7 +400,7 @@ cudaError_t launch_syrk_f64(const double *Xs, long long n, long long ldk, int p,
     syrk_split_shape(n, p, ntiles, splits, kchunk);
     if (ws_bytes < (size_t)ntiles * splits * 64 * 64 * sizeof(double)) return cudaErrorInvalidValue;
     syrk_f64_split_kernel<<<dim3(ntiles, splits), 256, 0, s>>>(Xs, n, ldk, p, kchunk, ws); note_launch();
-    syrk_reduce_kernel<<<ntiles, 256, 0, s>>>(ws, p, ntiles, splits, n, C64, ldc); note_launch();
+    syrk_reduce_kernel<<<dim3(ntiles, 8), 256, 0, s>>>(ws, p, ntiles, splits, n, C64, ldc); note_launch();
     return cudaGetLastError();
 }
 

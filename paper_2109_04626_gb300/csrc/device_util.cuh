@@ -39,16 +39,41 @@ __device__ __forceinline__ void sweep_inverse_block(double *A, int m, int lda, d
 }
 
 // Lexicographic unranking: positions pos[0..l) (ascending, in 0..d-1) of the
-// rank-th l-subset of d items; the number of subsets whose i-th position is x
-// is C(d-x-1, l-i-1).  binom is the (ldb x ldb) saturating table.
+// rank-th l-subset of d items.  The number of subsets whose i-th position is
+// x (positions before it fixed) is C(d-x-1, l-i-1), and by the hockey-stick
+// identity those with i-th position in [x0, x1) number C(d-x0, l-i) -
+// C(d-x1, l-i).  Each position is therefore either walked to (O(d) steps in
+// total, best when l is close to d) or found by binary search (O(l log d)
+// steps, best for small l).  binom is the (ldb x ldb) saturating table; rank
+// must be < C(d, l), in which case no table entry read here saturates.
 __device__ __forceinline__ void unrank_lex(unsigned long long rank, int d, int l,
                                            const unsigned long long *binom, int ldb, int *pos)
 {
+    int lg = 0;
+    while ((1 << lg) < d + 1) ++lg;
+    if (l * lg < d) {
+        int x = 0;
+        for (int i = 0; i < l; ++i) {
+            const int r1 = l - i;                              // size of the remaining subset
+            const unsigned long long base = __ldg(binom + (long long)(d - x) * ldb + r1);
+            const unsigned long long target = base - rank;     // want C(d-x', r1) >= target
+            int lo = x, hi = d - r1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (__ldg(binom + (long long)(d - mid) * ldb + r1) >= target) lo = mid;
+                else hi = mid - 1;
+            }
+            pos[i] = lo;
+            rank -= base - __ldg(binom + (long long)(d - lo) * ldb + r1);
+            x = lo + 1;
+        }
+        return;
+    }
     int x = 0;
     for (int i = 0; i < l; ++i) {
         // x never passes d-(l-i): there C(l-i-1, l-i-1) = 1 > any valid remainder
         while (x < d - (l - i)) {
-            unsigned long long c = binom[(long long)(d - x - 1) * ldb + (l - i - 1)];
+            unsigned long long c = __ldg(binom + (long long)(d - x - 1) * ldb + (l - i - 1));
             if (rank < c) break;
             rank -= c;
             ++x;

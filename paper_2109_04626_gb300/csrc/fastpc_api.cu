@@ -23,7 +23,7 @@ namespace fpc {
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 }
 
-constexpr int NCLS = 6;
+constexpr int NCLS = 7;
 struct TimedPair {
     int cls;
     cudaEvent_t a, b;
@@ -76,14 +76,27 @@ struct pc_handle {
     cudaGraphConditionalHandle hcond = 0;
     std::vector<double> graph_key;
     long long body_kernels = 0;      // kernel nodes in the captured stage body
-    double *syrk_ws = nullptr;
+    double *syrk_ws = nullptr, *stats_ws = nullptr;
+    size_t stats_ws_bytes = 0;
     size_t syrk_ws_bytes = 0;
+    // proposal network
+    int learned = 0;
+    float *theta = nullptr, *adam_m = nullptr, *adam_v = nullptr, *grad = nullptr;
+    uint8_t *wpack = nullptr;
+    int *mlp_err = nullptr;
+    double *mlp_loss = nullptr;
+    bool have_params = false;
+    int adam_step = 0;
+    unsigned long long *row_off = nullptr;
+    short *perm = nullptr;
+    float *stage_scores = nullptr;
+    long long rows_cap = 0;
     // per-kernel-class timing
     int timing = 0;
     std::vector<TimedPair> pending;
     std::vector<cudaEvent_t> evpool;
-    double cls_ms[NCLS] = {0, 0, 0, 0, 0, 0};
-    long long cls_n[NCLS] = {0, 0, 0, 0, 0, 0};
+    double cls_ms[NCLS] = {0, 0, 0, 0, 0, 0, 0};
+    long long cls_n[NCLS] = {0, 0, 0, 0, 0, 0, 0};
 };
 
 // Brackets the launches of one kernel class with events on the handle's stream.
@@ -252,6 +265,13 @@ extern "C" pc_status pc_create(int64_t n, int32_t p, double alpha, int32_t max_l
     A(dalloc(h, &h->C32, (size_t)p * h->ldc * sizeof(float)));
     A(dalloc(h, &h->singular, sizeof(int)));
     A(dalloc(h, &h->tc_err, sizeof(int)));
+    A(dalloc(h, &h->mlp_err, sizeof(int)));
+    A(dalloc(h, &h->mlp_loss, sizeof(double)));
+    A(dalloc(h, &h->theta, (size_t)fpc::mlp_nparam() * sizeof(float)));
+    A(dalloc(h, &h->adam_m, (size_t)fpc::mlp_nparam() * sizeof(float)));
+    A(dalloc(h, &h->adam_v, (size_t)fpc::mlp_nparam() * sizeof(float)));
+    A(dalloc(h, &h->grad, (size_t)fpc::mlp_nparam() * sizeof(float)));
+    A(dalloc(h, &h->wpack, fpc::mlp_pack_bytes()));
     A(dalloc(h, &h->work, (size_t)(2 * p + 16) * sizeof(double)));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&h->info_h, sizeof(LevelInfo));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&h->ctr_h, sizeof(DevCounters));
@@ -327,6 +347,13 @@ extern "C" pc_status pc_set_opt(pc_handle *h, const char *key, double val)
     } else if (k == "complement") h->complement = val != 0;
     else if (k == "timing") h->timing = val != 0;
     else if (k == "graph") h->use_graph = val != 0;
+    else if (k == "learned") {
+        if (val != 0 && !h->have_params) return fail(h, PC_ERR_STATE, "learned order needs parameters (pc_mlp_set_params or pc_mlp_train)");
+        h->learned = val != 0;
+    } else if (k == "learned_rows") {
+        if (!(val >= 0)) return fail(h, PC_ERR_ARG, "learned_rows must be >= 0");
+        h->rows_cap = (long long)val;
+    }
     else if (k == "budget") {
         if (!(val > 0)) return fail(h, PC_ERR_ARG, "budget must be > 0");
         h->budget = val;
@@ -346,6 +373,8 @@ extern "C" pc_status pc_get_opt(pc_handle *h, const char *key, double *val)
     else if (k == "complement") *val = h->complement;
     else if (k == "timing") *val = h->timing;
     else if (k == "graph") *val = h->use_graph;
+    else if (k == "learned") *val = h->learned;
+    else if (k == "learned_rows") *val = (double)h->rows_cap;
     else if (k == "budget") *val = h->budget;
     else if (k == "tensor_core_gemm") *val = h->used_tc ? 1.0 : 0.0;
     else return fail(h, PC_ERR_ARG, "unknown option: " + k);
@@ -449,7 +478,14 @@ extern "C" pc_status pc_corr(pc_handle *h, const void *X, int32_t dtype, int64_t
         CK(cudaMemsetAsync(h->Xlo, 0, plane * sizeof(uint16_t), s));
     }
     Timed tm(h, 0);
-    CK(fpc::launch_col_stats(Xd, dtype, n, p, ld, h->mean, h->rsd, s));
+    const size_t sws = fpc::col_stats_ws_bytes(n, p);
+    if (sws > h->stats_ws_bytes) {
+        dfree(h, h->stats_ws);
+        h->stats_ws = nullptr;
+        CK(dalloc(h, &h->stats_ws, sws));
+        h->stats_ws_bytes = sws;
+    }
+    CK(fpc::launch_col_stats_split(Xd, dtype, n, p, ld, h->mean, h->rsd, h->stats_ws, s));
     const bool want_bf16 = h->precision == 2 && fpc::tc_gemm_available();
     CK(fpc::launch_standardize(Xd, dtype, n, p, ld, h->mean, h->rsd, h->Xs64,
                                h->precision == 1 ? h->Xs32 : nullptr,
@@ -536,6 +572,12 @@ static pc_status enqueue_level(pc_handle *h, cudaStream_t s, int mmax, bool use_
         auto t = T(5);
         CK(fpc::launch_head(g, tp, h->budget, mmax, s));
     }
+    if (h->learned) {
+        auto t = T(6);
+        const float sqn_over_q = (float)(std::sqrt((double)h->n) / h->q);
+        CK(fpc::launch_mlp_score_stage(g, h->row_off, h->rows_cap, h->C32, h->ldc, sqn_over_q, h->wpack,
+                                       h->theta, h->stage_scores, h->perm, h->mlp_err, s));
+    }
     {
         auto t = T(3);
         CK(fpc::launch_ci_direct(g, tp, mmax, h->C32, h->C64, h->ldc, s));
@@ -560,7 +602,7 @@ static pc_status enqueue_level(pc_handle *h, cudaStream_t s, int mmax, bool use_
 static std::vector<double> graph_key(const pc_handle *h)
 {
     return {(double)h->order, (double)h->complement, (double)h->precision, h->band, h->guard,
-            (double)h->used_tc,
+            (double)h->used_tc, (double)h->learned, (double)(uintptr_t)h->perm, (double)h->rows_cap,
             h->budget, (double)level_cap(h), (double)(uintptr_t)h->g.pool, (double)h->g.pool_cap,
             (double)(uintptr_t)h->C32, (double)(uintptr_t)h->C64};
 }
@@ -635,6 +677,22 @@ static pc_status skeleton_once(pc_handle *h, pc_stats *st, bool *overflow)
     *overflow = false;
     const bool timed = h->timing != 0;
     const bool graph = h->use_graph && !timed;
+    if (h->learned) {
+        if (!h->row_off) {
+            if (h->rows_cap <= 0) h->rows_cap = 1ll << 24;
+            CK(dalloc(h, &h->row_off, (size_t)(p + 2) * sizeof(ull)));
+            CK(dalloc(h, &h->perm, (size_t)h->rows_cap * sizeof(short)));
+            CK(dalloc(h, &h->stage_scores, (size_t)h->rows_cap * sizeof(float)));
+        }
+        g.row_off = h->row_off;
+        g.perm = h->perm;
+        g.rows_cap = h->rows_cap;
+        CK(cudaMemsetAsync(h->mlp_err, 0, sizeof(int), s));
+    } else {
+        g.row_off = nullptr;
+        g.perm = nullptr;
+        g.rows_cap = 0;
+    }
     if (graph) {
         if (pc_status r = ensure_graph(h)) return r;
     }
@@ -724,6 +782,7 @@ static pc_status skeleton_once(pc_handle *h, pc_stats *st, bool *overflow)
         }
     }
     CK(cudaEventRecord(h->ev1, s));
+    if (h->learned) CK(fpc::launch_reverify(g, tp, h->C64, h->ldc, s));
     if (pc_status r = read_info(h)) return r;
     if (!h->info_h->done) return fail(h, PC_ERR_INTERNAL, "stage loop did not finish");
     CK(cudaMemcpyAsync(h->ctr_h, g.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
@@ -731,7 +790,10 @@ static pc_status skeleton_once(pc_handle *h, pc_stats *st, bool *overflow)
     const DevCounters &c = *h->ctr_h;
     const LevelInfo &I = *h->info_h;
     if (graph) g_launches.fetch_add((long long)I.body_runs * h->body_kernels);
-    if (c.status) return fail(h, (pc_status)c.status, "device-side error during the skeleton search");
+    if (c.status)
+        return fail(h, (pc_status)c.status,
+                    h->learned ? "device-side error during the skeleton search (or a proposed sepset failed the FP64 re-verification)"
+                               : "device-side error during the skeleton search");
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
     st->tests_executed = c.tests_executed;
@@ -884,4 +946,160 @@ extern "C" pc_status pc_last_stats(pc_handle *h, pc_stats *out)
     if (!h || !out) return PC_ERR_ARG;
     *out = h->last;
     return PC_OK;
+}
+
+// ---------------------------------------------------------------- proposal network
+extern "C" int32_t pc_mlp_nparam(void) { return fpc::mlp_nparam(); }
+
+extern "C" pc_status pc_mlp_set_params(pc_handle *h, const float *theta, int64_t count)
+{
+    if (!h || !theta || count != fpc::mlp_nparam()) return PC_ERR_ARG;
+    cudaStream_t s = h->stream;
+    const size_t bytes = (size_t)count * sizeof(float);
+    CK(cudaMemcpyAsync(h->theta, theta, bytes, cudaMemcpyDefault, s));
+    CK(cudaMemsetAsync(h->adam_m, 0, bytes, s));
+    CK(cudaMemsetAsync(h->adam_v, 0, bytes, s));
+    CK(fpc::launch_mlp_pack(h->theta, h->wpack, s));
+    CK(cudaStreamSynchronize(s));
+    h->have_params = true;
+    h->adam_step = 0;
+    return PC_OK;
+}
+
+extern "C" pc_status pc_mlp_get_params(pc_handle *h, float *theta, int64_t count)
+{
+    if (!h || !theta || count != fpc::mlp_nparam()) return PC_ERR_ARG;
+    if (!h->have_params) return fail(h, PC_ERR_STATE, "no parameters set");
+    CK(cudaMemcpyAsync(theta, h->theta, (size_t)count * sizeof(float), cudaMemcpyDefault, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return PC_OK;
+}
+
+extern "C" pc_status pc_mlp_features(pc_handle *h, const int32_t *quads, int64_t R, float *feats)
+{
+    if (!h || (R > 0 && (!quads || !feats)) || R < 0) return PC_ERR_ARG;
+    if (!h->have_corr) return fail(h, PC_ERR_STATE, "pc_mlp_features before pc_corr");
+    if (R == 0) return PC_OK;
+    CK(cudaMemsetAsync(h->mlp_err, 0, sizeof(int), h->stream));
+    CK(fpc::launch_mlp_features(quads, R, h->C32, h->ldc, h->p, h->n, h->q, feats, h->mlp_err, h->stream));
+    int e = 0;
+    CK(cudaMemcpyAsync(&e, h->mlp_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (e) return fail(h, PC_ERR_ARG, "pc_mlp_features: node id out of range or repeated in a quadruple");
+    return PC_OK;
+}
+
+// forward (and, with h1/h2, the activations a backward pass needs)
+static pc_status mlp_forward(pc_handle *h, const float *feats, long long R, float *scores, __nv_bfloat16 *h1,
+                             float *h2)
+{
+    CK(cudaMemsetAsync(h->mlp_err, 0, sizeof(int), h->stream));
+    CK(fpc::launch_mlp_forward_feats(feats, R, h->wpack, h->theta, scores, h1, h2, h->mlp_err, h->g, h->stream));
+    return PC_OK;
+}
+
+static pc_status mlp_check_err(pc_handle *h)
+{
+    int e = 0;
+    CK(cudaMemcpyAsync(&e, h->mlp_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (e) return fail(h, (pc_status)e, "proposal network: a bounded wait in the tensor-core forward pass expired");
+    return PC_OK;
+}
+
+extern "C" pc_status pc_mlp_forward(pc_handle *h, const float *feats, int64_t R, float *scores)
+{
+    if (!h || R < 0 || (R > 0 && (!feats || !scores))) return PC_ERR_ARG;
+    if (!h->have_params) return fail(h, PC_ERR_STATE, "no parameters set");
+    if (R == 0) return PC_OK;
+    if (pc_status r = mlp_forward(h, feats, R, scores, nullptr, nullptr)) return r;
+    return mlp_check_err(h);
+}
+
+struct MlpWork {
+    float *scores = nullptr, *h2 = nullptr;
+    __nv_bfloat16 *h1 = nullptr;
+};
+
+static pc_status mlp_work(pc_handle *h, long long rows, MlpWork &w)
+{
+    CK(dalloc(h, &w.scores, (size_t)rows * sizeof(float)));
+    CK(dalloc(h, &w.h2, (size_t)rows * 128 * sizeof(float)));
+    CK(dalloc(h, &w.h1, (size_t)rows * 128 * sizeof(__nv_bfloat16)));
+    return PC_OK;
+}
+
+static void mlp_work_free(pc_handle *h, MlpWork &w)
+{
+    dfree(h, w.scores);
+    dfree(h, w.h2);
+    dfree(h, w.h1);
+}
+
+extern "C" pc_status pc_mlp_grad(pc_handle *h, const float *feats, const float *labels, int64_t R, float *grad_out,
+                                 double *loss)
+{
+    if (!h || R <= 0 || !feats || !labels) return PC_ERR_ARG;
+    if (!h->have_params) return fail(h, PC_ERR_STATE, "no parameters set");
+    MlpWork w;
+    pc_status st = mlp_work(h, R, w);
+    if (st == PC_OK) st = mlp_forward(h, feats, R, w.scores, w.h1, w.h2);
+    if (st == PC_OK) {
+        cudaError_t e = cudaMemsetAsync(h->mlp_loss, 0, sizeof(double), h->stream);
+        if (e == cudaSuccess)
+            e = fpc::launch_mlp_backward(feats, labels, w.scores, w.h1, w.h2, R, 1.0f / (float)R, h->theta, h->grad,
+                                         h->mlp_loss, h->stream);
+        if (e != cudaSuccess) st = cuda_fail(h, e, "pc_mlp_grad");
+    }
+    if (st == PC_OK) st = mlp_check_err(h);
+    if (st == PC_OK && grad_out) {
+        cudaError_t e = cudaMemcpy(grad_out, h->grad, (size_t)fpc::mlp_nparam() * sizeof(float), cudaMemcpyDefault);
+        if (e != cudaSuccess) st = cuda_fail(h, e, "pc_mlp_grad copy");
+    }
+    if (st == PC_OK && loss) {
+        double ls = 0;
+        cudaError_t e = cudaMemcpy(&ls, h->mlp_loss, sizeof(double), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) st = cuda_fail(h, e, "pc_mlp_grad loss");
+        *loss = ls / (double)R;
+    }
+    cudaStreamSynchronize(h->stream);
+    mlp_work_free(h, w);
+    return st;
+}
+
+extern "C" pc_status pc_mlp_train(pc_handle *h, const float *feats, const float *labels, int64_t R, int32_t epochs,
+                                  int64_t batch, double lr, double *final_loss)
+{
+    if (!h || R <= 0 || !feats || !labels || epochs < 1 || batch < 1 || !(lr > 0)) return PC_ERR_ARG;
+    if (!h->have_params) return fail(h, PC_ERR_STATE, "no parameters set");
+    const long long B = std::min<long long>(batch, R);
+    MlpWork w;
+    pc_status st = mlp_work(h, B, w);
+    cudaStream_t s = h->stream;
+    double last = 0.0;
+    for (int ep = 0; ep < epochs && st == PC_OK; ++ep) {
+        cudaError_t e = cudaMemsetAsync(h->mlp_loss, 0, sizeof(double), s);
+        for (long long b0 = 0; b0 < R && e == cudaSuccess && st == PC_OK; b0 += B) {
+            const long long nb = std::min<long long>(B, R - b0);
+            st = mlp_forward(h, feats + b0 * 16, nb, w.scores, w.h1, w.h2);
+            if (st != PC_OK) break;
+            e = fpc::launch_mlp_backward(feats + b0 * 16, labels + b0, w.scores, w.h1, w.h2, nb, 1.0f / (float)nb,
+                                         h->theta, h->grad, h->mlp_loss, s);
+            if (e == cudaSuccess) e = fpc::launch_adam(h->theta, h->grad, h->adam_m, h->adam_v, (float)lr, ++h->adam_step, s);
+            if (e == cudaSuccess) e = fpc::launch_mlp_pack(h->theta, h->wpack, s);
+        }
+        if (e != cudaSuccess && st == PC_OK) st = cuda_fail(h, e, "pc_mlp_train");
+        if (st == PC_OK) {
+            double ls = 0;
+            e = cudaMemcpyAsync(&ls, h->mlp_loss, sizeof(double), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) st = cuda_fail(h, e, "pc_mlp_train loss");
+            last = ls / (double)R;
+        }
+    }
+    if (st == PC_OK) st = mlp_check_err(h);
+    cudaStreamSynchronize(s);
+    mlp_work_free(h, w);
+    if (final_loss) *final_loss = last;
+    return st;
 }

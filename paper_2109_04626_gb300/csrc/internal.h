@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <cuda_bf16.h>
 
 namespace fpc {
 
@@ -78,6 +79,12 @@ struct GraphDev {
     int *prec_mem;              // p x PREC_MAX: member node ids (ascending, u included)
     short *prec_pos;            // p x p: slot of node w in block u, -1 = absent/dead
     int *prec_need;             // p: build request flags
+    // learned proposal (optional): per node, the first score row of its
+    // candidates (pair j, position x) and, per row, the candidate position at
+    // each place of the proposal order
+    unsigned long long *row_off;   // p+1 (nullptr: plain lexicographic order)
+    const short *perm;
+    long long rows_cap;
     LevelInfo *info;
     DevCounters *ctr;
 };
@@ -101,6 +108,9 @@ void note_launch();
 // ---- correlation (corr.cu)
 cudaError_t launch_col_stats(const void *X, int dtype, long long n, int p, long long ld,
                              double *mean, double *rsd, cudaStream_t s);
+cudaError_t launch_col_stats_split(const void *X, int dtype, long long n, int p, long long ld,
+                                   double *mean, double *rsd, double *ws, cudaStream_t s);
+size_t col_stats_ws_bytes(long long n, int p);
 cudaError_t launch_standardize(const void *X, int dtype, long long n, int p, long long ld,
                                const double *mean, const double *rsd, double *Xs64,
                                float *Xs32, uint16_t *Xhi, uint16_t *Xlo, long long ldk,
@@ -137,6 +147,24 @@ cudaError_t launch_prec_update(GraphDev g, const double *C64, int ldc, cudaStrea
 cudaError_t launch_commit(GraphDev g, long long n_opairs_cap, int l_fixed, int explicit_sets,
                           cudaStream_t s);
 size_t scan_ws_bytes(long long n);
+
+// ---- proposal network (mlp.cu)
+int mlp_nparam();
+size_t mlp_pack_bytes();
+cudaError_t launch_mlp_pack(const float *theta, uint8_t *wpack, cudaStream_t s);
+cudaError_t launch_mlp_forward_feats(const float *feats, long long R, const uint8_t *wpack, const float *theta,
+                                     float *scores, __nv_bfloat16 *h1, float *h2, int *err, GraphDev g,
+                                     cudaStream_t s);
+cudaError_t launch_mlp_score_stage(GraphDev g, const unsigned long long *row_off, long long rows_cap,
+                                   const float *C32, int ldc, float sqn_over_q, const uint8_t *wpack,
+                                   const float *theta, float *scores, short *perm, int *err, cudaStream_t s);
+cudaError_t launch_mlp_backward(const float *feats, const float *labels, const float *scores,
+                                const __nv_bfloat16 *h1, const float *h2, long long R, float inv_b,
+                                const float *theta, float *grad, double *loss, cudaStream_t s);
+cudaError_t launch_adam(float *theta, const float *grad, float *m, float *v, float lr, int step, cudaStream_t s);
+cudaError_t launch_mlp_features(const int *quads, long long R, const float *C32, int ldc, int p, long long n,
+                                double q, float *feats, int *err, cudaStream_t s);
+cudaError_t launch_reverify(GraphDev g, TestParams tp, const double *C64, int ldc, cudaStream_t s);
 
 // ---- raw test batches (level.cu)
 cudaError_t launch_ci_list(const int *ij, const int *S, int l, long long b, const float *C32,

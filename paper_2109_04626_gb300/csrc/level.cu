@@ -188,14 +188,17 @@ __global__ void __launch_bounds__(1024) head_kernel(GraphDev g, TestParams tp, d
 {
     LevelInfo *I = g.info;
     if (stopped(I)) return;
-    __shared__ ull pd[1024], pc[1024];
+    __shared__ ull pd[1024], pc[1024], pr[1024];
     __shared__ int ssat;
     const int p = g.p, l = I->l, t = threadIdx.x;
     if (t == 0) ssat = 0;
     __syncthreads();
     const int per = (p + 1023) / 1024;
     const int s0 = min(p, t * per), s1 = min(p, s0 + per);
-    ull sd = 0, sc = 0;
+    // proposal rows: a node whose pairs have at least two sets to order gets
+    // deg*(deg-1) score rows (pair j, candidate position x)
+    auto prows = [&](int dg, ull T) -> ull { return (g.row_off && l >= 1 && T >= 2) ? (ull)dg * (ull)(dg - 1) : 0ull; };
+    ull sd = 0, sc = 0, sr = 0;
     for (int u = s0; u < s1; ++u) {
         const int dg = g.deg[u], d = dg - 1;
         const ull T = (dg > 0 && d >= l) ? g.binom[(long long)d * (p + 1) + l] : 0ull;
@@ -204,18 +207,23 @@ __global__ void __launch_bounds__(1024) head_kernel(GraphDev g, TestParams tp, d
         const bool comp = T && comp_eligible(d, l, tp) && g.prec_m[u] > 0;
         if (comp) sc = sat_add(sc, tot);
         else sd = sat_add(sd, tot);
+        sr += prows(dg, T);
     }
     pd[t] = sd;
     pc[t] = sc;
+    pr[t] = sr;
     __syncthreads();
     for (int off = 1; off < 1024; off <<= 1) {
         ull a = t >= off ? pd[t - off] : 0ull, b = t >= off ? pc[t - off] : 0ull;
+        ull c = t >= off ? pr[t - off] : 0ull;
         __syncthreads();
         pd[t] = sat_add(pd[t], a);
         pc[t] = sat_add(pc[t], b);
+        pr[t] += c;
         __syncthreads();
     }
-    ull rd = t ? pd[t - 1] : 0ull, rc = t ? pc[t - 1] : 0ull;
+    ull rd = t ? pd[t - 1] : 0ull, rc = t ? pc[t - 1] : 0ull, rr = t ? pr[t - 1] : 0ull;
+    const bool rows_fit = pr[1023] <= (ull)g.rows_cap;   // else: plain order this stage
     for (int u = s0; u < s1; ++u) {
         const int dg = g.deg[u], d = dg - 1;
         const ull T = (dg > 0 && d >= l) ? g.binom[(long long)d * (p + 1) + l] : 0ull;
@@ -223,14 +231,17 @@ __global__ void __launch_bounds__(1024) head_kernel(GraphDev g, TestParams tp, d
         const bool comp = T && comp_eligible(d, l, tp) && g.prec_m[u] > 0;
         g.tn_off[u] = rd;
         g.cn_off[u] = rc;
+        if (g.row_off) g.row_off[u] = rows_fit ? rr : 0ull;
         if (comp) rc = sat_add(rc, tot);
         else rd = sat_add(rd, tot);
+        rr += prows(dg, T);
     }
     __syncthreads();
     if (t == 0) {
         const ull td = pd[1023], tc = pc[1023];
         g.tn_off[p] = td;
         g.cn_off[p] = tc;
+        if (g.row_off) g.row_off[p] = rows_fit ? pr[1023] : 0ull;
         I->total_direct = td;
         I->total_comp = tc;
         I->saturated = ssat || td == KEY_NONE || tc == KEY_NONE;
@@ -401,6 +412,30 @@ __device__ __forceinline__ void flush_acc(const WarpAcc &acc, DevCounters *ctr)
     if (acc.maxdz > 0.f) atomic_max_float_pos(&ctr->max_dz_bits, acc.maxdz);
 }
 
+// Candidate position x of the ordered pair (u, j) (d candidates) -> index into
+// nbr[u] (v sits at index j), through the proposal order when the stage has one.
+__device__ __forceinline__ int cand_index(const GraphDev &g, int u, int j, int d, int x)
+{
+    if (g.row_off) {
+        const ull b = g.row_off[u];
+        if (g.row_off[u + 1] > b) x = g.perm[b + (ull)j * d + x];
+    }
+    return x + (x >= j);
+}
+
+__device__ __forceinline__ void sort_small(int *a, int n)
+{
+    for (int i = 1; i < n; ++i) {
+        const int x = a[i];
+        int k = i - 1;
+        while (k >= 0 && a[k] > x) {
+            a[k + 1] = a[k];
+            --k;
+        }
+        a[k + 1] = x;
+    }
+}
+
 // ---------------------------------------------------------------- direct path (skeleton)
 template <bool F64>
 __global__ void __launch_bounds__(256) ci_direct_kernel(GraphDev g, TestParams tp, int mmax,
@@ -435,10 +470,8 @@ __global__ void __launch_bounds__(256) ci_direct_kernel(GraphDev g, TestParams t
         if (*(volatile ull *)bp < key) continue;   // an earlier set already separates
         if (lane == 0) {
             unrank_lex(rank, d, l, g.binom, p + 1, pos);
-            for (int i = 0; i < l; ++i) {
-                int x = pos[i];
-                nd[i] = g.nbr[(long long)u * p + x + (x >= j)];
-            }
+            for (int i = 0; i < l; ++i) nd[i] = g.nbr[(long long)u * p + cand_index(g, u, j, d, pos[i])];
+            if (g.row_off) sort_small(nd, l);        // the set is tested in ascending-id order
             nd[l] = u;
             nd[l + 1] = v;
         }
@@ -486,10 +519,8 @@ __global__ void __launch_bounds__(128) ci_complement_kernel(GraphDev g, TestPara
         const short *ps = g.prec_pos + (long long)u * p;
         const int su = ps[u], sv = ps[v];
         int sr[KC_MAX];
-        for (int i = 0; i < k; ++i) {
-            int x = posR[i];
-            sr[i] = ps[g.nbr[(long long)u * p + x + (x >= j)]];
-        }
+        for (int i = 0; i < k; ++i) sr[i] = ps[g.nbr[(long long)u * p + cand_index(g, u, j, d, posR[i])]];
+        if (g.row_off) sort_small(sr, k);
         double L[KC_MAX][KC_MAX], yu[KC_MAX], yv[KC_MAX];
         bool bad = false;
         for (int i = 0; i < k && !bad; ++i) {
@@ -556,16 +587,33 @@ __global__ void __launch_bounds__(512) prec_update_kernel(GraphDev g, const doub
     const int p = g.p;
     const int m0 = g.prec_m[u];
     if (m0 > 0) {
+        __shared__ int nrem;
+        int *rem = mem;                                // the member scratch is free here
         double *colw = smd;
         double *P = g.prec + (long long)u * PREC_MAX * PREC_MAX;
         const int *pm = g.prec_mem + (long long)u * PREC_MAX;
         short *pos = g.prec_pos + (long long)u * p;
         const uint32_t *row = g.adj + (long long)u * g.W;
-        ull fl = 0;
-        for (int s = 0; s < m0; ++s) {
-            const int w = pm[s];
-            if (w == u || pos[w] < 0) continue;
-            if ((row[w >> 5] >> (w & 31)) & 1u) continue;   // still adjacent
+        // members deleted by the last commit, in ascending slot order (deterministic)
+        if (threadIdx.x < 32) {
+            int cnt = 0;
+            for (int s0 = 0; s0 < m0; s0 += 32) {
+                const int s = s0 + threadIdx.x;
+                bool gone = false;
+                if (s < m0) {
+                    const int w = pm[s];
+                    gone = w != u && pos[w] >= 0 && !((row[w >> 5] >> (w & 31)) & 1u);
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, gone);
+                if (gone) rem[cnt + __popc(bal & ((1u << threadIdx.x) - 1u))] = s;
+                cnt += __popc(bal);
+            }
+            if (threadIdx.x == 0) nrem = cnt;
+        }
+        __syncthreads();
+        const int nr = nrem;
+        for (int q = 0; q < nr; ++q) {
+            const int s = rem[q];
             for (int i = threadIdx.x; i < m0; i += blockDim.x) colw[i] = P[i * PREC_MAX + s];
             __syncthreads();
             const double ipww = 1.0 / colw[s];
@@ -576,11 +624,9 @@ __global__ void __launch_bounds__(512) prec_update_kernel(GraphDev g, const doub
                     if (c != s) P[i * PREC_MAX + c] = fma(-ci, colw[c], P[i * PREC_MAX + c]);
             }
             __syncthreads();
-            if (threadIdx.x == 0) pos[w] = -1;
-            fl += 2ull * m0 * m0;
-            __syncthreads();
         }
-        if (threadIdx.x == 0 && fl) atomicAdd(&g.ctr->flops_prec, fl);
+        for (int q = threadIdx.x; q < nr; q += blockDim.x) pos[pm[rem[q]]] = -1;
+        if (threadIdx.x == 0 && nr) atomicAdd(&g.ctr->flops_prec, 2ull * m0 * m0 * nr);
         return;
     }
     if (!g.prec_need[u]) return;
@@ -680,17 +726,35 @@ __global__ void commit_kernel(GraphDev g, int l_fixed, int explicit_sets, int co
             const int jj = side ? lower_bound_int(g.nbr + (long long)v * p, g.deg[v], u) : j;
             const int dd = g.deg[su] - 1;
             const int *nb = g.nbr + (long long)su * p;
-            ull r = rank;
-            int x = 0;
-            for (int i = 0; i < l; ++i) {
-                while (x < dd - (l - i)) {
-                    ull c = g.binom[(long long)(dd - x - 1) * (p + 1) + (l - i - 1)];
-                    if (r < c) break;
-                    r -= c;
+            const int kd = dd - l;                        // dropped members
+            if (kd <= KC_MAX && kd < l) {
+                // expand through the complement: R = the kd dropped positions, at lex
+                // rank C(dd,l) - 1 - rank among the kd-subsets; S = the rest, ascending
+                int posR[KC_MAX + 1], idxR[KC_MAX];
+                const ull T = g.binom[(long long)dd * (p + 1) + l];
+                unrank_lex(T - 1 - rank, dd, kd, g.binom, p + 1, posR);
+                for (int i = 0; i < kd; ++i) idxR[i] = cand_index(g, su, jj, dd, posR[i]);
+                int o = 0;
+                for (int y = 0; y <= dd; ++y) {
+                    if (y == jj) continue;
+                    bool dropped = false;
+                    for (int i = 0; i < kd; ++i) dropped |= idxR[i] == y;
+                    if (!dropped) g.pool[off + o++] = nb[y];
+                }
+            } else {
+                ull r = rank;
+                int x = 0;
+                for (int i = 0; i < l; ++i) {
+                    while (x < dd - (l - i)) {
+                        ull c = g.binom[(long long)(dd - x - 1) * (p + 1) + (l - i - 1)];
+                        if (r < c) break;
+                        r -= c;
+                        ++x;
+                    }
+                    g.pool[off + i] = nb[cand_index(g, su, jj, dd, x)];
                     ++x;
                 }
-                g.pool[off + i] = nb[x + (x >= jj)];
-                ++x;
+                if (g.row_off) sort_small(g.pool + off, l);
             }
         } else {
             g.sep_off[e] = -1;
@@ -698,6 +762,46 @@ __global__ void commit_kernel(GraphDev g, int l_fixed, int explicit_sets, int co
     }
     if (removed) atomicAdd(&g.ctr->edges_removed, removed);
     if (canon) atomicAdd(&g.ctr->tests_canonical, canon);
+}
+
+// ---------------------------------------------------------------- re-verification
+// Every explicit separating set recorded in the sepset store is tested again in
+// FP64 from the FP64 correlation matrix (one warp per removed pair); a set that
+// does not come out independent sets the device status (PC_ERR_INTERNAL).
+__global__ void __launch_bounds__(256) reverify_kernel(GraphDev g, TestParams tp, const double *C64, int ldc,
+                                                       int mmax, int ms, int per_warp_bytes)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    unsigned char *mine = smem_raw + (size_t)wib * per_warp_bytes;
+    double *Mbuf = (double *)mine;
+    int *nd = (int *)(mine + (size_t)mmax * ms * sizeof(double));
+    const int p = g.p;
+    const long long npairs = (long long)p * p;
+    const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    WarpAcc acc = {0, 0, 0, 0, 0, 0, 0, 0.f};
+    ull fails = 0;
+    for (long long e = gw; e < npairs; e += nw) {
+        const int a = (int)(e / p), b = (int)(e % p);
+        if (a >= b) continue;
+        const int l = g.sep_level[e];
+        const long long off = g.sep_off[e];
+        if (l < 0 || off < 0 || l + 2 > mmax) continue;
+        if (lane == 0) {
+            for (int i = 0; i < l; ++i) nd[i] = g.pool[off + i];
+            nd[l] = a;
+            nd[l + 1] = b;
+        }
+        __syncwarp();
+        const double sq = sqrt((double)(tp.n - l - 3));
+        double r;
+        float z;
+        const bool ind = warp_test<true>(nd, l + 2, l, nullptr, C64, ldc, tp, sq, (float)sq, Mbuf, ms, acc, r, z);
+        if (!ind) ++fails;
+        __syncwarp();
+    }
+    if (lane == 0 && fails) g.ctr->status = 8;
 }
 
 // ---------------------------------------------------------------- raw batches
@@ -837,6 +941,19 @@ cudaError_t launch_commit(GraphDev g, long long n_opairs_cap, int l_fixed, int e
     long long cap = n_opairs_cap > 0 ? n_opairs_cap : 1;
     int blocks = (int)std::min<long long>((cap + 255) / 256, (long long)num_sms() * 8);
     commit_kernel<<<blocks, 256, 0, s>>>(g, l_fixed, explicit_sets, explicit_sets); note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reverify(GraphDev g, TestParams tp, const double *C64, int ldc, cudaStream_t s)
+{
+    // sets up to the largest stage of the search (p - 3 at most) fit one warp's matrix
+    int mmax = std::min(g.p, 130);
+    int ms, per_warp, wpc;
+    direct_shape(mmax, ms, per_warp, wpc);
+    size_t smem = (size_t)wpc * per_warp;
+    cudaError_t e = cudaFuncSetAttribute(reverify_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    reverify_kernel<<<num_sms() * 2, wpc * 32, smem, s>>>(g, tp, C64, ldc, mmax, ms, per_warp); note_launch();
     return cudaGetLastError();
 }
 

@@ -1,0 +1,501 @@
+// mlp.cu -- the conditioning-set proposal network (not in the paper): a
+// member score s(u, v, k) for every candidate k of an ordered pair (u, v) at
+// stage l, used to enumerate the likeliest separating sets first.
+//
+//   h1 = relu(W1 x + b1)  (16 -> 128),  h2 = relu(W2 h1 + b2)  (128 -> 128),
+//   s = w3 . h2 + b3;     training loss: mean BCE(sigmoid(s), y).
+//
+// Forward on the tensor cores (tcgen05, BF16 operands, FP32 accumulators in
+// TMEM): the CTA writes a 128-row tile of features into a SWIZZLE_128B K-major
+// shared tile, one thread issues D1 = X W1^T (K = 16), the epilogue applies
+// bias + ReLU and writes h1 (BF16) into the A operand of D2 = h1 W2^T
+// (K = 128), and the second epilogue reduces h2 against w3.  Backward and Adam
+// run on the CUDA cores in FP32 from the saved activations.
+#include "internal.h"
+#include "device_util.cuh"
+#include "tc_util.cuh"
+
+#include <cuda_bf16.h>
+
+namespace fpc {
+
+constexpr int NF = 16, NH = 128;
+constexpr int NPARAM = NH * NF + NH + NH * NH + NH + NH + 1;   // 18817
+constexpr int OFF_W1 = 0, OFF_B1 = NH * NF, OFF_W2 = OFF_B1 + NH, OFF_B2 = OFF_W2 + NH * NH;
+constexpr int OFF_W3 = OFF_B2 + NH, OFF_B3 = OFF_W3 + NH;
+constexpr int T_ROWS = 128;
+constexpr int W1_TILE = 128 * 128;            // bytes: 128 rows x 64 bf16 (features in the first 16)
+constexpr int W2_TILE = 128 * 128;            // bytes per 64-wide K tile
+constexpr int A1_BYTES = 128 * 128;
+constexpr int A2_BYTES = 2 * 128 * 128;
+constexpr int MLP_SMEM = W1_TILE + 2 * W2_TILE + A1_BYTES + A2_BYTES + 1024;
+
+// byte offset of element (row, col) of a 128-byte-row K-major tile with the
+// 128-byte swizzle: the 16-byte chunk index is XORed with row mod 8
+__device__ __forceinline__ int sw128_off(int row, int col_bf16)
+{
+    const int chunk = col_bf16 >> 3, within = col_bf16 & 7;
+    return row * 128 + (((chunk ^ (row & 7)) << 4) | (within << 1));
+}
+
+// Member features of candidate k for the ordered pair (u, v) at stage l, from
+// the FP32 correlation matrix: marginal correlations, first-order partial
+// correlations, the first-order test statistic relative to the threshold,
+// and the stage shape.
+__device__ __forceinline__ void member_features(const float *C, int ldc, int u, int v, int k, int l, int d,
+                                                float sqn_over_q, float *f)
+{
+    const float cuv = C[(long long)u * ldc + v], cuk = C[(long long)u * ldc + k], cvk = C[(long long)v * ldc + k];
+    const float e = 1e-6f;
+    const float ruv_k = (cuv - cuk * cvk) * rsqrtf(fmaxf((1.f - cuk * cuk) * (1.f - cvk * cvk), e));
+    const float ruk_v = (cuk - cuv * cvk) * rsqrtf(fmaxf((1.f - cuv * cuv) * (1.f - cvk * cvk), e));
+    const float rvk_u = (cvk - cuv * cuk) * rsqrtf(fmaxf((1.f - cuv * cuv) * (1.f - cuk * cuk), e));
+    f[0] = fabsf(cuv);
+    f[1] = fabsf(cuk);
+    f[2] = fabsf(cvk);
+    f[3] = fabsf(cuk * cvk);
+    f[4] = fabsf(ruv_k);
+    f[5] = fabsf(ruk_v);
+    f[6] = fabsf(rvk_u);
+    f[7] = fminf(sqn_over_q * fabsf(ruv_k), 4.f);
+    f[8] = fminf(sqn_over_q * fabsf(cuv), 4.f);
+    f[9] = fminf(fmaxf(sqn_over_q * (fabsf(cuv) - fabsf(ruv_k)), -4.f), 4.f);
+    f[10] = d > 0 ? (float)l / (float)d : 0.f;
+    f[11] = log2f((float)d + 1.f) * 0.125f;
+    f[12] = (float)l * (1.f / 16.f);
+    f[13] = (cuv * cuk * cvk > 0.f) ? 1.f : 0.f;
+    f[14] = 1.f;
+    f[15] = 0.f;
+}
+
+// Packs the FP32 master parameters into the swizzled BF16 B-operand tiles of
+// W1 (128 x 64, features zero-padded) and W2 (two 128 x 64 K tiles).
+__global__ void mlp_pack_kernel(const float *theta, uint8_t *wpack)
+{
+    const int o = blockIdx.x;            // output unit (row of the B operand)
+    for (int c = threadIdx.x; c < 64; c += blockDim.x) {
+        const float w = c < NF ? theta[OFF_W1 + o * NF + c] : 0.f;
+        *(__nv_bfloat16 *)(wpack + sw128_off(o, c)) = __float2bfloat16_rn(w);
+    }
+    for (int c = threadIdx.x; c < NH; c += blockDim.x) {
+        const int t = c >> 6;
+        *(__nv_bfloat16 *)(wpack + W1_TILE + t * W2_TILE + sw128_off(o, c & 63)) =
+            __float2bfloat16_rn(theta[OFF_W2 + o * NH + c]);
+    }
+}
+
+// Where the rows of a forward pass come from.
+struct MlpRows {
+    // explicit features (R x 16 FP32), or ...
+    const float *feats;
+    long long R;
+    // ... the candidates of the current stage: node u owns deg_u * (deg_u - 1)
+    // rows starting at row_off[u] (pair j, candidate position x)
+    const GraphDev *gp;
+    const unsigned long long *row_off;
+    const float *C32;
+    int ldc;
+    float sqn_over_q;
+};
+
+__device__ __forceinline__ void row_features(const MlpRows &R, const GraphDev &g, long long row, float *f)
+{
+    if (R.feats) {
+#pragma unroll
+        for (int i = 0; i < NF; ++i) f[i] = R.feats[row * NF + i];
+        return;
+    }
+    const int p = g.p, l = g.info->l;
+    const int u = (int)(upper_bound_dev(R.row_off, (long long)p + 1, (unsigned long long)row) - 1);
+    const int dg = g.deg[u], d = dg - 1;
+    const long long w = row - (long long)R.row_off[u];
+    const int j = (int)(w / d), x = (int)(w - (long long)j * d);
+    const int v = g.nbr[(long long)u * p + j];
+    const int k = g.nbr[(long long)u * p + x + (x >= j)];
+    member_features(R.C32, R.ldc, u, v, k, l, d, R.sqn_over_q, f);
+}
+
+// Forward pass over rows [0, R): scores s, and for training h1 (BF16), h2 (FP32).
+__global__ void __launch_bounds__(128, 1) mlp_forward_kernel(MlpRows rows, GraphDev g, const uint8_t *wpack,
+                                                             const float *theta, float *scores,
+                                                             __nv_bfloat16 *h1_out, float *h2_out, int *err)
+{
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *sW1 = smem, *sW2 = smem + W1_TILE, *sA1 = sW2 + 2 * W2_TILE, *sA2 = sA1 + A1_BYTES;
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tmem_base;
+    __shared__ float b1[NH], b2[NH], w3[NH];
+    __shared__ float b3;
+    __shared__ long long nrows;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (!rows.feats && (g.info->done || g.info->halt)) return;
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        nrows = rows.feats ? rows.R : (long long)rows.row_off[g.p];
+    }
+    // weights (pre-swizzled) and vectors into shared memory; A1 zero-filled once
+    for (int i = tid; i < (W1_TILE + 2 * W2_TILE) / 16; i += blockDim.x)
+        ((uint4 *)smem)[i] = ((const uint4 *)wpack)[i];
+    for (int i = tid; i < A1_BYTES / 16; i += blockDim.x) ((uint4 *)sA1)[i] = make_uint4(0, 0, 0, 0);
+    for (int i = tid; i < NH; i += blockDim.x) {
+        b1[i] = theta[OFF_B1 + i];
+        b2[i] = theta[OFF_B2 + i];
+        w3[i] = theta[OFF_W3 + i];
+    }
+    if (tid == 0) b3 = theta[OFF_B3];
+    if (warp == 0) tc_alloc(&tmem_base, 256);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base, d1 = tmem, d2 = tmem + 128;
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    constexpr uint32_t idesc = idesc_bf16_f32(128, 128);
+    const long long R = nrows;
+    unsigned phase = 0;
+    bool ok = true;
+    for (long long t0 = (long long)blockIdx.x * T_ROWS; t0 < R && ok; t0 += (long long)gridDim.x * T_ROWS) {
+        const long long row = t0 + tid;
+        float f[NF];
+        if (row < R) row_features(rows, g, row, f);
+        else
+#pragma unroll
+            for (int i = 0; i < NF; ++i) f[i] = 0.f;
+#pragma unroll
+        for (int i = 0; i < NF; ++i) *(__nv_bfloat16 *)(sA1 + sw128_off(tid, i)) = __float2bfloat16_rn(f[i]);
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            tc_mma(d1, sw128_desc(smem_u32(sA1)), sw128_desc(smem_u32(sW1)), idesc, 0u);
+            tc_commit(&bar);
+        }
+        __syncwarp();
+        ok = mbar_wait(&bar, phase);
+        phase ^= 1u;
+        tc_fence_after();
+        // epilogue 1: h1 = relu(D1 + b1) -> BF16 into the A operand of layer 2
+#pragma unroll 1
+        for (int c0 = 0; c0 < NH; c0 += 32) {
+            float v[32];
+            tc_ld_32cols(d1 + lane_base + (uint32_t)c0, v);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int c = c0 + j;
+                const __nv_bfloat16 hb = __float2bfloat16_rn(fmaxf(v[j] + b1[c], 0.f));
+                *(__nv_bfloat16 *)(sA2 + (c >> 6) * (128 * 128) + sw128_off(tid, c & 63)) = hb;
+                if (h1_out && row < R) h1_out[row * NH + c] = hb;
+            }
+        }
+        tc_fence_before();
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            for (int t = 0; t < 2; ++t)
+                for (int ks = 0; ks < 4; ++ks)
+                    tc_mma(d2, sw128_desc(smem_u32(sA2 + t * 128 * 128) + ks * 32),
+                           sw128_desc(smem_u32(sW2 + t * W2_TILE) + ks * 32), idesc, (t | ks) ? 1u : 0u);
+            tc_commit(&bar);
+        }
+        __syncwarp();
+        ok = ok && mbar_wait(&bar, phase);
+        phase ^= 1u;
+        tc_fence_after();
+        // epilogue 2: s = w3 . relu(D2 + b2) + b3
+        float s = b3;
+#pragma unroll 1
+        for (int c0 = 0; c0 < NH; c0 += 32) {
+            float v[32];
+            tc_ld_32cols(d2 + lane_base + (uint32_t)c0, v);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const float h = fmaxf(v[j] + b2[c0 + j], 0.f);
+                s = fmaf(w3[c0 + j], h, s);
+                if (h2_out && row < R) h2_out[row * NH + c0 + j] = h;
+            }
+        }
+        if (row < R) scores[row] = s;
+        tc_fence_before();
+        __syncthreads();
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tc_dealloc(tmem, 256);
+    if (!ok && tid == 0) atomicExch(err, 7);   // a bounded wait expired
+}
+
+// Backward pass for rows [0, R) of a batch: per-CTA FP32 partial gradients in
+// registers, added into grad (atomics once per CTA).  Uses the activations the
+// forward pass saved (h1 BF16 as consumed by layer 2, h2 FP32) and the BF16
+// weights the forward pass used.
+__global__ void __launch_bounds__(256) mlp_backward_kernel(const float *feats, const float *labels,
+                                                           const float *scores, const __nv_bfloat16 *h1,
+                                                           const float *h2, long long R, float inv_b,
+                                                           const float *theta, float *grad, double *loss)
+{
+    extern __shared__ float bsm[];
+    float(*sdh2)[NH + 1] = (float(*)[NH + 1])bsm;                       // dL/dh2 (masked) of the tile
+    float(*sh1)[NH + 1] = (float(*)[NH + 1])(bsm + T_ROWS * (NH + 1));   // h1, then dL/dh1
+    float(*sW2)[NH + 1] = (float(*)[NH + 1])(bsm + 2 * T_ROWS * (NH + 1)); // W2 rounded to BF16
+    float(*sx)[NF] = (float(*)[NF])(bsm + 2 * T_ROWS * (NH + 1) + NH * (NH + 1));
+    float *sds = bsm + 2 * T_ROWS * (NH + 1) + NH * (NH + 1) + T_ROWS * NF;
+    const int tid = threadIdx.x;
+    for (int e = tid; e < NH * NH; e += blockDim.x)
+        sW2[e / NH][e % NH] = __bfloat162float(__float2bfloat16_rn(theta[OFF_W2 + e]));
+    // per-thread partials: dW2 entries (o, i) with o = tid/2, i in the half tid&1
+    float gW2[64];
+#pragma unroll
+    for (int i = 0; i < 64; ++i) gW2[i] = 0.f;
+    float gW1[8], gb1 = 0.f, gb2 = 0.f, gw3 = 0.f, gb3 = 0.f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) gW1[i] = 0.f;
+    double lsum = 0.0;
+    const int o = tid >> 1, ih = (tid & 1) * 64;
+    __syncthreads();
+    for (long long t0 = (long long)blockIdx.x * T_ROWS; t0 < R; t0 += (long long)gridDim.x * T_ROWS) {
+        const int nr = (int)(R - t0 < T_ROWS ? R - t0 : T_ROWS);
+        for (int r = tid; r < T_ROWS; r += blockDim.x) {
+            float ds = 0.f;
+            if (r < nr) {
+                const float s = scores[t0 + r], y = labels[t0 + r];
+                ds = (1.f / (1.f + __expf(-s)) - y) * inv_b;
+                lsum += (double)(fmaxf(s, 0.f) + log1pf(__expf(-fabsf(s))) - y * s);
+            }
+            sds[r] = ds;
+        }
+        for (int e = tid; e < T_ROWS * NH; e += blockDim.x) {
+            const int r = e / NH, c = e % NH;
+            float hv1 = 0.f, d2 = 0.f;
+            if (r < nr) {
+                hv1 = __bfloat162float(h1[(t0 + r) * NH + c]);
+                const float hv2 = h2[(t0 + r) * NH + c];
+                d2 = hv2 > 0.f ? 1.f : 0.f;
+            }
+            sh1[r][c] = hv1;
+            sdh2[r][c] = d2;                     // mask for now; scaled below
+        }
+        for (int e = tid; e < T_ROWS * NF; e += blockDim.x) {
+            const int r = e / NF, c = e % NF;
+            sx[r][c] = r < nr ? __bfloat162float(__float2bfloat16_rn(feats[(t0 + r) * NF + c])) : 0.f;
+        }
+        __syncthreads();
+        // dW3 / db3 (threads 0..127 own one unit each) and the masked dh2
+        for (int e = tid; e < T_ROWS * NH; e += blockDim.x) {
+            const int r = e / NH, c = e % NH;
+            sdh2[r][c] *= sds[r] * theta[OFF_W3 + c];
+        }
+        if (tid < NH) {
+            float a = 0.f;
+            for (int r = 0; r < nr; ++r) a = fmaf(sds[r], h2[(t0 + r) * NH + tid], a);
+            gw3 += a;
+        }
+        if (tid == 0)
+            for (int r = 0; r < nr; ++r) gb3 += sds[r];
+        __syncthreads();
+        // dW2[o][i] += sum_r dh2[r][o] h1[r][i]; db2[o]
+#pragma unroll 4
+        for (int r = 0; r < nr; ++r) {
+            const float a = sdh2[r][o];
+#pragma unroll
+            for (int i = 0; i < 64; ++i) gW2[i] = fmaf(a, sh1[r][ih + i], gW2[i]);
+        }
+        if ((tid & 1) == 0)
+            for (int r = 0; r < nr; ++r) gb2 += sdh2[r][o];
+        __syncthreads();
+        // dh1[r][i] = sum_o dh2[r][o] W2[o][i], masked by h1 > 0 (stored into sh1)
+        for (int e = tid; e < T_ROWS * NH; e += blockDim.x) {
+            const int r = e / NH, i = e % NH;
+            float a = 0.f;
+            if (r < nr && sh1[r][i] > 0.f)
+                for (int q = 0; q < NH; ++q) a = fmaf(sdh2[r][q], sW2[q][i], a);
+            sh1[r][i] = a;                   // sh1 now holds dh1 (masked); each (r, i) is read and
+                                             // written by the same thread only
+        }
+        __syncthreads();
+        // dW1[i][f] += sum_r dh1[r][i] x[r][f]; db1[i]   (thread -> unit i = tid/2, 8 features)
+        {
+            const int iu = tid >> 1, f0 = (tid & 1) * 8;
+            for (int r = 0; r < nr; ++r) {
+                const float a = sh1[r][iu];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) gW1[q] = fmaf(a, sx[r][f0 + q], gW1[q]);
+                if ((tid & 1) == 0) gb1 += a;
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 64; ++i) atomicAdd(&grad[OFF_W2 + o * NH + ih + i], gW2[i]);
+    if ((tid & 1) == 0) atomicAdd(&grad[OFF_B2 + o], gb2);
+    {
+        const int iu = tid >> 1, f0 = (tid & 1) * 8;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) atomicAdd(&grad[OFF_W1 + iu * NF + f0 + q], gW1[q]);
+        if ((tid & 1) == 0) atomicAdd(&grad[OFF_B1 + iu], gb1);
+    }
+    if (tid < NH) atomicAdd(&grad[OFF_W3 + tid], gw3);
+    if (tid == 0) atomicAdd(&grad[OFF_B3], gb3);
+    if (loss) {
+        // block-level sum of the loss terms
+        __shared__ double red[256];
+        red[tid] = lsum;
+        __syncthreads();
+        for (int s = 128; s > 0; s >>= 1) {
+            if (tid < s) red[tid] += red[tid + s];
+            __syncthreads();
+        }
+        if (tid == 0) atomicAdd(loss, red[0]);
+    }
+}
+
+// Adam (Kingma & Ba): m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+// theta -= lr * mhat / (sqrt(vhat) + eps).
+__global__ void adam_kernel(float *theta, const float *grad, float *m, float *v, int n, float lr, float bc1,
+                            float bc2)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float g = grad[i];
+    const float mi = 0.9f * m[i] + 0.1f * g, vi = 0.999f * v[i] + 0.001f * g * g;
+    m[i] = mi;
+    v[i] = vi;
+    theta[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + 1e-8f);
+}
+
+// Per ordered pair (u, j) of a node with scored candidates: the permutation of
+// its d candidate positions in descending score (ties: ascending position),
+// by counting ranks (O(d^2 / 32) per lane).  One warp per pair.
+__global__ void perm_kernel(GraphDev g, const unsigned long long *row_off, const float *scores, short *perm)
+{
+    if (g.info->done || g.info->halt) return;
+    const int p = g.p;
+    const long long npairs = g.info->n_opairs;
+    const int lane = threadIdx.x & 31;
+    for (long long o = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; o < npairs;
+         o += ((long long)gridDim.x * blockDim.x) >> 5) {
+        const int u = (int)(upper_bound_dev(g.ooff, (long long)p + 1, o) - 1);
+        if (row_off[u + 1] == row_off[u]) continue;
+        const int j = (int)(o - g.ooff[u]);
+        const int d = g.deg[u] - 1;
+        const long long base = (long long)row_off[u] + (long long)j * d;
+        for (int x = lane; x < d; x += 32) {
+            const float sx = scores[base + x];
+            int rank = 0;
+            for (int y = 0; y < d; ++y) {
+                const float sy = scores[base + y];
+                rank += (sy > sx) || (sy == sx && y < x);
+            }
+            perm[base + rank] = (short)x;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- host side
+int mlp_nparam() { return NPARAM; }
+size_t mlp_pack_bytes() { return (size_t)W1_TILE + 2 * W2_TILE; }
+
+cudaError_t launch_mlp_pack(const float *theta, uint8_t *wpack, cudaStream_t s)
+{
+    mlp_pack_kernel<<<NH, 64, 0, s>>>(theta, wpack);
+    note_launch();
+    return cudaGetLastError();
+}
+
+static int mlp_ctas(long long rows)
+{
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long long tiles = (rows + T_ROWS - 1) / T_ROWS;
+    long long c = tiles < (long long)sms ? tiles : (long long)sms;
+    return (int)(c < 1 ? 1 : c);
+}
+
+cudaError_t launch_mlp_forward_feats(const float *feats, long long R, const uint8_t *wpack, const float *theta,
+                                     float *scores, __nv_bfloat16 *h1, float *h2, int *err, GraphDev g,
+                                     cudaStream_t s)
+{
+    MlpRows rows{};
+    rows.feats = feats;
+    rows.R = R;
+    cudaError_t e = cudaFuncSetAttribute(mlp_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, MLP_SMEM);
+    if (e != cudaSuccess) return e;
+    mlp_forward_kernel<<<mlp_ctas(R), 128, MLP_SMEM, s>>>(rows, g, wpack, theta, scores, h1, h2, err);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_score_stage(GraphDev g, const unsigned long long *row_off, long long rows_cap,
+                                   const float *C32, int ldc, float sqn_over_q, const uint8_t *wpack,
+                                   const float *theta, float *scores, short *perm, int *err, cudaStream_t s)
+{
+    MlpRows rows{};
+    rows.feats = nullptr;
+    rows.row_off = row_off;
+    rows.C32 = C32;
+    rows.ldc = ldc;
+    rows.sqn_over_q = sqn_over_q;
+    cudaError_t e = cudaFuncSetAttribute(mlp_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, MLP_SMEM);
+    if (e != cudaSuccess) return e;
+    mlp_forward_kernel<<<mlp_ctas(rows_cap), 128, MLP_SMEM, s>>>(rows, g, wpack, theta, scores, nullptr, nullptr, err);
+    note_launch();
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    perm_kernel<<<sms * 4, 256, 0, s>>>(g, row_off, scores, perm);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_backward(const float *feats, const float *labels, const float *scores,
+                                const __nv_bfloat16 *h1, const float *h2, long long R, float inv_b,
+                                const float *theta, float *grad, double *loss, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(grad, 0, NPARAM * sizeof(float), s);
+    if (e != cudaSuccess) return e;
+    const size_t smem = (size_t)(2 * T_ROWS * (NH + 1) + NH * (NH + 1) + T_ROWS * NF + T_ROWS) * sizeof(float);
+    e = cudaFuncSetAttribute(mlp_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    mlp_backward_kernel<<<mlp_ctas(R), 256, smem, s>>>(feats, labels, scores, h1, h2, R, inv_b, theta, grad, loss);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adam(float *theta, const float *grad, float *m, float *v, float lr, int step, cudaStream_t s)
+{
+    const float bc1 = 1.f - powf(0.9f, (float)step), bc2 = 1.f - powf(0.999f, (float)step);
+    adam_kernel<<<(NPARAM + 255) / 256, 256, 0, s>>>(theta, grad, m, v, NPARAM, lr, bc1, bc2);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// Member features for explicit quadruples (u, v, k, l | d << 16): candidate k
+// of the ordered pair (u, v) at stage l with candidate-set size d.
+__global__ void mlp_features_kernel(const int *quads, long long R, const float *C32, int ldc, int p, long long n,
+                                    float inv_q, float *feats, int *err)
+{
+    const long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    const int u = quads[4 * r], v = quads[4 * r + 1], k = quads[4 * r + 2];
+    const int l = quads[4 * r + 3] & 0xffff, d = (int)((unsigned)quads[4 * r + 3] >> 16);
+    if (u < 0 || u >= p || v < 0 || v >= p || k < 0 || k >= p || u == v || k == u || k == v) {
+        *err = 1;
+        return;
+    }
+    float f[NF];
+    member_features(C32, ldc, u, v, k, l, d, sqrtf((float)n) * inv_q, f);
+    for (int i = 0; i < NF; ++i) feats[r * NF + i] = f[i];
+}
+
+cudaError_t launch_mlp_features(const int *quads, long long R, const float *C32, int ldc, int p, long long n,
+                                double q, float *feats, int *err, cudaStream_t s)
+{
+    mlp_features_kernel<<<(unsigned)((R + 255) / 256), 256, 0, s>>>(quads, R, C32, ldc, p, n, (float)(1.0 / q),
+                                                                      feats, err);
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace fpc

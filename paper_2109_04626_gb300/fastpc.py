@@ -85,6 +85,13 @@ def load():
         "pc_kernel_launches": (i64, []),
         "pc_timing": (i32, [vp, vp, vp, i32]),
         "pc_corr_noalloc": (i32, [vp, i32, i64, i32, i64, vp, i64, vp]),
+        "pc_mlp_nparam": (i32, []),
+        "pc_mlp_set_params": (i32, [vp, vp, i64]),
+        "pc_mlp_get_params": (i32, [vp, vp, i64]),
+        "pc_mlp_features": (i32, [vp, vp, i64, vp]),
+        "pc_mlp_forward": (i32, [vp, vp, i64, vp]),
+        "pc_mlp_grad": (i32, [vp, vp, vp, i64, vp, ctypes.POINTER(dbl)]),
+        "pc_mlp_train": (i32, [vp, vp, vp, i64, i32, i64, dbl, ctypes.POINTER(dbl)]),
         "pc_last_error": (cs, [vp]),
         "pc_status_string": (cs, [i32]),
     }
@@ -229,13 +236,13 @@ def pc_kernel_launches() -> int:
     return int(load().pc_kernel_launches())
 
 
-TIMING_CLASSES = ["corr", "stage_a", "prec", "ci_direct", "ci_complement", "bookkeeping"]
+TIMING_CLASSES = ["corr", "stage_a", "prec", "ci_direct", "ci_complement", "bookkeeping", "scoring"]
 
 
 def pc_timing(h, reset: bool = False) -> dict:
     """Per-kernel-class device ms and launch-group counts (option "timing" = 1)."""
-    ms = np.zeros(6, dtype=np.float64)
-    cnt = np.zeros(6, dtype=np.int64)
+    ms = np.zeros(7, dtype=np.float64)
+    cnt = np.zeros(7, dtype=np.int64)
     _check(h, load().pc_timing(h, ctypes.c_void_p(ms.ctypes.data), ctypes.c_void_p(cnt.ctypes.data),
                                1 if reset else 0))
     return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(TIMING_CLASSES)}
@@ -256,6 +263,54 @@ def pc_corr_noalloc(X, C_out, stream=None):
                                 ctypes.c_void_p(raw))
     if st != 0:
         raise PCError(st, "pc_corr_noalloc: p must be <= 4096, n >= 2, device pointers, valid dtype/strides")
+
+
+def pc_mlp_nparam() -> int:
+    return int(load().pc_mlp_nparam())
+
+
+def pc_mlp_set_params(h, theta):
+    theta = np.ascontiguousarray(theta, dtype=np.float32)
+    _check(h, load().pc_mlp_set_params(h, ctypes.c_void_p(theta.ctypes.data), theta.size))
+
+
+def pc_mlp_get_params(h) -> np.ndarray:
+    out = np.empty(pc_mlp_nparam(), dtype=np.float32)
+    _check(h, load().pc_mlp_get_params(h, ctypes.c_void_p(out.ctypes.data), out.size))
+    return out
+
+
+def pc_mlp_features(h, quads):
+    """quads: (R, 4) int32 CUDA tensor (u, v, k, l | d << 16) -> (R, 16) float32 CUDA tensor."""
+    import torch
+    R = quads.shape[0]
+    feats = torch.empty((R, 16), dtype=torch.float32, device=quads.device)
+    _check(h, load().pc_mlp_features(h, ctypes.c_void_p(_ptr(quads)), R, ctypes.c_void_p(_ptr(feats))))
+    return feats
+
+
+def pc_mlp_forward(h, feats):
+    import torch
+    R = feats.shape[0]
+    scores = torch.empty(R, dtype=torch.float32, device=feats.device)
+    _check(h, load().pc_mlp_forward(h, ctypes.c_void_p(_ptr(feats)), R, ctypes.c_void_p(_ptr(scores))))
+    return scores
+
+
+def pc_mlp_grad(h, feats, labels):
+    """(gradient as a numpy float32 vector, mean loss)."""
+    g = np.empty(pc_mlp_nparam(), dtype=np.float32)
+    loss = ctypes.c_double()
+    _check(h, load().pc_mlp_grad(h, ctypes.c_void_p(_ptr(feats)), ctypes.c_void_p(_ptr(labels)),
+                                 feats.shape[0], ctypes.c_void_p(g.ctypes.data), ctypes.byref(loss)))
+    return g, loss.value
+
+
+def pc_mlp_train(h, feats, labels, epochs: int, batch: int, lr: float) -> float:
+    loss = ctypes.c_double()
+    _check(h, load().pc_mlp_train(h, ctypes.c_void_p(_ptr(feats)), ctypes.c_void_p(_ptr(labels)),
+                                  feats.shape[0], int(epochs), int(batch), float(lr), ctypes.byref(loss)))
+    return loss.value
 
 
 class PC:

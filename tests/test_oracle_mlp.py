@@ -1,0 +1,38 @@
+"""Pins for the FP64 reference of the proposal network: the hand-written
+backward pass agrees with central finite differences of the loss."""
+import numpy as np
+
+from oracle import mlp
+
+
+def test_gradient_matches_finite_differences():
+    rng = np.random.default_rng(5)
+    theta = mlp.init(3) * 0.5
+    X = rng.standard_normal((40, mlp.NF))
+    y = (rng.random(40) < 0.3).astype(float)
+    g = mlp.grad(theta, X, y)
+    idx = rng.choice(mlp.NPARAM, size=60, replace=False)
+    idx = np.concatenate([idx, [mlp.NPARAM - 1, 0, 2048]])       # b3, a W1 entry, b1[0]
+    h = 1e-6
+    for i in idx:
+        tp, tm = theta.copy(), theta.copy()
+        tp[i] += h
+        tm[i] -= h
+        fd = (mlp.loss(tp, X, y) - mlp.loss(tm, X, y)) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 + 1e-5 * abs(fd), (i, fd, g[i])
+
+
+def test_loss_is_bce_of_sigmoid():
+    theta = mlp.init(1)
+    X = np.random.default_rng(2).standard_normal((7, mlp.NF))
+    y = np.array([0, 1, 1, 0, 1, 0, 0], dtype=float)
+    s, _ = mlp.forward(theta, X)
+    sig = 1 / (1 + np.exp(-s))
+    ref = -np.mean(y * np.log(sig) + (1 - y) * np.log(1 - sig))
+    assert abs(mlp.loss(theta, X, y) - ref) < 1e-12
+
+
+def test_pack_unpack_roundtrip():
+    theta = mlp.init(9)
+    assert theta.size == mlp.NPARAM == 18817
+    np.testing.assert_array_equal(mlp.pack(mlp.unpack(theta)), theta)
