@@ -97,6 +97,18 @@ void pc_destroy(pc_handle *h);
  *                 pc_mlp_set_params or pc_mlp_train); 0 = lexicographic (default)
  *   "learned_rows" capacity of the per-stage score buffer in rows (default 2^24);
  *                 a stage with more candidate rows runs in lexicographic order
+ *   "learned_min_tests" a stage is scored only if it schedules at least this
+ *                 many tests (default 1e6); smaller stages run all their tests
+ *                 in one wave, where the enumeration order saves nothing
+ * Launch shape of the test kernels (set by pc_autotune; results never depend on it):
+ *   "lane_chunk"  consecutive sets of one pair per thread in the kernel of the
+ *                 stages l <= 8 (1..256, default 8)
+ *   "lane_rounds" chunks of every pair run rank-major (chunk r of all pairs
+ *                 before chunk r+1) before the rest runs pair by pair (0..4096,
+ *                 default 32)
+ *   "lane_blocks" CTAs of 256 threads per SM of that kernel (1..32, default 8)
+ *   "direct_warps" at most this many warps per CTA of the warp-per-test kernel
+ *                 (1, 2, 4 or 8; default 8)
  * Unknown keys return PC_ERR_ARG. */
 pc_status pc_set_opt(pc_handle *h, const char *key, double val);
 pc_status pc_get_opt(pc_handle *h, const char *key, double *val);
@@ -126,6 +138,64 @@ pc_status pc_corr_get(pc_handle *h, float *C32, double *C64);
  * (host; may be NULL).  Sepsets stay in the handle (pc_sepsets_*).
  * Requires a prior pc_corr.  Synchronises. */
 pc_status pc_skeleton(pc_handle *h, uint8_t *adj_out, pc_stats *stats);
+
+/* pc_skeleton_many -- the skeleton searches of `count` independent problems
+ * (each handle after its own pc_corr) run concurrently: every search is first
+ * enqueued on its handle's stream (give each handle its own stream with
+ * pc_set_stream; handles on one stream run one after the other), then each is
+ * completed.  adj_out[i] (host or device, may be NULL; adj_out may be NULL),
+ * stats[i] and status[i] (host, may be NULL) receive the per-problem results.
+ * Returns the first failing status (each failure stays in its handle). */
+pc_status pc_skeleton_many(pc_handle **hs, int32_t count, uint8_t **adj_out, pc_stats *stats,
+                           pc_status *status);
+
+/* pc_autotune -- chooses the launch shape of the test kernels for this
+ * handle's problem (the data given to the last pc_corr): a coordinate search
+ * over lane_chunk {4,8,16,32}, lane_rounds {4,16,64,256}, lane_blocks {4,8,16}
+ * and direct_warps {2,4,8}, each candidate timed as the mean of `reps` (1..100)
+ * complete skeleton searches (CUDA events on the handle's stream) after one
+ * warm run.  The handle keeps the fastest shape; out (host, may be NULL)
+ * receives it with the times.  The shape changes no result, so the handle
+ * holds a valid skeleton afterwards (as after pc_skeleton).  Requires a prior
+ * pc_corr.  Not in the paper: a launch-shape search for this GPU.  Errors of
+ * any run are returned as pc_skeleton returns them. */
+typedef struct {
+    int32_t lane_chunk, lane_rounds, lane_blocks, direct_warps;
+    double ms_default;  /* mean skeleton time with the shape before the search */
+    double ms_best;     /* mean skeleton time with the chosen shape             */
+    int32_t runs;       /* skeleton searches executed                           */
+} pc_tune_result;
+pc_status pc_autotune(pc_handle *h, int32_t reps, pc_tune_result *out);
+
+/* pc_create_batch -- one handle over k independent problems (instance i: n[i]
+ * samples of p[i] variables; 4 <= n[i] <= 2^21, 2 <= p[i] <= 4096, sum p[i] <=
+ * 16384), all at the same alpha and max_level.  Instance i owns the global
+ * node ids [off_i, off_i + p[i]), off_i = p[0] + ... + p[i-1]; its adjacency
+ * starts as the complete graph on its own nodes, so every test stays inside
+ * one instance and uses that instance's n in sqrt(n-l-3) (Eq. 1).  Each stage
+ * of pc_skeleton is then one launch sequence over the tests of all instances;
+ * the skeleton restricted to instance i equals that of a pc_create handle on
+ * instance i alone.  Conventional order only (Algorithm 1; "order" 1 is
+ * rejected).  Not in the paper: the paper runs one problem at a time.  Give the
+ * data with pc_corr_block (pc_corr returns PC_ERR_STATE); pc_skeleton,
+ * pc_sepsets_*, pc_ci_batch, pc_autotune and the pc_mlp_* calls then work in
+ * global node ids (adj_out is sum p x sum p, block diagonal; the statistics
+ * are totals).  pc_ci_batch rejects a test whose nodes span instances
+ * (PC_ERR_ARG) and checks n-l-3 > 0 against the smallest n. */
+pc_status pc_create_batch(int32_t k, const int64_t *n, const int32_t *p, double alpha, int32_t max_level,
+                          pc_handle **out);
+
+/* pc_corr_block -- pc_corr for instance i (0 <= i < k) of a batched handle: X
+ * is n[i] x p[i] row-major with row stride ld >= p[i], PC_F32 or PC_F64, host
+ * or device, caller-owned, read only.  Fills the diagonal block of corr of
+ * instance i.  pc_skeleton needs every instance given at least once.
+ * PC_ERR_STATE on a handle from pc_create, PC_ERR_ARG on a bad index. */
+pc_status pc_corr_block(pc_handle *h, int32_t i, const void *X, int32_t dtype, int64_t ld);
+
+/* pc_batch_layout -- the number of instances (1 for a pc_create handle) into
+ * *k and, if offsets is not NULL, their first node ids plus the total
+ * (k + 1 entries, host). */
+pc_status pc_batch_layout(pc_handle *h, int32_t *k, int32_t *offsets);
 
 /* pc_sepsets_count -- number of removed pairs of the last pc_skeleton and the
  * total length of their explicit sepsets (stage l = p-2 sets V\{u,v} are not

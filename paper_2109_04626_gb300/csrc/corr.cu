@@ -3,6 +3,7 @@
 // and FP32 Gram kernels on the CUDA cores, and the FP64 -> FP32 cast.
 #include "internal.h"
 #include <cuda_bf16.h>
+#include <algorithm>
 
 namespace fpc {
 
@@ -324,11 +325,72 @@ size_t syrk_f64_ws_bytes(long long n, int p)
     return (size_t)ntiles * splits * 64 * 64 * sizeof(double);
 }
 
+// Lazy FP64 correlations: unit diagonal, no entry valid yet.
+__global__ void c64_lazy_init_kernel(double *C64, int ldc, unsigned char *valid, int p)
+{
+    const long long tot = (long long)p * p;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int a = (int)(i / p), b = (int)(i % p);
+        valid[i] = a == b;
+        if (a == b) C64[(long long)a * ldc + a] = 1.0;
+    }
+}
+
+cudaError_t launch_c64_lazy_init(double *C64, int ldc, unsigned char *valid, int p, cudaStream_t s)
+{
+    long long tot = (long long)p * p;
+    c64_lazy_init_kernel<<<(unsigned)std::min<long long>((tot + 255) / 256, 8192), 256, 0, s>>>(C64, ldc, valid, p);
+    note_launch();
+    return cudaGetLastError();
+}
+
 __global__ void cast_kernel(const double *C64, float *C32, int p, int ldc)
 {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     long long tot = (long long)p * ldc;
     if (i < tot) C32[i] = (float)C64[i];
+}
+
+// Batched problems: the same two steps on the diagonal block [o, o+pb) of a
+// matrix whose validity flags have row stride P.
+__global__ void c64_lazy_init_block_kernel(double *C64, int ldc, unsigned char *valid, int P, int o, int pb)
+{
+    const long long tot = (long long)pb * pb;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int a = o + (int)(i / pb), b = o + (int)(i % pb);
+        valid[(long long)a * P + b] = a == b;
+        if (a == b) C64[(long long)a * ldc + a] = 1.0;
+    }
+}
+
+__global__ void cast_block_kernel(const double *C64, float *C32, int ldc, int o, int pb)
+{
+    const long long tot = (long long)pb * pb;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long e = (long long)(o + (int)(i / pb)) * ldc + o + (int)(i % pb);
+        C32[e] = (float)C64[e];
+    }
+}
+
+cudaError_t launch_c64_lazy_init_block(double *C64, int ldc, unsigned char *valid, int P, int o, int pb,
+                                       cudaStream_t s)
+{
+    long long tot = (long long)pb * pb;
+    c64_lazy_init_block_kernel<<<(unsigned)std::min<long long>((tot + 255) / 256, 8192), 256, 0, s>>>(
+        C64, ldc, valid, P, o, pb);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cast_block(const double *C64, float *C32, int ldc, int o, int pb, cudaStream_t s)
+{
+    long long tot = (long long)pb * pb;
+    cast_block_kernel<<<(unsigned)std::min<long long>((tot + 255) / 256, 8192), 256, 0, s>>>(C64, C32, ldc, o, pb);
+    note_launch();
+    return cudaGetLastError();
 }
 
 cudaError_t launch_col_stats(const void *X, int dtype, long long n, int p, long long ld,

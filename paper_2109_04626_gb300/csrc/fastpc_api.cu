@@ -39,6 +39,15 @@ struct pc_handle {
     int order = 1, stage_a = 1, precision = 2, complement = 1;
     double band = 1e-3, guard = 1e-3;
     double budget = 2.0e10;
+    // batched problems (pc_create_batch): instance i owns nodes [boff[i], boff[i+1])
+    // and the diagonal block of corr there; nblk = 0 for one problem
+    int nblk = 0;
+    std::vector<int> boff;
+    std::vector<long long> bn;
+    std::vector<char> bdone;
+    long long n_min = 0;
+    // launch shape of the test kernels (pc_autotune)
+    int lane_chunk = 8, lane_rounds = 32, lane_blocks = 8, direct_warps = 8;
     cudaStream_t stream = 0;
     std::string err;
     // correlation
@@ -71,12 +80,17 @@ struct pc_handle {
     // captured stage loop (CUDA graph with a conditional WHILE node)
     int use_graph = 1;
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t br_stream = nullptr;      // captures the bodies of conditional nodes
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     cudaGraphConditionalHandle hcond = 0;
     std::vector<double> graph_key;
-    long long body_kernels = 0;      // kernel nodes in the captured stage body
+    long long body_kernels = 0;      // kernel nodes in the captured stage body (all branches)
     double *syrk_ws = nullptr, *stats_ws = nullptr;
+    unsigned char *c64_valid = nullptr;
+    unsigned long long *rq = nullptr, *rq_len = nullptr;   // FP64 re-decision queue of the lane kernel
+    unsigned long long rq_cap = 0;
+    bool c64_full = false;             // C64 fully computed (else lazily, per entry)
     size_t stats_ws_bytes = 0;
     size_t syrk_ws_bytes = 0;
     // proposal network
@@ -90,7 +104,9 @@ struct pc_handle {
     unsigned long long *row_off = nullptr;
     short *perm = nullptr;
     float *stage_scores = nullptr;
+    unsigned char *scored = nullptr;   // per stage: 1 if it ran in the proposed order
     long long rows_cap = 0;
+    double learned_min = 1.0e6;
     // per-kernel-class timing
     int timing = 0;
     std::vector<TimedPair> pending;
@@ -203,25 +219,35 @@ static TestParams make_tp(const pc_handle *h)
 {
     TestParams tp;
     tp.n = h->n;
+    tp.nvec = h->g.nvec;
     tp.q = h->q;
     tp.qf = (float)h->q;
     tp.band = h->band;
     tp.guard = h->guard;
     tp.eps_c = h->used_tc ? 1.0e-6f : 1.2e-7f;
+    tp.dr_max = 1e-4f;
+    tp.lane_chunk = h->lane_chunk;
+    tp.lane_rounds = h->lane_rounds;
+    tp.lane_blocks = h->lane_blocks;
+    tp.direct_warps = h->direct_warps;
     tp.precision = h->precision;
     tp.reversed = h->order == 1;
     tp.complement = h->complement;
+    tp.lazy = h->c64_full ? 0 : 1;
+    tp.learned_min = h->learned_min;
+    tp.p = h->p;
+    tp.xs64 = h->Xs64;
+    tp.ldk = h->ldk;
+    tp.c64_valid = h->c64_valid;
     return tp;
 }
 
 // ---------------------------------------------------------------- create / destroy
-extern "C" pc_status pc_create(int64_t n, int32_t p, double alpha, int32_t max_level,
-                               pc_handle **out)
+// pmax: largest problem size (binomial table), batch: block-diagonal batch
+// layout (no precision blocks, conventional order only)
+static pc_status create_impl(int64_t n, int32_t p, double alpha, int32_t max_level, int32_t pmax,
+                             long long pool_cap, bool batch, pc_handle **out)
 {
-    if (!out) return PC_ERR_ARG;
-    *out = nullptr;
-    if (n < 4 || n > (1ll << 21) || p < 2 || p > fpc::MAXP || !(alpha > 0.0 && alpha < 1.0))
-        return PC_ERR_ARG;
     pc_handle *h = new pc_handle();
     h->n = n;
     h->p = p;
@@ -244,15 +270,17 @@ extern "C" pc_status pc_create(int64_t n, int32_t p, double alpha, int32_t max_l
     h->opair_cap = (long long)p * (p - 1);
     A(dalloc(h, &g.tn_off, (size_t)(p + 2) * sizeof(ull)));
     A(dalloc(h, &g.cn_off, (size_t)(p + 2) * sizeof(ull)));
+    A(dalloc(h, &g.rn_off, (size_t)(p + 2) * sizeof(ull)));
     A(dalloc(h, &g.best, pp * sizeof(ull)));
-    A(dalloc(h, &h->binom, (size_t)(p + 1) * (p + 1) * sizeof(ull)));
+    A(dalloc(h, &h->binom, (size_t)(pmax + 1) * (pmax + 1) * sizeof(ull)));
     A(dalloc(h, &g.sep_level, pp * sizeof(int)));
     A(dalloc(h, &g.sep_side, pp * sizeof(int)));
     A(dalloc(h, &g.sep_rank, pp * sizeof(long long)));
     A(dalloc(h, &g.sep_off, pp * sizeof(long long)));
-    g.pool_cap = std::max<long long>(1 << 20, 16ll * p * p);
+    g.pool_cap = pool_cap;
     A(dalloc(h, &g.pool, (size_t)g.pool_cap * sizeof(int)));
-    A(dalloc(h, &g.prec, (size_t)p * fpc::PREC_MAX * fpc::PREC_MAX * sizeof(double)));
+    // neighbourhood precision blocks serve the reversed order only
+    A(dalloc(h, &g.prec, batch ? sizeof(double) : (size_t)p * fpc::PREC_MAX * fpc::PREC_MAX * sizeof(double)));
     A(dalloc(h, &g.prec_m, (size_t)p * sizeof(int)));
     A(dalloc(h, &g.prec_mem, (size_t)p * fpc::PREC_MAX * sizeof(int)));
     A(dalloc(h, &g.prec_pos, pp * sizeof(short)));
@@ -266,6 +294,9 @@ extern "C" pc_status pc_create(int64_t n, int32_t p, double alpha, int32_t max_l
     A(dalloc(h, &h->singular, sizeof(int)));
     A(dalloc(h, &h->tc_err, sizeof(int)));
     A(dalloc(h, &h->mlp_err, sizeof(int)));
+    h->rq_cap = 1ull << 24;
+    A(dalloc(h, &h->rq, (size_t)h->rq_cap * sizeof(ull)));
+    A(dalloc(h, &h->rq_len, sizeof(ull)));
     A(dalloc(h, &h->mlp_loss, sizeof(double)));
     A(dalloc(h, &h->theta, (size_t)fpc::mlp_nparam() * sizeof(float)));
     A(dalloc(h, &h->adam_m, (size_t)fpc::mlp_nparam() * sizeof(float)));
@@ -276,6 +307,7 @@ extern "C" pc_status pc_create(int64_t n, int32_t p, double alpha, int32_t max_l
     if (e == cudaSuccess) e = cudaMallocHost((void **)&h->info_h, sizeof(LevelInfo));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&h->ctr_h, sizeof(DevCounters));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->br_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreate(&h->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&h->ev1);
     if (e != cudaSuccess) {
@@ -284,15 +316,17 @@ extern "C" pc_status pc_create(int64_t n, int32_t p, double alpha, int32_t max_l
         return st;
     }
     g.binom = h->binom;
+    g.ldb = pmax + 1;
     // saturating Pascal triangle
-    std::vector<ull> B((size_t)(p + 1) * (p + 1), 0ull);
-    for (int a = 0; a <= p; ++a) {
-        B[(size_t)a * (p + 1)] = 1;
+    const int lb = pmax + 1;
+    std::vector<ull> B((size_t)lb * lb, 0ull);
+    for (int a = 0; a <= pmax; ++a) {
+        B[(size_t)a * lb] = 1;
         for (int b = 1; b <= a; ++b) {
-            ull x = B[(size_t)(a - 1) * (p + 1) + b - 1];
-            ull y = b <= a - 1 ? B[(size_t)(a - 1) * (p + 1) + b] : 0ull;
+            ull x = B[(size_t)(a - 1) * lb + b - 1];
+            ull y = b <= a - 1 ? B[(size_t)(a - 1) * lb + b] : 0ull;
             ull s = x + y;
-            B[(size_t)a * (p + 1) + b] = (s < x || x == fpc::KEY_NONE || y == fpc::KEY_NONE) ? fpc::KEY_NONE : s;
+            B[(size_t)a * lb + b] = (s < x || x == fpc::KEY_NONE || y == fpc::KEY_NONE) ? fpc::KEY_NONE : s;
         }
     }
     e = cudaMemcpy(h->binom, B.data(), B.size() * sizeof(ull), cudaMemcpyHostToDevice);
@@ -301,6 +335,96 @@ extern "C" pc_status pc_create(int64_t n, int32_t p, double alpha, int32_t max_l
         return PC_ERR_CUDA;
     }
     *out = h;
+    return PC_OK;
+}
+
+extern "C" pc_status pc_create(int64_t n, int32_t p, double alpha, int32_t max_level,
+                               pc_handle **out)
+{
+    if (!out) return PC_ERR_ARG;
+    *out = nullptr;
+    if (n < 4 || n > (1ll << 21) || p < 2 || p > fpc::MAXP || !(alpha > 0.0 && alpha < 1.0))
+        return PC_ERR_ARG;
+    return create_impl(n, p, alpha, max_level, p, std::max<long long>(1 << 20, 16ll * p * p), false, out);
+}
+
+// One handle over k independent problems laid out block-diagonally: instance i
+// owns the nodes [off_i, off_i + p_i) (off_i = p_0 + ... + p_{i-1}).  Its
+// adjacency starts as the complete graph on its own nodes only, so no test ever
+// mixes instances, and each node's Fisher-z statistic uses its instance's n.
+extern "C" pc_status pc_create_batch(int32_t k, const int64_t *n, const int32_t *p, double alpha,
+                                     int32_t max_level, pc_handle **out)
+{
+    if (!out) return PC_ERR_ARG;
+    *out = nullptr;
+    if (k < 1 || k > fpc::MAXP_BATCH / 2 || !n || !p || !(alpha > 0.0 && alpha < 1.0)) return PC_ERR_ARG;
+    long long ptot = 0, nmax = 0, nmin = 1ll << 40, pool = 0;
+    int pmax = 0;
+    for (int i = 0; i < k; ++i) {
+        if (n[i] < 4 || n[i] > (1ll << 21) || p[i] < 2 || p[i] > fpc::MAXP) return PC_ERR_ARG;
+        ptot += p[i];
+        nmax = std::max<long long>(nmax, n[i]);
+        nmin = std::min<long long>(nmin, n[i]);
+        pmax = std::max(pmax, (int)p[i]);
+        pool += 16ll * p[i] * p[i];
+    }
+    if (ptot > fpc::MAXP_BATCH) return PC_ERR_ARG;
+    pc_handle *h = nullptr;
+    if (pc_status r = create_impl(nmax, (int32_t)ptot, alpha, max_level, pmax, std::max<long long>(1 << 20, pool),
+                                  true, &h))
+        return r;
+    h->nblk = k;
+    h->order = 0;
+    h->n_min = nmin;
+    h->boff.assign(k + 1, 0);
+    h->bn.assign(n, n + k);
+    h->bdone.assign(k, 0);
+    for (int i = 0; i < k; ++i) h->boff[i + 1] = h->boff[i] + p[i];
+    std::vector<int> lo((size_t)ptot), hi((size_t)ptot);
+    std::vector<long long> nv((size_t)ptot);
+    for (int i = 0; i < k; ++i)
+        for (int u = h->boff[i]; u < h->boff[i + 1]; ++u) {
+            lo[u] = h->boff[i];
+            hi[u] = h->boff[i + 1];
+            nv[u] = n[i];
+        }
+    int *dlo = nullptr, *dhi = nullptr;
+    long long *dn = nullptr;
+    cudaError_t e = dalloc(h, &dlo, lo.size() * sizeof(int));
+    if (e == cudaSuccess) e = dalloc(h, &dhi, hi.size() * sizeof(int));
+    if (e == cudaSuccess) e = dalloc(h, &dn, nv.size() * sizeof(long long));
+    if (e == cudaSuccess) e = cudaMemcpy(dlo, lo.data(), lo.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dhi, hi.data(), hi.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dn, nv.data(), nv.size() * sizeof(long long), cudaMemcpyHostToDevice);
+    // blocks off the diagonal are never read; keep them zero all the same
+    if (e == cudaSuccess) e = cudaMemset(h->C32, 0, (size_t)h->p * h->ldc * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(h->C64, 0, (size_t)h->p * h->ldc * sizeof(double));
+    if (e != cudaSuccess) {
+        pc_status st = e == cudaErrorMemoryAllocation ? PC_ERR_OOM : PC_ERR_CUDA;
+        pc_destroy(h);
+        return st;
+    }
+    h->g.blk_lo = dlo;
+    h->g.blk_hi = dhi;
+    h->g.nvec = dn;
+    *out = h;
+    return PC_OK;
+}
+
+extern "C" pc_status pc_batch_layout(pc_handle *h, int32_t *k, int32_t *offsets)
+{
+    if (!h || !k) return PC_ERR_ARG;
+    if (!h->nblk) {
+        *k = 1;
+        if (offsets) {
+            offsets[0] = 0;
+            offsets[1] = h->p;
+        }
+        return PC_OK;
+    }
+    *k = h->nblk;
+    if (offsets)
+        for (int i = 0; i <= h->nblk; ++i) offsets[i] = h->boff[i];
     return PC_OK;
 }
 
@@ -322,6 +446,7 @@ extern "C" void pc_destroy(pc_handle *h)
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     if (h->graph) cudaGraphDestroy(h->graph);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->br_stream) cudaStreamDestroy(h->br_stream);
     delete h;
 }
 
@@ -332,12 +457,14 @@ extern "C" pc_status pc_set_opt(pc_handle *h, const char *key, double val)
     std::string k(key);
     if (k == "order") {
         if (val != 0 && val != 1) return fail(h, PC_ERR_ARG, "order must be 0 or 1");
+        if (val == 1 && h->nblk) return fail(h, PC_ERR_ARG, "batched problems run the conventional order");
         h->order = (int)val;
     } else if (k == "stage_a") h->stage_a = val != 0;
     else if (k == "precision") {
         if (val != 0 && val != 1 && val != 2) return fail(h, PC_ERR_ARG, "precision must be 0, 1 or 2");
         h->precision = (int)val;
         h->have_corr = false;
+        std::fill(h->bdone.begin(), h->bdone.end(), 0);   // batched: every instance again
     } else if (k == "band") {
         if (!(val >= 0)) return fail(h, PC_ERR_ARG, "band must be >= 0");
         h->band = val;
@@ -350,6 +477,9 @@ extern "C" pc_status pc_set_opt(pc_handle *h, const char *key, double val)
     else if (k == "learned") {
         if (val != 0 && !h->have_params) return fail(h, PC_ERR_STATE, "learned order needs parameters (pc_mlp_set_params or pc_mlp_train)");
         h->learned = val != 0;
+    } else if (k == "learned_min_tests") {
+        if (!(val >= 0)) return fail(h, PC_ERR_ARG, "learned_min_tests must be >= 0");
+        h->learned_min = val;
     } else if (k == "learned_rows") {
         if (!(val >= 0)) return fail(h, PC_ERR_ARG, "learned_rows must be >= 0");
         h->rows_cap = (long long)val;
@@ -357,6 +487,18 @@ extern "C" pc_status pc_set_opt(pc_handle *h, const char *key, double val)
     else if (k == "budget") {
         if (!(val > 0)) return fail(h, PC_ERR_ARG, "budget must be > 0");
         h->budget = val;
+    } else if (k == "lane_chunk") {
+        if (!(val >= 1 && val <= 256)) return fail(h, PC_ERR_ARG, "lane_chunk must be in [1, 256]");
+        h->lane_chunk = (int)val;
+    } else if (k == "lane_rounds") {
+        if (!(val >= 0 && val <= 4096)) return fail(h, PC_ERR_ARG, "lane_rounds must be in [0, 4096]");
+        h->lane_rounds = (int)val;
+    } else if (k == "lane_blocks") {
+        if (!(val >= 1 && val <= 32)) return fail(h, PC_ERR_ARG, "lane_blocks must be in [1, 32]");
+        h->lane_blocks = (int)val;
+    } else if (k == "direct_warps") {
+        if (val != 1 && val != 2 && val != 4 && val != 8) return fail(h, PC_ERR_ARG, "direct_warps must be 1, 2, 4 or 8");
+        h->direct_warps = (int)val;
     } else return fail(h, PC_ERR_ARG, "unknown option: " + k);
     return PC_OK;
 }
@@ -375,7 +517,12 @@ extern "C" pc_status pc_get_opt(pc_handle *h, const char *key, double *val)
     else if (k == "graph") *val = h->use_graph;
     else if (k == "learned") *val = h->learned;
     else if (k == "learned_rows") *val = (double)h->rows_cap;
+    else if (k == "learned_min_tests") *val = h->learned_min;
     else if (k == "budget") *val = h->budget;
+    else if (k == "lane_chunk") *val = h->lane_chunk;
+    else if (k == "lane_rounds") *val = h->lane_rounds;
+    else if (k == "lane_blocks") *val = h->lane_blocks;
+    else if (k == "direct_warps") *val = h->direct_warps;
     else if (k == "tensor_core_gemm") *val = h->used_tc ? 1.0 : 0.0;
     else return fail(h, PC_ERR_ARG, "unknown option: " + k);
     return PC_OK;
@@ -433,6 +580,35 @@ extern "C" const char *pc_status_string(pc_status s)
 }
 
 // ---------------------------------------------------------------- correlation
+// the full FP64 correlation matrix (split-K Gram of the FP64 planes)
+static pc_status syrk64_block(pc_handle *h, int o, long long n, int p)
+{
+    const size_t wsb = fpc::syrk_f64_ws_bytes(n, p);
+    if (wsb > h->syrk_ws_bytes) {
+        dfree(h, h->syrk_ws);
+        h->syrk_ws = nullptr;
+        CK(dalloc(h, &h->syrk_ws, wsb));
+        h->syrk_ws_bytes = wsb;
+    }
+    CK(fpc::launch_syrk_f64(h->Xs64 + (size_t)o * h->ldk, n, h->ldk, p, h->C64 + (size_t)o * h->ldc + o, h->ldc,
+                            h->syrk_ws, h->syrk_ws_bytes, h->stream));
+    return PC_OK;
+}
+
+static pc_status materialize_c64(pc_handle *h)
+{
+    if (h->c64_full) return PC_OK;
+    if (h->nblk) {
+        // batched problems: each diagonal block from its own samples
+        for (int i = 0; i < h->nblk; ++i)
+            if (pc_status r = syrk64_block(h, h->boff[i], h->bn[i], h->boff[i + 1] - h->boff[i])) return r;
+    } else {
+        if (pc_status r = syrk64_block(h, 0, h->n, h->p)) return r;
+    }
+    h->c64_full = true;
+    return PC_OK;
+}
+
 // a bounded wait inside the tensor-core GEMM expired (device-side error word)
 static pc_status check_tc(pc_handle *h)
 {
@@ -444,14 +620,17 @@ static pc_status check_tc(pc_handle *h)
     return PC_OK;
 }
 
-extern "C" pc_status pc_corr(pc_handle *h, const void *X, int32_t dtype, int64_t ld)
+// Standardisation and correlation GEMM of one problem, or of instance blk of a
+// batched handle (its columns are rows [o, o+p) of the planes, its block of
+// corr the diagonal block there).
+static pc_status corr_impl(pc_handle *h, const void *X, int32_t dtype, int64_t ld, int blk)
 {
-    if (!h) return PC_ERR_ARG;
-    if (!X || (dtype != PC_F32 && dtype != PC_F64) || ld < h->p)
-        return fail(h, PC_ERR_ARG, "pc_corr: bad X, dtype or ld");
     cudaStream_t s = h->stream;
-    const int p = h->p;
-    const long long n = h->n;
+    const int o = blk < 0 ? 0 : h->boff[blk];
+    const int p = blk < 0 ? h->p : h->boff[blk + 1] - o;
+    const long long n = blk < 0 ? h->n : h->bn[blk];
+    if (!X || (dtype != PC_F32 && dtype != PC_F64) || ld < p)
+        return fail(h, PC_ERR_ARG, "pc_corr: bad X, dtype or ld");
     const size_t esz = dtype == PC_F64 ? 8 : 4;
     const void *Xd = X;
     if (!is_device_ptr(X)) {
@@ -466,7 +645,7 @@ extern "C" pc_status pc_corr(pc_handle *h, const void *X, int32_t dtype, int64_t
         CK(cudaMemcpyAsync(h->Xstage, X, bytes, cudaMemcpyHostToDevice, s));
         Xd = h->Xstage;
     }
-    const size_t plane = (size_t)p * h->ldk;
+    const size_t plane = (size_t)h->p * h->ldk;
     if (!h->Xs64) {
         CK(dalloc(h, &h->Xs64, plane * sizeof(double)));
         CK(dalloc(h, &h->Xs32, plane * sizeof(float)));
@@ -485,30 +664,45 @@ extern "C" pc_status pc_corr(pc_handle *h, const void *X, int32_t dtype, int64_t
         CK(dalloc(h, &h->stats_ws, sws));
         h->stats_ws_bytes = sws;
     }
-    CK(fpc::launch_col_stats_split(Xd, dtype, n, p, ld, h->mean, h->rsd, h->stats_ws, s));
+    const size_t po = (size_t)o * h->ldk;                  // first plane row of this problem
+    CK(fpc::launch_col_stats_split(Xd, dtype, n, p, ld, h->mean + o, h->rsd + o, h->stats_ws, s));
     const bool want_bf16 = h->precision == 2 && fpc::tc_gemm_available();
-    CK(fpc::launch_standardize(Xd, dtype, n, p, ld, h->mean, h->rsd, h->Xs64,
-                               h->precision == 1 ? h->Xs32 : nullptr,
-                               want_bf16 ? h->Xhi : nullptr, want_bf16 ? h->Xlo : nullptr, h->ldk,
+    CK(fpc::launch_standardize(Xd, dtype, n, p, ld, h->mean + o, h->rsd + o, h->Xs64 + po,
+                               h->precision == 1 ? h->Xs32 + po : nullptr,
+                               want_bf16 ? h->Xhi + po : nullptr, want_bf16 ? h->Xlo + po : nullptr, h->ldk,
                                s));
-    const size_t wsb = fpc::syrk_f64_ws_bytes(n, p);
-    if (wsb > h->syrk_ws_bytes) {
-        dfree(h, h->syrk_ws);
-        h->syrk_ws = nullptr;
-        CK(dalloc(h, &h->syrk_ws, wsb));
-        h->syrk_ws_bytes = wsb;
+    // FP64 correlations: all of them when a stage needs whole blocks (reversed
+    // order: closed-form stage, precision blocks) or the tests run in FP64;
+    // otherwise per entry on demand when a test is re-decided in FP64
+    h->c64_full = false;
+    if (blk >= 0) {
+        if (h->precision == 0) {
+            if (pc_status r = syrk64_block(h, o, n, p)) return r;
+        } else {
+            if (!h->c64_valid) {
+                CK(dalloc(h, &h->c64_valid, (size_t)h->p * h->p));
+                CK(cudaMemsetAsync(h->c64_valid, 0, (size_t)h->p * h->p, s));
+            }
+            CK(fpc::launch_c64_lazy_init_block(h->C64, h->ldc, h->c64_valid, h->p, o, p, s));
+        }
+    } else if (h->precision == 0 || h->order == 1) {
+        if (pc_status r = materialize_c64(h)) return r;
+    } else {
+        if (!h->c64_valid) CK(dalloc(h, &h->c64_valid, (size_t)p * p));
+        CK(fpc::launch_c64_lazy_init(h->C64, h->ldc, h->c64_valid, p, s));
     }
-    CK(fpc::launch_syrk_f64(h->Xs64, n, h->ldk, p, h->C64, h->ldc, h->syrk_ws, h->syrk_ws_bytes, s));
-    h->used_tc = false;
+    float *C32b = h->C32 + (size_t)o * h->ldc + o;
+    bool tc = false;
     if (h->precision == 0) {
-        CK(fpc::launch_cast_c(h->C64, h->C32, p, h->ldc, s));
+        if (blk >= 0) CK(fpc::launch_cast_block(h->C64, h->C32, h->ldc, o, p, s));
+        else CK(fpc::launch_cast_c(h->C64, h->C32, p, h->ldc, s));
     } else if (h->precision == 1 || !want_bf16) {
         if (h->precision == 2) {
             // tensor-core path not available in this build: FP32 operands on the CUDA cores
-            CK(fpc::launch_standardize(Xd, dtype, n, p, ld, h->mean, h->rsd, nullptr, h->Xs32,
+            CK(fpc::launch_standardize(Xd, dtype, n, p, ld, h->mean + o, h->rsd + o, nullptr, h->Xs32 + po,
                                        nullptr, nullptr, h->ldk, s));
         }
-        CK(fpc::launch_syrk_f32(h->Xs32, n, h->ldk, p, h->C32, h->ldc, s));
+        CK(fpc::launch_syrk_f32(h->Xs32 + po, n, h->ldk, p, C32b, h->ldc, s));
     } else {
         const size_t need = fpc::corr_bf16x3_ws_bytes(n, p);
         if (need > h->tc_ws_bytes) {
@@ -517,14 +711,42 @@ extern "C" pc_status pc_corr(pc_handle *h, const void *X, int32_t dtype, int64_t
             CK(dalloc(h, &h->tc_ws, need));
             h->tc_ws_bytes = need;
         }
-        CK(cudaMemsetAsync(h->tc_err, 0, sizeof(int), s));
-        CK(fpc::launch_corr_bf16x3(h->Xhi, h->Xlo, n, h->ldk, p, h->C32, h->ldc, h->tc_ws,
+        if (blk <= 0) CK(cudaMemsetAsync(h->tc_err, 0, sizeof(int), s));
+        CK(fpc::launch_corr_bf16x3(h->Xhi + po, h->Xlo + po, n, h->ldk, p, C32b, h->ldc, h->tc_ws,
                                    h->tc_ws_bytes, h->tc_err, s));
-        h->used_tc = true;
+        tc = true;
     }
-    h->have_corr = true;
+    if (blk < 0) {
+        h->used_tc = tc;
+        if (!h->Pbuf) CK(dalloc(h, &h->Pbuf, (size_t)p * h->ldc * sizeof(double)));
+        h->have_corr = true;
+    } else {
+        // every instance runs the same GEMM path (one precision per handle)
+        h->used_tc = tc;
+        h->bdone[blk] = 1;
+        bool all = true;
+        for (char d : h->bdone) all = all && d;
+        h->have_corr = all;
+        // FP64 tests read whole blocks: every block was formed in full above
+        h->c64_full = all && h->precision == 0;
+    }
     h->have_skel = false;
     return PC_OK;
+}
+
+extern "C" pc_status pc_corr(pc_handle *h, const void *X, int32_t dtype, int64_t ld)
+{
+    if (!h) return PC_ERR_ARG;
+    if (h->nblk) return fail(h, PC_ERR_STATE, "batched handle: give each instance with pc_corr_block");
+    return corr_impl(h, X, dtype, ld, -1);
+}
+
+extern "C" pc_status pc_corr_block(pc_handle *h, int32_t i, const void *X, int32_t dtype, int64_t ld)
+{
+    if (!h) return PC_ERR_ARG;
+    if (!h->nblk) return fail(h, PC_ERR_STATE, "pc_corr_block needs a batched handle (pc_create_batch)");
+    if (i < 0 || i >= h->nblk) return fail(h, PC_ERR_ARG, "pc_corr_block: instance index out of range");
+    return corr_impl(h, X, dtype, ld, i);
 }
 
 extern "C" pc_status pc_corr_get(pc_handle *h, float *C32, double *C64)
@@ -533,6 +755,10 @@ extern "C" pc_status pc_corr_get(pc_handle *h, float *C32, double *C64)
     if (!h->have_corr) return fail(h, PC_ERR_STATE, "pc_corr_get before pc_corr");
     cudaStream_t s = h->stream;
     const int p = h->p;
+    if (C64 && !h->c64_full) {
+        Timed tm(h, 0);
+        if (pc_status r = materialize_c64(h)) return r;
+    }
     if (C32)
         CK(cudaMemcpy2DAsync(C32, p * sizeof(float), h->C32, h->ldc * sizeof(float),
                              p * sizeof(float), p, cudaMemcpyDefault, s));
@@ -562,39 +788,132 @@ static int level_cap(const pc_handle *h)
 // One stage of the loop (every kernel reads l from the device): counts, scan
 // and gate, the CI tests, the PC-stable commit, the next frozen graph, the
 // next l and the loop condition, then the precision blocks of the next stage.
+// Adds a conditional node (IF or SWITCH on handle hc) after the current capture
+// dependencies of s and captures fn(i, stream) into its i-th body on the
+// handle's branch stream.
+template <class F>
+static pc_status cond_node(pc_handle *h, cudaStream_t s, cudaGraphConditionalHandle hc,
+                           cudaGraphConditionalNodeType type, unsigned size, F fn)
+{
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    CK(cudaStreamGetCaptureInfo(s, &cst, nullptr, &cg, &deps, nullptr, &nd));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = hc;
+    cp.conditional.type = type;
+    cp.conditional.size = size;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, cg, deps, nullptr, nd, &cp));
+    CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    for (unsigned i = 0; i < size; ++i) {
+        CK(cudaStreamBeginCaptureToGraph(h->br_stream, cp.conditional.phGraph_out[i], nullptr, nullptr, 0,
+                                         cudaStreamCaptureModeRelaxed));
+        pc_status st = fn((int)i, h->br_stream);
+        cudaGraph_t out = nullptr;
+        cudaError_t e = cudaStreamEndCapture(h->br_stream, &out);
+        if (st != PC_OK) return st;
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture (conditional body)");
+    }
+    return PC_OK;
+}
+
+// One stage of the loop (Algorithm 1 / 2 body).  use_cond: being captured into
+// the WHILE body; the kernels without work in a stage then sit behind
+// conditional nodes that the head and tail kernels set.  Otherwise (host loop)
+// every kernel is launched and returns at once when it has nothing to do.
 static pc_status enqueue_level(pc_handle *h, cudaStream_t s, int mmax, bool use_cond, bool timed)
 {
     GraphDev &g = h->g;
     TestParams tp = make_tp(h);
     const bool use_prec = h->order == 1 && h->complement;
     auto T = [&](int cls) { return Timed(h, timed ? cls : -1); };
+    fpc::StageConds sc = {};
+    if (use_cond) {
+        cudaStreamCaptureStatus cst;
+        cudaGraph_t cg = nullptr;
+        CK(cudaStreamGetCaptureInfo(s, &cst, nullptr, &cg, nullptr, nullptr, nullptr));
+        sc.use = 1;
+        sc.has_comp = use_prec;
+        sc.has_score = h->learned;
+        sc.has_prec = use_prec;
+        CK(cudaGraphConditionalHandleCreate(&sc.lane, cg, fpc::LANE_RANGES, 0));
+        CK(cudaGraphConditionalHandleCreate(&sc.direct, cg, 0, 0));
+        if (sc.has_comp) CK(cudaGraphConditionalHandleCreate(&sc.comp, cg, 0, 0));
+        if (sc.has_score) CK(cudaGraphConditionalHandleCreate(&sc.score, cg, 0, 0));
+        if (sc.has_prec) CK(cudaGraphConditionalHandleCreate(&sc.prec, cg, 0, 0));
+    }
     {
         auto t = T(5);
-        CK(fpc::launch_head(g, tp, h->budget, mmax, s));
+        CK(fpc::launch_head(g, tp, h->budget, mmax, sc, s));
     }
-    if (h->learned) {
-        auto t = T(6);
-        const float sqn_over_q = (float)(std::sqrt((double)h->n) / h->q);
-        CK(fpc::launch_mlp_score_stage(g, h->row_off, h->rows_cap, h->C32, h->ldc, sqn_over_q, h->wpack,
-                                       h->theta, h->stage_scores, h->perm, h->mlp_err, s));
-    }
-    {
-        auto t = T(3);
-        CK(fpc::launch_ci_direct(g, tp, mmax, h->C32, h->C64, h->ldc, s));
-    }
-    if (use_prec) {
-        auto t = T(4);
-        CK(fpc::launch_ci_complement(g, tp, s));
+    const float sqn_over_q = (float)(std::sqrt((double)h->n) / h->q);
+    auto score = [&](int, cudaStream_t st) -> pc_status {
+        CK(fpc::launch_mlp_score_stage(g, h->row_off, h->rows_cap, h->C32, h->ldc, sqn_over_q,
+                                       (float)(1.0 / h->q), h->wpack, h->theta, h->stage_scores, h->perm,
+                                       h->mlp_err, st));
+        return PC_OK;
+    };
+    // small stages: one lane-kernel range, the FP64 pass over its queue, and the
+    // warp-per-test kernel that re-runs the stage if that queue overflowed
+    auto lane = [&](int range, cudaStream_t st) -> pc_status {
+        CK(fpc::launch_ci_lane(g, tp, h->C32, h->C64, h->ldc, h->rq, h->rq_cap, h->rq_len, range, h->learned, st));
+        CK(fpc::launch_ci_direct(g, tp, fpc::LANE_LMAX + 2, h->C32, h->C64, h->ldc, st));
+        return PC_OK;
+    };
+    auto direct = [&](int, cudaStream_t st) -> pc_status {
+        CK(fpc::launch_ci_direct(g, tp, mmax, h->C32, h->C64, h->ldc, st));
+        return PC_OK;
+    };
+    auto comp = [&](int, cudaStream_t st) -> pc_status {
+        CK(fpc::launch_ci_complement(g, tp, st));
+        return PC_OK;
+    };
+    auto prec = [&](int, cudaStream_t st) -> pc_status {
+        CK(fpc::launch_prec_update(g, h->C64, h->ldc, st));
+        return PC_OK;
+    };
+    if (use_cond) {
+        if (sc.has_score)
+            if (pc_status r = cond_node(h, s, sc.score, cudaGraphCondTypeIf, 1, score)) return r;
+        if (pc_status r = cond_node(h, s, sc.lane, cudaGraphCondTypeSwitch, fpc::LANE_RANGES, lane)) return r;
+        if (pc_status r = cond_node(h, s, sc.direct, cudaGraphCondTypeIf, 1, direct)) return r;
+        if (sc.has_comp)
+            if (pc_status r = cond_node(h, s, sc.comp, cudaGraphCondTypeIf, 1, comp)) return r;
+    } else {
+        if (h->learned) {
+            auto t = T(6);
+            if (pc_status r = score(0, s)) return r;
+        }
+        {
+            auto t = T(3);
+            const int l = h->info_h->l;
+            if (h->precision != 0 && l >= 0 && l <= fpc::LANE_LMAX) {
+                if (pc_status r = lane(fpc::lane_range_of(l), s)) return r;
+            } else {
+                if (pc_status r = direct(0, s)) return r;
+            }
+        }
+        if (use_prec) {
+            auto t = T(4);
+            if (pc_status r = comp(0, s)) return r;
+        }
     }
     {
         auto t = T(5);
         CK(fpc::launch_commit(g, h->opair_cap, -1, 1, s));
         CK(fpc::launch_level_degrees(g, s));
-        CK(fpc::launch_tail(g, tp, level_cap(h), 0, h->singular, 0, h->hcond, use_cond ? 1 : 0, s));
+        CK(fpc::launch_tail(g, tp, level_cap(h), 0, h->singular, 0, h->hcond, use_cond ? 1 : 0, sc, s));
     }
     if (use_prec) {
-        auto t = T(2);
-        CK(fpc::launch_prec_update(g, h->C64, h->ldc, s));
+        if (use_cond) {
+            if (pc_status r = cond_node(h, s, sc.prec, cudaGraphCondTypeIf, 1, prec)) return r;
+        } else {
+            auto t = T(2);
+            if (pc_status r = prec(0, s)) return r;
+        }
     }
     return PC_OK;
 }
@@ -602,9 +921,10 @@ static pc_status enqueue_level(pc_handle *h, cudaStream_t s, int mmax, bool use_
 static std::vector<double> graph_key(const pc_handle *h)
 {
     return {(double)h->order, (double)h->complement, (double)h->precision, h->band, h->guard,
-            (double)h->used_tc, (double)h->learned, (double)(uintptr_t)h->perm, (double)h->rows_cap,
+            (double)h->used_tc, (double)h->c64_full, (double)h->learned, (double)(uintptr_t)h->perm, (double)h->rows_cap, h->learned_min, (double)(uintptr_t)h->rq,
             h->budget, (double)level_cap(h), (double)(uintptr_t)h->g.pool, (double)h->g.pool_cap,
-            (double)(uintptr_t)h->C32, (double)(uintptr_t)h->C64};
+            (double)(uintptr_t)h->C32, (double)(uintptr_t)h->C64, (double)h->lane_chunk,
+            (double)h->lane_rounds, (double)h->lane_blocks, (double)h->direct_warps};
 }
 
 static void drop_graph(pc_handle *h)
@@ -665,16 +985,18 @@ static pc_status clear_halt(pc_handle *h)
     return PC_OK;
 }
 
-static pc_status skeleton_once(pc_handle *h, pc_stats *st, bool *overflow)
+static pc_status skeleton_enqueue(pc_handle *h)
 {
+    if (h->order == 1 && !h->c64_full) {
+        Timed tm(h, 0);
+        if (pc_status r = materialize_c64(h)) return r;
+    }
     GraphDev &g = h->g;
     cudaStream_t s = h->stream;
     const int p = h->p;
     const long long n = h->n;
     const size_t pp = (size_t)p * p;
     TestParams tp = make_tp(h);
-    std::memset(st, 0, sizeof(*st));
-    *overflow = false;
     const bool timed = h->timing != 0;
     const bool graph = h->use_graph && !timed;
     if (h->learned) {
@@ -683,26 +1005,26 @@ static pc_status skeleton_once(pc_handle *h, pc_stats *st, bool *overflow)
             CK(dalloc(h, &h->row_off, (size_t)(p + 2) * sizeof(ull)));
             CK(dalloc(h, &h->perm, (size_t)h->rows_cap * sizeof(short)));
             CK(dalloc(h, &h->stage_scores, (size_t)h->rows_cap * sizeof(float)));
+            CK(dalloc(h, &h->scored, (size_t)p));
         }
         g.row_off = h->row_off;
         g.perm = h->perm;
         g.rows_cap = h->rows_cap;
+        g.scored = h->scored;
         CK(cudaMemsetAsync(h->mlp_err, 0, sizeof(int), s));
+        CK(cudaMemsetAsync(h->scored, 0, (size_t)p, s));
     } else {
         g.row_off = nullptr;
         g.perm = nullptr;
         g.rows_cap = 0;
+        g.scored = nullptr;
     }
     if (graph) {
         if (pc_status r = ensure_graph(h)) return r;
     }
 
     // complete graph, empty sepset store
-    std::vector<uint32_t> full((size_t)p * g.W, 0u);
-    for (int u = 0; u < p; ++u)
-        for (int v = 0; v < p; ++v)
-            if (u != v) full[(size_t)u * g.W + (v >> 5)] |= 1u << (v & 31);
-    CK(cudaMemcpyAsync(g.adj, full.data(), full.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+    CK(fpc::launch_init_adj(g, s));
     CK(cudaMemsetAsync(g.best, 0xff, pp * sizeof(ull), s));
     CK(cudaMemsetAsync(g.sep_level, 0xff, pp * sizeof(int), s));
     CK(cudaMemsetAsync(g.sep_off, 0xff, pp * sizeof(long long), s));
@@ -713,18 +1035,16 @@ static pc_status skeleton_once(pc_handle *h, pc_stats *st, bool *overflow)
     CK(cudaMemsetAsync(g.info, 0, sizeof(LevelInfo), s));
     CK(cudaMemsetAsync(&g.info->lstar, 0xff, sizeof(int), s));
     CK(cudaMemsetAsync(h->singular, 0, sizeof(int), s));
-    CK(cudaStreamSynchronize(s));   // 'full' is pageable host memory
     CK(cudaEventRecord(h->ev0, s));
 
     int stage_a_launched = 0;
     {
         Timed t(h, 5);
         CK(fpc::launch_level_degrees(g, s));
-        CK(fpc::launch_tail(g, tp, level_cap(h), 2, h->singular, 0, h->hcond, 0, s));
+        CK(fpc::launch_tail(g, tp, level_cap(h), 2, h->singular, 0, h->hcond, 0, fpc::StageConds{}, s));
     }
     if (h->order == 1 && h->stage_a && n - p - 1 > 0) {
         stage_a_launched = 1;
-        if (!h->Pbuf) CK(dalloc(h, &h->Pbuf, (size_t)p * h->ldc * sizeof(double)));
         {
             Timed t(h, 1);
             CK(cudaMemcpyAsync(h->Pbuf, h->C64, (size_t)p * h->ldc * sizeof(double),
@@ -740,17 +1060,32 @@ static pc_status skeleton_once(pc_handle *h, pc_stats *st, bool *overflow)
     }
     {
         Timed t(h, 5);
-        CK(fpc::launch_tail(g, tp, level_cap(h), 1, h->singular, stage_a_launched, h->hcond, 0, s));
+        CK(fpc::launch_tail(g, tp, level_cap(h), 1, h->singular, stage_a_launched, h->hcond, 0, fpc::StageConds{},
+                            s));
     }
     if (h->order == 1 && h->complement) {
         Timed t(h, 2);
         CK(fpc::launch_prec_update(g, h->C64, h->ldc, s));
     }
 
+    if (graph) CK(cudaGraphLaunch(h->gexec, s));
+    return PC_OK;
+}
+
+static pc_status skeleton_complete(pc_handle *h, pc_stats *st, bool *overflow)
+{
+    GraphDev &g = h->g;
+    cudaStream_t s = h->stream;
+    const int p = h->p;
+    TestParams tp = make_tp(h);
+    std::memset(st, 0, sizeof(*st));
+    *overflow = false;
+    const bool timed = h->timing != 0;
+    const bool graph = h->use_graph && !timed;
     // the stage loop
     for (int guard_iter = 0; guard_iter < 4 * p + 16; ++guard_iter) {
         if (graph) {
-            CK(cudaGraphLaunch(h->gexec, s));
+            if (guard_iter > 0) CK(cudaGraphLaunch(h->gexec, s));
             if (pc_status r = read_info(h)) return r;
         } else {
             if (pc_status r = read_info(h)) return r;
@@ -758,6 +1093,10 @@ static pc_status skeleton_once(pc_handle *h, pc_stats *st, bool *overflow)
                 // fall through to the checks below
             } else {
                 int mmax = std::max(fpc::LG_DIRECT + 2, h->info_h->l + 2);
+                if (mmax > fpc::DIRECT_MMAX) {
+                    // the gate halts the stage if it really has direct tests that large
+                    mmax = fpc::DIRECT_MMAX;
+                }
                 if (pc_status r = enqueue_level(h, s, mmax, false, timed)) return r;
                 continue;
             }
@@ -776,7 +1115,13 @@ static pc_status skeleton_once(pc_handle *h, pc_stats *st, bool *overflow)
         }
         if (I.done) break;
         if (I.need_host) {
-            // a direct-path stage too large for the captured layout: run it here
+            // a direct-path stage too large for the captured layout: run it here, up to
+            // the largest matrix one warp can hold in shared memory
+            if (I.l + 2 > fpc::DIRECT_MMAX)
+                return fail(h, PC_ERR_BUDGET,
+                            "stage l=" + std::to_string(I.l) + " needs direct tests of size " +
+                                std::to_string(I.l + 2) + " (largest supported " +
+                                std::to_string(fpc::DIRECT_MMAX) + "); use the conventional order");
             if (pc_status r = clear_halt(h)) return r;
             if (pc_status r = enqueue_level(h, s, I.l + 2, false, timed)) return r;
         }
@@ -789,7 +1134,8 @@ static pc_status skeleton_once(pc_handle *h, pc_stats *st, bool *overflow)
     CK(cudaStreamSynchronize(s));
     const DevCounters &c = *h->ctr_h;
     const LevelInfo &I = *h->info_h;
-    if (graph) g_launches.fetch_add((long long)I.body_runs * h->body_kernels);
+    // the captured body counts the kernels its conditional nodes actually ran
+    if (graph) g_launches.fetch_add((long long)I.kernels_run);
     if (c.status)
         return fail(h, (pc_status)c.status,
                     h->learned ? "device-side error during the skeleton search (or a proposed sepset failed the FP64 re-verification)"
@@ -821,6 +1167,12 @@ static pc_status skeleton_once(pc_handle *h, pc_stats *st, bool *overflow)
     return PC_OK;
 }
 
+static pc_status skeleton_once(pc_handle *h, pc_stats *st, bool *overflow)
+{
+    if (pc_status r = skeleton_enqueue(h)) return r;
+    return skeleton_complete(h, st, overflow);
+}
+
 static pc_status skeleton_run(pc_handle *h, pc_stats *st)
 {
     for (int attempt = 0; attempt < 6; ++attempt) {
@@ -838,6 +1190,86 @@ static pc_status skeleton_run(pc_handle *h, pc_stats *st)
     return fail(h, PC_ERR_INTERNAL, "sepset pool could not be sized");
 }
 
+static pc_status copy_adj(pc_handle *h, uint8_t *adj_out);
+
+// Coordinate search over the launch shape of the test kernels: each knob in
+// turn takes the candidate with the least mean skeleton time (CUDA events on
+// the handle's stream, `reps` runs after one warm run); the others stay at
+// their current best.  The skeleton and sepsets do not depend on the shape
+// (frozen adjacency per stage, smallest key wins), so every run is a valid
+// search and the handle keeps the fastest shape.
+extern "C" pc_status pc_autotune(pc_handle *h, int32_t reps, pc_tune_result *out)
+{
+    if (!h || reps < 1 || reps > 100) return PC_ERR_ARG;
+    if (!h->have_corr) return fail(h, PC_ERR_STATE, "pc_autotune before pc_corr");
+    if (pc_status r = check_tc(h)) return r;
+    static const int chunks[] = {4, 8, 16, 32};
+    static const int rounds[] = {4, 16, 64, 256};
+    static const int blocks[] = {4, 8, 16};
+    static const int warps[] = {2, 4, 8};
+    struct Knob {
+        int *field;
+        const int *cand;
+        int nc;
+    } knobs[] = {{&h->lane_chunk, chunks, 4}, {&h->lane_rounds, rounds, 4}, {&h->lane_blocks, blocks, 3},
+                 {&h->direct_warps, warps, 3}};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    pc_status rs = PC_OK;
+    int runs = 0;
+    auto measure = [&](double *ms) -> pc_status {
+        pc_stats st;
+        if (pc_status r = skeleton_run(h, &st)) return r;            // warm run (graph capture)
+        double tot = 0.0;
+        for (int i = 0; i < reps; ++i) {
+            CK(cudaEventRecord(e0, h->stream));
+            if (pc_status r = skeleton_run(h, &st)) return r;
+            CK(cudaEventRecord(e1, h->stream));
+            CK(cudaEventSynchronize(e1));
+            float t = 0.f;
+            CK(cudaEventElapsedTime(&t, e0, e1));
+            tot += t;
+        }
+        runs += reps + 1;
+        h->last = st;
+        *ms = tot / reps;
+        return PC_OK;
+    };
+    double best = 0.0;
+    rs = measure(&best);
+    const double first = best;
+    for (int k = 0; k < 4 && rs == PC_OK; ++k) {
+        const int keep = *knobs[k].field;
+        int pick = keep;
+        for (int c = 0; c < knobs[k].nc && rs == PC_OK; ++c) {
+            if (knobs[k].cand[c] == keep) continue;
+            *knobs[k].field = knobs[k].cand[c];
+            double t = 0.0;
+            rs = measure(&t);
+            if (rs == PC_OK && t < best) {
+                best = t;
+                pick = knobs[k].cand[c];
+            }
+        }
+        *knobs[k].field = pick;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rs != PC_OK) return rs;
+    h->have_skel = true;
+    if (out) {
+        out->lane_chunk = h->lane_chunk;
+        out->lane_rounds = h->lane_rounds;
+        out->lane_blocks = h->lane_blocks;
+        out->direct_warps = h->direct_warps;
+        out->ms_default = first;
+        out->ms_best = best;
+        out->runs = runs;
+    }
+    return PC_OK;
+}
+
 extern "C" pc_status pc_skeleton(pc_handle *h, uint8_t *adj_out, pc_stats *stats)
 {
     if (!h) return PC_ERR_ARG;
@@ -849,16 +1281,62 @@ extern "C" pc_status pc_skeleton(pc_handle *h, uint8_t *adj_out, pc_stats *stats
     h->last = st;
     h->have_skel = true;
     if (stats) *stats = st;
-    if (adj_out) {
-        const int p = h->p, W = h->g.W;
-        std::vector<uint32_t> bits((size_t)p * W);
-        CK(cudaMemcpy(bits.data(), h->g.adj, bits.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost));
-        std::vector<uint8_t> A((size_t)p * p);
-        for (int u = 0; u < p; ++u)
-            for (int v = 0; v < p; ++v) A[(size_t)u * p + v] = (bits[(size_t)u * W + (v >> 5)] >> (v & 31)) & 1u;
-        CK(cudaMemcpy(adj_out, A.data(), A.size(), cudaMemcpyDefault));
-    }
+    if (adj_out) return copy_adj(h, adj_out);
     return PC_OK;
+}
+
+static pc_status copy_adj(pc_handle *h, uint8_t *adj_out)
+{
+    const int p = h->p, W = h->g.W;
+    std::vector<uint32_t> bits((size_t)p * W);
+    CK(cudaMemcpy(bits.data(), h->g.adj, bits.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    std::vector<uint8_t> A((size_t)p * p);
+    for (int u = 0; u < p; ++u)
+        for (int v = 0; v < p; ++v) A[(size_t)u * p + v] = (bits[(size_t)u * W + (v >> 5)] >> (v & 31)) & 1u;
+    CK(cudaMemcpy(adj_out, A.data(), A.size(), cudaMemcpyDefault));
+    return PC_OK;
+}
+
+extern "C" pc_status pc_skeleton_many(pc_handle **hs, int32_t count, uint8_t **adj_out, pc_stats *stats,
+                                      pc_status *status)
+{
+    if (!hs || count < 0) return PC_ERR_ARG;
+    std::vector<pc_status> st((size_t)count, PC_OK);
+    // phase 1: every search is enqueued on its handle's stream (no host wait)
+    for (int i = 0; i < count; ++i) {
+        pc_handle *h = hs[i];
+        if (!h) {
+            st[i] = PC_ERR_ARG;
+            continue;
+        }
+        if (!h->have_corr) {
+            st[i] = fail(h, PC_ERR_STATE, "pc_skeleton_many: handle without pc_corr");
+            continue;
+        }
+        st[i] = check_tc(h);
+        if (st[i] == PC_OK) st[i] = skeleton_enqueue(h);
+    }
+    // phase 2: each search completes on its own stream
+    pc_status first = PC_OK;
+    for (int i = 0; i < count; ++i) {
+        pc_handle *h = hs[i];
+        pc_stats one;
+        std::memset(&one, 0, sizeof(one));
+        if (st[i] == PC_OK) {
+            bool overflow = false;
+            st[i] = skeleton_complete(h, &one, &overflow);
+            if (st[i] == PC_OK && overflow) st[i] = skeleton_run(h, &one);   // larger pool, serial rerun
+        }
+        if (st[i] == PC_OK) {
+            h->last = one;
+            h->have_skel = true;
+            if (adj_out && adj_out[i]) st[i] = copy_adj(h, adj_out[i]);
+        }
+        if (stats) stats[i] = one;
+        if (status) status[i] = st[i];
+        if (st[i] != PC_OK && first == PC_OK) first = st[i];
+    }
+    return first;
 }
 
 extern "C" pc_status pc_sepsets_count(pc_handle *h, int64_t *n_removed, int64_t *pool_len)
@@ -921,17 +1399,20 @@ extern "C" pc_status pc_ci_batch(pc_handle *h, const int32_t *ij, const int32_t 
     if (!h->have_corr) return fail(h, PC_ERR_STATE, "pc_ci_batch before pc_corr");
     if (l < 0 || l > h->p - 2 || l > 126 || b < 0 || !ij || (l > 0 && !S))
         return fail(h, PC_ERR_ARG, "pc_ci_batch: bad l, b or pointers");
-    if (h->n - l - 3 <= 0) return fail(h, PC_ERR_DOF, "n - l - 3 <= 0");
+    // batched problems: the smallest instance bounds l for every test
+    if ((h->nblk ? h->n_min : h->n) - l - 3 <= 0) return fail(h, PC_ERR_DOF, "n - l - 3 <= 0");
     if (b == 0) return PC_OK;
     cudaStream_t s = h->stream;
     TestParams tp = make_tp(h);
+    tp.dr_max = 5e-6f;                                   // r itself is returned
     CK(cudaMemsetAsync(h->g.ctr, 0, sizeof(DevCounters), s));
     CK(fpc::launch_ci_list(ij, S, l, b, h->C32, h->C64, h->ldc, h->p, tp, r_out, indep_out, z_out,
-                           h->g.ctr, s));
+                           h->g.ctr, h->g.blk_lo, h->g.blk_hi, s));
     CK(cudaMemcpyAsync(h->ctr_h, h->g.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (h->ctr_h->status)
-        return fail(h, (pc_status)h->ctr_h->status, "pc_ci_batch: node id out of range or u == v");
+        return fail(h, (pc_status)h->ctr_h->status,
+                    "pc_ci_batch: node id out of range, u == v, or nodes of different instances");
     std::memset(&h->last, 0, sizeof(h->last));
     h->last.tests_executed = h->ctr_h->tests_executed;
     h->last.tests_redecided = h->ctr_h->redecided;
@@ -981,7 +1462,8 @@ extern "C" pc_status pc_mlp_features(pc_handle *h, const int32_t *quads, int64_t
     if (!h->have_corr) return fail(h, PC_ERR_STATE, "pc_mlp_features before pc_corr");
     if (R == 0) return PC_OK;
     CK(cudaMemsetAsync(h->mlp_err, 0, sizeof(int), h->stream));
-    CK(fpc::launch_mlp_features(quads, R, h->C32, h->ldc, h->p, h->n, h->q, feats, h->mlp_err, h->stream));
+    CK(fpc::launch_mlp_features(quads, R, h->C32, h->ldc, h->p, h->n, h->g.nvec, h->q, feats, h->mlp_err,
+                                h->stream));
     int e = 0;
     CK(cudaMemcpyAsync(&e, h->mlp_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));

@@ -10,6 +10,7 @@ namespace fpc {
 constexpr unsigned long long KEY_NONE = ~0ull;
 constexpr double DEGEN = 1e-12;        // degeneracy floor on conditional variances
 constexpr int MAXP = 4096;             // largest p a handle accepts
+constexpr int MAXP_BATCH = 32768;      // largest total p of a batched handle
 constexpr int KC_MAX = 8;              // largest dropped-set size of the complement path
 constexpr int PREC_MAX = 168;          // largest neighbourhood (|adj(u)|+1) kept as a precision block
 
@@ -53,7 +54,24 @@ struct LevelInfo {
     int first_level;                    // first enumerated stage (-1: none)
     int stage_a_ran;                    // the closed-form stage l = p-2 ran
     int body_runs;                      // executions of the stage body (kernel accounting)
+    int lane_rounds;                    // rank-major rounds of the small-stage kernel
+    int lane_overflow;                  // the FP64 re-decision queue overflowed this stage
+    int kernels_run;                    // kernels the captured stage loop executed
 };
+
+// Conditional nodes of the captured stage body: the head kernel decides which
+// kernels of a stage have work (switch over the small-stage kernel ranges, and
+// if-nodes for the warp-per-test, complement and scoring kernels); the tail
+// kernel decides the precision-block updates.
+struct StageConds {
+    cudaGraphConditionalHandle lane, direct, comp, score, prec;
+    int use;                            // 1 inside the captured stage body
+    int has_comp, has_score, has_prec;  // which nodes the body has
+};
+constexpr int LANE_LMAX = 8;            // stages the lane-per-test kernel runs (FP32 modes)
+constexpr int LANE_RANGES = 4;          // small-stage kernel instantiations: l 0-2, 3-4, 5-6, 7-8
+// kernels of a stage outside conditional nodes: head, commit, degrees, tail
+constexpr int STAGE_FIXED_KERNELS = 4;
 
 // Everything the stage kernels need, by value.
 struct GraphDev {
@@ -65,8 +83,15 @@ struct GraphDev {
     long long *ooff;            // p+1, exclusive scan of deg (ordered-pair offsets)
     unsigned long long *tn_off; // p+1: first direct test of each node (exclusive scan)
     unsigned long long *cn_off; // p+1: first complement test of each node
+    unsigned long long *rn_off; // p+1: first remainder test of each node (small-stage kernel)
     unsigned long long *best;   // p x p, best (side<<62 | rank) per unordered pair (a<b at a*p+b)
-    const unsigned long long *binom;   // (p+1) x (p+1) saturating binomials
+    const unsigned long long *binom;   // ldb x ldb saturating binomials
+    int ldb;                    // p+1 (batched problems: largest instance p + 1)
+    // batched problems (one handle over independent instances, block-diagonal):
+    // the node range [blk_lo[u], blk_hi[u]) of u's instance; null for one problem
+    const int *blk_lo, *blk_hi;
+    const long long *nvec;      // batched problems: samples of each node's instance
+    unsigned char *scored;      // learned order: per stage, 1 if its sets ran in the proposed order
     int *sep_level;             // p x p (a<b at a*p+b), -1 none
     int *sep_side;
     long long *sep_rank;
@@ -91,14 +116,31 @@ struct GraphDev {
 
 struct TestParams {
     long long n;        // samples
+    const long long *nvec;  // batched problems: samples of each node's instance (null: n)
     double q;           // threshold Phi^{-1}(1-alpha/2)
     float qf;
     double band;        // |z - q| band for FP64 re-decision
     double guard;       // pivot guard
     float eps_c;        // bound on |C32 - corr| (FP32 GEMM or cast: 2^-23; BF16x3 tensor cores: 1e-6)
+    float dr_max;       // largest FP32 error bound on r trusted without FP64: 5e-6 where r is
+                        // returned (raw tests), 1e-4 where only the decision is (skeleton)
+    // launch shape (autotuned; results do not depend on them)
+    int lane_chunk;     // consecutive sets of one pair per thread in the small-stage kernel
+    int lane_rounds;    // rank-major chunk rounds before the pair-major remainder
+    int lane_blocks;    // CTAs of 256 threads per SM of the small-stage kernel
+    int direct_warps;   // at most this many warps per CTA of the warp-per-test kernel
     int precision;      // 0 fp64, 1/2 fp32 tests with FP64 re-decision
     int reversed;
     int complement;
+    // lazily filled FP64 correlations: entry (a,b) of C64 is valid once
+    // c64_valid[a*p+b] is set; a missing entry is the warp's dot product of
+    // the FP64 standardised columns a and b divided by n
+    int lazy;
+    int p;
+    double learned_min;  // a stage is scored only if it schedules at least this many tests
+    const double *xs64;
+    long long ldk;
+    unsigned char *c64_valid;
 };
 
 // counts kernel launches (defined in fastpc_api.cu); inside a stream capture the
@@ -120,7 +162,11 @@ cudaError_t launch_syrk_f64(const double *Xs, long long n, long long ldk, int p,
 size_t syrk_f64_ws_bytes(long long n, int p);
 cudaError_t launch_syrk_f32(const float *Xs, long long n, long long ldk, int p, float *C32,
                             int ldc, cudaStream_t s);
+cudaError_t launch_c64_lazy_init(double *C64, int ldc, unsigned char *valid, int p, cudaStream_t s);
 cudaError_t launch_cast_c(const double *C64, float *C32, int p, int ldc, cudaStream_t s);
+cudaError_t launch_c64_lazy_init_block(double *C64, int ldc, unsigned char *valid, int P, int o, int pb,
+                                       cudaStream_t s);
+cudaError_t launch_cast_block(const double *C64, float *C32, int ldc, int o, int pb, cudaStream_t s);
 bool tc_gemm_available();
 cudaError_t launch_corr_bf16x3(const uint16_t *Xhi, const uint16_t *Xlo, long long n, long long ldk,
                                int p, float *C32, int ldc, float *ws, size_t ws_bytes, int *err,
@@ -136,13 +182,22 @@ cudaError_t launch_stage_a_decide(const double *P, int p, int ldp, const int *si
 // ---- stage kernels (level.cu); they read the stage index from info->l and
 // return at once when info->done or info->halt is set
 constexpr int LG_DIRECT = 24;          // direct-path stages a captured stage loop can run
+constexpr int DIRECT_MMAX = 160;       // largest (l+2) matrix one warp holds in shared memory
+cudaError_t launch_init_adj(GraphDev g, cudaStream_t s);
 cudaError_t launch_level_degrees(GraphDev g, cudaStream_t s);
 cudaError_t launch_tail(GraphDev g, TestParams tp, int cap, int mode, const int *stagea_singular,
-                        int stagea_launched, cudaGraphConditionalHandle hc, int use_cond, cudaStream_t s);
-cudaError_t launch_head(GraphDev g, TestParams tp, double budget, int mmax_direct, cudaStream_t s);
+                        int stagea_launched, cudaGraphConditionalHandle hc, int use_cond, StageConds sc,
+                        cudaStream_t s);
+cudaError_t launch_head(GraphDev g, TestParams tp, double budget, int mmax_direct, StageConds sc, cudaStream_t s);
 cudaError_t launch_ci_direct(GraphDev g, TestParams tp, int mmax, const float *C32,
                              const double *C64, int ldc, cudaStream_t s);
 cudaError_t launch_ci_complement(GraphDev g, TestParams tp, cudaStream_t s);
+// range: one instantiation (0 .. LANE_RANGES-1) or -1 for all; prop: the
+// variant for handles with a proposal network
+cudaError_t launch_ci_lane(GraphDev g, TestParams tp, const float *C32, const double *C64, int ldc,
+                           unsigned long long *queue, unsigned long long qcap, unsigned long long *qlen,
+                           int range, bool prop, cudaStream_t s);
+int lane_range_of(int l);
 cudaError_t launch_prec_update(GraphDev g, const double *C64, int ldc, cudaStream_t s);
 cudaError_t launch_commit(GraphDev g, long long n_opairs_cap, int l_fixed, int explicit_sets,
                           cudaStream_t s);
@@ -156,19 +211,20 @@ cudaError_t launch_mlp_forward_feats(const float *feats, long long R, const uint
                                      float *scores, __nv_bfloat16 *h1, float *h2, int *err, GraphDev g,
                                      cudaStream_t s);
 cudaError_t launch_mlp_score_stage(GraphDev g, const unsigned long long *row_off, long long rows_cap,
-                                   const float *C32, int ldc, float sqn_over_q, const uint8_t *wpack,
+                                   const float *C32, int ldc, float sqn_over_q, float inv_q, const uint8_t *wpack,
                                    const float *theta, float *scores, short *perm, int *err, cudaStream_t s);
 cudaError_t launch_mlp_backward(const float *feats, const float *labels, const float *scores,
                                 const __nv_bfloat16 *h1, const float *h2, long long R, float inv_b,
                                 const float *theta, float *grad, double *loss, cudaStream_t s);
 cudaError_t launch_adam(float *theta, const float *grad, float *m, float *v, float lr, int step, cudaStream_t s);
 cudaError_t launch_mlp_features(const int *quads, long long R, const float *C32, int ldc, int p, long long n,
-                                double q, float *feats, int *err, cudaStream_t s);
+                                const long long *nvec, double q, float *feats, int *err, cudaStream_t s);
 cudaError_t launch_reverify(GraphDev g, TestParams tp, const double *C64, int ldc, cudaStream_t s);
 
 // ---- raw test batches (level.cu)
 cudaError_t launch_ci_list(const int *ij, const int *S, int l, long long b, const float *C32,
                            const double *C64, int ldc, int p, TestParams tp, double *r_out,
-                           uint8_t *indep_out, float *z_out, DevCounters *ctr, cudaStream_t s);
+                           uint8_t *indep_out, float *z_out, DevCounters *ctr, const int *blk_lo,
+                           const int *blk_hi, cudaStream_t s);
 
 }  // namespace fpc

@@ -30,10 +30,53 @@ __device__ __forceinline__ ull sat_add(ull a, ull b)
     return c < a ? KEY_NONE : c;
 }
 
+
+// small-stage kernel instantiation that runs stage l (l <= LANE_LMAX)
+__host__ __device__ __forceinline__ int lane_range_of_dev(int l)
+{
+    return l <= 2 ? 0 : (l <= 4 ? 1 : (l <= 6 ? 2 : 3));
+}
+int lane_range_of(int l) { return lane_range_of_dev(l); }
+
+// samples behind the tests of node u (batched problems: its instance's n)
+__device__ __forceinline__ long long n_of(const TestParams &tp, int u)
+{
+    return tp.nvec ? __ldg(tp.nvec + u) : tp.n;
+}
+
+// node u has tests at stage l only while n_u - l - 3 > 0 (one problem: the
+// stage cap n - 4 already ensures it; batched problems differ in n)
+__device__ __forceinline__ bool dof_ok(const TestParams &tp, int u, int l)
+{
+    return !tp.nvec || n_of(tp, u) - l - 3 > 0;
+}
+
 // the stage loop has finished or has been halted: nothing to do
 __device__ __forceinline__ bool stopped(const LevelInfo *I) { return I->done || I->halt; }
 
 // ---------------------------------------------------------------- frozen graph
+// The complete graph (Algorithm 1/2 input): every bit v != u of row u set.
+__global__ void init_adj_kernel(GraphDev g)
+{
+    const long long tot = (long long)g.p * g.W;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int u = (int)(i / g.W), w = (int)(i % g.W);
+        uint32_t bits = 0xffffffffu;
+        const int lo = w * 32;
+        if (lo + 32 > g.p) bits = g.p - lo >= 32 ? 0xffffffffu : ((1u << (g.p - lo)) - 1u);
+        if (u >= lo && u < lo + 32) bits &= ~(1u << (u - lo));
+        if (g.blk_lo) {
+            // batched problems: only nodes of u's own instance are adjacent
+            const int b0 = g.blk_lo[u] - lo, b1 = g.blk_hi[u] - lo;
+            const uint32_t keep_lo = b0 <= 0 ? 0xffffffffu : (b0 >= 32 ? 0u : ~((1u << b0) - 1u));
+            const uint32_t keep_hi = b1 >= 32 ? 0xffffffffu : (b1 <= 0 ? 0u : ((1u << b1) - 1u));
+            bits &= keep_lo & keep_hi;
+        }
+        g.adj[i] = bits;
+    }
+}
+
 // Degrees and ascending neighbour lists of the current graph, one warp per node.
 __global__ void degrees_kernel(GraphDev g)
 {
@@ -77,18 +120,21 @@ __device__ __forceinline__ bool comp_eligible(int d, int l, const TestParams &tp
 //                then l <- min(l-1, L*) while l >= 0.
 __global__ void __launch_bounds__(1024) tail_kernel(GraphDev g, TestParams tp, int cap, int mode,
                                                     const int *stagea_singular, int stagea_launched,
-                                                    cudaGraphConditionalHandle hc, int use_cond)
+                                                    cudaGraphConditionalHandle hc, int use_cond, StageConds sc)
 {
     LevelInfo *I = g.info;
     __shared__ long long part[1024];
     __shared__ int smax[1024];
-    __shared__ int sh_l, sh_go;
+    __shared__ int sh_l, sh_go, sh_need, sh_removed;
     const int p = g.p, t = threadIdx.x;
     if (mode == 0 && t == 0) I->body_runs++;
     if (stopped(I)) {
         if (use_cond && t == 0) cudaGraphSetConditional(hc, 0u);
+        if (sc.use && sc.has_prec && t == 0) cudaGraphSetConditional(sc.prec, 0u);
+        if (sc.use && t == 0) I->kernels_run += 1;
         return;
     }
+    if (t == 0) sh_need = 0;
     const int per = (p + 1023) / 1024;
     const int s0 = min(p, t * per), s1 = min(p, s0 + per);
     long long sum = 0;
@@ -118,6 +164,7 @@ __global__ void __launch_bounds__(1024) tail_kernel(GraphDev g, TestParams tp, i
         const int lstar = smax[1023] - 1;              // -1 when no edge is left
         g.ooff[p] = tot;
         I->n_opairs = tot;
+        sh_removed = I->edges != (unsigned long long)tot;   // the commit deleted edges
         I->edges = (unsigned long long)tot;
         I->lstar = lstar;
         if (mode == 1) {
@@ -163,12 +210,23 @@ __global__ void __launch_bounds__(1024) tail_kernel(GraphDev g, TestParams tp, i
         for (int u = t; u < p; u += blockDim.x) {
             const int dg = g.deg[u];
             bool need;
-            if (mode == 1) need = dg >= 2 && dg + 1 <= PREC_MAX && g.prec_m[u] == 0;
-            else need = dg > 0 && comp_eligible(dg - 1, sh_l, tp) && g.prec_m[u] == 0;
+            const int pmu = g.prec_m[u];
+            if (mode == 1) need = dg >= 2 && dg + 1 <= PREC_MAX && pmu == 0;
+            else need = dg > 0 && comp_eligible(dg - 1, sh_l, tp) && (pmu == 0 || pmu == -2);
             g.prec_need[u] = need;
+            if (need) sh_need = 1;
         }
     }
+    __syncthreads();
     if (use_cond && t == 0) cudaGraphSetConditional(hc, sh_go ? 1u : 0u);
+    if (sc.use && sc.has_prec && t == 0) {
+        // precision blocks change when a node asks for one or blocks lost members
+        const int run = sh_go && (sh_need || sh_removed);
+        cudaGraphSetConditional(sc.prec, run ? 1u : 0u);
+        I->kernels_run += 1 + (run ? 2 : 0);             // the tail itself, prec update + mark
+    } else if (sc.use && t == 0) {
+        I->kernels_run += 1;
+    }
 }
 
 __device__ __forceinline__ ull sat_mul(ull a, ull b)
@@ -183,11 +241,26 @@ __device__ __forceinline__ ull sat_mul(ull a, ull b)
 // One CTA scans the per-node totals into tn_off / cn_off and gates the stage:
 // budget and saturation (PC_ERR_BUDGET), or direct tests at an l larger than
 // the direct kernel's shared-memory layout (the host runs that stage).
+__device__ __forceinline__ void set_stage_conds(const StageConds &sc, LevelInfo *I, int lane, int direct, int comp,
+                                                int score)
+{
+    cudaGraphSetConditional(sc.lane, (unsigned)lane);
+    cudaGraphSetConditional(sc.direct, (unsigned)direct);
+    if (sc.has_comp) cudaGraphSetConditional(sc.comp, (unsigned)comp);
+    if (sc.has_score) cudaGraphSetConditional(sc.score, (unsigned)score);
+    // head, commit, degrees + lane branch (kernel, FP64 pass, overflow pass) + the rest
+    // (the tail counts itself and the precision update)
+    I->kernels_run += STAGE_FIXED_KERNELS - 1 + (lane < LANE_RANGES ? 3 : 0) + direct + comp + 2 * score;
+}
+
 __global__ void __launch_bounds__(1024) head_kernel(GraphDev g, TestParams tp, double budget,
-                                                    int mmax_direct)
+                                                    int mmax_direct, StageConds conds)
 {
     LevelInfo *I = g.info;
-    if (stopped(I)) return;
+    if (stopped(I)) {
+        if (conds.use && threadIdx.x == 0) set_stage_conds(conds, I, LANE_RANGES, 0, 0, 0);
+        return;
+    }
     __shared__ ull pd[1024], pc[1024], pr[1024];
     __shared__ int ssat;
     const int p = g.p, l = I->l, t = threadIdx.x;
@@ -201,7 +274,7 @@ __global__ void __launch_bounds__(1024) head_kernel(GraphDev g, TestParams tp, d
     ull sd = 0, sc = 0, sr = 0;
     for (int u = s0; u < s1; ++u) {
         const int dg = g.deg[u], d = dg - 1;
-        const ull T = (dg > 0 && d >= l) ? g.binom[(long long)d * (p + 1) + l] : 0ull;
+        const ull T = (dg > 0 && d >= l && dof_ok(tp, u, l)) ? g.binom[(long long)d * g.ldb + l] : 0ull;
         const ull tot = sat_mul(T, (ull)dg);
         if (tot == KEY_NONE) ssat = 1;
         const bool comp = T && comp_eligible(d, l, tp) && g.prec_m[u] > 0;
@@ -223,10 +296,13 @@ __global__ void __launch_bounds__(1024) head_kernel(GraphDev g, TestParams tp, d
         __syncthreads();
     }
     ull rd = t ? pd[t - 1] : 0ull, rc = t ? pc[t - 1] : 0ull, rr = t ? pr[t - 1] : 0ull;
-    const bool rows_fit = pr[1023] <= (ull)g.rows_cap;   // else: plain order this stage
+    // else: plain order this stage (too many rows, or too few tests for the order to matter)
+    const bool rows_fit = pr[1023] <= (ull)g.rows_cap && (double)pd[1023] + (double)pc[1023] >= tp.learned_min;
+    const ull rows_total = pr[1023];
+    if (t == 0 && g.scored) g.scored[l] = rows_fit && rows_total > 0;
     for (int u = s0; u < s1; ++u) {
         const int dg = g.deg[u], d = dg - 1;
-        const ull T = (dg > 0 && d >= l) ? g.binom[(long long)d * (p + 1) + l] : 0ull;
+        const ull T = (dg > 0 && d >= l && dof_ok(tp, u, l)) ? g.binom[(long long)d * g.ldb + l] : 0ull;
         const ull tot = sat_mul(T, (ull)dg);
         const bool comp = T && comp_eligible(d, l, tp) && g.prec_m[u] > 0;
         g.tn_off[u] = rd;
@@ -237,11 +313,62 @@ __global__ void __launch_bounds__(1024) head_kernel(GraphDev g, TestParams tp, d
         rr += prows(dg, T);
     }
     __syncthreads();
+    // rank-major rounds of the lane kernel: at most tp.lane_rounds chunks of every
+    // direct pair, the rest in the pair-major remainder space rn_off
+    {
+        ull mx = 0;
+        for (int u = s0; u < s1; ++u) {
+            const int dg = g.deg[u], d = dg - 1;
+            const ull T = (dg > 0 && d >= l && dof_ok(tp, u, l)) ? g.binom[(long long)d * g.ldb + l] : 0ull;
+            const bool comp = T && comp_eligible(d, l, tp) && g.prec_m[u] > 0;
+            if (!comp && T > mx) mx = T;
+        }
+        pr[t] = mx;
+        __syncthreads();
+        for (int off = 512; off > 0; off >>= 1) {
+            if (t < off) pr[t] = pr[t] > pr[t + off] ? pr[t] : pr[t + off];
+            __syncthreads();
+        }
+        const ull maxT = pr[0];
+        __syncthreads();
+        const ull chunk = (ull)tp.lane_chunk;
+        const int rounds = (int)(maxT == 0 ? 0 : min((ull)tp.lane_rounds, (maxT + chunk - 1) / chunk));
+        const ull skip = (ull)rounds * chunk;
+        ull sr2 = 0;
+        for (int u = s0; u < s1; ++u) {
+            const int dg = g.deg[u], d = dg - 1;
+            const ull T = (dg > 0 && d >= l && dof_ok(tp, u, l)) ? g.binom[(long long)d * g.ldb + l] : 0ull;
+            const bool comp = T && comp_eligible(d, l, tp) && g.prec_m[u] > 0;
+            if (!comp && T > skip) sr2 = sat_add(sr2, sat_mul(T - skip, (ull)dg));
+        }
+        pr[t] = sr2;
+        __syncthreads();
+        for (int off = 1; off < 1024; off <<= 1) {
+            ull c = t >= off ? pr[t - off] : 0ull;
+            __syncthreads();
+            pr[t] = sat_add(pr[t], c);
+            __syncthreads();
+        }
+        ull rr2 = t ? pr[t - 1] : 0ull;
+        for (int u = s0; u < s1; ++u) {
+            const int dg = g.deg[u], d = dg - 1;
+            const ull T = (dg > 0 && d >= l && dof_ok(tp, u, l)) ? g.binom[(long long)d * g.ldb + l] : 0ull;
+            const bool comp = T && comp_eligible(d, l, tp) && g.prec_m[u] > 0;
+            g.rn_off[u] = rr2;
+            if (!comp && T > skip) rr2 = sat_add(rr2, sat_mul(T - skip, (ull)dg));
+        }
+        if (t == 1023) g.rn_off[p] = pr[1023];
+        if (t == 0) {
+            I->lane_rounds = rounds;
+            I->lane_overflow = 0;
+        }
+    }
+    __syncthreads();
     if (t == 0) {
         const ull td = pd[1023], tc = pc[1023];
         g.tn_off[p] = td;
         g.cn_off[p] = tc;
-        if (g.row_off) g.row_off[p] = rows_fit ? pr[1023] : 0ull;
+        if (g.row_off) g.row_off[p] = rows_fit ? rows_total : 0ull;
         I->total_direct = td;
         I->total_comp = tc;
         I->saturated = ssat || td == KEY_NONE || tc == KEY_NONE;
@@ -251,6 +378,13 @@ __global__ void __launch_bounds__(1024) head_kernel(GraphDev g, TestParams tp, d
         } else if (td > 0 && l + 2 > mmax_direct) {
             I->need_host = 1;
             I->halt = 1;
+        }
+        if (conds.use) {
+            const bool run = !I->halt;
+            const bool small = tp.precision != 0 && l <= LANE_LMAX;
+            set_stage_conds(conds, I, run && small && td > 0 ? lane_range_of_dev(l) : LANE_RANGES,
+                            run && td > 0 && !small, run && tc > 0,
+                            run && g.row_off && rows_fit && rows_total > 0);
         }
     }
 }
@@ -263,7 +397,7 @@ __device__ __forceinline__ void locate_test(const GraphDev &g, const ull *noff, 
     const int p = g.p;
     u = (int)(upper_bound_dev(noff, (long long)p + 1, t) - 1);
     d = g.deg[u] - 1;
-    const ull T = g.binom[(long long)d * (p + 1) + l];
+    const ull T = g.binom[(long long)d * g.ldb + l];
     const ull w = t - noff[u];
     const ull jj = w / T;
     j = (int)jj;
@@ -326,6 +460,53 @@ __device__ __forceinline__ ull flops_direct(int l)
     return (L * L * L) / 3 + 2 * L * L + 6 * L + 10;
 }
 
+// Fills the FP64 correlations the lower triangle of corr[nd, nd] needs (lazy
+// mode): every missing entry is computed once by a whole warp -- lane t sums
+// samples t, t+32, ... in order, a fixed butterfly adds the lanes -- and
+// published with a fence before its flag, so racing warps write equal values.
+__device__ __noinline__ void ensure_c64(const int *nd, int m, const TestParams &tp, double *C64, int ldc)
+{
+    const int lane = threadIdx.x & 31;
+    const int ne = m * (m + 1) / 2;
+    volatile unsigned char *valid = tp.c64_valid;
+    for (int e0 = 0; e0 < ne; e0 += 32) {
+        const int e = e0 + lane;
+        bool miss = false;
+        int a = 0, b = 0;
+        if (e < ne) {
+            int i = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+            while (i * (i + 1) / 2 > e) --i;
+            while ((i + 1) * (i + 2) / 2 <= e) ++i;
+            const int c = e - i * (i + 1) / 2;
+            a = nd[i];
+            b = nd[c];
+            miss = a != b && !valid[(long long)a * tp.p + b];
+        }
+        unsigned bal = __ballot_sync(0xffffffffu, miss);
+        while (bal) {
+            const int src = __ffs(bal) - 1;
+            const int aa = __shfl_sync(0xffffffffu, a, src), bb = __shfl_sync(0xffffffffu, b, src);
+            const double *xa = tp.xs64 + (long long)aa * tp.ldk, *xb = tp.xs64 + (long long)bb * tp.ldk;
+            const long long na = n_of(tp, aa);
+            double acc = 0.0;
+            for (long long t = lane; t < na; t += 32) acc = fma(xa[t], xb[t], acc);
+            for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+            if (lane == 0) {
+                const double v = acc / (double)na;
+                C64[(long long)aa * ldc + bb] = v;
+                C64[(long long)bb * ldc + aa] = v;
+                __threadfence();
+                valid[(long long)aa * tp.p + bb] = 1;
+                valid[(long long)bb * tp.p + aa] = 1;
+            }
+            bal &= bal - 1;
+        }
+        __syncwarp();
+    }
+    __threadfence_block();
+    __syncwarp();
+}
+
 // One CI test for node ids nd[0..m) (S..., u, v) by the calling warp.
 // Returns independent; writes r and z (of the path that decided).
 template <bool F64>
@@ -357,7 +538,7 @@ __device__ __forceinline__ bool warp_test(const int *nd, int m, int l, const flo
             const float omr = fmaxf(1.0f - rf * rf, 1e-3f);
             zf = fabsf(rf) < 1.0f ? sqf * fabsf(atanhf(rf)) : INFINITY;
             const float dz = sqf * dr / omr;
-            if (dr > 5e-6f) {
+            if (dr > tp.dr_max) {
                 need64 = true;
                 ++acc.guard;
             } else if (fabsf(zf - tp.qf) < (float)tp.band + 4.0f * dz) {
@@ -373,8 +554,12 @@ __device__ __forceinline__ bool warp_test(const int *nd, int m, int l, const flo
     float z = zf;
     if (need64) {
         double *M = (double *)Mbuf;
+        if (tp.lazy) ensure_c64(nd, m, tp, (double *)C64, ldc);
         for (int i = 0; i < m; ++i)
-            for (int c = lane; c <= i; c += 32) M[i * ms + c] = C64[(long long)nd[i] * ldc + nd[c]];
+            for (int c = lane; c <= i; c += 32) {
+                const long long o = (long long)nd[i] * ldc + nd[c];
+                M[i * ms + c] = tp.lazy ? ((volatile const double *)C64)[o] : C64[o];
+            }
         __syncwarp();
         double pmin;
         bool bad;
@@ -448,6 +633,7 @@ __global__ void __launch_bounds__(256) ci_direct_kernel(GraphDev g, TestParams t
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int m = l + 2, p = g.p;
     if (m > mmax) return;
+    if (!F64 && l <= LANE_LMAX && !g.info->lane_overflow) return;  // small stages: ci_lane_kernel
     unsigned char *mine = smem_raw + (size_t)wib * per_warp_bytes;
     double *Mbuf = (double *)mine;
     int *nd = (int *)(mine + (size_t)mmax * ms * sizeof(double));
@@ -469,7 +655,7 @@ __global__ void __launch_bounds__(256) ci_direct_kernel(GraphDev g, TestParams t
         ull *bp = g.best + (long long)a * p + b;
         if (*(volatile ull *)bp < key) continue;   // an earlier set already separates
         if (lane == 0) {
-            unrank_lex(rank, d, l, g.binom, p + 1, pos);
+            unrank_lex(rank, d, l, g.binom, g.ldb, pos);
             for (int i = 0; i < l; ++i) nd[i] = g.nbr[(long long)u * p + cand_index(g, u, j, d, pos[i])];
             if (g.row_off) sort_small(nd, l);        // the set is tested in ascending-id order
             nd[l] = u;
@@ -479,11 +665,395 @@ __global__ void __launch_bounds__(256) ci_direct_kernel(GraphDev g, TestParams t
         double r;
         float z;
         ++acc.tests;
-        bool ind = warp_test<F64>(nd, m, l, C32, C64, ldc, tp, sq, sqf, Mbuf, ms, acc, r, z);
+        const double squ = tp.nvec ? sqrt((double)(n_of(tp, u) - l - 3)) : sq;
+        bool ind = warp_test<F64>(nd, m, l, C32, C64, ldc, tp, squ, tp.nvec ? (float)squ : sqf, Mbuf, ms, acc,
+                                  r, z);
         if (ind && lane == 0) atomicMin(bp, key);
         __syncwarp();
     }
     if (lane == 0) flush_acc(acc, g.ctr);
+}
+
+
+// ---------------------------------------------------------------- direct path, small stages
+// One thread per chunk of tp.lane_chunk consecutive sets of one ordered pair
+// (l <= LANE_LMAX): one unranking, then lexicographic successors; the
+// (l+2)x(l+2) lower triangle (order S..., u, v) lives in registers and is
+// factored with compile-time indices.  A chunk stops at the first set its pair
+// already beats.  Tests the FP32 error model cannot trust go to a queue that a
+// warp-per-test FP64 pass drains before the commit; when the queue is full the
+// direct kernel re-runs the stage.
+
+// Decision of one FP32 test of the small-stage kernel from the trailing 2x2
+// (h11, h12, h22) and the smallest pivot: true = independent (the caller
+// records the key and stops); a test the FP32 error model cannot trust goes
+// to the FP64 queue.
+template <int L>
+__device__ __forceinline__ bool lane_decide(const TestParams &tp, float sqf, float h11, float h12, float h22,
+                                            float pmin, bool bad, ull flat, ull *queue, ull qcap, ull *qlen,
+                                            WarpAcc &acc)
+{
+    constexpr int M = L + 2;
+    pmin = fminf(pmin, fminf(h11, h22));
+    bad |= !(h11 > 1e-12f) || !(h22 > 1e-12f);
+    ++acc.tests;
+    acc.fl32 += flops_direct(L);
+    bool queue_it = false, ind = false;
+    if (bad || pmin < (float)tp.guard) {
+        queue_it = true;
+        ++acc.guard;
+    } else {
+        const float rf = h12 * rsqrtf(h11 * h22);
+        const float dr = 2.0f * ((float)M * 5.96e-8f + tp.eps_c) / pmin;
+        const float zf = fabsf(rf) < 1.0f ? sqf * fabsf(atanhf(rf)) : INFINITY;
+        const float dz = sqf * dr / fmaxf(1.0f - rf * rf, 1e-3f);
+        if (dr > tp.dr_max) {
+            queue_it = true;
+            ++acc.guard;
+        } else if (fabsf(zf - tp.qf) < (float)tp.band + 4.0f * dz) {
+            queue_it = true;
+            ++acc.band;
+        } else {
+            ind = zf <= tp.qf;
+        }
+    }
+    if (queue_it) {
+        const ull slot = atomicAdd(qlen, 1ull);
+        if (slot < qcap) queue[slot] = flat;
+    }
+    return ind;
+}
+
+// lexicographic successor of pos (L of d); returns the first position that changed
+template <int L>
+__device__ __forceinline__ int lex_next(int *pos, int d)
+{
+    int i = L - 1;
+    while (i >= 0 && pos[i] == d - L + i) --i;
+    if (i >= 0) {
+        ++pos[i];
+        for (int k2 = i + 1; k2 < L; ++k2) pos[k2] = pos[k2 - 1] + 1;
+    }
+    return i;
+}
+
+// Proposal order (the sets of a pair in the order the scoring network gave):
+// every test gathers and factors its whole matrix, members sorted by id.
+template <int L>
+__device__ __forceinline__ void lane_tests(const GraphDev &g, const TestParams &tp, const float *C32, int ldc,
+                                           int u, int j, int d, ull T, ull rank, ull rank_end, ull *queue,
+                                           ull qcap, ull *qlen, WarpAcc &acc)
+{
+    constexpr int M = L + 2;
+    const int p = g.p;
+    const float sqf = sqrtf((float)(n_of(tp, u) - L - 3));
+    const int v = g.nbr[(long long)u * p + j];
+    const int side = u > v;
+    ull *bp = g.best + (long long)min(u, v) * p + max(u, v);
+    const ull tbase = g.tn_off[u] + (ull)j * T;          // flat index of (u, j, rank 0)
+    int pos[L > 0 ? L : 1];
+    unrank_lex(rank, d, L, g.binom, g.ldb, pos);
+    for (; rank < rank_end; ++rank) {
+        const ull key = ((ull)side << 62) | rank;
+        if (*(volatile ull *)bp < key) return;          // an earlier set of this pair separates
+        int nd[M];
+#pragma unroll
+        for (int i = 0; i < L; ++i) nd[i] = g.nbr[(long long)u * p + cand_index(g, u, j, d, pos[i])];
+        sort_small(nd, L);
+        nd[L] = u;
+        nd[L + 1] = v;
+        float a[M * (M + 1) / 2];
+#pragma unroll
+        for (int i = 0; i < M; ++i)
+#pragma unroll
+            for (int c = 0; c <= i; ++c) a[i * (i + 1) / 2 + c] = __ldg(C32 + (long long)nd[i] * ldc + nd[c]);
+        // Cholesky of the S block, trailing 2x2 = H (Sec. 4)
+        float pmin = 1e30f;
+        bool bad = false;
+#pragma unroll
+        for (int k = 0; k < L; ++k) {
+            const float piv = a[k * (k + 1) / 2 + k];
+            pmin = fminf(pmin, piv);
+            bad |= !(piv > 1e-12f);
+            const float rl = rsqrtf(fmaxf(piv, 1e-30f));
+#pragma unroll
+            for (int i = k + 1; i < M; ++i) a[i * (i + 1) / 2 + k] *= rl;
+#pragma unroll
+            for (int i = k + 1; i < M; ++i)
+#pragma unroll
+                for (int c = k + 1; c <= i; ++c) a[i * (i + 1) / 2 + c] -= a[i * (i + 1) / 2 + k] * a[c * (c + 1) / 2 + k];
+        }
+        if (lane_decide<L>(tp, sqf, a[L * (L + 1) / 2 + L], a[(L + 1) * (L + 2) / 2 + L],
+                           a[(L + 1) * (L + 2) / 2 + L + 1], pmin, bad, tbase + rank, queue, qcap, qlen, acc)) {
+            atomicMin(bp, key);
+            return;                                      // later sets of this pair cannot win
+        }
+        if (rank + 1 < rank_end) lex_next<L>(pos, d);
+    }
+}
+
+// Lexicographic order: consecutive sets share their first L-1 members (all but
+// one step in d-L+1).  The Cholesky factor of that prefix P, the rows of u and
+// v eliminated by it (lu, lv) and the Schur block of (u, v) given P are kept in
+// registers; each test borders them with the last member s: one row of corr
+// (L+1 loads; corr_ss = 1), a forward substitution against P, then
+//   x = 1 - |l_s|^2,  c_u = corr_us - lu.l_s,  c_v = corr_vs - lv.l_s,
+//   H = H_P - [c_u c_v]^T [c_u c_v] / x
+// -- the same Cholesky of the S block (Sec. 4) in bordered form, O(L^2) work.
+template <int L>
+__device__ __forceinline__ void lane_tests_lex(const GraphDev &g, const TestParams &tp, const float *C32, int ldc,
+                                               int u, int j, int d, ull T, ull rank, ull rank_end, ull *queue,
+                                               ull qcap, ull *qlen, WarpAcc &acc)
+{
+    constexpr int K = L > 0 ? L - 1 : 0;                 // prefix length
+    constexpr int KA = K > 0 ? K : 1;
+    const int p = g.p;
+    const float sqf = sqrtf((float)(n_of(tp, u) - L - 3));
+    const int *nb = g.nbr + (long long)u * p;
+    const int v = nb[j];
+    const int side = u > v;
+    ull *bp = g.best + (long long)min(u, v) * p + max(u, v);
+    const ull tbase = g.tn_off[u] + (ull)j * T;
+    const float *Cu = C32 + (long long)u * ldc, *Cv = C32 + (long long)v * ldc;
+    const float cuv = __ldg(Cu + v);
+    int pos[L > 0 ? L : 1];
+    unrank_lex(rank, d, L, g.binom, g.ldb, pos);
+    int sp[KA];
+    float Lp[KA * (KA + 1) / 2], rd[KA], lu[KA], lv[KA];
+    float huu = 1.f, hvv = 1.f, huv = cuv, ppmin = 1e30f;
+    bool pbad = false, fresh = true;
+    for (; rank < rank_end; ++rank) {
+        const ull key = ((ull)side << 62) | rank;
+        if (*(volatile ull *)bp < key) return;
+        if (K > 0 && fresh) {
+            // factor the prefix and eliminate the rows of u and v by it
+            ppmin = 1e30f;
+            pbad = false;
+#pragma unroll
+            for (int i = 0; i < K; ++i) sp[i] = nb[pos[i] + (pos[i] >= j)];
+#pragma unroll
+            for (int i = 0; i < K; ++i) {
+                const float *Ci = C32 + (long long)sp[i] * ldc;
+                float dd = 1.f;
+#pragma unroll
+                for (int c = 0; c < i; ++c) {
+                    float t = __ldg(Ci + sp[c]);
+#pragma unroll
+                    for (int c2 = 0; c2 < c; ++c2) t -= Lp[i * (i + 1) / 2 + c2] * Lp[c * (c + 1) / 2 + c2];
+                    t *= rd[c];
+                    Lp[i * (i + 1) / 2 + c] = t;
+                    dd -= t * t;
+                }
+                ppmin = fminf(ppmin, dd);
+                pbad |= !(dd > 1e-12f);
+                const float rl = rsqrtf(fmaxf(dd, 1e-30f));
+                Lp[i * (i + 1) / 2 + i] = dd * rl;
+                rd[i] = rl;
+                float tu = __ldg(Cu + sp[i]), tv = __ldg(Cv + sp[i]);
+#pragma unroll
+                for (int c = 0; c < i; ++c) {
+                    tu -= lu[c] * Lp[i * (i + 1) / 2 + c];
+                    tv -= lv[c] * Lp[i * (i + 1) / 2 + c];
+                }
+                lu[i] = tu * rl;
+                lv[i] = tv * rl;
+            }
+            huu = 1.f;
+            hvv = 1.f;
+            huv = cuv;
+#pragma unroll
+            for (int i = 0; i < K; ++i) {
+                huu -= lu[i] * lu[i];
+                hvv -= lv[i] * lv[i];
+                huv -= lu[i] * lv[i];
+            }
+            fresh = false;
+        }
+        float h11 = huu, h22 = hvv, h12 = huv, pmin = ppmin;
+        bool bad = pbad;
+        if (L > 0) {
+            const int s = nb[pos[L - 1] + (pos[L - 1] >= j)];
+            const float *Cs = C32 + (long long)s * ldc;
+            float ls[KA];
+            float x = 1.f;
+#pragma unroll
+            for (int i = 0; i < K; ++i) {
+                float t = __ldg(Cs + sp[i]);
+#pragma unroll
+                for (int c = 0; c < i; ++c) t -= ls[c] * Lp[i * (i + 1) / 2 + c];
+                t *= rd[i];
+                ls[i] = t;
+                x -= t * t;
+            }
+            float cu = __ldg(Cs + u), cv = __ldg(Cs + v);
+#pragma unroll
+            for (int i = 0; i < K; ++i) {
+                cu -= lu[i] * ls[i];
+                cv -= lv[i] * ls[i];
+            }
+            pmin = fminf(pmin, x);
+            bad |= !(x > 1e-12f);
+            const float rx = 1.f / fmaxf(x, 1e-30f);
+            h11 -= cu * cu * rx;
+            h22 -= cv * cv * rx;
+            h12 -= cu * cv * rx;
+        }
+        if (lane_decide<L>(tp, sqf, h11, h12, h22, pmin, bad, tbase + rank, queue, qcap, qlen, acc)) {
+            atomicMin(bp, key);
+            return;
+        }
+        if (rank + 1 < rank_end && lex_next<L>(pos, d) < L - 1) fresh = true;
+    }
+}
+
+// one chunk of a pair: bordered lexicographic tests, or the proposal order
+// (PROP: the kernel variant of handles with a proposal network)
+template <int L, bool PROP>
+__device__ __forceinline__ void lane_chunk(const GraphDev &g, const TestParams &tp, const float *C32, int ldc,
+                                           int u, int j, int d, ull T, ull rank, ull rank_end, ull *queue,
+                                           ull qcap, ull *qlen, WarpAcc &acc)
+{
+    if (PROP && g.row_off && g.row_off[u + 1] > g.row_off[u])
+        lane_tests<L>(g, tp, C32, ldc, u, j, d, T, rank, rank_end, queue, qcap, qlen, acc);
+    else
+        lane_tests_lex<L>(g, tp, C32, ldc, u, j, d, T, rank, rank_end, queue, qcap, qlen, acc);
+}
+
+// Phase A, rank-major: item g = (round r, ordered pair o), r = g / NP -- a wave
+// covers rank chunk r of every direct pair, so a pair whose first chunks
+// separate skips the rest.  Phase B: the ranks beyond rounds * lane_chunk of
+// the pairs that have them, pair-major (per-node offsets rn_off).
+template <int L, bool PROP>
+__device__ __forceinline__ void lane_dispatch(const GraphDev &g, const TestParams &tp, const float *C32, int ldc,
+                                              ull *queue, ull qcap, ull *qlen)
+{
+    WarpAcc acc = {0, 0, 0, 0, 0, 0, 0, 0.f};
+    const int p = g.p;
+    const long long NP = g.info->n_opairs;
+    const int rounds = g.info->lane_rounds;
+    const ull chunk = (ull)tp.lane_chunk;
+    const ull gstride = (ull)gridDim.x * blockDim.x;
+    const ull tid = blockIdx.x * (ull)blockDim.x + threadIdx.x;
+    const ull na = (ull)rounds * (ull)NP;
+    for (ull gi = tid; gi < na; gi += gstride) {
+        const int r = (int)(gi / (ull)NP);
+        const long long o = (long long)(gi - (ull)r * NP);
+        const int u = (int)(upper_bound_dev(g.ooff, (long long)p + 1, o) - 1);
+        if (g.tn_off[u + 1] == g.tn_off[u]) continue;     // not a direct node this stage
+        const int d = g.deg[u] - 1;
+        const ull T = g.binom[(long long)d * g.ldb + L];
+        const ull r0 = (ull)r * chunk;
+        if (r0 >= T) continue;
+        const ull r1 = r0 + chunk < T ? r0 + chunk : T;
+        lane_chunk<L, PROP>(g, tp, C32, ldc, u, (int)(o - g.ooff[u]), d, T, r0, r1, queue, qcap, qlen, acc);
+    }
+    const ull nb = g.rn_off[p];
+    const ull skip = (ull)rounds * chunk;
+    const ull nbc = (nb + chunk - 1) / chunk;
+    for (ull c = tid; c < nbc; c += gstride) {
+        // chunk c of the remainder space; it may cross pairs
+        ull t = c * chunk;
+        const ull tend = t + chunk < nb ? t + chunk : nb;
+        while (t < tend) {
+            const int u = (int)(upper_bound_dev(g.rn_off, (long long)p + 1, t) - 1);
+            const int d = g.deg[u] - 1;
+            const ull T = g.binom[(long long)d * g.ldb + L];
+            const ull per = T - skip;                     // remainder ranks per pair of u
+            const ull w = t - g.rn_off[u];
+            const int j = (int)(w / per);
+            const ull rr = w - (ull)j * per;
+            const ull take = per - rr < tend - t ? per - rr : tend - t;
+            lane_chunk<L, PROP>(g, tp, C32, ldc, u, j, d, T, skip + rr, skip + rr + take, queue, qcap, qlen, acc);
+            t += take;
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        acc.tests += __shfl_xor_sync(0xffffffffu, acc.tests, off);
+        acc.band += __shfl_xor_sync(0xffffffffu, acc.band, off);
+        acc.guard += __shfl_xor_sync(0xffffffffu, acc.guard, off);
+        acc.fl32 += __shfl_xor_sync(0xffffffffu, acc.fl32, off);
+    }
+    if ((threadIdx.x & 31) == 0) flush_acc(acc, g.ctr);
+}
+
+template <int L, int HI, bool PROP>
+__device__ __forceinline__ void lane_switch(int l, const GraphDev &g, const TestParams &tp, const float *C32, int ldc,
+                                            ull *queue, ull qcap, ull *qlen)
+{
+    if constexpr (L <= HI) {
+        if (l == L) lane_dispatch<L, PROP>(g, tp, C32, ldc, queue, qcap, qlen);
+        else lane_switch<L + 1, HI, PROP>(l, g, tp, C32, ldc, queue, qcap, qlen);
+    }
+}
+
+// Stages LO <= l <= HI (one instantiation per range keeps the register count of
+// small l low: the launch sequence runs every range, all but one return at once).
+template <int LO, int HI, bool PROP>
+__global__ void __launch_bounds__(256) ci_lane_kernel(GraphDev g, TestParams tp, const float *C32, int ldc,
+                                                      ull *queue, ull qcap, ull *qlen)
+{
+    if (stopped(g.info)) return;
+    const int l = g.info->l;
+    const ull total = g.info->total_direct;
+    if (tp.precision == 0 || l < LO || l > HI || total == 0) return;
+    lane_switch<LO, HI, PROP>(l, g, tp, C32, ldc, queue, qcap, qlen);
+}
+
+// FP64 pass over the queued tests of the lane kernel (one warp per test).
+__global__ void __launch_bounds__(256) ci_redecide_kernel(GraphDev g, TestParams tp, const double *C64, int ldc,
+                                                          const ull *queue, const ull *qlen, ull qcap, int ms,
+                                                          int per_warp_bytes)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (stopped(g.info)) return;
+    const int l = g.info->l;
+    if (tp.precision == 0 || l > LANE_LMAX) return;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int m = l + 2, p = g.p;
+    unsigned char *mine = smem_raw + (size_t)wib * per_warp_bytes;
+    double *Mbuf = (double *)mine;
+    int *nd = (int *)(mine + (size_t)(LANE_LMAX + 2) * ms * sizeof(double));
+    int *pos = nd + LANE_LMAX + 2;
+    const ull nq = *qlen < qcap ? *qlen : qcap;
+    // A full queue dropped tests: the direct kernel that follows then re-runs the
+    // whole stage (FP32 first, FP64 inline), so no test goes undecided.  Keys
+    // already set here are keys of independent tests, hence still valid minima.
+    if (*qlen > qcap && blockIdx.x == 0 && threadIdx.x == 0) g.info->lane_overflow = 1;
+    const double sq = sqrt((double)(tp.n - l - 3));
+    WarpAcc acc = {0, 0, 0, 0, 0, 0, 0, 0.f};
+    for (ull qi = (blockIdx.x * (ull)blockDim.x + threadIdx.x) >> 5; qi < nq;
+         qi += ((ull)gridDim.x * blockDim.x) >> 5) {
+        const ull t = queue[qi];
+        int u, j, d;
+        ull rank;
+        locate_test(g, g.tn_off, l, t, u, j, d, rank);
+        const int v = g.nbr[(long long)u * p + j];
+        const int side = u > v;
+        const ull key = ((ull)side << 62) | rank;
+        ull *bp = g.best + (long long)min(u, v) * p + max(u, v);
+        if (*(volatile ull *)bp < key) continue;
+        if (lane == 0) {
+            unrank_lex(rank, d, l, g.binom, g.ldb, pos);
+            for (int i = 0; i < l; ++i) nd[i] = g.nbr[(long long)u * p + cand_index(g, u, j, d, pos[i])];
+            if (g.row_off) sort_small(nd, l);
+            nd[l] = u;
+            nd[l + 1] = v;
+        }
+        __syncwarp();
+        double r;
+        float z;
+        const double squ = tp.nvec ? sqrt((double)(n_of(tp, u) - l - 3)) : sq;
+        const bool ind = warp_test<true>(nd, m, l, nullptr, C64, ldc, tp, squ, (float)squ, Mbuf, ms, acc, r, z);
+        ++acc.red;
+        if (ind && lane == 0) atomicMin(bp, key);
+        __syncwarp();
+    }
+    acc.fl32 = 0;
+    if (lane == 0) {
+        if (acc.red) atomicAdd(&g.ctr->redecided, acc.red);
+        if (acc.degen) atomicAdd(&g.ctr->degenerate, acc.degen);
+        if (acc.fl64) atomicAdd(&g.ctr->flops64_direct, acc.fl64);
+    }
 }
 
 // ---------------------------------------------------------------- complement path
@@ -512,9 +1082,9 @@ __global__ void __launch_bounds__(128) ci_complement_kernel(GraphDev g, TestPara
         const ull key = ((ull)side << 62) | rank;
         ull *bp = g.best + (long long)a * p + b;
         if (*(volatile ull *)bp < key) continue;
-        const ull T = g.binom[(long long)d * (p + 1) + l];
+        const ull T = g.binom[(long long)d * g.ldb + l];
         int posR[KC_MAX];
-        unrank_lex(T - 1 - rank, d, k, g.binom, p + 1, posR);   // complement of lex is reverse lex
+        unrank_lex(T - 1 - rank, d, k, g.binom, g.ldb, posR);   // complement of lex is reverse lex
         const double *P = g.prec + (long long)u * PREC_MAX * PREC_MAX;
         const short *ps = g.prec_pos + (long long)u * p;
         const int su = ps[u], sv = ps[v];
@@ -557,7 +1127,8 @@ __global__ void __launch_bounds__(128) ci_complement_kernel(GraphDev g, TestPara
             ++ndg;
         } else {
             const double r = -Quv / sqrt(Quu * Qvv);
-            const double z = fabs(r) < 1.0 ? sq * fabs(atanh(r)) : INFINITY;
+            const double squ = tp.nvec ? sqrt((double)(n_of(tp, u) - l - 3)) : sq;
+            const double z = fabs(r) < 1.0 ? squ * fabs(atanh(r)) : INFINITY;
             ind = z <= tp.q;
         }
         ++nt;
@@ -577,24 +1148,32 @@ __global__ void __launch_bounds__(128) ci_complement_kernel(GraphDev g, TestPara
 // deleted (P <- P - P[:,w] P[w,:] / P_ww: the inverse of a principal
 // submatrix); a requested block is built by a symmetric sweep of corr[F,F],
 // F = adj(u) u {u} (ascending ids).
+constexpr int PREC_CHUNKS = 8;        // CTAs sharing one node's block downdate
+constexpr int PREC_RMAX = 48;         // removals applied in one block downdate
+
+// One node per blockIdx.x, its rows split over blockIdx.y.  A maintained block
+// drops the members the last commit deleted, R, all at once:
+//   P_TT <- P_TT - P_TR P_RR^{-1} P_RT      (T = the members kept),
+// i.e. row i gains y_i P[R,:] with y_i = -P[i,R] P_RR^{-1}.  Every CTA reads
+// only its own rows and the rows of R, which no CTA writes, so the chunks need
+// no synchronisation; prec_mark_kernel retires R afterwards.  A requested
+// block (chunk 0) is built by a symmetric sweep of corr[F,F], F = adj(u) u {u}.
 __global__ void __launch_bounds__(512) prec_update_kernel(GraphDev g, const double *C64, int ldc)
 {
     const int u = blockIdx.x;
     if (stopped(g.info)) return;
     extern __shared__ double smd[];
     __shared__ int mem[PREC_MAX];
-    __shared__ int bad;
+    __shared__ int bad, nrem;
     const int p = g.p;
     const int m0 = g.prec_m[u];
     if (m0 > 0) {
-        __shared__ int nrem;
-        int *rem = mem;                                // the member scratch is free here
-        double *colw = smd;
+        int *rem = mem;
         double *P = g.prec + (long long)u * PREC_MAX * PREC_MAX;
         const int *pm = g.prec_mem + (long long)u * PREC_MAX;
-        short *pos = g.prec_pos + (long long)u * p;
+        const short *pos = g.prec_pos + (long long)u * p;
         const uint32_t *row = g.adj + (long long)u * g.W;
-        // members deleted by the last commit, in ascending slot order (deterministic)
+        // members deleted by the last commit, ascending slots (same in every chunk)
         if (threadIdx.x < 32) {
             int cnt = 0;
             for (int s0 = 0; s0 < m0; s0 += 32) {
@@ -612,24 +1191,55 @@ __global__ void __launch_bounds__(512) prec_update_kernel(GraphDev g, const doub
         }
         __syncthreads();
         const int nr = nrem;
-        for (int q = 0; q < nr; ++q) {
-            const int s = rem[q];
-            for (int i = threadIdx.x; i < m0; i += blockDim.x) colw[i] = P[i * PREC_MAX + s];
-            __syncthreads();
-            const double ipww = 1.0 / colw[s];
-            for (int i = threadIdx.x >> 5; i < m0; i += blockDim.x >> 5) {
-                if (i == s) continue;
-                const double ci = colw[i] * ipww;
-                for (int c = threadIdx.x & 31; c < m0; c += 32)
-                    if (c != s) P[i * PREC_MAX + c] = fma(-ci, colw[c], P[i * PREC_MAX + c]);
-            }
-            __syncthreads();
+        if (nr == 0) return;
+        if (nr > PREC_RMAX) {
+            // too many at once: drop the block; it is rebuilt if the node needs it again
+            if (blockIdx.y == 0 && threadIdx.x == 0) g.prec_m[u] = -2;
+            return;
         }
-        for (int q = threadIdx.x; q < nr; q += blockDim.x) pos[pm[rem[q]]] = -1;
-        if (threadIdx.x == 0 && nr) atomicAdd(&g.ctr->flops_prec, 2ull * m0 * m0 * nr);
+        const int rows_per = (m0 + PREC_CHUNKS - 1) / PREC_CHUNKS;
+        const int r0 = blockIdx.y * rows_per, r1 = min(m0, r0 + rows_per);
+        if (r0 >= r1) return;
+        double *S = smd;                         // nr x nr: P_RR, then -P_RR^{-1}
+        double *PR = S + nr * nr;                // nr x m0: rows of R
+        double *Y = PR + (size_t)nr * m0;        // (r1 - r0) x nr
+        double *ck = Y + (size_t)(r1 - r0) * nr; // sweep column buffer
+        __shared__ int sbad;
+        if (threadIdx.x == 0) sbad = 0;
+        for (int e = threadIdx.x; e < nr * nr; e += blockDim.x) S[e] = P[rem[e / nr] * PREC_MAX + rem[e % nr]];
+        for (int e = threadIdx.x; e < nr * m0; e += blockDim.x) PR[e] = P[rem[e / m0] * PREC_MAX + e % m0];
+        __syncthreads();
+        sweep_inverse_block(S, nr, nr, ck, &sbad);   // S = -P_RR^{-1}
+        __syncthreads();
+        if (sbad) {
+            // P_RR is a principal block of an SPD inverse; a pivot at the floor means the
+            // block has lost accuracy: drop it (rebuilt from corr if the node needs it)
+            if (blockIdx.y == 0 && threadIdx.x == 0) g.prec_m[u] = -2;
+            return;
+        }
+        // y_i = P[i,R] S  for the chunk's rows
+        for (int e = threadIdx.x; e < (r1 - r0) * nr; e += blockDim.x) {
+            const int i = r0 + e / nr, b = e % nr;
+            double acc = 0.0;
+            for (int a2 = 0; a2 < nr; ++a2) acc = fma(P[i * PREC_MAX + rem[a2]], S[a2 * nr + b], acc);
+            Y[e] = acc;
+        }
+        __syncthreads();
+        for (int i = r0 + (threadIdx.x >> 5); i < r1; i += blockDim.x >> 5) {
+            bool in_r = false;
+            for (int a2 = 0; a2 < nr; ++a2) in_r |= rem[a2] == i;
+            if (in_r) continue;                  // rows of R are read by the other chunks
+            const double *y = Y + (size_t)(i - r0) * nr;
+            for (int c = threadIdx.x & 31; c < m0; c += 32) {
+                double v = P[i * PREC_MAX + c];
+                for (int b = 0; b < nr; ++b) v = fma(y[b], PR[b * m0 + c], v);
+                P[i * PREC_MAX + c] = v;
+            }
+        }
+        if (blockIdx.y == 0 && threadIdx.x == 0) atomicAdd(&g.ctr->flops_prec, 2ull * m0 * m0 * nr);
         return;
     }
-    if (!g.prec_need[u]) return;
+    if (blockIdx.y != 0 || !g.prec_need[u]) return;
     const int m = g.deg[u] + 1;
     if (threadIdx.x == 0) {
         bad = 0;
@@ -661,6 +1271,9 @@ __global__ void __launch_bounds__(512) prec_update_kernel(GraphDev g, const doub
         return;
     }
     double *P = g.prec + (long long)u * PREC_MAX * PREC_MAX;
+    // a block rebuilt after being dropped: clear the stale slot map first
+    for (int w = threadIdx.x; w < p; w += blockDim.x) g.prec_pos[(long long)u * p + w] = -1;
+    __syncthreads();
     for (int i = threadIdx.x >> 5; i < m; i += blockDim.x >> 5)
         for (int c = threadIdx.x & 31; c < m; c += 32) P[i * PREC_MAX + c] = -A[i * m + c];
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
@@ -671,6 +1284,23 @@ __global__ void __launch_bounds__(512) prec_update_kernel(GraphDev g, const doub
         g.prec_m[u] = m;
         g.prec_need[u] = 0;
         atomicAdd(&g.ctr->flops_prec, (ull)m * m * m);
+    }
+}
+
+// Retires the members the block downdate dropped (slot map entry -1).
+__global__ void prec_mark_kernel(GraphDev g)
+{
+    const int u = blockIdx.x;
+    if (stopped(g.info)) return;
+    const int m0 = g.prec_m[u];
+    if (m0 <= 0) return;
+    const int p = g.p;
+    const int *pm = g.prec_mem + (long long)u * PREC_MAX;
+    short *pos = g.prec_pos + (long long)u * p;
+    const uint32_t *row = g.adj + (long long)u * g.W;
+    for (int s = threadIdx.x; s < m0; s += blockDim.x) {
+        const int w = pm[s];
+        if (w != u && pos[w] >= 0 && !((row[w >> 5] >> (w & 31)) & 1u)) pos[w] = -1;
     }
 }
 
@@ -697,8 +1327,9 @@ __global__ void commit_kernel(GraphDev g, int l_fixed, int explicit_sets, int co
         g.best[e] = KEY_NONE;                         // ready for the next stage
         if (count_canonical) {
             const int du = g.deg[u] - 1, dv = g.deg[v] - 1;
-            const ull T0 = du >= l ? g.binom[(long long)du * (p + 1) + l] : 0ull;
-            const ull T1 = dv >= l ? g.binom[(long long)dv * (p + 1) + l] : 0ull;
+            const bool dof = !g.nvec || g.nvec[u] - l - 3 > 0;   // u and v share their instance
+            const ull T0 = du >= l && dof ? g.binom[(long long)du * g.ldb + l] : 0ull;
+            const ull T1 = dv >= l && dof ? g.binom[(long long)dv * g.ldb + l] : 0ull;
             ull c;
             if (key == KEY_NONE) c = sat_add(T0, T1);
             else if ((key >> 62) == 0) c = key + 1;
@@ -731,8 +1362,8 @@ __global__ void commit_kernel(GraphDev g, int l_fixed, int explicit_sets, int co
                 // expand through the complement: R = the kd dropped positions, at lex
                 // rank C(dd,l) - 1 - rank among the kd-subsets; S = the rest, ascending
                 int posR[KC_MAX + 1], idxR[KC_MAX];
-                const ull T = g.binom[(long long)dd * (p + 1) + l];
-                unrank_lex(T - 1 - rank, dd, kd, g.binom, p + 1, posR);
+                const ull T = g.binom[(long long)dd * g.ldb + l];
+                unrank_lex(T - 1 - rank, dd, kd, g.binom, g.ldb, posR);
                 for (int i = 0; i < kd; ++i) idxR[i] = cand_index(g, su, jj, dd, posR[i]);
                 int o = 0;
                 for (int y = 0; y <= dd; ++y) {
@@ -746,7 +1377,7 @@ __global__ void commit_kernel(GraphDev g, int l_fixed, int explicit_sets, int co
                 int x = 0;
                 for (int i = 0; i < l; ++i) {
                     while (x < dd - (l - i)) {
-                        ull c = g.binom[(long long)(dd - x - 1) * (p + 1) + (l - i - 1)];
+                        ull c = g.binom[(long long)(dd - x - 1) * g.ldb + (l - i - 1)];
                         if (r < c) break;
                         r -= c;
                         ++x;
@@ -788,13 +1419,14 @@ __global__ void __launch_bounds__(256) reverify_kernel(GraphDev g, TestParams tp
         const int l = g.sep_level[e];
         const long long off = g.sep_off[e];
         if (l < 0 || off < 0 || l + 2 > mmax) continue;
+        if (g.scored && !g.scored[l]) continue;        // a plain-order stage: its sepset is canonical
         if (lane == 0) {
             for (int i = 0; i < l; ++i) nd[i] = g.pool[off + i];
             nd[l] = a;
             nd[l + 1] = b;
         }
         __syncwarp();
-        const double sq = sqrt((double)(tp.n - l - 3));
+        const double sq = sqrt((double)(n_of(tp, a) - l - 3));
         double r;
         float z;
         const bool ind = warp_test<true>(nd, l + 2, l, nullptr, C64, ldc, tp, sq, (float)sq, Mbuf, ms, acc, r, z);
@@ -810,7 +1442,8 @@ __global__ void __launch_bounds__(256) ci_list_kernel(const int *ij, const int *
                                                       const float *C32, const double *C64, int ldc,
                                                       int p, TestParams tp, double *r_out,
                                                       uint8_t *indep_out, float *z_out,
-                                                      DevCounters *ctr, int ms, int per_warp_bytes)
+                                                      DevCounters *ctr, const int *blk_lo,
+                                                      const int *blk_hi, int ms, int per_warp_bytes)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -833,6 +1466,11 @@ __global__ void __launch_bounds__(256) ci_list_kernel(const int *ij, const int *
         __syncwarp();
         for (int i = 0; i < m; ++i) okid = okid && nd[i] >= 0 && nd[i] < p;
         okid = okid && nd[l] != nd[l + 1];
+        if (okid && blk_lo) {
+            // batched problems: every node of a test must be in x's instance
+            const int lo = blk_lo[nd[l]], hi = blk_hi[nd[l]];
+            for (int i = 0; i < m; ++i) okid = okid && nd[i] >= lo && nd[i] < hi;
+        }
         if (!okid) {
             if (lane == 0) ctr->status = 1;
             __syncwarp();
@@ -841,7 +1479,9 @@ __global__ void __launch_bounds__(256) ci_list_kernel(const int *ij, const int *
         double r;
         float z;
         ++acc.tests;
-        bool ind = warp_test<F64>(nd, m, l, C32, C64, ldc, tp, sq, sqf, Mbuf, ms, acc, r, z);
+        const double sqt = tp.nvec ? sqrt((double)(n_of(tp, nd[l]) - l - 3)) : sq;
+        bool ind = warp_test<F64>(nd, m, l, C32, C64, ldc, tp, sqt, tp.nvec ? (float)sqt : sqf, Mbuf, ms, acc,
+                                  r, z);
         if (lane == 0) {
             if (r_out) r_out[t] = r;
             if (z_out) z_out[t] = z;
@@ -865,6 +1505,13 @@ static int num_sms()
     return g_num_sms;
 }
 
+cudaError_t launch_init_adj(GraphDev g, cudaStream_t s)
+{
+    long long tot = (long long)g.p * g.W;
+    init_adj_kernel<<<(unsigned)std::min<long long>((tot + 255) / 256, 4096), 256, 0, s>>>(g); note_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_level_degrees(GraphDev g, cudaStream_t s)
 {
     degrees_kernel<<<(g.p * 32 + 255) / 256, 256, 0, s>>>(g); note_launch();
@@ -872,15 +1519,16 @@ cudaError_t launch_level_degrees(GraphDev g, cudaStream_t s)
 }
 
 cudaError_t launch_tail(GraphDev g, TestParams tp, int cap, int mode, const int *stagea_singular,
-                        int stagea_launched, cudaGraphConditionalHandle hc, int use_cond, cudaStream_t s)
+                        int stagea_launched, cudaGraphConditionalHandle hc, int use_cond, StageConds sc,
+                        cudaStream_t s)
 {
-    tail_kernel<<<1, 1024, 0, s>>>(g, tp, cap, mode, stagea_singular, stagea_launched, hc, use_cond); note_launch();
+    tail_kernel<<<1, 1024, 0, s>>>(g, tp, cap, mode, stagea_singular, stagea_launched, hc, use_cond, sc); note_launch();
     return cudaGetLastError();
 }
 
-cudaError_t launch_head(GraphDev g, TestParams tp, double budget, int mmax_direct, cudaStream_t s)
+cudaError_t launch_head(GraphDev g, TestParams tp, double budget, int mmax_direct, StageConds sc, cudaStream_t s)
 {
-    head_kernel<<<1, 1024, 0, s>>>(g, tp, budget, mmax_direct); note_launch();
+    head_kernel<<<1, 1024, 0, s>>>(g, tp, budget, mmax_direct, sc); note_launch();
     return cudaGetLastError();
 }
 
@@ -893,11 +1541,19 @@ static void direct_shape(int mmax, int &ms, int &per_warp, int &wpc)
     while (wpc > 1 && (size_t)wpc * per_warp > 96 * 1024) wpc >>= 1;
 }
 
+static int pow2_floor(int x)
+{
+    int r = 1;
+    while (r * 2 <= x) r *= 2;
+    return r;
+}
+
 cudaError_t launch_ci_direct(GraphDev g, TestParams tp, int mmax, const float *C32,
                              const double *C64, int ldc, cudaStream_t s)
 {
     int ms, per_warp, wpc;
     direct_shape(mmax, ms, per_warp, wpc);
+    wpc = std::min(wpc, pow2_floor(std::max(1, tp.direct_warps)));
     size_t smem = (size_t)wpc * per_warp;
     if (smem > 220 * 1024) return cudaErrorInvalidValue;
     // persistent grid: as many CTAs as can be resident (shared memory bound)
@@ -918,6 +1574,36 @@ cudaError_t launch_ci_direct(GraphDev g, TestParams tp, int mmax, const float *C
     return cudaGetLastError();
 }
 
+template <int LO, int HI>
+static void lane_launch(GraphDev g, TestParams tp, const float *C32, int ldc, ull *queue, ull qcap, ull *qlen,
+                        bool prop, cudaStream_t s)
+{
+    if (prop)
+        ci_lane_kernel<LO, HI, true><<<num_sms() * tp.lane_blocks, 256, 0, s>>>(g, tp, C32, ldc, queue, qcap, qlen);
+    else
+        ci_lane_kernel<LO, HI, false><<<num_sms() * tp.lane_blocks, 256, 0, s>>>(g, tp, C32, ldc, queue, qcap, qlen);
+    note_launch();
+}
+
+cudaError_t launch_ci_lane(GraphDev g, TestParams tp, const float *C32, const double *C64, int ldc,
+                           unsigned long long *queue, unsigned long long qcap, unsigned long long *qlen,
+                           int range, bool prop, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(qlen, 0, sizeof(ull), s);
+    if (e != cudaSuccess) return e;
+    if (range < 0 || range == 0) lane_launch<0, 2>(g, tp, C32, ldc, queue, qcap, qlen, prop, s);
+    if (range < 0 || range == 1) lane_launch<3, 4>(g, tp, C32, ldc, queue, qcap, qlen, prop, s);
+    if (range < 0 || range == 2) lane_launch<5, 6>(g, tp, C32, ldc, queue, qcap, qlen, prop, s);
+    if (range < 0 || range == 3) lane_launch<7, 8>(g, tp, C32, ldc, queue, qcap, qlen, prop, s);
+    int ms, per_warp, wpc;
+    direct_shape(LANE_LMAX + 2, ms, per_warp, wpc);
+    size_t smem = (size_t)wpc * per_warp;
+    e = cudaFuncSetAttribute(ci_redecide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    ci_redecide_kernel<<<num_sms() * 4, wpc * 32, smem, s>>>(g, tp, C64, ldc, queue, qlen, qcap, ms, per_warp); note_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_ci_complement(GraphDev g, TestParams tp, cudaStream_t s)
 {
     ci_complement_kernel<<<num_sms() * 2, 128, 0, s>>>(g, tp); note_launch();
@@ -926,12 +1612,17 @@ cudaError_t launch_ci_complement(GraphDev g, TestParams tp, cudaStream_t s)
 
 cudaError_t launch_prec_update(GraphDev g, const double *C64, int ldc, cudaStream_t s)
 {
-    int mmax = std::min(g.p + 1, PREC_MAX);
-    size_t smem = ((size_t)mmax * mmax + (size_t)mmax) * sizeof(double);
+    const int mmax = std::min(g.p + 1, PREC_MAX);
+    const int rows = (mmax + PREC_CHUNKS - 1) / PREC_CHUNKS;
+    const size_t build = ((size_t)mmax * mmax + (size_t)mmax) * sizeof(double);
+    const size_t down = ((size_t)PREC_RMAX * PREC_RMAX + (size_t)PREC_RMAX * mmax + (size_t)rows * PREC_RMAX +
+                         PREC_RMAX) * sizeof(double);
+    const size_t smem = std::max(build, down);
     cudaError_t e = cudaFuncSetAttribute(prec_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    prec_update_kernel<<<g.p, 512, smem, s>>>(g, C64, ldc); note_launch();
+    prec_update_kernel<<<dim3(g.p, PREC_CHUNKS), 512, smem, s>>>(g, C64, ldc); note_launch();
+    prec_mark_kernel<<<g.p, 128, 0, s>>>(g); note_launch();
     return cudaGetLastError();
 }
 
@@ -959,7 +1650,8 @@ cudaError_t launch_reverify(GraphDev g, TestParams tp, const double *C64, int ld
 
 cudaError_t launch_ci_list(const int *ij, const int *S, int l, long long b, const float *C32,
                            const double *C64, int ldc, int p, TestParams tp, double *r_out,
-                           uint8_t *indep_out, float *z_out, DevCounters *ctr, cudaStream_t s)
+                           uint8_t *indep_out, float *z_out, DevCounters *ctr, const int *blk_lo,
+                           const int *blk_hi, cudaStream_t s)
 {
     int ms, per_warp, wpc;
     direct_shape(l + 2, ms, per_warp, wpc);
@@ -974,13 +1666,13 @@ cudaError_t launch_ci_list(const int *ij, const int *S, int l, long long b, cons
                                  (int)smem);
         if (e != cudaSuccess) return e;
         ci_list_kernel<true><<<blocks, wpc * 32, smem, s>>>(ij, S, l, b, C32, C64, ldc, p, tp, r_out,
-                                                           indep_out, z_out, ctr, ms, per_warp); note_launch();
+                                                           indep_out, z_out, ctr, blk_lo, blk_hi, ms, per_warp); note_launch();
     } else {
         e = cudaFuncSetAttribute(ci_list_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e != cudaSuccess) return e;
         ci_list_kernel<false><<<blocks, wpc * 32, smem, s>>>(ij, S, l, b, C32, C64, ldc, p, tp, r_out,
-                                                            indep_out, z_out, ctr, ms, per_warp); note_launch();
+                                                            indep_out, z_out, ctr, blk_lo, blk_hi, ms, per_warp); note_launch();
     }
     return cudaGetLastError();
 }

@@ -96,6 +96,8 @@ struct MlpRows {
     const float *C32;
     int ldc;
     float sqn_over_q;
+    const long long *nvec;   // batched problems: per-node samples (sqrt(n_u)/q per row)
+    float inv_q;
 };
 
 __device__ __forceinline__ void row_features(const MlpRows &R, const GraphDev &g, long long row, float *f)
@@ -112,7 +114,8 @@ __device__ __forceinline__ void row_features(const MlpRows &R, const GraphDev &g
     const int j = (int)(w / d), x = (int)(w - (long long)j * d);
     const int v = g.nbr[(long long)u * p + j];
     const int k = g.nbr[(long long)u * p + x + (x >= j)];
-    member_features(R.C32, R.ldc, u, v, k, l, d, R.sqn_over_q, f);
+    const float sq = R.nvec ? sqrtf((float)R.nvec[u]) * R.inv_q : R.sqn_over_q;
+    member_features(R.C32, R.ldc, u, v, k, l, d, sq, f);
 }
 
 // Forward pass over rows [0, R): scores s, and for training h1 (BF16), h2 (FP32).
@@ -130,6 +133,9 @@ __global__ void __launch_bounds__(128, 1) mlp_forward_kernel(MlpRows rows, Graph
     __shared__ long long nrows;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (!rows.feats && (g.info->done || g.info->halt)) return;
+    // a stage without proposal rows (or a CTA past the last tile) leaves before
+    // loading the weights and allocating tensor memory
+    if (!rows.feats && (long long)blockIdx.x * T_ROWS >= (long long)rows.row_off[g.p]) return;
     if (tid == 0) {
         mbar_init(&bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -370,6 +376,7 @@ __global__ void adam_kernel(float *theta, const float *grad, float *m, float *v,
 __global__ void perm_kernel(GraphDev g, const unsigned long long *row_off, const float *scores, short *perm)
 {
     if (g.info->done || g.info->halt) return;
+    if (row_off[g.p] == 0) return;                     // this stage runs in plain order
     const int p = g.p;
     const long long npairs = g.info->n_opairs;
     const int lane = threadIdx.x & 31;
@@ -428,7 +435,7 @@ cudaError_t launch_mlp_forward_feats(const float *feats, long long R, const uint
 }
 
 cudaError_t launch_mlp_score_stage(GraphDev g, const unsigned long long *row_off, long long rows_cap,
-                                   const float *C32, int ldc, float sqn_over_q, const uint8_t *wpack,
+                                   const float *C32, int ldc, float sqn_over_q, float inv_q, const uint8_t *wpack,
                                    const float *theta, float *scores, short *perm, int *err, cudaStream_t s)
 {
     MlpRows rows{};
@@ -437,6 +444,8 @@ cudaError_t launch_mlp_score_stage(GraphDev g, const unsigned long long *row_off
     rows.C32 = C32;
     rows.ldc = ldc;
     rows.sqn_over_q = sqn_over_q;
+    rows.nvec = g.nvec;
+    rows.inv_q = inv_q;
     cudaError_t e = cudaFuncSetAttribute(mlp_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, MLP_SMEM);
     if (e != cudaSuccess) return e;
     mlp_forward_kernel<<<mlp_ctas(rows_cap), 128, MLP_SMEM, s>>>(rows, g, wpack, theta, scores, nullptr, nullptr, err);
@@ -474,7 +483,7 @@ cudaError_t launch_adam(float *theta, const float *grad, float *m, float *v, flo
 // Member features for explicit quadruples (u, v, k, l | d << 16): candidate k
 // of the ordered pair (u, v) at stage l with candidate-set size d.
 __global__ void mlp_features_kernel(const int *quads, long long R, const float *C32, int ldc, int p, long long n,
-                                    float inv_q, float *feats, int *err)
+                                    const long long *nvec, float inv_q, float *feats, int *err)
 {
     const long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (r >= R) return;
@@ -485,15 +494,15 @@ __global__ void mlp_features_kernel(const int *quads, long long R, const float *
         return;
     }
     float f[NF];
-    member_features(C32, ldc, u, v, k, l, d, sqrtf((float)n) * inv_q, f);
+    member_features(C32, ldc, u, v, k, l, d, sqrtf((float)(nvec ? nvec[u] : n)) * inv_q, f);
     for (int i = 0; i < NF; ++i) feats[r * NF + i] = f[i];
 }
 
 cudaError_t launch_mlp_features(const int *quads, long long R, const float *C32, int ldc, int p, long long n,
-                                double q, float *feats, int *err, cudaStream_t s)
+                                const long long *nvec, double q, float *feats, int *err, cudaStream_t s)
 {
-    mlp_features_kernel<<<(unsigned)((R + 255) / 256), 256, 0, s>>>(quads, R, C32, ldc, p, n, (float)(1.0 / q),
-                                                                      feats, err);
+    mlp_features_kernel<<<(unsigned)((R + 255) / 256), 256, 0, s>>>(quads, R, C32, ldc, p, n, nvec,
+                                                                      (float)(1.0 / q), feats, err);
     note_launch();
     return cudaGetLastError();
 }

@@ -85,6 +85,12 @@ def load():
         "pc_kernel_launches": (i64, []),
         "pc_timing": (i32, [vp, vp, vp, i32]),
         "pc_corr_noalloc": (i32, [vp, i32, i64, i32, i64, vp, i64, vp]),
+        "pc_skeleton_many": (i32, [ctypes.POINTER(vp), i32, ctypes.POINTER(vp), ctypes.POINTER(pc_stats),
+                                   ctypes.POINTER(i32)]),
+        "pc_autotune": (i32, [vp, i32, ctypes.POINTER(pc_tune_result)]),
+        "pc_create_batch": (i32, [i32, vp, vp, dbl, i32, ctypes.POINTER(vp)]),
+        "pc_corr_block": (i32, [vp, i32, vp, i32, i64]),
+        "pc_batch_layout": (i32, [vp, ctypes.POINTER(i32), vp]),
         "pc_mlp_nparam": (i32, []),
         "pc_mlp_set_params": (i32, [vp, vp, i64]),
         "pc_mlp_get_params": (i32, [vp, vp, i64]),
@@ -147,6 +153,44 @@ def pc_set_stream(h, stream):
     _check(h, load().pc_set_stream(h, ctypes.c_void_p(raw)))
 
 
+def _x_args(X):
+    if isinstance(X, np.ndarray):
+        X = np.ascontiguousarray(X)
+        assert X.dtype in (np.float32, np.float64)
+        return X, (PC_F64 if X.dtype == np.float64 else PC_F32), X.shape[1]
+    import torch
+    assert X.dtype in (torch.float32, torch.float64) and X.stride(1) == 1
+    return X, (PC_F64 if X.dtype == torch.float64 else PC_F32), X.stride(0)
+
+
+def pc_create_batch(ns, ps, alpha: float, max_level: int = -1):
+    """Batched handle over len(ns) independent problems (instance i: ns[i] x ps[i])."""
+    k = len(ns)
+    n_arr = np.ascontiguousarray(ns, dtype=np.int64)
+    p_arr = np.ascontiguousarray(ps, dtype=np.int32)
+    h = ctypes.c_void_p()
+    st = load().pc_create_batch(k, n_arr.ctypes.data, p_arr.ctypes.data, float(alpha), int(max_level),
+                                ctypes.byref(h))
+    if st != 0:
+        raise PCError(st, "pc_create_batch failed")
+    return h
+
+
+def pc_corr_block(h, i: int, X):
+    """Instance i's data (n_i x p_i row-major, numpy host or torch CUDA tensor)."""
+    X, dt, ld = _x_args(X)
+    _check(h, load().pc_corr_block(h, int(i), ctypes.c_void_p(_ptr(X)), dt, int(ld)))
+
+
+def pc_batch_layout(h):
+    """First global node id of every instance plus the total (list of k + 1 ints)."""
+    k = ctypes.c_int32()
+    _check(h, load().pc_batch_layout(h, ctypes.byref(k), None))
+    off = np.empty(k.value + 1, dtype=np.int32)
+    _check(h, load().pc_batch_layout(h, ctypes.byref(k), off.ctypes.data))
+    return [int(x) for x in off]
+
+
 def pc_corr(h, X):
     """X: n x p row-major (torch CUDA tensor or numpy host array), float32 or float64."""
     if isinstance(X, np.ndarray):
@@ -175,6 +219,35 @@ def pc_skeleton(h, p: int, adj_out=None):
     adj = adj_out if adj_out is not None else np.empty((p, p), dtype=np.uint8)
     _check(h, load().pc_skeleton(h, ctypes.c_void_p(_ptr(adj)), ctypes.byref(st)))
     return adj, st.as_dict()
+
+
+def pc_skeleton_many(handles, ps):
+    """Concurrent searches of independent problems: handles (list of c_void_p, each
+    after pc_corr, ideally each on its own stream), ps their p.  Returns
+    (list of adjacency arrays or None, list of stats dicts, list of status codes)."""
+    k = len(handles)
+    H = (ctypes.c_void_p * k)(*[h.value for h in handles])
+    adjs = [np.empty((p, p), dtype=np.uint8) for p in ps]
+    A = (ctypes.c_void_p * k)(*[a.ctypes.data for a in adjs])
+    S = (pc_stats * k)()
+    st = (ctypes.c_int32 * k)()
+    load().pc_skeleton_many(H, k, A, S, st)
+    status = [int(x) for x in st]
+    return [a if s_ == 0 else None for a, s_ in zip(adjs, status)], [x.as_dict() for x in S], status
+
+
+class pc_tune_result(ctypes.Structure):
+    _fields_ = [("lane_chunk", ctypes.c_int32), ("lane_rounds", ctypes.c_int32),
+                ("lane_blocks", ctypes.c_int32), ("direct_warps", ctypes.c_int32),
+                ("ms_default", ctypes.c_double), ("ms_best", ctypes.c_double), ("runs", ctypes.c_int32)]
+
+
+def pc_autotune(h, reps: int = 3) -> dict:
+    """Launch-shape search of the test kernels (pc_autotune); returns the chosen
+    shape and the mean skeleton times before and after."""
+    r = pc_tune_result()
+    _check(h, load().pc_autotune(h, int(reps), ctypes.byref(r)))
+    return {k: getattr(r, k) for k, _ in pc_tune_result._fields_}
 
 
 def pc_last_stats(h) -> dict:
@@ -363,3 +436,36 @@ class PC:
             self.close()
         except Exception:
             pass
+
+
+class PCBatch(PC):
+    """Batched handle over independent problems (pc_create_batch): instance i has
+    ns[i] samples of ps[i] variables; give its data with corr_block(i, X)."""
+
+    def __init__(self, ns, ps, alpha: float, max_level: int = -1, **opts):
+        self.h = pc_create_batch(ns, ps, alpha, max_level)
+        self.ns, self.ps = list(ns), list(ps)
+        self.n, self.p = max(ns), int(sum(ps))
+        self.offsets = pc_batch_layout(self.h)
+        for k, v in opts.items():
+            pc_set_opt(self.h, k, v)
+
+    def corr(self, X):
+        raise PCError(4, "a batched handle takes its data per instance: corr_block(i, X)")
+
+    def corr_block(self, i, X):
+        pc_corr_block(self.h, i, X)
+        return self
+
+    def split(self, adj, sepsets=None):
+        """Per-instance adjacency blocks and sepsets (local node ids)."""
+        o = self.offsets
+        adjs = [adj[o[i]:o[i + 1], o[i]:o[i + 1]] for i in range(len(self.ps))]
+        if sepsets is None:
+            return adjs
+        seps = [dict() for _ in self.ps]
+        import bisect
+        for (a, b), (lv, side, rank, nodes) in sepsets.items():
+            i = bisect.bisect_right(o, a) - 1
+            seps[i][(a - o[i], b - o[i])] = (lv, side, rank, tuple(x - o[i] for x in nodes))
+        return adjs, seps

@@ -296,3 +296,36 @@ def test_levels_run_and_first_level_match_schedule(fp):
         assert st["levels_run"] == len(R["levels"])
         lv = R["levels"][1:] if order else R["levels"]
         assert st["first_level"] == lv[0]
+
+
+def test_skeleton_many_concurrent_matches_oracle(fp):
+    """pc_skeleton_many: independent problems on their own streams, each identical
+    to the oracle; a problem over its test budget fails alone."""
+    cases = [(101, 40, 2000, 0.3, 1), (102, 73, 5000, 0.25, 1), (103, 25, 800, 0.5, 0),
+             (104, 96, 3000, 0.08, 0), (105, 57, 9000, 0.2, 1), (106, 31, 1200, 0.35, 1)]
+    pcs, ps, refs, streams = [], [], [], []
+    for seed, p, n, prob, order in cases:
+        X = _sem_case(seed, p, n, prob)
+        C = oracle.pearson(X)
+        refs.append(oracle.skeleton(C, n, 0.01, -1, reversed_order=bool(order)))
+        pc = fp.PC(n, p, 0.01, -1, order=order)
+        s = torch.cuda.Stream()
+        fp.pc_set_stream(pc.h, s)
+        pc.corr(torch.from_numpy(X).cuda())
+        pcs.append(pc)
+        ps.append(p)
+        streams.append(s)
+    # one extra problem whose first stage exceeds its budget
+    Xb = _sem_case(107, 60, 3000, 0.3)
+    pcb = fp.PC(3000, 60, 0.01, -1, order=0, budget=10)
+    fp.pc_set_stream(pcb.h, torch.cuda.Stream())
+    pcb.corr(torch.from_numpy(Xb).cuda())
+    adjs, stats, status = fp.pc_skeleton_many([pc.h for pc in pcs] + [pcb.h], ps + [60])
+    assert status[-1] == 6 and adjs[-1] is None
+    for pc, adj, st, code, R in zip(pcs, adjs, stats, status, refs):
+        assert code == 0
+        np.testing.assert_array_equal(adj, R["adj"])
+        assert pc.sepsets() == R["sepsets"]
+        assert st["tests_canonical"] == R["tests_total"]
+    for pc in pcs + [pcb]:
+        pc.close()
