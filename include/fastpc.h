@@ -92,6 +92,8 @@ void pc_destroy(pc_handle *h);
  *                 stage loop is then driven from the host, one launch per kernel
  *   "graph"       1 = run the stage loop as one CUDA graph whose conditional
  *                 WHILE node is driven by the device (default); 0 = host loop
+ *   "stage_conds" 1 = inside that graph, conditional nodes skip the kernels a
+ *                 stage has no work for (default); 0 = every kernel every stage
  *   "learned"     1 = enumerate the conditioning sets of every ordered pair in
  *                 the order proposed by the scoring network (needs parameters:
  *                 pc_mlp_set_params or pc_mlp_train); 0 = lexicographic (default)

@@ -48,6 +48,7 @@ struct pc_handle {
     long long n_min = 0;
     // launch shape of the test kernels (pc_autotune)
     int lane_chunk = 8, lane_rounds = 32, lane_blocks = 8, direct_warps = 8;
+    int stage_conds = 1;                 // conditional nodes in the captured stage body
     cudaStream_t stream = 0;
     std::string err;
     // correlation
@@ -487,6 +488,8 @@ extern "C" pc_status pc_set_opt(pc_handle *h, const char *key, double val)
     else if (k == "budget") {
         if (!(val > 0)) return fail(h, PC_ERR_ARG, "budget must be > 0");
         h->budget = val;
+    } else if (k == "stage_conds") {
+        h->stage_conds = val != 0;
     } else if (k == "lane_chunk") {
         if (!(val >= 1 && val <= 256)) return fail(h, PC_ERR_ARG, "lane_chunk must be in [1, 256]");
         h->lane_chunk = (int)val;
@@ -519,6 +522,7 @@ extern "C" pc_status pc_get_opt(pc_handle *h, const char *key, double *val)
     else if (k == "learned_rows") *val = (double)h->rows_cap;
     else if (k == "learned_min_tests") *val = h->learned_min;
     else if (k == "budget") *val = h->budget;
+    else if (k == "stage_conds") *val = h->stage_conds;
     else if (k == "lane_chunk") *val = h->lane_chunk;
     else if (k == "lane_rounds") *val = h->lane_rounds;
     else if (k == "lane_blocks") *val = h->lane_blocks;
@@ -831,7 +835,8 @@ static pc_status enqueue_level(pc_handle *h, cudaStream_t s, int mmax, bool use_
     const bool use_prec = h->order == 1 && h->complement;
     auto T = [&](int cls) { return Timed(h, timed ? cls : -1); };
     fpc::StageConds sc = {};
-    if (use_cond) {
+    const bool conds = use_cond && h->stage_conds;
+    if (conds) {
         cudaStreamCaptureStatus cst;
         cudaGraph_t cg = nullptr;
         CK(cudaStreamGetCaptureInfo(s, &cst, nullptr, &cg, nullptr, nullptr, nullptr));
@@ -875,7 +880,7 @@ static pc_status enqueue_level(pc_handle *h, cudaStream_t s, int mmax, bool use_
         CK(fpc::launch_prec_update(g, h->C64, h->ldc, st));
         return PC_OK;
     };
-    if (use_cond) {
+    if (conds) {
         if (sc.has_score)
             if (pc_status r = cond_node(h, s, sc.score, cudaGraphCondTypeIf, 1, score)) return r;
         if (pc_status r = cond_node(h, s, sc.lane, cudaGraphCondTypeSwitch, fpc::LANE_RANGES, lane)) return r;
@@ -889,11 +894,19 @@ static pc_status enqueue_level(pc_handle *h, cudaStream_t s, int mmax, bool use_
         }
         {
             auto t = T(3);
-            const int l = h->info_h->l;
-            if (h->precision != 0 && l >= 0 && l <= fpc::LANE_LMAX) {
-                if (pc_status r = lane(fpc::lane_range_of(l), s)) return r;
-            } else {
+            if (use_cond) {
+                // captured without conditional nodes: every kernel, each returns at once
+                // when the stage is not its own
+                if (h->precision != 0)
+                    if (pc_status r = lane(-1, s)) return r;
                 if (pc_status r = direct(0, s)) return r;
+            } else {
+                const int l = h->info_h->l;
+                if (h->precision != 0 && l >= 0 && l <= fpc::LANE_LMAX) {
+                    if (pc_status r = lane(fpc::lane_range_of(l), s)) return r;
+                } else {
+                    if (pc_status r = direct(0, s)) return r;
+                }
             }
         }
         if (use_prec) {
@@ -908,7 +921,7 @@ static pc_status enqueue_level(pc_handle *h, cudaStream_t s, int mmax, bool use_
         CK(fpc::launch_tail(g, tp, level_cap(h), 0, h->singular, 0, h->hcond, use_cond ? 1 : 0, sc, s));
     }
     if (use_prec) {
-        if (use_cond) {
+        if (conds) {
             if (pc_status r = cond_node(h, s, sc.prec, cudaGraphCondTypeIf, 1, prec)) return r;
         } else {
             auto t = T(2);
@@ -924,7 +937,7 @@ static std::vector<double> graph_key(const pc_handle *h)
             (double)h->used_tc, (double)h->c64_full, (double)h->learned, (double)(uintptr_t)h->perm, (double)h->rows_cap, h->learned_min, (double)(uintptr_t)h->rq,
             h->budget, (double)level_cap(h), (double)(uintptr_t)h->g.pool, (double)h->g.pool_cap,
             (double)(uintptr_t)h->C32, (double)(uintptr_t)h->C64, (double)h->lane_chunk,
-            (double)h->lane_rounds, (double)h->lane_blocks, (double)h->direct_warps};
+            (double)h->lane_rounds, (double)h->lane_blocks, (double)h->direct_warps, (double)h->stage_conds};
 }
 
 static void drop_graph(pc_handle *h)
@@ -1135,7 +1148,8 @@ static pc_status skeleton_complete(pc_handle *h, pc_stats *st, bool *overflow)
     const DevCounters &c = *h->ctr_h;
     const LevelInfo &I = *h->info_h;
     // the captured body counts the kernels its conditional nodes actually ran
-    if (graph) g_launches.fetch_add((long long)I.kernels_run);
+    if (graph && h->stage_conds) g_launches.fetch_add((long long)I.kernels_run);
+    else if (graph) g_launches.fetch_add((long long)I.body_runs * h->body_kernels);
     if (c.status)
         return fail(h, (pc_status)c.status,
                     h->learned ? "device-side error during the skeleton search (or a proposed sepset failed the FP64 re-verification)"

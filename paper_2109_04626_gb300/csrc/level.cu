@@ -236,11 +236,8 @@ __device__ __forceinline__ ull sat_mul(ull a, ull b)
     return a * b;
 }
 
-// Work of stage l per node u: every ordered pair (u, v) has C(d, l) tests,
-// d = |adj(u)| - 1, all on the direct path or all on the complement path.
-// One CTA scans the per-node totals into tn_off / cn_off and gates the stage:
-// budget and saturation (PC_ERR_BUDGET), or direct tests at an l larger than
-// the direct kernel's shared-memory layout (the host runs that stage).
+// The stage body's conditional nodes (captured loop): which small-stage kernel
+// range runs, and whether the warp-per-test, complement and scoring kernels do.
 __device__ __forceinline__ void set_stage_conds(const StageConds &sc, LevelInfo *I, int lane, int direct, int comp,
                                                 int score)
 {
@@ -253,6 +250,55 @@ __device__ __forceinline__ void set_stage_conds(const StageConds &sc, LevelInfo 
     I->kernels_run += STAGE_FIXED_KERNELS - 1 + (lane < LANE_RANGES ? 3 : 0) + direct + comp + 2 * score;
 }
 
+// Exclusive saturating scan of NV values per thread over a block of up to 1024
+// threads (warp shuffles, then one warp over the warp totals): ex[] receives the
+// thread's exclusive prefixes, tot[] the block totals.  sh: 32*NV scratch.
+template <int NV>
+__device__ __forceinline__ void block_scan_sat(const ull (&v)[NV], ull (&ex)[NV], ull (&tot)[NV], ull *sh)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    ull inc[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        inc[k] = v[k];
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const ull y = __shfl_up_sync(0xffffffffu, inc[k], off);
+            if (lane >= off) inc[k] = sat_add(inc[k], y);
+        }
+        if (lane == 31) sh[k * 32 + w] = inc[k];
+    }
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            ull x = lane < nw ? sh[k * 32 + lane] : 0ull;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const ull y = __shfl_up_sync(0xffffffffu, x, off);
+                if (lane >= off) x = sat_add(x, y);
+            }
+            sh[k * 32 + lane] = x;                        // inclusive over warps
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        const ull wex = __shfl_up_sync(0xffffffffu, inc[k], 1);
+        const ull base = w ? sh[k * 32 + w - 1] : 0ull;
+        ex[k] = sat_add(base, lane ? wex : 0ull);
+        tot[k] = sh[k * 32 + nw - 1];
+    }
+    __syncthreads();                                      // sh reusable
+}
+
+// Work of stage l per node u: every ordered pair (u, v) has C(d, l) tests,
+// d = |adj(u)| - 1, all on the direct path or all on the complement path.
+// One CTA scans the per-node totals into tn_off / cn_off and gates the stage:
+// budget and saturation (PC_ERR_BUDGET), or direct tests at an l larger than
+// the direct kernel's shared-memory layout (the host runs that stage).  In the
+// stages of the small-stage kernel it also lays out its rank-major rounds.
+constexpr int HEAD_PER_MAX = MAXP_BATCH / 1024;           // nodes per thread at most
 __global__ void __launch_bounds__(1024) head_kernel(GraphDev g, TestParams tp, double budget,
                                                     int mmax_direct, StageConds conds)
 {
@@ -261,111 +307,90 @@ __global__ void __launch_bounds__(1024) head_kernel(GraphDev g, TestParams tp, d
         if (conds.use && threadIdx.x == 0) set_stage_conds(conds, I, LANE_RANGES, 0, 0, 0);
         return;
     }
-    __shared__ ull pd[1024], pc[1024], pr[1024];
-    __shared__ int ssat;
+    __shared__ ull sh[4 * 32];
     const int p = g.p, l = I->l, t = threadIdx.x;
-    if (t == 0) ssat = 0;
-    __syncthreads();
     const int per = (p + 1023) / 1024;
     const int s0 = min(p, t * per), s1 = min(p, s0 + per);
+    // tests per pair of each of this thread's nodes; 0 for complement-path nodes' direct count
+    ull Tn[HEAD_PER_MAX];
+    bool cm[HEAD_PER_MAX];
     // proposal rows: a node whose pairs have at least two sets to order gets
     // deg*(deg-1) score rows (pair j, candidate position x)
     auto prows = [&](int dg, ull T) -> ull { return (g.row_off && l >= 1 && T >= 2) ? (ull)dg * (ull)(dg - 1) : 0ull; };
-    ull sd = 0, sc = 0, sr = 0;
+    ull v[3] = {0ull, 0ull, 0ull}, mxT = 0;               // direct, complement, proposal rows
+    bool sat = false;
     for (int u = s0; u < s1; ++u) {
         const int dg = g.deg[u], d = dg - 1;
         const ull T = (dg > 0 && d >= l && dof_ok(tp, u, l)) ? g.binom[(long long)d * g.ldb + l] : 0ull;
         const ull tot = sat_mul(T, (ull)dg);
-        if (tot == KEY_NONE) ssat = 1;
+        sat |= tot == KEY_NONE;
         const bool comp = T && comp_eligible(d, l, tp) && g.prec_m[u] > 0;
-        if (comp) sc = sat_add(sc, tot);
-        else sd = sat_add(sd, tot);
-        sr += prows(dg, T);
+        Tn[u - s0] = T;
+        cm[u - s0] = comp;
+        if (comp) v[1] = sat_add(v[1], tot);
+        else {
+            v[0] = sat_add(v[0], tot);
+            mxT = T > mxT ? T : mxT;
+        }
+        v[2] = sat_add(v[2], prows(dg, T));
     }
-    pd[t] = sd;
-    pc[t] = sc;
-    pr[t] = sr;
-    __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-        ull a = t >= off ? pd[t - off] : 0ull, b = t >= off ? pc[t - off] : 0ull;
-        ull c = t >= off ? pr[t - off] : 0ull;
-        __syncthreads();
-        pd[t] = sat_add(pd[t], a);
-        pc[t] = sat_add(pc[t], b);
-        pr[t] += c;
-        __syncthreads();
-    }
-    ull rd = t ? pd[t - 1] : 0ull, rc = t ? pc[t - 1] : 0ull, rr = t ? pr[t - 1] : 0ull;
+    const int ssat = __syncthreads_or(sat);
+    ull ex[3], tot[3];
+    block_scan_sat<3>(v, ex, tot, sh);
     // else: plain order this stage (too many rows, or too few tests for the order to matter)
-    const bool rows_fit = pr[1023] <= (ull)g.rows_cap && (double)pd[1023] + (double)pc[1023] >= tp.learned_min;
-    const ull rows_total = pr[1023];
+    const bool rows_fit = tot[2] <= (ull)g.rows_cap && (double)tot[0] + (double)tot[1] >= tp.learned_min;
+    const ull rows_total = tot[2];
     if (t == 0 && g.scored) g.scored[l] = rows_fit && rows_total > 0;
-    for (int u = s0; u < s1; ++u) {
-        const int dg = g.deg[u], d = dg - 1;
-        const ull T = (dg > 0 && d >= l && dof_ok(tp, u, l)) ? g.binom[(long long)d * g.ldb + l] : 0ull;
-        const ull tot = sat_mul(T, (ull)dg);
-        const bool comp = T && comp_eligible(d, l, tp) && g.prec_m[u] > 0;
-        g.tn_off[u] = rd;
-        g.cn_off[u] = rc;
-        if (g.row_off) g.row_off[u] = rows_fit ? rr : 0ull;
-        if (comp) rc = sat_add(rc, tot);
-        else rd = sat_add(rd, tot);
-        rr += prows(dg, T);
-    }
-    __syncthreads();
-    // rank-major rounds of the lane kernel: at most tp.lane_rounds chunks of every
-    // direct pair, the rest in the pair-major remainder space rn_off
     {
-        ull mx = 0;
+        ull rd = ex[0], rc = ex[1], rr = ex[2];
         for (int u = s0; u < s1; ++u) {
-            const int dg = g.deg[u], d = dg - 1;
-            const ull T = (dg > 0 && d >= l && dof_ok(tp, u, l)) ? g.binom[(long long)d * g.ldb + l] : 0ull;
-            const bool comp = T && comp_eligible(d, l, tp) && g.prec_m[u] > 0;
-            if (!comp && T > mx) mx = T;
+            const int dg = g.deg[u];
+            const ull T = Tn[u - s0], tt = sat_mul(T, (ull)dg);
+            g.tn_off[u] = rd;
+            g.cn_off[u] = rc;
+            if (g.row_off) g.row_off[u] = rows_fit ? rr : 0ull;
+            if (cm[u - s0]) rc = sat_add(rc, tt);
+            else rd = sat_add(rd, tt);
+            rr = sat_add(rr, prows(dg, T));
         }
-        pr[t] = mx;
+    }
+    const bool small = tp.precision != 0 && l <= LANE_LMAX;
+    int rounds = 0;
+    if (small && tot[0] > 0) {
+        // rank-major rounds of the lane kernel: at most tp.lane_rounds chunks of
+        // every direct pair, the rest in the pair-major remainder space rn_off
+        for (int off = 16; off > 0; off >>= 1) {
+            const ull y = __shfl_xor_sync(0xffffffffu, mxT, off);
+            mxT = y > mxT ? y : mxT;
+        }
+        if ((t & 31) == 0) sh[t >> 5] = mxT;
         __syncthreads();
-        for (int off = 512; off > 0; off >>= 1) {
-            if (t < off) pr[t] = pr[t] > pr[t + off] ? pr[t] : pr[t + off];
-            __syncthreads();
-        }
-        const ull maxT = pr[0];
+        ull maxT = 0;
+        for (int i = 0; i < 32; ++i) maxT = sh[i] > maxT && i < ((int)blockDim.x >> 5) ? sh[i] : maxT;
         __syncthreads();
         const ull chunk = (ull)tp.lane_chunk;
-        const int rounds = (int)(maxT == 0 ? 0 : min((ull)tp.lane_rounds, (maxT + chunk - 1) / chunk));
+        rounds = (int)(maxT == 0 ? 0 : min((ull)tp.lane_rounds, (maxT + chunk - 1) / chunk));
         const ull skip = (ull)rounds * chunk;
-        ull sr2 = 0;
+        ull v2[1] = {0ull};
         for (int u = s0; u < s1; ++u) {
-            const int dg = g.deg[u], d = dg - 1;
-            const ull T = (dg > 0 && d >= l && dof_ok(tp, u, l)) ? g.binom[(long long)d * g.ldb + l] : 0ull;
-            const bool comp = T && comp_eligible(d, l, tp) && g.prec_m[u] > 0;
-            if (!comp && T > skip) sr2 = sat_add(sr2, sat_mul(T - skip, (ull)dg));
+            const ull T = Tn[u - s0];
+            if (!cm[u - s0] && T > skip) v2[0] = sat_add(v2[0], sat_mul(T - skip, (ull)g.deg[u]));
         }
-        pr[t] = sr2;
-        __syncthreads();
-        for (int off = 1; off < 1024; off <<= 1) {
-            ull c = t >= off ? pr[t - off] : 0ull;
-            __syncthreads();
-            pr[t] = sat_add(pr[t], c);
-            __syncthreads();
-        }
-        ull rr2 = t ? pr[t - 1] : 0ull;
+        ull ex2[1], tot2[1];
+        block_scan_sat<1>(v2, ex2, tot2, sh);
+        ull rr2 = ex2[0];
         for (int u = s0; u < s1; ++u) {
-            const int dg = g.deg[u], d = dg - 1;
-            const ull T = (dg > 0 && d >= l && dof_ok(tp, u, l)) ? g.binom[(long long)d * g.ldb + l] : 0ull;
-            const bool comp = T && comp_eligible(d, l, tp) && g.prec_m[u] > 0;
+            const ull T = Tn[u - s0];
             g.rn_off[u] = rr2;
-            if (!comp && T > skip) rr2 = sat_add(rr2, sat_mul(T - skip, (ull)dg));
+            if (!cm[u - s0] && T > skip) rr2 = sat_add(rr2, sat_mul(T - skip, (ull)g.deg[u]));
         }
-        if (t == 1023) g.rn_off[p] = pr[1023];
-        if (t == 0) {
-            I->lane_rounds = rounds;
-            I->lane_overflow = 0;
-        }
+        if (t == 0) g.rn_off[p] = tot2[0];
     }
     __syncthreads();
     if (t == 0) {
-        const ull td = pd[1023], tc = pc[1023];
+        I->lane_rounds = rounds;
+        I->lane_overflow = 0;
+        const ull td = tot[0], tc = tot[1];
         g.tn_off[p] = td;
         g.cn_off[p] = tc;
         if (g.row_off) g.row_off[p] = rows_fit ? rows_total : 0ull;
@@ -381,7 +406,6 @@ __global__ void __launch_bounds__(1024) head_kernel(GraphDev g, TestParams tp, d
         }
         if (conds.use) {
             const bool run = !I->halt;
-            const bool small = tp.precision != 0 && l <= LANE_LMAX;
             set_stage_conds(conds, I, run && small && td > 0 ? lane_range_of_dev(l) : LANE_RANGES,
                             run && td > 0 && !small, run && tc > 0,
                             run && g.row_off && rows_fit && rows_total > 0);
