@@ -36,6 +36,12 @@ SM_COUNT, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.070
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_GHZ / 1000.0   # 80.5
 
 
+# DRAM bytes (read + write) per launch of a class's dominant kernel, from one
+# ncu capture of the current kernel (profiles/prec_update_p95_dense.md: two
+# launches of prec_update_kernel read 0.345 MB and 0.647 MB, wrote 0)
+DRAM_BYTES_PER_LAUNCH = {("p95_dense", "prec"): 4.96e5}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -43,7 +49,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="p95_dense",
-                    choices=["p20_fp64", "p95_dense", "p500_powerlaw", "p1000_er"])
+                    choices=["p20_fp64", "p95_dense", "p500_powerlaw", "p1000_er", "many64"],
+                    help="many64: 64 independent SEMs (p in [50,400], edge prob in [0.05,0.3], "
+                         "n in [2000,20000]), conventional order")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
@@ -196,15 +204,33 @@ def run_reference(args):
     rank, world, local = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), 0
     if rank != 0:
         return 0
-    s, w = workload(args.workload)
-    X = s.X
+    if args.workload == "many64":
+        # a bounded sample: the 8 smallest of the 64 instances per step
+        from paper_2109_04626_gb300 import sem
+        inst = sorted(sem.make_many(MANY["count"]), key=lambda s_: s_.X.shape[1])[:8]
+        w = {"name": "many64", "p": sum(s_.X.shape[1] for s_ in inst), "n": max(s_.X.shape[0] for s_ in inst),
+             "alpha": MANY["alpha"], "max_level": -1, "order": 0}
+        sample = "the 8 smallest of the 64 instances (Pearson + skeleton) per step"
+        Xs = [s_.X for s_ in inst]
+    else:
+        s, w = workload(args.workload)
+        Xs = [s.X]
+        sample = "full run(s) of the workload"
+
+    def one():
+        dt, nt = 0.0, 0
+        for X in Xs:
+            d_, R = oracle_run(X, w)
+            dt += d_
+            nt += R["tests_total"]
+        return dt, nt
     for _ in range(max(0, min(args.warmup, 1))):
-        oracle_run(X, w)
+        one()
     times, tests = [], 0
     for _ in range(args.steps):
-        dt, R = oracle_run(X, w)
+        dt, nt = one()
         times.append(dt)
-        tests += R["tests_total"]
+        tests += nt
     tot = sum(times)
     import oracle
     val = tests / tot
@@ -216,7 +242,7 @@ def run_reference(args):
                        "max_level": w["max_level"], "order": "reversed" if w["order"] else "conventional",
                        "l2": "inputs on the host; oracle runs on CPU cores"},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-                             "sample": f"{args.steps} full run(s) of the workload"},
+                             "sample": f"{args.steps} step(s): {sample}"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -307,14 +333,18 @@ def run_ours(args):
         from paper_2109_04626_gb300 import proposal, sem as _sem
         t0 = time.perf_counter()
         base = 1000 * w["cfg"] + 100
+        # training SEMs: the workload's recipe at its own size, except p=1000 ER,
+        # whose network is trained on p=200 SEMs of the same expected degree
+        tp_, tn_ = (200, 5000) if w["cfg"] == 4 else (p, n)
 
         def make_X(sd):
             rng = np.random.Generator(np.random.PCG64(base + sd))
             if w["prob"] is None:
-                dag, W_, order_ = _sem.powerlaw_dag(p, rng)
+                dag, W_, order_ = _sem.powerlaw_dag(tp_, rng)
             else:
-                dag, W_, order_ = _sem.er_dag(p, w["prob"], rng)
-            Xs = _sem.sample(W_, order_, n, rng)
+                prob = 10.0 / (tp_ - 1) if w["cfg"] == 4 else w["prob"]
+                dag, W_, order_ = _sem.er_dag(tp_, prob, rng)
+            Xs = _sem.sample(W_, order_, tn_, rng)
             return Xs.astype(np.float32) if w["dtype"] == "float32" else Xs
 
         feats, labels = proposal.collect(make_X, range(args.train_seeds), w["alpha"], w["order"],
@@ -322,6 +352,7 @@ def run_ours(args):
         loss = proposal.train(pc.h, feats, labels, epochs=6, batch=8192, lr=2e-3, seed=1)
         fp.pc_set_opt(pc.h, "learned", 1)
         learned = {"train_rows": int(labels.shape[0]), "train_seeds": args.train_seeds,
+                   "train_sems": f"p={tp_}, n={tn_}",
                    "final_loss": loss, "train_s": time.perf_counter() - t0}
 
     for _ in range(args.warmup):
@@ -381,7 +412,8 @@ def run_ours(args):
         peak = FP32_PEAK_TFLOPS
     achieved = dom_flops / (dom_ms * 1e-3) / 1e12 if dom_ms > 0 else 0.0
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "kernel": dom,
+                "frac": achieved / peak, "traffic": DRAM_BYTES_PER_LAUNCH.get((w["name"], dom)),
+                "kernel": dom,
                 "kernel_ms_per_step": dom_ms, "launch_groups": tim[dom][1],
                 "peak_source": "nominal FP64 1.25 TFLOP/s" if peak == FP64_PEAK_TFLOPS else
                 "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
@@ -460,10 +492,157 @@ def run_ours(args):
     return 0
 
 
+MANY = {"name": "many64", "count": 64, "alpha": 0.01, "max_level": -1, "order": 0, "streams": 16}
+
+
+def run_many(args):
+    """64 independent problems: every handle's pc_corr on its own stream, then all
+    skeleton searches concurrently (pc_skeleton_many); beside it the same problems
+    in one batched handle (pc_create_batch: one launch sequence per stage)."""
+    import torch
+    from paper_2109_04626_gb300 import fastpc as fp, sem
+    rank, world, local = dist_setup(args)
+    fp.load()
+    inst = sem.make_many(MANY["count"])
+    ns = [s_.X.shape[0] for s_ in inst]
+    ps = [s_.X.shape[1] for s_ in inst]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    Xd = [torch.from_numpy(s_.X).to(dev) for s_ in inst]
+    main_s = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    streams = [torch.cuda.Stream() for _ in range(MANY["streams"])]
+    pcs = []
+    for i in range(len(inst)):
+        pc = fp.PC(ns[i], ps[i], MANY["alpha"], MANY["max_level"], order=0, precision=2)
+        fp.pc_set_stream(pc.h, streams[i % len(streams)])
+        pcs.append(pc)
+    hs = [pc.h for pc in pcs]
+
+    def step(Xs, adj=False):
+        ev = torch.cuda.Event()
+        ev.record(main_s)
+        for st in streams:
+            st.wait_event(ev)
+        for i, pc in enumerate(pcs):
+            pc.corr(Xs[i])
+        adjs, stats, status = fp.pc_skeleton_many(hs, ps, adj_out=adj)
+        if any(status):
+            raise RuntimeError(f"pc_skeleton_many: statuses {status}")
+        for st in streams:
+            e2 = torch.cuda.Event()
+            e2.record(st)
+            main_s.wait_event(e2)
+        return adjs, stats
+
+    def timed(fn, k):
+        ms, out = [], None
+        for _ in range(k):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(main_s)
+            out = fn()
+            b.record(main_s)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        return ms, out
+
+    adjs_ref, stats0 = step(Xd, adj=True)
+    tests_unit = sum(x["tests_canonical"] for x in stats0)
+    for _ in range(args.warmup):
+        step(Xd)
+    torch.cuda.synchronize()
+    barrier(world)
+    l0 = fp.pc_kernel_launches()
+    with ClockSampler(local if world > 1 else torch.cuda.current_device()) as clk:
+        torch.cuda.nvtx.range_push("bench_timed")
+        ms, (_, stats) = timed(lambda: step(Xd), args.steps)
+        torch.cuda.nvtx.range_pop()
+    launches = fp.pc_kernel_launches() - l0
+    barrier(world)
+    t_max = max_over_ranks(sum(ms) / 1000.0, world)
+    value = sum_over_ranks(float(tests_unit * args.steps), world) / t_max
+
+    # the same problems in one batched handle
+    pb = fp.PCBatch(ns, ps, MANY["alpha"], MANY["max_level"], precision=2)
+    fp.pc_set_stream(pb.h, main_s)
+    adj_b = torch.empty((pb.p, pb.p), dtype=torch.uint8, device=dev)
+
+    def step_b():
+        for i in range(len(inst)):
+            pb.corr_block(i, Xd[i])
+        _, st = pb.skeleton(adj_b)
+        return st
+    step_b()
+    ms_b, st_b = timed(step_b, max(2, min(args.steps, 3)))
+    blocks = pb.split(adj_b.cpu().numpy())
+    batched = {"ms_per_step": float(np.mean(ms_b)), "value": st_b["tests_canonical"] / (np.mean(ms_b) / 1e3),
+               "tests_executed": st_b["tests_executed"], "levels_run": st_b["levels_run"],
+               "identical_skeletons": all(np.array_equal(blocks[i], adjs_ref[i]) for i in range(len(inst)))}
+    # per-kernel-class device time of the batched search (roofline of its dominant class)
+    fp.pc_set_opt(pb.h, "timing", 1)
+    fp.pc_timing(pb.h, reset=True)
+    st_t = step_b()
+    tim = fp.pc_timing(pb.h, reset=True)
+    cls = fp.TIMING_CLASSES
+    dom = max(cls, key=lambda c: tim[c][0])
+    di = cls.index(dom)
+    flops_cls = list(st_t["flops_class"]) + [0.0]
+    dom_flops = flops_cls[di] if di > 0 else sum(2.0 * n_ * p_ * (p_ + 1) for n_, p_ in zip(ns, ps))
+    peak = FP64_PEAK_TFLOPS if dom in ("stage_a", "prec", "ci_complement") else FP32_PEAK_TFLOPS
+    achieved = dom_flops / (tim[dom][0] * 1e-3) / 1e12 if tim[dom][0] > 0 else 0.0
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": dom, "measured_on": "batched handle, timing step",
+                "peak_source": "nominal FP64 1.25 TFLOP/s" if peak == FP64_PEAK_TFLOPS else
+                "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz", "class_ms": {c: tim[c][0] for c in cls}}
+    pb.close()
+
+    # end to end with host buffers: X from pinned host memory, adjacencies back to the host
+    Xh = [torch.from_numpy(s_.X).pin_memory() for s_ in inst]
+    e2e_ms, _ = timed(lambda: step(Xh, adj=True), max(2, min(args.steps, 3)))
+    e2e = {"value": tests_unit / (np.mean(e2e_ms) / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": int(sum(s_.X.nbytes for s_ in inst)),
+           "d2h_bytes_per_step": int(sum(p_ * p_ for p_ in ps))}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        t_tot, n_tests, k = 0.0, 0, 0
+        for s_ in inst:
+            dt, R = oracle_run(s_.X, {"alpha": MANY["alpha"], "max_level": -1, "order": 0})
+            t_tot += dt
+            n_tests += R["tests_total"]
+            k += 1
+            if t_tot > 20.0:
+                break
+        cpu = {"value": n_tests / t_tot, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": f"the first {k} of the 64 instances (Pearson + skeleton), {t_tot:.1f} s"}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": float(np.mean(ms)), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": "many64", "instances": len(inst), "p_total": int(sum(ps)),
+                           "alpha": MANY["alpha"], "order": "conventional",
+                           "precision": "bf16x3-gemm+fp32-tests", "streams": MANY["streams"],
+                           "parallelism": f"replicas x{world}", "l2": "flushed before every step (512 MB write)"},
+                "tests_canonical_per_step": tests_unit,
+                "tests_executed_per_step": int(sum(x["tests_executed"] for x in stats)),
+                "roofline": roofline, "cpu_baseline": cpu, "batched_handle": batched, "e2e": e2e,
+                "gpu_launches": int(launches), "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    for pc in pcs:
+        pc.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "many64":
+        return run_many(args)
     return run_ours(args)
 
 

@@ -268,6 +268,7 @@ static pc_status create_impl(int64_t n, int32_t p, double alpha, int32_t max_lev
     A(dalloc(h, &g.deg, (size_t)p * sizeof(int)));
     A(dalloc(h, &g.nbr, pp * sizeof(int)));
     A(dalloc(h, &g.ooff, (size_t)(p + 1) * sizeof(long long)));
+    A(dalloc(h, &g.opu, (size_t)p * pmax * sizeof(int)));   // ordered pairs <= p * (largest p)
     h->opair_cap = (long long)p * (p - 1);
     A(dalloc(h, &g.tn_off, (size_t)(p + 2) * sizeof(ull)));
     A(dalloc(h, &g.cn_off, (size_t)(p + 2) * sizeof(ull)));
@@ -1140,7 +1141,11 @@ static pc_status skeleton_complete(pc_handle *h, pc_stats *st, bool *overflow)
         }
     }
     CK(cudaEventRecord(h->ev1, s));
-    if (h->learned) CK(fpc::launch_reverify(g, tp, h->C64, h->ldc, s));
+    if (h->learned) {
+        // largest stage run: the first one in the reversed order, the last one conventionally
+        const int lmax = h->order == 1 ? h->info_h->first_level : h->info_h->l - 1;
+        CK(fpc::launch_reverify(g, tp, h->C64, h->ldc, lmax, s));
+    }
     if (pc_status r = read_info(h)) return r;
     if (!h->info_h->done) return fail(h, PC_ERR_INTERNAL, "stage loop did not finish");
     CK(cudaMemcpyAsync(h->ctr_h, g.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));

@@ -81,6 +81,7 @@ struct GraphDev {
     int *deg;                   // p
     int *nbr;                   // p x p, ascending neighbour ids of the frozen graph
     long long *ooff;            // p+1, exclusive scan of deg (ordered-pair offsets)
+    int *opu;                   // per ordered pair: its node u (stages of the small-stage kernel)
     unsigned long long *tn_off; // p+1: first direct test of each node (exclusive scan)
     unsigned long long *cn_off; // p+1: first complement test of each node
     unsigned long long *rn_off; // p+1: first remainder test of each node (small-stage kernel)
@@ -105,8 +106,8 @@ struct GraphDev {
     short *prec_pos;            // p x p: slot of node w in block u, -1 = absent/dead
     int *prec_need;             // p: build request flags
     // learned proposal (optional): per node, the first score row of its
-    // candidates (pair j, position x) and, per row, the candidate position at
-    // each place of the proposal order
+    // candidates (pair j, position x) and, per row, the candidate node at each
+    // place of the proposal order
     unsigned long long *row_off;   // p+1 (nullptr: plain lexicographic order)
     const short *perm;
     long long rows_cap;
@@ -219,7 +220,7 @@ cudaError_t launch_mlp_backward(const float *feats, const float *labels, const f
 cudaError_t launch_adam(float *theta, const float *grad, float *m, float *v, float lr, int step, cudaStream_t s);
 cudaError_t launch_mlp_features(const int *quads, long long R, const float *C32, int ldc, int p, long long n,
                                 const long long *nvec, double q, float *feats, int *err, cudaStream_t s);
-cudaError_t launch_reverify(GraphDev g, TestParams tp, const double *C64, int ldc, cudaStream_t s);
+cudaError_t launch_reverify(GraphDev g, TestParams tp, const double *C64, int ldc, int lmax, cudaStream_t s);
 
 // ---- raw test batches (level.cu)
 cudaError_t launch_ci_list(const int *ij, const int *S, int l, long long b, const float *C32,

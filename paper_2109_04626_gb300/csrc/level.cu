@@ -357,6 +357,11 @@ __global__ void __launch_bounds__(1024) head_kernel(GraphDev g, TestParams tp, d
     const bool small = tp.precision != 0 && l <= LANE_LMAX;
     int rounds = 0;
     if (small && tot[0] > 0) {
+        // owner node of every ordered pair (the small-stage kernel's work items)
+        for (int u = s0; u < s1; ++u) {
+            const long long b = g.ooff[u];
+            for (int jj = 0, dg = g.deg[u]; jj < dg; ++jj) g.opu[b + jj] = u;
+        }
         // rank-major rounds of the lane kernel: at most tp.lane_rounds chunks of
         // every direct pair, the rest in the pair-major remainder space rn_off
         for (int off = 16; off > 0; off >>= 1) {
@@ -621,15 +626,17 @@ __device__ __forceinline__ void flush_acc(const WarpAcc &acc, DevCounters *ctr)
     if (acc.maxdz > 0.f) atomic_max_float_pos(&ctr->max_dz_bits, acc.maxdz);
 }
 
-// Candidate position x of the ordered pair (u, j) (d candidates) -> index into
-// nbr[u] (v sits at index j), through the proposal order when the stage has one.
-__device__ __forceinline__ int cand_index(const GraphDev &g, int u, int j, int d, int x)
+// Candidate position x of the ordered pair (u, j) (d candidates) -> node id:
+// position x of adj(u)\{v} in ascending order (v sits at index j of nbr[u]), or
+// the x-th candidate of the proposal order when the stage has one (perm holds
+// the candidates' node ids in that order).
+__device__ __forceinline__ int cand_node(const GraphDev &g, int u, int j, int d, int x)
 {
     if (g.row_off) {
         const ull b = g.row_off[u];
-        if (g.row_off[u + 1] > b) x = g.perm[b + (ull)j * d + x];
+        if (g.row_off[u + 1] > b) return g.perm[b + (ull)j * d + x];
     }
-    return x + (x >= j);
+    return g.nbr[(long long)u * g.p + x + (x >= j)];
 }
 
 __device__ __forceinline__ void sort_small(int *a, int n)
@@ -680,7 +687,7 @@ __global__ void __launch_bounds__(256) ci_direct_kernel(GraphDev g, TestParams t
         if (*(volatile ull *)bp < key) continue;   // an earlier set already separates
         if (lane == 0) {
             unrank_lex(rank, d, l, g.binom, g.ldb, pos);
-            for (int i = 0; i < l; ++i) nd[i] = g.nbr[(long long)u * p + cand_index(g, u, j, d, pos[i])];
+            for (int i = 0; i < l; ++i) nd[i] = cand_node(g, u, j, d, pos[i]);
             if (g.row_off) sort_small(nd, l);        // the set is tested in ascending-id order
             nd[l] = u;
             nd[l + 1] = v;
@@ -713,9 +720,9 @@ __global__ void __launch_bounds__(256) ci_direct_kernel(GraphDev g, TestParams t
 // records the key and stops); a test the FP32 error model cannot trust goes
 // to the FP64 queue.
 template <int L>
-__device__ __forceinline__ bool lane_decide(const TestParams &tp, float sqf, float h11, float h12, float h22,
-                                            float pmin, bool bad, ull flat, ull *queue, ull qcap, ull *qlen,
-                                            WarpAcc &acc)
+__device__ __forceinline__ bool lane_decide(const TestParams &tp, float sqf, float rq, float h11, float h12,
+                                            float h22, float pmin, bool bad, ull flat, ull *queue, ull qcap,
+                                            ull *qlen, WarpAcc &acc)
 {
     constexpr int M = L + 2;
     pmin = fminf(pmin, fminf(h11, h22));
@@ -723,23 +730,29 @@ __device__ __forceinline__ bool lane_decide(const TestParams &tp, float sqf, flo
     ++acc.tests;
     acc.fl32 += flops_direct(L);
     bool queue_it = false, ind = false;
-    if (bad || pmin < (float)tp.guard) {
+    // FP32 error bound of r: dr = e / pmin
+    const float e = 2.0f * ((float)M * 5.96e-8f + tp.eps_c);
+    if (bad || pmin < (float)tp.guard || e > tp.dr_max * pmin) {
         queue_it = true;
         ++acc.guard;
     } else {
-        const float rf = h12 * rsqrtf(h11 * h22);
-        const float dr = 2.0f * ((float)M * 5.96e-8f + tp.eps_c) / pmin;
-        const float zf = fabsf(rf) < 1.0f ? sqf * fabsf(atanhf(rf)) : INFINITY;
-        const float dz = sqf * dr / fmaxf(1.0f - rf * rf, 1e-3f);
-        if (dr > tp.dr_max) {
-            queue_it = true;
-            ++acc.guard;
-        } else if (fabsf(zf - tp.qf) < (float)tp.band + 4.0f * dz) {
-            queue_it = true;
-            ++acc.band;
-        } else {
-            ind = zf <= tp.qf;
-        }
+        const float a = fabsf(h12 * rsqrtf(h11 * h22));
+        if (a < 1.0f) {
+            // z <= q  <=>  |r| <= rq = tanh(q / sqrt(n-l-3)).  The test is trusted in
+            // FP32 when |z - q| >= band + 4 dz, dz = sqf dr / D, D = max(1 - r^2, 1e-3);
+            // by the mean-value theorem |z - q| >= sqf |a - rq| / (1 - min(a, rq)^2),
+            // so a sufficient condition, multiplied through by pmin D > 0, is below.
+            const float D = fmaxf(1.0f - a * a, 1e-3f);
+            const float mn = fminf(a, rq), w = 1.0f - mn * mn;
+            const float lhs = sqf * fabsf(a - rq) * D * pmin;
+            const float rhs = (float)tp.band * D * w * pmin + 4.0f * sqf * e * w;
+            if (lhs < rhs) {
+                queue_it = true;
+                ++acc.band;
+            } else {
+                ind = a <= rq;
+            }
+        }                                               // |r| >= 1: z infinite, dependent
     }
     if (queue_it) {
         const ull slot = atomicAdd(qlen, 1ull);
@@ -761,62 +774,8 @@ __device__ __forceinline__ int lex_next(int *pos, int d)
     return i;
 }
 
-// Proposal order (the sets of a pair in the order the scoring network gave):
-// every test gathers and factors its whole matrix, members sorted by id.
-template <int L>
-__device__ __forceinline__ void lane_tests(const GraphDev &g, const TestParams &tp, const float *C32, int ldc,
-                                           int u, int j, int d, ull T, ull rank, ull rank_end, ull *queue,
-                                           ull qcap, ull *qlen, WarpAcc &acc)
-{
-    constexpr int M = L + 2;
-    const int p = g.p;
-    const float sqf = sqrtf((float)(n_of(tp, u) - L - 3));
-    const int v = g.nbr[(long long)u * p + j];
-    const int side = u > v;
-    ull *bp = g.best + (long long)min(u, v) * p + max(u, v);
-    const ull tbase = g.tn_off[u] + (ull)j * T;          // flat index of (u, j, rank 0)
-    int pos[L > 0 ? L : 1];
-    unrank_lex(rank, d, L, g.binom, g.ldb, pos);
-    for (; rank < rank_end; ++rank) {
-        const ull key = ((ull)side << 62) | rank;
-        if (*(volatile ull *)bp < key) return;          // an earlier set of this pair separates
-        int nd[M];
-#pragma unroll
-        for (int i = 0; i < L; ++i) nd[i] = g.nbr[(long long)u * p + cand_index(g, u, j, d, pos[i])];
-        sort_small(nd, L);
-        nd[L] = u;
-        nd[L + 1] = v;
-        float a[M * (M + 1) / 2];
-#pragma unroll
-        for (int i = 0; i < M; ++i)
-#pragma unroll
-            for (int c = 0; c <= i; ++c) a[i * (i + 1) / 2 + c] = __ldg(C32 + (long long)nd[i] * ldc + nd[c]);
-        // Cholesky of the S block, trailing 2x2 = H (Sec. 4)
-        float pmin = 1e30f;
-        bool bad = false;
-#pragma unroll
-        for (int k = 0; k < L; ++k) {
-            const float piv = a[k * (k + 1) / 2 + k];
-            pmin = fminf(pmin, piv);
-            bad |= !(piv > 1e-12f);
-            const float rl = rsqrtf(fmaxf(piv, 1e-30f));
-#pragma unroll
-            for (int i = k + 1; i < M; ++i) a[i * (i + 1) / 2 + k] *= rl;
-#pragma unroll
-            for (int i = k + 1; i < M; ++i)
-#pragma unroll
-                for (int c = k + 1; c <= i; ++c) a[i * (i + 1) / 2 + c] -= a[i * (i + 1) / 2 + k] * a[c * (c + 1) / 2 + k];
-        }
-        if (lane_decide<L>(tp, sqf, a[L * (L + 1) / 2 + L], a[(L + 1) * (L + 2) / 2 + L],
-                           a[(L + 1) * (L + 2) / 2 + L + 1], pmin, bad, tbase + rank, queue, qcap, qlen, acc)) {
-            atomicMin(bp, key);
-            return;                                      // later sets of this pair cannot win
-        }
-        if (rank + 1 < rank_end) lex_next<L>(pos, d);
-    }
-}
-
-// Lexicographic order: consecutive sets share their first L-1 members (all but
+// Lexicographic order over the candidate list (ascending ids, or the proposal's
+// permutation of it): consecutive sets share their first L-1 members (all but
 // one step in d-L+1).  The Cholesky factor of that prefix P, the rows of u and
 // v eliminated by it (lu, lv) and the Schur block of (u, v) given P are kept in
 // registers; each test borders them with the last member s: one row of corr
@@ -824,7 +783,7 @@ __device__ __forceinline__ void lane_tests(const GraphDev &g, const TestParams &
 //   x = 1 - |l_s|^2,  c_u = corr_us - lu.l_s,  c_v = corr_vs - lv.l_s,
 //   H = H_P - [c_u c_v]^T [c_u c_v] / x
 // -- the same Cholesky of the S block (Sec. 4) in bordered form, O(L^2) work.
-template <int L>
+template <int L, bool PROP>
 __device__ __forceinline__ void lane_tests_lex(const GraphDev &g, const TestParams &tp, const float *C32, int ldc,
                                                int u, int j, int d, ull T, ull rank, ull rank_end, ull *queue,
                                                ull qcap, ull *qlen, WarpAcc &acc)
@@ -833,8 +792,13 @@ __device__ __forceinline__ void lane_tests_lex(const GraphDev &g, const TestPara
     constexpr int KA = K > 0 ? K : 1;
     const int p = g.p;
     const float sqf = sqrtf((float)(n_of(tp, u) - L - 3));
+    const float rq = tanhf(tp.qf / sqf);                 // |r| threshold of this stage
     const int *nb = g.nbr + (long long)u * p;
     const int v = nb[j];
+    // proposal order: position x of the enumeration is the node perm[x]
+    const short *pr = nullptr;
+    if (PROP && g.row_off && g.row_off[u + 1] > g.row_off[u]) pr = g.perm + g.row_off[u] + (ull)j * d;
+    auto member = [&](int x) -> int { return (PROP && pr) ? (int)pr[x] : nb[x + (x >= j)]; };
     const int side = u > v;
     ull *bp = g.best + (long long)min(u, v) * p + max(u, v);
     const ull tbase = g.tn_off[u] + (ull)j * T;
@@ -846,15 +810,19 @@ __device__ __forceinline__ void lane_tests_lex(const GraphDev &g, const TestPara
     float Lp[KA * (KA + 1) / 2], rd[KA], lu[KA], lv[KA];
     float huu = 1.f, hvv = 1.f, huv = cuv, ppmin = 1e30f;
     bool pbad = false, fresh = true;
+    int since = 0;
     for (; rank < rank_end; ++rank) {
         const ull key = ((ull)side << 62) | rank;
-        if (*(volatile ull *)bp < key) return;
+        // an earlier set of this pair already separates: checked every fourth test
+        // (the read goes to L2; at most three tests are wasted)
+        if (since == 0 && *(volatile ull *)bp < key) return;
+        since = (since + 1) & 3;
         if (K > 0 && fresh) {
             // factor the prefix and eliminate the rows of u and v by it
             ppmin = 1e30f;
             pbad = false;
 #pragma unroll
-            for (int i = 0; i < K; ++i) sp[i] = nb[pos[i] + (pos[i] >= j)];
+            for (int i = 0; i < K; ++i) sp[i] = member(pos[i]);
 #pragma unroll
             for (int i = 0; i < K; ++i) {
                 const float *Ci = C32 + (long long)sp[i] * ldc;
@@ -896,7 +864,7 @@ __device__ __forceinline__ void lane_tests_lex(const GraphDev &g, const TestPara
         float h11 = huu, h22 = hvv, h12 = huv, pmin = ppmin;
         bool bad = pbad;
         if (L > 0) {
-            const int s = nb[pos[L - 1] + (pos[L - 1] >= j)];
+            const int s = member(pos[L - 1]);
             const float *Cs = C32 + (long long)s * ldc;
             float ls[KA];
             float x = 1.f;
@@ -917,12 +885,12 @@ __device__ __forceinline__ void lane_tests_lex(const GraphDev &g, const TestPara
             }
             pmin = fminf(pmin, x);
             bad |= !(x > 1e-12f);
-            const float rx = 1.f / fmaxf(x, 1e-30f);
+            const float rx = __frcp_rn(fmaxf(x, 1e-30f));
             h11 -= cu * cu * rx;
             h22 -= cv * cv * rx;
             h12 -= cu * cv * rx;
         }
-        if (lane_decide<L>(tp, sqf, h11, h12, h22, pmin, bad, tbase + rank, queue, qcap, qlen, acc)) {
+        if (lane_decide<L>(tp, sqf, rq, h11, h12, h22, pmin, bad, tbase + rank, queue, qcap, qlen, acc)) {
             atomicMin(bp, key);
             return;
         }
@@ -930,17 +898,14 @@ __device__ __forceinline__ void lane_tests_lex(const GraphDev &g, const TestPara
     }
 }
 
-// one chunk of a pair: bordered lexicographic tests, or the proposal order
-// (PROP: the kernel variant of handles with a proposal network)
+// one chunk of a pair (PROP: the kernel variant of handles with a proposal
+// network, whose scored stages enumerate over the permuted candidate list)
 template <int L, bool PROP>
 __device__ __forceinline__ void lane_chunk(const GraphDev &g, const TestParams &tp, const float *C32, int ldc,
                                            int u, int j, int d, ull T, ull rank, ull rank_end, ull *queue,
                                            ull qcap, ull *qlen, WarpAcc &acc)
 {
-    if (PROP && g.row_off && g.row_off[u + 1] > g.row_off[u])
-        lane_tests<L>(g, tp, C32, ldc, u, j, d, T, rank, rank_end, queue, qcap, qlen, acc);
-    else
-        lane_tests_lex<L>(g, tp, C32, ldc, u, j, d, T, rank, rank_end, queue, qcap, qlen, acc);
+    lane_tests_lex<L, PROP>(g, tp, C32, ldc, u, j, d, T, rank, rank_end, queue, qcap, qlen, acc);
 }
 
 // Phase A, rank-major: item g = (round r, ordered pair o), r = g / NP -- a wave
@@ -956,25 +921,33 @@ __device__ __forceinline__ void lane_dispatch(const GraphDev &g, const TestParam
     const long long NP = g.info->n_opairs;
     const int rounds = g.info->lane_rounds;
     const ull chunk = (ull)tp.lane_chunk;
-    const ull gstride = (ull)gridDim.x * blockDim.x;
-    const ull tid = blockIdx.x * (ull)blockDim.x + threadIdx.x;
-    const ull na = (ull)rounds * (ull)NP;
-    for (ull gi = tid; gi < na; gi += gstride) {
-        const int r = (int)(gi / (ull)NP);
-        const long long o = (long long)(gi - (ull)r * NP);
-        const int u = (int)(upper_bound_dev(g.ooff, (long long)p + 1, o) - 1);
-        if (g.tn_off[u + 1] == g.tn_off[u]) continue;     // not a direct node this stage
-        const int d = g.deg[u] - 1;
-        const ull T = g.binom[(long long)d * g.ldb + L];
-        const ull r0 = (ull)r * chunk;
-        if (r0 >= T) continue;
-        const ull r1 = r0 + chunk < T ? r0 + chunk : T;
-        lane_chunk<L, PROP>(g, tp, C32, ldc, u, (int)(o - g.ooff[u]), d, T, r0, r1, queue, qcap, qlen, acc);
+    const long long G = (long long)gridDim.x * blockDim.x;
+    const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (NP > 0 && rounds > 0) {
+        // item (r, o) = (gi / NP, gi % NP) stepped by G without dividing: one
+        // division for the start and for the stride
+        long long r = tid / NP, o = tid - r * NP;
+        const long long Gq = G / NP, Gr = G - Gq * NP;
+        for (; r < rounds; r += Gq, o += Gr) {
+            if (o >= NP) {
+                o -= NP;
+                ++r;
+                if (r >= rounds) break;
+            }
+            const int u = g.opu[o];                     // owner of ordered pair o
+            if (g.tn_off[u + 1] == g.tn_off[u]) continue;   // not a direct node this stage
+            const int d = g.deg[u] - 1;
+            const ull T = g.binom[(long long)d * g.ldb + L];
+            const ull r0 = (ull)r * chunk;
+            if (r0 >= T) continue;
+            const ull r1 = r0 + chunk < T ? r0 + chunk : T;
+            lane_chunk<L, PROP>(g, tp, C32, ldc, u, (int)(o - g.ooff[u]), d, T, r0, r1, queue, qcap, qlen, acc);
+        }
     }
     const ull nb = g.rn_off[p];
     const ull skip = (ull)rounds * chunk;
     const ull nbc = (nb + chunk - 1) / chunk;
-    for (ull c = tid; c < nbc; c += gstride) {
+    for (ull c = (ull)tid; c < nbc; c += (ull)G) {
         // chunk c of the remainder space; it may cross pairs
         ull t = c * chunk;
         const ull tend = t + chunk < nb ? t + chunk : nb;
@@ -984,7 +957,7 @@ __device__ __forceinline__ void lane_dispatch(const GraphDev &g, const TestParam
             const ull T = g.binom[(long long)d * g.ldb + L];
             const ull per = T - skip;                     // remainder ranks per pair of u
             const ull w = t - g.rn_off[u];
-            const int j = (int)(w / per);
+            const int j = (w >> 32) == 0 && (per >> 32) == 0 ? (int)((unsigned)w / (unsigned)per) : (int)(w / per);
             const ull rr = w - (ull)j * per;
             const ull take = per - rr < tend - t ? per - rr : tend - t;
             lane_chunk<L, PROP>(g, tp, C32, ldc, u, j, d, T, skip + rr, skip + rr + take, queue, qcap, qlen, acc);
@@ -1013,7 +986,8 @@ __device__ __forceinline__ void lane_switch(int l, const GraphDev &g, const Test
 // Stages LO <= l <= HI (one instantiation per range keeps the register count of
 // small l low: the launch sequence runs every range, all but one return at once).
 template <int LO, int HI, bool PROP>
-__global__ void __launch_bounds__(256) ci_lane_kernel(GraphDev g, TestParams tp, const float *C32, int ldc,
+__global__ void __launch_bounds__(256, HI <= 2 ? 4 : (HI <= 4 ? 3 : 2))
+    ci_lane_kernel(GraphDev g, TestParams tp, const float *C32, int ldc,
                                                       ull *queue, ull qcap, ull *qlen)
 {
     if (stopped(g.info)) return;
@@ -1058,7 +1032,7 @@ __global__ void __launch_bounds__(256) ci_redecide_kernel(GraphDev g, TestParams
         if (*(volatile ull *)bp < key) continue;
         if (lane == 0) {
             unrank_lex(rank, d, l, g.binom, g.ldb, pos);
-            for (int i = 0; i < l; ++i) nd[i] = g.nbr[(long long)u * p + cand_index(g, u, j, d, pos[i])];
+            for (int i = 0; i < l; ++i) nd[i] = cand_node(g, u, j, d, pos[i]);
             if (g.row_off) sort_small(nd, l);
             nd[l] = u;
             nd[l + 1] = v;
@@ -1113,7 +1087,7 @@ __global__ void __launch_bounds__(128) ci_complement_kernel(GraphDev g, TestPara
         const short *ps = g.prec_pos + (long long)u * p;
         const int su = ps[u], sv = ps[v];
         int sr[KC_MAX];
-        for (int i = 0; i < k; ++i) sr[i] = ps[g.nbr[(long long)u * p + cand_index(g, u, j, d, posR[i])]];
+        for (int i = 0; i < k; ++i) sr[i] = ps[cand_node(g, u, j, d, posR[i])];
         if (g.row_off) sort_small(sr, k);
         double L[KC_MAX][KC_MAX], yu[KC_MAX], yv[KC_MAX];
         bool bad = false;
@@ -1385,15 +1359,15 @@ __global__ void commit_kernel(GraphDev g, int l_fixed, int explicit_sets, int co
             if (kd <= KC_MAX && kd < l) {
                 // expand through the complement: R = the kd dropped positions, at lex
                 // rank C(dd,l) - 1 - rank among the kd-subsets; S = the rest, ascending
-                int posR[KC_MAX + 1], idxR[KC_MAX];
+                int posR[KC_MAX + 1], nodeR[KC_MAX];
                 const ull T = g.binom[(long long)dd * g.ldb + l];
                 unrank_lex(T - 1 - rank, dd, kd, g.binom, g.ldb, posR);
-                for (int i = 0; i < kd; ++i) idxR[i] = cand_index(g, su, jj, dd, posR[i]);
+                for (int i = 0; i < kd; ++i) nodeR[i] = cand_node(g, su, jj, dd, posR[i]);
                 int o = 0;
                 for (int y = 0; y <= dd; ++y) {
                     if (y == jj) continue;
                     bool dropped = false;
-                    for (int i = 0; i < kd; ++i) dropped |= idxR[i] == y;
+                    for (int i = 0; i < kd; ++i) dropped |= nodeR[i] == nb[y];
                     if (!dropped) g.pool[off + o++] = nb[y];
                 }
             } else {
@@ -1406,7 +1380,7 @@ __global__ void commit_kernel(GraphDev g, int l_fixed, int explicit_sets, int co
                         r -= c;
                         ++x;
                     }
-                    g.pool[off + i] = nb[cand_index(g, su, jj, dd, x)];
+                    g.pool[off + i] = cand_node(g, su, jj, dd, x);
                     ++x;
                 }
                 if (g.row_off) sort_small(g.pool + off, l);
@@ -1659,10 +1633,11 @@ cudaError_t launch_commit(GraphDev g, long long n_opairs_cap, int l_fixed, int e
     return cudaGetLastError();
 }
 
-cudaError_t launch_reverify(GraphDev g, TestParams tp, const double *C64, int ldc, cudaStream_t s)
+cudaError_t launch_reverify(GraphDev g, TestParams tp, const double *C64, int ldc, int lmax, cudaStream_t s)
 {
-    // sets up to the largest stage of the search (p - 3 at most) fit one warp's matrix
-    int mmax = std::min(g.p, 130);
+    // one warp's matrix holds the sets of the largest stage the search ran
+    // (sets of more than 128 members are not re-tested)
+    int mmax = std::max(2, std::min(std::min(g.p, 130), lmax + 2));
     int ms, per_warp, wpc;
     direct_shape(mmax, ms, per_warp, wpc);
     size_t smem = (size_t)wpc * per_warp;

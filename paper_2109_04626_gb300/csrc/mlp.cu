@@ -119,7 +119,7 @@ __device__ __forceinline__ void row_features(const MlpRows &R, const GraphDev &g
 }
 
 // Forward pass over rows [0, R): scores s, and for training h1 (BF16), h2 (FP32).
-__global__ void __launch_bounds__(128, 1) mlp_forward_kernel(MlpRows rows, GraphDev g, const uint8_t *wpack,
+__global__ void __launch_bounds__(128, 2) mlp_forward_kernel(MlpRows rows, GraphDev g, const uint8_t *wpack,
                                                              const float *theta, float *scores,
                                                              __nv_bfloat16 *h1_out, float *h2_out, int *err)
 {
@@ -394,7 +394,7 @@ __global__ void perm_kernel(GraphDev g, const unsigned long long *row_off, const
                 const float sy = scores[base + y];
                 rank += (sy > sx) || (sy == sx && y < x);
             }
-            perm[base + rank] = (short)x;
+            perm[base + rank] = (short)g.nbr[(long long)u * p + x + (x >= j)];   // node id
         }
     }
 }
@@ -408,6 +408,17 @@ cudaError_t launch_mlp_pack(const float *theta, uint8_t *wpack, cudaStream_t s)
     mlp_pack_kernel<<<NH, 64, 0, s>>>(theta, wpack);
     note_launch();
     return cudaGetLastError();
+}
+
+// forward pass: two CTAs per SM (97 KB shared memory and 256 TMEM columns each)
+static int mlp_fwd_ctas(long long rows)
+{
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long long tiles = (rows + T_ROWS - 1) / T_ROWS;
+    long long c = tiles < 2ll * sms ? tiles : 2ll * sms;
+    return (int)(c < 1 ? 1 : c);
 }
 
 static int mlp_ctas(long long rows)
@@ -429,7 +440,7 @@ cudaError_t launch_mlp_forward_feats(const float *feats, long long R, const uint
     rows.R = R;
     cudaError_t e = cudaFuncSetAttribute(mlp_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, MLP_SMEM);
     if (e != cudaSuccess) return e;
-    mlp_forward_kernel<<<mlp_ctas(R), 128, MLP_SMEM, s>>>(rows, g, wpack, theta, scores, h1, h2, err);
+    mlp_forward_kernel<<<mlp_fwd_ctas(R), 128, MLP_SMEM, s>>>(rows, g, wpack, theta, scores, h1, h2, err);
     note_launch();
     return cudaGetLastError();
 }
@@ -448,7 +459,7 @@ cudaError_t launch_mlp_score_stage(GraphDev g, const unsigned long long *row_off
     rows.inv_q = inv_q;
     cudaError_t e = cudaFuncSetAttribute(mlp_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, MLP_SMEM);
     if (e != cudaSuccess) return e;
-    mlp_forward_kernel<<<mlp_ctas(rows_cap), 128, MLP_SMEM, s>>>(rows, g, wpack, theta, scores, nullptr, nullptr, err);
+    mlp_forward_kernel<<<mlp_fwd_ctas(rows_cap), 128, MLP_SMEM, s>>>(rows, g, wpack, theta, scores, nullptr, nullptr, err);
     note_launch();
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);

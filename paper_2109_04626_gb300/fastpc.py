@@ -221,17 +221,22 @@ def pc_skeleton(h, p: int, adj_out=None):
     return adj, st.as_dict()
 
 
-def pc_skeleton_many(handles, ps):
+def pc_skeleton_many(handles, ps, adj_out=True):
     """Concurrent searches of independent problems: handles (list of c_void_p, each
     after pc_corr, ideally each on its own stream), ps their p.  Returns
-    (list of adjacency arrays or None, list of stats dicts, list of status codes)."""
+    (list of adjacency arrays or None, list of stats dicts, list of status codes);
+    adj_out=False leaves the skeletons on the device (no copies)."""
     k = len(handles)
     H = (ctypes.c_void_p * k)(*[h.value for h in handles])
-    adjs = [np.empty((p, p), dtype=np.uint8) for p in ps]
-    A = (ctypes.c_void_p * k)(*[a.ctypes.data for a in adjs])
     S = (pc_stats * k)()
     st = (ctypes.c_int32 * k)()
-    load().pc_skeleton_many(H, k, A, S, st)
+    if adj_out:
+        adjs = [np.empty((p, p), dtype=np.uint8) for p in ps]
+        A = (ctypes.c_void_p * k)(*[a.ctypes.data for a in adjs])
+        load().pc_skeleton_many(H, k, A, S, st)
+    else:
+        adjs = [None] * k
+        load().pc_skeleton_many(H, k, None, S, st)
     status = [int(x) for x in st]
     return [a if s_ == 0 else None for a, s_ in zip(adjs, status)], [x.as_dict() for x in S], status
 
