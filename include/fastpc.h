@@ -63,7 +63,8 @@ typedef struct {
     int32_t levels_run;         /* stages visited                                             */
     int32_t stage_a_ran;        /* 1 if the l = p-2 stage ran in closed form                  */
     int32_t first_level;        /* first enumerated stage                                     */
-    int32_t reserved;
+    int32_t queue_overflows;    /* stages whose FP64 re-decision queue overflowed (each was re-run
+                                   by the warp-per-test kernel; the queue grows for later runs) */
 } pc_stats;
 
 /* pc_create -- a handle for data of n samples over p variables, significance
@@ -240,7 +241,8 @@ int64_t pc_kernel_launches(void);
  * with CUDA events on its stream, grouped by kernel class: 0 correlation,
  * 1 closed-form stage l=p-2, 2 neighbourhood precision builds and downdates,
  * 3 direct CI tests, 4 complement CI tests, 5 stage bookkeeping (neighbour
- * lists, counts, scans, commit), 6 proposal scoring and ordering.  Writes
+ * lists, counts, scans, commit), 6 proposal scoring, ordering and the FP64
+ * re-test of the sepsets found in the proposal order.  Writes
  * per-class device milliseconds and launch-group counts accumulated since the
  * last reset (reset != 0 clears them afterwards).  ms and count have 7
  * entries; either may be NULL. */

@@ -4,6 +4,21 @@
 
 namespace fpc {
 
+// Index of the pair (a, c) in a per-pair array, of a's neighbour list, and of
+// the entry (a, c) of a correlation matrix (see GraphDev::prow).
+__device__ __forceinline__ long long pidx(const GraphDev &g, int a, int c)
+{
+    return g.prow ? __ldg(g.prow + a) + c : (long long)a * g.p + c;
+}
+__device__ __forceinline__ long long nidx(const GraphDev &g, int a)
+{
+    return g.nrow ? __ldg(g.nrow + a) : (long long)a * g.p;
+}
+__device__ __forceinline__ long long cidx(const long long *prow, int ldc, int a, int c)
+{
+    return prow ? __ldg(prow + a) + c : (long long)a * ldc + c;
+}
+
 // Symmetric sweep of every pivot of an SPD matrix in shared memory:
 // A <- -A^{-1}.  Pivot k is used without row exchanges, so it equals the
 // conditional variance of k given 0..k-1 (the degeneracy test of the oracle's

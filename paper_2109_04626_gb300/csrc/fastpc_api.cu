@@ -43,6 +43,9 @@ struct pc_handle {
     // and the diagonal block of corr there; nblk = 0 for one problem
     int nblk = 0;
     std::vector<int> boff;
+    std::vector<long long> pbase;        // first packed element of each instance's blocks
+    size_t pair_elems = 0;               // entries of a per-pair array (p*p, or sum p_i^2)
+    size_t c_elems = 0;                  // entries of a correlation matrix (p*ldc, or sum p_i^2)
     std::vector<long long> bn;
     std::vector<char> bdone;
     long long n_min = 0;
@@ -221,6 +224,7 @@ static TestParams make_tp(const pc_handle *h)
     TestParams tp;
     tp.n = h->n;
     tp.nvec = h->g.nvec;
+    tp.prow = h->g.prow;
     tp.q = h->q;
     tp.qf = (float)h->q;
     tp.band = h->band;
@@ -247,7 +251,7 @@ static TestParams make_tp(const pc_handle *h)
 // pmax: largest problem size (binomial table), batch: block-diagonal batch
 // layout (no precision blocks, conventional order only)
 static pc_status create_impl(int64_t n, int32_t p, double alpha, int32_t max_level, int32_t pmax,
-                             long long pool_cap, bool batch, pc_handle **out)
+                             long long pool_cap, bool batch, size_t packed, pc_handle **out)
 {
     pc_handle *h = new pc_handle();
     h->n = n;
@@ -261,7 +265,11 @@ static pc_status create_impl(int64_t n, int32_t p, double alpha, int32_t max_lev
     GraphDev &g = h->g;
     g.p = p;
     g.W = W;
-    size_t pp = (size_t)p * p;
+    // per-pair arrays and correlation matrices: p x p (p x ldc), or the packed
+    // diagonal blocks of a batch
+    const size_t pp = batch ? packed : (size_t)p * p;
+    h->pair_elems = pp;
+    h->c_elems = batch ? packed : (size_t)p * h->ldc;
     cudaError_t e = cudaSuccess;
     auto A = [&](cudaError_t ee) { if (e == cudaSuccess) e = ee; };
     A(dalloc(h, &g.adj, (size_t)p * W * sizeof(uint32_t)));
@@ -291,8 +299,8 @@ static pc_status create_impl(int64_t n, int32_t p, double alpha, int32_t max_lev
     A(dalloc(h, &g.ctr, sizeof(DevCounters)));
     A(dalloc(h, &h->mean, (size_t)p * sizeof(double)));
     A(dalloc(h, &h->rsd, (size_t)p * sizeof(double)));
-    A(dalloc(h, &h->C64, (size_t)p * h->ldc * sizeof(double)));
-    A(dalloc(h, &h->C32, (size_t)p * h->ldc * sizeof(float)));
+    A(dalloc(h, &h->C64, h->c_elems * sizeof(double)));
+    A(dalloc(h, &h->C32, h->c_elems * sizeof(float)));
     A(dalloc(h, &h->singular, sizeof(int)));
     A(dalloc(h, &h->tc_err, sizeof(int)));
     A(dalloc(h, &h->mlp_err, sizeof(int)));
@@ -347,7 +355,7 @@ extern "C" pc_status pc_create(int64_t n, int32_t p, double alpha, int32_t max_l
     *out = nullptr;
     if (n < 4 || n > (1ll << 21) || p < 2 || p > fpc::MAXP || !(alpha > 0.0 && alpha < 1.0))
         return PC_ERR_ARG;
-    return create_impl(n, p, alpha, max_level, p, std::max<long long>(1 << 20, 16ll * p * p), false, out);
+    return create_impl(n, p, alpha, max_level, p, std::max<long long>(1 << 20, 16ll * p * p), false, 0, out);
 }
 
 // One handle over k independent problems laid out block-diagonally: instance i
@@ -371,9 +379,11 @@ extern "C" pc_status pc_create_batch(int32_t k, const int64_t *n, const int32_t 
         pool += 16ll * p[i] * p[i];
     }
     if (ptot > fpc::MAXP_BATCH) return PC_ERR_ARG;
+    size_t packed = 0;
+    for (int i = 0; i < k; ++i) packed += (size_t)p[i] * p[i];
     pc_handle *h = nullptr;
     if (pc_status r = create_impl(nmax, (int32_t)ptot, alpha, max_level, pmax, std::max<long long>(1 << 20, pool),
-                                  true, &h))
+                                  true, packed, &h))
         return r;
     h->nblk = k;
     h->order = 0;
@@ -381,26 +391,33 @@ extern "C" pc_status pc_create_batch(int32_t k, const int64_t *n, const int32_t 
     h->boff.assign(k + 1, 0);
     h->bn.assign(n, n + k);
     h->bdone.assign(k, 0);
-    for (int i = 0; i < k; ++i) h->boff[i + 1] = h->boff[i] + p[i];
+    h->pbase.assign(k + 1, 0);
+    for (int i = 0; i < k; ++i) {
+        h->boff[i + 1] = h->boff[i] + p[i];
+        h->pbase[i + 1] = h->pbase[i] + (long long)p[i] * p[i];
+    }
     std::vector<int> lo((size_t)ptot), hi((size_t)ptot);
-    std::vector<long long> nv((size_t)ptot);
+    std::vector<long long> nv((size_t)ptot), prow((size_t)ptot), nrow((size_t)ptot);
     for (int i = 0; i < k; ++i)
         for (int u = h->boff[i]; u < h->boff[i + 1]; ++u) {
             lo[u] = h->boff[i];
             hi[u] = h->boff[i + 1];
             nv[u] = n[i];
+            nrow[u] = h->pbase[i] + (long long)(u - h->boff[i]) * p[i];   // row u of block i
+            prow[u] = nrow[u] - h->boff[i];                                // + global column id
         }
     int *dlo = nullptr, *dhi = nullptr;
-    long long *dn = nullptr;
+    long long *dn = nullptr, *dprow = nullptr, *dnrow = nullptr;
     cudaError_t e = dalloc(h, &dlo, lo.size() * sizeof(int));
     if (e == cudaSuccess) e = dalloc(h, &dhi, hi.size() * sizeof(int));
     if (e == cudaSuccess) e = dalloc(h, &dn, nv.size() * sizeof(long long));
+    if (e == cudaSuccess) e = dalloc(h, &dprow, prow.size() * sizeof(long long));
+    if (e == cudaSuccess) e = dalloc(h, &dnrow, nrow.size() * sizeof(long long));
     if (e == cudaSuccess) e = cudaMemcpy(dlo, lo.data(), lo.size() * sizeof(int), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(dhi, hi.data(), hi.size() * sizeof(int), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(dn, nv.data(), nv.size() * sizeof(long long), cudaMemcpyHostToDevice);
-    // blocks off the diagonal are never read; keep them zero all the same
-    if (e == cudaSuccess) e = cudaMemset(h->C32, 0, (size_t)h->p * h->ldc * sizeof(float));
-    if (e == cudaSuccess) e = cudaMemset(h->C64, 0, (size_t)h->p * h->ldc * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemcpy(dprow, prow.data(), prow.size() * sizeof(long long), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dnrow, nrow.data(), nrow.size() * sizeof(long long), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         pc_status st = e == cudaErrorMemoryAllocation ? PC_ERR_OOM : PC_ERR_CUDA;
         pc_destroy(h);
@@ -409,6 +426,8 @@ extern "C" pc_status pc_create_batch(int32_t k, const int64_t *n, const int32_t 
     h->g.blk_lo = dlo;
     h->g.blk_hi = dhi;
     h->g.nvec = dn;
+    h->g.prow = dprow;
+    h->g.nrow = dnrow;
     *out = h;
     return PC_OK;
 }
@@ -586,8 +605,12 @@ extern "C" const char *pc_status_string(pc_status s)
 
 // ---------------------------------------------------------------- correlation
 // the full FP64 correlation matrix (split-K Gram of the FP64 planes)
-static pc_status syrk64_block(pc_handle *h, int o, long long n, int p)
+// FP64 Gram block of the planes' rows [o, o+p) into C64 (one problem: at row and
+// column o with ldc; a batch instance: its packed block, leading dimension p)
+static pc_status syrk64_block(pc_handle *h, int o, long long n, int p, int blk)
 {
+    double *out = blk < 0 ? h->C64 + (size_t)o * h->ldc + o : h->C64 + h->pbase[blk];
+    const int ld = blk < 0 ? h->ldc : p;
     const size_t wsb = fpc::syrk_f64_ws_bytes(n, p);
     if (wsb > h->syrk_ws_bytes) {
         dfree(h, h->syrk_ws);
@@ -595,8 +618,8 @@ static pc_status syrk64_block(pc_handle *h, int o, long long n, int p)
         CK(dalloc(h, &h->syrk_ws, wsb));
         h->syrk_ws_bytes = wsb;
     }
-    CK(fpc::launch_syrk_f64(h->Xs64 + (size_t)o * h->ldk, n, h->ldk, p, h->C64 + (size_t)o * h->ldc + o, h->ldc,
-                            h->syrk_ws, h->syrk_ws_bytes, h->stream));
+    CK(fpc::launch_syrk_f64(h->Xs64 + (size_t)o * h->ldk, n, h->ldk, p, out, ld, h->syrk_ws, h->syrk_ws_bytes,
+                            h->stream));
     return PC_OK;
 }
 
@@ -606,9 +629,9 @@ static pc_status materialize_c64(pc_handle *h)
     if (h->nblk) {
         // batched problems: each diagonal block from its own samples
         for (int i = 0; i < h->nblk; ++i)
-            if (pc_status r = syrk64_block(h, h->boff[i], h->bn[i], h->boff[i + 1] - h->boff[i])) return r;
+            if (pc_status r = syrk64_block(h, h->boff[i], h->bn[i], h->boff[i + 1] - h->boff[i], i)) return r;
     } else {
-        if (pc_status r = syrk64_block(h, 0, h->n, h->p)) return r;
+        if (pc_status r = syrk64_block(h, 0, h->n, h->p, -1)) return r;
     }
     h->c64_full = true;
     return PC_OK;
@@ -682,13 +705,14 @@ static pc_status corr_impl(pc_handle *h, const void *X, int32_t dtype, int64_t l
     h->c64_full = false;
     if (blk >= 0) {
         if (h->precision == 0) {
-            if (pc_status r = syrk64_block(h, o, n, p)) return r;
+            if (pc_status r = syrk64_block(h, o, n, p, blk)) return r;
         } else {
             if (!h->c64_valid) {
-                CK(dalloc(h, &h->c64_valid, (size_t)h->p * h->p));
-                CK(cudaMemsetAsync(h->c64_valid, 0, (size_t)h->p * h->p, s));
+                CK(dalloc(h, &h->c64_valid, h->pair_elems));
+                CK(cudaMemsetAsync(h->c64_valid, 0, h->pair_elems, s));
             }
-            CK(fpc::launch_c64_lazy_init_block(h->C64, h->ldc, h->c64_valid, h->p, o, p, s));
+            CK(fpc::launch_c64_lazy_init_block(h->C64 + h->pbase[blk], p, h->c64_valid + h->pbase[blk], p, 0, p,
+                                               s));
         }
     } else if (h->precision == 0 || h->order == 1) {
         if (pc_status r = materialize_c64(h)) return r;
@@ -696,10 +720,12 @@ static pc_status corr_impl(pc_handle *h, const void *X, int32_t dtype, int64_t l
         if (!h->c64_valid) CK(dalloc(h, &h->c64_valid, (size_t)p * p));
         CK(fpc::launch_c64_lazy_init(h->C64, h->ldc, h->c64_valid, p, s));
     }
-    float *C32b = h->C32 + (size_t)o * h->ldc + o;
+    // this problem's correlation block and its leading dimension
+    float *C32b = blk < 0 ? h->C32 : h->C32 + h->pbase[blk];
+    const int ldb = blk < 0 ? h->ldc : p;
     bool tc = false;
     if (h->precision == 0) {
-        if (blk >= 0) CK(fpc::launch_cast_block(h->C64, h->C32, h->ldc, o, p, s));
+        if (blk >= 0) CK(fpc::launch_cast_block(h->C64 + h->pbase[blk], h->C32 + h->pbase[blk], p, 0, p, s));
         else CK(fpc::launch_cast_c(h->C64, h->C32, p, h->ldc, s));
     } else if (h->precision == 1 || !want_bf16) {
         if (h->precision == 2) {
@@ -707,7 +733,7 @@ static pc_status corr_impl(pc_handle *h, const void *X, int32_t dtype, int64_t l
             CK(fpc::launch_standardize(Xd, dtype, n, p, ld, h->mean + o, h->rsd + o, nullptr, h->Xs32 + po,
                                        nullptr, nullptr, h->ldk, s));
         }
-        CK(fpc::launch_syrk_f32(h->Xs32 + po, n, h->ldk, p, C32b, h->ldc, s));
+        CK(fpc::launch_syrk_f32(h->Xs32 + po, n, h->ldk, p, C32b, ldb, s));
     } else {
         const size_t need = fpc::corr_bf16x3_ws_bytes(n, p);
         if (need > h->tc_ws_bytes) {
@@ -717,7 +743,7 @@ static pc_status corr_impl(pc_handle *h, const void *X, int32_t dtype, int64_t l
             h->tc_ws_bytes = need;
         }
         if (blk <= 0) CK(cudaMemsetAsync(h->tc_err, 0, sizeof(int), s));
-        CK(fpc::launch_corr_bf16x3(h->Xhi + po, h->Xlo + po, n, h->ldk, p, C32b, h->ldc, h->tc_ws,
+        CK(fpc::launch_corr_bf16x3(h->Xhi + po, h->Xlo + po, n, h->ldk, p, C32b, ldb, h->tc_ws,
                                    h->tc_ws_bytes, h->tc_err, s));
         tc = true;
     }
@@ -764,12 +790,36 @@ extern "C" pc_status pc_corr_get(pc_handle *h, float *C32, double *C64)
         Timed tm(h, 0);
         if (pc_status r = materialize_c64(h)) return r;
     }
-    if (C32)
-        CK(cudaMemcpy2DAsync(C32, p * sizeof(float), h->C32, h->ldc * sizeof(float),
-                             p * sizeof(float), p, cudaMemcpyDefault, s));
-    if (C64)
-        CK(cudaMemcpy2DAsync(C64, p * sizeof(double), h->C64, h->ldc * sizeof(double),
-                             p * sizeof(double), p, cudaMemcpyDefault, s));
+    if (h->nblk) {
+        // batched problems: the dense p x p matrix, zero off the diagonal blocks
+        auto unpack = [&](void *dst, const void *src, size_t esz) -> cudaError_t {
+            if (is_device_ptr(dst)) {
+                cudaError_t e = cudaMemsetAsync(dst, 0, (size_t)p * p * esz, s);
+                if (e != cudaSuccess) return e;
+            } else {
+                cudaError_t e = cudaStreamSynchronize(s);
+                if (e != cudaSuccess) return e;
+                std::memset(dst, 0, (size_t)p * p * esz);
+            }
+            for (int i = 0; i < h->nblk; ++i) {
+                const int o = h->boff[i], pb = h->boff[i + 1] - o;
+                cudaError_t e = cudaMemcpy2DAsync((char *)dst + ((size_t)o * p + o) * esz, (size_t)p * esz,
+                                                  (const char *)src + (size_t)h->pbase[i] * esz, (size_t)pb * esz,
+                                                  (size_t)pb * esz, pb, cudaMemcpyDefault, s);
+                if (e != cudaSuccess) return e;
+            }
+            return cudaSuccess;
+        };
+        if (C32) CK(unpack(C32, h->C32, sizeof(float)));
+        if (C64) CK(unpack(C64, h->C64, sizeof(double)));
+    } else {
+        if (C32)
+            CK(cudaMemcpy2DAsync(C32, p * sizeof(float), h->C32, h->ldc * sizeof(float),
+                                 p * sizeof(float), p, cudaMemcpyDefault, s));
+        if (C64)
+            CK(cudaMemcpy2DAsync(C64, p * sizeof(double), h->C64, h->ldc * sizeof(double),
+                                 p * sizeof(double), p, cudaMemcpyDefault, s));
+    }
     CK(cudaStreamSynchronize(s));
     return check_tc(h);
 }
@@ -1009,7 +1059,7 @@ static pc_status skeleton_enqueue(pc_handle *h)
     cudaStream_t s = h->stream;
     const int p = h->p;
     const long long n = h->n;
-    const size_t pp = (size_t)p * p;
+    const size_t pp = h->pair_elems;
     TestParams tp = make_tp(h);
     const bool timed = h->timing != 0;
     const bool graph = h->use_graph && !timed;
@@ -1143,8 +1193,9 @@ static pc_status skeleton_complete(pc_handle *h, pc_stats *st, bool *overflow)
     CK(cudaEventRecord(h->ev1, s));
     if (h->learned) {
         // largest stage run: the first one in the reversed order, the last one conventionally
+        Timed tm(h, h->timing ? 6 : -1);
         const int lmax = h->order == 1 ? h->info_h->first_level : h->info_h->l - 1;
-        CK(fpc::launch_reverify(g, tp, h->C64, h->ldc, lmax, s));
+        CK(fpc::launch_reverify(g, tp, h->C32, h->C64, h->ldc, lmax, s));
     }
     if (pc_status r = read_info(h)) return r;
     if (!h->info_h->done) return fail(h, PC_ERR_INTERNAL, "stage loop did not finish");
@@ -1178,6 +1229,7 @@ static pc_status skeleton_complete(pc_handle *h, pc_stats *st, bool *overflow)
     st->stage_a_ran = I.stage_a_ran;
     st->levels_run = I.levels_run;
     st->first_level = I.first_level;
+    st->queue_overflows = c.queue_overflows;
     st->flops_class[1] = (double)c.flops_stagea + (I.stage_a_ran ? (double)p * p * p : 0.0);
     st->flops_class[2] = (double)c.flops_prec;
     st->flops_class[3] = (double)c.flops + (double)c.flops64_direct;
@@ -1197,7 +1249,21 @@ static pc_status skeleton_run(pc_handle *h, pc_stats *st)
     for (int attempt = 0; attempt < 6; ++attempt) {
         bool overflow = false;
         if (pc_status r = skeleton_once(h, st, &overflow)) return r;
-        if (!overflow) return PC_OK;
+        if (!overflow) {
+            // an overflowing FP64 re-decision queue made a stage re-run all its
+            // tests on the warp-per-test kernel (correct, slow): a larger queue
+            // for the later runs of this handle, up to 2^28 entries (2 GiB)
+            if (st->queue_overflows > 0 && h->rq_cap < (1ull << 28)) {
+                ull *nq = nullptr;
+                const ull cap = h->rq_cap * 4;
+                if (dalloc(h, &nq, (size_t)cap * sizeof(ull)) == cudaSuccess) {
+                    dfree(h, h->rq);
+                    h->rq = nq;
+                    h->rq_cap = cap;
+                }
+            }
+            return PC_OK;
+        }
         // the sepset pool was too small: enlarge it and run again (deterministic)
         int *np = nullptr;
         long long cap = h->g.pool_cap * 4;
@@ -1358,16 +1424,33 @@ extern "C" pc_status pc_skeleton_many(pc_handle **hs, int32_t count, uint8_t **a
     return first;
 }
 
+// every pair a < b of the handle's problem(s) in ascending (a, b) with its
+// index in the per-pair arrays
+template <class F>
+static void for_pairs(const pc_handle *h, F fn)
+{
+    if (!h->nblk) {
+        const int p = h->p;
+        for (int a = 0; a < p; ++a)
+            for (int b = a + 1; b < p; ++b) fn(a, b, (size_t)a * p + b);
+        return;
+    }
+    for (int i = 0; i < h->nblk; ++i) {
+        const int o = h->boff[i], pb = h->boff[i + 1] - o;
+        for (int a = o; a < o + pb; ++a)
+            for (int b = a + 1; b < o + pb; ++b)
+                fn(a, b, (size_t)h->pbase[i] + (size_t)(a - o) * pb + (b - o));
+    }
+}
+
 extern "C" pc_status pc_sepsets_count(pc_handle *h, int64_t *n_removed, int64_t *pool_len)
 {
     if (!h) return PC_ERR_ARG;
     if (!h->have_skel) return fail(h, PC_ERR_STATE, "no skeleton yet");
-    const int p = h->p;
-    std::vector<int> lv((size_t)p * p);
+    std::vector<int> lv(h->pair_elems);
     CK(cudaMemcpy(lv.data(), h->g.sep_level, lv.size() * sizeof(int), cudaMemcpyDeviceToHost));
     long long cnt = 0;
-    for (int a = 0; a < p; ++a)
-        for (int b = a + 1; b < p; ++b) cnt += lv[(size_t)a * p + b] >= 0;
+    for_pairs(h, [&](int, int, size_t e) { cnt += lv[e] >= 0; });
     if (n_removed) *n_removed = cnt;
     if (pool_len) {
         ull pl = 0;
@@ -1382,8 +1465,7 @@ extern "C" pc_status pc_sepsets_get(pc_handle *h, int32_t *pairs, int32_t *level
 {
     if (!h) return PC_ERR_ARG;
     if (!h->have_skel) return fail(h, PC_ERR_STATE, "no skeleton yet");
-    const int p = h->p;
-    const size_t pp = (size_t)p * p;
+    const size_t pp = h->pair_elems;
     std::vector<int> lv(pp), sd(pp);
     std::vector<long long> rk(pp), of(pp);
     CK(cudaMemcpy(lv.data(), h->g.sep_level, pp * sizeof(int), cudaMemcpyDeviceToHost));
@@ -1391,17 +1473,15 @@ extern "C" pc_status pc_sepsets_get(pc_handle *h, int32_t *pairs, int32_t *level
     CK(cudaMemcpy(rk.data(), h->g.sep_rank, pp * sizeof(long long), cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(of.data(), h->g.sep_off, pp * sizeof(long long), cudaMemcpyDeviceToHost));
     long long k = 0;
-    for (int a = 0; a < p; ++a)
-        for (int b = a + 1; b < p; ++b) {
-            size_t e = (size_t)a * p + b;
-            if (lv[e] < 0) continue;
-            if (pairs) { pairs[2 * k] = a; pairs[2 * k + 1] = b; }
-            if (level) level[k] = lv[e];
-            if (side) side[k] = sd[e];
-            if (rank) rank[k] = rk[e];
-            if (off) off[k] = of[e];
-            ++k;
-        }
+    for_pairs(h, [&](int a, int b, size_t e) {
+        if (lv[e] < 0) return;
+        if (pairs) { pairs[2 * k] = a; pairs[2 * k + 1] = b; }
+        if (level) level[k] = lv[e];
+        if (side) side[k] = sd[e];
+        if (rank) rank[k] = rk[e];
+        if (off) off[k] = of[e];
+        ++k;
+    });
     if (pool) {
         ull pl = 0;
         CK(cudaMemcpy(&pl, &h->g.ctr->pool_len, sizeof(ull), cudaMemcpyDeviceToHost));
@@ -1481,8 +1561,8 @@ extern "C" pc_status pc_mlp_features(pc_handle *h, const int32_t *quads, int64_t
     if (!h->have_corr) return fail(h, PC_ERR_STATE, "pc_mlp_features before pc_corr");
     if (R == 0) return PC_OK;
     CK(cudaMemsetAsync(h->mlp_err, 0, sizeof(int), h->stream));
-    CK(fpc::launch_mlp_features(quads, R, h->C32, h->ldc, h->p, h->n, h->g.nvec, h->q, feats, h->mlp_err,
-                                h->stream));
+    CK(fpc::launch_mlp_features(quads, R, h->C32, h->ldc, h->g.prow, h->p, h->n, h->g.nvec, h->q, feats,
+                                h->mlp_err, h->stream));
     int e = 0;
     CK(cudaMemcpyAsync(&e, h->mlp_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));

@@ -32,6 +32,7 @@ struct DevCounters {
     unsigned long long flops_stagea;   // closed-form stage l = p-2 (FP64)
     unsigned int max_dz_bits;          // float bits of max |z32 - z64|
     int status;                        // device-side error (pc_status value)
+    int queue_overflows;               // stages whose FP64 re-decision queue overflowed
 };
 
 // Per-stage scalars: the stage index lives on the device so that the whole
@@ -92,6 +93,11 @@ struct GraphDev {
     // the node range [blk_lo[u], blk_hi[u]) of u's instance; null for one problem
     const int *blk_lo, *blk_hi;
     const long long *nvec;      // batched problems: samples of each node's instance
+    // batched problems: per-pair arrays (best, sep_*, prec_pos, c64 flags) and the
+    // correlation matrices hold only the diagonal blocks, packed; pair (a, c) of one
+    // instance is at prow[a] + c and the neighbour list of a at nrow[a].  Null for
+    // one problem: a * p + c (a * ldc + c for the correlation matrices).
+    const long long *prow, *nrow;
     unsigned char *scored;      // learned order: per stage, 1 if its sets ran in the proposed order
     int *sep_level;             // p x p (a<b at a*p+b), -1 none
     int *sep_side;
@@ -118,6 +124,7 @@ struct GraphDev {
 struct TestParams {
     long long n;        // samples
     const long long *nvec;  // batched problems: samples of each node's instance (null: n)
+    const long long *prow;  // batched problems: packed row bases of the correlation blocks
     double q;           // threshold Phi^{-1}(1-alpha/2)
     float qf;
     double band;        // |z - q| band for FP64 re-decision
@@ -218,9 +225,11 @@ cudaError_t launch_mlp_backward(const float *feats, const float *labels, const f
                                 const __nv_bfloat16 *h1, const float *h2, long long R, float inv_b,
                                 const float *theta, float *grad, double *loss, cudaStream_t s);
 cudaError_t launch_adam(float *theta, const float *grad, float *m, float *v, float lr, int step, cudaStream_t s);
-cudaError_t launch_mlp_features(const int *quads, long long R, const float *C32, int ldc, int p, long long n,
-                                const long long *nvec, double q, float *feats, int *err, cudaStream_t s);
-cudaError_t launch_reverify(GraphDev g, TestParams tp, const double *C64, int ldc, int lmax, cudaStream_t s);
+cudaError_t launch_mlp_features(const int *quads, long long R, const float *C32, int ldc, const long long *prow,
+                                int p, long long n, const long long *nvec, double q, float *feats, int *err,
+                                cudaStream_t s);
+cudaError_t launch_reverify(GraphDev g, TestParams tp, const float *C32, const double *C64, int ldc, int lmax,
+                            cudaStream_t s);
 
 // ---- raw test batches (level.cu)
 cudaError_t launch_ci_list(const int *ij, const int *S, int l, long long b, const float *C32,

@@ -97,7 +97,7 @@ __global__ void degrees_kernel(GraphDev g)
         int pos = base + incl - c;
         while (bits) {
             int t = __ffs(bits) - 1;
-            g.nbr[(long long)u * g.p + pos++] = w * 32 + t;
+            g.nbr[nidx(g, u) + pos++] = w * 32 + t;
             bits &= bits - 1;
         }
         base += __shfl_sync(0xffffffffu, incl, 31);
@@ -509,7 +509,7 @@ __device__ __noinline__ void ensure_c64(const int *nd, int m, const TestParams &
             const int c = e - i * (i + 1) / 2;
             a = nd[i];
             b = nd[c];
-            miss = a != b && !valid[(long long)a * tp.p + b];
+            miss = a != b && !valid[cidx(tp.prow, tp.p, a, b)];
         }
         unsigned bal = __ballot_sync(0xffffffffu, miss);
         while (bal) {
@@ -517,16 +517,35 @@ __device__ __noinline__ void ensure_c64(const int *nd, int m, const TestParams &
             const int aa = __shfl_sync(0xffffffffu, a, src), bb = __shfl_sync(0xffffffffu, b, src);
             const double *xa = tp.xs64 + (long long)aa * tp.ldk, *xb = tp.xs64 + (long long)bb * tp.ldk;
             const long long na = n_of(tp, aa);
-            double acc = 0.0;
-            for (long long t = lane; t < na; t += 32) acc = fma(xa[t], xb[t], acc);
+            // rows start 512-byte aligned (ldk is a multiple of 64): 16-byte loads,
+            // four independent FMA chains per lane
+            const double2 *xa2 = (const double2 *)xa, *xb2 = (const double2 *)xb;
+            const long long nh = na >> 1;
+            double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
+            long long t = lane;
+            for (; t + 32 < nh; t += 64) {
+                const double2 a0 = __ldg(xa2 + t), b0 = __ldg(xb2 + t);
+                const double2 a1 = __ldg(xa2 + t + 32), b1 = __ldg(xb2 + t + 32);
+                acc0 = fma(a0.x, b0.x, acc0);
+                acc1 = fma(a0.y, b0.y, acc1);
+                acc2 = fma(a1.x, b1.x, acc2);
+                acc3 = fma(a1.y, b1.y, acc3);
+            }
+            if (t < nh) {
+                const double2 a0 = __ldg(xa2 + t), b0 = __ldg(xb2 + t);
+                acc0 = fma(a0.x, b0.x, acc0);
+                acc1 = fma(a0.y, b0.y, acc1);
+            }
+            if ((na & 1) && lane == 0) acc0 = fma(xa[na - 1], xb[na - 1], acc0);
+            double acc = (acc0 + acc1) + (acc2 + acc3);
             for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
             if (lane == 0) {
                 const double v = acc / (double)na;
-                C64[(long long)aa * ldc + bb] = v;
-                C64[(long long)bb * ldc + aa] = v;
+                C64[cidx(tp.prow, ldc, aa, bb)] = v;
+                C64[cidx(tp.prow, ldc, bb, aa)] = v;
                 __threadfence();
-                valid[(long long)aa * tp.p + bb] = 1;
-                valid[(long long)bb * tp.p + aa] = 1;
+                valid[cidx(tp.prow, tp.p, aa, bb)] = 1;
+                valid[cidx(tp.prow, tp.p, bb, aa)] = 1;
             }
             bal &= bal - 1;
         }
@@ -551,7 +570,7 @@ __device__ __forceinline__ bool warp_test(const int *nd, int m, int l, const flo
     if (!F64) {
         float *M = (float *)Mbuf;
         for (int i = 0; i < m; ++i)
-            for (int c = lane; c <= i; c += 32) M[i * ms + c] = C32[(long long)nd[i] * ldc + nd[c]];
+            for (int c = lane; c <= i; c += 32) M[i * ms + c] = C32[cidx(tp.prow, ldc, nd[i], nd[c])];
         __syncwarp();
         float pmin;
         bool bad;
@@ -586,7 +605,7 @@ __device__ __forceinline__ bool warp_test(const int *nd, int m, int l, const flo
         if (tp.lazy) ensure_c64(nd, m, tp, (double *)C64, ldc);
         for (int i = 0; i < m; ++i)
             for (int c = lane; c <= i; c += 32) {
-                const long long o = (long long)nd[i] * ldc + nd[c];
+                const long long o = cidx(tp.prow, ldc, nd[i], nd[c]);
                 M[i * ms + c] = tp.lazy ? ((volatile const double *)C64)[o] : C64[o];
             }
         __syncwarp();
@@ -636,7 +655,7 @@ __device__ __forceinline__ int cand_node(const GraphDev &g, int u, int j, int d,
         const ull b = g.row_off[u];
         if (g.row_off[u + 1] > b) return g.perm[b + (ull)j * d + x];
     }
-    return g.nbr[(long long)u * g.p + x + (x >= j)];
+    return g.nbr[nidx(g, u) + x + (x >= j)];
 }
 
 __device__ __forceinline__ void sort_small(int *a, int n)
@@ -679,11 +698,11 @@ __global__ void __launch_bounds__(256) ci_direct_kernel(GraphDev g, TestParams t
         int u, j, d;
         ull rank;
         locate_test(g, g.tn_off, l, t, u, j, d, rank);
-        const int v = g.nbr[(long long)u * p + j];
+        const int v = g.nbr[nidx(g, u) + j];
         const int side = u > v;
         const int a = min(u, v), b = max(u, v);
         const ull key = ((ull)side << 62) | rank;
-        ull *bp = g.best + (long long)a * p + b;
+        ull *bp = g.best + pidx(g, a, b);
         if (*(volatile ull *)bp < key) continue;   // an earlier set already separates
         if (lane == 0) {
             unrank_lex(rank, d, l, g.binom, g.ldb, pos);
@@ -793,16 +812,16 @@ __device__ __forceinline__ void lane_tests_lex(const GraphDev &g, const TestPara
     const int p = g.p;
     const float sqf = sqrtf((float)(n_of(tp, u) - L - 3));
     const float rq = tanhf(tp.qf / sqf);                 // |r| threshold of this stage
-    const int *nb = g.nbr + (long long)u * p;
+    const int *nb = g.nbr + nidx(g, u);
     const int v = nb[j];
     // proposal order: position x of the enumeration is the node perm[x]
     const short *pr = nullptr;
     if (PROP && g.row_off && g.row_off[u + 1] > g.row_off[u]) pr = g.perm + g.row_off[u] + (ull)j * d;
     auto member = [&](int x) -> int { return (PROP && pr) ? (int)pr[x] : nb[x + (x >= j)]; };
     const int side = u > v;
-    ull *bp = g.best + (long long)min(u, v) * p + max(u, v);
+    ull *bp = g.best + pidx(g, min(u, v), max(u, v));
     const ull tbase = g.tn_off[u] + (ull)j * T;
-    const float *Cu = C32 + (long long)u * ldc, *Cv = C32 + (long long)v * ldc;
+    const float *Cu = C32 + cidx(tp.prow, ldc, u, 0), *Cv = C32 + cidx(tp.prow, ldc, v, 0);
     const float cuv = __ldg(Cu + v);
     int pos[L > 0 ? L : 1];
     unrank_lex(rank, d, L, g.binom, g.ldb, pos);
@@ -825,7 +844,7 @@ __device__ __forceinline__ void lane_tests_lex(const GraphDev &g, const TestPara
             for (int i = 0; i < K; ++i) sp[i] = member(pos[i]);
 #pragma unroll
             for (int i = 0; i < K; ++i) {
-                const float *Ci = C32 + (long long)sp[i] * ldc;
+                const float *Ci = C32 + cidx(tp.prow, ldc, sp[i], 0);
                 float dd = 1.f;
 #pragma unroll
                 for (int c = 0; c < i; ++c) {
@@ -865,7 +884,7 @@ __device__ __forceinline__ void lane_tests_lex(const GraphDev &g, const TestPara
         bool bad = pbad;
         if (L > 0) {
             const int s = member(pos[L - 1]);
-            const float *Cs = C32 + (long long)s * ldc;
+            const float *Cs = C32 + cidx(tp.prow, ldc, s, 0);
             float ls[KA];
             float x = 1.f;
 #pragma unroll
@@ -1016,7 +1035,10 @@ __global__ void __launch_bounds__(256) ci_redecide_kernel(GraphDev g, TestParams
     // A full queue dropped tests: the direct kernel that follows then re-runs the
     // whole stage (FP32 first, FP64 inline), so no test goes undecided.  Keys
     // already set here are keys of independent tests, hence still valid minima.
-    if (*qlen > qcap && blockIdx.x == 0 && threadIdx.x == 0) g.info->lane_overflow = 1;
+    if (*qlen > qcap && blockIdx.x == 0 && threadIdx.x == 0) {
+        g.info->lane_overflow = 1;
+        atomicAdd(&g.ctr->queue_overflows, 1);
+    }
     const double sq = sqrt((double)(tp.n - l - 3));
     WarpAcc acc = {0, 0, 0, 0, 0, 0, 0, 0.f};
     for (ull qi = (blockIdx.x * (ull)blockDim.x + threadIdx.x) >> 5; qi < nq;
@@ -1025,10 +1047,10 @@ __global__ void __launch_bounds__(256) ci_redecide_kernel(GraphDev g, TestParams
         int u, j, d;
         ull rank;
         locate_test(g, g.tn_off, l, t, u, j, d, rank);
-        const int v = g.nbr[(long long)u * p + j];
+        const int v = g.nbr[nidx(g, u) + j];
         const int side = u > v;
         const ull key = ((ull)side << 62) | rank;
-        ull *bp = g.best + (long long)min(u, v) * p + max(u, v);
+        ull *bp = g.best + pidx(g, min(u, v), max(u, v));
         if (*(volatile ull *)bp < key) continue;
         if (lane == 0) {
             unrank_lex(rank, d, l, g.binom, g.ldb, pos);
@@ -1073,18 +1095,18 @@ __global__ void __launch_bounds__(128) ci_complement_kernel(GraphDev g, TestPara
         int u, j, d;
         ull rank;
         locate_test(g, g.cn_off, l, t, u, j, d, rank);
-        const int v = g.nbr[(long long)u * p + j];
+        const int v = g.nbr[nidx(g, u) + j];
         const int k = d - l;
         const int side = u > v;
         const int a = min(u, v), b = max(u, v);
         const ull key = ((ull)side << 62) | rank;
-        ull *bp = g.best + (long long)a * p + b;
+        ull *bp = g.best + pidx(g, a, b);
         if (*(volatile ull *)bp < key) continue;
         const ull T = g.binom[(long long)d * g.ldb + l];
         int posR[KC_MAX];
         unrank_lex(T - 1 - rank, d, k, g.binom, g.ldb, posR);   // complement of lex is reverse lex
         const double *P = g.prec + (long long)u * PREC_MAX * PREC_MAX;
-        const short *ps = g.prec_pos + (long long)u * p;
+        const short *ps = g.prec_pos + pidx(g, u, 0);
         const int su = ps[u], sv = ps[v];
         int sr[KC_MAX];
         for (int i = 0; i < k; ++i) sr[i] = ps[cand_node(g, u, j, d, posR[i])];
@@ -1169,7 +1191,7 @@ __global__ void __launch_bounds__(512) prec_update_kernel(GraphDev g, const doub
         int *rem = mem;
         double *P = g.prec + (long long)u * PREC_MAX * PREC_MAX;
         const int *pm = g.prec_mem + (long long)u * PREC_MAX;
-        const short *pos = g.prec_pos + (long long)u * p;
+        const short *pos = g.prec_pos + pidx(g, u, 0);
         const uint32_t *row = g.adj + (long long)u * g.W;
         // members deleted by the last commit, ascending slots (same in every chunk)
         if (threadIdx.x < 32) {
@@ -1242,7 +1264,7 @@ __global__ void __launch_bounds__(512) prec_update_kernel(GraphDev g, const doub
     if (threadIdx.x == 0) {
         bad = 0;
         int o = 0;
-        const int *nb = g.nbr + (long long)u * p;
+        const int *nb = g.nbr + nidx(g, u);
         const int dg = g.deg[u];
         bool placed = false;
         for (int i = 0; i < dg; ++i) {
@@ -1257,7 +1279,7 @@ __global__ void __launch_bounds__(512) prec_update_kernel(GraphDev g, const doub
     __syncthreads();
     double *A = smd, *colk = A + m * m;
     for (int i = threadIdx.x >> 5; i < m; i += blockDim.x >> 5)
-        for (int c = threadIdx.x & 31; c < m; c += 32) A[i * m + c] = C64[(long long)mem[i] * ldc + mem[c]];
+        for (int c = threadIdx.x & 31; c < m; c += 32) A[i * m + c] = C64[cidx(g.prow, ldc, mem[i], mem[c])];
     __syncthreads();
     sweep_inverse_block(A, m, m, colk, &bad);     // A = -corr[F,F]^{-1}
     __syncthreads();
@@ -1270,13 +1292,13 @@ __global__ void __launch_bounds__(512) prec_update_kernel(GraphDev g, const doub
     }
     double *P = g.prec + (long long)u * PREC_MAX * PREC_MAX;
     // a block rebuilt after being dropped: clear the stale slot map first
-    for (int w = threadIdx.x; w < p; w += blockDim.x) g.prec_pos[(long long)u * p + w] = -1;
+    for (int w = threadIdx.x; w < p; w += blockDim.x) g.prec_pos[pidx(g, u, w)] = -1;
     __syncthreads();
     for (int i = threadIdx.x >> 5; i < m; i += blockDim.x >> 5)
         for (int c = threadIdx.x & 31; c < m; c += 32) P[i * PREC_MAX + c] = -A[i * m + c];
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
         g.prec_mem[(long long)u * PREC_MAX + i] = mem[i];
-        g.prec_pos[(long long)u * p + mem[i]] = (short)i;
+        g.prec_pos[pidx(g, u, mem[i])] = (short)i;
     }
     if (threadIdx.x == 0) {
         g.prec_m[u] = m;
@@ -1294,7 +1316,7 @@ __global__ void prec_mark_kernel(GraphDev g)
     if (m0 <= 0) return;
     const int p = g.p;
     const int *pm = g.prec_mem + (long long)u * PREC_MAX;
-    short *pos = g.prec_pos + (long long)u * p;
+    short *pos = g.prec_pos + pidx(g, u, 0);
     const uint32_t *row = g.adj + (long long)u * g.W;
     for (int s = threadIdx.x; s < m0; s += blockDim.x) {
         const int w = pm[s];
@@ -1318,9 +1340,9 @@ __global__ void commit_kernel(GraphDev g, int l_fixed, int explicit_sets, int co
          o += (long long)gridDim.x * blockDim.x) {
         const int u = (int)(upper_bound_dev(g.ooff, (long long)p + 1, o) - 1);
         const int j = (int)(o - g.ooff[u]);
-        const int v = g.nbr[(long long)u * p + j];
+        const int v = g.nbr[nidx(g, u) + j];
         if (u > v) continue;
-        const long long e = (long long)u * p + v;
+        const long long e = pidx(g, u, v);
         const ull key = g.best[e];
         g.best[e] = KEY_NONE;                         // ready for the next stage
         if (count_canonical) {
@@ -1352,9 +1374,9 @@ __global__ void commit_kernel(GraphDev g, int l_fixed, int explicit_sets, int co
                 continue;
             }
             const int su = side ? v : u;
-            const int jj = side ? lower_bound_int(g.nbr + (long long)v * p, g.deg[v], u) : j;
+            const int jj = side ? lower_bound_int(g.nbr + nidx(g, v), g.deg[v], u) : j;
             const int dd = g.deg[su] - 1;
-            const int *nb = g.nbr + (long long)su * p;
+            const int *nb = g.nbr + nidx(g, su);
             const int kd = dd - l;                        // dropped members
             if (kd <= KC_MAX && kd < l) {
                 // expand through the complement: R = the kd dropped positions, at lex
@@ -1397,8 +1419,9 @@ __global__ void commit_kernel(GraphDev g, int l_fixed, int explicit_sets, int co
 // Every explicit separating set recorded in the sepset store is tested again in
 // FP64 from the FP64 correlation matrix (one warp per removed pair); a set that
 // does not come out independent sets the device status (PC_ERR_INTERNAL).
-__global__ void __launch_bounds__(256) reverify_kernel(GraphDev g, TestParams tp, const double *C64, int ldc,
-                                                       int mmax, int ms, int per_warp_bytes)
+__global__ void __launch_bounds__(256) reverify_kernel(GraphDev g, TestParams tp, const float *C32,
+                                                       const double *C64, int ldc, int mmax, int ms,
+                                                       int per_warp_bytes)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -1406,14 +1429,14 @@ __global__ void __launch_bounds__(256) reverify_kernel(GraphDev g, TestParams tp
     double *Mbuf = (double *)mine;
     int *nd = (int *)(mine + (size_t)mmax * ms * sizeof(double));
     const int p = g.p;
-    const long long npairs = (long long)p * p;
     const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     WarpAcc acc = {0, 0, 0, 0, 0, 0, 0, 0.f};
     ull fails = 0;
-    for (long long e = gw; e < npairs; e += nw) {
-        const int a = (int)(e / p), b = (int)(e % p);
-        if (a >= b) continue;
+    // pair (a, b), a < b within a's instance: row a of the pair arrays
+    for (long long a_ = gw; a_ < p; a_ += nw)
+    for (int b = (int)a_ + 1, a = (int)a_, bend = g.blk_hi ? g.blk_hi[a] : p; b < bend; ++b) {
+        const long long e = pidx(g, a, b);
         const int l = g.sep_level[e];
         const long long off = g.sep_off[e];
         if (l < 0 || off < 0 || l + 2 > mmax) continue;
@@ -1427,7 +1450,12 @@ __global__ void __launch_bounds__(256) reverify_kernel(GraphDev g, TestParams tp
         const double sq = sqrt((double)(n_of(tp, a) - l - 3));
         double r;
         float z;
-        const bool ind = warp_test<true>(nd, l + 2, l, nullptr, C64, ldc, tp, sq, (float)sq, Mbuf, ms, acc, r, z);
+        // FP32 with the error model's guard and band, FP64 where they require it
+        // (FP64 throughout in the FP64 mode): the warp-per-test evaluation, members
+        // in ascending order, independent of the kernel that found the set
+        const bool ind = tp.precision == 0
+                             ? warp_test<true>(nd, l + 2, l, nullptr, C64, ldc, tp, sq, (float)sq, Mbuf, ms, acc, r, z)
+                             : warp_test<false>(nd, l + 2, l, C32, C64, ldc, tp, sq, (float)sq, Mbuf, ms, acc, r, z);
         if (!ind) ++fails;
         __syncwarp();
     }
@@ -1633,7 +1661,8 @@ cudaError_t launch_commit(GraphDev g, long long n_opairs_cap, int l_fixed, int e
     return cudaGetLastError();
 }
 
-cudaError_t launch_reverify(GraphDev g, TestParams tp, const double *C64, int ldc, int lmax, cudaStream_t s)
+cudaError_t launch_reverify(GraphDev g, TestParams tp, const float *C32, const double *C64, int ldc, int lmax,
+                            cudaStream_t s)
 {
     // one warp's matrix holds the sets of the largest stage the search ran
     // (sets of more than 128 members are not re-tested)
@@ -1643,7 +1672,7 @@ cudaError_t launch_reverify(GraphDev g, TestParams tp, const double *C64, int ld
     size_t smem = (size_t)wpc * per_warp;
     cudaError_t e = cudaFuncSetAttribute(reverify_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    reverify_kernel<<<num_sms() * 2, wpc * 32, smem, s>>>(g, tp, C64, ldc, mmax, ms, per_warp); note_launch();
+    reverify_kernel<<<num_sms() * 2, wpc * 32, smem, s>>>(g, tp, C32, C64, ldc, mmax, ms, per_warp); note_launch();
     return cudaGetLastError();
 }
 

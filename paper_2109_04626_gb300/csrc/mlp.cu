@@ -42,10 +42,10 @@ __device__ __forceinline__ int sw128_off(int row, int col_bf16)
 // the FP32 correlation matrix: marginal correlations, first-order partial
 // correlations, the first-order test statistic relative to the threshold,
 // and the stage shape.
-__device__ __forceinline__ void member_features(const float *C, int ldc, int u, int v, int k, int l, int d,
-                                                float sqn_over_q, float *f)
+__device__ __forceinline__ void member_features(const float *C, int ldc, const long long *prow, int u, int v, int k,
+                                                int l, int d, float sqn_over_q, float *f)
 {
-    const float cuv = C[(long long)u * ldc + v], cuk = C[(long long)u * ldc + k], cvk = C[(long long)v * ldc + k];
+    const float cuv = C[cidx(prow, ldc, u, v)], cuk = C[cidx(prow, ldc, u, k)], cvk = C[cidx(prow, ldc, v, k)];
     const float e = 1e-6f;
     const float ruv_k = (cuv - cuk * cvk) * rsqrtf(fmaxf((1.f - cuk * cuk) * (1.f - cvk * cvk), e));
     const float ruk_v = (cuk - cuv * cvk) * rsqrtf(fmaxf((1.f - cuv * cuv) * (1.f - cvk * cvk), e));
@@ -112,10 +112,10 @@ __device__ __forceinline__ void row_features(const MlpRows &R, const GraphDev &g
     const int dg = g.deg[u], d = dg - 1;
     const long long w = row - (long long)R.row_off[u];
     const int j = (int)(w / d), x = (int)(w - (long long)j * d);
-    const int v = g.nbr[(long long)u * p + j];
-    const int k = g.nbr[(long long)u * p + x + (x >= j)];
+    const int v = g.nbr[nidx(g, u) + j];
+    const int k = g.nbr[nidx(g, u) + x + (x >= j)];
     const float sq = R.nvec ? sqrtf((float)R.nvec[u]) * R.inv_q : R.sqn_over_q;
-    member_features(R.C32, R.ldc, u, v, k, l, d, sq, f);
+    member_features(R.C32, R.ldc, g.prow, u, v, k, l, d, sq, f);
 }
 
 // Forward pass over rows [0, R): scores s, and for training h1 (BF16), h2 (FP32).
@@ -394,7 +394,7 @@ __global__ void perm_kernel(GraphDev g, const unsigned long long *row_off, const
                 const float sy = scores[base + y];
                 rank += (sy > sx) || (sy == sx && y < x);
             }
-            perm[base + rank] = (short)g.nbr[(long long)u * p + x + (x >= j)];   // node id
+            perm[base + rank] = (short)g.nbr[nidx(g, u) + x + (x >= j)];   // node id
         }
     }
 }
@@ -493,8 +493,8 @@ cudaError_t launch_adam(float *theta, const float *grad, float *m, float *v, flo
 
 // Member features for explicit quadruples (u, v, k, l | d << 16): candidate k
 // of the ordered pair (u, v) at stage l with candidate-set size d.
-__global__ void mlp_features_kernel(const int *quads, long long R, const float *C32, int ldc, int p, long long n,
-                                    const long long *nvec, float inv_q, float *feats, int *err)
+__global__ void mlp_features_kernel(const int *quads, long long R, const float *C32, int ldc, const long long *prow,
+                                    int p, long long n, const long long *nvec, float inv_q, float *feats, int *err)
 {
     const long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (r >= R) return;
@@ -505,14 +505,15 @@ __global__ void mlp_features_kernel(const int *quads, long long R, const float *
         return;
     }
     float f[NF];
-    member_features(C32, ldc, u, v, k, l, d, sqrtf((float)(nvec ? nvec[u] : n)) * inv_q, f);
+    member_features(C32, ldc, prow, u, v, k, l, d, sqrtf((float)(nvec ? nvec[u] : n)) * inv_q, f);
     for (int i = 0; i < NF; ++i) feats[r * NF + i] = f[i];
 }
 
-cudaError_t launch_mlp_features(const int *quads, long long R, const float *C32, int ldc, int p, long long n,
-                                const long long *nvec, double q, float *feats, int *err, cudaStream_t s)
+cudaError_t launch_mlp_features(const int *quads, long long R, const float *C32, int ldc, const long long *prow,
+                                int p, long long n, const long long *nvec, double q, float *feats, int *err,
+                                cudaStream_t s)
 {
-    mlp_features_kernel<<<(unsigned)((R + 255) / 256), 256, 0, s>>>(quads, R, C32, ldc, p, n, nvec,
+    mlp_features_kernel<<<(unsigned)((R + 255) / 256), 256, 0, s>>>(quads, R, C32, ldc, prow, p, n, nvec,
                                                                       (float)(1.0 / q), feats, err);
     note_launch();
     return cudaGetLastError();

@@ -102,7 +102,7 @@ __global__ void stage_a_decide_kernel(const double *P, int p, int ldp, const int
                 ind = z <= tp.q;
             }
             ++nt;
-            if (ind) g.best[(long long)a * p + b] = 0ull;
+            if (ind) g.best[pidx(g, a, b)] = 0ull;
         }
     if (nt) {
         atomicAdd(&g.ctr->tests_executed, nt);

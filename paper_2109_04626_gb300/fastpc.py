@@ -44,11 +44,11 @@ class pc_stats(ctypes.Structure):
         ("levels_run", ctypes.c_int32),
         ("stage_a_ran", ctypes.c_int32),
         ("first_level", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("queue_overflows", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:
-        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        d = {k: getattr(self, k) for k, _ in self._fields_}
         d["flops_class"] = list(self.flops_class)
         return d
 
