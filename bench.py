@@ -36,6 +36,18 @@ SM_COUNT, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.070
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_GHZ / 1000.0   # 80.5
 
 
+def measured_peaks():
+    """(bf16 TFLOP/s burst, HBM GB/s, source): the machine's measured peaks when the
+    file is present, else the fallback figures."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["bf16_tflops"]), float(d["hbm_gbs"]), "of measured"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, 6800.0, "of fallback"
+
+
 # DRAM bytes (read + write) per launch of a class's dominant kernel, from one
 # ncu capture of the current kernel (profiles/prec_update_p95_dense.md: two
 # launches of prec_update_kernel read 0.345 MB and 0.647 MB, wrote 0)
@@ -419,11 +431,25 @@ def run_ours(args):
                 "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
                 "class_ms": {c: tim[c][0] for c in cls}}
 
-    # plain GPU form: FP32 SIMT GEMM + FP32 direct tests only, one host-driven
-    # launch sequence per stage (no graph), lexicographic order
+    # the correlation step against the tensor roofline: useful flops n p (p+1) of the
+    # symmetric product (the BF16x3 split issues three products per useful one)
+    roofline_corr = None
+    if tim["corr"][0] > 0:
+        bf16, hbm, src = measured_peaks()
+        ach = n * p * (p + 1) / (tim["corr"][0] * 1e-3) / 1e12
+        roofline_corr = {"bound": "tensor", "kernel": "pc_corr (column statistics, standardisation, "
+                         "BF16x3 tcgen05 GEMM, FP64 split-K reduce)" if mixed_prec == 2 else "pc_corr",
+                         "achieved": ach, "peak": bf16, "unit": "TFLOP/s", "frac": ach / bf16,
+                         "issued_tflops": 3 * ach if mixed_prec == 2 else ach, "ms_per_step": tim["corr"][0],
+                         "peak_source": f"bf16 dense burst, {src}"}
+
+    # plain GPU form: FP32 SIMT GEMM, FP32 tests one warp per test (no rank-major
+    # small-stage kernel, no complement path), one host-driven launch sequence per
+    # stage (no graph), lexicographic order
     plain = None
     if not args.no_plain:
         pcp = make(1 if w["cfg"] != 1 else 0, 0, graph=0)
+        fp.pc_set_opt(pcp.h, "small_stage_kernel", 0)
         step(pcp)
         pms, stp = timed_steps(pcp, max(3, min(args.steps, 5)))
         plain = {"ms_per_step": pms, "value": stp["tests_canonical"] / (pms / 1000.0),
@@ -474,6 +500,7 @@ def run_ours(args):
                 "redecided": stats[-1]["tests_redecided"],
                 "complement_tests": stats[-1]["complement_tests"],
                 "roofline": roofline,
+                "roofline_corr": roofline_corr,
                 "autotune": tune,
                 "cpu_baseline": cpu,
                 "skeleton_matches_oracle": matches,

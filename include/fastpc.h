@@ -95,6 +95,9 @@ void pc_destroy(pc_handle *h);
  *                 WHILE node is driven by the device (default); 0 = host loop
  *   "stage_conds" 1 = inside that graph, conditional nodes skip the kernels a
  *                 stage has no work for (default); 0 = every kernel every stage
+ *   "small_stage_kernel" 1 = stages l <= 8 of the FP32 modes run on the
+ *                 rank-major one-thread-per-chunk kernel with bordered tests
+ *                 (default); 0 = every stage on the one-warp-per-test kernel
  *   "learned"     1 = enumerate the conditioning sets of every ordered pair in
  *                 the order proposed by the scoring network (needs parameters:
  *                 pc_mlp_set_params or pc_mlp_train); 0 = lexicographic (default)
@@ -103,6 +106,9 @@ void pc_destroy(pc_handle *h);
  *   "learned_min_tests" a stage is scored only if it schedules at least this
  *                 many tests (default 1e6); smaller stages run all their tests
  *                 in one wave, where the enumeration order saves nothing
+ *   "learned_min_ratio" ... and at least this many tests per score row (one
+ *                 row per candidate of a pair; default 8): at l = 1 a pair has
+ *                 as many sets as candidates and scoring costs as much as testing
  * Launch shape of the test kernels (set by pc_autotune; results never depend on it):
  *   "lane_chunk"  consecutive sets of one pair per thread in the kernel of the
  *                 stages l <= 8 (1..256, default 8)

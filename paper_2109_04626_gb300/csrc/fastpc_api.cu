@@ -52,6 +52,7 @@ struct pc_handle {
     // launch shape of the test kernels (pc_autotune)
     int lane_chunk = 8, lane_rounds = 32, lane_blocks = 8, direct_warps = 8;
     int stage_conds = 1;                 // conditional nodes in the captured stage body
+    int lane_stages = 1;                 // small stages on the rank-major small-stage kernel
     cudaStream_t stream = 0;
     std::string err;
     // correlation
@@ -111,6 +112,7 @@ struct pc_handle {
     unsigned char *scored = nullptr;   // per stage: 1 if it ran in the proposed order
     long long rows_cap = 0;
     double learned_min = 1.0e6;
+    double learned_ratio = 8.0;
     // per-kernel-class timing
     int timing = 0;
     std::vector<TimedPair> pending;
@@ -235,11 +237,13 @@ static TestParams make_tp(const pc_handle *h)
     tp.lane_rounds = h->lane_rounds;
     tp.lane_blocks = h->lane_blocks;
     tp.direct_warps = h->direct_warps;
+    tp.lane_stages = h->lane_stages;
     tp.precision = h->precision;
     tp.reversed = h->order == 1;
     tp.complement = h->complement;
     tp.lazy = h->c64_full ? 0 : 1;
     tp.learned_min = h->learned_min;
+    tp.learned_ratio = h->learned_ratio;
     tp.p = h->p;
     tp.xs64 = h->Xs64;
     tp.ldk = h->ldk;
@@ -501,6 +505,9 @@ extern "C" pc_status pc_set_opt(pc_handle *h, const char *key, double val)
     } else if (k == "learned_min_tests") {
         if (!(val >= 0)) return fail(h, PC_ERR_ARG, "learned_min_tests must be >= 0");
         h->learned_min = val;
+    } else if (k == "learned_min_ratio") {
+        if (!(val >= 0)) return fail(h, PC_ERR_ARG, "learned_min_ratio must be >= 0");
+        h->learned_ratio = val;
     } else if (k == "learned_rows") {
         if (!(val >= 0)) return fail(h, PC_ERR_ARG, "learned_rows must be >= 0");
         h->rows_cap = (long long)val;
@@ -510,6 +517,8 @@ extern "C" pc_status pc_set_opt(pc_handle *h, const char *key, double val)
         h->budget = val;
     } else if (k == "stage_conds") {
         h->stage_conds = val != 0;
+    } else if (k == "small_stage_kernel") {
+        h->lane_stages = val != 0;
     } else if (k == "lane_chunk") {
         if (!(val >= 1 && val <= 256)) return fail(h, PC_ERR_ARG, "lane_chunk must be in [1, 256]");
         h->lane_chunk = (int)val;
@@ -541,8 +550,10 @@ extern "C" pc_status pc_get_opt(pc_handle *h, const char *key, double *val)
     else if (k == "learned") *val = h->learned;
     else if (k == "learned_rows") *val = (double)h->rows_cap;
     else if (k == "learned_min_tests") *val = h->learned_min;
+    else if (k == "learned_min_ratio") *val = h->learned_ratio;
     else if (k == "budget") *val = h->budget;
     else if (k == "stage_conds") *val = h->stage_conds;
+    else if (k == "small_stage_kernel") *val = h->lane_stages;
     else if (k == "lane_chunk") *val = h->lane_chunk;
     else if (k == "lane_rounds") *val = h->lane_rounds;
     else if (k == "lane_blocks") *val = h->lane_blocks;
@@ -948,12 +959,12 @@ static pc_status enqueue_level(pc_handle *h, cudaStream_t s, int mmax, bool use_
             if (use_cond) {
                 // captured without conditional nodes: every kernel, each returns at once
                 // when the stage is not its own
-                if (h->precision != 0)
+                if (h->precision != 0 && h->lane_stages)
                     if (pc_status r = lane(-1, s)) return r;
                 if (pc_status r = direct(0, s)) return r;
             } else {
                 const int l = h->info_h->l;
-                if (h->precision != 0 && l >= 0 && l <= fpc::LANE_LMAX) {
+                if (h->lane_stages && h->precision != 0 && l >= 0 && l <= fpc::LANE_LMAX) {
                     if (pc_status r = lane(fpc::lane_range_of(l), s)) return r;
                 } else {
                     if (pc_status r = direct(0, s)) return r;
@@ -985,10 +996,11 @@ static pc_status enqueue_level(pc_handle *h, cudaStream_t s, int mmax, bool use_
 static std::vector<double> graph_key(const pc_handle *h)
 {
     return {(double)h->order, (double)h->complement, (double)h->precision, h->band, h->guard,
-            (double)h->used_tc, (double)h->c64_full, (double)h->learned, (double)(uintptr_t)h->perm, (double)h->rows_cap, h->learned_min, (double)(uintptr_t)h->rq,
+            (double)h->used_tc, (double)h->c64_full, (double)h->learned, (double)(uintptr_t)h->perm, (double)h->rows_cap, h->learned_min, h->learned_ratio, (double)(uintptr_t)h->rq,
             h->budget, (double)level_cap(h), (double)(uintptr_t)h->g.pool, (double)h->g.pool_cap,
             (double)(uintptr_t)h->C32, (double)(uintptr_t)h->C64, (double)h->lane_chunk,
-            (double)h->lane_rounds, (double)h->lane_blocks, (double)h->direct_warps, (double)h->stage_conds};
+            (double)h->lane_rounds, (double)h->lane_blocks, (double)h->direct_warps, (double)h->stage_conds,
+            (double)h->lane_stages};
 }
 
 static void drop_graph(pc_handle *h)

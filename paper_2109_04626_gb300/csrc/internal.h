@@ -137,6 +137,8 @@ struct TestParams {
     int lane_rounds;    // rank-major chunk rounds before the pair-major remainder
     int lane_blocks;    // CTAs of 256 threads per SM of the small-stage kernel
     int direct_warps;   // at most this many warps per CTA of the warp-per-test kernel
+    int lane_stages;    // 1: stages l <= LANE_LMAX on the small-stage kernel (FP32 modes);
+                        // 0: every stage on the warp-per-test kernel
     int precision;      // 0 fp64, 1/2 fp32 tests with FP64 re-decision
     int reversed;
     int complement;
@@ -146,6 +148,7 @@ struct TestParams {
     int lazy;
     int p;
     double learned_min;  // a stage is scored only if it schedules at least this many tests
+    double learned_ratio;  // ... and at least this many tests per score row
     const double *xs64;
     long long ldk;
     unsigned char *c64_valid;

@@ -338,7 +338,11 @@ __global__ void __launch_bounds__(1024) head_kernel(GraphDev g, TestParams tp, d
     ull ex[3], tot[3];
     block_scan_sat<3>(v, ex, tot, sh);
     // else: plain order this stage (too many rows, or too few tests for the order to matter)
-    const bool rows_fit = tot[2] <= (ull)g.rows_cap && (double)tot[0] + (double)tot[1] >= tp.learned_min;
+    // score rows are one per candidate; the order pays off only when a pair has
+    // many more sets than candidates (l >= 2 and large neighbourhoods)
+    const double tests_all = (double)tot[0] + (double)tot[1];
+    const bool rows_fit = tot[2] <= (ull)g.rows_cap && tests_all >= tp.learned_min &&
+                          tests_all >= tp.learned_ratio * (double)tot[2];
     const ull rows_total = tot[2];
     if (t == 0 && g.scored) g.scored[l] = rows_fit && rows_total > 0;
     {
@@ -354,7 +358,7 @@ __global__ void __launch_bounds__(1024) head_kernel(GraphDev g, TestParams tp, d
             rr = sat_add(rr, prows(dg, T));
         }
     }
-    const bool small = tp.precision != 0 && l <= LANE_LMAX;
+    const bool small = tp.lane_stages && tp.precision != 0 && l <= LANE_LMAX;
     int rounds = 0;
     if (small && tot[0] > 0) {
         // owner node of every ordered pair (the small-stage kernel's work items)
@@ -683,7 +687,7 @@ __global__ void __launch_bounds__(256) ci_direct_kernel(GraphDev g, TestParams t
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int m = l + 2, p = g.p;
     if (m > mmax) return;
-    if (!F64 && l <= LANE_LMAX && !g.info->lane_overflow) return;  // small stages: ci_lane_kernel
+    if (!F64 && tp.lane_stages && l <= LANE_LMAX && !g.info->lane_overflow) return;  // small stages: ci_lane_kernel
     unsigned char *mine = smem_raw + (size_t)wib * per_warp_bytes;
     double *Mbuf = (double *)mine;
     int *nd = (int *)(mine + (size_t)mmax * ms * sizeof(double));

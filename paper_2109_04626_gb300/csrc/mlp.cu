@@ -187,11 +187,14 @@ __global__ void __launch_bounds__(128, 2) mlp_forward_kernel(MlpRows rows, Graph
             float v[32];
             tc_ld_32cols(d1 + lane_base + (uint32_t)c0, v);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const int c = c0 + j;
-                const __nv_bfloat16 hb = __float2bfloat16_rn(fmaxf(v[j] + b1[c], 0.f));
-                *(__nv_bfloat16 *)(sA2 + (c >> 6) * (128 * 128) + sw128_off(tid, c & 63)) = hb;
-                if (h1_out && row < R) h1_out[row * NH + c] = hb;
+            for (int q = 0; q < 4; ++q) {
+                // 8 columns: one 16-byte chunk of the swizzled row (and of h1's row)
+                __align__(16) __nv_bfloat16 hb[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) hb[j] = __float2bfloat16_rn(fmaxf(v[q * 8 + j] + b1[c0 + q * 8 + j], 0.f));
+                const int c = c0 + q * 8;
+                *(uint4 *)(sA2 + (c >> 6) * (128 * 128) + sw128_off(tid, c & 63)) = *(const uint4 *)hb;
+                if (h1_out && row < R) *(uint4 *)(h1_out + row * NH + c) = *(const uint4 *)hb;
             }
         }
         tc_fence_before();

@@ -57,3 +57,21 @@ def test_autotune_bad_args(fp):
         for k, v in (("lane_chunk", 0), ("lane_rounds", -1), ("lane_blocks", 33), ("direct_warps", 3)):
             with pytest.raises(fp.PCError):
                 fp.pc_set_opt(pc.h, k, v)
+
+
+@pytest.mark.parametrize("cfg,order", [(2, 1), (4, 0)])
+def test_warp_kernel_only_same_result(fp, cfg, order):
+    """Every stage on the one-warp-per-test kernel (the plain form's kernel) gives
+    the same skeleton, sepsets and canonical count as the small-stage kernel."""
+    w = sem.WORKLOADS[cfg]
+    X = sem.make(cfg).X
+    n, p = X.shape
+    out = []
+    for lane in (1, 0):
+        with fp.PC(n, p, w["alpha"], w["max_level"], order=order, small_stage_kernel=lane) as pc:
+            pc.corr(torch.from_numpy(np.ascontiguousarray(X)).cuda())
+            adj, st = pc.skeleton()
+            out.append((adj, pc.sepsets(), st["tests_canonical"]))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][1] == out[1][1]
+    assert out[0][2] == out[1][2]

@@ -90,6 +90,7 @@ def test_batch_learned_order_keeps_skeleton(fp):
         fp.pc_mlp_set_params(pb.h, proposal.initial_params(3))
         fp.pc_set_opt(pb.h, "learned", 1)
         fp.pc_set_opt(pb.h, "learned_min_tests", 0)
+        fp.pc_set_opt(pb.h, "learned_min_ratio", 0)
         adj1, st1 = pb.skeleton()
     np.testing.assert_array_equal(adj0, adj1)
 

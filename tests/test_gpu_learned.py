@@ -127,6 +127,7 @@ def test_learned_skeleton_identical_and_fewer_tests(fp, trained):
             fp.pc_mlp_set_params(pc.h, theta)
             fp.pc_set_opt(pc.h, "learned", 1)
             fp.pc_set_opt(pc.h, "learned_min_tests", 0)   # score every stage
+            fp.pc_set_opt(pc.h, "learned_min_ratio", 0)
             adj_l, st_l = pc.skeleton()               # sepsets re-verified in FP64 inside
             seps = pc.sepsets()
         np.testing.assert_array_equal(adj_p, R["adj"])
@@ -151,6 +152,7 @@ def test_learned_reversed_order_identical(fp, trained):
         fp.pc_mlp_set_params(pc.h, theta)
         fp.pc_set_opt(pc.h, "learned", 1)
         fp.pc_set_opt(pc.h, "learned_min_tests", 0)
+        fp.pc_set_opt(pc.h, "learned_min_ratio", 0)
         adj, st = pc.skeleton()
         seps = pc.sepsets()
     np.testing.assert_array_equal(adj, R["adj"])
