@@ -106,9 +106,9 @@ __global__ void col_stats_merge_kernel(const double *ws, int chunks, int p, doub
         const double *w = ws + (size_t)c * 3 * p;
         const double nb = w[col], mb = w[p + col], Mb = w[2 * p + col];
         if (nb == 0.0) continue;
-        const double nn = na + nb, dl = mb - ma;
-        ma += dl * (nb / nn);
-        Ma += Mb + dl * dl * (na * nb / nn);
+        const double nn = na + nb, dl = mb - ma, rn = 1.0 / nn;
+        ma += dl * (nb * rn);
+        Ma += Mb + dl * dl * (na * nb * rn);
         na = nn;
     }
     const double var = Ma / na;
@@ -434,7 +434,7 @@ cudaError_t launch_col_stats_split(const void *X, int dtype, long long n, int p,
     else
         col_stats_part_kernel<float><<<g, 256, 0, s>>>((const float *)X, n, p, ld, rows_per, ws);
     note_launch();
-    col_stats_merge_kernel<<<(p + 127) / 128, 128, 0, s>>>(ws, chunks, p, mean, rsd); note_launch();
+    col_stats_merge_kernel<<<(p + 31) / 32, 32, 0, s>>>(ws, chunks, p, mean, rsd); note_launch();
     return cudaGetLastError();
 }
 

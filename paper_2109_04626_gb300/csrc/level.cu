@@ -685,7 +685,7 @@ __global__ void __launch_bounds__(256) ci_direct_kernel(GraphDev g, TestParams t
     if (stopped(g.info)) return;
     const int l = g.info->l;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int m = l + 2, p = g.p;
+    const int m = l + 2;
     if (m > mmax) return;
     if (!F64 && tp.lane_stages && l <= LANE_LMAX && !g.info->lane_overflow) return;  // small stages: ci_lane_kernel
     unsigned char *mine = smem_raw + (size_t)wib * per_warp_bytes;
@@ -813,7 +813,6 @@ __device__ __forceinline__ void lane_tests_lex(const GraphDev &g, const TestPara
 {
     constexpr int K = L > 0 ? L - 1 : 0;                 // prefix length
     constexpr int KA = K > 0 ? K : 1;
-    const int p = g.p;
     const float sqf = sqrtf((float)(n_of(tp, u) - L - 3));
     const float rq = tanhf(tp.qf / sqf);                 // |r| threshold of this stage
     const int *nb = g.nbr + nidx(g, u);
@@ -1030,7 +1029,7 @@ __global__ void __launch_bounds__(256) ci_redecide_kernel(GraphDev g, TestParams
     const int l = g.info->l;
     if (tp.precision == 0 || l > LANE_LMAX) return;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int m = l + 2, p = g.p;
+    const int m = l + 2;
     unsigned char *mine = smem_raw + (size_t)wib * per_warp_bytes;
     double *Mbuf = (double *)mine;
     int *nd = (int *)(mine + (size_t)(LANE_LMAX + 2) * ms * sizeof(double));
@@ -1091,7 +1090,6 @@ __global__ void __launch_bounds__(128) ci_complement_kernel(GraphDev g, TestPara
     if (stopped(g.info)) return;
     const int l = g.info->l;
     const ull total = g.info->total_comp;
-    const int p = g.p;
     const double sq = sqrt((double)(tp.n - l - 3));
     ull nt = 0, ndg = 0, nfl = 0;
     for (ull t = blockIdx.x * (ull)blockDim.x + threadIdx.x; t < total;
@@ -1197,21 +1195,30 @@ __global__ void __launch_bounds__(512) prec_update_kernel(GraphDev g, const doub
         const int *pm = g.prec_mem + (long long)u * PREC_MAX;
         const short *pos = g.prec_pos + pidx(g, u, 0);
         const uint32_t *row = g.adj + (long long)u * g.W;
-        // members deleted by the last commit, ascending slots (same in every chunk)
-        if (threadIdx.x < 32) {
-            int cnt = 0;
-            for (int s0 = 0; s0 < m0; s0 += 32) {
-                const int s = s0 + threadIdx.x;
-                bool gone = false;
-                if (s < m0) {
-                    const int w = pm[s];
-                    gone = w != u && pos[w] >= 0 && !((row[w >> 5] >> (w & 31)) & 1u);
-                }
-                const unsigned bal = __ballot_sync(0xffffffffu, gone);
-                if (gone) rem[cnt + __popc(bal & ((1u << threadIdx.x) - 1u))] = s;
-                cnt += __popc(bal);
+        // members deleted by the last commit, ascending slots (same in every chunk):
+        // one slot per thread (m0 <= PREC_MAX < blockDim.x), ballots, warp offsets
+        __shared__ int wcnt[16];
+        {
+            const int sl = threadIdx.x, wid = threadIdx.x >> 5, ln = threadIdx.x & 31;
+            bool gone = false;
+            if (sl < m0) {
+                const int w = pm[sl];
+                gone = w != u && pos[w] >= 0 && !((row[w >> 5] >> (w & 31)) & 1u);
             }
-            if (threadIdx.x == 0) nrem = cnt;
+            const unsigned bal = __ballot_sync(0xffffffffu, gone);
+            if (ln == 0) wcnt[wid] = __popc(bal);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int acc = 0;
+                for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+                    const int c = wcnt[i];
+                    wcnt[i] = acc;
+                    acc += c;
+                }
+                nrem = acc;
+            }
+            __syncthreads();
+            if (gone) rem[wcnt[wid] + __popc(bal & ((1u << ln) - 1u))] = sl;
         }
         __syncthreads();
         const int nr = nrem;
@@ -1233,7 +1240,12 @@ __global__ void __launch_bounds__(512) prec_update_kernel(GraphDev g, const doub
         for (int e = threadIdx.x; e < nr * nr; e += blockDim.x) S[e] = P[rem[e / nr] * PREC_MAX + rem[e % nr]];
         for (int e = threadIdx.x; e < nr * m0; e += blockDim.x) PR[e] = P[rem[e / m0] * PREC_MAX + e % m0];
         __syncthreads();
-        sweep_inverse_block(S, nr, nr, ck, &sbad);   // S = -P_RR^{-1}
+        if (nr <= 16) {
+            // a few removals: one warp sweeps (warp-level sync per pivot)
+            if (threadIdx.x < 32) sweep_inverse_warp(S, nr, nr, ck, &sbad);
+        } else {
+            sweep_inverse_block(S, nr, nr, ck, &sbad);   // S = -P_RR^{-1}
+        }
         __syncthreads();
         if (sbad) {
             // P_RR is a principal block of an SPD inverse; a pivot at the floor means the
@@ -1318,7 +1330,6 @@ __global__ void prec_mark_kernel(GraphDev g)
     if (stopped(g.info)) return;
     const int m0 = g.prec_m[u];
     if (m0 <= 0) return;
-    const int p = g.p;
     const int *pm = g.prec_mem + (long long)u * PREC_MAX;
     short *pos = g.prec_pos + pidx(g, u, 0);
     const uint32_t *row = g.adj + (long long)u * g.W;
@@ -1339,80 +1350,109 @@ __global__ void commit_kernel(GraphDev g, int l_fixed, int explicit_sets, int co
     const int l = l_fixed >= 0 ? l_fixed : g.info->l;
     const long long nop = g.info->n_opairs;
     const int p = g.p;
+    const int lane = threadIdx.x & 31;
     ull removed = 0, canon = 0;
-    for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < nop;
-         o += (long long)gridDim.x * blockDim.x) {
-        const int u = (int)(upper_bound_dev(g.ooff, (long long)p + 1, o) - 1);
-        const int j = (int)(o - g.ooff[u]);
-        const int v = g.nbr[nidx(g, u) + j];
-        if (u > v) continue;
-        const long long e = pidx(g, u, v);
-        const ull key = g.best[e];
-        g.best[e] = KEY_NONE;                         // ready for the next stage
-        if (count_canonical) {
-            const int du = g.deg[u] - 1, dv = g.deg[v] - 1;
-            const bool dof = !g.nvec || g.nvec[u] - l - 3 > 0;   // u and v share their instance
-            const ull T0 = du >= l && dof ? g.binom[(long long)du * g.ldb + l] : 0ull;
-            const ull T1 = dv >= l && dof ? g.binom[(long long)dv * g.ldb + l] : 0ull;
-            ull c;
-            if (key == KEY_NONE) c = sat_add(T0, T1);
-            else if ((key >> 62) == 0) c = key + 1;
-            else c = sat_add(T0, (key & ((1ull << 62) - 1)) + 1);
-            canon = sat_add(canon, c);
-        }
-        if (key == KEY_NONE) continue;
-        atomicAnd(g.adj + (long long)u * g.W + (v >> 5), ~(1u << (v & 31)));
-        atomicAnd(g.adj + (long long)v * g.W + (u >> 5), ~(1u << (u & 31)));
-        const int side = (int)(key >> 62);
-        const ull rank = key & ((1ull << 62) - 1);
-        g.sep_level[e] = l;
-        g.sep_side[e] = side;
-        g.sep_rank[e] = (long long)rank;
-        ++removed;
-        if (explicit_sets) {
-            const ull off = atomicAdd(&g.ctr->pool_len, (ull)l);
-            g.sep_off[e] = (long long)off;
-            if ((long long)(off + l) > g.pool_cap) {
-                g.info->pool_overflow = 1;           // the host enlarges the pool and reruns
-                g.info->halt = 1;
-                continue;
+    // warp-uniform trip count: the sepsets of a warp's removed pairs are expanded
+    // by the whole warp below
+    for (long long base = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); base < nop;
+         base += (long long)gridDim.x * blockDim.x) {
+        const long long o = base + lane;
+        bool expand = false;
+        int su = 0, jj = 0, dd = 0;
+        ull rank = 0, off = 0;
+        if (o < nop) {
+            const int u = (int)(upper_bound_dev(g.ooff, (long long)p + 1, o) - 1);
+            const int j = (int)(o - g.ooff[u]);
+            const int v = g.nbr[nidx(g, u) + j];
+            if (u < v) {
+                const long long e = pidx(g, u, v);
+                const ull key = g.best[e];
+                g.best[e] = KEY_NONE;                     // ready for the next stage
+                if (count_canonical) {
+                    const int du = g.deg[u] - 1, dv = g.deg[v] - 1;
+                    const bool dof = !g.nvec || g.nvec[u] - l - 3 > 0;   // u and v share their instance
+                    const ull T0 = du >= l && dof ? g.binom[(long long)du * g.ldb + l] : 0ull;
+                    const ull T1 = dv >= l && dof ? g.binom[(long long)dv * g.ldb + l] : 0ull;
+                    ull c;
+                    if (key == KEY_NONE) c = sat_add(T0, T1);
+                    else if ((key >> 62) == 0) c = key + 1;
+                    else c = sat_add(T0, (key & ((1ull << 62) - 1)) + 1);
+                    canon = sat_add(canon, c);
+                }
+                if (key != KEY_NONE) {
+                    atomicAnd(g.adj + (long long)u * g.W + (v >> 5), ~(1u << (v & 31)));
+                    atomicAnd(g.adj + (long long)v * g.W + (u >> 5), ~(1u << (u & 31)));
+                    const int side = (int)(key >> 62);
+                    rank = key & ((1ull << 62) - 1);
+                    g.sep_level[e] = l;
+                    g.sep_side[e] = side;
+                    g.sep_rank[e] = (long long)rank;
+                    ++removed;
+                    if (explicit_sets) {
+                        off = atomicAdd(&g.ctr->pool_len, (ull)l);
+                        g.sep_off[e] = (long long)off;
+                        if ((long long)(off + l) > g.pool_cap) {
+                            g.info->pool_overflow = 1;   // the host enlarges the pool and reruns
+                            g.info->halt = 1;
+                        } else {
+                            su = side ? v : u;
+                            jj = side ? lower_bound_int(g.nbr + nidx(g, v), g.deg[v], u) : j;
+                            dd = g.deg[su] - 1;
+                            expand = true;
+                        }
+                    } else {
+                        g.sep_off[e] = -1;
+                    }
+                }
             }
-            const int su = side ? v : u;
-            const int jj = side ? lower_bound_int(g.nbr + nidx(g, v), g.deg[v], u) : j;
-            const int dd = g.deg[su] - 1;
-            const int *nb = g.nbr + nidx(g, su);
-            const int kd = dd - l;                        // dropped members
+        }
+        unsigned pend = __ballot_sync(0xffffffffu, expand);
+        while (pend) {
+            const int src = __ffs(pend) - 1;
+            pend &= pend - 1;
+            const int s_su = __shfl_sync(0xffffffffu, su, src), s_jj = __shfl_sync(0xffffffffu, jj, src);
+            const int s_dd = __shfl_sync(0xffffffffu, dd, src);
+            const ull s_rank = __shfl_sync(0xffffffffu, rank, src), s_off = __shfl_sync(0xffffffffu, off, src);
+            const int *nb = g.nbr + nidx(g, s_su);
+            const int kd = s_dd - l;                      // dropped members
             if (kd <= KC_MAX && kd < l) {
                 // expand through the complement: R = the kd dropped positions, at lex
-                // rank C(dd,l) - 1 - rank among the kd-subsets; S = the rest, ascending
+                // rank C(dd,l) - 1 - rank among the kd-subsets; S = the rest,
+                // ascending (a ballot prefix keeps the order)
                 int posR[KC_MAX + 1], nodeR[KC_MAX];
-                const ull T = g.binom[(long long)dd * g.ldb + l];
-                unrank_lex(T - 1 - rank, dd, kd, g.binom, g.ldb, posR);
-                for (int i = 0; i < kd; ++i) nodeR[i] = cand_node(g, su, jj, dd, posR[i]);
-                int o = 0;
-                for (int y = 0; y <= dd; ++y) {
-                    if (y == jj) continue;
-                    bool dropped = false;
-                    for (int i = 0; i < kd; ++i) dropped |= nodeR[i] == nb[y];
-                    if (!dropped) g.pool[off + o++] = nb[y];
+                const ull T = g.binom[(long long)s_dd * g.ldb + l];
+                unrank_lex(T - 1 - s_rank, s_dd, kd, g.binom, g.ldb, posR);
+                for (int i = 0; i < kd; ++i) nodeR[i] = cand_node(g, s_su, s_jj, s_dd, posR[i]);
+                int o2 = 0;
+                for (int y0 = 0; y0 <= s_dd; y0 += 32) {
+                    const int y = y0 + lane;
+                    bool keep = false;
+                    int w = 0;
+                    if (y <= s_dd && y != s_jj) {
+                        w = nb[y];
+                        keep = true;
+                        for (int i = 0; i < kd; ++i) keep &= nodeR[i] != w;
+                    }
+                    const unsigned kb = __ballot_sync(0xffffffffu, keep);
+                    if (keep) g.pool[s_off + o2 + __popc(kb & ((1u << lane) - 1u))] = w;
+                    o2 += __popc(kb);
                 }
-            } else {
-                ull r = rank;
+            } else if (lane == 0) {
+                ull r = s_rank;
                 int x = 0;
                 for (int i = 0; i < l; ++i) {
-                    while (x < dd - (l - i)) {
-                        ull c = g.binom[(long long)(dd - x - 1) * g.ldb + (l - i - 1)];
+                    while (x < s_dd - (l - i)) {
+                        ull c = g.binom[(long long)(s_dd - x - 1) * g.ldb + (l - i - 1)];
                         if (r < c) break;
                         r -= c;
                         ++x;
                     }
-                    g.pool[off + i] = cand_node(g, su, jj, dd, x);
+                    g.pool[s_off + i] = cand_node(g, s_su, s_jj, s_dd, x);
                     ++x;
                 }
-                if (g.row_off) sort_small(g.pool + off, l);
+                if (g.row_off) sort_small(g.pool + s_off, l);
             }
-        } else {
-            g.sep_off[e] = -1;
+            __syncwarp();
         }
     }
     if (removed) atomicAdd(&g.ctr->edges_removed, removed);
