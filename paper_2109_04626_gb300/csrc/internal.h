@@ -33,6 +33,9 @@ struct DevCounters {
     unsigned int max_dz_bits;          // float bits of max |z32 - z64|
     int status;                        // device-side error (pc_status value)
     int queue_overflows;               // stages whose FP64 re-decision queue overflowed
+    unsigned long long prec_downdates; // neighbourhood blocks downdated
+    unsigned long long prec_deferred;  // downdates deferred (block unused at the next stage)
+    unsigned long long prec_builds;    // neighbourhood blocks built
 };
 
 // Per-stage scalars: the stage index lives on the device so that the whole
@@ -137,6 +140,7 @@ struct TestParams {
     int lane_rounds;    // rank-major chunk rounds before the pair-major remainder
     int lane_blocks;    // CTAs of 256 threads per SM of the small-stage kernel
     int direct_warps;   // at most this many warps per CTA of the warp-per-test kernel
+    int prec_defer;     // 1: defer the downdates of blocks the next stage does not use
     int lane_stages;    // 1: stages l <= LANE_LMAX on the small-stage kernel (FP32 modes);
                         // 0: every stage on the warp-per-test kernel
     int precision;      // 0 fp64, 1/2 fp32 tests with FP64 re-decision
@@ -209,7 +213,7 @@ cudaError_t launch_ci_lane(GraphDev g, TestParams tp, const float *C32, const do
                            unsigned long long *queue, unsigned long long qcap, unsigned long long *qlen,
                            int range, bool prop, cudaStream_t s);
 int lane_range_of(int l);
-cudaError_t launch_prec_update(GraphDev g, const double *C64, int ldc, cudaStream_t s);
+cudaError_t launch_prec_update(GraphDev g, TestParams tp, const double *C64, int ldc, cudaStream_t s);
 cudaError_t launch_commit(GraphDev g, long long n_opairs_cap, int l_fixed, int explicit_sets,
                           cudaStream_t s);
 size_t scan_ws_bytes(long long n);

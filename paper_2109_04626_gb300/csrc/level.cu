@@ -1180,10 +1180,14 @@ constexpr int PREC_RMAX = 48;         // removals applied in one block downdate
 // only its own rows and the rows of R, which no CTA writes, so the chunks need
 // no synchronisation; prec_mark_kernel retires R afterwards.  A requested
 // block (chunk 0) is built by a symmetric sweep of corr[F,F], F = adj(u) u {u}.
-__global__ void __launch_bounds__(512) prec_update_kernel(GraphDev g, const double *C64, int ldc)
+__global__ void __launch_bounds__(512) prec_update_kernel(GraphDev g, TestParams tp, const double *C64, int ldc)
 {
     const int u = blockIdx.x;
     if (stopped(g.info)) return;
+    // a block the next stage does not use keeps its removed members: they are
+    // found and applied together once the node is on the complement path again
+    // (prec_mark skips the node likewise)
+    const bool defer = tp.prec_defer && g.prec_m[u] > 0 && g.deg[u] > 0 && !comp_eligible(g.deg[u] - 1, g.info->l, tp);
     extern __shared__ double smd[];
     __shared__ int mem[PREC_MAX];
     __shared__ int bad, nrem;
@@ -1223,6 +1227,11 @@ __global__ void __launch_bounds__(512) prec_update_kernel(GraphDev g, const doub
         __syncthreads();
         const int nr = nrem;
         if (nr == 0) return;
+        if (defer) {
+            if (blockIdx.y == 0 && threadIdx.x == 0) atomicAdd(&g.ctr->prec_deferred, 1ull);
+            return;
+        }
+        if (blockIdx.y == 0 && threadIdx.x == 0) atomicAdd(&g.ctr->prec_downdates, 1ull);
         if (nr > PREC_RMAX) {
             // too many at once: drop the block; it is rebuilt if the node needs it again
             if (blockIdx.y == 0 && threadIdx.x == 0) g.prec_m[u] = -2;
@@ -1320,16 +1329,18 @@ __global__ void __launch_bounds__(512) prec_update_kernel(GraphDev g, const doub
         g.prec_m[u] = m;
         g.prec_need[u] = 0;
         atomicAdd(&g.ctr->flops_prec, (ull)m * m * m);
+        atomicAdd(&g.ctr->prec_builds, 1ull);
     }
 }
 
 // Retires the members the block downdate dropped (slot map entry -1).
-__global__ void prec_mark_kernel(GraphDev g)
+__global__ void prec_mark_kernel(GraphDev g, TestParams tp)
 {
     const int u = blockIdx.x;
     if (stopped(g.info)) return;
     const int m0 = g.prec_m[u];
     if (m0 <= 0) return;
+    if (tp.prec_defer && g.deg[u] > 0 && !comp_eligible(g.deg[u] - 1, g.info->l, tp)) return;   // deferred downdate
     const int *pm = g.prec_mem + (long long)u * PREC_MAX;
     short *pos = g.prec_pos + pidx(g, u, 0);
     const uint32_t *row = g.adj + (long long)u * g.W;
@@ -1680,7 +1691,7 @@ cudaError_t launch_ci_complement(GraphDev g, TestParams tp, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_prec_update(GraphDev g, const double *C64, int ldc, cudaStream_t s)
+cudaError_t launch_prec_update(GraphDev g, TestParams tp, const double *C64, int ldc, cudaStream_t s)
 {
     const int mmax = std::min(g.p + 1, PREC_MAX);
     const int rows = (mmax + PREC_CHUNKS - 1) / PREC_CHUNKS;
@@ -1691,8 +1702,8 @@ cudaError_t launch_prec_update(GraphDev g, const double *C64, int ldc, cudaStrea
     cudaError_t e = cudaFuncSetAttribute(prec_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    prec_update_kernel<<<dim3(g.p, PREC_CHUNKS), 512, smem, s>>>(g, C64, ldc); note_launch();
-    prec_mark_kernel<<<g.p, 128, 0, s>>>(g); note_launch();
+    prec_update_kernel<<<dim3(g.p, PREC_CHUNKS), 512, smem, s>>>(g, tp, C64, ldc); note_launch();
+    prec_mark_kernel<<<g.p, 128, 0, s>>>(g, tp); note_launch();
     return cudaGetLastError();
 }
 

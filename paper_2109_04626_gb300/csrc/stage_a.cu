@@ -6,7 +6,61 @@
 #include "internal.h"
 #include "device_util.cuh"
 
+#include <cooperative_groups.h>
+
 namespace fpc {
+
+namespace cg = cooperative_groups;
+
+// The same symmetric sweep (A <- -A^{-1}, pivots in order, no exchanges) on a
+// cluster of SA_CLUSTER CTAs: CTA r holds rows [r*rpc, (r+1)*rpc) in shared
+// memory; at pivot k every CTA copies row k (= column k, A stays symmetric) from
+// its owner through distributed shared memory, then updates its own rows.  Each
+// entry (i, j) is computed with the operands the one-CTA sweep uses for the
+// pair {i, j}, so the result is bit-identical to it; GB300's FP64 rate (about
+// 2 FMA per clock per SM) is what the cluster multiplies.
+constexpr int SA_CLUSTER = 8;
+__global__ void __cluster_dims__(SA_CLUSTER, 1, 1) __launch_bounds__(256)
+    inverse_cluster_kernel(double *A, int m, int lda, int *singular)
+{
+    extern __shared__ double smc[];
+    cg::cluster_group cl = cg::this_cluster();
+    const int r = (int)cl.block_rank();
+    const int rpc = (m + SA_CLUSTER - 1) / SA_CLUSTER;
+    const int i0 = min(m, r * rpc), i1 = min(m, i0 + rpc), nr = i1 - i0;
+    double *R = smc;                                   // own rows, row-major, m per row
+    double *colk = smc + (size_t)rpc * m;
+    for (int e = threadIdx.x; e < nr * m; e += blockDim.x) R[e] = A[(long long)(i0 + e / m) * lda + e % m];
+    bool bad = false;
+    cl.sync();
+    for (int k = 0; k < m; ++k) {
+        const int owner = k / rpc;
+        const double *rowk = cl.map_shared_rank(R, owner) + (size_t)(k - owner * rpc) * m;
+        for (int j = threadIdx.x; j < m; j += blockDim.x) colk[j] = rowk[j];
+        cl.sync();                                     // row k copied everywhere: its owner may update it
+        const double D = colk[k];
+        if (!(D > DEGEN)) {                            // the same pivot in every CTA: a uniform exit
+            bad = true;
+            break;
+        }
+        const double iD = 1.0 / D;
+        for (int e = threadIdx.x; e < nr * m; e += blockDim.x) {
+            const int i = i0 + e / m, j = e - (e / m) * m;
+            double v;
+            if (i == k) v = (j == k) ? -iD : colk[j] * iD;
+            else if (j == k) v = colk[i] * iD;
+            else if (i <= j) v = fma(-(colk[i] * iD), colk[j], R[e]);
+            else v = fma(-(colk[j] * iD), colk[i], R[e]);
+            R[e] = v;
+        }
+        cl.sync();                                     // pivot k applied before row k+1 is read
+    }
+    if (bad) {
+        if (r == 0 && threadIdx.x == 0) *singular = 1;
+        return;
+    }
+    for (int e = threadIdx.x; e < nr * m; e += blockDim.x) A[(long long)(i0 + e / m) * lda + e % m] = -R[e];
+}
 
 __global__ void __launch_bounds__(1024) inverse_smem_kernel(double *A, int m, int lda, int *singular)
 {
@@ -58,6 +112,14 @@ cudaError_t launch_inverse_spd(double *A, int m, int lda, double *work, int *sin
 {
     cudaError_t e = cudaMemsetAsync(singular, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
+    // a cluster of SA_CLUSTER CTAs when the rows fit their shared memory
+    const size_t smem_c = ((size_t)((m + SA_CLUSTER - 1) / SA_CLUSTER) * m + (size_t)m) * sizeof(double);
+    if (m >= 32 && smem_c <= 200 * 1024) {
+        e = cudaFuncSetAttribute(inverse_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c);
+        if (e != cudaSuccess) return e;
+        inverse_cluster_kernel<<<SA_CLUSTER, 256, smem_c, s>>>(A, m, lda, singular); note_launch();
+        return cudaGetLastError();
+    }
     size_t smem = ((size_t)m * m + (size_t)m) * sizeof(double);
     if (smem <= 220 * 1024) {
         e = cudaFuncSetAttribute(inverse_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -45,6 +45,9 @@ class pc_stats(ctypes.Structure):
         ("stage_a_ran", ctypes.c_int32),
         ("first_level", ctypes.c_int32),
         ("queue_overflows", ctypes.c_int32),
+        ("prec_builds", ctypes.c_uint64),
+        ("prec_downdates", ctypes.c_uint64),
+        ("prec_deferred", ctypes.c_uint64),
     ]
 
     def as_dict(self) -> dict:

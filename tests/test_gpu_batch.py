@@ -124,3 +124,37 @@ def test_batch_ci_batch_and_errors(fp):
     with pytest.raises(fp.PCError):
         pb.ci_batch(torch.tensor([[o[0], o[1]]], dtype=torch.int32).cuda(), None, 0)
     pb.close()
+
+
+def test_many64_full_size_equals_oracle(fp):
+    """The 64-instance workload at its full sizes: every instance's skeleton and
+    sepsets from the batched handle and from 64 concurrent handles equal the
+    FP64 oracle's (conventional order)."""
+    inst = sem.make_many(64)
+    ns = [s.X.shape[0] for s in inst]
+    ps = [s.X.shape[1] for s in inst]
+    pcs = []
+    streams = [torch.cuda.Stream() for _ in range(8)]
+    for i, s in enumerate(inst):
+        pc = fp.PC(ns[i], ps[i], 0.01, -1, order=0)
+        fp.pc_set_stream(pc.h, streams[i % len(streams)])
+        pc.corr(torch.from_numpy(s.X).cuda())
+        pcs.append(pc)
+    torch.cuda.synchronize()
+    adjs, stats, status = fp.pc_skeleton_many([pc.h for pc in pcs], ps)
+    assert all(x == 0 for x in status)
+    seps_many = [pc.sepsets() for pc in pcs]
+    for pc in pcs:
+        pc.close()
+    with fp.PCBatch(ns, ps, 0.01, -1) as pb:
+        for i, s in enumerate(inst):
+            pb.corr_block(i, torch.from_numpy(s.X).cuda())
+        adj_b, _ = pb.skeleton()
+        blocks, seps_b = pb.split(adj_b, pb.sepsets())
+    for i, s in enumerate(inst):
+        R = _oracle(s.X, 0.01, -1)
+        np.testing.assert_array_equal(adjs[i], R["adj"])
+        np.testing.assert_array_equal(blocks[i], R["adj"])
+        assert seps_many[i] == R["sepsets"], i
+        assert seps_b[i] == R["sepsets"], i
+        assert stats[i]["tests_canonical"] == R["tests_total"], i

@@ -218,6 +218,25 @@ def test_skeleton_degenerate_duplicate_column(fp):
     assert st["degenerate"] > 0 or R["degenerate"] == 0
 
 
+@pytest.mark.parametrize("precision", [0, 2])
+def test_stage_a_singular_cluster_sweep(fp, precision):
+    # p >= 32: the closed-form stage inverts corr on a CTA cluster; an exactly
+    # collinear pair makes corr singular, so the stage is skipped as in the oracle
+    X = _sem_case(73, 48, 4000, 0.2, np.float64)
+    X[:, 30] = X[:, 7]
+    R, st = _check_skeleton(fp, X, order=1, precision=precision)
+    assert R["stageA_ran"] is False or R["stageA_ran"] == 0
+    assert st["stage_a_ran"] == 0
+
+
+@pytest.mark.parametrize("p", [32, 57, 130])
+def test_stage_a_cluster_sizes(fp, p):
+    # the cluster sweep over 8 CTAs with ragged row blocks (p not a multiple of 8)
+    X = _sem_case(90 + p, p, max(2000, 4 * p), 0.15 if p < 100 else 0.04)
+    R, st = _check_skeleton(fp, X, order=1, precision=2)
+    assert st["stage_a_ran"] == int(bool(R["stageA_ran"]))
+
+
 def test_skeleton_host_buffers(fp):
     X = sem.make(1).X
     _check_skeleton(fp, X, device_input=False)
