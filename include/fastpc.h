@@ -67,7 +67,6 @@ typedef struct {
                                    by the warp-per-test kernel; the queue grows for later runs) */
     uint64_t prec_builds;       /* neighbourhood precision blocks built (reversed order)      */
     uint64_t prec_downdates;    /* block downdates applied after deletions                    */
-    uint64_t prec_deferred;     /* downdates deferred: the block was unused at the next stage  */
 } pc_stats;
 
 /* pc_create -- a handle for data of n samples over p variables, significance
@@ -98,9 +97,6 @@ void pc_destroy(pc_handle *h);
  *                 WHILE node is driven by the device (default); 0 = host loop
  *   "stage_conds" 1 = inside that graph, conditional nodes skip the kernels a
  *                 stage has no work for (default); 0 = every kernel every stage
- *   "defer_downdates" 1 = a neighbourhood precision block that the next stage
- *                 does not use keeps its deleted members until it is used again
- *                 (default); 0 = every block is downdated after every stage
  *   "small_stage_kernel" 1 = stages l <= 8 of the FP32 modes run on the
  *                 rank-major one-thread-per-chunk kernel with bordered tests
  *                 (default); 0 = every stage on the one-warp-per-test kernel

@@ -53,7 +53,6 @@ struct pc_handle {
     int lane_chunk = 8, lane_rounds = 32, lane_blocks = 8, direct_warps = 8;
     int stage_conds = 1;                 // conditional nodes in the captured stage body
     int lane_stages = 1;                 // small stages on the rank-major small-stage kernel
-    int prec_defer = 1;                  // defer downdates of blocks unused at the next stage
     cudaStream_t stream = 0;
     std::string err;
     // correlation
@@ -239,7 +238,6 @@ static TestParams make_tp(const pc_handle *h)
     tp.lane_blocks = h->lane_blocks;
     tp.direct_warps = h->direct_warps;
     tp.lane_stages = h->lane_stages;
-    tp.prec_defer = h->prec_defer;
     tp.precision = h->precision;
     tp.reversed = h->order == 1;
     tp.complement = h->complement;
@@ -521,8 +519,7 @@ extern "C" pc_status pc_set_opt(pc_handle *h, const char *key, double val)
         h->stage_conds = val != 0;
     } else if (k == "small_stage_kernel") {
         h->lane_stages = val != 0;
-    } else if (k == "defer_downdates") {
-        h->prec_defer = val != 0;
+
     } else if (k == "lane_chunk") {
         if (!(val >= 1 && val <= 256)) return fail(h, PC_ERR_ARG, "lane_chunk must be in [1, 256]");
         h->lane_chunk = (int)val;
@@ -558,7 +555,6 @@ extern "C" pc_status pc_get_opt(pc_handle *h, const char *key, double *val)
     else if (k == "budget") *val = h->budget;
     else if (k == "stage_conds") *val = h->stage_conds;
     else if (k == "small_stage_kernel") *val = h->lane_stages;
-    else if (k == "defer_downdates") *val = h->prec_defer;
     else if (k == "lane_chunk") *val = h->lane_chunk;
     else if (k == "lane_rounds") *val = h->lane_rounds;
     else if (k == "lane_blocks") *val = h->lane_blocks;
@@ -1005,7 +1001,7 @@ static std::vector<double> graph_key(const pc_handle *h)
             h->budget, (double)level_cap(h), (double)(uintptr_t)h->g.pool, (double)h->g.pool_cap,
             (double)(uintptr_t)h->C32, (double)(uintptr_t)h->C64, (double)h->lane_chunk,
             (double)h->lane_rounds, (double)h->lane_blocks, (double)h->direct_warps, (double)h->stage_conds,
-            (double)h->lane_stages, (double)h->prec_defer};
+            (double)h->lane_stages};
 }
 
 static void drop_graph(pc_handle *h)
@@ -1249,7 +1245,6 @@ static pc_status skeleton_complete(pc_handle *h, pc_stats *st, bool *overflow)
     st->queue_overflows = c.queue_overflows;
     st->prec_builds = c.prec_builds;
     st->prec_downdates = c.prec_downdates;
-    st->prec_deferred = c.prec_deferred;
     st->flops_class[1] = (double)c.flops_stagea + (I.stage_a_ran ? (double)p * p * p : 0.0);
     st->flops_class[2] = (double)c.flops_prec;
     st->flops_class[3] = (double)c.flops + (double)c.flops64_direct;

@@ -34,7 +34,6 @@ struct DevCounters {
     int status;                        // device-side error (pc_status value)
     int queue_overflows;               // stages whose FP64 re-decision queue overflowed
     unsigned long long prec_downdates; // neighbourhood blocks downdated
-    unsigned long long prec_deferred;  // downdates deferred (block unused at the next stage)
     unsigned long long prec_builds;    // neighbourhood blocks built
 };
 
@@ -140,7 +139,6 @@ struct TestParams {
     int lane_rounds;    // rank-major chunk rounds before the pair-major remainder
     int lane_blocks;    // CTAs of 256 threads per SM of the small-stage kernel
     int direct_warps;   // at most this many warps per CTA of the warp-per-test kernel
-    int prec_defer;     // 1: defer the downdates of blocks the next stage does not use
     int lane_stages;    // 1: stages l <= LANE_LMAX on the small-stage kernel (FP32 modes);
                         // 0: every stage on the warp-per-test kernel
     int precision;      // 0 fp64, 1/2 fp32 tests with FP64 re-decision

@@ -1184,10 +1184,6 @@ __global__ void __launch_bounds__(512) prec_update_kernel(GraphDev g, TestParams
 {
     const int u = blockIdx.x;
     if (stopped(g.info)) return;
-    // a block the next stage does not use keeps its removed members: they are
-    // found and applied together once the node is on the complement path again
-    // (prec_mark skips the node likewise)
-    const bool defer = tp.prec_defer && g.prec_m[u] > 0 && g.deg[u] > 0 && !comp_eligible(g.deg[u] - 1, g.info->l, tp);
     extern __shared__ double smd[];
     __shared__ int mem[PREC_MAX];
     __shared__ int bad, nrem;
@@ -1227,10 +1223,6 @@ __global__ void __launch_bounds__(512) prec_update_kernel(GraphDev g, TestParams
         __syncthreads();
         const int nr = nrem;
         if (nr == 0) return;
-        if (defer) {
-            if (blockIdx.y == 0 && threadIdx.x == 0) atomicAdd(&g.ctr->prec_deferred, 1ull);
-            return;
-        }
         if (blockIdx.y == 0 && threadIdx.x == 0) atomicAdd(&g.ctr->prec_downdates, 1ull);
         if (nr > PREC_RMAX) {
             // too many at once: drop the block; it is rebuilt if the node needs it again
@@ -1340,7 +1332,6 @@ __global__ void prec_mark_kernel(GraphDev g, TestParams tp)
     if (stopped(g.info)) return;
     const int m0 = g.prec_m[u];
     if (m0 <= 0) return;
-    if (tp.prec_defer && g.deg[u] > 0 && !comp_eligible(g.deg[u] - 1, g.info->l, tp)) return;   // deferred downdate
     const int *pm = g.prec_mem + (long long)u * PREC_MAX;
     short *pos = g.prec_pos + pidx(g, u, 0);
     const uint32_t *row = g.adj + (long long)u * g.W;

@@ -47,7 +47,6 @@ class pc_stats(ctypes.Structure):
         ("queue_overflows", ctypes.c_int32),
         ("prec_builds", ctypes.c_uint64),
         ("prec_downdates", ctypes.c_uint64),
-        ("prec_deferred", ctypes.c_uint64),
     ]
 
     def as_dict(self) -> dict:
