@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(128, 2) mlp_forward_kernel(MlpRows rows, Graph
     __shared__ float b1[NH], b2[NH], w3[NH];
     __shared__ float b3;
     __shared__ long long nrows;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tid = threadIdx.x, warp = tid >> 5;
     if (!rows.feats && (g.info->done || g.info->halt)) return;
     // a stage without proposal rows (or a CTA past the last tile) leaves before
     // loading the weights and allocating tensor memory
