@@ -97,6 +97,102 @@ __global__ void __launch_bounds__(256) col_stats_part_kernel(const T *__restrict
     }
 }
 
+// FP32 input: the same two-pass chunk statistics with the per-element work in
+// FP32 (GB300 runs FP64 at 1/64 of FP32).  Runs of 8 elements are summed
+// exactly as double-single (TwoSum into hi + lo) and each run is added to an
+// FP64 accumulator; the deviation d = x - mean is formed exactly against the
+// FP64 mean split into two floats and squared with FMA-exact products.  About
+// 0.5 FP64 operations per element instead of 4; the results agree with FP64
+// two-pass sums to about 1e-15 relative.
+__device__ __forceinline__ void two_sum_f(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bv = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bv)), __fsub_rn(b, bv));
+}
+
+// x - (mh + ml) = sd + dl + dll exactly (mh + ml: an FP64 value split into floats)
+__device__ __forceinline__ void dev_split(float x, float mh, float ml, float &sd, float &dl, float &dll)
+{
+    float e;
+    two_sum_f(x, -mh, sd, e);
+    two_sum_f(e, -ml, dl, dll);
+}
+
+constexpr int STAT_RUN = 8;
+
+__global__ void __launch_bounds__(256) col_stats_part_f32_kernel(const float *__restrict__ X, long long n, int p,
+                                                                 long long ld, long long rows_per, double *ws)
+{
+    __shared__ double red[8][33];
+    __shared__ double mu_s[32];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int col = blockIdx.x * 32 + tx;
+    const bool ok = col < p;
+    const long long r0 = (long long)blockIdx.y * rows_per;
+    const long long r1 = r0 + rows_per < n ? r0 + rows_per : n;
+    const double cnt = (double)(r1 - r0);
+    double S = 0.0;
+    {
+        float hi = 0.f, lo = 0.f;
+        int k = 0;
+        if (ok)
+            for (long long t = r0 + ty; t < r1; t += 8) {
+                float e;
+                two_sum_f(hi, X[t * ld + col], hi, e);
+                lo = __fadd_rn(lo, e);
+                if (++k == STAT_RUN) {
+                    S += (double)hi + (double)lo;
+                    hi = lo = 0.f;
+                    k = 0;
+                }
+            }
+        S += (double)hi + (double)lo;
+    }
+    red[ty][tx] = S;
+    __syncthreads();
+    if (ty == 0) {
+        double a = 0.0;
+        for (int k = 0; k < 8; ++k) a += red[k][tx];
+        mu_s[tx] = cnt > 0 ? a / cnt : 0.0;
+    }
+    __syncthreads();
+    const double mu = mu_s[tx];
+    const float mh = (float)mu, ml = (float)(mu - (double)mh);
+    double Q = 0.0;
+    {
+        float hi = 0.f, lo = 0.f, sm = 0.f;
+        int k = 0;
+        if (ok)
+            for (long long t = r0 + ty; t < r1; t += 8) {
+                float sd, dl, dll, e;
+                dev_split(X[t * ld + col], mh, ml, sd, dl, dll);
+                const float pp = __fmul_rn(sd, sd);
+                const float pe = __fmaf_rn(sd, sd, -pp);           // sd^2 = pp + pe exactly
+                // d^2 - pp = pe + 2 sd (dl + dll) + (dl + dll)^2, to FP32 accuracy
+                sm = __fadd_rn(sm, __fmaf_rn(dl, dl, __fmaf_rn(__fmul_rn(2.f, sd), __fadd_rn(dl, dll), pe)));
+                two_sum_f(hi, pp, hi, e);
+                lo = __fadd_rn(lo, e);
+                if (++k == STAT_RUN) {
+                    Q += (double)hi + ((double)lo + (double)sm);
+                    hi = lo = sm = 0.f;
+                    k = 0;
+                }
+            }
+        Q += (double)hi + ((double)lo + (double)sm);
+    }
+    red[ty][tx] = Q;
+    __syncthreads();
+    if (ty == 0 && ok) {
+        double a = 0.0;
+        for (int k = 0; k < 8; ++k) a += red[k][tx];
+        double *w = ws + (size_t)blockIdx.y * 3 * p;
+        w[col] = cnt;
+        w[p + col] = mu;
+        w[2 * p + col] = a;
+    }
+}
+
 __global__ void col_stats_merge_kernel(const double *ws, int chunks, int p, double *mean, double *rsd)
 {
     const int col = blockIdx.x * blockDim.x + threadIdx.x;
@@ -153,6 +249,55 @@ __global__ void __launch_bounds__(256) standardize_kernel(const T *__restrict__ 
                 __nv_bfloat16 lo = __float2bfloat16_rn(rem);
                 Xhi[o] = __bfloat16_as_ushort(hi);
                 Xlo[o] = __bfloat16_as_ushort(lo);
+            }
+        }
+    }
+}
+
+// FP32 input: Xs = (x - mean) * rsd formed in double-single FP32 (the FP64
+// mean and 1/sd split into two floats; TwoSum and an FMA-exact product), so
+// that the FP64 plane needs only hi + lo, the FP32 and BF16 planes none.
+__global__ void __launch_bounds__(256) standardize_f32_kernel(const float *__restrict__ X, long long n, int p,
+                                                              long long ld, const double *mean, const double *rsd,
+                                                              double *Xs64, float *Xs32, uint16_t *Xhi,
+                                                              uint16_t *Xlo, long long ldk)
+{
+    __shared__ float th[32][33], tl[32][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int col0 = blockIdx.x * 32;
+    const long long row0 = (long long)blockIdx.y * 32;
+    const int col = col0 + tx;
+    const double mu = col < p ? mean[col] : 0.0, rs = col < p ? rsd[col] : 0.0;
+    const float mh = (float)mu, ml = (float)(mu - (double)mh);
+    const float rh = (float)rs, rl = (float)(rs - (double)rh);
+    for (int k = 0; k < 4; ++k) {
+        const long long r = row0 + ty + 8 * k;
+        float vh = 0.f, vl = 0.f;
+        if (r < n && col < p) {
+            float sd, dl, dll;
+            dev_split(X[r * ld + col], mh, ml, sd, dl, dll);          // x - mean = sd + dl + dll
+            vh = __fmul_rn(sd, rh);
+            const float ve = __fmaf_rn(sd, rh, -vh);               // sd * rh = vh + ve exactly
+            vl = __fmaf_rn(__fadd_rn(dl, dll), rh, __fmaf_rn(sd, rl, ve));
+        }
+        th[ty + 8 * k][tx] = vh;
+        tl[ty + 8 * k][tx] = vl;
+    }
+    __syncthreads();
+    for (int k = 0; k < 4; ++k) {
+        const int c = col0 + ty + 8 * k;
+        const long long r = row0 + tx;
+        if (c < p && r < n) {
+            const float vh = th[tx][ty + 8 * k], vl = tl[tx][ty + 8 * k];
+            const long long o = (long long)c * ldk + r;
+            if (Xs64) Xs64[o] = (double)vh + (double)vl;
+            const float f = __fadd_rn(vh, vl);
+            if (Xs32) Xs32[o] = f;
+            if (Xhi) {
+                const __nv_bfloat16 hi = __float2bfloat16_rn(f);
+                const float rem = __fadd_rn(__fsub_rn(vh, __bfloat162float(hi)), vl);
+                Xhi[o] = __bfloat16_as_ushort(hi);
+                Xlo[o] = __bfloat16_as_ushort(__float2bfloat16_rn(rem));
             }
         }
     }
@@ -432,7 +577,7 @@ cudaError_t launch_col_stats_split(const void *X, int dtype, long long n, int p,
     if (dtype == 1)
         col_stats_part_kernel<double><<<g, 256, 0, s>>>((const double *)X, n, p, ld, rows_per, ws);
     else
-        col_stats_part_kernel<float><<<g, 256, 0, s>>>((const float *)X, n, p, ld, rows_per, ws);
+        col_stats_part_f32_kernel<<<g, 256, 0, s>>>((const float *)X, n, p, ld, rows_per, ws);
     note_launch();
     col_stats_merge_kernel<<<(p + 31) / 32, 32, 0, s>>>(ws, chunks, p, mean, rsd); note_launch();
     return cudaGetLastError();
@@ -448,8 +593,7 @@ cudaError_t launch_standardize(const void *X, int dtype, long long n, int p, lon
         standardize_kernel<double><<<g, 256, 0, s>>>((const double *)X, n, p, ld, mean, rsd,
                                                      Xs64, Xs32, Xhi, Xlo, ldk);
     else
-        standardize_kernel<float><<<g, 256, 0, s>>>((const float *)X, n, p, ld, mean, rsd,
-                                                    Xs64, Xs32, Xhi, Xlo, ldk);
+        standardize_f32_kernel<<<g, 256, 0, s>>>((const float *)X, n, p, ld, mean, rsd, Xs64, Xs32, Xhi, Xlo, ldk);
     note_launch();
     return cudaGetLastError();
 }
