@@ -707,7 +707,7 @@ static pc_status corr_impl(pc_handle *h, const void *X, int32_t dtype, int64_t l
     const size_t po = (size_t)o * h->ldk;                  // first plane row of this problem
     CK(fpc::launch_col_stats_split(Xd, dtype, n, p, ld, h->mean + o, h->rsd + o, h->stats_ws, s));
     const bool want_bf16 = h->precision == 2 && fpc::tc_gemm_available();
-    CK(fpc::launch_standardize(Xd, dtype, n, p, ld, h->mean + o, h->rsd + o, h->Xs64 + po,
+    CK(fpc::launch_standardize(Xd, dtype, n, p, ld, h->mean + o, h->rsd + o, h->stats_ws, h->Xs64 + po,
                                h->precision == 1 ? h->Xs32 + po : nullptr,
                                want_bf16 ? h->Xhi + po : nullptr, want_bf16 ? h->Xlo + po : nullptr, h->ldk,
                                s));
@@ -742,7 +742,7 @@ static pc_status corr_impl(pc_handle *h, const void *X, int32_t dtype, int64_t l
     } else if (h->precision == 1 || !want_bf16) {
         if (h->precision == 2) {
             // tensor-core path not available in this build: FP32 operands on the CUDA cores
-            CK(fpc::launch_standardize(Xd, dtype, n, p, ld, h->mean + o, h->rsd + o, nullptr, h->Xs32 + po,
+            CK(fpc::launch_standardize(Xd, dtype, n, p, ld, h->mean + o, h->rsd + o, h->stats_ws, nullptr, h->Xs32 + po,
                                        nullptr, nullptr, h->ldk, s));
         }
         CK(fpc::launch_syrk_f32(h->Xs32 + po, n, h->ldk, p, C32b, ldb, s));

@@ -166,8 +166,10 @@ cudaError_t launch_col_stats(const void *X, int dtype, long long n, int p, long 
 cudaError_t launch_col_stats_split(const void *X, int dtype, long long n, int p, long long ld,
                                    double *mean, double *rsd, double *ws, cudaStream_t s);
 size_t col_stats_ws_bytes(long long n, int p);
+// stats_ws: the workspace launch_col_stats_split filled for the same X (FP32
+// input reads the float splits of mean and 1/sd from it)
 cudaError_t launch_standardize(const void *X, int dtype, long long n, int p, long long ld,
-                               const double *mean, const double *rsd, double *Xs64,
+                               const double *mean, const double *rsd, const double *stats_ws, double *Xs64,
                                float *Xs32, uint16_t *Xhi, uint16_t *Xlo, long long ldk,
                                cudaStream_t s);
 cudaError_t launch_syrk_f64(const double *Xs, long long n, long long ldk, int p, double *C64,

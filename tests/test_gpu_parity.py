@@ -76,6 +76,28 @@ def test_corr_matches_oracle(fp, precision, shape):
     assert np.all(np.diag(C32) == 1.0) and np.all(np.diag(C64) == 1.0)
 
 
+@pytest.mark.parametrize("pad", [0, 3])
+def test_corr_large_means_and_strided_rows(fp, pad):
+    # FP32 columns whose means are large against their spread (the statistics take
+    # x - mean in split FP32 arithmetic), read through a row stride that is not a
+    # multiple of 4 floats when pad = 3 (per-element loads instead of 16-byte rows)
+    n, p = 2113, 45
+    X = _sem_case(23, p, n, 0.3, np.float32).astype(np.float64)
+    rng = np.random.default_rng(5)
+    X = X * rng.uniform(0.01, 3.0, p) + rng.choice([-1.0, 1.0], p) * 10.0 ** rng.uniform(0, 4, p)
+    X = X.astype(np.float32)
+    W = np.zeros((n, p + pad), dtype=np.float32)
+    W[:, :p] = X
+    Xd = torch.from_numpy(W).cuda()[:, :p]
+    with fp.PC(n, p, 0.01, -1, precision=2) as pc:
+        pc.corr(Xd)
+        C32, C64 = pc.corr_get()
+    Co = oracle.pearson(X)
+    # the oracle's own FP64 rounding of x - mean is about 1e-16 * |mean| / sd here
+    assert np.abs(C64 - Co).max() <= 1e-10
+    assert np.abs(C32.astype(np.float64) - Co).max() <= 2e-6
+
+
 def test_corr_host_input_equals_device_input(fp):
     X = _sem_case(5, 40, 2000, 0.3)
     n, p = X.shape
