@@ -36,6 +36,15 @@ SM_COUNT, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.070
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_GHZ / 1000.0   # 80.5
 
 
+def dominant_class(tim):
+    """The kernel class with the most device time among those with algorithmic work.
+    The stage bookkeeping (head, commit, degrees, tail: counts, scans, sepset records)
+    and the proposal scoring have none of their own; their time stays in class_ms and
+    the largest class of all is named beside the roofline."""
+    from paper_2109_04626_gb300 import fastpc as fp
+    return max((c for c in fp.TIMING_CLASSES if c not in ("bookkeeping", "scoring")), key=lambda c: tim[c][0])
+
+
 def measured_peaks():
     """(bf16 TFLOP/s burst, HBM GB/s, source): the machine's measured peaks when the
     file is present, else the fallback figures."""
@@ -49,9 +58,9 @@ def measured_peaks():
 
 
 # DRAM bytes (read + write) per launch of a class's dominant kernel, from one
-# ncu capture of the current kernel (profiles/prec_update_p95_dense.md: two
-# launches of prec_update_kernel read 0.345 MB and 0.647 MB, wrote 0)
-DRAM_BYTES_PER_LAUNCH = {("p95_dense", "prec"): 4.96e5}
+# ncu capture of the current kernel (profiles/); absent: not captured since the
+# kernel last changed (the roofline's traffic is then null)
+DRAM_BYTES_PER_LAUNCH = {}
 
 
 def parse():
@@ -412,7 +421,7 @@ def run_ours(args):
     tim = fp.pc_timing(pc.h, reset=True)
     fp.pc_set_opt(pc.h, "timing", 0)
     cls = fp.TIMING_CLASSES
-    dom = max(cls, key=lambda c: tim[c][0])
+    dom = dominant_class(tim)
     di = cls.index(dom)
     dom_ms = tim[dom][0]
     flops_cls = list(st_t["flops_class"]) + [0.0]
@@ -429,7 +438,8 @@ def run_ours(args):
                 "kernel_ms_per_step": dom_ms, "launch_groups": tim[dom][1],
                 "peak_source": "nominal FP64 1.25 TFLOP/s" if peak == FP64_PEAK_TFLOPS else
                 "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
-                "class_ms": {c: tim[c][0] for c in cls}}
+                "class_ms": {c: tim[c][0] for c in cls},
+                "largest_class": max(cls, key=lambda c: tim[c][0])}
 
     # the correlation step against the tensor roofline: useful flops n p (p+1) of the
     # symmetric product (the BF16x3 split issues three products per useful one)
@@ -611,7 +621,7 @@ def run_many(args):
     st_t = step_b()
     tim = fp.pc_timing(pb.h, reset=True)
     cls = fp.TIMING_CLASSES
-    dom = max(cls, key=lambda c: tim[c][0])
+    dom = dominant_class(tim)
     di = cls.index(dom)
     flops_cls = list(st_t["flops_class"]) + [0.0]
     dom_flops = flops_cls[di] if di > 0 else sum(2.0 * n_ * p_ * (p_ + 1) for n_, p_ in zip(ns, ps))
@@ -620,7 +630,8 @@ def run_many(args):
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": None, "kernel": dom, "measured_on": "batched handle, timing step",
                 "peak_source": "nominal FP64 1.25 TFLOP/s" if peak == FP64_PEAK_TFLOPS else
-                "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz", "class_ms": {c: tim[c][0] for c in cls}}
+                "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz", "class_ms": {c: tim[c][0] for c in cls},
+                "largest_class": max(cls, key=lambda c: tim[c][0])}
     pb.close()
 
     # end to end with host buffers: X from pinned host memory, adjacencies back to the host

@@ -15,6 +15,8 @@ Paper passages followed (see the C file for each routine):
   * Fisher-z test: Sec. 2.2.2, Eq. 1 and the replacement of line 7 of Alg. 1.
   * Skeleton: Algorithm 1 (conventional) and Algorithm 2 (reversed order),
     PC-stable deletion at the end of each stage.
+  * Orientation: Algorithm 1, Phase II (unshielded colliders, rules R1-R4),
+    which Algorithm 2 shares (Sec. 3.3).
 """
 from __future__ import annotations
 
@@ -90,6 +92,14 @@ def _load():
         lib.oracle_result_scalars.argtypes = [ctypes.c_void_p, lp]
         lib.oracle_num_threads.restype = ctypes.c_int
         lib.oracle_num_threads.argtypes = []
+        u8 = ctypes.POINTER(ctypes.c_uint8)
+        i64 = ctypes.POINTER(ctypes.c_int64)
+        lib.oracle_meek.restype = ctypes.c_int32
+        lib.oracle_meek.argtypes = [u8, u8, ctypes.c_int32]
+        lib.oracle_codes.restype = None
+        lib.oracle_codes.argtypes = [u8, u8, ctypes.c_int32, ctypes.POINTER(ctypes.c_int8)]
+        lib.oracle_orient.restype = ctypes.c_int32
+        lib.oracle_orient.argtypes = [u8, ctypes.c_int32, i64, ip, ip, ctypes.POINTER(ctypes.c_int8)]
         _lib = lib
         return lib
 
@@ -240,3 +250,55 @@ def skeleton(C, n: int, alpha: float, max_level: int = -1, reversed_order: bool 
         "stageA_ran": bool(sc[2]),
         "levels": [int(x) for x in ls[: int(sc[3])]],
     }
+
+
+# --------------------------------------------------------------------------- Phase II
+# Codes of an oriented graph, per ordered pair (a, b): 0 no edge, 1 a - b,
+# 2 a -> b, 3 a <- b, 4 a <-> b (two colliders or rules disagree).
+NONE, UNDIRECTED, FORWARD, BACKWARD, BIDIRECTED = 0, 1, 2, 3, 4
+
+
+def _u8p(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+
+
+def orient(adj, sepsets) -> tuple:
+    """Phase II of Algorithm 1 on a skeleton and its separation sets.
+
+    ``sepsets`` maps (a, b) to the separating set's nodes, or to a skeleton()
+    record (level, side, rank, nodes); a pair missing from it decides no
+    collider.  Returns (codes p x p int8, rule rounds)."""
+    lib = _load()
+    adj = np.ascontiguousarray(adj, dtype=np.uint8)
+    p = adj.shape[0]
+    off = np.full(p * p, -2, dtype=np.int64)
+    ln = np.zeros(p * p, dtype=np.int32)
+    pool = []
+    for (a, b), v in sepsets.items():
+        nodes = v[3] if isinstance(v, tuple) and len(v) == 4 and isinstance(v[3], tuple) else v
+        e = min(a, b) * p + max(a, b)
+        if nodes is None:
+            off[e] = -1
+            continue
+        off[e] = len(pool)
+        ln[e] = len(nodes)
+        pool.extend(int(x) for x in nodes)
+    pool_a = np.ascontiguousarray(pool if pool else [0], dtype=np.int32)
+    out = np.empty(p * p, dtype=np.int8)
+    rounds = lib.oracle_orient(_u8p(adj), p, off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _ip(ln),
+                               _ip(pool_a), out.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)))
+    return out.reshape(p, p), int(rounds)
+
+
+def meek(adj, marks) -> tuple:
+    """Rules R1-R4 (Algorithm 1, Phase II) on a partially directed graph given by
+    its skeleton and arrowhead marks (marks[a, b] = 1: arrowhead at b on {a,b}).
+    Returns (codes, rule rounds)."""
+    lib = _load()
+    adj = np.ascontiguousarray(adj, dtype=np.uint8)
+    mk = np.ascontiguousarray(marks, dtype=np.uint8).copy()
+    p = adj.shape[0]
+    rounds = lib.oracle_meek(_u8p(adj), _u8p(mk), p)
+    out = np.empty(p * p, dtype=np.int8)
+    lib.oracle_codes(_u8p(adj), _u8p(mk), p, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)))
+    return out.reshape(p, p), int(rounds)

@@ -594,3 +594,137 @@ int oracle_num_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------ */
+/* Phase II of Algorithm 1 (Sec. 3.3: Algorithm 2 leaves it unchanged): the
+ * skeleton is oriented from the separation sets, first the unshielded
+ * colliders, then rules R1-R4 repeated until none orients an edge.
+ *
+ * Edge marks: mk[a*p+b] = 1 iff the edge {a,b} carries an arrowhead at b.
+ * a - b: no mark on either end; a -> b: mk[a*p+b] only; both: a <-> b.
+ * Output codes per ordered pair: 0 no edge, 1 a - b, 2 a -> b, 3 a <- b,
+ * 4 a <-> b.
+ *
+ * Reading R15: the listing orders neither loop.  Every collider found marks
+ * both of its edges at once (an edge marked from both ends by two colliders
+ * is bidirected); the rules run in rounds, each evaluating R1-R4 on every
+ * undirected edge against the marks at the start of the round and then
+ * applying all orientations found (found in both directions: bidirected),
+ * until a round orients nothing.
+ * Reading R16: R4 as printed requires X_k -> X_l and calls X_k, X_l
+ * non-adjacent; read as X_k and X_j non-adjacent (the published form of the
+ * rule, Meek 1995).                                                         */
+
+static int ph2_dir(const uint8_t *adj, const uint8_t *mk, int32_t p, int32_t x, int32_t y)
+{   /* x -> y */
+    return adj[(size_t)x * p + y] && mk[(size_t)x * p + y] && !mk[(size_t)y * p + x];
+}
+
+static int ph2_und(const uint8_t *adj, const uint8_t *mk, int32_t p, int32_t x, int32_t y)
+{   /* x - y */
+    return adj[(size_t)x * p + y] && !mk[(size_t)x * p + y] && !mk[(size_t)y * p + x];
+}
+
+/* Does one of R1-R4 (Algorithm 1, Phase II) change the undirected edge a - b
+ * into a -> b?  Returns the rule number, or 0.  The paper's letters: the edge
+ * oriented is X_i - X_j with X_i = a, X_j = b for R2-R4, and X_j - X_k with
+ * X_j = a, X_k = b for R1.                                                  */
+static int ph2_rule(const uint8_t *adj, const uint8_t *mk, int32_t p, int32_t a, int32_t b)
+{
+    /* R1: X_i -> X_j, X_i and X_k non-adjacent */
+    for (int32_t c = 0; c < p; ++c)
+        if (c != b && ph2_dir(adj, mk, p, c, a) && !adj[(size_t)c * p + b]) return 1;
+    /* R2: X_i -> X_k -> X_j */
+    for (int32_t c = 0; c < p; ++c)
+        if (ph2_dir(adj, mk, p, a, c) && ph2_dir(adj, mk, p, c, b)) return 2;
+    /* R3: X_i - X_k -> X_j and X_i - X_l -> X_j, X_k and X_l non-adjacent */
+    for (int32_t c = 0; c < p; ++c) {
+        if (!(ph2_und(adj, mk, p, a, c) && ph2_dir(adj, mk, p, c, b))) continue;
+        for (int32_t d = c + 1; d < p; ++d)
+            if (ph2_und(adj, mk, p, a, d) && ph2_dir(adj, mk, p, d, b) && !adj[(size_t)c * p + d]) return 3;
+    }
+    /* R4: X_i - X_k -> X_l and X_k -> X_l -> X_j, X_k and X_j non-adjacent */
+    for (int32_t c = 0; c < p; ++c) {
+        if (c == b || !ph2_und(adj, mk, p, a, c) || adj[(size_t)c * p + b]) continue;
+        for (int32_t d = 0; d < p; ++d)
+            if (ph2_dir(adj, mk, p, c, d) && ph2_dir(adj, mk, p, d, b)) return 4;
+    }
+    return 0;
+}
+
+/* R1-R4 in rounds (Reading R15) on the marks mk, in place.  Returns the number
+ * of rounds that oriented at least one edge.                                */
+int32_t oracle_meek(const uint8_t *adj, uint8_t *mk, int32_t p)
+{
+    const size_t pp = (size_t)p * p;
+    uint8_t *next = (uint8_t *)malloc(pp ? pp : 1);
+    int32_t rounds = 0;
+    for (;;) {
+        int changed = 0;
+        memcpy(next, mk, pp);
+        for (int32_t a = 0; a < p; ++a)
+            for (int32_t b = 0; b < p; ++b)
+                if (a != b && ph2_und(adj, mk, p, a, b) && ph2_rule(adj, mk, p, a, b)) {
+                    next[(size_t)a * p + b] = 1;
+                    changed = 1;
+                }
+        memcpy(mk, next, pp);
+        if (!changed) break;
+        ++rounds;
+    }
+    free(next);
+    return rounds;
+}
+
+/* Unshielded colliders (Algorithm 1, Phase II, lines 1-5): for every pair of
+ * non-adjacent vertices i < j and every common neighbour k, k not in S(i,j)
+ * puts arrowheads at k on i - k and j - k (Reading R15).  S(i,j) is given as
+ * sep_off[i*p+j]: an offset into pool with sep_len[i*p+j] members, -1 for
+ * "every other node" (the closed-form stage l = p-2), -2 when no set was
+ * recorded (no collider is decided from such a pair).                       */
+void oracle_vstructures(const uint8_t *adj, int32_t p, const int64_t *sep_off, const int32_t *sep_len,
+                        const int32_t *pool, uint8_t *mk)
+{
+    memset(mk, 0, (size_t)p * p);
+    for (int32_t i = 0; i < p; ++i)
+        for (int32_t j = i + 1; j < p; ++j) {
+            if (adj[(size_t)i * p + j]) continue;
+            const int64_t off = sep_off[(size_t)i * p + j];
+            if (off < 0) continue;                      /* every other node, or none */
+            const int32_t len = sep_len[(size_t)i * p + j];
+            for (int32_t k = 0; k < p; ++k) {
+                if (k == i || k == j || !adj[(size_t)i * p + k] || !adj[(size_t)j * p + k]) continue;
+                int in_s = 0;
+                for (int32_t t = 0; t < len; ++t) in_s |= pool[off + t] == k;
+                if (!in_s) {
+                    mk[(size_t)i * p + k] = 1;
+                    mk[(size_t)j * p + k] = 1;
+                }
+            }
+        }
+}
+
+/* Marks -> codes (0 none, 1 a - b, 2 a -> b, 3 a <- b, 4 a <-> b). */
+void oracle_codes(const uint8_t *adj, const uint8_t *mk, int32_t p, int8_t *out)
+{
+    for (int32_t a = 0; a < p; ++a)
+        for (int32_t b = 0; b < p; ++b) {
+            const size_t e = (size_t)a * p + b, t = (size_t)b * p + a;
+            int8_t c = 0;
+            if (a != b && adj[e]) c = (int8_t)(mk[e] ? (mk[t] ? 4 : 2) : (mk[t] ? 3 : 1));
+            out[e] = c;
+        }
+}
+
+/* The whole Phase II: colliders, rules, codes.  Returns the rule rounds.    */
+int32_t oracle_orient(const uint8_t *adj, int32_t p, const int64_t *sep_off, const int32_t *sep_len,
+                      const int32_t *pool, int8_t *out)
+{
+    const size_t pp = (size_t)p * p;
+    uint8_t *mk = (uint8_t *)malloc(pp > 0 ? pp : 1);
+    oracle_vstructures(adj, p, sep_off, sep_len, pool, mk);
+    const int32_t rounds = oracle_meek(adj, mk, p);
+    oracle_codes(adj, mk, p, out);
+    free(mk);
+    return rounds;
+}

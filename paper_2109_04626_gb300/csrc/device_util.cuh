@@ -126,6 +126,62 @@ __device__ __forceinline__ void unrank_lex(unsigned long long rank, int d, int l
     }
 }
 
+// unrank_lex with the positions in a fixed-size array (l <= KM): the loops run
+// to the compile-time bound with guards, so pos stays in registers.  Same
+// positions as unrank_lex; entries from l on are 0.  binom (row stride ldb) may
+// be a shared-memory copy of the table's first columns (plain loads).
+template <int KM>
+__device__ __forceinline__ void unrank_lex_fixed(unsigned long long rank, int d, int l,
+                                                 const unsigned long long *binom, int ldb, int (&pos)[KM])
+{
+    int lg = 0;
+    while ((1 << lg) < d + 1) ++lg;
+    const bool search = l * lg < d;
+    int x = 0;
+#pragma unroll
+    for (int i = 0; i < KM; ++i) {
+        pos[i] = 0;
+        if (i >= l) continue;
+        const int r1 = l - i;                                  // size of the remaining subset
+        if (search) {
+            const unsigned long long base = binom[(long long)(d - x) * ldb + r1];
+            const unsigned long long target = base - rank;
+            int lo = x, hi = d - r1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (binom[(long long)(d - mid) * ldb + r1] >= target) lo = mid;
+                else hi = mid - 1;
+            }
+            pos[i] = lo;
+            rank -= base - binom[(long long)(d - lo) * ldb + r1];
+            x = lo + 1;
+        } else {
+            while (x < d - r1) {
+                const unsigned long long c = binom[(long long)(d - x - 1) * ldb + (r1 - 1)];
+                if (rank < c) break;
+                rank -= c;
+                ++x;
+            }
+            pos[i] = x++;
+        }
+    }
+}
+
+// Ascending sort of a fixed-size register array (odd-even transposition
+// network: compile-time indices only).
+template <int KM>
+__device__ __forceinline__ void sort_fixed(int (&a)[KM])
+{
+#pragma unroll
+    for (int r = 0; r < KM; ++r)
+#pragma unroll
+        for (int i = r & 1; i + 1 < KM; i += 2) {
+            const int x = a[i], y = a[i + 1];
+            a[i] = min(x, y);
+            a[i + 1] = max(x, y);
+        }
+}
+
 // First index i in [0, len) with a[i] > key (len if none).
 template <typename T>
 __device__ __forceinline__ long long upper_bound_dev(const T *a, long long len, T key)

@@ -135,7 +135,8 @@ __global__ void __launch_bounds__(1024) tail_kernel(GraphDev g, TestParams tp, i
         return;
     }
     if (t == 0) sh_need = 0;
-    const int per = (p + 1023) / 1024;
+    const int nth = blockDim.x;                          // 32..1024, a multiple of 32
+    const int per = (p + nth - 1) / nth;
     const int s0 = min(p, t * per), s1 = min(p, s0 + per);
     long long sum = 0;
     int mx = 0;
@@ -146,7 +147,7 @@ __global__ void __launch_bounds__(1024) tail_kernel(GraphDev g, TestParams tp, i
     part[t] = sum;
     smax[t] = mx;
     __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
+    for (int off = 1; off < nth; off <<= 1) {
         long long v = (t >= off) ? part[t - off] : 0;
         int m2 = (t >= off) ? smax[t - off] : 0;
         __syncthreads();
@@ -160,8 +161,8 @@ __global__ void __launch_bounds__(1024) tail_kernel(GraphDev g, TestParams tp, i
         run += g.deg[i];
     }
     if (t == 0) {
-        const long long tot = part[1023];
-        const int lstar = smax[1023] - 1;              // -1 when no edge is left
+        const long long tot = part[nth - 1];
+        const int lstar = smax[nth - 1] - 1;              // -1 when no edge is left
         g.ooff[p] = tot;
         I->n_opairs = tot;
         sh_removed = I->edges != (unsigned long long)tot;   // the commit deleted edges
@@ -309,7 +310,7 @@ __global__ void __launch_bounds__(1024) head_kernel(GraphDev g, TestParams tp, d
     }
     __shared__ ull sh[4 * 32];
     const int p = g.p, l = I->l, t = threadIdx.x;
-    const int per = (p + 1023) / 1024;
+    const int per = (p + (int)blockDim.x - 1) / (int)blockDim.x;   // <= HEAD_PER_MAX
     const int s0 = min(p, t * per), s1 = min(p, s0 + per);
     // tests per pair of each of this thread's nodes; 0 for complement-path nodes' direct count
     ull Tn[HEAD_PER_MAX];
@@ -358,14 +359,14 @@ __global__ void __launch_bounds__(1024) head_kernel(GraphDev g, TestParams tp, d
             rr = sat_add(rr, prows(dg, T));
         }
     }
+    // owner node of every ordered pair (the small-stage kernel's work items; the commit)
+    for (int u = s0; u < s1; ++u) {
+        const long long b = g.ooff[u];
+        for (int jj = 0, dg = g.deg[u]; jj < dg; ++jj) g.opu[b + jj] = u;
+    }
     const bool small = tp.lane_stages && tp.precision != 0 && l <= LANE_LMAX;
     int rounds = 0;
     if (small && tot[0] > 0) {
-        // owner node of every ordered pair (the small-stage kernel's work items)
-        for (int u = s0; u < s1; ++u) {
-            const long long b = g.ooff[u];
-            for (int jj = 0, dg = g.deg[u]; jj < dg; ++jj) g.opu[b + jj] = u;
-        }
         // rank-major rounds of the lane kernel: at most tp.lane_rounds chunks of
         // every direct pair, the rest in the pair-major remainder space rn_off
         for (int off = 16; off > 0; off >>= 1) {
@@ -1079,24 +1080,53 @@ __global__ void __launch_bounds__(256) ci_redecide_kernel(GraphDev g, TestParams
     }
 }
 
+// ---------------------------------------------------------------- small binomial table
+// C(x, r) for x < SB_ROWS, r <= KC_MAX copied to shared memory, so that the
+// unranking of a dropped set (at most KC_MAX positions of at most SB_ROWS - 1
+// candidates) reads no global table: its binary searches are chains of
+// dependent loads.
+constexpr int SB_ROWS = PREC_MAX;
+constexpr int SB_COLS = KC_MAX + 1;
+__device__ __forceinline__ void load_small_binom(const GraphDev &g, ull *sb)
+{
+    for (int e = threadIdx.x; e < SB_ROWS * SB_COLS; e += blockDim.x) {
+        const int x = e / SB_COLS, r = e - x * SB_COLS;
+        sb[e] = x < g.ldb && r < g.ldb ? g.binom[(long long)x * g.ldb + r] : 0ull;
+    }
+}
+
 // ---------------------------------------------------------------- complement path
 // With P = corr[F,F]^{-1}, F = adj(u) u {u}, and the dropped set R
 // (S = adj(u)\{v}\R, |R| = k = d - l), the {u,v} block of corr[T,T]^{-1},
 // T = S u {u,v}, is Q = P_TT - P_TR P_RR^{-1} P_RT restricted to {u,v}
 // (inverse of a principal submatrix); r = -Q_uv / sqrt(Q_uu Q_vv), and the
 // Schur complement H of Sec. 4 is Q^{-1}: h11 = Q_vv/det, h22 = Q_uu/det.
+constexpr int COMP_OFF_MAX = 2048;    // per-node offsets staged in shared memory up to this p
 __global__ void __launch_bounds__(128) ci_complement_kernel(GraphDev g, TestParams tp)
 {
     if (stopped(g.info)) return;
     const int l = g.info->l;
     const ull total = g.info->total_comp;
+    if ((ull)blockIdx.x >= total) return;                // no test reaches this CTA
+    // the unranking table and, when they fit, the per-node test offsets in shared
+    // memory: the searches in both are chains of dependent loads
+    __shared__ ull sb[SB_ROWS * SB_COLS];
+    __shared__ ull soff[COMP_OFF_MAX];
+    load_small_binom(g, sb);
+    const bool off_sm = g.p < COMP_OFF_MAX;
+    if (off_sm)
+        for (int i = threadIdx.x; i <= g.p; i += blockDim.x) soff[i] = g.cn_off[i];
+    __syncthreads();
+    const ull *noff = off_sm ? soff : g.cn_off;
     const double sq = sqrt((double)(tp.n - l - 3));
     ull nt = 0, ndg = 0, nfl = 0;
-    for (ull t = blockIdx.x * (ull)blockDim.x + threadIdx.x; t < total;
-         t += (ull)gridDim.x * blockDim.x) {
+    const ull nthr = (ull)gridDim.x * blockDim.x;
+    // tests are dealt CTA-first, so that a stage with a few thousand tests still
+    // spreads its FP64 work (the bound of a test) over every SM
+    for (ull t = (ull)threadIdx.x * gridDim.x + blockIdx.x; t < total; t += nthr) {
         int u, j, d;
         ull rank;
-        locate_test(g, g.cn_off, l, t, u, j, d, rank);
+        locate_test(g, noff, l, t, u, j, d, rank);
         const int v = g.nbr[nidx(g, u) + j];
         const int k = d - l;
         const int side = u > v;
@@ -1106,40 +1136,67 @@ __global__ void __launch_bounds__(128) ci_complement_kernel(GraphDev g, TestPara
         if (*(volatile ull *)bp < key) continue;
         const ull T = g.binom[(long long)d * g.ldb + l];
         int posR[KC_MAX];
-        unrank_lex(T - 1 - rank, d, k, g.binom, g.ldb, posR);   // complement of lex is reverse lex
+        unrank_lex_fixed<KC_MAX>(T - 1 - rank, d, k, sb, SB_COLS, posR);   // complement of lex is reverse lex
         const double *P = g.prec + (long long)u * PREC_MAX * PREC_MAX;
         const short *ps = g.prec_pos + pidx(g, u, 0);
         const int su = ps[u], sv = ps[v];
         int sr[KC_MAX];
-        for (int i = 0; i < k; ++i) sr[i] = ps[cand_node(g, u, j, d, posR[i])];
-        if (g.row_off) sort_small(sr, k);
-        double L[KC_MAX][KC_MAX], yu[KC_MAX], yv[KC_MAX];
-        bool bad = false;
-        for (int i = 0; i < k && !bad; ++i) {
-            for (int c = 0; c <= i; ++c) {
-                double s = P[sr[i] * PREC_MAX + sr[c]];
-                for (int q = 0; q < c; ++q) s -= L[i][q] * L[c][q];
-                if (c == i) {
-                    if (!(s > 0.0)) { bad = true; break; }
-                    L[i][i] = sqrt(s);
-                } else {
-                    L[i][c] = s / L[c][c];
-                }
+#pragma unroll
+        for (int i = 0; i < KC_MAX; ++i) sr[i] = i < k ? ps[cand_node(g, u, j, d, posR[i])] : 0x7fffffff;
+        if (g.row_off) sort_fixed<KC_MAX>(sr);                   // ascending slots (ids); unused entries last
+        // every entry of P the test reads (P_RR lower triangle, P_Ru, P_Rv and the {u,v}
+        // block) is loaded before the factorisation starts: one round of independent
+        // loads instead of one per row
+        double L[KC_MAX][KC_MAX], pu[KC_MAX], pv[KC_MAX];
+#pragma unroll
+        for (int i = 0; i < KC_MAX; ++i) {
+            pu[i] = pv[i] = 0.0;
+            if (i < k) {
+                const double *Pi = P + (long long)sr[i] * PREC_MAX;
+#pragma unroll
+                for (int c = 0; c <= i; ++c) L[i][c] = Pi[sr[c]];
+                pu[i] = Pi[su];
+                pv[i] = Pi[sv];
             }
-            if (bad) break;
-            double su_ = P[sr[i] * PREC_MAX + su], sv_ = P[sr[i] * PREC_MAX + sv];
-            for (int q = 0; q < i; ++q) {
-                su_ -= L[i][q] * yu[q];
-                sv_ -= L[i][q] * yv[q];
-            }
-            yu[i] = su_ / L[i][i];
-            yv[i] = sv_ / L[i][i];
         }
         double Quu = P[su * PREC_MAX + su], Qvv = P[sv * PREC_MAX + sv], Quv = P[su * PREC_MAX + sv];
-        for (int i = 0; i < k; ++i) {
-            Quu -= yu[i] * yu[i];
-            Qvv -= yv[i] * yv[i];
-            Quv -= yu[i] * yv[i];
+        // Cholesky of P_RR in place and the solves for P_Ru, P_Rv; every loop runs to
+        // KC_MAX with guards so that L, the reciprocal pivots and y stay in registers
+        double ri[KC_MAX], yu[KC_MAX], yv[KC_MAX];
+        bool bad = false;
+#pragma unroll
+        for (int i = 0; i < KC_MAX; ++i) {
+            yu[i] = yv[i] = 0.0;
+            if (i >= k || bad) continue;
+#pragma unroll
+            for (int c = 0; c < i; ++c) {
+                double s = L[i][c];
+#pragma unroll
+                for (int q = 0; q < c; ++q) s = fma(-L[i][q], L[c][q], s);
+                L[i][c] = s * ri[c];
+            }
+            double s = L[i][i];
+#pragma unroll
+            for (int q = 0; q < i; ++q) s = fma(-L[i][q], L[i][q], s);
+            if (!(s > 0.0)) {
+                bad = true;
+                continue;
+            }
+            ri[i] = 1.0 / sqrt(s);
+            double su_ = pu[i], sv_ = pv[i];
+#pragma unroll
+            for (int q = 0; q < i; ++q) {
+                su_ = fma(-L[i][q], yu[q], su_);
+                sv_ = fma(-L[i][q], yv[q], sv_);
+            }
+            yu[i] = su_ * ri[i];
+            yv[i] = sv_ * ri[i];
+        }
+#pragma unroll
+        for (int i = 0; i < KC_MAX; ++i) {
+            Quu = fma(-yu[i], yu[i], Quu);
+            Qvv = fma(-yv[i], yv[i], Qvv);
+            Quv = fma(-yu[i], yv[i], Quv);
         }
         const double det = Quu * Qvv - Quv * Quv;
         const double h11 = Qvv / det, h22 = Quu / det;
@@ -1171,15 +1228,20 @@ __global__ void __launch_bounds__(128) ci_complement_kernel(GraphDev g, TestPara
 // submatrix); a requested block is built by a symmetric sweep of corr[F,F],
 // F = adj(u) u {u} (ascending ids).
 constexpr int PREC_CHUNKS = 8;        // CTAs sharing one node's block downdate
-constexpr int PREC_RMAX = 48;         // removals applied in one block downdate
+constexpr int PREC_RMAX = 64;         // removals applied in one block downdate (two per lane)
+constexpr int PREC_JPL = (PREC_MAX + 31) / 32;   // kept columns per lane
 
-// One node per blockIdx.x, its rows split over blockIdx.y.  A maintained block
-// drops the members the last commit deleted, R, all at once:
-//   P_TT <- P_TT - P_TR P_RR^{-1} P_RT      (T = the members kept),
-// i.e. row i gains y_i P[R,:] with y_i = -P[i,R] P_RR^{-1}.  Every CTA reads
-// only its own rows and the rows of R, which no CTA writes, so the chunks need
-// no synchronisation; prec_mark_kernel retires R afterwards.  A requested
-// block (chunk 0) is built by a symmetric sweep of corr[F,F], F = adj(u) u {u}.
+// One node per blockIdx.x, its kept rows split over blockIdx.y.  A maintained
+// block drops the members the last commit deleted, R, all at once (the inverse
+// of a principal submatrix):
+//   P_TT <- P_TT - P_TR P_RR^{-1} P_RT      (T = the members kept).
+// Every CTA factors P_RR = L D L^T (the same arithmetic in each), then each warp
+// takes one of the CTA's kept rows i: y = P_RR^{-1} P_Ri by two triangular
+// solves (lanes own entries of y), and P_ij -= y . P_Rj for the kept columns j.
+// Only rows of R (never written here) and a warp's own row are read, so the
+// CTAs need no synchronisation; members retired earlier are skipped, and
+// prec_mark_kernel retires R afterwards.  A requested block (chunk 0) is built by
+// a symmetric sweep of corr[F,F], F = adj(u) u {u}.
 __global__ void __launch_bounds__(512) prec_update_kernel(GraphDev g, TestParams tp, const double *C64, int ldc)
 {
     const int u = blockIdx.x;
@@ -1191,37 +1253,53 @@ __global__ void __launch_bounds__(512) prec_update_kernel(GraphDev g, TestParams
     const int m0 = g.prec_m[u];
     if (m0 > 0) {
         int *rem = mem;
+        __shared__ int keep[PREC_MAX];
+        __shared__ int nkeep;
         double *P = g.prec + (long long)u * PREC_MAX * PREC_MAX;
         const int *pm = g.prec_mem + (long long)u * PREC_MAX;
         const short *pos = g.prec_pos + pidx(g, u, 0);
         const uint32_t *row = g.adj + (long long)u * g.W;
-        // members deleted by the last commit, ascending slots (same in every chunk):
-        // one slot per thread (m0 <= PREC_MAX < blockDim.x), ballots, warp offsets
-        __shared__ int wcnt[16];
+        // the block's slots: deleted by the last commit (R), kept (T: u and the members
+        // still adjacent), or retired earlier; both lists in ascending slot order (one
+        // slot per thread, m0 <= PREC_MAX < blockDim.x), by ballots and warp offsets
+        __shared__ int wcnt[16], wkc[16];
         {
             const int sl = threadIdx.x, wid = threadIdx.x >> 5, ln = threadIdx.x & 31;
-            bool gone = false;
+            bool gone = false, kept = false;
             if (sl < m0) {
                 const int w = pm[sl];
-                gone = w != u && pos[w] >= 0 && !((row[w >> 5] >> (w & 31)) & 1u);
+                if (w == u) {
+                    kept = true;
+                } else if (pos[w] >= 0) {
+                    kept = (row[w >> 5] >> (w & 31)) & 1u;
+                    gone = !kept;
+                }
             }
-            const unsigned bal = __ballot_sync(0xffffffffu, gone);
-            if (ln == 0) wcnt[wid] = __popc(bal);
+            const unsigned bal = __ballot_sync(0xffffffffu, gone), balk = __ballot_sync(0xffffffffu, kept);
+            if (ln == 0) {
+                wcnt[wid] = __popc(bal);
+                wkc[wid] = __popc(balk);
+            }
             __syncthreads();
             if (threadIdx.x == 0) {
-                int acc = 0;
+                int acc = 0, acck = 0;
                 for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
-                    const int c = wcnt[i];
+                    const int c = wcnt[i], ck = wkc[i];
                     wcnt[i] = acc;
+                    wkc[i] = acck;
                     acc += c;
+                    acck += ck;
                 }
                 nrem = acc;
+                nkeep = acck;
             }
             __syncthreads();
-            if (gone) rem[wcnt[wid] + __popc(bal & ((1u << ln) - 1u))] = sl;
+            const unsigned lt = (1u << ln) - 1u;
+            if (gone) rem[wcnt[wid] + __popc(bal & lt)] = sl;
+            if (kept) keep[wkc[wid] + __popc(balk & lt)] = sl;
         }
         __syncthreads();
-        const int nr = nrem;
+        const int nr = nrem, nt = nkeep;
         if (nr == 0) return;
         if (blockIdx.y == 0 && threadIdx.x == 0) atomicAdd(&g.ctr->prec_downdates, 1ull);
         if (nr > PREC_RMAX) {
@@ -1229,51 +1307,97 @@ __global__ void __launch_bounds__(512) prec_update_kernel(GraphDev g, TestParams
             if (blockIdx.y == 0 && threadIdx.x == 0) g.prec_m[u] = -2;
             return;
         }
-        const int rows_per = (m0 + PREC_CHUNKS - 1) / PREC_CHUNKS;
-        const int r0 = blockIdx.y * rows_per, r1 = min(m0, r0 + rows_per);
-        if (r0 >= r1) return;
-        double *S = smd;                         // nr x nr: P_RR, then -P_RR^{-1}
-        double *PR = S + nr * nr;                // nr x m0: rows of R
-        double *Y = PR + (size_t)nr * m0;        // (r1 - r0) x nr
-        double *ck = Y + (size_t)(r1 - r0) * nr; // sweep column buffer
-        __shared__ int sbad;
-        if (threadIdx.x == 0) sbad = 0;
-        for (int e = threadIdx.x; e < nr * nr; e += blockDim.x) S[e] = P[rem[e / nr] * PREC_MAX + rem[e % nr]];
-        for (int e = threadIdx.x; e < nr * m0; e += blockDim.x) PR[e] = P[rem[e / m0] * PREC_MAX + e % m0];
-        __syncthreads();
-        if (nr <= 16) {
-            // a few removals: one warp sweeps (warp-level sync per pivot)
-            if (threadIdx.x < 32) sweep_inverse_warp(S, nr, nr, ck, &sbad);
-        } else {
-            sweep_inverse_block(S, nr, nr, ck, &sbad);   // S = -P_RR^{-1}
+        const int per = (nt + PREC_CHUNKS - 1) / PREC_CHUNKS;
+        const int t0 = blockIdx.y * per, t1 = min(nt, t0 + per);
+        if (t0 >= t1) return;                    // no kept rows in this chunk
+        // P_RR = L D L^T, right-looking with one barrier per pivot: the trailing update of
+        // pivot k reads the unscaled column k (times 1/D_k); column k-1 is scaled to L in
+        // the same phase; thread 0 updates the next diagonal entry first and forms 1/D.
+        double *A = smd;                         // nr x nr row-major: L below the diagonal
+        double *rdv = A + nr * nr;               // 1/D
+        for (int e = threadIdx.x; e < nr * nr; e += blockDim.x) {
+            const int a2 = e / nr, b2 = e - a2 * nr;
+            if (b2 <= a2) A[e] = P[rem[a2] * PREC_MAX + rem[b2]];
         }
         __syncthreads();
-        if (sbad) {
+        // pivot flags alternate by parity: thread 0 writes the flag of pivot k+1 while
+        // the other threads may still read the flag of pivot k
+        __shared__ int badv[2];
+        if (threadIdx.x == 0) {
+            const double d = A[0];
+            badv[0] = !(d > DEGEN);
+            rdv[0] = 1.0 / d;
+        }
+        const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+        bool brk = false;
+        for (int k = 0; k < nr; ++k) {
+            __syncthreads();                     // column k and 1/D_k final
+            if (badv[k & 1]) {                   // uniform: every thread reads the same flag
+                brk = true;
+                break;
+            }
+            if (k > 0)
+                for (int i = k + threadIdx.x; i < nr; i += blockDim.x) A[i * nr + k - 1] *= rdv[k - 1];
+            const double rk = rdv[k];
+            for (int i = k + 1 + w; i < nr; i += nw) {
+                const double lik = A[i * nr + k] * rk;
+                for (int c = k + 1 + lane; c <= i; c += 32) {
+                    const double v = fma(-lik, A[c * nr + k], A[i * nr + c]);
+                    A[i * nr + c] = v;
+                    if (c == k + 1 && i == k + 1) {          // thread 0: the next pivot
+                        badv[(k + 1) & 1] = !(v > DEGEN);
+                        rdv[k + 1] = 1.0 / v;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (brk) {
             // P_RR is a principal block of an SPD inverse; a pivot at the floor means the
             // block has lost accuracy: drop it (rebuilt from corr if the node needs it)
             if (blockIdx.y == 0 && threadIdx.x == 0) g.prec_m[u] = -2;
             return;
         }
-        // y_i = P[i,R] S  for the chunk's rows
-        for (int e = threadIdx.x; e < (r1 - r0) * nr; e += blockDim.x) {
-            const int i = r0 + e / nr, b = e % nr;
-            double acc = 0.0;
-            for (int a2 = 0; a2 < nr; ++a2) acc = fma(P[i * PREC_MAX + rem[a2]], S[a2 * nr + b], acc);
-            Y[e] = acc;
-        }
-        __syncthreads();
-        for (int i = r0 + (threadIdx.x >> 5); i < r1; i += blockDim.x >> 5) {
-            bool in_r = false;
-            for (int a2 = 0; a2 < nr; ++a2) in_r |= rem[a2] == i;
-            if (in_r) continue;                  // rows of R are read by the other chunks
-            const double *y = Y + (size_t)(i - r0) * nr;
-            for (int c = threadIdx.x & 31; c < m0; c += 32) {
-                double v = P[i * PREC_MAX + c];
-                for (int b = 0; b < nr; ++b) v = fma(y[b], PR[b * m0 + c], v);
-                P[i * PREC_MAX + c] = v;
+        const bool two = nr > 32;                // lanes hold y_q for q = lane, lane + 32
+        for (int t = t0 + w; t < t1; t += nw) {
+            double *Pi = P + (long long)keep[t] * PREC_MAX;
+            double b0 = lane < nr ? Pi[rem[lane]] : 0.0;
+            double b1 = two && lane + 32 < nr ? Pi[rem[lane + 32]] : 0.0;
+            for (int k = 0; k < nr; ++k) {        // L z = b (unit lower)
+                const double zk = __shfl_sync(0xffffffffu, k < 32 ? b0 : b1, k & 31);
+                if (lane > k && lane < nr) b0 = fma(-A[lane * nr + k], zk, b0);
+                if (two && lane + 32 > k && lane + 32 < nr) b1 = fma(-A[(lane + 32) * nr + k], zk, b1);
+            }
+            if (lane < nr) b0 *= rdv[lane];
+            if (two && lane + 32 < nr) b1 *= rdv[lane + 32];
+            for (int k = nr - 1; k > 0; --k) {    // L^T y = D^{-1} z
+                const double yk = __shfl_sync(0xffffffffu, k < 32 ? b0 : b1, k & 31);
+                if (lane < k) b0 = fma(-A[k * nr + lane], yk, b0);
+                if (two && lane + 32 < k) b1 = fma(-A[k * nr + lane + 32], yk, b1);
+            }
+            double acc[PREC_JPL];
+#pragma unroll
+            for (int x = 0; x < PREC_JPL; ++x) {
+                const int jj = lane + 32 * x;
+                acc[x] = jj < nt ? Pi[keep[jj]] : 0.0;
+            }
+            for (int q = 0; q < nr; ++q) {
+                const double yq = __shfl_sync(0xffffffffu, q < 32 ? b0 : b1, q & 31);
+                const double *Pq = P + (long long)rem[q] * PREC_MAX;
+#pragma unroll
+                for (int x = 0; x < PREC_JPL; ++x) {
+                    const int jj = lane + 32 * x;
+                    if (jj < nt) acc[x] = fma(-yq, Pq[keep[jj]], acc[x]);
+                }
+            }
+#pragma unroll
+            for (int x = 0; x < PREC_JPL; ++x) {
+                const int jj = lane + 32 * x;
+                if (jj < nt) Pi[keep[jj]] = acc[x];
             }
         }
-        if (blockIdx.y == 0 && threadIdx.x == 0) atomicAdd(&g.ctr->flops_prec, 2ull * m0 * m0 * nr);
+        if (blockIdx.y == 0 && threadIdx.x == 0)
+            atomicAdd(&g.ctr->flops_prec, (ull)nr * nr * nr / 3 + 2ull * nt * nr * (nr + nt));
         return;
     }
     if (blockIdx.y != 0 || !g.prec_need[u]) return;
@@ -1354,6 +1478,9 @@ __global__ void commit_kernel(GraphDev g, int l_fixed, int explicit_sets, int co
     const int p = g.p;
     const int lane = threadIdx.x & 31;
     ull removed = 0, canon = 0;
+    __shared__ ull sb[SB_ROWS * SB_COLS];
+    load_small_binom(g, sb);
+    __syncthreads();
     // warp-uniform trip count: the sepsets of a warp's removed pairs are expanded
     // by the whole warp below
     for (long long base = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); base < nop;
@@ -1363,7 +1490,8 @@ __global__ void commit_kernel(GraphDev g, int l_fixed, int explicit_sets, int co
         int su = 0, jj = 0, dd = 0;
         ull rank = 0, off = 0;
         if (o < nop) {
-            const int u = (int)(upper_bound_dev(g.ooff, (long long)p + 1, o) - 1);
+            // owner node: the head kernel's table inside the stage loop, else a search
+            const int u = l_fixed < 0 ? g.opu[o] : (int)(upper_bound_dev(g.ooff, (long long)p + 1, o) - 1);
             const int j = (int)(o - g.ooff[u]);
             const int v = g.nbr[nidx(g, u) + j];
             if (u < v) {
@@ -1421,10 +1549,13 @@ __global__ void commit_kernel(GraphDev g, int l_fixed, int explicit_sets, int co
                 // expand through the complement: R = the kd dropped positions, at lex
                 // rank C(dd,l) - 1 - rank among the kd-subsets; S = the rest,
                 // ascending (a ballot prefix keeps the order)
-                int posR[KC_MAX + 1], nodeR[KC_MAX];
+                int posR[KC_MAX], nodeR[KC_MAX];
                 const ull T = g.binom[(long long)s_dd * g.ldb + l];
-                unrank_lex(T - 1 - s_rank, s_dd, kd, g.binom, g.ldb, posR);
-                for (int i = 0; i < kd; ++i) nodeR[i] = cand_node(g, s_su, s_jj, s_dd, posR[i]);
+                const bool small_d = s_dd < SB_ROWS;
+                unrank_lex_fixed<KC_MAX>(T - 1 - s_rank, s_dd, kd, small_d ? sb : g.binom, small_d ? SB_COLS : g.ldb,
+                                         posR);
+#pragma unroll
+                for (int i = 0; i < KC_MAX; ++i) nodeR[i] = i < kd ? cand_node(g, s_su, s_jj, s_dd, posR[i]) : -1;
                 int o2 = 0;
                 for (int y0 = 0; y0 <= s_dd; y0 += 32) {
                     const int y = y0 + lane;
@@ -1433,7 +1564,8 @@ __global__ void commit_kernel(GraphDev g, int l_fixed, int explicit_sets, int co
                     if (y <= s_dd && y != s_jj) {
                         w = nb[y];
                         keep = true;
-                        for (int i = 0; i < kd; ++i) keep &= nodeR[i] != w;
+#pragma unroll
+                        for (int i = 0; i < KC_MAX; ++i) keep &= nodeR[i] != w;
                     }
                     const unsigned kb = __ballot_sync(0xffffffffu, keep);
                     if (keep) g.pool[s_off + o2 + __popc(kb & ((1u << lane) - 1u))] = w;
@@ -1590,17 +1722,22 @@ cudaError_t launch_level_degrees(GraphDev g, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// One-CTA stage kernels (head, tail): one thread per node up to 1024 (fewer warps
+// at each barrier for small p), else 1024 threads with several nodes each.
+static int stage_threads(int p) { return p >= 1024 ? 1024 : std::max(32, (p + 31) / 32 * 32); }
+
 cudaError_t launch_tail(GraphDev g, TestParams tp, int cap, int mode, const int *stagea_singular,
                         int stagea_launched, cudaGraphConditionalHandle hc, int use_cond, StageConds sc,
                         cudaStream_t s)
 {
-    tail_kernel<<<1, 1024, 0, s>>>(g, tp, cap, mode, stagea_singular, stagea_launched, hc, use_cond, sc); note_launch();
+    tail_kernel<<<1, stage_threads(g.p), 0, s>>>(g, tp, cap, mode, stagea_singular, stagea_launched, hc, use_cond, sc);
+    note_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_head(GraphDev g, TestParams tp, double budget, int mmax_direct, StageConds sc, cudaStream_t s)
 {
-    head_kernel<<<1, 1024, 0, s>>>(g, tp, budget, mmax_direct, sc); note_launch();
+    head_kernel<<<1, stage_threads(g.p), 0, s>>>(g, tp, budget, mmax_direct, sc); note_launch();
     return cudaGetLastError();
 }
 
@@ -1685,10 +1822,8 @@ cudaError_t launch_ci_complement(GraphDev g, TestParams tp, cudaStream_t s)
 cudaError_t launch_prec_update(GraphDev g, TestParams tp, const double *C64, int ldc, cudaStream_t s)
 {
     const int mmax = std::min(g.p + 1, PREC_MAX);
-    const int rows = (mmax + PREC_CHUNKS - 1) / PREC_CHUNKS;
     const size_t build = ((size_t)mmax * mmax + (size_t)mmax) * sizeof(double);
-    const size_t down = ((size_t)PREC_RMAX * PREC_RMAX + (size_t)PREC_RMAX * mmax + (size_t)rows * PREC_RMAX +
-                         PREC_RMAX) * sizeof(double);
+    const size_t down = ((size_t)PREC_RMAX * PREC_RMAX + (size_t)PREC_RMAX) * sizeof(double);
     const size_t smem = std::max(build, down);
     cudaError_t e = cudaFuncSetAttribute(prec_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
