@@ -453,6 +453,23 @@ def run_ours(args):
                          "issued_tflops": 3 * ach if mixed_prec == 2 else ach, "ms_per_step": tim["corr"][0],
                          "peak_source": f"bf16 dense burst, {src}"}
 
+    # Phase II of Algorithm 1 (pc_orient) on this skeleton: outside the metric's step,
+    # timed on its own (host wall time; pc_orient synchronises once per rule round)
+    codes = np.empty((p, p), dtype=np.int8)
+    fp.pc_orient(pc.h, p, codes)
+    o_t = []
+    for _ in range(5):
+        t0 = time.perf_counter()
+        _, o_rounds = fp.pc_orient(pc.h, p, codes)
+        o_t.append(time.perf_counter() - t0)
+    orient = {"ms": 1e3 * float(np.median(o_t)), "rule_rounds": o_rounds,
+              "directed": int((codes == 2).sum()), "undirected": int((codes == 1).sum() // 2),
+              "bidirected": int((codes == 4).sum() // 2)}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        ref, _ = oracle.orient(adj_ours, fp.pc_sepsets(pc.h, p))
+        orient["matches_oracle_phase2"] = bool(np.array_equal(codes, ref))
+
     # plain GPU form: FP32 SIMT GEMM, FP32 tests one warp per test (no rank-major
     # small-stage kernel, no complement path), one host-driven launch sequence per
     # stage (no graph), lexicographic order
@@ -518,6 +535,7 @@ def run_ours(args):
                                   "tests_executed": lex_st["tests_executed"]},
                 "learned": learned,
                 "plain_gpu": plain,
+                "orient": orient,
                 "e2e": e2e,
                 "gpu_launches": int(launches),
                 "clocks": clk.summary()}

@@ -220,6 +220,20 @@ pc_status pc_sepsets_count(pc_handle *h, int64_t *n_removed, int64_t *pool_len);
 pc_status pc_sepsets_get(pc_handle *h, int32_t *pairs, int32_t *level, int32_t *side,
                          int64_t *rank, int64_t *off, int32_t *pool);
 
+/* pc_orient -- Phase II of Algorithm 1 (which Algorithm 2 shares, Sec. 3.3) on
+ * the last pc_skeleton result and its separation sets: every unshielded triple
+ * i - k - j with k not in S(i,j) becomes i -> k <- j, then rules R1-R4 are
+ * applied until none orients an edge.  Order-free: all colliders are marked at
+ * once and each rule round reads the marks of the round before; an edge marked
+ * from both ends is bidirected.  R4 is taken with X_k and X_j non-adjacent.
+ * codes_out: p x p int8, row-major, host or device, caller-owned; for the
+ * ordered pair (a, b): 0 no edge, 1 a - b, 2 a -> b, 3 a <- b, 4 a <-> b (a
+ * batched handle: the block-diagonal p x p matrix of all instances).
+ * rounds_out (host, may be NULL): rule rounds that oriented an edge.
+ * PC_ERR_STATE before pc_skeleton, PC_ERR_ARG for a NULL codes_out.  Runs on
+ * the handle's stream; synchronises once per rule round. */
+pc_status pc_orient(pc_handle *h, int8_t *codes_out, int32_t *rounds_out);
+
 /* pc_ci_batch -- b raw CI tests on the current correlation matrix (the index
  * matrix B of Sec. 4 / Algorithm 3): test k is (ij[2k], ij[2k+1] | S[k*l .. k*l+l-1]).
  * Outputs r_out[k] (partial correlation), z_out[k] (sqrt(n-l-3)|atanh r|),

@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfastpc.so")
-SOURCES = ["corr.cu", "corr_tc.cu", "stage_a.cu", "level.cu", "fastpc_api.cu", "corr_noalloc.cu", "mlp.cu"]
+SOURCES = ["corr.cu", "corr_tc.cu", "stage_a.cu", "level.cu", "fastpc_api.cu", "corr_noalloc.cu", "mlp.cu",
+           "orient.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

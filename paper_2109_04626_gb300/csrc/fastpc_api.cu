@@ -78,6 +78,10 @@ struct pc_handle {
     LevelInfo *info_h = nullptr;     // pinned mirror
     DevCounters *ctr_h = nullptr;    // pinned mirror
     ull *sepcnt_h = nullptr;
+    // orientation (Phase II): arrowhead bitsets, two rounds' worth, and a flag
+    uint32_t *or_mk = nullptr;
+    int *or_changed = nullptr;
+    int8_t *or_codes = nullptr;
     bool have_skel = false;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     pc_stats last{};
@@ -1502,6 +1506,48 @@ extern "C" pc_status pc_sepsets_get(pc_handle *h, int32_t *pairs, int32_t *level
         CK(cudaMemcpy(&pl, &h->g.ctr->pool_len, sizeof(ull), cudaMemcpyDeviceToHost));
         if (pl) CK(cudaMemcpy(pool, h->g.pool, (size_t)pl * sizeof(int), cudaMemcpyDeviceToHost));
     }
+    return PC_OK;
+}
+
+// ---------------------------------------------------------------- orientation
+// Algorithm 1, Phase II on the last skeleton and its separation sets: colliders,
+// then rounds of R1-R4 until one orients nothing (order-free reading).
+extern "C" pc_status pc_orient(pc_handle *h, int8_t *codes_out, int32_t *rounds_out)
+{
+    if (!h) return PC_ERR_ARG;
+    if (!h->have_skel) return fail(h, PC_ERR_STATE, "pc_orient before pc_skeleton");
+    if (!codes_out) return fail(h, PC_ERR_ARG, "pc_orient: codes_out is null");
+    cudaStream_t s = h->stream;
+    const size_t words = (size_t)h->p * h->g.W;
+    if (!h->or_mk) {
+        CK(dalloc(h, &h->or_mk, 4 * words * sizeof(uint32_t)));
+        CK(dalloc(h, &h->or_changed, sizeof(int)));
+    }
+    uint32_t *ah = h->or_mk, *at = ah + words, *ah2 = at + words, *at2 = ah2 + words;
+    CK(fpc::launch_orient_colliders(h->g, ah, at, s));
+    // each round that changes something adds a mark; there are at most 32 W p marks
+    const long long max_rounds = (long long)words * 32 + 1;
+    int32_t rounds = 0;
+    for (;;) {
+        CK(fpc::launch_orient_round(h->g, ah, at, ah2, at2, h->or_changed, s));
+        int changed = 0;
+        CK(cudaMemcpyAsync(&changed, h->or_changed, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        std::swap(ah, ah2);
+        std::swap(at, at2);
+        if (!changed) break;
+        if (++rounds > max_rounds) return fail(h, PC_ERR_INTERNAL, "pc_orient: rules did not settle");
+    }
+    const size_t pp = (size_t)h->p * h->p;
+    int8_t *dst = codes_out;
+    if (!is_device_ptr(codes_out)) {
+        if (!h->or_codes) CK(dalloc(h, &h->or_codes, pp));
+        dst = h->or_codes;
+    }
+    CK(fpc::launch_orient_codes(h->g, ah, at, dst, s));
+    if (dst != codes_out) CK(cudaMemcpyAsync(codes_out, dst, pp, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (rounds_out) *rounds_out = rounds;
     return PC_OK;
 }
 

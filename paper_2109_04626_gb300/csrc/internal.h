@@ -214,6 +214,11 @@ cudaError_t launch_ci_lane(GraphDev g, TestParams tp, const float *C32, const do
                            int range, bool prop, cudaStream_t s);
 int lane_range_of(int l);
 cudaError_t launch_prec_update(GraphDev g, TestParams tp, const double *C64, int ldc, cudaStream_t s);
+// ---- orientation, Algorithm 1 Phase II (orient.cu): arrowhead bitsets ah/at (p x W)
+cudaError_t launch_orient_colliders(GraphDev g, uint32_t *ah, uint32_t *at, cudaStream_t s);
+cudaError_t launch_orient_round(GraphDev g, const uint32_t *ah, const uint32_t *at, uint32_t *ah2, uint32_t *at2,
+                                int *changed, cudaStream_t s);
+cudaError_t launch_orient_codes(GraphDev g, const uint32_t *ah, const uint32_t *at, int8_t *out, cudaStream_t s);
 cudaError_t launch_commit(GraphDev g, long long n_opairs_cap, int l_fixed, int explicit_sets,
                           cudaStream_t s);
 size_t scan_ws_bytes(long long n);

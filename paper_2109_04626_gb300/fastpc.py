@@ -80,6 +80,7 @@ def load():
         "pc_skeleton": (i32, [vp, vp, ctypes.POINTER(pc_stats)]),
         "pc_sepsets_count": (i32, [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
         "pc_sepsets_get": (i32, [vp, vp, vp, vp, vp, vp, vp]),
+        "pc_orient": (i32, [vp, vp, ctypes.POINTER(i32)]),
         "pc_ci_batch": (i32, [vp, vp, vp, i32, i64, vp, vp, vp]),
         "pc_last_stats": (i32, [vp, ctypes.POINTER(pc_stats)]),
         "pc_threshold": (dbl, [vp]),
@@ -288,6 +289,20 @@ def pc_sepsets(h, p: int) -> dict:
     return out
 
 
+# codes of pc_orient per ordered pair (a, b)
+NO_EDGE, UNDIRECTED, FORWARD, BACKWARD, BIDIRECTED = 0, 1, 2, 3, 4
+
+
+def pc_orient(h, p: int, out=None):
+    """Phase II (Algorithm 1) on the last skeleton: (codes, rule rounds).  codes is a
+    p x p int8 numpy array (or ``out``, a host array or CUDA tensor of that shape):
+    0 no edge, 1 a - b, 2 a -> b, 3 a <- b, 4 a <-> b."""
+    codes = out if out is not None else np.empty((p, p), dtype=np.int8)
+    rounds = ctypes.c_int32()
+    _check(h, load().pc_orient(h, ctypes.c_void_p(_ptr(codes)), ctypes.byref(rounds)))
+    return codes, int(rounds.value)
+
+
 def pc_ci_batch(h, ij, S, l: int, r_out=None, indep_out=None, z_out=None):
     """ij: (b,2) int32 CUDA tensor, S: (b,l) int32 CUDA tensor.  Returns (r, indep, z) tensors."""
     import torch
@@ -416,6 +431,9 @@ class PC:
 
     def sepsets(self):
         return pc_sepsets(self.h, self.p)
+
+    def orient(self, out=None):
+        return pc_orient(self.h, self.p, out)
 
     def ci_batch(self, ij, S, l):
         return pc_ci_batch(self.h, ij, S, l)
