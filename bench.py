@@ -70,9 +70,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="p95_dense",
-                    choices=["p20_fp64", "p95_dense", "p500_powerlaw", "p1000_er", "many64"],
+                    choices=["p20_fp64", "p95_dense", "p500_powerlaw", "p1000_er", "many64", "paper_sweep"],
                     help="many64: 64 independent SEMs (p in [50,400], edge prob in [0.05,0.3], "
-                         "n in [2000,20000]), conventional order")
+                         "n in [2000,20000]), conventional order; paper_sweep: the paper's "
+                         "simulation (p = 15..100, both orders, CI tests per graph)")
+    ap.add_argument("--sweep-mc", type=int, default=100, help="paper_sweep: graphs per size")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
@@ -224,6 +226,11 @@ def cpu_baseline(X, w, budget_s=20.0):
 def run_reference(args):
     rank, world, local = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), 0
     if rank != 0:
+        return 0
+    if args.workload == "paper_sweep":
+        # the sweep's metric is a ratio of test counts, which the oracle recounts inside it
+        print(json.dumps({"impl": "reference", "unavailable": "paper_sweep reports test-count ratios; "
+                          "the oracle's counts are checked inside the sweep itself"}), flush=True)
         return 0
     if args.workload == "many64":
         # a bounded sample: the 8 smallest of the 64 instances per step
@@ -693,12 +700,76 @@ def run_many(args):
     return 0
 
 
+SWEEP = {"sizes": list(range(15, 101, 5)), "n": 5000, "alpha": 1e-3, "oracle_instances": 5}
+# Sec. 6.2: CI tests for the 95-node graphs (PC, PC-reverse, PC-reverse-parallel)
+PAPER_TESTS_P95 = {"pc": 90394, "pc_reverse": 8678, "pc_reverse_parallel": 4563}
+
+
+def run_sweep(args):
+    """The paper's simulation (Sec. 6.1-6.2): for p = 15, 20, ..., 100, args.sweep_mc
+    graphs each (mean degree 5, two hubs of 10 neighbours, weights +-U[0.2,0.8],
+    alpha = 1e-3), CI tests per graph and skeleton time of the conventional
+    (Algorithm 1) and reversed (Algorithm 2) orders on the GPU.  The oracle recounts
+    the first graphs of every size."""
+    import torch
+    from paper_2109_04626_gb300 import fastpc as fp, sem
+    rank, world, local = dist_setup(args)
+    fp.load()
+    check = rank == 0 and world == 1 and not args.no_cpu_baseline
+    if check:
+        import oracle
+    n, alpha = SWEEP["n"], SWEEP["alpha"]
+    rows = []
+    with ClockSampler(local if world > 1 else torch.cuda.current_device()) as clk:
+        for p in SWEEP["sizes"]:
+            pcs = {o: fp.PC(n, p, alpha, -1, order=o) for o in (0, 1)}
+            acc = {o: np.zeros(3) for o in (0, 1)}      # canonical tests, executed tests, skeleton ms
+            equal = True
+            for m in range(args.sweep_mc):
+                s = sem.make_sweep(p, m, n=n)
+                Xd = torch.from_numpy(s.X).cuda()
+                counts = {}
+                for o, pc in pcs.items():
+                    pc.corr(Xd)
+                    pc.skeleton()                        # the first search of a handle builds its graph
+                    _, st = pc.skeleton()
+                    counts[o] = st["tests_canonical"]
+                    acc[o] += (st["tests_canonical"], st["tests_executed"], st["t_skeleton_ms"])
+                if check and m < SWEEP["oracle_instances"]:
+                    C = oracle.pearson(s.X.astype(np.float64))
+                    for o in (0, 1):
+                        R = oracle.skeleton(C, n, alpha, -1, reversed_order=bool(o))
+                        equal &= R["tests_total"] == counts[o]
+            for pc in pcs.values():
+                pc.close()
+            mc = float(args.sweep_mc)
+            conv = {"tests": acc[0][0] / mc, "executed": acc[0][1] / mc, "skeleton_ms": acc[0][2] / mc}
+            rev = {"tests": acc[1][0] / mc, "executed": acc[1][1] / mc, "skeleton_ms": acc[1][2] / mc}
+            rows.append({"p": p, "conventional": conv, "reversed": rev,
+                         "tests_ratio": conv["tests"] / rev["tests"] if rev["tests"] else None,
+                         "time_ratio": conv["skeleton_ms"] / rev["skeleton_ms"] if rev["skeleton_ms"] else None,
+                         "oracle_counts_equal": bool(equal) if check else None})
+    if rank == 0:
+        r95 = next(r for r in rows if r["p"] == 95)
+        line = {"metric": "CI tests per graph: conventional / reversed order (the paper's simulation, Sec. 6.2)",
+                "value": r95["tests_ratio"], "unit": "ratio", "higher_is_better": True, "n_gpus": world,
+                "data": "synthetic",
+                "config": {"workload": "paper_sweep", "sizes": SWEEP["sizes"], "graphs_per_size": args.sweep_mc,
+                           "n": n, "alpha": alpha, "generator": "mean degree 5, two hubs of 10, +-U[0.2,0.8]",
+                           "oracle_recount": f"first {SWEEP['oracle_instances']} graphs per size" if check else None},
+                "sweep": rows, "paper_p95_tests": PAPER_TESTS_P95, "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "many64":
         return run_many(args)
+    if args.workload == "paper_sweep":
+        return run_sweep(args)
     return run_ours(args)
 
 

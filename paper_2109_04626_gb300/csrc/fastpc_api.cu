@@ -984,8 +984,7 @@ static pc_status enqueue_level(pc_handle *h, cudaStream_t s, int mmax, bool use_
     {
         auto t = T(5);
         CK(fpc::launch_commit(g, h->opair_cap, -1, 1, s));
-        CK(fpc::launch_level_degrees(g, s));
-        CK(fpc::launch_tail(g, tp, level_cap(h), 0, h->singular, 0, h->hcond, use_cond ? 1 : 0, sc, s));
+        CK(fpc::launch_degrees_tail(g, tp, level_cap(h), h->hcond, use_cond ? 1 : 0, sc, s));
     }
     if (use_prec) {
         if (conds) {

@@ -60,6 +60,7 @@ struct LevelInfo {
     int lane_rounds;                    // rank-major rounds of the small-stage kernel
     int lane_overflow;                  // the FP64 re-decision queue overflowed this stage
     int kernels_run;                    // kernels the captured stage loop executed
+    unsigned deg_ticket;                // CTAs of the stage's degrees kernel done (last one runs the tail)
 };
 
 // Conditional nodes of the captured stage body: the head kernel decides which
@@ -73,8 +74,8 @@ struct StageConds {
 };
 constexpr int LANE_LMAX = 8;            // stages the lane-per-test kernel runs (FP32 modes)
 constexpr int LANE_RANGES = 4;          // small-stage kernel instantiations: l 0-2, 3-4, 5-6, 7-8
-// kernels of a stage outside conditional nodes: head, commit, degrees, tail
-constexpr int STAGE_FIXED_KERNELS = 4;
+// kernels of a stage outside conditional nodes: head, commit, degrees + tail (one kernel)
+constexpr int STAGE_FIXED_KERNELS = 3;
 
 // Everything the stage kernels need, by value.
 struct GraphDev {
@@ -219,6 +220,9 @@ cudaError_t launch_orient_colliders(GraphDev g, uint32_t *ah, uint32_t *at, cuda
 cudaError_t launch_orient_round(GraphDev g, const uint32_t *ah, const uint32_t *at, uint32_t *ah2, uint32_t *at2,
                                 int *changed, cudaStream_t s);
 cudaError_t launch_orient_codes(GraphDev g, const uint32_t *ah, const uint32_t *at, int8_t *out, cudaStream_t s);
+// degrees of the frozen graph, then (last CTA) the stage tail of mode 0 in the same kernel
+cudaError_t launch_degrees_tail(GraphDev g, TestParams tp, int cap, cudaGraphConditionalHandle hc, int use_cond,
+                                StageConds sc, cudaStream_t s);
 cudaError_t launch_commit(GraphDev g, long long n_opairs_cap, int l_fixed, int explicit_sets,
                           cudaStream_t s);
 size_t scan_ws_bytes(long long n);

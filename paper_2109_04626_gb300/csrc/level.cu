@@ -19,8 +19,11 @@
 #include "internal.h"
 #include "device_util.cuh"
 #include <algorithm>
+#include <cooperative_groups.h>
 
 namespace fpc {
+
+namespace cg = cooperative_groups;
 
 typedef unsigned long long ull;
 
@@ -105,6 +108,51 @@ __global__ void degrees_kernel(GraphDev g)
     if (lane == 0) g.deg[u] = base;
 }
 
+__device__ void tail_body(GraphDev g, TestParams tp, int cap, int mode, const int *stagea_singular,
+                          int stagea_launched, cudaGraphConditionalHandle hc, int use_cond, StageConds sc,
+                          bool fused);
+
+// The degrees of a stage's frozen graph, then the stage tail (mode 0) in the last
+// CTA to finish: the CTAs publish their degrees, take a ticket, and the last one
+// resets the ticket and runs tail_body on the complete degree array.
+__global__ void __launch_bounds__(256) degrees_tail_kernel(GraphDev g, TestParams tp, int cap,
+                                                           cudaGraphConditionalHandle hc, int use_cond, StageConds sc)
+{
+    const int lane = threadIdx.x & 31;
+    const int u = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+    if (u < g.p && !stopped(g.info)) {
+        const uint32_t *row = g.adj + (long long)u * g.W;
+        int base = 0;
+        for (int w0 = 0; w0 < g.W; w0 += 32) {
+            const int w = w0 + lane;
+            uint32_t bits = (w < g.W) ? row[w] : 0u;
+            const int c = __popc(bits);
+            int incl = c;
+            for (int off = 1; off < 32; off <<= 1) {
+                int t = __shfl_up_sync(0xffffffffu, incl, off);
+                if (lane >= off) incl += t;
+            }
+            int pos = base + incl - c;
+            while (bits) {
+                int t = __ffs(bits) - 1;
+                g.nbr[nidx(g, u) + pos++] = w * 32 + t;
+                bits &= bits - 1;
+            }
+            base += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        if (lane == 0) g.deg[u] = base;
+    }
+    __shared__ int last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&g.info->deg_ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (threadIdx.x == 0) g.info->deg_ticket = 0u;     // every CTA has taken its ticket
+    tail_body(g, tp, cap, 0, nullptr, 0, hc, use_cond, sc, true);
+}
+
 __device__ __forceinline__ bool comp_eligible(int d, int l, const TestParams &tp)
 {
     const int k = d - l;
@@ -118,9 +166,13 @@ __device__ __forceinline__ bool comp_eligible(int d, int l, const TestParams &tp
 //   Algorithm 1: l = 0, 1, ... while some pair has |adj(u)\{v}| >= l and l <= cap.
 //   Algorithm 2: l = min(cap, L*) (below p-2 once the closed-form stage ran),
 //                then l <- min(l-1, L*) while l >= 0.
-__global__ void __launch_bounds__(1024) tail_kernel(GraphDev g, TestParams tp, int cap, int mode,
-                                                    const int *stagea_singular, int stagea_launched,
-                                                    cudaGraphConditionalHandle hc, int use_cond, StageConds sc)
+// The tail of a stage (any block size that is a multiple of 32, up to 1024): the
+// scan of the degrees into ordered-pair offsets, L*, the next stage and the loop
+// condition, and the precision-block requests.  fused: run by the last CTA of the
+// degrees kernel (which counts itself), whose other CTAs wrote deg: read through L2.
+__device__ void tail_body(GraphDev g, TestParams tp, int cap, int mode, const int *stagea_singular,
+                          int stagea_launched, cudaGraphConditionalHandle hc, int use_cond, StageConds sc,
+                          bool fused)
 {
     LevelInfo *I = g.info;
     __shared__ long long part[1024];
@@ -128,10 +180,11 @@ __global__ void __launch_bounds__(1024) tail_kernel(GraphDev g, TestParams tp, i
     __shared__ int sh_l, sh_go, sh_need, sh_removed;
     const int p = g.p, t = threadIdx.x;
     if (mode == 0 && t == 0) I->body_runs++;
+    const int self = fused ? 0 : 1;                       // this kernel, when it is a launch of its own
     if (stopped(I)) {
         if (use_cond && t == 0) cudaGraphSetConditional(hc, 0u);
         if (sc.use && sc.has_prec && t == 0) cudaGraphSetConditional(sc.prec, 0u);
-        if (sc.use && t == 0) I->kernels_run += 1;
+        if (sc.use && t == 0) I->kernels_run += self;
         return;
     }
     if (t == 0) sh_need = 0;
@@ -141,8 +194,9 @@ __global__ void __launch_bounds__(1024) tail_kernel(GraphDev g, TestParams tp, i
     long long sum = 0;
     int mx = 0;
     for (int i = s0; i < s1; ++i) {
-        sum += g.deg[i];
-        mx = max(mx, g.deg[i]);
+        const int dg = __ldcg(g.deg + i);
+        sum += dg;
+        mx = max(mx, dg);
     }
     part[t] = sum;
     smax[t] = mx;
@@ -158,7 +212,7 @@ __global__ void __launch_bounds__(1024) tail_kernel(GraphDev g, TestParams tp, i
     long long run = part[t] - sum;
     for (int i = s0; i < s1; ++i) {
         g.ooff[i] = run;
-        run += g.deg[i];
+        run += __ldcg(g.deg + i);
     }
     if (t == 0) {
         const long long tot = part[nth - 1];
@@ -209,7 +263,7 @@ __global__ void __launch_bounds__(1024) tail_kernel(GraphDev g, TestParams tp, i
         // precision blocks: all nodes that fit at the first stage, then the nodes
         // that have become small enough for the complement path at this stage
         for (int u = t; u < p; u += blockDim.x) {
-            const int dg = g.deg[u];
+            const int dg = __ldcg(g.deg + u);
             bool need;
             const int pmu = g.prec_m[u];
             if (mode == 1) need = dg >= 2 && dg + 1 <= PREC_MAX && pmu == 0;
@@ -224,10 +278,17 @@ __global__ void __launch_bounds__(1024) tail_kernel(GraphDev g, TestParams tp, i
         // precision blocks change when a node asks for one or blocks lost members
         const int run = sh_go && (sh_need || sh_removed);
         cudaGraphSetConditional(sc.prec, run ? 1u : 0u);
-        I->kernels_run += 1 + (run ? 2 : 0);             // the tail itself, prec update + mark
+        I->kernels_run += self + (run ? 1 : 0);          // the tail itself, the precision update
     } else if (sc.use && t == 0) {
-        I->kernels_run += 1;
+        I->kernels_run += self;
     }
+}
+
+__global__ void __launch_bounds__(1024) tail_kernel(GraphDev g, TestParams tp, int cap, int mode,
+                                                    const int *stagea_singular, int stagea_launched,
+                                                    cudaGraphConditionalHandle hc, int use_cond, StageConds sc)
+{
+    tail_body(g, tp, cap, mode, stagea_singular, stagea_launched, hc, use_cond, sc, false);
 }
 
 __device__ __forceinline__ ull sat_mul(ull a, ull b)
@@ -246,9 +307,9 @@ __device__ __forceinline__ void set_stage_conds(const StageConds &sc, LevelInfo 
     cudaGraphSetConditional(sc.direct, (unsigned)direct);
     if (sc.has_comp) cudaGraphSetConditional(sc.comp, (unsigned)comp);
     if (sc.has_score) cudaGraphSetConditional(sc.score, (unsigned)score);
-    // head, commit, degrees + lane branch (kernel, FP64 pass, overflow pass) + the rest
-    // (the tail counts itself and the precision update)
-    I->kernels_run += STAGE_FIXED_KERNELS - 1 + (lane < LANE_RANGES ? 3 : 0) + direct + comp + 2 * score;
+    // head, commit, degrees + tail, the lane branch (kernel, FP64 pass, overflow pass) and
+    // the rest (the tail counts the precision update)
+    I->kernels_run += STAGE_FIXED_KERNELS + (lane < LANE_RANGES ? 3 : 0) + direct + comp + 2 * score;
 }
 
 // Exclusive saturating scan of NV values per thread over a block of up to 1024
@@ -315,8 +376,9 @@ __global__ void __launch_bounds__(1024) head_kernel(GraphDev g, TestParams tp, d
     // tests per pair of each of this thread's nodes; 0 for complement-path nodes' direct count
     ull Tn[HEAD_PER_MAX];
     bool cm[HEAD_PER_MAX];
-    // proposal rows: a node whose pairs have at least two sets to order gets
-    // deg*(deg-1) score rows (pair j, candidate position x)
+    // proposal rows: a direct-path node whose pairs have at least two sets to order
+    // gets deg*(deg-1) score rows (pair j, candidate position x); the complement path
+    // (dropped sets of at most KC_MAX members, reverse-lexicographic) keeps the plain order
     auto prows = [&](int dg, ull T) -> ull { return (g.row_off && l >= 1 && T >= 2) ? (ull)dg * (ull)(dg - 1) : 0ull; };
     ull v[3] = {0ull, 0ull, 0ull}, mxT = 0;               // direct, complement, proposal rows
     bool sat = false;
@@ -332,8 +394,8 @@ __global__ void __launch_bounds__(1024) head_kernel(GraphDev g, TestParams tp, d
         else {
             v[0] = sat_add(v[0], tot);
             mxT = T > mxT ? T : mxT;
+            v[2] = sat_add(v[2], prows(dg, T));           // complement-path pairs keep the plain order
         }
-        v[2] = sat_add(v[2], prows(dg, T));
     }
     const int ssat = __syncthreads_or(sat);
     ull ex[3], tot[3];
@@ -355,8 +417,10 @@ __global__ void __launch_bounds__(1024) head_kernel(GraphDev g, TestParams tp, d
             g.cn_off[u] = rc;
             if (g.row_off) g.row_off[u] = rows_fit ? rr : 0ull;
             if (cm[u - s0]) rc = sat_add(rc, tt);
-            else rd = sat_add(rd, tt);
-            rr = sat_add(rr, prows(dg, T));
+            else {
+                rd = sat_add(rd, tt);
+                rr = sat_add(rr, prows(dg, T));
+            }
         }
     }
     // owner node of every ordered pair (the small-stage kernel's work items; the commit)
@@ -654,13 +718,20 @@ __device__ __forceinline__ void flush_acc(const WarpAcc &acc, DevCounters *ctr)
 // position x of adj(u)\{v} in ascending order (v sits at index j of nbr[u]), or
 // the x-th candidate of the proposal order when the stage has one (perm holds
 // the candidates' node ids in that order).
-__device__ __forceinline__ int cand_node(const GraphDev &g, int u, int j, int d, int x)
+__device__ __forceinline__ int cand_node(const GraphDev &g, bool prop, int u, int j, int d, int x)
 {
-    if (g.row_off) {
+    if (prop) {
         const ull b = g.row_off[u];
         if (g.row_off[u + 1] > b) return g.perm[b + (ull)j * d + x];
     }
     return g.nbr[nidx(g, u) + x + (x >= j)];
+}
+
+// Did the head order stage l's candidates by the proposal?  Read once per kernel:
+// the plain-order stages of a learned search then touch no proposal table.
+__device__ __forceinline__ bool stage_prop(const GraphDev &g, int l)
+{
+    return g.row_off && g.scored && l >= 0 && g.scored[l];
 }
 
 __device__ __forceinline__ void sort_small(int *a, int n)
@@ -685,6 +756,7 @@ __global__ void __launch_bounds__(256) ci_direct_kernel(GraphDev g, TestParams t
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (stopped(g.info)) return;
     const int l = g.info->l;
+    const bool prop = stage_prop(g, l);
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int m = l + 2;
     if (m > mmax) return;
@@ -711,8 +783,8 @@ __global__ void __launch_bounds__(256) ci_direct_kernel(GraphDev g, TestParams t
         if (*(volatile ull *)bp < key) continue;   // an earlier set already separates
         if (lane == 0) {
             unrank_lex(rank, d, l, g.binom, g.ldb, pos);
-            for (int i = 0; i < l; ++i) nd[i] = cand_node(g, u, j, d, pos[i]);
-            if (g.row_off) sort_small(nd, l);        // the set is tested in ascending-id order
+            for (int i = 0; i < l; ++i) nd[i] = cand_node(g, prop, u, j, d, pos[i]);
+            if (prop) sort_small(nd, l);        // the set is tested in ascending-id order
             nd[l] = u;
             nd[l + 1] = v;
         }
@@ -820,7 +892,7 @@ __device__ __forceinline__ void lane_tests_lex(const GraphDev &g, const TestPara
     const int v = nb[j];
     // proposal order: position x of the enumeration is the node perm[x]
     const short *pr = nullptr;
-    if (PROP && g.row_off && g.row_off[u + 1] > g.row_off[u]) pr = g.perm + g.row_off[u] + (ull)j * d;
+    if (PROP && stage_prop(g, L) && g.row_off[u + 1] > g.row_off[u]) pr = g.perm + g.row_off[u] + (ull)j * d;
     auto member = [&](int x) -> int { return (PROP && pr) ? (int)pr[x] : nb[x + (x >= j)]; };
     const int side = u > v;
     ull *bp = g.best + pidx(g, min(u, v), max(u, v));
@@ -1043,6 +1115,7 @@ __global__ void __launch_bounds__(256) ci_redecide_kernel(GraphDev g, TestParams
         g.info->lane_overflow = 1;
         atomicAdd(&g.ctr->queue_overflows, 1);
     }
+    const bool prop = stage_prop(g, l);
     const double sq = sqrt((double)(tp.n - l - 3));
     WarpAcc acc = {0, 0, 0, 0, 0, 0, 0, 0.f};
     for (ull qi = (blockIdx.x * (ull)blockDim.x + threadIdx.x) >> 5; qi < nq;
@@ -1058,8 +1131,8 @@ __global__ void __launch_bounds__(256) ci_redecide_kernel(GraphDev g, TestParams
         if (*(volatile ull *)bp < key) continue;
         if (lane == 0) {
             unrank_lex(rank, d, l, g.binom, g.ldb, pos);
-            for (int i = 0; i < l; ++i) nd[i] = cand_node(g, u, j, d, pos[i]);
-            if (g.row_off) sort_small(nd, l);
+            for (int i = 0; i < l; ++i) nd[i] = cand_node(g, prop, u, j, d, pos[i]);
+            if (prop) sort_small(nd, l);
             nd[l] = u;
             nd[l + 1] = v;
         }
@@ -1106,6 +1179,7 @@ __global__ void __launch_bounds__(128) ci_complement_kernel(GraphDev g, TestPara
 {
     if (stopped(g.info)) return;
     const int l = g.info->l;
+    const bool prop = stage_prop(g, l);
     const ull total = g.info->total_comp;
     if ((ull)blockIdx.x >= total) return;                // no test reaches this CTA
     // the unranking table and, when they fit, the per-node test offsets in shared
@@ -1119,6 +1193,9 @@ __global__ void __launch_bounds__(128) ci_complement_kernel(GraphDev g, TestPara
     __syncthreads();
     const ull *noff = off_sm ? soff : g.cn_off;
     const double sq = sqrt((double)(tp.n - l - 3));
+    // |r| threshold of the stage: z <= q  <=>  |r| <= tanh(q / sqrt(n - l - 3)); tests within a
+    // relative 1e-12 of it are decided by z itself, exactly as the z form would
+    const double rq = tanh(tp.q / sq);
     ull nt = 0, ndg = 0, nfl = 0;
     const ull nthr = (ull)gridDim.x * blockDim.x;
     // tests are dealt CTA-first, so that a stage with a few thousand tests still
@@ -1133,7 +1210,7 @@ __global__ void __launch_bounds__(128) ci_complement_kernel(GraphDev g, TestPara
         const int a = min(u, v), b = max(u, v);
         const ull key = ((ull)side << 62) | rank;
         ull *bp = g.best + pidx(g, a, b);
-        if (*(volatile ull *)bp < key) continue;
+        const ull best0 = *(volatile ull *)bp;            // checked below, once the candidates are known
         const ull T = g.binom[(long long)d * g.ldb + l];
         int posR[KC_MAX];
         unrank_lex_fixed<KC_MAX>(T - 1 - rank, d, k, sb, SB_COLS, posR);   // complement of lex is reverse lex
@@ -1142,8 +1219,9 @@ __global__ void __launch_bounds__(128) ci_complement_kernel(GraphDev g, TestPara
         const int su = ps[u], sv = ps[v];
         int sr[KC_MAX];
 #pragma unroll
-        for (int i = 0; i < KC_MAX; ++i) sr[i] = i < k ? ps[cand_node(g, u, j, d, posR[i])] : 0x7fffffff;
-        if (g.row_off) sort_fixed<KC_MAX>(sr);                   // ascending slots (ids); unused entries last
+        for (int i = 0; i < KC_MAX; ++i) sr[i] = i < k ? ps[cand_node(g, prop, u, j, d, posR[i])] : 0x7fffffff;
+        if (prop) sort_fixed<KC_MAX>(sr);                   // ascending slots (ids); unused entries last
+        if (best0 < key) continue;                          // an earlier set of this pair separates
         // every entry of P the test reads (P_RR lower triangle, P_Ru, P_Rv and the {u,v}
         // block) is loaded before the factorisation starts: one round of independent
         // loads instead of one per row
@@ -1182,7 +1260,7 @@ __global__ void __launch_bounds__(128) ci_complement_kernel(GraphDev g, TestPara
                 bad = true;
                 continue;
             }
-            ri[i] = 1.0 / sqrt(s);
+            ri[i] = rsqrt(s);
             double su_ = pu[i], sv_ = pv[i];
 #pragma unroll
             for (int q = 0; q < i; ++q) {
@@ -1205,10 +1283,15 @@ __global__ void __launch_bounds__(128) ci_complement_kernel(GraphDev g, TestPara
             ind = true;
             ++ndg;
         } else {
-            const double r = -Quv / sqrt(Quu * Qvv);
-            const double squ = tp.nvec ? sqrt((double)(n_of(tp, u) - l - 3)) : sq;
-            const double z = fabs(r) < 1.0 ? squ * fabs(atanh(r)) : INFINITY;
-            ind = z <= tp.q;
+            const double r = -Quv * rsqrt(Quu * Qvv);
+            const double ar = fabs(r);
+            if (!tp.nvec && fabs(ar - rq) > 1e-12 * rq) {
+                ind = ar < rq;
+            } else {
+                const double squ = tp.nvec ? sqrt((double)(n_of(tp, u) - l - 3)) : sq;
+                const double z = ar < 1.0 ? squ * fabs(atanh(r)) : INFINITY;
+                ind = z <= tp.q;
+            }
         }
         ++nt;
         nfl += (ull)(k * k * k) / 3 + 2ull * k * k + 6ull * k + 20;
@@ -1229,6 +1312,7 @@ __global__ void __launch_bounds__(128) ci_complement_kernel(GraphDev g, TestPara
 // F = adj(u) u {u} (ascending ids).
 constexpr int PREC_CHUNKS = 8;        // CTAs sharing one node's block downdate
 constexpr int PREC_RMAX = 64;         // removals applied in one block downdate (two per lane)
+constexpr int PREC_SHARE_MIN = 16;    // from this many removals one CTA of the cluster factors P_RR
 constexpr int PREC_JPL = (PREC_MAX + 31) / 32;   // kept columns per lane
 
 // One node per blockIdx.x, its kept rows split over blockIdx.y.  A maintained
@@ -1238,11 +1322,13 @@ constexpr int PREC_JPL = (PREC_MAX + 31) / 32;   // kept columns per lane
 // Every CTA factors P_RR = L D L^T (the same arithmetic in each), then each warp
 // takes one of the CTA's kept rows i: y = P_RR^{-1} P_Ri by two triangular
 // solves (lanes own entries of y), and P_ij -= y . P_Rj for the kept columns j.
-// Only rows of R (never written here) and a warp's own row are read, so the
-// CTAs need no synchronisation; members retired earlier are skipped, and
-// prec_mark_kernel retires R afterwards.  A requested block (chunk 0) is built by
-// a symmetric sweep of corr[F,F], F = adj(u) u {u}.
-__global__ void __launch_bounds__(512) prec_update_kernel(GraphDev g, TestParams tp, const double *C64, int ldc)
+// Only rows of R (never written here) and a warp's own row are read; the chunks
+// of a node form one cluster, which meets once after every chunk has read the
+// slot map, so that chunk 0 can retire R (slot map entry -1) at once; members
+// retired earlier are skipped.  A requested block (chunk 0) is built by a
+// symmetric sweep of corr[F,F], F = adj(u) u {u}.
+__global__ void __cluster_dims__(1, PREC_CHUNKS, 1) __launch_bounds__(512)
+    prec_update_kernel(GraphDev g, TestParams tp, const double *C64, int ldc)
 {
     const int u = blockIdx.x;
     if (stopped(g.info)) return;
@@ -1307,14 +1393,25 @@ __global__ void __launch_bounds__(512) prec_update_kernel(GraphDev g, TestParams
             if (blockIdx.y == 0 && threadIdx.x == 0) g.prec_m[u] = -2;
             return;
         }
+        // every chunk of the node's cluster has read the slot map (the exits above are
+        // the same in all of them): chunk 0 retires R while the others go on
+        cg::this_cluster().sync();
+        if (blockIdx.y == 0)
+            for (int i = threadIdx.x; i < nr; i += blockDim.x) g.prec_pos[pidx(g, u, pm[rem[i]])] = -1;
         const int per = (nt + PREC_CHUNKS - 1) / PREC_CHUNKS;
         const int t0 = blockIdx.y * per, t1 = min(nt, t0 + per);
-        if (t0 >= t1) return;                    // no kept rows in this chunk
+        // many removals: cluster rank 0 factors P_RR and the others copy the factor
+        // (distributed shared memory); few: every chunk with rows factors it itself
+        const bool share = nr >= PREC_SHARE_MIN;       // the same in every chunk
+        if (!share && t0 >= t1) return;                // no kept rows in this chunk
         // P_RR = L D L^T, right-looking with one barrier per pivot: the trailing update of
         // pivot k reads the unscaled column k (times 1/D_k); column k-1 is scaled to L in
         // the same phase; thread 0 updates the next diagonal entry first and forms 1/D.
         double *A = smd;                         // nr x nr row-major: L below the diagonal
         double *rdv = A + nr * nr;               // 1/D
+        const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+        bool brk = false;
+        if (!share || blockIdx.y == 0) {
         for (int e = threadIdx.x; e < nr * nr; e += blockDim.x) {
             const int a2 = e / nr, b2 = e - a2 * nr;
             if (b2 <= a2) A[e] = P[rem[a2] * PREC_MAX + rem[b2]];
@@ -1328,8 +1425,6 @@ __global__ void __launch_bounds__(512) prec_update_kernel(GraphDev g, TestParams
             badv[0] = !(d > DEGEN);
             rdv[0] = 1.0 / d;
         }
-        const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-        bool brk = false;
         for (int k = 0; k < nr; ++k) {
             __syncthreads();                     // column k and 1/D_k final
             if (badv[k & 1]) {                   // uniform: every thread reads the same flag
@@ -1339,25 +1434,45 @@ __global__ void __launch_bounds__(512) prec_update_kernel(GraphDev g, TestParams
             if (k > 0)
                 for (int i = k + threadIdx.x; i < nr; i += blockDim.x) A[i * nr + k - 1] *= rdv[k - 1];
             const double rk = rdv[k];
-            for (int i = k + 1 + w; i < nr; i += nw) {
-                const double lik = A[i * nr + k] * rk;
-                for (int c = k + 1 + lane; c <= i; c += 32) {
-                    const double v = fma(-lik, A[c * nr + k], A[i * nr + c]);
-                    A[i * nr + c] = v;
-                    if (c == k + 1 && i == k + 1) {          // thread 0: the next pivot
-                        badv[(k + 1) & 1] = !(v > DEGEN);
-                        rdv[k + 1] = 1.0 / v;
-                    }
+            // the trailing triangle k < c <= i < nr, flattened row by row over the threads
+            // (entry e = r (r + 1) / 2 + c' for row k + 1 + r, column k + 1 + c'), so that a
+            // warp's FP64 instructions carry 32 entries; entry 0, the next pivot, is thread 0's
+            const int mt = nr - k - 1;
+            for (int e = threadIdx.x; e < mt * (mt + 1) / 2; e += blockDim.x) {
+                int r = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+                if (r * (r + 1) / 2 > e) --r;
+                else if ((r + 1) * (r + 2) / 2 <= e) ++r;
+                const int i = k + 1 + r, c = k + 1 + (e - r * (r + 1) / 2);
+                const double v = fma(-(A[i * nr + k] * rk), A[c * nr + k], A[i * nr + c]);
+                A[i * nr + c] = v;
+                if (e == 0) {                                // thread 0: the next pivot
+                    badv[(k + 1) & 1] = !(v > DEGEN);
+                    rdv[k + 1] = 1.0 / v;
                 }
             }
         }
         __syncthreads();
+        }
+        if (share) {
+            __shared__ int fac_bad;
+            if (blockIdx.y == 0 && threadIdx.x == 0) fac_bad = brk;
+            cg::cluster_group cl = cg::this_cluster();
+            cl.sync();                                 // rank 0's factor and flag are ready
+            if (blockIdx.y != 0) {
+                brk = *cl.map_shared_rank(&fac_bad, 0) != 0;
+                const double *A0 = cl.map_shared_rank(smd, 0);
+                if (!brk)
+                    for (int e = threadIdx.x; e < nr * nr + nr; e += blockDim.x) smd[e] = A0[e];   // L, then 1/D
+            }
+            cl.sync();                                 // rank 0 keeps its shared memory until every copy is done
+        }
         if (brk) {
             // P_RR is a principal block of an SPD inverse; a pivot at the floor means the
             // block has lost accuracy: drop it (rebuilt from corr if the node needs it)
             if (blockIdx.y == 0 && threadIdx.x == 0) g.prec_m[u] = -2;
             return;
         }
+        if (t0 >= t1) return;                          // no kept rows in this chunk
         const bool two = nr > 32;                // lanes hold y_q for q = lane, lane + 32
         for (int t = t0 + w; t < t1; t += nw) {
             double *Pi = P + (long long)keep[t] * PREC_MAX;
@@ -1381,7 +1496,8 @@ __global__ void __launch_bounds__(512) prec_update_kernel(GraphDev g, TestParams
                 const int jj = lane + 32 * x;
                 acc[x] = jj < nt ? Pi[keep[jj]] : 0.0;
             }
-            for (int q = 0; q < nr; ++q) {
+#pragma unroll 4
+            for (int q = 0; q < nr; ++q) {                // unrolled: four rows of R in flight
                 const double yq = __shfl_sync(0xffffffffu, q < 32 ? b0 : b1, q & 31);
                 const double *Pq = P + (long long)rem[q] * PREC_MAX;
 #pragma unroll
@@ -1449,22 +1565,6 @@ __global__ void __launch_bounds__(512) prec_update_kernel(GraphDev g, TestParams
     }
 }
 
-// Retires the members the block downdate dropped (slot map entry -1).
-__global__ void prec_mark_kernel(GraphDev g, TestParams tp)
-{
-    const int u = blockIdx.x;
-    if (stopped(g.info)) return;
-    const int m0 = g.prec_m[u];
-    if (m0 <= 0) return;
-    const int *pm = g.prec_mem + (long long)u * PREC_MAX;
-    short *pos = g.prec_pos + pidx(g, u, 0);
-    const uint32_t *row = g.adj + (long long)u * g.W;
-    for (int s = threadIdx.x; s < m0; s += blockDim.x) {
-        const int w = pm[s];
-        if (w != u && pos[w] >= 0 && !((row[w >> 5] >> (w & 31)) & 1u)) pos[w] = -1;
-    }
-}
-
 // ---------------------------------------------------------------- commit
 // End of stage l (PC-stable): delete every pair with a recorded key, store its
 // first separating set (side, rank, and the expanded node list), reset the
@@ -1474,6 +1574,7 @@ __global__ void commit_kernel(GraphDev g, int l_fixed, int explicit_sets, int co
 {
     if (stopped(g.info)) return;
     const int l = l_fixed >= 0 ? l_fixed : g.info->l;
+    const bool prop = stage_prop(g, l);
     const long long nop = g.info->n_opairs;
     const int p = g.p;
     const int lane = threadIdx.x & 31;
@@ -1555,7 +1656,7 @@ __global__ void commit_kernel(GraphDev g, int l_fixed, int explicit_sets, int co
                 unrank_lex_fixed<KC_MAX>(T - 1 - s_rank, s_dd, kd, small_d ? sb : g.binom, small_d ? SB_COLS : g.ldb,
                                          posR);
 #pragma unroll
-                for (int i = 0; i < KC_MAX; ++i) nodeR[i] = i < kd ? cand_node(g, s_su, s_jj, s_dd, posR[i]) : -1;
+                for (int i = 0; i < KC_MAX; ++i) nodeR[i] = i < kd ? cand_node(g, prop, s_su, s_jj, s_dd, posR[i]) : -1;
                 int o2 = 0;
                 for (int y0 = 0; y0 <= s_dd; y0 += 32) {
                     const int y = y0 + lane;
@@ -1581,10 +1682,10 @@ __global__ void commit_kernel(GraphDev g, int l_fixed, int explicit_sets, int co
                         r -= c;
                         ++x;
                     }
-                    g.pool[s_off + i] = cand_node(g, s_su, s_jj, s_dd, x);
+                    g.pool[s_off + i] = cand_node(g, prop, s_su, s_jj, s_dd, x);
                     ++x;
                 }
-                if (g.row_off) sort_small(g.pool + s_off, l);
+                if (prop) sort_small(g.pool + s_off, l);
             }
             __syncwarp();
         }
@@ -1726,6 +1827,13 @@ cudaError_t launch_level_degrees(GraphDev g, cudaStream_t s)
 // at each barrier for small p), else 1024 threads with several nodes each.
 static int stage_threads(int p) { return p >= 1024 ? 1024 : std::max(32, (p + 31) / 32 * 32); }
 
+cudaError_t launch_degrees_tail(GraphDev g, TestParams tp, int cap, cudaGraphConditionalHandle hc, int use_cond,
+                                StageConds sc, cudaStream_t s)
+{
+    degrees_tail_kernel<<<(g.p * 32 + 255) / 256, 256, 0, s>>>(g, tp, cap, hc, use_cond, sc); note_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_tail(GraphDev g, TestParams tp, int cap, int mode, const int *stagea_singular,
                         int stagea_launched, cudaGraphConditionalHandle hc, int use_cond, StageConds sc,
                         cudaStream_t s)
@@ -1829,7 +1937,6 @@ cudaError_t launch_prec_update(GraphDev g, TestParams tp, const double *C64, int
                                          (int)smem);
     if (e != cudaSuccess) return e;
     prec_update_kernel<<<dim3(g.p, PREC_CHUNKS), 512, smem, s>>>(g, tp, C64, ldc); note_launch();
-    prec_mark_kernel<<<g.p, 128, 0, s>>>(g, tp); note_launch();
     return cudaGetLastError();
 }
 

@@ -20,6 +20,14 @@ Workloads (seed of instance s of workload c is 1000*c + s):
   3 ``p500_powerlaw`` p=500, n=10000, power law mean degree 6, max in 40, FP32
   4 ``p1000_er``      p=1000,n=20000, ER prob 10/999, FP32
   5 ``many64``        64 instances, p~U[50,400], prob~U[0.05,0.3], n~U[2000,20000]
+
+The paper's own simulation (Sec. 6.1, ``make_sweep``): a fixed order X_1..X_p,
+edges i -> j (i < j) Bernoulli(5/(p-1)) so that a node has 5 neighbours on
+average, then two hub nodes drawn uniformly whose neighbour sets are replaced by
+10 uniformly drawn other nodes (directions by the order), weights uniform on
+[-0.8,-0.2] U [0.2,0.8], eps ~ N(0,1).  The sample size is not stated there;
+n = 5000 (the p = 95 workload's) is used.  Instance m of size p has seed
+100000 + 100 p + m.
 """
 from __future__ import annotations
 
@@ -162,6 +170,34 @@ def make_many(count: int = 64, base_seed: int = 5000, p_range=(50, 400),
         X = sample(W, order, n, rng).astype(np.float32)
         out.append(SEM(X=np.ascontiguousarray(X), dag=dag, weights=W, order=order, seed=seed))
     return out
+
+
+def hub_dag(p: int, rng, mean_degree: float = 5.0, hubs: int = 2, hub_degree: int = 10,
+            lo: float = 0.2, hi: float = 0.8):
+    """The Sec. 6.1 graph: Bernoulli(mean_degree/(p-1)) edges along the order 0..p-1,
+    then ``hubs`` nodes whose neighbours are replaced by ``hub_degree`` random others."""
+    A = np.triu(rng.random((p, p)) < mean_degree / (p - 1), 1)
+    H = rng.choice(p, size=hubs, replace=False)
+    A[H, :] = False
+    A[:, H] = False
+    for h in H:
+        others = np.array([x for x in range(p) if x != h])
+        for x in rng.choice(others, size=min(hub_degree, p - 1), replace=False):
+            A[min(h, x), max(h, x)] = True
+    dag = A.astype(np.uint8)
+    W = np.zeros((p, p), dtype=np.float64)
+    ii, jj = np.nonzero(A)
+    W[ii, jj] = _weights(rng, ii.size, lo, hi)
+    return dag, W, np.arange(p)
+
+
+def make_sweep(p: int, instance: int, n: int = 5000, dtype=np.float32) -> SEM:
+    """Instance ``instance`` of size p of the paper's simulation (Sec. 6.1)."""
+    seed = 100000 + 100 * p + instance
+    rng = np.random.Generator(np.random.PCG64(seed))
+    dag, W, order = hub_dag(p, rng)
+    X = sample(W, order, n, rng).astype(dtype)
+    return SEM(np.ascontiguousarray(X), dag, W, order, seed)
 
 
 def population_corr(W: np.ndarray) -> np.ndarray:
