@@ -705,12 +705,30 @@ SWEEP = {"sizes": list(range(15, 101, 5)), "n": 5000, "alpha": 1e-3, "oracle_ins
 PAPER_TESTS_P95 = {"pc": 90394, "pc_reverse": 8678, "pc_reverse_parallel": 4563}
 
 
+def dag_scores(codes, dag):
+    """Skeleton TPR / FPR against the true DAG's skeleton, and the structural Hamming
+    distance of the oriented graph to the DAG (Sec. 6.3: one count per pair whose state
+    -- no edge, a -> b, b -> a -- differs; an undirected or bidirected edge differs from
+    any directed one)."""
+    p = dag.shape[0]
+    iu = np.triu_indices(p, 1)
+    est = codes[iu]
+    t_ab, t_ba = dag[iu] == 1, dag.T[iu] == 1
+    true_edge = t_ab | t_ba
+    found = est != 0
+    tpr = float((found & true_edge).sum() / max(1, true_edge.sum()))
+    fpr = float((found & ~true_edge).sum() / max(1, (~true_edge).sum()))
+    same = (~found & ~true_edge) | ((est == 2) & t_ab) | ((est == 3) & t_ba)
+    return tpr, fpr, int((~same).sum())
+
+
 def run_sweep(args):
-    """The paper's simulation (Sec. 6.1-6.2): for p = 15, 20, ..., 100, args.sweep_mc
+    """The paper's simulation (Sec. 6.1-6.3): for p = 15, 20, ..., 100, args.sweep_mc
     graphs each (mean degree 5, two hubs of 10 neighbours, weights +-U[0.2,0.8],
-    alpha = 1e-3), CI tests per graph and skeleton time of the conventional
-    (Algorithm 1) and reversed (Algorithm 2) orders on the GPU.  The oracle recounts
-    the first graphs of every size."""
+    alpha = 1e-3): CI tests per graph, skeleton time, and the accuracy of the oriented
+    graph (skeleton TPR / FPR, SHD to the DAG) of the conventional (Algorithm 1) and
+    reversed (Algorithm 2) orders on the GPU.  The oracle, timed as the CPU baseline,
+    recounts the first graphs of every size."""
     import torch
     from paper_2109_04626_gb300 import fastpc as fp, sem
     rank, world, local = dist_setup(args)
@@ -720,11 +738,13 @@ def run_sweep(args):
         import oracle
     n, alpha = SWEEP["n"], SWEEP["alpha"]
     rows = []
+    cpu_t, cpu_tests = 0.0, 0
     with ClockSampler(local if world > 1 else torch.cuda.current_device()) as clk:
         for p in SWEEP["sizes"]:
             pcs = {o: fp.PC(n, p, alpha, -1, order=o) for o in (0, 1)}
-            acc = {o: np.zeros(3) for o in (0, 1)}      # canonical tests, executed tests, skeleton ms
+            acc = {o: np.zeros(6) for o in (0, 1)}   # tests, executed, skeleton ms, TPR, FPR, SHD
             equal = True
+            codes = np.empty((p, p), dtype=np.int8)
             for m in range(args.sweep_mc):
                 s = sem.make_sweep(p, m, n=n)
                 Xd = torch.from_numpy(s.X).cuda()
@@ -733,31 +753,44 @@ def run_sweep(args):
                     pc.corr(Xd)
                     pc.skeleton()                        # the first search of a handle builds its graph
                     _, st = pc.skeleton()
+                    fp.pc_orient(pc.h, p, codes)
                     counts[o] = st["tests_canonical"]
-                    acc[o] += (st["tests_canonical"], st["tests_executed"], st["t_skeleton_ms"])
+                    acc[o] += (st["tests_canonical"], st["tests_executed"], st["t_skeleton_ms"],
+                               *dag_scores(codes, s.dag))
                 if check and m < SWEEP["oracle_instances"]:
+                    t0 = time.perf_counter()
                     C = oracle.pearson(s.X.astype(np.float64))
                     for o in (0, 1):
                         R = oracle.skeleton(C, n, alpha, -1, reversed_order=bool(o))
                         equal &= R["tests_total"] == counts[o]
+                        cpu_tests += R["tests_total"]
+                    cpu_t += time.perf_counter() - t0
             for pc in pcs.values():
                 pc.close()
             mc = float(args.sweep_mc)
-            conv = {"tests": acc[0][0] / mc, "executed": acc[0][1] / mc, "skeleton_ms": acc[0][2] / mc}
-            rev = {"tests": acc[1][0] / mc, "executed": acc[1][1] / mc, "skeleton_ms": acc[1][2] / mc}
+            res = {}
+            for o, name in ((0, "conventional"), (1, "reversed")):
+                a_ = acc[o] / mc
+                res[name] = {"tests": a_[0], "executed": a_[1], "skeleton_ms": a_[2], "tpr": a_[3], "fpr": a_[4],
+                             "shd": a_[5]}
+            conv, rev = res["conventional"], res["reversed"]
             rows.append({"p": p, "conventional": conv, "reversed": rev,
                          "tests_ratio": conv["tests"] / rev["tests"] if rev["tests"] else None,
                          "time_ratio": conv["skeleton_ms"] / rev["skeleton_ms"] if rev["skeleton_ms"] else None,
                          "oracle_counts_equal": bool(equal) if check else None})
     if rank == 0:
         r95 = next(r for r in rows if r["p"] == 95)
+        cpu = None
+        if check and cpu_t > 0:
+            cpu = {"value": cpu_tests / cpu_t, "unit": "CI tests/s", "cores": oracle.num_threads(), "kind": "oracle",
+                   "sample": f"Pearson + skeleton, both orders, first {SWEEP['oracle_instances']} graphs per size "
+                             f"({cpu_t:.1f} s)"}
         line = {"metric": "CI tests per graph: conventional / reversed order (the paper's simulation, Sec. 6.2)",
                 "value": r95["tests_ratio"], "unit": "ratio", "higher_is_better": True, "n_gpus": world,
                 "data": "synthetic",
                 "config": {"workload": "paper_sweep", "sizes": SWEEP["sizes"], "graphs_per_size": args.sweep_mc,
-                           "n": n, "alpha": alpha, "generator": "mean degree 5, two hubs of 10, +-U[0.2,0.8]",
-                           "oracle_recount": f"first {SWEEP['oracle_instances']} graphs per size" if check else None},
-                "sweep": rows, "paper_p95_tests": PAPER_TESTS_P95, "clocks": clk.summary()}
+                           "n": n, "alpha": alpha, "generator": "mean degree 5, two hubs of 10, +-U[0.2,0.8]"},
+                "sweep": rows, "paper_p95_tests": PAPER_TESTS_P95, "cpu_baseline": cpu, "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
     return 0
 

@@ -111,6 +111,9 @@ void pc_destroy(pc_handle *h);
  *   "learned_min_ratio" ... and at least this many tests per score row (one
  *                 row per candidate of a pair; default 8): at l = 1 a pair has
  *                 as many sets as candidates and scoring costs as much as testing
+ *   "learned_max_level" ... and its l is at most this (default 8, the stages of
+ *                 the small-stage kernel): in larger stages a pair's first sets
+ *                 are decided in one wave, before any later set could be skipped
  * Launch shape of the test kernels (set by pc_autotune; results never depend on it):
  *   "lane_chunk"  consecutive sets of one pair per thread in the kernel of the
  *                 stages l <= 8 (1..256, default 8)

@@ -117,6 +117,7 @@ struct pc_handle {
     long long rows_cap = 0;
     double learned_min = 1.0e6;
     double learned_ratio = 8.0;
+    int learned_lmax = 8;
     // per-kernel-class timing
     int timing = 0;
     std::vector<TimedPair> pending;
@@ -248,6 +249,7 @@ static TestParams make_tp(const pc_handle *h)
     tp.lazy = h->c64_full ? 0 : 1;
     tp.learned_min = h->learned_min;
     tp.learned_ratio = h->learned_ratio;
+    tp.learned_lmax = h->learned_lmax;
     tp.p = h->p;
     tp.xs64 = h->Xs64;
     tp.ldk = h->ldk;
@@ -512,6 +514,9 @@ extern "C" pc_status pc_set_opt(pc_handle *h, const char *key, double val)
     } else if (k == "learned_min_ratio") {
         if (!(val >= 0)) return fail(h, PC_ERR_ARG, "learned_min_ratio must be >= 0");
         h->learned_ratio = val;
+    } else if (k == "learned_max_level") {
+        if (!(val >= 0) || val > 1e6) return fail(h, PC_ERR_ARG, "learned_max_level must be in [0, 1e6]");
+        h->learned_lmax = (int)val;
     } else if (k == "learned_rows") {
         if (!(val >= 0)) return fail(h, PC_ERR_ARG, "learned_rows must be >= 0");
         h->rows_cap = (long long)val;
@@ -556,6 +561,7 @@ extern "C" pc_status pc_get_opt(pc_handle *h, const char *key, double *val)
     else if (k == "learned_rows") *val = (double)h->rows_cap;
     else if (k == "learned_min_tests") *val = h->learned_min;
     else if (k == "learned_min_ratio") *val = h->learned_ratio;
+    else if (k == "learned_max_level") *val = h->learned_lmax;
     else if (k == "budget") *val = h->budget;
     else if (k == "stage_conds") *val = h->stage_conds;
     else if (k == "small_stage_kernel") *val = h->lane_stages;

@@ -152,6 +152,7 @@ struct TestParams {
     int p;
     double learned_min;  // a stage is scored only if it schedules at least this many tests
     double learned_ratio;  // ... and at least this many tests per score row
+    int learned_lmax;      // ... and its l is at most this
     const double *xs64;
     long long ldk;
     unsigned char *c64_valid;

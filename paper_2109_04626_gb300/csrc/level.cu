@@ -379,7 +379,9 @@ __global__ void __launch_bounds__(1024) head_kernel(GraphDev g, TestParams tp, d
     // proposal rows: a direct-path node whose pairs have at least two sets to order
     // gets deg*(deg-1) score rows (pair j, candidate position x); the complement path
     // (dropped sets of at most KC_MAX members, reverse-lexicographic) keeps the plain order
-    auto prows = [&](int dg, ull T) -> ull { return (g.row_off && l >= 1 && T >= 2) ? (ull)dg * (ull)(dg - 1) : 0ull; };
+    auto prows = [&](int dg, ull T) -> ull {
+        return (g.row_off && l >= 1 && l <= tp.learned_lmax && T >= 2) ? (ull)dg * (ull)(dg - 1) : 0ull;
+    };
     ull v[3] = {0ull, 0ull, 0ull}, mxT = 0;               // direct, complement, proposal rows
     bool sat = false;
     for (int u = s0; u < s1; ++u) {
