@@ -58,9 +58,10 @@ def measured_peaks():
 
 
 # DRAM bytes (read + write) per launch of a class's dominant kernel, from one
-# ncu capture of the current kernel (profiles/); absent: not captured since the
-# kernel last changed (the roofline's traffic is then null)
-DRAM_BYTES_PER_LAUNCH = {}
+# ncu capture of the current kernel (profiles/prec_update_p95_dense.md: three
+# launches read 0.109, 1.824 and 0.231 MB and wrote nothing; their mean); absent:
+# not captured since the kernel last changed (the roofline's traffic is then null)
+DRAM_BYTES_PER_LAUNCH = {("p95_dense", "prec"): 7.21e5}
 
 
 def parse():
@@ -70,11 +71,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="p95_dense",
-                    choices=["p20_fp64", "p95_dense", "p500_powerlaw", "p1000_er", "many64", "paper_sweep"],
+                    choices=["p20_fp64", "p95_dense", "p500_powerlaw", "p1000_er", "many64", "paper_sweep", "power"],
                     help="many64: 64 independent SEMs (p in [50,400], edge prob in [0.05,0.3], "
                          "n in [2000,20000]), conventional order; paper_sweep: the paper's "
                          "simulation (p = 15..100, both orders, CI tests per graph)")
     ap.add_argument("--sweep-mc", type=int, default=100, help="paper_sweep: graphs per size")
+    ap.add_argument("--power-datasets", type=int, default=500, help="power: datasets of the 10-node graph")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
@@ -227,10 +229,10 @@ def run_reference(args):
     rank, world, local = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), 0
     if rank != 0:
         return 0
-    if args.workload == "paper_sweep":
-        # the sweep's metric is a ratio of test counts, which the oracle recounts inside it
-        print(json.dumps({"impl": "reference", "unavailable": "paper_sweep reports test-count ratios; "
-                          "the oracle's counts are checked inside the sweep itself"}), flush=True)
+    if args.workload in ("paper_sweep", "power"):
+        # these metrics are counts and fractions, which the oracle recomputes inside them
+        print(json.dumps({"impl": "reference", "unavailable": f"{args.workload} reports counts and fractions; "
+                          "the oracle recomputes them inside the workload itself"}), flush=True)
         return 0
     if args.workload == "many64":
         # a bounded sample: the 8 smallest of the 64 instances per step
@@ -795,6 +797,89 @@ def run_sweep(args):
     return 0
 
 
+POWER = {"n": 100000, "alpha": 1e-3, "oracle_datasets": 5,
+         "tests": [("X5-X6 | {0}", 5, 6, [0]), ("X5-X6 | {0,1,2,3,4,7,8}", 5, 6, [0, 1, 2, 3, 4, 7, 8]),
+                   ("X8-X9 | {0}", 8, 9, [0]), ("X8-X9 | {0,...,7}", 8, 9, list(range(8)))]}
+
+
+def run_power(args):
+    """The power experiment (Sec. 6.4) on the substitute 10-node graph: datasets of
+    N = 100000 samples, alpha = 1e-3.  Per dataset the GPU computes the four partial
+    correlations of the text (pc_ci_batch) and both orders' skeletons; reported: the
+    Fisher statistic |F_Z(r)| = |atanh r| of each test against its threshold
+    Phi^{-1}(1 - alpha/2) / sqrt(N - |S| - 3), the stage at which X5 - X6 is removed
+    and how often X8 - X9 is kept.  The oracle recomputes the first datasets."""
+    import torch
+    from paper_2109_04626_gb300 import fastpc as fp, sem
+    rank, world, local = dist_setup(args)
+    fp.load()
+    check = rank == 0 and world == 1 and not args.no_cpu_baseline
+    if check:
+        import oracle
+    n, alpha, D = POWER["n"], POWER["alpha"], args.power_datasets
+    q = fp.pc_fisher_threshold(alpha)
+    stat = {name: [] for name, *_ in POWER["tests"]}
+    stage56 = {0: {}, 1: {}}
+    kept89 = {0: 0, 1: 0}
+    dr, cpu_t, cpu_tests = 0.0, 0.0, 0
+    pcs = {o: fp.PC(n, 10, alpha, -1, order=o) for o in (0, 1)}
+    with ClockSampler(local if world > 1 else torch.cuda.current_device()) as clk:
+        for m in range(D):
+            s = sem.make_power(m, n=n)
+            Xd = torch.from_numpy(s.X).cuda()
+            for o, pc in pcs.items():
+                pc.corr(Xd)
+                if o == 0:
+                    for name, a, b, S in POWER["tests"]:
+                        ij = torch.tensor([[a, b]], dtype=torch.int32, device="cuda")
+                        Sd = torch.tensor([S], dtype=torch.int32, device="cuda")
+                        r, _, _ = fp.pc_ci_batch(pc.h, ij, Sd, len(S))
+                        rv = float(r.item())
+                        stat[name].append(abs(float(np.arctanh(rv))))
+                        if check and m < POWER["oracle_datasets"]:
+                            C = oracle.pearson(s.X.astype(np.float64))
+                            dr = max(dr, abs(rv - oracle.partial_corr(C, a, b, S)[0]))
+                adj, st = pc.skeleton()
+                seps = pc.sepsets()
+                lv = seps[(5, 6)][0] if (5, 6) in seps else -1
+                stage56[o][lv] = stage56[o].get(lv, 0) + 1
+                kept89[o] += int(adj[8, 9])
+            if check and m < POWER["oracle_datasets"]:
+                t0 = time.perf_counter()
+                C = oracle.pearson(s.X.astype(np.float64))
+                for o in (0, 1):
+                    cpu_tests += oracle.skeleton(C, n, alpha, -1, reversed_order=bool(o))["tests_total"]
+                cpu_t += time.perf_counter() - t0
+    for pc in pcs.values():
+        pc.close()
+    if rank == 0:
+        tests = []
+        for name, a, b, S in POWER["tests"]:
+            v = np.array(stat[name])
+            thr = q / np.sqrt(n - len(S) - 3)
+            tests.append({"test": name, "threshold": thr, "mean": float(v.mean()), "min": float(v.min()),
+                          "max": float(v.max()), "below_threshold": float((v <= thr).mean())})
+        removed = {o: sum(c for lv, c in stage56[o].items() if lv >= 0) / D for o in (0, 1)}
+        value = min(removed[0], removed[1], kept89[0] / D, kept89[1] / D)
+        cpu = None
+        if check and cpu_t > 0:
+            cpu = {"value": cpu_tests / cpu_t, "unit": "CI tests/s", "cores": oracle.num_threads(), "kind": "oracle",
+                   "sample": f"Pearson + skeleton, both orders, first {POWER['oracle_datasets']} datasets "
+                             f"({cpu_t:.1f} s)"}
+        line = {"metric": "fraction of datasets with X5 - X6 removed and X8 - X9 kept, both orders "
+                          "(the power experiment, Sec. 6.4, substitute graph)",
+                "value": value, "unit": "fraction", "higher_is_better": True, "n_gpus": world, "data": "synthetic",
+                "config": {"workload": "power", "datasets": D, "n": n, "alpha": alpha,
+                           "graph": "substitute: X0 -> X5, X6; X0 -> X1 -> X2 -> X3 -> X4 -> X7 -> X8 -> X9; X0 -> X8"},
+                "tests": tests,
+                "x5_x6_removed_at_stage": {"conventional": {str(k): v for k, v in sorted(stage56[0].items())},
+                                           "reversed": {str(k): v for k, v in sorted(stage56[1].items())}},
+                "x8_x9_kept": {"conventional": kept89[0] / D, "reversed": kept89[1] / D},
+                "max_abs_r_vs_oracle": dr if check else None, "cpu_baseline": cpu, "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -803,6 +888,8 @@ def main():
         return run_many(args)
     if args.workload == "paper_sweep":
         return run_sweep(args)
+    if args.workload == "power":
+        return run_power(args)
     return run_ours(args)
 
 

@@ -28,6 +28,12 @@ average, then two hub nodes drawn uniformly whose neighbour sets are replaced by
 [-0.8,-0.2] U [0.2,0.8], eps ~ N(0,1).  The sample size is not stated there;
 n = 5000 (the p = 95 workload's) is used.  Instance m of size p has seed
 100000 + 100 p + m.
+
+The power experiment (Sec. 6.4) uses a 10-node graph shown only in a figure that
+the text does not carry; ``power_dag`` is a substitute with the relations the text
+states: X5 and X6 separated by {X0} and by {X0,X1,X2,X3,X4,X7,X8}, X8 and X9
+adjacent (dependent given {X0} and given {X0,...,X7}).  Dataset m has seed
+200000 + m.
 """
 from __future__ import annotations
 
@@ -197,6 +203,31 @@ def make_sweep(p: int, instance: int, n: int = 5000, dtype=np.float32) -> SEM:
     rng = np.random.Generator(np.random.PCG64(seed))
     dag, W, order = hub_dag(p, rng)
     X = sample(W, order, n, rng).astype(dtype)
+    return SEM(np.ascontiguousarray(X), dag, W, order, seed)
+
+
+POWER_EDGES = [(0, 5), (0, 6), (0, 1), (1, 2), (2, 3), (3, 4), (4, 7), (7, 8), (8, 9), (0, 8)]
+
+
+def power_dag(seed: int = 199999):
+    """The substitute 10-node DAG of the power experiment: X0 a common cause of the
+    leaves X5 and X6, a chain X0 -> X1 -> ... -> X4 -> X7 -> X8 -> X9, and X0 -> X8;
+    weights uniform on [-0.8,-0.2] U [0.2,0.8] (Sec. 6.1) drawn once."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    dag = np.zeros((10, 10), dtype=np.uint8)
+    W = np.zeros((10, 10), dtype=np.float64)
+    for a, b in POWER_EDGES:
+        dag[a, b] = 1
+    ii, jj = np.nonzero(dag)
+    W[ii, jj] = _weights(rng, ii.size, 0.2, 0.8)
+    return dag, W, np.arange(10)
+
+
+def make_power(m: int, n: int = 100000, dtype=np.float32) -> SEM:
+    """Dataset m of the power experiment (Sec. 6.4): n samples of the substitute graph."""
+    dag, W, order = power_dag()
+    seed = 200000 + m
+    X = sample(W, order, n, np.random.Generator(np.random.PCG64(seed))).astype(dtype)
     return SEM(np.ascontiguousarray(X), dag, W, order, seed)
 
 

@@ -23,3 +23,18 @@ def test_sweep_graphs_follow_the_recipe():
     a = sem.make_sweep(40, 3)
     b = sem.make_sweep(40, 3)
     assert np.array_equal(a.X, b.X) and a.seed == b.seed       # seeded
+
+
+def test_power_graph_has_the_stated_relations():
+    # Sec. 6.4: X5 _|_ X6 | {X0} and | {X0,X1,X2,X3,X4,X7,X8}; X8, X9 dependent given
+    # {X0} and given {X0..X7} -- checked by d-separation on the substitute DAG
+    from tests.dsep import d_separated
+    dag, W, order = sem.power_dag()
+    assert d_separated(dag, 5, 6, [0])
+    assert d_separated(dag, 5, 6, [0, 1, 2, 3, 4, 7, 8])
+    assert not d_separated(dag, 5, 6, [])
+    assert not d_separated(dag, 8, 9, [0])
+    assert not d_separated(dag, 8, 9, list(range(8)))
+    assert np.all((np.abs(W[dag == 1]) >= 0.2) & (np.abs(W[dag == 1]) <= 0.8))
+    s = sem.make_power(0, n=1000)
+    assert s.X.shape == (1000, 10)
