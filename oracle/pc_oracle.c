@@ -100,7 +100,9 @@ double oracle_norm_ppf(double p)
 /* ------------------------------------------------------------------------ */
 /* Pearson correlation matrix corr = {rho_ij} (Sec. 4, definition of corr),
  * by two-pass summation: column means first, then centred cross products.
- * X is row-major n x p.  C is row-major p x p with the diagonal set to 1.  */
+ * X is row-major n x p.  C is row-major p x p with the diagonal set to 1.
+ * Reading R18: a constant column (zero sum of squares) has correlation 0 with
+ * every other column (its standardised values are all zero).               */
 void oracle_pearson(const double *X, int64_t n, int32_t p, double *C)
 {
     double *D = (double *)malloc(sizeof(double) * (size_t)n * (size_t)p);
@@ -124,7 +126,7 @@ void oracle_pearson(const double *X, int64_t n, int32_t p, double *C)
             double s = 0.0;
             const double *da = D + (size_t)a * n, *db = D + (size_t)b * n;
             for (int64_t t = 0; t < n; ++t) s += da[t] * db[t];
-            double r = s / sqrt(ss[a] * ss[b]);
+            double r = (ss[a] > 0.0 && ss[b] > 0.0) ? s / sqrt(ss[a] * ss[b]) : 0.0;
             C[(size_t)a * p + b] = r;
             C[(size_t)b * p + a] = r;
         }

@@ -233,6 +233,22 @@ def test_skeleton_edge_cases(fp):
         _check_skeleton(fp, X, order=order)
 
 
+@pytest.mark.parametrize("order", [1, 0])
+def test_skeleton_constant_column(fp, order):
+    # Reading R18: a constant column correlates 0 with everything (GPU: 1/sd := 0)
+    X = _sem_case(73, 30, 1500, 0.2)
+    X[:, 11] = 3.25
+    _check_skeleton(fp, X, order=order)
+
+
+def test_skeleton_maximum_p(fp):
+    # the largest p a handle accepts (4096), conventional order up to l = 1
+    rng = np.random.Generator(np.random.PCG64(4096))
+    dag, W, order = sem.er_dag(4096, 3.0 / 4095, rng)
+    X = np.ascontiguousarray(sem.sample(W, order, 1000, rng).astype(np.float32))
+    _check_skeleton(fp, X, max_level=1, order=0)
+
+
 def test_skeleton_degenerate_duplicate_column(fp):
     X = _sem_case(71, 15, 1200, 0.3, np.float64)
     X[:, 9] = X[:, 4]                                  # exactly collinear pair

@@ -51,6 +51,21 @@ def test_pearson_matches_numpy():
     assert np.all(np.diag(C) == 1.0)
 
 
+def test_pearson_constant_column_reading():
+    # Reading R18: a constant column correlates 0 with every other column; the rest of
+    # the matrix is numpy's Pearson; every pair of the constant column is removed at l = 0
+    rng = np.random.default_rng(8)
+    X = rng.standard_normal((500, 7))
+    X[:, 3] = 2.5
+    C = oracle.pearson(X)
+    keep = [0, 1, 2, 4, 5, 6]
+    np.testing.assert_allclose(C[np.ix_(keep, keep)], np.corrcoef(X[:, keep].T), atol=1e-13)
+    assert np.all(C[3, keep] == 0.0) and np.all(C[keep, 3] == 0.0) and C[3, 3] == 1.0
+    R = oracle.skeleton(C, 500, 0.01, -1, reversed_order=False)
+    assert not R["adj"][3].any()
+    assert all(R["sepsets"][(min(3, b), max(3, b))][0] == 0 for b in keep)
+
+
 # --------------------------------------------------------------------------- partial corr
 def _rand_corr(rng, p, cond_boost=0.0):
     A = rng.standard_normal((p + 5, p))
