@@ -53,35 +53,6 @@ __device__ __forceinline__ void sweep_inverse_block(double *A, int m, int lda, d
     }
 }
 
-// The same sweep by one warp (for small m): A <- -A^{-1}, identical arithmetic per
-// entry, __syncwarp between pivots.  Call from all 32 lanes of one warp.
-__device__ __forceinline__ void sweep_inverse_warp(double *A, int m, int lda, double *colk, int *bad)
-{
-    const int lane = threadIdx.x & 31;
-    for (int k = 0; k < m; ++k) {
-        const double D = A[k * lda + k];
-        if (!(D > DEGEN)) {
-            if (lane == 0) *bad = 1;
-            return;                                   // uniform across the warp
-        }
-        for (int i = lane; i < m; i += 32) colk[i] = A[i * lda + k];
-        __syncwarp();
-        const double iD = 1.0 / D;
-        for (int e = lane; e < m * m; e += 32) {
-            const int i = e / m, j = e - i * m;
-            if (j < i) continue;
-            const double ci = colk[i] * iD;
-            double v;
-            if (i == k) v = (j == k) ? -iD : colk[j] * iD;
-            else if (j == k) v = ci;
-            else v = fma(-ci, colk[j], A[i * lda + j]);
-            A[i * lda + j] = v;
-            A[j * lda + i] = v;
-        }
-        __syncwarp();
-    }
-}
-
 // Lexicographic unranking: positions pos[0..l) (ascending, in 0..d-1) of the
 // rank-th l-subset of d items.  The number of subsets whose i-th position is
 // x (positions before it fixed) is C(d-x-1, l-i-1), and by the hockey-stick
