@@ -97,6 +97,8 @@ struct pc_handle {
     long long body_kernels = 0;      // kernel nodes in the captured stage body (all branches)
     double *syrk_ws = nullptr, *stats_ws = nullptr;
     unsigned char *c64_valid = nullptr;
+    int2 *c64_list = nullptr;                  // FP64 entries claimed for the parallel fill
+    unsigned long long *c64_list_len = nullptr;
     unsigned long long *rq = nullptr, *rq_len = nullptr;   // FP64 re-decision queue of the lane kernel
     unsigned long long rq_cap = 0;
     bool c64_full = false;             // C64 fully computed (else lazily, per entry)
@@ -226,6 +228,8 @@ static double upper_quantile(double a)
     return x;
 }
 
+static constexpr unsigned long long C64_LIST_CAP = 1ull << 20;   // pairs (8 MB)
+
 static TestParams make_tp(const pc_handle *h)
 {
     TestParams tp;
@@ -254,6 +258,9 @@ static TestParams make_tp(const pc_handle *h)
     tp.xs64 = h->Xs64;
     tp.ldk = h->ldk;
     tp.c64_valid = h->c64_valid;
+    tp.c64_list = h->c64_list;
+    tp.c64_list_len = h->c64_list_len;
+    tp.c64_list_cap = h->c64_list ? C64_LIST_CAP : 0;
     return tp;
 }
 
@@ -670,6 +677,16 @@ static pc_status check_tc(pc_handle *h)
     return PC_OK;
 }
 
+// The pair list of the FP64 entries formed in parallel before a small stage's FP64
+// pass (entries beyond it are formed on demand by the pass itself).
+static pc_status alloc_c64_list(pc_handle *h)
+{
+    if (h->c64_list) return PC_OK;
+    CK(dalloc(h, &h->c64_list, C64_LIST_CAP * sizeof(int2)));
+    CK(dalloc(h, &h->c64_list_len, sizeof(unsigned long long)));
+    return PC_OK;
+}
+
 // Standardisation and correlation GEMM of one problem, or of instance blk of a
 // batched handle (its columns are rows [o, o+p) of the planes, its block of
 // corr the diagonal block there).
@@ -730,8 +747,10 @@ static pc_status corr_impl(pc_handle *h, const void *X, int32_t dtype, int64_t l
             if (pc_status r = syrk64_block(h, o, n, p, blk)) return r;
         } else {
             if (!h->c64_valid) {
-                CK(dalloc(h, &h->c64_valid, h->pair_elems));
-                CK(cudaMemsetAsync(h->c64_valid, 0, h->pair_elems, s));
+                // whole 32-bit words: the claims of c64_collect CAS the word of a flag
+                CK(dalloc(h, &h->c64_valid, (h->pair_elems + 7) / 4 * 4));
+                CK(cudaMemsetAsync(h->c64_valid, 0, (h->pair_elems + 7) / 4 * 4, s));
+                if (pc_status r = alloc_c64_list(h)) return r;
             }
             CK(fpc::launch_c64_lazy_init_block(h->C64 + h->pbase[blk], p, h->c64_valid + h->pbase[blk], p, 0, p,
                                                s));
@@ -739,7 +758,11 @@ static pc_status corr_impl(pc_handle *h, const void *X, int32_t dtype, int64_t l
     } else if (h->precision == 0 || h->order == 1) {
         if (pc_status r = materialize_c64(h)) return r;
     } else {
-        if (!h->c64_valid) CK(dalloc(h, &h->c64_valid, (size_t)p * p));
+        if (!h->c64_valid) {
+            CK(dalloc(h, &h->c64_valid, ((size_t)p * p + 7) / 4 * 4));
+            CK(cudaMemsetAsync(h->c64_valid, 0, ((size_t)p * p + 7) / 4 * 4, s));
+            if (pc_status r = alloc_c64_list(h)) return r;
+        }
         CK(fpc::launch_c64_lazy_init(h->C64, h->ldc, h->c64_valid, p, s));
     }
     // this problem's correlation block and its leading dimension

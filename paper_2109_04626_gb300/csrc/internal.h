@@ -155,7 +155,10 @@ struct TestParams {
     int learned_lmax;      // ... and its l is at most this
     const double *xs64;
     long long ldk;
-    unsigned char *c64_valid;
+    unsigned char *c64_valid;   // 0 missing, 1 valid, 2 claimed by c64_collect (allocated in whole words)
+    int2 *c64_list;             // pairs (a < b) claimed for c64_fill
+    unsigned long long *c64_list_len;
+    unsigned long long c64_list_cap;
 };
 
 // counts kernel launches (defined in fastpc_api.cu); inside a stream capture the

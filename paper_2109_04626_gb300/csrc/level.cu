@@ -301,15 +301,15 @@ __device__ __forceinline__ ull sat_mul(ull a, ull b)
 // The stage body's conditional nodes (captured loop): which small-stage kernel
 // range runs, and whether the warp-per-test, complement and scoring kernels do.
 __device__ __forceinline__ void set_stage_conds(const StageConds &sc, LevelInfo *I, int lane, int direct, int comp,
-                                                int score)
+                                                int score, int lane_kernels)
 {
     cudaGraphSetConditional(sc.lane, (unsigned)lane);
     cudaGraphSetConditional(sc.direct, (unsigned)direct);
     if (sc.has_comp) cudaGraphSetConditional(sc.comp, (unsigned)comp);
     if (sc.has_score) cudaGraphSetConditional(sc.score, (unsigned)score);
-    // head, commit, degrees + tail, the lane branch (kernel, FP64 pass, overflow pass) and
-    // the rest (the tail counts the precision update)
-    I->kernels_run += STAGE_FIXED_KERNELS + (lane < LANE_RANGES ? 3 : 0) + direct + comp + 2 * score;
+    // head, commit, degrees + tail, the lane branch (kernel, [FP64 entries: collect, fill,]
+    // FP64 pass, overflow pass) and the rest (the tail counts the precision update)
+    I->kernels_run += STAGE_FIXED_KERNELS + (lane < LANE_RANGES ? lane_kernels : 0) + direct + comp + 2 * score;
 }
 
 // Exclusive saturating scan of NV values per thread over a block of up to 1024
@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(1024) head_kernel(GraphDev g, TestParams tp, d
 {
     LevelInfo *I = g.info;
     if (stopped(I)) {
-        if (conds.use && threadIdx.x == 0) set_stage_conds(conds, I, LANE_RANGES, 0, 0, 0);
+        if (conds.use && threadIdx.x == 0) set_stage_conds(conds, I, LANE_RANGES, 0, 0, 0, 0);
         return;
     }
     __shared__ ull sh[4 * 32];
@@ -484,7 +484,7 @@ __global__ void __launch_bounds__(1024) head_kernel(GraphDev g, TestParams tp, d
             const bool run = !I->halt;
             set_stage_conds(conds, I, run && small && td > 0 ? lane_range_of_dev(l) : LANE_RANGES,
                             run && td > 0 && !small, run && tc > 0,
-                            run && g.row_off && rows_fit && rows_total > 0);
+                            run && g.row_off && rows_fit && rows_total > 0, tp.lazy && tp.c64_list ? 5 : 3);
         }
     }
 }
@@ -580,7 +580,7 @@ __device__ __noinline__ void ensure_c64(const int *nd, int m, const TestParams &
             const int c = e - i * (i + 1) / 2;
             a = nd[i];
             b = nd[c];
-            miss = a != b && !valid[cidx(tp.prow, tp.p, a, b)];
+            miss = a != b && valid[cidx(tp.prow, tp.p, a, b)] != 1;
         }
         unsigned bal = __ballot_sync(0xffffffffu, miss);
         while (bal) {
@@ -1152,6 +1152,118 @@ __global__ void __launch_bounds__(256) ci_redecide_kernel(GraphDev g, TestParams
         if (acc.red) atomicAdd(&g.ctr->redecided, acc.red);
         if (acc.degen) atomicAdd(&g.ctr->degenerate, acc.degen);
         if (acc.fl64) atomicAdd(&g.ctr->flops64_direct, acc.fl64);
+    }
+}
+
+// ---------------------------------------------------------------- FP64 entries of the queued tests
+// The FP64 pass of a small stage needs, per queued test, the FP64 correlations of
+// its l + 2 nodes.  Formed one by one by the warp that runs the test, each missing
+// entry is a length-n dot product of FP64 standardised columns streamed from HBM,
+// and a test's entries follow one another.  Instead, every missing entry is first
+// claimed once (byte 0 -> 2 of its validity flag, by a CAS on the containing word)
+// and listed; a whole CTA per listed entry then forms it; the FP64 pass finds them
+// all present.
+__device__ __forceinline__ bool claim_byte(unsigned char *flags, long long e)
+{
+    unsigned int *w = reinterpret_cast<unsigned int *>(reinterpret_cast<uintptr_t>(flags + e) & ~(uintptr_t)3);
+    const int sh = (int)(reinterpret_cast<uintptr_t>(flags + e) & 3) * 8;
+    unsigned int old = *(volatile unsigned int *)w;
+    for (int it = 0; it < 64; ++it) {                    // bounded: a contended entry is formed on demand
+        if ((old >> sh) & 0xffu) return false;          // valid, or claimed by another test
+        const unsigned int prev = atomicCAS(w, old, old | (2u << sh));
+        if (prev == old) return true;
+        old = prev;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void release_byte(unsigned char *flags, long long e)
+{
+    unsigned int *w = reinterpret_cast<unsigned int *>(reinterpret_cast<uintptr_t>(flags + e) & ~(uintptr_t)3);
+    const int sh = (int)(reinterpret_cast<uintptr_t>(flags + e) & 3) * 8;
+    atomicAnd(w, ~(0xffu << sh));
+}
+
+// One warp per queued test: its node set (as the FP64 pass builds it), then each
+// missing pair (a < b) of it is claimed and listed.
+__global__ void __launch_bounds__(256) c64_collect_kernel(GraphDev g, TestParams tp, const ull *queue,
+                                                          const ull *qlen, ull qcap)
+{
+    __shared__ int nds[8][LANE_LMAX + 2], poss[8][LANE_LMAX + 2];
+    if (stopped(g.info)) return;
+    const int l = g.info->l;
+    if (tp.precision == 0 || l > LANE_LMAX || !tp.lazy || !tp.c64_list) return;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    int *nd = nds[wib], *pos = poss[wib];
+    const ull nq = *qlen < qcap ? *qlen : qcap;
+    const bool prop = stage_prop(g, l);
+    const int m = l + 2;
+    for (ull qi = (blockIdx.x * (ull)blockDim.x + threadIdx.x) >> 5; qi < nq;
+         qi += ((ull)gridDim.x * blockDim.x) >> 5) {
+        const ull t = queue[qi];
+        int u, j, d;
+        ull rank;
+        locate_test(g, g.tn_off, l, t, u, j, d, rank);
+        const int v = g.nbr[nidx(g, u) + j];
+        const ull key = ((ull)(u > v) << 62) | rank;
+        if (*(volatile ull *)(g.best + pidx(g, min(u, v), max(u, v))) < key) continue;   // no FP64 test follows
+        if (lane == 0) {
+            unrank_lex(rank, d, l, g.binom, g.ldb, pos);
+            for (int i = 0; i < l; ++i) nd[i] = cand_node(g, prop, u, j, d, pos[i]);
+            nd[l] = u;
+            nd[l + 1] = v;
+        }
+        __syncwarp();
+        for (int i = 1; i < m; ++i)
+            for (int c = lane; c < i; c += 32) {
+                const int a = min(nd[i], nd[c]), b = max(nd[i], nd[c]);
+                if (a == b) continue;
+                const long long e = cidx(tp.prow, tp.p, a, b);
+                if (tp.c64_valid[e] || !claim_byte(tp.c64_valid, e)) continue;
+                const ull k = atomicAdd(tp.c64_list_len, 1ull);
+                if (k < tp.c64_list_cap) tp.c64_list[k] = make_int2(a, b);
+                else release_byte(tp.c64_valid, e);      // the list is full: formed on demand later
+            }
+        __syncwarp();
+    }
+}
+
+// One CTA per listed pair: the dot product of the FP64 standardised columns over
+// all 256 threads (a fixed summation order), then the entry, its mirror and both flags.
+__global__ void __launch_bounds__(256) c64_fill_kernel(GraphDev g, TestParams tp, double *C64, int ldc)
+{
+    __shared__ double red[8];
+    if (stopped(g.info) || !tp.lazy || !tp.c64_list) return;
+    const ull nl = *tp.c64_list_len < tp.c64_list_cap ? *tp.c64_list_len : tp.c64_list_cap;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (ull k = blockIdx.x; k < nl; k += gridDim.x) {
+        const int2 ab = tp.c64_list[k];
+        const double *xa = tp.xs64 + (long long)ab.x * tp.ldk, *xb = tp.xs64 + (long long)ab.y * tp.ldk;
+        const long long na = n_of(tp, ab.x), nh = na >> 1;
+        const double2 *xa2 = reinterpret_cast<const double2 *>(xa), *xb2 = reinterpret_cast<const double2 *>(xb);
+        double acc0 = 0.0, acc1 = 0.0;
+#pragma unroll 4
+        for (long long t = threadIdx.x; t < nh; t += blockDim.x) {
+            const double2 a2 = __ldg(xa2 + t), b2 = __ldg(xb2 + t);
+            acc0 = fma(a2.x, b2.x, acc0);
+            acc1 = fma(a2.y, b2.y, acc1);
+        }
+        if ((na & 1) && threadIdx.x == 0) acc0 = fma(xa[na - 1], xb[na - 1], acc0);
+        double acc = acc0 + acc1;
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if (lane == 0) red[w] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double sum = 0.0;
+            for (int i = 0; i < (int)(blockDim.x >> 5); ++i) sum += red[i];
+            const double val = sum / (double)na;
+            C64[cidx(tp.prow, ldc, ab.x, ab.y)] = val;
+            C64[cidx(tp.prow, ldc, ab.y, ab.x)] = val;
+            __threadfence();
+            tp.c64_valid[cidx(tp.prow, tp.p, ab.x, ab.y)] = 1;
+            tp.c64_valid[cidx(tp.prow, tp.p, ab.y, ab.x)] = 1;
+        }
+        __syncthreads();
     }
 }
 
@@ -1919,6 +2031,13 @@ cudaError_t launch_ci_lane(GraphDev g, TestParams tp, const float *C32, const do
     size_t smem = (size_t)wpc * per_warp;
     e = cudaFuncSetAttribute(ci_redecide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    if (tp.lazy && tp.c64_list) {
+        // the FP64 entries the queued tests need, formed in parallel before the FP64 pass
+        e = cudaMemsetAsync(tp.c64_list_len, 0, sizeof(ull), s);
+        if (e != cudaSuccess) return e;
+        c64_collect_kernel<<<num_sms() * 4, 256, 0, s>>>(g, tp, queue, qlen, qcap); note_launch();
+        c64_fill_kernel<<<num_sms() * 4, 256, 0, s>>>(g, tp, const_cast<double *>(C64), ldc); note_launch();
+    }
     ci_redecide_kernel<<<num_sms() * 4, wpc * 32, smem, s>>>(g, tp, C64, ldc, queue, qlen, qcap, ms, per_warp); note_launch();
     return cudaGetLastError();
 }
