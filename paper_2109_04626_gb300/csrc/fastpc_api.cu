@@ -99,6 +99,8 @@ struct pc_handle {
     unsigned char *c64_valid = nullptr;
     int2 *c64_list = nullptr;                  // FP64 entries claimed for the parallel fill
     unsigned long long *c64_list_len = nullptr;
+    unsigned char *pair_seen = nullptr;        // per tested pair: first queued test claimed
+    size_t pair_seen_bytes = 0;
     unsigned long long *rq = nullptr, *rq_len = nullptr;   // FP64 re-decision queue of the lane kernel
     unsigned long long rq_cap = 0;
     bool c64_full = false;             // C64 fully computed (else lazily, per entry)
@@ -261,6 +263,8 @@ static TestParams make_tp(const pc_handle *h)
     tp.c64_list = h->c64_list;
     tp.c64_list_len = h->c64_list_len;
     tp.c64_list_cap = h->c64_list ? C64_LIST_CAP : 0;
+    tp.pair_seen = h->pair_seen;
+    tp.pair_seen_bytes = h->pair_seen_bytes;
     return tp;
 }
 
@@ -684,6 +688,8 @@ static pc_status alloc_c64_list(pc_handle *h)
     if (h->c64_list) return PC_OK;
     CK(dalloc(h, &h->c64_list, C64_LIST_CAP * sizeof(int2)));
     CK(dalloc(h, &h->c64_list_len, sizeof(unsigned long long)));
+    h->pair_seen_bytes = (h->pair_elems + 7) / 4 * 4;    // whole words: claimed by CAS
+    CK(dalloc(h, &h->pair_seen, h->pair_seen_bytes));
     return PC_OK;
 }
 

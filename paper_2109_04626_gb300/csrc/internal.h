@@ -159,6 +159,8 @@ struct TestParams {
     int2 *c64_list;             // pairs (a < b) claimed for c64_fill
     unsigned long long *c64_list_len;
     unsigned long long c64_list_cap;
+    unsigned char *pair_seen;   // per tested pair: its first queued test of the stage claimed (whole words)
+    unsigned long long pair_seen_bytes;
 };
 
 // counts kernel launches (defined in fastpc_api.cu); inside a stream capture the

@@ -484,7 +484,8 @@ __global__ void __launch_bounds__(1024) head_kernel(GraphDev g, TestParams tp, d
             const bool run = !I->halt;
             set_stage_conds(conds, I, run && small && td > 0 ? lane_range_of_dev(l) : LANE_RANGES,
                             run && td > 0 && !small, run && tc > 0,
-                            run && g.row_off && rows_fit && rows_total > 0, tp.lazy && tp.c64_list ? 5 : 3);
+                            run && g.row_off && rows_fit && rows_total > 0,
+                            tp.lazy && tp.c64_list && tp.pair_seen ? 5 : 3);
         }
     }
 }
@@ -1185,14 +1186,17 @@ __device__ __forceinline__ void release_byte(unsigned char *flags, long long e)
 }
 
 // One warp per queued test: its node set (as the FP64 pass builds it), then each
-// missing pair (a < b) of it is claimed and listed.
+// missing pair (a < b) of it is claimed and listed -- for the first queued test of
+// each tested pair only: a later one runs only if that test does not separate the
+// pair, and then forms its entries on demand (dense problems queue many tests per
+// pair, most of which an earlier set decides).
 __global__ void __launch_bounds__(256) c64_collect_kernel(GraphDev g, TestParams tp, const ull *queue,
                                                           const ull *qlen, ull qcap)
 {
     __shared__ int nds[8][LANE_LMAX + 2], poss[8][LANE_LMAX + 2];
     if (stopped(g.info)) return;
     const int l = g.info->l;
-    if (tp.precision == 0 || l > LANE_LMAX || !tp.lazy || !tp.c64_list) return;
+    if (tp.precision == 0 || l > LANE_LMAX || !tp.lazy || !tp.c64_list || !tp.pair_seen) return;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     int *nd = nds[wib], *pos = poss[wib];
     const ull nq = *qlen < qcap ? *qlen : qcap;
@@ -1206,7 +1210,11 @@ __global__ void __launch_bounds__(256) c64_collect_kernel(GraphDev g, TestParams
         locate_test(g, g.tn_off, l, t, u, j, d, rank);
         const int v = g.nbr[nidx(g, u) + j];
         const ull key = ((ull)(u > v) << 62) | rank;
-        if (*(volatile ull *)(g.best + pidx(g, min(u, v), max(u, v))) < key) continue;   // no FP64 test follows
+        const long long ep = pidx(g, min(u, v), max(u, v));
+        if (*(volatile ull *)(g.best + ep) < key) continue;   // no FP64 test follows
+        int first = 0;
+        if (lane == 0) first = claim_byte(tp.pair_seen, ep);
+        if (!__shfl_sync(0xffffffffu, first, 0)) continue;    // not the pair's first queued test
         if (lane == 0) {
             unrank_lex(rank, d, l, g.binom, g.ldb, pos);
             for (int i = 0; i < l; ++i) nd[i] = cand_node(g, prop, u, j, d, pos[i]);
@@ -1233,7 +1241,7 @@ __global__ void __launch_bounds__(256) c64_collect_kernel(GraphDev g, TestParams
 __global__ void __launch_bounds__(256) c64_fill_kernel(GraphDev g, TestParams tp, double *C64, int ldc)
 {
     __shared__ double red[8];
-    if (stopped(g.info) || !tp.lazy || !tp.c64_list) return;
+    if (stopped(g.info) || !tp.lazy || !tp.c64_list || !tp.pair_seen) return;
     const ull nl = *tp.c64_list_len < tp.c64_list_cap ? *tp.c64_list_len : tp.c64_list_cap;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (ull k = blockIdx.x; k < nl; k += gridDim.x) {
@@ -2031,9 +2039,10 @@ cudaError_t launch_ci_lane(GraphDev g, TestParams tp, const float *C32, const do
     size_t smem = (size_t)wpc * per_warp;
     e = cudaFuncSetAttribute(ci_redecide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    if (tp.lazy && tp.c64_list) {
+    if (tp.lazy && tp.c64_list && tp.pair_seen) {
         // the FP64 entries the queued tests need, formed in parallel before the FP64 pass
         e = cudaMemsetAsync(tp.c64_list_len, 0, sizeof(ull), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(tp.pair_seen, 0, tp.pair_seen_bytes, s);
         if (e != cudaSuccess) return e;
         c64_collect_kernel<<<num_sms() * 4, 256, 0, s>>>(g, tp, queue, qlen, qcap); note_launch();
         c64_fill_kernel<<<num_sms() * 4, 256, 0, s>>>(g, tp, const_cast<double *>(C64), ldc); note_launch();
