@@ -81,6 +81,8 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--train-seeds", type=int, default=24)
+    ap.add_argument("--learned-max-level", type=int, default=None,
+                    help="largest stage the proposal network scores (library default if unset)")
     ap.add_argument("--corr-only", action="store_true",
                     help="time only pc_corr (standardise + tensor-core correlation GEMM) on the workload")
     ap.add_argument("--no-autotune", action="store_true",
@@ -381,9 +383,12 @@ def run_ours(args):
                                          w["max_level"], mixed_prec)
         loss = proposal.train(pc.h, feats, labels, epochs=6, batch=8192, lr=2e-3, seed=1)
         fp.pc_set_opt(pc.h, "learned", 1)
+        if args.learned_max_level is not None:
+            fp.pc_set_opt(pc.h, "learned_max_level", args.learned_max_level)
         learned = {"train_rows": int(labels.shape[0]), "train_seeds": args.train_seeds,
                    "train_sems": f"p={tp_}, n={tn_}",
-                   "final_loss": loss, "train_s": time.perf_counter() - t0}
+                   "final_loss": loss, "train_s": time.perf_counter() - t0,
+                   "max_level": int(fp.pc_get_opt(pc.h, "learned_max_level"))}
 
     for _ in range(args.warmup):
         st = step(pc)

@@ -97,7 +97,7 @@ void pc_destroy(pc_handle *h);
  *                 WHILE node is driven by the device (default); 0 = host loop
  *   "stage_conds" 1 = inside that graph, conditional nodes skip the kernels a
  *                 stage has no work for (default); 0 = every kernel every stage
- *   "small_stage_kernel" 1 = stages l <= 8 of the FP32 modes run on the
+ *   "small_stage_kernel" 1 = stages l <= 12 of the FP32 modes run on the
  *                 rank-major one-thread-per-chunk kernel with bordered tests
  *                 (default); 0 = every stage on the one-warp-per-test kernel
  *   "learned"     1 = enumerate the conditioning sets of every ordered pair in
@@ -111,12 +111,12 @@ void pc_destroy(pc_handle *h);
  *   "learned_min_ratio" ... and at least this many tests per score row (one
  *                 row per candidate of a pair; default 8): at l = 1 a pair has
  *                 as many sets as candidates and scoring costs as much as testing
- *   "learned_max_level" ... and its l is at most this (default 8, the stages of
- *                 the small-stage kernel): in larger stages a pair's first sets
- *                 are decided in one wave, before any later set could be skipped
+ *   "learned_max_level" ... and its l is at most this (default 8): a pair of a
+ *                 larger stage has few candidates left, and scoring them saved
+ *                 no time in the p = 1000 measurements
  * Launch shape of the test kernels (set by pc_autotune; results never depend on it):
  *   "lane_chunk"  consecutive sets of one pair per thread in the kernel of the
- *                 stages l <= 8 (1..256, default 8)
+ *                 stages l <= 12 (1..256, default 8)
  *   "lane_rounds" chunks of every pair run rank-major (chunk r of all pairs
  *                 before chunk r+1) before the rest runs pair by pair (0..4096,
  *                 default 32)

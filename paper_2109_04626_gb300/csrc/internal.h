@@ -72,8 +72,8 @@ struct StageConds {
     int use;                            // 1 inside the captured stage body
     int has_comp, has_score, has_prec;  // which nodes the body has
 };
-constexpr int LANE_LMAX = 8;            // stages the lane-per-test kernel runs (FP32 modes)
-constexpr int LANE_RANGES = 4;          // small-stage kernel instantiations: l 0-2, 3-4, 5-6, 7-8
+constexpr int LANE_LMAX = 12;           // stages the lane-per-test kernel runs (FP32 modes)
+constexpr int LANE_RANGES = 6;          // small-stage kernel instantiations: l 0-2, 3-4, 5-6, 7-8, 9-10, 11-12
 // kernels of a stage outside conditional nodes: head, commit, degrees + tail (one kernel)
 constexpr int STAGE_FIXED_KERNELS = 3;
 

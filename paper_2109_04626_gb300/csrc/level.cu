@@ -37,7 +37,7 @@ __device__ __forceinline__ ull sat_add(ull a, ull b)
 // small-stage kernel instantiation that runs stage l (l <= LANE_LMAX)
 __host__ __device__ __forceinline__ int lane_range_of_dev(int l)
 {
-    return l <= 2 ? 0 : (l <= 4 ? 1 : (l <= 6 ? 2 : 3));
+    return l <= 2 ? 0 : (l <= 4 ? 1 : (l <= 6 ? 2 : (l <= 8 ? 3 : (l <= 10 ? 4 : 5))));
 }
 int lane_range_of(int l) { return lane_range_of_dev(l); }
 
@@ -1084,7 +1084,7 @@ __device__ __forceinline__ void lane_switch(int l, const GraphDev &g, const Test
 // Stages LO <= l <= HI (one instantiation per range keeps the register count of
 // small l low: the launch sequence runs every range, all but one return at once).
 template <int LO, int HI, bool PROP>
-__global__ void __launch_bounds__(256, HI <= 2 ? 4 : (HI <= 4 ? 3 : 2))
+__global__ void __launch_bounds__(256, HI <= 2 ? 4 : (HI <= 4 ? 3 : (HI <= 8 ? 2 : 1)))
     ci_lane_kernel(GraphDev g, TestParams tp, const float *C32, int ldc,
                                                       ull *queue, ull qcap, ull *qlen)
 {
@@ -2034,6 +2034,8 @@ cudaError_t launch_ci_lane(GraphDev g, TestParams tp, const float *C32, const do
     if (range < 0 || range == 1) lane_launch<3, 4>(g, tp, C32, ldc, queue, qcap, qlen, prop, s);
     if (range < 0 || range == 2) lane_launch<5, 6>(g, tp, C32, ldc, queue, qcap, qlen, prop, s);
     if (range < 0 || range == 3) lane_launch<7, 8>(g, tp, C32, ldc, queue, qcap, qlen, prop, s);
+    if (range < 0 || range == 4) lane_launch<9, 10>(g, tp, C32, ldc, queue, qcap, qlen, prop, s);
+    if (range < 0 || range == 5) lane_launch<11, 12>(g, tp, C32, ldc, queue, qcap, qlen, prop, s);
     int ms, per_warp, wpc;
     direct_shape(LANE_LMAX + 2, ms, per_warp, wpc);
     size_t smem = (size_t)wpc * per_warp;

@@ -199,6 +199,46 @@ def test_skeleton_p95_dense_conventional(fp):
     _check_skeleton(fp, sem.make(2).X, order=0, precision=2)
 
 
+def _hub_case(seed=613, p=70, hub_degree=20, n=30000):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    dag, W, order = sem.hub_dag(p, rng, mean_degree=3.0, hubs=3, hub_degree=hub_degree, lo=0.4, hi=0.9)
+    return np.ascontiguousarray(sem.sample(W, order, n, rng).astype(np.float32))
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_skeleton_deep_stages_conventional(fp, precision):
+    """Three hubs of degree 20 keep their edges to stage 15 (Algorithm 1): stages 9-12
+    run on the register-resident small-stage kernel (ranges 9-10 and 11-12), 13-15 on
+    the warp-per-test kernel."""
+    X = _hub_case()
+    R, st = _check_skeleton(fp, X, order=0, precision=precision)
+    assert R["levels"][-1] >= 13 and sum(int(t) for t in R["tests_level"][9:13]) > 10 ** 5
+    assert st["levels_run"] == len(R["levels"])
+
+
+def test_skeleton_deep_stages_proposal_order(fp):
+    """The same stages with a proposal order (random network parameters, scored up
+    to l = 12): the skeleton equals the oracle's, every set separates in FP64."""
+    X = _hub_case()
+    n, p = X.shape
+    C = oracle.pearson(X)
+    R = oracle.skeleton(C, n, 0.01, -1, reversed_order=False)
+    theta = np.random.default_rng(8).standard_normal(fp.pc_mlp_nparam()).astype(np.float32) * 0.2
+    with fp.PC(n, p, 0.01, -1, order=0) as pc:
+        pc.corr(torch.from_numpy(X).cuda())
+        fp.pc_mlp_set_params(pc.h, theta)
+        for k, v in (("learned", 1), ("learned_min_tests", 0), ("learned_min_ratio", 0),
+                     ("learned_max_level", 12)):
+            fp.pc_set_opt(pc.h, k, v)
+        adj, st = pc.skeleton()
+        seps = pc.sepsets()
+    np.testing.assert_array_equal(adj, R["adj"])
+    assert set(seps) == set(R["sepsets"])
+    for (a, b), (lv, side, rank, nodes) in seps.items():
+        assert lv == R["sepsets"][(a, b)][0]
+        assert oracle.ci_test(C, n, 0.01, a, b, list(nodes))[0]
+
+
 @pytest.mark.parametrize("seed", range(6))
 def test_skeleton_random_small(fp, seed):
     rng = np.random.default_rng(seed)
