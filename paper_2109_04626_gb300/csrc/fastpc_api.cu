@@ -946,10 +946,8 @@ static pc_status enqueue_level(pc_handle *h, cudaStream_t s, int mmax, bool use_
         sc.has_comp = use_prec;
         sc.has_score = h->learned;
         sc.has_prec = use_prec;
-        CK(cudaGraphConditionalHandleCreate(&sc.lane, cg, fpc::LANE_RANGES, 0));
-        CK(cudaGraphConditionalHandleCreate(&sc.direct, cg, 0, 0));
-        if (sc.has_comp) CK(cudaGraphConditionalHandleCreate(&sc.comp, cg, 0, 0));
-        if (sc.has_score) CK(cudaGraphConditionalHandleCreate(&sc.score, cg, 0, 0));
+        CK(cudaGraphConditionalHandleCreate(&sc.tests, cg, (unsigned)fpc::stage_branches(sc.has_comp, sc.has_score),
+                                            0));
         if (sc.has_prec) CK(cudaGraphConditionalHandleCreate(&sc.prec, cg, 0, 0));
     }
     {
@@ -983,12 +981,30 @@ static pc_status enqueue_level(pc_handle *h, cudaStream_t s, int mmax, bool use_
         return PC_OK;
     };
     if (conds) {
-        if (sc.has_score)
-            if (pc_status r = cond_node(h, s, sc.score, cudaGraphCondTypeIf, 1, score)) return r;
-        if (pc_status r = cond_node(h, s, sc.lane, cudaGraphCondTypeSwitch, fpc::LANE_RANGES, lane)) return r;
-        if (pc_status r = cond_node(h, s, sc.direct, cudaGraphCondTypeIf, 1, direct)) return r;
-        if (sc.has_comp)
-            if (pc_status r = cond_node(h, s, sc.comp, cudaGraphCondTypeIf, 1, comp)) return r;
+        // one switch node: branch i runs [scoring,] the test kernel of its kind [, complement]
+        auto branch = [&](int i, cudaStream_t st) -> pc_status {
+            for (int sco = 0; sco <= sc.has_score; ++sco)
+                for (int cmp = 0; cmp <= sc.has_comp; ++cmp)
+                    for (int kind = 0; kind <= fpc::STAGE_KIND_NONE; ++kind) {
+                        if ((kind == fpc::STAGE_KIND_NONE && (!cmp || sco)) ||
+                            fpc::stage_branch(kind, cmp, sco, sc.has_comp, sc.has_score) != i)
+                            continue;
+                        if (sco)
+                            if (pc_status r = score(0, st)) return r;
+                        if (kind < fpc::LANE_RANGES) {
+                            if (pc_status r = lane(kind, st)) return r;
+                        } else if (kind == fpc::STAGE_KIND_DIRECT) {
+                            if (pc_status r = direct(0, st)) return r;
+                        }
+                        if (cmp)
+                            if (pc_status r = comp(0, st)) return r;
+                        return PC_OK;
+                    }
+            return fail(h, PC_ERR_INTERNAL, "stage switch branch without a combination");
+        };
+        if (pc_status r = cond_node(h, s, sc.tests, cudaGraphCondTypeSwitch,
+                                    (unsigned)fpc::stage_branches(sc.has_comp, sc.has_score), branch))
+            return r;
     } else {
         if (h->learned) {
             auto t = T(6);

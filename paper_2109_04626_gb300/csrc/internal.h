@@ -63,17 +63,41 @@ struct LevelInfo {
     unsigned deg_ticket;                // CTAs of the stage's degrees kernel done (last one runs the tail)
 };
 
-// Conditional nodes of the captured stage body: the head kernel decides which
-// kernels of a stage have work (switch over the small-stage kernel ranges, and
-// if-nodes for the warp-per-test, complement and scoring kernels); the tail
+// Conditional nodes of the captured stage body: the head kernel picks one branch
+// of a switch over the stage's test kernels (stage_branch below); the tail
 // kernel decides the precision-block updates.
 struct StageConds {
-    cudaGraphConditionalHandle lane, direct, comp, score, prec;
+    cudaGraphConditionalHandle tests, prec;
     int use;                            // 1 inside the captured stage body
-    int has_comp, has_score, has_prec;  // which nodes the body has
+    int has_comp, has_score, has_prec;  // which kernels the body has
 };
 constexpr int LANE_LMAX = 12;           // stages the lane-per-test kernel runs (FP32 modes)
 constexpr int LANE_RANGES = 6;          // small-stage kernel instantiations: l 0-2, 3-4, 5-6, 7-8, 9-10, 11-12
+
+// Branches of the stage's switch node.  kind: 0 .. LANE_RANGES-1 a small-stage
+// kernel range, STAGE_KIND_DIRECT the warp-per-test kernel, STAGE_KIND_NONE
+// neither; comp: the complement kernel as well; score: the proposal's scoring
+// kernels first.  Only combinations with work have a branch, in four blocks:
+// (comp 0, score 0) kinds but NONE, (comp 1, score 0) every kind, then with
+// scoring (kinds but NONE) comp 0 and comp 1; blocks a handle cannot use
+// (no complement or no proposal) are left out.  One switch node replaces a
+// chain of four conditional nodes, each of which sat on the stage's critical path.
+constexpr int STAGE_KIND_DIRECT = LANE_RANGES, STAGE_KIND_NONE = LANE_RANGES + 1;
+__host__ __device__ inline int stage_branches(int has_comp, int has_score)
+{
+    const int k0 = LANE_RANGES + 1, k1 = LANE_RANGES + 2;
+    return k0 + (has_comp ? k1 : 0) + (has_score ? k0 * (has_comp ? 2 : 1) : 0);
+}
+// Branch index of (kind, comp, score); stage_branches(...) when nothing runs.
+__host__ __device__ inline int stage_branch(int kind, int comp, int score, int has_comp, int has_score)
+{
+    const int k0 = LANE_RANGES + 1, k1 = LANE_RANGES + 2;
+    comp = comp && has_comp;
+    score = score && has_score && kind != STAGE_KIND_NONE;
+    if (kind == STAGE_KIND_NONE && !comp) return stage_branches(has_comp, has_score);
+    if (!score) return comp ? k0 + kind : kind;
+    return k0 + (has_comp ? k1 : 0) + (comp ? k0 : 0) + kind;
+}
 // kernels of a stage outside conditional nodes: head, commit, degrees + tail (one kernel)
 constexpr int STAGE_FIXED_KERNELS = 3;
 

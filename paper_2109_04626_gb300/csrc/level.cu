@@ -298,18 +298,20 @@ __device__ __forceinline__ ull sat_mul(ull a, ull b)
     return a * b;
 }
 
-// The stage body's conditional nodes (captured loop): which small-stage kernel
-// range runs, and whether the warp-per-test, complement and scoring kernels do.
+// The stage body's switch node (captured loop): which small-stage kernel range
+// runs, or the warp-per-test kernel, and whether the complement and scoring
+// kernels do.
 __device__ __forceinline__ void set_stage_conds(const StageConds &sc, LevelInfo *I, int lane, int direct, int comp,
                                                 int score, int lane_kernels)
 {
-    cudaGraphSetConditional(sc.lane, (unsigned)lane);
-    cudaGraphSetConditional(sc.direct, (unsigned)direct);
-    if (sc.has_comp) cudaGraphSetConditional(sc.comp, (unsigned)comp);
-    if (sc.has_score) cudaGraphSetConditional(sc.score, (unsigned)score);
+    const int kind = lane < LANE_RANGES ? lane : (direct ? STAGE_KIND_DIRECT : STAGE_KIND_NONE);
+    comp = comp && sc.has_comp;
+    score = score && sc.has_score && kind != STAGE_KIND_NONE;
+    cudaGraphSetConditional(sc.tests, (unsigned)stage_branch(kind, comp, score, sc.has_comp, sc.has_score));
     // head, commit, degrees + tail, the lane branch (kernel, [FP64 entries: collect, fill,]
     // FP64 pass, overflow pass) and the rest (the tail counts the precision update)
-    I->kernels_run += STAGE_FIXED_KERNELS + (lane < LANE_RANGES ? lane_kernels : 0) + direct + comp + 2 * score;
+    I->kernels_run += STAGE_FIXED_KERNELS + (lane < LANE_RANGES ? lane_kernels : 0) + (kind == STAGE_KIND_DIRECT) +
+                      comp + 2 * score;
 }
 
 // Exclusive saturating scan of NV values per thread over a block of up to 1024
