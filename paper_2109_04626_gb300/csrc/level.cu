@@ -1706,8 +1706,7 @@ __global__ void commit_kernel(GraphDev g, int l_fixed, int explicit_sets, int co
     __shared__ ull sb[SB_ROWS * SB_COLS];
     load_small_binom(g, sb);
     __syncthreads();
-    // warp-uniform trip count: the sepsets of a warp's removed pairs are expanded
-    // by the whole warp below
+    // one ordered pair per thread (grid-stride in warp-aligned steps)
     for (long long base = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); base < nop;
          base += (long long)gridDim.x * blockDim.x) {
         const long long o = base + lane;
@@ -1761,57 +1760,46 @@ __global__ void commit_kernel(GraphDev g, int l_fixed, int explicit_sets, int co
                 }
             }
         }
-        unsigned pend = __ballot_sync(0xffffffffu, expand);
-        while (pend) {
-            const int src = __ffs(pend) - 1;
-            pend &= pend - 1;
-            const int s_su = __shfl_sync(0xffffffffu, su, src), s_jj = __shfl_sync(0xffffffffu, jj, src);
-            const int s_dd = __shfl_sync(0xffffffffu, dd, src);
-            const ull s_rank = __shfl_sync(0xffffffffu, rank, src), s_off = __shfl_sync(0xffffffffu, off, src);
-            const int *nb = g.nbr + nidx(g, s_su);
-            const int kd = s_dd - l;                      // dropped members
+        // each lane expands its own removed pair (the pairs of a warp are consecutive
+        // neighbours of one node, so removals cluster; one pair at a time per warp
+        // serialised them)
+        if (expand) {
+            const int *nb = g.nbr + nidx(g, su);
+            const int kd = dd - l;                        // dropped members
             if (kd <= KC_MAX && kd < l) {
-                // expand through the complement: R = the kd dropped positions, at lex
-                // rank C(dd,l) - 1 - rank among the kd-subsets; S = the rest,
-                // ascending (a ballot prefix keeps the order)
+                // through the complement: R = the kd dropped positions, at lex rank
+                // C(dd,l) - 1 - rank among the kd-subsets; S = the rest, ascending
                 int posR[KC_MAX], nodeR[KC_MAX];
-                const ull T = g.binom[(long long)s_dd * g.ldb + l];
-                const bool small_d = s_dd < SB_ROWS;
-                unrank_lex_fixed<KC_MAX>(T - 1 - s_rank, s_dd, kd, small_d ? sb : g.binom, small_d ? SB_COLS : g.ldb,
+                const ull T = g.binom[(long long)dd * g.ldb + l];
+                const bool small_d = dd < SB_ROWS;
+                unrank_lex_fixed<KC_MAX>(T - 1 - rank, dd, kd, small_d ? sb : g.binom, small_d ? SB_COLS : g.ldb,
                                          posR);
 #pragma unroll
-                for (int i = 0; i < KC_MAX; ++i) nodeR[i] = i < kd ? cand_node(g, prop, s_su, s_jj, s_dd, posR[i]) : -1;
+                for (int i = 0; i < KC_MAX; ++i) nodeR[i] = i < kd ? cand_node(g, prop, su, jj, dd, posR[i]) : -1;
                 int o2 = 0;
-                for (int y0 = 0; y0 <= s_dd; y0 += 32) {
-                    const int y = y0 + lane;
-                    bool keep = false;
-                    int w = 0;
-                    if (y <= s_dd && y != s_jj) {
-                        w = nb[y];
-                        keep = true;
+                for (int y = 0; y <= dd; ++y) {
+                    if (y == jj) continue;
+                    const int w = nb[y];
+                    bool keep = true;
 #pragma unroll
-                        for (int i = 0; i < KC_MAX; ++i) keep &= nodeR[i] != w;
-                    }
-                    const unsigned kb = __ballot_sync(0xffffffffu, keep);
-                    if (keep) g.pool[s_off + o2 + __popc(kb & ((1u << lane) - 1u))] = w;
-                    o2 += __popc(kb);
+                    for (int i = 0; i < KC_MAX; ++i) keep &= nodeR[i] != w;
+                    if (keep) g.pool[off + o2++] = w;
                 }
-            } else if (lane == 0) {
-                ull r = s_rank;
+            } else {
+                ull r = rank;
                 int x = 0;
                 for (int i = 0; i < l; ++i) {
-                    while (x < s_dd - (l - i)) {
-                        ull c = g.binom[(long long)(s_dd - x - 1) * g.ldb + (l - i - 1)];
+                    while (x < dd - (l - i)) {
+                        ull c = g.binom[(long long)(dd - x - 1) * g.ldb + (l - i - 1)];
                         if (r < c) break;
                         r -= c;
                         ++x;
                     }
-                    g.pool[s_off + i] = cand_node(g, prop, s_su, s_jj, s_dd, x);
+                    g.pool[off + i] = cand_node(g, prop, su, jj, dd, x);
                     ++x;
                 }
-                if (prop) sort_small(g.pool + s_off, l);
+                if (prop) sort_small(g.pool + off, l);
             }
-            __syncwarp();
         }
     }
     if (removed) atomicAdd(&g.ctr->edges_removed, removed);
