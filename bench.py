@@ -11,7 +11,7 @@ counted in the lexicographic order (the tests the sequential algorithm of the
 oracle executes, so the CPU baseline and every GPU configuration are counted
 alike; the learned order reaches the same skeleton with fewer tests); the L2 is
 flushed (a 512 MB write) before every timed step.  --impl reference times the FP64 CPU oracle
-on the same workload (the reference arm of this build).
+on the same workload (the reference arm).
 """
 from __future__ import annotations
 

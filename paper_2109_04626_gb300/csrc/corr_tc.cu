@@ -255,7 +255,7 @@ static void tc_init()
     if (cudaGetDevice(&dev) != cudaSuccess) return;
     cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
     cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
-    if (major != 10 || minor != 3) return;           // this build targets sm_103a only
+    if (major != 10 || minor != 3) return;           // the kernels are compiled for sm_103a only
     void *fn = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=

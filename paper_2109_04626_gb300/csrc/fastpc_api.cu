@@ -780,7 +780,7 @@ static pc_status corr_impl(pc_handle *h, const void *X, int32_t dtype, int64_t l
         else CK(fpc::launch_cast_c(h->C64, h->C32, p, h->ldc, s));
     } else if (h->precision == 1 || !want_bf16) {
         if (h->precision == 2) {
-            // tensor-core path not available in this build: FP32 operands on the CUDA cores
+            // tensor-core path not available on this device: FP32 operands on the CUDA cores
             CK(fpc::launch_standardize(Xd, dtype, n, p, ld, h->mean + o, h->rsd + o, h->stats_ws, nullptr, h->Xs32 + po,
                                        nullptr, nullptr, h->ldk, s));
         }

@@ -1,6 +1,6 @@
 """GPU parity: the CUDA path (through the C-ABI) against the FP64 CPU oracle.
 
-Bars (the benchmark spec): partial correlations within 1e-5 absolute, decisions and the
+Bars: partial correlations within 1e-5 absolute, decisions and the
 removed-edge set bit-exact, sepsets (level, side, rank, nodes) identical, and
 the sequential canonical test count equal to the oracle's.
 """
