@@ -16,8 +16,10 @@ on the same workload (the reference arm).
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import os
+import signal
 import subprocess
 import sys
 import threading
@@ -107,26 +109,39 @@ def workload(name):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
-    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi clocks and throttle reasons sampled during the timed region.
+
+    Samples are taken every PERIOD_MS; each carries nvidia-smi's own timestamp, and
+    the summary keeps those taken between entering and leaving the ``with`` block (the
+    timed region), so that a region of a few tens of milliseconds still holds samples.
+    Entering waits (bounded) for the first sample, so the sampler is running when the
+    region starts.  Where no timestamp parses, every sample is kept."""
+    Q = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 20
+    START_WAIT_S = 2.0
 
     def __init__(self, index):
         self.index = index
         self.proc = None
         self.lines = []
+        self.t_begin = self.t_end = None
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", str(self.PERIOD_MS)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            deadline = time.monotonic() + self.START_WAIT_S
+            while not self.lines and self.proc.poll() is None and time.monotonic() < deadline:
+                time.sleep(0.005)
         except (OSError, FileNotFoundError):
             self.proc = None
+        self.t_begin = time.time()
         return self
 
     def _read(self):
@@ -134,30 +149,46 @@ class ClockSampler:
             self.lines.append(ln.strip())
 
     def __exit__(self, *a):
+        self.t_end = time.time()
         if self.proc:
-            self.proc.terminate()
+            time.sleep(2 * self.PERIOD_MS / 1000.0)      # the sample that covers the end
             try:
+                self.proc.send_signal(signal.SIGINT)     # its loop's own exit: output flushed
                 self.proc.wait(timeout=5)
-            except subprocess.TimeoutExpired:
+            except (subprocess.TimeoutExpired, OSError):
                 self.proc.kill()
+            self.t.join(timeout=5)
+
+    @staticmethod
+    def _stamp(s):
+        try:
+            return datetime.datetime.strptime(s.strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
 
     def summary(self):
-        sm, mx, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
         for ln in self.lines:
             f = [x.strip() for x in ln.split(",")]
-            if len(f) < 8:
+            if len(f) < 9:
                 continue
             try:
-                sm.append(float(f[0]))
-                mx = float(f[1])
+                rows.append((self._stamp(f[0]), float(f[1]), float(f[2]), f[5:9]))
             except ValueError:
                 continue
-            for nm, v in zip(names, f[4:8]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        stamped = [r for r in rows if r[0] is not None]
+        window = "timed region"
+        inside = [r for r in stamped if self.t_begin is not None and self.t_end is not None
+                  and self.t_begin <= r[0] <= self.t_end]
+        if inside:
+            rows = inside
+        elif rows:
+            window = "whole sampler run (no sample stamped inside the region)"
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = {nm for r in rows for nm, v in zip(names, r[3]) if v.lower() == "active"}
+        sm = [r[1] for r in rows]
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": rows[-1][2] if rows else None,
+                "reasons": sorted(reasons), "samples": len(sm), "period_ms": self.PERIOD_MS, "window": window}
 
 
 def dist_setup(args):
