@@ -4,9 +4,9 @@ written here -- every stage l freezes the adjacency, every adjacent pair tries
 the l-subsets of adj(a)\\{b} and then of adj(b)\\{a} in lexicographic order, the
 first independent set separates, all deletions of the stage happen at its end --
 with each partial correlation taken from numpy's inverse of the (l+2)x(l+2)
-correlation block instead of the oracle's elimination.  The removed pairs, every separating set (stage, side,
-rank, members), the pairs that no set separates and the sequential test counts
-per stage must agree (no GPU needed)."""
+correlation block instead of the oracle's elimination.  The removed pairs,
+every separating set (stage, side, rank, members), the pairs that no set
+separates and the sequential test counts per stage must agree (no GPU needed)."""
 import itertools
 import math
 import statistics
