@@ -11,7 +11,9 @@ conditioning, with n chosen so that the FP64 statistic lies within 1 % of the
 threshold.  Every decision the model trusts must equal the FP64 decision, with
 the FP32 statistic's error well inside the distance to the threshold: for
 correlations exact in FP32 (the FP32 GEMM and cast paths, eps_C = 1.2e-7) and
-for entry errors of 2e-7 (the size the BF16x3 tensor-core GEMM typically leaves)."""
+for entry errors of 2e-7 (the size the BF16x3 tensor-core GEMM typically leaves).
+The split-precision product itself is emulated too: on SEM data of the workloads'
+recipes its entry errors stay below the level at which the model stops holding."""
 import math
 import statistics
 
@@ -131,3 +133,44 @@ def test_trusted_fp32_decisions_equal_fp64(regime):
         assert ind == ind64, label
         # the FP32 statistic's error stays well inside the distance to the threshold
         assert abs(sq * math.atanh(float(a)) - z64) < 0.5 * abs(z64 - q), label
+
+
+def _bf16(x):
+    """Round float32 values to bfloat16 (nearest, ties to even), kept as float32."""
+    b = np.asarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    return ((b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000).astype(np.uint32).view(np.float32)
+
+
+def _corr_bf16x3(Xs, ktile=64):
+    """The split-precision product: X = hi + lo in BF16, hi*hi + hi*lo + lo*hi summed in
+    FP32 within a tile of samples, compensated (Kahan) sums across tiles."""
+    hi = _bf16(Xs)
+    lo = _bf16(Xs.astype(np.float32) - hi)
+    n, p = Xs.shape
+    acc = np.zeros((p, p), np.float32)
+    comp = np.zeros((p, p), np.float32)
+    for k0 in range(0, n, ktile):
+        H, Lo = hi[k0:k0 + ktile], lo[k0:k0 + ktile]
+        part = (H.T @ H + H.T @ Lo + Lo.T @ H).astype(np.float32)
+        y = part - comp
+        t = acc + y
+        comp = (t - acc) - y
+        acc = t
+    return acc / np.float32(n)
+
+
+@pytest.mark.parametrize("shape", [(95, 5000, 0.3), (200, 20000, None)])
+def test_bf16x3_entry_errors_stay_below_the_models_breakdown(shape):
+    # on SEM data of the workloads' recipes the split-precision correlations stay well
+    # below the +-5e-7 entry error from which the emulated model stops holding
+    from paper_2109_04626_gb300 import sem
+    p, n, prob = shape
+    rng = np.random.Generator(np.random.PCG64(77))
+    dag, W, order = sem.er_dag(p, prob if prob else 10.0 / (p - 1), rng)
+    X = sem.sample(W, order, n, rng)
+    Xs = (X - X.mean(0)) / X.std(0)
+    C64 = Xs.T @ Xs / n
+    E = np.abs(_corr_bf16x3(Xs).astype(np.float64) - C64)
+    np.fill_diagonal(E, 0.0)
+    assert E.max() < 5e-7
+    assert np.median(E[np.triu_indices(p, 1)]) < 1e-7
