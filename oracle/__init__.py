@@ -12,7 +12,7 @@ marshals numpy arrays through ctypes.
 Paper passages followed (see the C file for each routine):
   * Pearson corr: Sec. 4 (definition of ``corr``).
   * Partial correlation: Sec. 4, H = H0 - H1 H2^-1 H1^T, rho = h12/sqrt(h11 h22).
-  * Fisher-z test: Sec. 2.2.2, Eq. 1 and the replacement of line 7 of Alg. 1.
+  * Fisher-z test: Sec. 2.2.2, Eq. 1 and the rule that replaces Alg. 1's independence query.
   * Skeleton: Algorithm 1 (conventional) and Algorithm 2 (reversed order),
     PC-stable deletion at the end of each stage.
   * Orientation: Algorithm 1, Phase II (unshielded colliders, rules R1-R4),

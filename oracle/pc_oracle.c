@@ -41,7 +41,7 @@
 /* Inverse standard normal CDF: Wichura (1988), Algorithm AS 241 (PPND16),
  * Applied Statistics 37(3):477-484.  Used for the threshold
  * Phi^{-1}(1 - alpha/2) of the Fisher-z test (Sec. 2.2.2, Eq. 1 and the
- * replacement of line 7 of Algorithm 1).                                  */
+ * rule that replaces the independence query of Algorithm 1).             */
 double oracle_norm_ppf(double p)
 {
     static const double a[8] = {
@@ -194,7 +194,7 @@ int oracle_partial_corr(const double *C, int32_t ldc, int32_t u, int32_t v,
 }
 
 /* Fisher-z statistic sqrt(n-l-3)*|arctanh r| (Eq. 1 and the rule that
- * replaces line 7 of Algorithm 1; the absolute value follows that rule,
+ * replaces Algorithm 1's independence query; the absolute value follows that rule,
  * Reading R5).  |r| >= 1 gives +inf (dependent). */
 static double fisher_z(double r, int64_t n, int32_t l)
 {
@@ -302,7 +302,7 @@ static void build_nbrs(const uint8_t *adj, int32_t p, int32_t *deg, int32_t *nbr
 /* Enumerate the size-l subsets of cand \ {excl} (cand ascending, length dc)
  * in lexicographic order of positions; stop at the first independent one.
  * Returns 1 if found (rank, positions -> nodes written to S_out).  The test
- * count is added to *ntests.  Algorithm 1 lines 6-7 / Algorithm 2 lines 4-5. */
+ * count is added to *ntests.  The inner search over S of Algorithms 1 and 2. */
 static int search_side(const double *C, int32_t p, int64_t n, double q, double tol,
                        int32_t u, int32_t v, const int32_t *nb, int32_t dn, int32_t l,
                        int64_t *ntests, int64_t *rank_out, int32_t *S_out,
@@ -338,8 +338,8 @@ static int search_side(const double *C, int32_t p, int64_t n, double q, double t
     return 0;
 }
 
-/* One stage l with the adjacency frozen at its start (PC-stable, Algorithm 1
- * lines 3-13 and 18-20 with stable = True).  Edges {a,b}, a<b, are tested on
+/* One stage l with the adjacency frozen at its start (PC-stable: the stage
+ * body of Algorithm 1 with stable = True).  Edges {a,b}, a<b, are tested on
  * side 0 (S from adj(a)\{b}) and, if that finds no separating set, side 1
  * (S from adj(b)\{a}) -- Reading R1/R2.  Deletions are applied at the end. */
 static void stable_level(oracle_result *R, const double *C, uint8_t *adj, int32_t p,
@@ -397,7 +397,7 @@ static void stable_level(oracle_result *R, const double *C, uint8_t *adj, int32_
 }
 
 /* One stage l of the original (order-dependent) PC: an edge is deleted as
- * soon as a separating set is found (Algorithm 1 line 9, stable = False), so
+ * soon as a separating set is found (Algorithm 1 with stable = False), so
  * later pairs see the current graph.  Sequential by construction. */
 static void nonstable_level(oracle_result *R, const double *C, uint8_t *adj, int32_t p,
                             int64_t n, double q, double tol, int32_t l, int flags)
@@ -493,7 +493,7 @@ static void stage_a(oracle_result *R, const double *C, uint8_t *adj, int32_t p,
  * Fisher-z threshold, tol >= 0 selects population mode, max_level < 0 means
  * no cap.  Schedules:
  *  conventional (Algorithm 1): l = 0,1,... while some adjacent ordered pair
- *    has |adj(u)\{v}| >= l (the early termination of lines 21-23), l <= cap;
+ *    has |adj(u)\{v}| >= l (Algorithm 1's early termination), l <= cap;
  *  reversed (Algorithm 2): the stage l = p-2 first (closed form, Reading R4),
  *    then l = min(cap, L*) and l <- min(l-1, L*) down to 0, where L* is the
  *    largest candidate-set size in the current graph (levels no pair can use
@@ -678,7 +678,7 @@ int32_t oracle_meek(const uint8_t *adj, uint8_t *mk, int32_t p)
     return rounds;
 }
 
-/* Unshielded colliders (Algorithm 1, Phase II, lines 1-5): for every pair of
+/* Unshielded colliders (Algorithm 1, Phase II, its first step): for every pair of
  * non-adjacent vertices i < j and every common neighbour k, k not in S(i,j)
  * puts arrowheads at k on i - k and j - k (Reading R15).  S(i,j) is given as
  * sep_off[i*p+j]: an offset into pool with sep_len[i*p+j] members, -1 for

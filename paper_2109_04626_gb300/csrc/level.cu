@@ -1,5 +1,5 @@
-// level.cu -- one PC-stable stage of the skeleton search (Algorithm 1 lines
-// 3-20 / Algorithm 2 lines 2-18) on the GPU.
+// level.cu -- one PC-stable stage of the skeleton search (the stage body of
+// Algorithm 1 / Algorithm 2) on the GPU.
 //
 //  degrees      frozen neighbour lists (ascending) from the adjacency bitset
 //  counts+scan  C(d, l) tests per adjacent ordered pair (u,v), d = |adj(u)\{v}|,
