@@ -40,6 +40,7 @@ ONESIDED_J = 8
 STAGEA_GENERIC = 16
 NO_STAGEA = 32
 POPULATION = 64
+PATHPOOL = 128     # one candidate pool per pair: adj(G,a,b) on a-b paths (PC-stable search)
 
 
 def build(force: bool = False) -> str:

@@ -31,6 +31,7 @@
 #define ORACLE_STAGEA_GENERIC 16   /* reversed: run l=p-2 through enumeration     */
 #define ORACLE_NO_STAGEA      32   /* reversed: skip the l=p-2 stage entirely     */
 #define ORACLE_POPULATION     64   /* CI by |r| <= tol instead of Fisher z        */
+#define ORACLE_PATHPOOL      128   /* one pool per pair: adj(G,a,b) on a-b paths  */
 
 /* Degeneracy floor (Reading R8): a conditional variance at or below this
  * value means the variable is (numerically) determined by the conditioning
@@ -338,6 +339,51 @@ static int search_side(const double *C, int32_t p, int64_t n, double q, double t
     return 0;
 }
 
+/* comp[x*p + k]: the connected component of node k in the frozen graph with
+ * node x removed (-1 at k = x).  Depth-first over the adjacency matrix. */
+static void components_without(const uint8_t *adj, int32_t p, int32_t *comp)
+{
+    int32_t *stack = (int32_t *)malloc(sizeof(int32_t) * (size_t)(p > 0 ? p : 1));
+    for (int32_t x = 0; x < p; ++x) {
+        int32_t *c = comp + (size_t)x * p;
+        for (int32_t k = 0; k < p; ++k) c[k] = -1;
+        int32_t id = 0;
+        for (int32_t s0 = 0; s0 < p; ++s0) {
+            if (s0 == x || c[s0] >= 0) continue;
+            int32_t top = 0;
+            stack[top++] = s0;
+            c[s0] = id;
+            while (top) {
+                int32_t y = stack[--top];
+                for (int32_t z = 0; z < p; ++z)
+                    if (z != x && c[z] < 0 && adj[(size_t)y * p + z]) { c[z] = id; stack[top++] = z; }
+            }
+            ++id;
+        }
+    }
+    free(stack);
+}
+
+/* The candidate pool of the pair {a,b} in the paper's notation,
+ * adj(G,a,b) intersected with path(G,a,b) (Sec. 2.1 definitions, used by
+ * Algorithms 1 and 2): the nodes adjacent to a or to b, other than a and b,
+ * that lie on some simple a-b path of the frozen graph.  A neighbour k of a
+ * lies on one iff k reaches b without passing through a (then a, k, ..., b is
+ * such a path), a neighbour of b iff it reaches a without passing through b.
+ * Written ascending to pool; returns its size. */
+static int32_t path_pool(const uint8_t *adj, int32_t p, const int32_t *comp, int32_t a, int32_t b,
+                         int32_t *pool)
+{
+    const int32_t *ca = comp + (size_t)a * p, *cb = comp + (size_t)b * p;
+    int32_t d = 0;
+    for (int32_t k = 0; k < p; ++k) {
+        if (k == a || k == b) continue;
+        int on = (adj[(size_t)a * p + k] && ca[k] == ca[b]) || (adj[(size_t)b * p + k] && cb[k] == cb[a]);
+        if (on) pool[d++] = k;
+    }
+    return d;
+}
+
 /* One stage l with the adjacency frozen at its start (PC-stable: the stage
  * body of Algorithm 1 with stable = True).  Edges {a,b}, a<b, are tested on
  * side 0 (S from adj(a)\{b}) and, if that finds no separating set, side 1
@@ -364,11 +410,24 @@ static void stable_level(oracle_result *R, const double *C, uint8_t *adj, int32_
     int32_t *fS = (int32_t *)malloc(sizeof(int32_t) * (size_t)(E ? E : 1) * (size_t)lw);
     int64_t *ft = (int64_t *)calloc((size_t)(E ? E : 1), sizeof(int64_t));
     int64_t *fd = (int64_t *)calloc((size_t)(E ? E : 1), sizeof(int64_t));
+    int32_t *comp = NULL;
+    if (flags & ORACLE_PATHPOOL) {
+        comp = (int32_t *)malloc(sizeof(int32_t) * (size_t)p * (size_t)p);
+        components_without(adj, p, comp);
+    }
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t k = 0; k < E; ++k) {
         int32_t a = ea[k], b = eb[k];
         int64_t rank = 0;
         int got = 0;
+        if (flags & ORACLE_PATHPOOL) {
+            /* one pool for the pair, searched once (side 0) */
+            int32_t pool[p];
+            int32_t dp = path_pool(adj, p, comp, a, b, pool);
+            got = search_side(C, p, n, q, tol, a, b, pool, dp, l, &ft[k], &rank, fS + (size_t)k * lw, &fd[k]);
+            if (got) { found[k] = 1; fside[k] = 0; frank[k] = rank; }
+            continue;
+        }
         if (!(flags & ORACLE_ONESIDED_J))
             got = search_side(C, p, n, q, tol, a, b, nbr + (size_t)a * p, deg[a], l,
                               &ft[k], &rank, fS + (size_t)k * lw, &fd[k]);
@@ -393,7 +452,7 @@ static void stable_level(oracle_result *R, const double *C, uint8_t *adj, int32_
         R->removed_level[l]++;
     }
     free(deg); free(nbr); free(ea); free(eb); free(found); free(fside);
-    free(frank); free(fS); free(ft); free(fd);
+    free(frank); free(fS); free(ft); free(fd); free(comp);
 }
 
 /* One stage l of the original (order-dependent) PC: an edge is deleted as
@@ -444,6 +503,31 @@ static int32_t max_cand(const uint8_t *adj, int32_t p)
         if (d > 0 && d - 1 > best) best = d - 1;
     }
     return best;
+}
+
+/* The largest pool of an adjacent pair (ORACLE_PATHPOOL), -1 without edges. */
+static int32_t max_path_pool(const uint8_t *adj, int32_t p)
+{
+    int32_t *comp = (int32_t *)malloc(sizeof(int32_t) * (size_t)p * (size_t)p);
+    int32_t *pool = (int32_t *)malloc(sizeof(int32_t) * (size_t)p);
+    components_without(adj, p, comp);
+    int32_t best = -1;
+    for (int32_t a = 0; a < p; ++a)
+        for (int32_t b = a + 1; b < p; ++b)
+            if (adj[(size_t)a * p + b]) {
+                int32_t d = path_pool(adj, p, comp, a, b, pool);
+                if (d > best) best = d;
+            }
+    free(comp);
+    free(pool);
+    return best;
+}
+
+/* Size of the largest candidate set of the current graph: adj(u)\{v} over
+ * adjacent ordered pairs, or the pair pools with ORACLE_PATHPOOL. */
+static int32_t largest_candidates(const uint8_t *adj, int32_t p, int flags)
+{
+    return (flags & ORACLE_PATHPOOL) ? max_path_pool(adj, p) : max_cand(adj, p);
 }
 
 /* The stage l = p-2 of Algorithm 2 in closed form: on the complete graph the
@@ -522,7 +606,7 @@ oracle_result *oracle_skeleton(const double *C, int32_t p, int64_t n, double q, 
     int nonstable = flags & ORACLE_NONSTABLE;
     if (!(flags & ORACLE_REVERSED)) {
         for (int32_t l = 0; l <= cap; ++l) {
-            if (max_cand(R->adj, p) < l) break;
+            if (largest_candidates(R->adj, p, flags) < l) break;
             R->level_seq[R->n_levels++] = l;
             if (nonstable) nonstable_level(R, C, R->adj, p, n, q, tol, l, flags);
             else stable_level(R, C, R->adj, p, n, q, tol, l, flags);
@@ -535,14 +619,14 @@ oracle_result *oracle_skeleton(const double *C, int32_t p, int64_t n, double q, 
         }
         l = cap;
         if (R->stageA_ran && l > p - 3) l = p - 3;
-        int32_t ls = max_cand(R->adj, p);
+        int32_t ls = largest_candidates(R->adj, p, flags);
         if (ls < l) l = ls;
         while (l >= 0) {
             R->level_seq[R->n_levels++] = l;
             if (nonstable) nonstable_level(R, C, R->adj, p, n, q, tol, l, flags);
             else stable_level(R, C, R->adj, p, n, q, tol, l, flags);
             int32_t nl = l - 1;
-            ls = max_cand(R->adj, p);
+            ls = largest_candidates(R->adj, p, flags);
             if (ls < nl) nl = ls;
             l = nl;
         }
