@@ -81,6 +81,9 @@ def _load():
         lib.oracle_skeleton.restype = ctypes.c_void_p
         lib.oracle_skeleton.argtypes = [dp, ctypes.c_int32, ctypes.c_int64, ctypes.c_double,
                                         ctypes.c_double, ctypes.c_int32, ctypes.c_int]
+        lib.oracle_skeleton_batched.restype = ctypes.c_void_p
+        lib.oracle_skeleton_batched.argtypes = [dp, ctypes.c_int32, ctypes.c_int64, ctypes.c_double,
+                                                ctypes.c_double, ctypes.c_int32, ctypes.c_int64]
         lib.oracle_result_free.restype = None
         lib.oracle_result_free.argtypes = [ctypes.c_void_p]
         lib.oracle_result_copy.restype = None
@@ -205,6 +208,23 @@ def skeleton(C, n: int, alpha: float, max_level: int = -1, reversed_order: bool 
         f |= POPULATION
     q = threshold(alpha)
     R = lib.oracle_skeleton(_dp(C), p, int(n), q, float(tol), int(max_level), f)
+    return _unpack(lib, R, p)
+
+
+def skeleton_batched(C, n: int, alpha: float, batch: int, max_level: int = -1, tol: float = -1.0) -> dict:
+    """Algorithm 3 (the batched form of Algorithm 2, Sec. 4): the tests of a stage
+    are queued pair by pair over the path-restricted pools (Reading R19) and
+    decided ``batch`` at a time, each batch's deletions applied before the next
+    is formed (Reading R20 for the partial batches).  Same result dict as
+    ``skeleton``; every separating set is recorded on side 0."""
+    lib = _load()
+    C = np.ascontiguousarray(C, dtype=np.float64)
+    p = C.shape[0]
+    R = lib.oracle_skeleton_batched(_dp(C), p, int(n), threshold(alpha), float(tol), int(max_level), int(batch))
+    return _unpack(lib, R, p)
+
+
+def _unpack(lib, R, p: int) -> dict:
     try:
         pp = p * p
         adj = np.empty(pp, dtype=np.uint8)

@@ -583,8 +583,8 @@ static void stage_a(oracle_result *R, const double *C, uint8_t *adj, int32_t p,
  *    largest candidate-set size in the current graph (levels no pair can use
  *    are empty and are skipped; Algorithm 2 has no early termination).
  * Levels are also capped at n-4 so that n-l-3 > 0 (Reading R9).            */
-oracle_result *oracle_skeleton(const double *C, int32_t p, int64_t n, double q, double tol,
-                               int32_t max_level, int flags)
+/* A result on the complete graph, no separating sets yet. */
+static oracle_result *result_new(int32_t p, int64_t n)
 {
     oracle_result *R = (oracle_result *)calloc(1, sizeof(oracle_result));
     R->p = p; R->n = n;
@@ -599,6 +599,13 @@ oracle_result *oracle_skeleton(const double *C, int32_t p, int64_t n, double q, 
     R->level_seq = (int32_t *)calloc((size_t)p + 1, sizeof(int32_t));
     for (size_t k = 0; k < pp; ++k) { R->sep_level[k] = -1; R->adj[k] = 1; }
     for (int32_t a = 0; a < p; ++a) R->adj[(size_t)a * p + a] = 0;
+    return R;
+}
+
+oracle_result *oracle_skeleton(const double *C, int32_t p, int64_t n, double q, double tol,
+                               int32_t max_level, int flags)
+{
+    oracle_result *R = result_new(p, n);
     if (p < 2) return R;
     int32_t cap = p - 2;
     if (max_level >= 0 && max_level < cap) cap = max_level;
@@ -632,6 +639,111 @@ oracle_result *oracle_skeleton(const double *C, int32_t p, int64_t n, double q, 
         }
     }
     for (int32_t l = 0; l <= p; ++l) R->tests_total += R->tests_level[l];
+    return R;
+}
+
+/* Algorithm 3, the batched form of Algorithm 2: stage l = p-2 down to 0; the
+ * loop reaches the adjacent pairs {a,b}, a<b, in order, forms each pair's pool
+ * adj(G,a,b) intersected with path(G,a,b) (Reading R19) from the graph as it is
+ * when the pair is reached, and queues its l-subsets in lexicographic order;
+ * whenever `batch` tests are queued they are decided together and the edges
+ * found independent are deleted at once.  Readings (R20): the partial batch is
+ * flushed at the end of every stage (the listing resets its counter per stage
+ * and flushes only after the last one, which would drop tests); a pair deleted
+ * by an earlier batch queues no further subsets; within a batch a pair's first
+ * independent test in queue order gives its separating set (side 0, the rank
+ * of the set in its pool).  Empty stages are skipped as in Reading R4, and
+ * stage p-2 is enumerated (no closed form: deletions inside it change later
+ * pools). */
+typedef struct {
+    int32_t a, b;
+    int64_t rank;
+} batch_entry;
+
+static void flush_batch(oracle_result *R, const double *C, uint8_t *adj, int32_t p, int64_t n, double q,
+                        double tol, int32_t l, const batch_entry *E, const int32_t *ES, int64_t m,
+                        int *dirty)
+{
+    int32_t lw = l > 0 ? l : 1;
+    for (int64_t t = 0; t < m; ++t) {
+        int32_t a = E[t].a, b = E[t].b;
+        size_t ab = (size_t)a * p + b, ba = (size_t)b * p + a;
+        int degen = 0;
+        int ind = oracle_ci_test(C, p, n, q, tol, a, b, ES + (size_t)t * lw, l, NULL, NULL, &degen);
+        R->tests_level[l]++;
+        if (degen) R->degenerate++;
+        if (!ind || R->sep_level[ab] == l) continue;   /* dependent, or already separated here */
+        R->sep_level[ab] = R->sep_level[ba] = l;
+        R->sep_side[ab] = R->sep_side[ba] = 0;
+        R->sep_rank[ab] = R->sep_rank[ba] = E[t].rank;
+        R->sep_off[ab] = R->sep_off[ba] = R->pool_len;
+        pool_push(R, ES + (size_t)t * lw, l);
+        R->removed_level[l]++;
+    }
+    for (int64_t t = 0; t < m; ++t) {
+        size_t ab = (size_t)E[t].a * p + E[t].b, ba = (size_t)E[t].b * p + E[t].a;
+        if (R->sep_level[ab] == l && adj[ab]) { adj[ab] = adj[ba] = 0; *dirty = 1; }
+    }
+}
+
+oracle_result *oracle_skeleton_batched(const double *C, int32_t p, int64_t n, double q, double tol,
+                                       int32_t max_level, int64_t batch)
+{
+    oracle_result *R = result_new(p, n);
+    if (p < 2 || batch < 1) return R;
+    int32_t cap = p - 2;
+    if (max_level >= 0 && max_level < cap) cap = max_level;
+    if (n - 4 < cap) cap = (int32_t)(n - 4);
+    uint8_t *adj = R->adj;
+    int32_t *comp = (int32_t *)malloc(sizeof(int32_t) * (size_t)p * (size_t)p);
+    int32_t *pool = (int32_t *)malloc(sizeof(int32_t) * (size_t)p);
+    int64_t ecap = 1024;
+    batch_entry *E = (batch_entry *)malloc(sizeof(batch_entry) * (size_t)ecap);
+    int32_t *ES = (int32_t *)malloc(sizeof(int32_t) * (size_t)ecap * (size_t)(p > 0 ? p : 1));
+    int32_t l = cap;
+    int32_t ls = max_path_pool(adj, p);
+    if (ls < l) l = ls;
+    while (l >= 0) {
+        R->level_seq[R->n_levels++] = l;
+        int32_t lw = l > 0 ? l : 1;
+        int64_t m = 0;
+        int dirty = 1;
+        for (int32_t a = 0; a < p; ++a)
+            for (int32_t b = a + 1; b < p; ++b) {
+                if (!adj[(size_t)a * p + b]) continue;
+                if (dirty) { components_without(adj, p, comp); dirty = 0; }
+                int32_t d = path_pool(adj, p, comp, a, b, pool);
+                if (d < l) continue;
+                int32_t idx[lw];
+                for (int32_t k = 0; k < l; ++k) idx[k] = k;
+                for (int64_t rank = 0;; ++rank) {
+                    if (!adj[(size_t)a * p + b]) break;        /* deleted by an earlier batch */
+                    if (m == ecap) {
+                        ecap *= 2;
+                        E = (batch_entry *)realloc(E, sizeof(batch_entry) * (size_t)ecap);
+                        ES = (int32_t *)realloc(ES, sizeof(int32_t) * (size_t)ecap * (size_t)(p > 0 ? p : 1));
+                    }
+                    E[m].a = a; E[m].b = b; E[m].rank = rank;
+                    for (int32_t k = 0; k < l; ++k) ES[(size_t)m * lw + k] = pool[idx[k]];
+                    if (++m == batch) {
+                        flush_batch(R, C, adj, p, n, q, tol, l, E, ES, m, &dirty);
+                        m = 0;
+                    }
+                    int32_t i = l - 1;
+                    while (i >= 0 && idx[i] == d - l + i) --i;
+                    if (i < 0) break;
+                    ++idx[i];
+                    for (int32_t j = i + 1; j < l; ++j) idx[j] = idx[j - 1] + 1;
+                }
+            }
+        if (m) flush_batch(R, C, adj, p, n, q, tol, l, E, ES, m, &dirty);
+        int32_t nl = l - 1;
+        ls = max_path_pool(adj, p);
+        if (ls < nl) nl = ls;
+        l = nl;
+    }
+    for (int32_t k = 0; k <= p; ++k) R->tests_total += R->tests_level[k];
+    free(comp); free(pool); free(E); free(ES);
     return R;
 }
 

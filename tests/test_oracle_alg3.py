@@ -1,0 +1,101 @@
+"""Pins for the oracle's Algorithm 3 (the batched form of Algorithm 2, Sec. 4;
+readings R19 for the pool, R20 for the batches), each reducing it to something
+computed another way (no GPU needed):
+
+* a batch larger than any stage decides a whole stage on the graph it started
+  with -- the PC-stable search over the same pools (the oracle's PATHPOOL
+  switch, stage p-2 enumerated) must give the same skeleton and separating sets;
+* a batch of one deletes an edge as soon as a test separates it -- a plain
+  enumeration written here (pools from walking all simple paths, decisions from
+  numpy's block inverses) must give the same skeleton, sets and test counts;
+* any batch size recovers the true skeleton from faithful population
+  correlations."""
+import itertools
+import statistics
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2109_04626_gb300 import sem
+from tests.test_oracle_bruteforce import _indep
+from tests.test_oracle_orient import _tiny_dags
+from tests.test_oracle_pathpool import _largest, _pool
+
+
+def _case(seed, p, n, prob):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    dag, W, order = sem.er_dag(p, prob, rng)
+    return oracle.pearson(sem.sample(W, order, n, rng)), n
+
+
+def brute_batch_of_one(C, n, alpha):
+    """Stage l = p-2 down to 0 (empty stages skipped); each adjacent pair, reached
+    in order, searches its current pool lexicographically and is deleted at its
+    first independent set."""
+    p = C.shape[0]
+    q = -statistics.NormalDist().inv_cdf(alpha / 2)
+    adj = np.ones((p, p), dtype=bool)
+    np.fill_diagonal(adj, False)
+    seps, tests, levels = {}, {}, []
+    l = min(p - 2, _largest(adj))
+    while l >= 0:
+        levels.append(l)
+        tests[l] = 0
+        for a in range(p):
+            for b in range(a + 1, p):
+                if not adj[a, b]:
+                    continue
+                for rank, S in enumerate(itertools.combinations(_pool(adj, a, b), l)):
+                    tests[l] += 1
+                    if _indep(C, n, a, b, S, q)[0]:
+                        seps[(a, b)] = (l, 0, rank, tuple(int(x) for x in S))
+                        adj[a, b] = adj[b, a] = False
+                        break
+        l = min(l - 1, _largest(adj))
+    return adj.astype(np.uint8), seps, tests, levels
+
+
+@pytest.mark.parametrize("case", [(7101, 7, 400, 0.45), (7102, 8, 1500, 0.35), (7103, 9, 3000, 0.3)])
+def test_whole_stage_batch_is_pc_stable_over_the_same_pools(case):
+    C, n = _case(*case)
+    B = oracle.skeleton_batched(C, n, 0.01, batch=10 ** 12)
+    R = oracle.skeleton(C, n, 0.01, -1, reversed_order=True, flags=oracle.PATHPOOL | oracle.STAGEA_GENERIC)
+    np.testing.assert_array_equal(B["adj"], R["adj"])
+    assert B["sepsets"] == R["sepsets"]
+    assert B["levels"] == R["levels"]
+    # a stage queues every subset of every pool, the stable search stops at the first
+    assert B["tests_total"] >= R["tests_total"]
+
+
+@pytest.mark.parametrize("case", [(7201, 7, 400, 0.45), (7202, 8, 1500, 0.35), (7203, 9, 3000, 0.3)])
+def test_batch_of_one_deletes_at_once(case):
+    C, n = _case(*case)
+    B = oracle.skeleton_batched(C, n, 0.01, batch=1)
+    adj, seps, tests, levels = brute_batch_of_one(C, n, 0.01)
+    np.testing.assert_array_equal(B["adj"], adj)
+    assert B["sepsets"] == seps
+    assert B["levels"] == levels
+    assert {l: int(B["tests_level"][l]) for l in levels} == tests
+
+
+def test_batch_size_changes_the_sample_result_somewhere():
+    # the batched form is order dependent in sample mode (its deletions inside a
+    # stage change the pools of the pairs that follow): some graph shows it
+    differ = 0
+    for seed in range(7300, 7310):
+        C, n = _case(seed, 9, 300, 0.4)
+        a = oracle.skeleton_batched(C, n, 0.05, batch=1)
+        b = oracle.skeleton_batched(C, n, 0.05, batch=10 ** 12)
+        differ += int(a["tests_total"] != b["tests_total"] or a["sepsets"] != b["sepsets"])
+    assert differ > 0
+
+
+@pytest.mark.parametrize("batch", [1, 5, 10 ** 12])
+def test_population_recovers_the_skeleton(batch):
+    for dag, W in _tiny_dags(25, 7600, pmin=5, pmax=8, max_edges=12):
+        C = sem.population_corr(W)
+        B = oracle.skeleton_batched(C, 10 ** 9, 0.01, batch=batch, tol=1e-10)
+        np.testing.assert_array_equal(B["adj"], ((dag + dag.T) > 0).astype(np.uint8))
+        for (a, b), (lv, side, rank, nodes) in B["sepsets"].items():
+            assert abs(oracle.partial_corr(C, a, b, list(nodes))[0]) <= 1e-10
