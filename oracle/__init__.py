@@ -14,7 +14,9 @@ Paper passages followed (see the C file for each routine):
   * Partial correlation: Sec. 4, H = H0 - H1 H2^-1 H1^T, rho = h12/sqrt(h11 h22).
   * Fisher-z test: Sec. 2.2.2, Eq. 1 and the rule that replaces Alg. 1's independence query.
   * Skeleton: Algorithm 1 (conventional) and Algorithm 2 (reversed order),
-    PC-stable deletion at the end of each stage.
+    PC-stable deletion at the end of each stage; the path-restricted pool
+    adj(G,i,j) on i-j paths (Sec. 2.1 notation, switch PATHPOOL); Algorithm 3,
+    the batched form of Algorithm 2 (Sec. 4, ``skeleton_batched``).
   * Orientation: Algorithm 1, Phase II (unshielded colliders, rules R1-R4),
     which Algorithm 2 shares (Sec. 3.3).
 """
