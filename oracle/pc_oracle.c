@@ -463,13 +463,22 @@ static void nonstable_level(oracle_result *R, const double *C, uint8_t *adj, int
 {
     int32_t *nb = (int32_t *)malloc(sizeof(int32_t) * (size_t)p);
     int32_t *S = (int32_t *)malloc(sizeof(int32_t) * (size_t)(l > 0 ? l : 1));
+    int32_t *comp = (flags & ORACLE_PATHPOOL) ? (int32_t *)malloc(sizeof(int32_t) * (size_t)p * (size_t)p) : NULL;
+    int dirty = 1;
     for (int32_t a = 0; a < p; ++a)
         for (int32_t b = a + 1; b < p; ++b) {
             size_t ab = (size_t)a * p + b, ba = (size_t)b * p + a;
             if (!adj[ab]) continue;
             int64_t rank = 0, nt = 0, nd = 0;
             int got = 0, side = 0;
-            for (int s = 0; s < 2 && !got; ++s) {
+            if (comp) {
+                /* the pair's pool in the graph as it is now (deletions are immediate) */
+                if (dirty) { components_without(adj, p, comp); dirty = 0; }
+                int32_t dp = path_pool(adj, p, comp, a, b, nb);
+                got = search_side(C, p, n, q, tol, a, b, nb, dp, l, &nt, &rank, S, &nd);
+                dirty = got;
+            }
+            for (int s = 0; s < 2 && !got && !comp; ++s) {
                 if (s == 0 && (flags & ORACLE_ONESIDED_J)) continue;
                 if (s == 1 && (flags & ORACLE_ONESIDED_I)) continue;
                 int32_t u = s ? b : a, v = s ? a : b, dn = 0;
@@ -491,6 +500,7 @@ static void nonstable_level(oracle_result *R, const double *C, uint8_t *adj, int
         }
     free(nb);
     free(S);
+    free(comp);
 }
 
 /* Largest candidate-set size max |adj(u)\{v}| over adjacent ordered pairs. */

@@ -99,3 +99,16 @@ def test_population_recovers_the_skeleton(batch):
         np.testing.assert_array_equal(B["adj"], ((dag + dag.T) > 0).astype(np.uint8))
         for (a, b), (lv, side, rank, nodes) in B["sepsets"].items():
             assert abs(oracle.partial_corr(C, a, b, list(nodes))[0]) <= 1e-10
+
+
+@pytest.mark.parametrize("seed", range(930, 935))
+def test_batch_of_one_is_the_nonstable_search_over_the_same_pools(seed):
+    # two separate routines of the oracle: Algorithm 3 with b = 1 and the non-stable
+    # Algorithm 2 over the path-restricted pools (stage p-2 enumerated)
+    C, n = _case(seed, 9, 700, 0.35)
+    A = oracle.skeleton(C, n, 0.01, -1, True, flags=oracle.NONSTABLE | oracle.PATHPOOL | oracle.STAGEA_GENERIC)
+    B = oracle.skeleton_batched(C, n, 0.01, batch=1)
+    np.testing.assert_array_equal(A["adj"], B["adj"])
+    assert A["sepsets"] == B["sepsets"]
+    assert A["levels"] == B["levels"]
+    assert A["tests_total"] == B["tests_total"]

@@ -157,3 +157,17 @@ def test_pathpool_population_recovers_the_skeleton(rev):
         C = sem.population_corr(W)
         R = oracle.skeleton(C, 10 ** 9, 0.01, -1, reversed_order=rev, tol=1e-10, flags=oracle.PATHPOOL)
         np.testing.assert_array_equal(R["adj"], ((dag + dag.T) > 0).astype(np.uint8))
+
+
+def test_four_node_example_conventional_count_with_the_papers_pool():
+    # Sec. 3.1: with the paper's own pool adj(G,i,j) on i-j paths, Algorithm 1 runs the
+    # printed 17 tests (PC-stable and non-stable alike on this example); the reversed
+    # order runs 13 against the printed 14 (Reading R12)
+    from tests.test_oracle import _four_node
+    spec, indeps, dag, W = _four_node()
+    C = sem.population_corr(W)
+    for flags in (oracle.PATHPOOL, oracle.PATHPOOL | oracle.NONSTABLE):
+        R = oracle.skeleton(C, 10 ** 9, 0.01, -1, False, flags=flags, tol=1e-10)
+        assert R["tests_total"] == int(spec["count_pc"][0]) == 17
+    R = oracle.skeleton(C, 10 ** 9, 0.01, -1, True, flags=oracle.PATHPOOL | oracle.STAGEA_GENERIC, tol=1e-10)
+    assert R["tests_total"] == 13 and int(spec["count_pc_reverse"][0]) == 14
