@@ -3,8 +3,11 @@
 
 One step = the whole hot path on one synthetic input resident in HBM:
 pc_corr (standardise + correlation GEMM) followed by pc_skeleton (every stage
-of Algorithm 2 with PC-stable deletion).  Default workload: the dense p=95 SEM
-(edge prob 0.3, n=5000, FP32 data, alpha=0.01, all stages).
+of the skeleton search with PC-stable deletion).  Default workload: the p=1000
+Erdos-Renyi SEM (expected degree 10, n=20000, FP32 data, alpha=0.01, all
+stages, conventional order), with the proposal network trained on 200 seeded
+p=200 SEMs of the same recipe; --workload p95_dense runs the dense p=95 SEM in
+the reversed order (Algorithm 2).
 
 Prints ONE JSON line.  ``value`` is canonical CI tests per second of step time,
 counted in the lexicographic order (the tests the sequential algorithm of the
@@ -42,9 +45,22 @@ def dominant_class(tim):
     """The kernel class with the most device time among those with algorithmic work.
     The stage bookkeeping (head, commit, degrees, tail: counts, scans, sepset records)
     and the proposal scoring have none of their own; their time stays in class_ms and
-    the largest class of all is named beside the roofline."""
+    the largest class of all is named beside the roofline.  corr_gemm is a part of
+    corr and is reported on its own line (roofline_gemm)."""
     from paper_2109_04626_gb300 import fastpc as fp
-    return max((c for c in fp.TIMING_CLASSES if c not in ("bookkeeping", "scoring")), key=lambda c: tim[c][0])
+    return max((c for c in fp.TIMING_CLASSES if c not in ("bookkeeping", "scoring", "corr_gemm")),
+               key=lambda c: tim[c][0])
+
+
+# the kernels behind each timing class that the roofline names
+CLASS_KERNELS = {
+    "ci_direct": "ci_lane_kernel (stages l <= 12, one thread per chunk of sets) + ci_direct_kernel "
+                 "(one warp per test) + ci_redecide_kernel (FP64 pass)",
+    "ci_complement": "ci_complement_kernel (FP64, from neighbourhood precision blocks)",
+    "prec": "prec_update_kernel (neighbourhood precision blocks, FP64)",
+    "stage_a": "stage_a sweep inverse (FP64)",
+    "corr": "pc_corr: column statistics, standardisation, correlation GEMM",
+}
 
 
 def measured_peaks():
@@ -59,11 +75,11 @@ def measured_peaks():
         return 1900.0, 6800.0, "of fallback"
 
 
-# DRAM bytes (read + write) per launch of a class's dominant kernel, from one
-# ncu capture of the current kernel (profiles/prec_update_p95_dense.md: three
-# launches read 0.109, 1.824 and 0.231 MB and wrote nothing; their mean); absent:
-# not captured since the kernel last changed (the roofline's traffic is then null)
-DRAM_BYTES_PER_LAUNCH = {("p95_dense", "prec"): 7.21e5}
+# DRAM bytes (read + write) per launch of a class's kernels, from one ncu
+# capture of the current kernels (the profile summary of that workload and
+# kernel gives the command and the per-launch figures); absent: not captured
+# since the kernels last changed (the roofline's traffic is then null)
+DRAM_BYTES_PER_LAUNCH = {}
 
 
 def parse():
@@ -72,7 +88,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="p95_dense",
+    ap.add_argument("--workload", default="p1000_er",
                     choices=["p20_fp64", "p95_dense", "p500_powerlaw", "p1000_er", "many64", "paper_sweep", "power"],
                     help="many64: 64 independent SEMs (p in [50,400], edge prob in [0.05,0.3], "
                          "n in [2000,20000]), conventional order; paper_sweep: the paper's "
@@ -82,7 +98,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
-    ap.add_argument("--train-seeds", type=int, default=24)
+    ap.add_argument("--train-seeds", type=int, default=None,
+                    help="training SEMs of the proposal network (default: 200 for p1000_er, "
+                         "whose network is trained on p=200 SEMs; 24 otherwise)")
     ap.add_argument("--learned-max-level", type=int, default=None,
                     help="largest stage the proposal network scores (library default if unset)")
     ap.add_argument("--corr-only", action="store_true",
@@ -287,7 +305,7 @@ def run_reference(args):
             dt += d_
             nt += R["tests_total"]
         return dt, nt
-    for _ in range(max(0, min(args.warmup, 1))):
+    for _ in range(max(0, args.warmup)):
         one()
     times, tests = [], 0
     for _ in range(args.steps):
@@ -383,15 +401,10 @@ def run_ours(args):
             out.append(a.elapsed_time(b))
         return float(np.mean(out)), st
 
-    # lexicographic order first: its canonical count is the oracle's, the unit of the metric
-    step(pc)
-    lex_ms, lex_st = timed_steps(pc, max(3, min(args.steps, 5)))
-    adj_lex = adj_d.cpu().numpy()
-    tests_unit = lex_st["tests_canonical"]
-
     # proposal network: trained on plain-run outcomes of other seeds of the same recipe
     # (untimed); the timed configuration then enumerates in its order
     learned = None
+    train_seeds = args.train_seeds if args.train_seeds is not None else (200 if w["cfg"] == 4 else 24)
     if not args.no_learned:
         from paper_2109_04626_gb300 import proposal, sem as _sem
         t0 = time.perf_counter()
@@ -410,22 +423,35 @@ def run_ours(args):
             Xs = _sem.sample(W_, order_, tn_, rng)
             return Xs.astype(np.float32) if w["dtype"] == "float32" else Xs
 
-        feats, labels = proposal.collect(make_X, range(args.train_seeds), w["alpha"], w["order"],
+        feats, labels = proposal.collect(make_X, range(train_seeds), w["alpha"], w["order"],
                                          w["max_level"], mixed_prec)
         loss = proposal.train(pc.h, feats, labels, epochs=6, batch=8192, lr=2e-3, seed=1)
-        fp.pc_set_opt(pc.h, "learned", 1)
         if args.learned_max_level is not None:
             fp.pc_set_opt(pc.h, "learned_max_level", args.learned_max_level)
-        learned = {"train_rows": int(labels.shape[0]), "train_seeds": args.train_seeds,
+        learned = {"train_rows": int(labels.shape[0]), "train_seeds": train_seeds,
                    "train_sems": f"p={tp_}, n={tn_}",
                    "final_loss": loss, "train_s": time.perf_counter() - t0,
                    "max_level": int(fp.pc_get_opt(pc.h, "learned_max_level"))}
+        fp.pc_set_opt(pc.h, "learned", 1)
 
     for _ in range(args.warmup):
         st = step(pc)
     torch.cuda.synchronize()
-    # launch shape of the test kernels for this problem (untimed; results do not depend on it)
+    # launch shape of the test kernels for this problem (untimed; results do not depend
+    # on it), chosen for the configuration that is timed; the lexicographic order below
+    # runs with the same shape, so the two orders differ in the enumeration order only
     tune = fp.pc_autotune(pc.h, 2) if not args.no_autotune else None
+
+    # lexicographic order: its canonical count is the oracle's, the unit of the metric
+    fp.pc_set_opt(pc.h, "learned", 0)
+    for _ in range(args.warmup):
+        step(pc)
+    lex_ms, lex_st = timed_steps(pc, max(3, min(args.steps, 5)))
+    adj_lex = adj_d.cpu().numpy()
+    tests_unit = lex_st["tests_canonical"]
+    if learned is not None:
+        fp.pc_set_opt(pc.h, "learned", 1)
+
     for _ in range(args.warmup):
         st = step(pc)
     torch.cuda.synchronize()
@@ -479,7 +505,10 @@ def run_ours(args):
     achieved = dom_flops / (dom_ms * 1e-3) / 1e12 if dom_ms > 0 else 0.0
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": DRAM_BYTES_PER_LAUNCH.get((w["name"], dom)),
-                "kernel": dom,
+                "kernel": dom, "kernels": CLASS_KERNELS.get(dom, dom),
+                "work": "algorithmic flops F(l) = l^3/3 + 2l^2 + 6l + 10 per executed test (direct), "
+                        "k^3/3 + 2k^2 + 6k + 20 (complement)" if dom in ("ci_direct", "ci_complement") else
+                        "algorithmic flops counted by the kernels",
                 "kernel_ms_per_step": dom_ms, "launch_groups": tim[dom][1],
                 "peak_source": "nominal FP64 1.25 TFLOP/s" if peak == FP64_PEAK_TFLOPS else
                 "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
@@ -487,13 +516,25 @@ def run_ours(args):
                 "largest_class": max(cls, key=lambda c: tim[c][0])}
 
     # the correlation step against the tensor roofline: useful flops n p (p+1) of the
-    # symmetric product (the BF16x3 split issues three products per useful one)
-    roofline_corr = None
+    # symmetric product (the BF16x3 split issues three products per useful one); the
+    # GEMM kernels alone (class corr_gemm) and the whole pc_corr (statistics,
+    # standardisation, GEMM, reduce)
+    roofline_gemm = roofline_corr = None
+    bf16, hbm, src = measured_peaks()
+    gemm_flops = n * p * (p + 1)
+    if tim["corr_gemm"][0] > 0:
+        ach = gemm_flops / (tim["corr_gemm"][0] * 1e-3) / 1e12
+        roofline_gemm = {"bound": "tensor", "kernel": "corr_bf16x3_kernel (tcgen05, TMA) + corr_tc_reduce_kernel"
+                         if mixed_prec == 2 else "Gram kernel (CUDA cores)",
+                         "achieved": ach, "peak": bf16, "unit": "TFLOP/s", "frac": ach / bf16,
+                         "issued_tflops": 3 * ach if mixed_prec == 2 else ach,
+                         "useful_flops_per_launch": gemm_flops, "ms_per_step": tim["corr_gemm"][0],
+                         "launch_groups": tim["corr_gemm"][1],
+                         "peak_source": f"bf16 dense burst, {src}"}
     if tim["corr"][0] > 0:
-        bf16, hbm, src = measured_peaks()
-        ach = n * p * (p + 1) / (tim["corr"][0] * 1e-3) / 1e12
+        ach = gemm_flops / (tim["corr"][0] * 1e-3) / 1e12
         roofline_corr = {"bound": "tensor", "kernel": "pc_corr (column statistics, standardisation, "
-                         "BF16x3 tcgen05 GEMM, FP64 split-K reduce)" if mixed_prec == 2 else "pc_corr",
+                         "BF16x3 tcgen05 GEMM, Kahan FP32 split-K reduce)" if mixed_prec == 2 else "pc_corr",
                          "achieved": ach, "peak": bf16, "unit": "TFLOP/s", "frac": ach / bf16,
                          "issued_tflops": 3 * ach if mixed_prec == 2 else ach, "ms_per_step": tim["corr"][0],
                          "peak_source": f"bf16 dense burst, {src}"}
@@ -572,6 +613,7 @@ def run_ours(args):
                 "redecided": stats[-1]["tests_redecided"],
                 "complement_tests": stats[-1]["complement_tests"],
                 "roofline": roofline,
+                "roofline_gemm": roofline_gemm,
                 "roofline_corr": roofline_corr,
                 "autotune": tune,
                 "cpu_baseline": cpu,

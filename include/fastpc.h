@@ -267,10 +267,11 @@ int64_t pc_kernel_launches(void);
  * 1 closed-form stage l=p-2, 2 neighbourhood precision builds and downdates,
  * 3 direct CI tests, 4 complement CI tests, 5 stage bookkeeping (neighbour
  * lists, counts, scans, commit), 6 proposal scoring, ordering and the FP64
- * re-test of the sepsets found in the proposal order.  Writes
- * per-class device milliseconds and launch-group counts accumulated since the
- * last reset (reset != 0 clears them afterwards).  ms and count have 7
- * entries; either may be NULL. */
+ * re-test of the sepsets found in the proposal order, 7 the correlation GEMM
+ * kernels alone (the tensor-core product and its split-K reduce, or the SIMT
+ * Gram kernel; a part of class 0).  Writes per-class device milliseconds and
+ * launch-group counts accumulated since the last reset (reset != 0 clears them
+ * afterwards).  ms and count have 8 entries; either may be NULL. */
 pc_status pc_timing(pc_handle *h, double *ms, int64_t *count, int32_t reset);
 
 /* pc_corr_noalloc -- the correlation matrix without any allocation, for
@@ -288,7 +289,8 @@ pc_status pc_timing(pc_handle *h, double *ms, int64_t *count, int32_t reset);
  * Its scratch (column means and 1/sd) is a file-scope __device__ array sized
  * for p <= 4096 (64 KiB on every GPU that loads the library, held until the
  * process exits); p > 4096, n < 2, host pointers or a bad dtype/stride return
- * PC_ERR_ARG before anything is launched.  It calls no cudaMalloc, cudaFree
+ * PC_ERR_ARG before anything is launched; so do X or C_out on a device other
+ * than the current one (make the buffers' device current before the call).  It calls no cudaMalloc, cudaFree
  * or other allocating routine.  The first call on each device looks up the
  * array's device address with that device current (cudaGetSymbolAddress) and
  * caches it; make that first call before any stream capture.  All calls share

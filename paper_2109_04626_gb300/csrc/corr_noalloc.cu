@@ -96,14 +96,16 @@ __global__ void __launch_bounds__(256) gram_raw_kernel(const T *__restrict__ X, 
         }
 }
 
-static bool on_device(const void *p)
+// True when p is device (or managed) memory of device `dev`, the device the
+// kernels will run on: a buffer of another GPU is rejected before any launch.
+static bool on_device(const void *p, int dev)
 {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
 }
 
 }  // namespace fpc
@@ -114,7 +116,12 @@ extern "C" pc_status pc_corr_noalloc(const void *X, int32_t dtype, int64_t n, in
     using namespace fpc;
     if (!X || !C_out || (dtype != PC_F32 && dtype != PC_F64)) return PC_ERR_ARG;
     if (n < 2 || n > (1ll << 31) || p < 1 || p > NOALLOC_MAXP || ld < p || ldc < p) return PC_ERR_ARG;
-    if (!on_device(X) || !on_device(C_out)) return PC_ERR_ARG;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return PC_ERR_ARG;                  // no usable device: nothing can be on it
+    }
+    if (!on_device(X, dev) || !on_device(C_out, dev)) return PC_ERR_ARG;
     double *stats = nullptr;
     if (noalloc_scratch(&stats) != cudaSuccess) return PC_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;

@@ -23,7 +23,7 @@ namespace fpc {
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 }
 
-constexpr int NCLS = 7;
+constexpr int NCLS = 8;   // class 7 (the correlation GEMM kernels) lies inside class 0
 struct TimedPair {
     int cls;
     cudaEvent_t a, b;
@@ -126,8 +126,8 @@ struct pc_handle {
     int timing = 0;
     std::vector<TimedPair> pending;
     std::vector<cudaEvent_t> evpool;
-    double cls_ms[NCLS] = {0, 0, 0, 0, 0, 0, 0};
-    long long cls_n[NCLS] = {0, 0, 0, 0, 0, 0, 0};
+    double cls_ms[NCLS] = {0, 0, 0, 0, 0, 0, 0, 0};
+    long long cls_n[NCLS] = {0, 0, 0, 0, 0, 0, 0, 0};
 };
 
 // Brackets the launches of one kernel class with events on the handle's stream.
@@ -784,6 +784,7 @@ static pc_status corr_impl(pc_handle *h, const void *X, int32_t dtype, int64_t l
             CK(fpc::launch_standardize(Xd, dtype, n, p, ld, h->mean + o, h->rsd + o, h->stats_ws, nullptr, h->Xs32 + po,
                                        nullptr, nullptr, h->ldk, s));
         }
+        Timed tg(h, 7);
         CK(fpc::launch_syrk_f32(h->Xs32 + po, n, h->ldk, p, C32b, ldb, s));
     } else {
         const size_t need = fpc::corr_bf16x3_ws_bytes(n, p);
@@ -794,6 +795,7 @@ static pc_status corr_impl(pc_handle *h, const void *X, int32_t dtype, int64_t l
             h->tc_ws_bytes = need;
         }
         if (blk <= 0) CK(cudaMemsetAsync(h->tc_err, 0, sizeof(int), s));
+        Timed tg(h, 7);
         CK(fpc::launch_corr_bf16x3(h->Xhi + po, h->Xlo + po, n, h->ldk, p, C32b, ldb, h->tc_ws,
                                    h->tc_ws_bytes, h->tc_err, s));
         tc = true;

@@ -331,13 +331,14 @@ def pc_kernel_launches() -> int:
     return int(load().pc_kernel_launches())
 
 
-TIMING_CLASSES = ["corr", "stage_a", "prec", "ci_direct", "ci_complement", "bookkeeping", "scoring"]
+# class "corr_gemm" (the correlation GEMM kernels alone) is a part of class "corr"
+TIMING_CLASSES = ["corr", "stage_a", "prec", "ci_direct", "ci_complement", "bookkeeping", "scoring", "corr_gemm"]
 
 
 def pc_timing(h, reset: bool = False) -> dict:
     """Per-kernel-class device ms and launch-group counts (option "timing" = 1)."""
-    ms = np.zeros(7, dtype=np.float64)
-    cnt = np.zeros(7, dtype=np.int64)
+    ms = np.zeros(len(TIMING_CLASSES), dtype=np.float64)
+    cnt = np.zeros(len(TIMING_CLASSES), dtype=np.int64)
     _check(h, load().pc_timing(h, ctypes.c_void_p(ms.ctypes.data), ctypes.c_void_p(cnt.ctypes.data),
                                1 if reset else 0))
     return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(TIMING_CLASSES)}
@@ -348,16 +349,22 @@ def pc_corr_noalloc(X, C_out, stream=None):
     into C_out (p x p float64 CUDA tensor) with no device allocation; see
     include/fastpc.h.  Issued on ``stream`` (torch stream, raw handle or None)."""
     import torch
+    if X.device.type != "cuda" or C_out.device != X.device:
+        raise ValueError(f"pc_corr_noalloc: X and C_out must be CUDA tensors on one device "
+                         f"(X on {X.device}, C_out on {C_out.device})")
     assert X.dtype in (torch.float32, torch.float64) and X.stride(1) == 1
     assert C_out.dtype == torch.float64 and C_out.stride(1) == 1
     n, p = X.shape
     dt = PC_F64 if X.dtype == torch.float64 else PC_F32
     raw = 0 if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
-    st = load().pc_corr_noalloc(ctypes.c_void_p(X.data_ptr()), dt, int(n), int(p), int(X.stride(0)),
-                                ctypes.c_void_p(C_out.data_ptr()), int(C_out.stride(0)),
-                                ctypes.c_void_p(raw))
+    lib = load()
+    with torch.cuda.device(X.device):          # the library checks both buffers against the current device
+        st = lib.pc_corr_noalloc(ctypes.c_void_p(X.data_ptr()), dt, int(n), int(p), int(X.stride(0)),
+                                 ctypes.c_void_p(C_out.data_ptr()), int(C_out.stride(0)),
+                                 ctypes.c_void_p(raw))
     if st != 0:
-        raise PCError(st, "pc_corr_noalloc: p must be <= 4096, n >= 2, device pointers, valid dtype/strides")
+        raise PCError(st, "pc_corr_noalloc: p must be <= 4096, n >= 2, device pointers of the current "
+                          "device, valid dtype/strides")
 
 
 def pc_mlp_nparam() -> int:

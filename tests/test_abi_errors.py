@@ -43,6 +43,12 @@ p = (ctypes.c_int32 * 2)(10, 1)
 res["batch_bad_p"] = int(lib.pc_create_batch(2, ctypes.cast(n, ctypes.c_void_p), ctypes.cast(p, ctypes.c_void_p),
                                              0.01, -1, ctypes.byref(h)))
 res["noalloc_bad"] = int(lib.pc_corr_noalloc(None, 0, 0, 0, 0, None, 0, None))
+# valid sizes but buffers that are not device memory of the current device (host
+# arrays here): rejected by the pointer check before any launch
+Xh = (ctypes.c_float * 32)()
+Ch = (ctypes.c_double * 16)()
+res["noalloc_not_device"] = int(lib.pc_corr_noalloc(ctypes.cast(Xh, ctypes.c_void_p), 0, 8, 4, 4,
+                                                    ctypes.cast(Ch, ctypes.c_void_p), 4, None))
 if WITH_CREATE:
     st = int(lib.pc_create(1000, 10, 0.01, -1, ctypes.byref(h)))
     res["create_valid"] = st
@@ -73,7 +79,20 @@ def test_entry_points_reject_null_handles_and_fail_without_a_device():
     assert not bad, bad
     assert res["pc_threshold"] is True
     for k in ("create_bad_n", "create_bad_p", "create_bad_alpha", "create_null_out", "batch_bad_p",
-              "noalloc_bad"):
+              "noalloc_bad", "noalloc_not_device"):
         assert res[k] == arg, (k, res[k])
     if no_gpu:
         assert res["create_valid"] == 2 and res["create_handle_null"]   # PC_ERR_CUDA, no handle
+
+
+def test_noalloc_binding_rejects_buffers_off_one_cuda_device():
+    # the binding issues the call with X's device current and refuses buffers that
+    # are not both CUDA tensors of that device, before the library is called
+    torch = pytest.importorskip("torch")
+    from paper_2109_04626_gb300 import fastpc
+    X = torch.zeros((8, 4), dtype=torch.float32)
+    C = torch.zeros((4, 4), dtype=torch.float64)
+    with pytest.raises(ValueError):
+        fastpc.pc_corr_noalloc(X, C)
+    with pytest.raises(ValueError):
+        fastpc.pc_corr_noalloc(X.to("meta"), C.to("meta"))

@@ -379,6 +379,8 @@ def test_stage_loop_drivers_agree(fp, mode):
             if mode == "timed":
                 tm = fp.pc_timing(pc.h)
                 assert tm["bookkeeping"][1] > 0 and tm["corr"][1] > 0
+                # the GEMM kernels are timed inside the correlation step
+                assert tm["corr_gemm"][1] > 0 and 0 < tm["corr_gemm"][0] <= tm["corr"][0]
 
 
 def test_levels_run_and_first_level_match_schedule(fp):

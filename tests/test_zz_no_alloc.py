@@ -55,6 +55,47 @@ def test_noalloc_matches_pc_corr_on_two_calls_in_a_row(fp):
         assert np.all(np.diag(C) == 1.0)
 
 
+def test_noalloc_small_then_large_with_shifted_means(fp):
+    # a small problem, then a larger one whose columns have different, large means:
+    # the second call must use its own statistics for every column, including the
+    # columns beyond the first call's p (a wrong offset into the shared array shows)
+    rng = np.random.default_rng(5)
+    Xs = rng.standard_normal((300, 12)) + np.arange(12) * 3.0
+    Xl = rng.standard_normal((700, 150)) @ (np.eye(150) + 0.1 * rng.standard_normal((150, 150)))
+    Xl = Xl + 1000.0 * (1 + np.arange(150))[None, :] - 40.0
+    for X in (Xs, Xl):
+        n, p = X.shape
+        C = torch.full((p, p), float("nan"), dtype=torch.float64, device="cuda")
+        fp.pc_corr_noalloc(torch.from_numpy(X).cuda(), C)
+        torch.cuda.synchronize()
+        assert np.abs(C.cpu().numpy() - _reference_c64(fp, X)).max() <= 1e-10
+
+
+def test_noalloc_strided_rows_leave_padding_untouched(fp):
+    # X and C_out with row strides above p (ld > p, ldc > p): the padding columns
+    # of C_out keep their sentinel and the p x p part equals pc_corr's
+    X = sem.make(2).X                                     # p=95, n=5000, FP32
+    n, p = X.shape
+    Xpad = torch.full((n, p + 13), 7.0, dtype=torch.float32, device="cuda")
+    Xpad[:, :p] = torch.from_numpy(X).cuda()
+    Cpad = torch.full((p, p + 5), -3.25, dtype=torch.float64, device="cuda")
+    fp.pc_corr_noalloc(Xpad[:, :p], Cpad[:, :p])
+    torch.cuda.synchronize()
+    out = Cpad.cpu().numpy()
+    assert np.all(out[:, p:] == -3.25)
+    assert np.abs(out[:, :p] - _reference_c64(fp, X)).max() <= TOL
+
+
+def test_noalloc_at_its_maximum_p(fp):
+    # p = 4096, the size the fixed array is sized for (few samples keep it quick)
+    rng = np.random.default_rng(9)
+    X = rng.standard_normal((64, 4096)) * (1 + np.arange(4096) % 7) + np.arange(4096) % 11
+    C = torch.empty((4096, 4096), dtype=torch.float64, device="cuda")
+    fp.pc_corr_noalloc(torch.from_numpy(X).cuda(), C)
+    torch.cuda.synchronize()
+    assert np.abs(C.cpu().numpy() - _reference_c64(fp, X)).max() <= 1e-10
+
+
 def test_noalloc_repeat_same_input_is_stable(fp):
     X = sem.make(1).X
     n, p = X.shape
