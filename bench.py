@@ -423,8 +423,10 @@ def run_ours(args):
             Xs = _sem.sample(W_, order_, tn_, rng)
             return Xs.astype(np.float32) if w["dtype"] == "float32" else Xs
 
+        # at most 100k rows of each training run (seeded draw): 200 p=200 runs give
+        # about 1.6M rows each, far more than the 16->128->128->1 network needs
         feats, labels = proposal.collect(make_X, range(train_seeds), w["alpha"], w["order"],
-                                         w["max_level"], mixed_prec)
+                                         w["max_level"], mixed_prec, max_rows_per_seed=100_000)
         loss = proposal.train(pc.h, feats, labels, epochs=6, batch=8192, lr=2e-3, seed=1)
         if args.learned_max_level is not None:
             fp.pc_set_opt(pc.h, "learned_max_level", args.learned_max_level)

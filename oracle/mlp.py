@@ -38,12 +38,16 @@ def pack(parts) -> np.ndarray:
     return np.concatenate([np.asarray(parts[name], dtype=np.float64).reshape(-1) for name, _ in SIZES])
 
 
-def forward(theta, X):
-    """Scores s (rows,) and the activations (h1, h2, pre-activations)."""
+def forward(theta, X, h1_store=None):
+    """Scores s (rows,) and the activations (h1, h2, pre-activations).
+    h1_store: optional map applied to h1 before the second layer reads it (the
+    precision a network stores its hidden activations in; identity if None)."""
     P = unpack(theta)
     X = np.asarray(X, dtype=np.float64)
     a1 = X @ P["W1"].T + P["b1"]
     h1 = np.maximum(a1, 0.0)
+    if h1_store is not None:
+        h1 = np.asarray(h1_store(h1), dtype=np.float64)
     a2 = h1 @ P["W2"].T + P["b2"]
     h2 = np.maximum(a2, 0.0)
     s = h2 @ P["w3"] + P["b3"][0]
@@ -54,17 +58,18 @@ def softplus(s):
     return np.logaddexp(0.0, s)
 
 
-def loss(theta, X, y):
-    s, _ = forward(theta, X)
+def loss(theta, X, y, h1_store=None):
+    s, _ = forward(theta, X, h1_store)
     return float(np.mean(softplus(s) - np.asarray(y, dtype=np.float64) * s))
 
 
-def grad(theta, X, y) -> np.ndarray:
-    """Gradient of loss() by the chain rule written out layer by layer."""
+def grad(theta, X, y, h1_store=None) -> np.ndarray:
+    """Gradient of loss() by the chain rule written out layer by layer (h1_store as
+    in forward(): the second layer and its weight gradient use the stored h1)."""
     P = unpack(theta)
     X = np.asarray(X, dtype=np.float64)
     y = np.asarray(y, dtype=np.float64)
-    s, (a1, h1, a2, h2) = forward(theta, X)
+    s, (a1, h1, a2, h2) = forward(theta, X, h1_store)
     B = X.shape[0]
     ds = (1.0 / (1.0 + np.exp(-s)) - y) / B            # d loss / d s
     g = {}

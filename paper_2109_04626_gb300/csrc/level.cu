@@ -557,6 +557,12 @@ struct WarpAcc {
     float maxdz;
 };
 
+// per-thread counters of the small-stage kernel (32-bit: a thread runs far fewer
+// than 2^32 tests of one stage); its FP32 flops are tests x F(L), formed at the end
+struct LaneAcc {
+    unsigned tests, band, guard;
+};
+
 __device__ __forceinline__ ull flops_direct(int l)
 {
     ull L = (ull)l;
@@ -629,6 +635,70 @@ __device__ __noinline__ void ensure_c64(const int *nd, int m, const TestParams &
     __syncwarp();
 }
 
+// ---------------------------------------------------------------- FP32 trust rule
+// The FP32 trailing block (h11, h12, h22) of a test is the exact Schur
+// complement of corr + E, where E holds the correlation step's entry errors
+// (|E_ij| <= eps_c) and the backward error of the FP32 factorisation (every
+// row of the Cholesky factor of a correlation matrix has unit norm, so each
+// entry of that backward error is below a few m eps32; 4 m eps32 is taken).
+// With b_u = corr_SS^{-1} corr_Su and b_v the regression coefficients of u
+// and v on S, to first order in eps = eps_c + 4 m eps32
+//   |dh12| <= eps A_u A_v,  |dh11| <= eps A_u^2,  |dh22| <= eps A_v^2,
+//   A_u = 1 + |b_u|_1,  A_v = 1 + |b_v|_1,
+// hence |dr| <= eps (A_u A_v / sqrt(h11 h22) + |r|/2 (A_u^2/h11 + A_v^2/h22)).
+// The expansion is used only while eps A_u^2/h11, eps A_v^2/h22 and
+// m eps |corr_SS^{-1}| (kap) stay below 0.05, and the bound is doubled to
+// cover the higher-order terms and the rounding of the final ratio.  A test
+// is trusted when |r| clears the threshold r_q = tanh(q / sqrt(n-l-3)) by
+// more than that bound (then the FP64 decision of Eq. 1 is the same) and the
+// statistic lies at least `band` from q; otherwise it is re-decided in FP64.
+// Returns 0 trusted, 1 band (re-decide), 2 guard (re-decide); dr_out: the bound.
+constexpr float EPS32 = 5.96e-8f;
+
+__device__ __forceinline__ int fp32_trust(const TestParams &tp, int m, float sqf, float rq, float a, float h11,
+                                          float h22, float ih, float Au, float Av, float kap, float &dr_out)
+{
+    const float eps = tp.eps_c + (4.0f * (float)m) * EPS32;
+    const float i11 = __frcp_rn(h11), i22 = __frcp_rn(h22);
+    const float qu = eps * Au * Au * i11, qv = eps * Av * Av * i22;
+    dr_out = INFINITY;
+    if (fmaxf(fmaxf(qu, qv), kap) > 0.05f) return 2;
+    const float dr = 2.0f * eps * (Au * Av * ih + 0.5f * a * (Au * Au * i11 + Av * Av * i22)) + 8.0f * EPS32;
+    dr_out = dr;
+    if (dr > tp.dr_max) return 2;
+    // |z - q| >= sqf |a - rq| / (1 - min(a, rq)^2) (mean-value theorem on atanh)
+    const float gap = fabsf(a - rq), mn = fminf(a, rq);
+    if (gap <= dr || sqf * gap < (float)tp.band * (1.0f - mn * mn)) return 1;
+    return 0;
+}
+
+// l1 norms of the regression coefficients b_u = corr_SS^{-1} corr_Su and b_v
+// from the factor warp_chol_test left in M (column k below the diagonal holds
+// L_ik, the diagonal the pivots L_kk^2, rows l and l+1 hold L^{-1} corr_Su and
+// L^{-1} corr_Sv): back substitution L^T b = y by the warp, column by column.
+// Overwrites the first l entries of rows l and l+1.
+__device__ __forceinline__ void warp_beta_l1(float *M, int ms, int l, float &bu, float &bv)
+{
+    const int lane = threadIdx.x & 31;
+    float *yu = M + (long long)l * ms, *yv = M + (long long)(l + 1) * ms;
+    float su = 0.f, sv = 0.f;
+    for (int k = l - 1; k >= 0; --k) {
+        __syncwarp();
+        const float rl = rsqrtf(M[k * ms + k]);
+        const float b_u = yu[k] * rl, b_v = yv[k] * rl;
+        su += fabsf(b_u);
+        sv += fabsf(b_v);
+        for (int j = lane; j < k; j += 32) {
+            const float lkj = M[k * ms + j];
+            yu[j] -= lkj * b_u;
+            yv[j] -= lkj * b_v;
+        }
+    }
+    __syncwarp();
+    bu = su;
+    bv = sv;
+}
+
 // One CI test for node ids nd[0..m) (S..., u, v) by the calling warp.
 // Returns independent; writes r and z (of the path that decided).
 template <bool F64>
@@ -655,19 +725,24 @@ __device__ __forceinline__ bool warp_test(const int *nd, int m, int l, const flo
             need64 = true;
             ++acc.guard;
         } else {
-            // error model of the FP32 evaluation: dr ~ (m eps32 + eps_C) / pmin
-            const float dr = 2.0f * ((float)m * 5.96e-8f + tp.eps_c) / pmin;
-            const float omr = fmaxf(1.0f - rf * rf, 1e-3f);
-            zf = fabsf(rf) < 1.0f ? sqf * fabsf(atanhf(rf)) : INFINITY;
-            const float dz = sqf * dr / omr;
-            if (dr > tp.dr_max) {
+            const float h11 = M[l * ms + l], h22 = M[(l + 1) * ms + l + 1];
+            float bu, bv, dr;
+            warp_beta_l1(M, ms, l, bu, bv);
+            const float ih = rsqrtf(h11 * h22);
+            const float a = fabsf(rf);
+            const float rq = tanhf(tp.qf / sqf);
+            // kap is not formed here (it would need corr_SS^{-1}); the pivot guard
+            // and the two first-order ratios bound the expansion instead
+            const int t = fp32_trust(tp, m, sqf, rq, a, h11, h22, ih, 1.0f + bu, 1.0f + bv, 0.0f, dr);
+            zf = a < 1.0f ? sqf * atanhf(a) : INFINITY;
+            if (t == 2) {
                 need64 = true;
                 ++acc.guard;
-            } else if (fabsf(zf - tp.qf) < (float)tp.band + 4.0f * dz) {
+            } else if (t == 1) {
                 need64 = true;
                 ++acc.band;
             } else {
-                indep = zf <= tp.qf;
+                indep = a <= rq;
                 f32ok = true;
             }
         }
@@ -820,40 +895,42 @@ __global__ void __launch_bounds__(256) ci_direct_kernel(GraphDev g, TestParams t
 // (h11, h12, h22) and the smallest pivot: true = independent (the caller
 // records the key and stops); a test the FP32 error model cannot trust goes
 // to the FP64 queue.
+// x: pivot of the border member given the prefix (1 without a prefix), bsu/bsv:
+// |its regression coefficients| c_u/x, c_v/x; gs bounds the l1 norm of the
+// regression coefficients of the border member on the prefix, so that
+// A_u = A0u + bsu (1 + gs), A0u = 1 + |b_u(P)|_1, bounds 1 + |b_u(S)|_1 (and
+// likewise for v).  With F = |Lp^{-1}|_F^2 >= |corr_PP^{-1}|_2, (F + 1)/x
+// bounds |corr_SS^{-1}|_2; kapP = m eps (F + 1).
 template <int L>
 __device__ __forceinline__ bool lane_decide(const TestParams &tp, float sqf, float rq, float h11, float h12,
-                                            float h22, float pmin, bool bad, ull flat, ull *queue, ull qcap,
-                                            ull *qlen, WarpAcc &acc)
+                                            float h22, float pmin, bool bad, float x, float bsu, float bsv,
+                                            float gs, float kapP, float A0u, float A0v, ull flat, ull *queue,
+                                            ull qcap, ull *qlen, LaneAcc &acc)
 {
     constexpr int M = L + 2;
     pmin = fminf(pmin, fminf(h11, h22));
     bad |= !(h11 > 1e-12f) || !(h22 > 1e-12f);
     ++acc.tests;
-    acc.fl32 += flops_direct(L);
     bool queue_it = false, ind = false;
-    // FP32 error bound of r: dr = e / pmin
-    const float e = 2.0f * ((float)M * 5.96e-8f + tp.eps_c);
-    if (bad || pmin < (float)tp.guard || e > tp.dr_max * pmin) {
+    if (bad || pmin < (float)tp.guard) {
         queue_it = true;
         ++acc.guard;
     } else {
-        const float a = fabsf(h12 * rsqrtf(h11 * h22));
-        if (a < 1.0f) {
-            // z <= q  <=>  |r| <= rq = tanh(q / sqrt(n-l-3)).  The test is trusted in
-            // FP32 when |z - q| >= band + 4 dz, dz = sqf dr / D, D = max(1 - r^2, 1e-3);
-            // by the mean-value theorem |z - q| >= sqf |a - rq| / (1 - min(a, rq)^2),
-            // so a sufficient condition, multiplied through by pmin D > 0, is below.
-            const float D = fmaxf(1.0f - a * a, 1e-3f);
-            const float mn = fminf(a, rq), w = 1.0f - mn * mn;
-            const float lhs = sqf * fabsf(a - rq) * D * pmin;
-            const float rhs = (float)tp.band * D * w * pmin + 4.0f * sqf * e * w;
-            if (lhs < rhs) {
-                queue_it = true;
-                ++acc.band;
-            } else {
-                ind = a <= rq;
-            }
-        }                                               // |r| >= 1: z infinite, dependent
+        const float ih = rsqrtf(h11 * h22);
+        const float a = fabsf(h12 * ih);
+        const float Au = fmaf(bsu, 1.0f + gs, A0u), Av = fmaf(bsv, 1.0f + gs, A0v);
+        const float kap = kapP * __frcp_rn(x);
+        float dr;
+        const int t = fp32_trust(tp, M, sqf, rq, a, h11, h22, ih, Au, Av, kap, dr);
+        if (t == 2) {
+            queue_it = true;
+            ++acc.guard;
+        } else if (t == 1) {
+            queue_it = true;
+            ++acc.band;
+        } else {
+            ind = a <= rq;                              // |r| >= 1: z infinite, dependent
+        }
     }
     if (queue_it) {
         const ull slot = atomicAdd(qlen, 1ull);
@@ -887,7 +964,7 @@ __device__ __forceinline__ int lex_next(int *pos, int d)
 template <int L, bool PROP>
 __device__ __forceinline__ void lane_tests_lex(const GraphDev &g, const TestParams &tp, const float *C32, int ldc,
                                                int u, int j, int d, ull T, ull rank, ull rank_end, ull *queue,
-                                               ull qcap, ull *qlen, WarpAcc &acc)
+                                               ull qcap, ull *qlen, LaneAcc &acc)
 {
     constexpr int K = L > 0 ? L - 1 : 0;                 // prefix length
     constexpr int KA = K > 0 ? K : 1;
@@ -909,6 +986,10 @@ __device__ __forceinline__ void lane_tests_lex(const GraphDev &g, const TestPara
     int sp[KA];
     float Lp[KA * (KA + 1) / 2], rd[KA], lu[KA], lv[KA];
     float huu = 1.f, hvv = 1.f, huv = cuv, ppmin = 1e30f;
+    // prefix terms of the trust rule: 1 + |b_u(P)|_1, 1 + |b_v(P)|_1, sqrt(K |Lp^{-1}|_F^2)
+    // and m eps (|Lp^{-1}|_F^2 + 1)
+    const float kap_c = (float)(L + 2) * (tp.eps_c + (4.0f * (float)(L + 2)) * EPS32);
+    float A0u = 1.f, A0v = 1.f, sKF = 0.f, kapP = kap_c;
     bool pbad = false, fresh = true;
     int since = 0;
     for (; rank < rank_end; ++rank) {
@@ -959,9 +1040,49 @@ __device__ __forceinline__ void lane_tests_lex(const GraphDev &g, const TestPara
                 hvv -= lv[i] * lv[i];
                 huv -= lu[i] * lv[i];
             }
+            // for the trust rule: F = |Lp^{-1}|_F^2 (columns of Lp^{-1} by forward
+            // substitution) and the l1 norms of the prefix regression coefficients
+            // b_u(P) = Lp^{-T} lu, b_v(P) = Lp^{-T} lv (back substitution)
+            float Fp = 0.f;
+#pragma unroll
+            for (int c = 0; c < K; ++c) {
+                float zc[KA];
+                zc[c] = rd[c];
+                Fp = fmaf(zc[c], zc[c], Fp);
+#pragma unroll
+                for (int k2 = c + 1; k2 < K; ++k2) {
+                    float t = 0.f;
+#pragma unroll
+                    for (int j2 = c; j2 < k2; ++j2) t = fmaf(Lp[k2 * (k2 + 1) / 2 + j2], zc[j2], t);
+                    zc[k2] = -t * rd[k2];
+                    Fp = fmaf(zc[k2], zc[k2], Fp);
+                }
+            }
+            sKF = sqrtf((float)K * Fp);
+            float BuP = 0.f, BvP = 0.f;
+            {
+                float bu_[KA], bv_[KA];
+#pragma unroll
+                for (int k2 = K - 1; k2 >= 0; --k2) {
+                    float tu = lu[k2], tv = lv[k2];
+#pragma unroll
+                    for (int j2 = k2 + 1; j2 < K; ++j2) {
+                        tu -= Lp[j2 * (j2 + 1) / 2 + k2] * bu_[j2];
+                        tv -= Lp[j2 * (j2 + 1) / 2 + k2] * bv_[j2];
+                    }
+                    bu_[k2] = tu * rd[k2];
+                    bv_[k2] = tv * rd[k2];
+                    BuP += fabsf(bu_[k2]);
+                    BvP += fabsf(bv_[k2]);
+                }
+            }
+            A0u = 1.0f + BuP;
+            A0v = 1.0f + BvP;
+            kapP = kap_c * (Fp + 1.0f);
             fresh = false;
         }
         float h11 = huu, h22 = hvv, h12 = huv, pmin = ppmin;
+        float xs = 1.f, bsu = 0.f, bsv = 0.f, gs = 0.f;
         bool bad = pbad;
         if (L > 0) {
             const int s = member(pos[L - 1]);
@@ -989,8 +1110,13 @@ __device__ __forceinline__ void lane_tests_lex(const GraphDev &g, const TestPara
             h11 -= cu * cu * rx;
             h22 -= cv * cv * rx;
             h12 -= cu * cv * rx;
+            xs = fmaxf(x, 1e-30f);
+            bsu = fabsf(cu * rx);
+            bsv = fabsf(cv * rx);
+            gs = K > 0 ? sKF * sqrtf(fmaxf(1.0f - x, 0.0f)) : 0.f;
         }
-        if (lane_decide<L>(tp, sqf, rq, h11, h12, h22, pmin, bad, tbase + rank, queue, qcap, qlen, acc)) {
+        if (lane_decide<L>(tp, sqf, rq, h11, h12, h22, pmin, bad, xs, bsu, bsv, gs, kapP, A0u, A0v, tbase + rank,
+                           queue, qcap, qlen, acc)) {
             atomicMin(bp, key);
             return;
         }
@@ -1003,7 +1129,7 @@ __device__ __forceinline__ void lane_tests_lex(const GraphDev &g, const TestPara
 template <int L, bool PROP>
 __device__ __forceinline__ void lane_chunk(const GraphDev &g, const TestParams &tp, const float *C32, int ldc,
                                            int u, int j, int d, ull T, ull rank, ull rank_end, ull *queue,
-                                           ull qcap, ull *qlen, WarpAcc &acc)
+                                           ull qcap, ull *qlen, LaneAcc &acc)
 {
     lane_tests_lex<L, PROP>(g, tp, C32, ldc, u, j, d, T, rank, rank_end, queue, qcap, qlen, acc);
 }
@@ -1016,7 +1142,7 @@ template <int L, bool PROP>
 __device__ __forceinline__ void lane_dispatch(const GraphDev &g, const TestParams &tp, const float *C32, int ldc,
                                               ull *queue, ull qcap, ull *qlen)
 {
-    WarpAcc acc = {0, 0, 0, 0, 0, 0, 0, 0.f};
+    LaneAcc acc = {0u, 0u, 0u};
     const int p = g.p;
     const long long NP = g.info->n_opairs;
     const int rounds = g.info->lane_rounds;
@@ -1064,13 +1190,16 @@ __device__ __forceinline__ void lane_dispatch(const GraphDev &g, const TestParam
             t += take;
         }
     }
+    ull tests = acc.tests, band = acc.band, guard = acc.guard;
     for (int off = 16; off > 0; off >>= 1) {
-        acc.tests += __shfl_xor_sync(0xffffffffu, acc.tests, off);
-        acc.band += __shfl_xor_sync(0xffffffffu, acc.band, off);
-        acc.guard += __shfl_xor_sync(0xffffffffu, acc.guard, off);
-        acc.fl32 += __shfl_xor_sync(0xffffffffu, acc.fl32, off);
+        tests += __shfl_xor_sync(0xffffffffu, tests, off);
+        band += __shfl_xor_sync(0xffffffffu, band, off);
+        guard += __shfl_xor_sync(0xffffffffu, guard, off);
     }
-    if ((threadIdx.x & 31) == 0) flush_acc(acc, g.ctr);
+    if ((threadIdx.x & 31) == 0) {
+        WarpAcc w = {tests, 0, band, guard, 0, tests * flops_direct(L), 0, 0.f};
+        flush_acc(w, g.ctr);
+    }
 }
 
 template <int L, int HI, bool PROP>

@@ -20,36 +20,55 @@ from . import fastpc as fp
 
 
 def training_rows(adj_final: np.ndarray, sepsets: dict, reversed_order: bool):
-    """(quads int32 (R, 4), labels float32 (R,)) for the removed pairs of one run."""
+    """(quads int32 (R, 4), labels float32 (R,)) for the removed pairs of one run.
+    Rows are grouped by stage (ascending), then by pair in the order of
+    ``sepsets``, each pair's candidates ascending."""
     p = adj_final.shape[0]
     by_level: dict[int, list] = {}
     for (a, b), (lv, side, rank, nodes) in sepsets.items():
         by_level.setdefault(lv, []).append((a, b, side, nodes))
+    base = adj_final.astype(bool)
     quads, labels = [], []
-    for l, items in by_level.items():
+    for l in sorted(by_level):
         if l < 1 or l >= p - 2:
             continue
-        frozen = adj_final.astype(bool).copy()
+        items = by_level[l]
+        # the frozen graph of stage l: pairs removed at this stage or later
+        # (Algorithm 1), at this stage or earlier (Algorithm 2), were adjacent
+        frozen = base.copy()
         for lv2, items2 in by_level.items():
             if (lv2 <= l) if reversed_order else (lv2 >= l):
-                for a, b, _, _ in items2:
-                    frozen[a, b] = frozen[b, a] = True
-        for a, b, side, nodes in items:
-            u, v = (a, b) if side == 0 else (b, a)
-            cand = [int(k) for k in np.nonzero(frozen[u])[0] if k != v]
-            d = len(cand)
-            S = set(nodes)
-            for k in cand:
-                quads.append((u, v, k, l | (d << 16)))
-                labels.append(1.0 if k in S else 0.0)
+                ab = np.array([(a, b) for a, b, _, _ in items2], dtype=np.int64)
+                frozen[ab[:, 0], ab[:, 1]] = True
+                frozen[ab[:, 1], ab[:, 0]] = True
+        k = len(items)
+        u = np.array([a if side == 0 else b for a, b, side, _ in items], dtype=np.int64)
+        v = np.array([b if side == 0 else a for a, b, side, _ in items], dtype=np.int64)
+        cand = frozen[u].copy()                  # (k, p): adj(u)
+        cand[np.arange(k), v] = False            # \ {v}
+        member = np.zeros((k, p), dtype=bool)
+        for i, (_, _, _, nodes) in enumerate(items):
+            member[i, list(nodes)] = True
+        d = cand.sum(axis=1)
+        pi, kk = np.nonzero(cand)
+        q = np.empty((pi.size, 4), dtype=np.int32)
+        q[:, 0] = u[pi]
+        q[:, 1] = v[pi]
+        q[:, 2] = kk
+        q[:, 3] = l | (d[pi] << 16)
+        quads.append(q)
+        labels.append(member[pi, kk].astype(np.float32))
     if not quads:
         return np.zeros((0, 4), np.int32), np.zeros(0, np.float32)
-    return np.asarray(quads, dtype=np.int32), np.asarray(labels, dtype=np.float32)
+    return np.concatenate(quads), np.concatenate(labels)
 
 
-def collect(make_X, seeds, alpha: float, order: int, max_level: int = -1, precision: int = 2):
+def collect(make_X, seeds, alpha: float, order: int, max_level: int = -1, precision: int = 2,
+            max_rows_per_seed: int | None = None):
     """Runs the plain search on each seeded input and returns the feature rows
-    (torch CUDA tensors, concatenated) and labels.  make_X(seed) -> X (n x p)."""
+    (torch CUDA tensors, concatenated) and labels.  make_X(seed) -> X (n x p).
+    max_rows_per_seed: keep at most this many rows of each run, drawn without
+    replacement by a generator seeded with the run's seed (None: all rows)."""
     import torch
     feats, labs = [], []
     for sd in seeds:
@@ -61,7 +80,11 @@ def collect(make_X, seeds, alpha: float, order: int, max_level: int = -1, precis
             q, y = training_rows(adj, pc.sepsets(), bool(order))
             if len(y) == 0:
                 continue
-            feats.append(fp.pc_mlp_features(pc.h, torch.from_numpy(q).cuda()))
+            if max_rows_per_seed is not None and len(y) > max_rows_per_seed:
+                keep = np.sort(np.random.Generator(np.random.PCG64(sd)).choice(len(y), max_rows_per_seed,
+                                                                               replace=False))
+                q, y = q[keep], y[keep]
+            feats.append(fp.pc_mlp_features(pc.h, torch.from_numpy(np.ascontiguousarray(q)).cuda()))
             labs.append(torch.from_numpy(y).cuda())
     return torch.cat(feats), torch.cat(labs)
 

@@ -36,3 +36,23 @@ def test_pack_unpack_roundtrip():
     theta = mlp.init(9)
     assert theta.size == mlp.NPARAM == 18817
     np.testing.assert_array_equal(mlp.pack(mlp.unpack(theta)), theta)
+
+
+def test_stored_h1_gradient_matches_finite_differences():
+    # with a storage map of derivative one (here a fixed offset added to h1), the
+    # chain rule through the stored h1 is the exact gradient of the loss
+    rng = np.random.default_rng(6)
+    theta = mlp.init(4) * 0.5
+    X = rng.standard_normal((30, mlp.NF))
+    y = (rng.random(30) < 0.4).astype(float)
+    off = 1e-3 * rng.standard_normal((30, mlp.NH))
+    store = lambda h: h + off                                     # noqa: E731
+    g = mlp.grad(theta, X, y, h1_store=store)
+    assert np.abs(g - mlp.grad(theta, X, y)).max() > 0            # the map is applied
+    h = 1e-6
+    for i in np.concatenate([rng.choice(mlp.NPARAM, size=40, replace=False), [0, 2048, mlp.NPARAM - 1]]):
+        tp, tm = theta.copy(), theta.copy()
+        tp[i] += h
+        tm[i] -= h
+        fd = (mlp.loss(tp, X, y, h1_store=store) - mlp.loss(tm, X, y, h1_store=store)) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 + 1e-5 * abs(fd), (i, fd, g[i])
