@@ -166,18 +166,24 @@ pc_status pc_skeleton_many(pc_handle **hs, int32_t count, uint8_t **adj_out, pc_
 /* pc_autotune -- chooses the launch shape of the test kernels for this
  * handle's problem (the data given to the last pc_corr): a coordinate search
  * over lane_chunk {4,8,16,32}, lane_rounds {4,16,64,256}, lane_blocks {4,8,16}
- * and direct_warps {2,4,8}, each candidate timed as the mean of `reps` (1..100)
- * complete skeleton searches (CUDA events on the handle's stream) after one
- * warm run.  The handle keeps the fastest shape; out (host, may be NULL)
- * receives it with the times.  The shape changes no result, so the handle
- * holds a valid skeleton afterwards (as after pc_skeleton).  Requires a prior
- * pc_corr.  Not in the paper: a launch-shape search for this GPU.  Errors of
- * any run are returned as pc_skeleton returns them. */
+ * and direct_warps {2,4,8} -- and, for a handle that enumerates in the
+ * proposal order ("learned" 1 with parameters), learned_max_level
+ * {0 (no stage scored), 2, 4, 8}: the cost gate that keeps the scoring off
+ * the stages where it costs more than the tests it saves -- each candidate
+ * timed as the mean of `reps` (1..100) complete skeleton searches (CUDA events
+ * on the handle's stream) after one warm run.  The handle keeps the fastest
+ * shape; out (host, may be NULL) receives it with the times.  The shape
+ * changes no skeleton (the proposal order changes only which separating set
+ * is found first), so the handle holds a valid skeleton afterwards (as after
+ * pc_skeleton).  Requires a prior pc_corr.  Not in the paper: a launch-shape
+ * search for this GPU.  Errors of any run are returned as pc_skeleton returns
+ * them. */
 typedef struct {
     int32_t lane_chunk, lane_rounds, lane_blocks, direct_warps;
     double ms_default;  /* mean skeleton time with the shape before the search */
     double ms_best;     /* mean skeleton time with the chosen shape             */
     int32_t runs;       /* skeleton searches executed                           */
+    int32_t learned_max_level;   /* the chosen option (searched only for a proposal-order handle) */
 } pc_tune_result;
 pc_status pc_autotune(pc_handle *h, int32_t reps, pc_tune_result *out);
 

@@ -1363,12 +1363,17 @@ extern "C" pc_status pc_autotune(pc_handle *h, int32_t reps, pc_tune_result *out
     static const int rounds[] = {4, 16, 64, 256};
     static const int blocks[] = {4, 8, 16};
     static const int warps[] = {2, 4, 8};
+    // the cost gate of the proposal order: the largest scored stage (0: none,
+    // stage 0 has no sets to order), searched only when the handle enumerates in
+    // the proposed order
+    static const int lmaxs[] = {0, 2, 4, 8};
     struct Knob {
         int *field;
         const int *cand;
         int nc;
     } knobs[] = {{&h->lane_chunk, chunks, 4}, {&h->lane_rounds, rounds, 4}, {&h->lane_blocks, blocks, 3},
-                 {&h->direct_warps, warps, 3}};
+                 {&h->direct_warps, warps, 3}, {&h->learned_lmax, lmaxs, 4}};
+    const int nknobs = (h->learned && h->have_params) ? 5 : 4;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -1395,7 +1400,7 @@ extern "C" pc_status pc_autotune(pc_handle *h, int32_t reps, pc_tune_result *out
     double best = 0.0;
     rs = measure(&best);
     const double first = best;
-    for (int k = 0; k < 4 && rs == PC_OK; ++k) {
+    for (int k = 0; k < nknobs && rs == PC_OK; ++k) {
         const int keep = *knobs[k].field;
         int pick = keep;
         for (int c = 0; c < knobs[k].nc && rs == PC_OK; ++c) {
@@ -1419,6 +1424,7 @@ extern "C" pc_status pc_autotune(pc_handle *h, int32_t reps, pc_tune_result *out
         out->lane_rounds = h->lane_rounds;
         out->lane_blocks = h->lane_blocks;
         out->direct_warps = h->direct_warps;
+        out->learned_max_level = h->learned_lmax;
         out->ms_default = first;
         out->ms_best = best;
         out->runs = runs;

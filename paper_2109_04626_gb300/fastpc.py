@@ -247,7 +247,8 @@ def pc_skeleton_many(handles, ps, adj_out=True):
 class pc_tune_result(ctypes.Structure):
     _fields_ = [("lane_chunk", ctypes.c_int32), ("lane_rounds", ctypes.c_int32),
                 ("lane_blocks", ctypes.c_int32), ("direct_warps", ctypes.c_int32),
-                ("ms_default", ctypes.c_double), ("ms_best", ctypes.c_double), ("runs", ctypes.c_int32)]
+                ("ms_default", ctypes.c_double), ("ms_best", ctypes.c_double), ("runs", ctypes.c_int32),
+                ("learned_max_level", ctypes.c_int32)]
 
 
 def pc_autotune(h, reps: int = 3) -> dict:
