@@ -1215,7 +1215,7 @@ __device__ __forceinline__ void lane_switch(int l, const GraphDev &g, const Test
 // Stages LO <= l <= HI (one instantiation per range keeps the register count of
 // small l low: the launch sequence runs every range, all but one return at once).
 template <int LO, int HI, bool PROP>
-__global__ void __launch_bounds__(256, HI <= 2 ? 4 : (HI <= 4 ? 3 : (HI <= 8 ? 2 : 1)))
+__global__ void __launch_bounds__(256, HI <= 2 ? 3 : (HI <= 4 ? 2 : (HI <= 8 ? 2 : 1)))
     ci_lane_kernel(GraphDev g, TestParams tp, const float *C32, int ldc,
                                                       ull *queue, ull qcap, ull *qlen)
 {
