@@ -51,6 +51,7 @@ struct pc_handle {
     long long n_min = 0;
     // launch shape of the test kernels (pc_autotune)
     int lane_chunk = 8, lane_rounds = 32, lane_blocks = 8, direct_warps = 8;
+    int node_dmax = fpc::NODE_DMAX;   // staged small-stage kernel: largest node degree (0: off)
     int stage_conds = 1;                 // conditional nodes in the captured stage body
     int lane_stages = 1;                 // small stages on the rank-major small-stage kernel
     cudaStream_t stream = 0;
@@ -247,6 +248,7 @@ static TestParams make_tp(const pc_handle *h)
     tp.lane_chunk = h->lane_chunk;
     tp.lane_rounds = h->lane_rounds;
     tp.lane_blocks = h->lane_blocks;
+    tp.node_dmax = h->node_dmax;
     tp.direct_warps = h->direct_warps;
     tp.lane_stages = h->lane_stages;
     tp.precision = h->precision;
@@ -302,6 +304,7 @@ static pc_status create_impl(int64_t n, int32_t p, double alpha, int32_t max_lev
     A(dalloc(h, &g.tn_off, (size_t)(p + 2) * sizeof(ull)));
     A(dalloc(h, &g.cn_off, (size_t)(p + 2) * sizeof(ull)));
     A(dalloc(h, &g.rn_off, (size_t)(p + 2) * sizeof(ull)));
+    A(dalloc(h, &g.it_off, (size_t)(p + 2) * sizeof(ull)));
     A(dalloc(h, &g.best, pp * sizeof(ull)));
     A(dalloc(h, &h->binom, (size_t)(pmax + 1) * (pmax + 1) * sizeof(ull)));
     A(dalloc(h, &g.sep_level, pp * sizeof(int)));
@@ -549,6 +552,10 @@ extern "C" pc_status pc_set_opt(pc_handle *h, const char *key, double val)
     } else if (k == "lane_blocks") {
         if (!(val >= 1 && val <= 32)) return fail(h, PC_ERR_ARG, "lane_blocks must be in [1, 32]");
         h->lane_blocks = (int)val;
+    } else if (k == "node_dmax") {
+        if (!(val >= 0 && val <= fpc::NODE_DMAX))
+            return fail(h, PC_ERR_ARG, "node_dmax must be in [0, " + std::to_string(fpc::NODE_DMAX) + "]");
+        h->node_dmax = (int)val;
     } else if (k == "direct_warps") {
         if (val != 1 && val != 2 && val != 4 && val != 8) return fail(h, PC_ERR_ARG, "direct_warps must be 1, 2, 4 or 8");
         h->direct_warps = (int)val;
@@ -579,6 +586,7 @@ extern "C" pc_status pc_get_opt(pc_handle *h, const char *key, double *val)
     else if (k == "lane_chunk") *val = h->lane_chunk;
     else if (k == "lane_rounds") *val = h->lane_rounds;
     else if (k == "lane_blocks") *val = h->lane_blocks;
+    else if (k == "node_dmax") *val = h->node_dmax;
     else if (k == "direct_warps") *val = h->direct_warps;
     else if (k == "tensor_core_gemm") *val = h->used_tc ? 1.0 : 0.0;
     else return fail(h, PC_ERR_ARG, "unknown option: " + k);
@@ -1057,6 +1065,7 @@ static std::vector<double> graph_key(const pc_handle *h)
             h->budget, (double)level_cap(h), (double)(uintptr_t)h->g.pool, (double)h->g.pool_cap,
             (double)(uintptr_t)h->C32, (double)(uintptr_t)h->C64, (double)h->lane_chunk,
             (double)h->lane_rounds, (double)h->lane_blocks, (double)h->direct_warps, (double)h->stage_conds,
+            (double)h->node_dmax, (double)h->learned_lmax,
             (double)h->lane_stages};
 }
 

@@ -61,6 +61,7 @@ struct LevelInfo {
     int lane_overflow;                  // the FP64 re-decision queue overflowed this stage
     int kernels_run;                    // kernels the captured stage loop executed
     unsigned deg_ticket;                // CTAs of the stage's degrees kernel done (last one runs the tail)
+    unsigned long long node_next;       // next work item of the staged small-stage kernel
 };
 
 // Conditional nodes of the captured stage body: the head kernel picks one branch
@@ -72,6 +73,12 @@ struct StageConds {
     int has_comp, has_score, has_prec;  // which kernels the body has
 };
 constexpr int LANE_LMAX = 12;           // stages the lane-per-test kernel runs (FP32 modes)
+// Staged small-stage kernel: a node whose frozen degree is at most NODE_DMAX has
+// the block corr[adj(u), adj(u)] staged in shared memory by the CTA that runs
+// its pairs; larger neighbourhoods stay on the kernel that reads corr from L2.
+constexpr int NODE_DMAX = 128;
+constexpr int NODE_THREADS = 256;
+constexpr unsigned long long NODE_ITEM_TESTS = 16384;   // tests per work item (a slice of a node's pairs)
 constexpr int LANE_RANGES = 6;          // small-stage kernel instantiations: l 0-2, 3-4, 5-6, 7-8, 9-10, 11-12
 
 // Branches of the stage's switch node.  kind: 0 .. LANE_RANGES-1 a small-stage
@@ -113,6 +120,7 @@ struct GraphDev {
     unsigned long long *tn_off; // p+1: first direct test of each node (exclusive scan)
     unsigned long long *cn_off; // p+1: first complement test of each node
     unsigned long long *rn_off; // p+1: first remainder test of each node (small-stage kernel)
+    unsigned long long *it_off; // p+1: first work item of each node on the staged small-stage kernel
     unsigned long long *best;   // p x p, best (side<<62 | rank) per unordered pair (a<b at a*p+b)
     const unsigned long long *binom;   // ldb x ldb saturating binomials
     int ldb;                    // p+1 (batched problems: largest instance p + 1)
@@ -139,8 +147,8 @@ struct GraphDev {
     short *prec_pos;            // p x p: slot of node w in block u, -1 = absent/dead
     int *prec_need;             // p: build request flags
     // learned proposal (optional): per node, the first score row of its
-    // candidates (pair j, position x) and, per row, the candidate node at each
-    // place of the proposal order
+    // candidates (pair j, position x) and, per row, the candidate at each place
+    // of the proposal order as its index into nbr[u]
     unsigned long long *row_off;   // p+1 (nullptr: plain lexicographic order)
     const short *perm;
     long long rows_cap;
@@ -166,6 +174,8 @@ struct TestParams {
     int direct_warps;   // at most this many warps per CTA of the warp-per-test kernel
     int lane_stages;    // 1: stages l <= LANE_LMAX on the small-stage kernel (FP32 modes);
                         // 0: every stage on the warp-per-test kernel
+    int node_dmax;      // stages 1 <= l <= LANE_LMAX: nodes of degree <= node_dmax run on the
+                        // staged kernel (corr block in shared memory); 0: none
     int precision;      // 0 fp64, 1/2 fp32 tests with FP64 re-decision
     int reversed;
     int complement;

@@ -153,6 +153,13 @@ __global__ void __launch_bounds__(256) degrees_tail_kernel(GraphDev g, TestParam
     tail_body(g, tp, cap, 0, nullptr, 0, hc, use_cond, sc, true);
 }
 
+// The small-stage tests of a node of degree dg at stage l >= 1 run on the staged
+// kernel when its neighbourhood block fits the shared-memory layout.
+__device__ __forceinline__ bool node_staged(const TestParams &tp, int l, int dg)
+{
+    return l >= 1 && dg <= tp.node_dmax;
+}
+
 __device__ __forceinline__ bool comp_eligible(int d, int l, const TestParams &tp)
 {
     const int k = d - l;
@@ -384,7 +391,15 @@ __global__ void __launch_bounds__(1024) head_kernel(GraphDev g, TestParams tp, d
     auto prows = [&](int dg, ull T) -> ull {
         return (g.row_off && l >= 1 && l <= tp.learned_lmax && T >= 2) ? (ull)dg * (ull)(dg - 1) : 0ull;
     };
-    ull v[3] = {0ull, 0ull, 0ull}, mxT = 0;               // direct, complement, proposal rows
+    const bool small = tp.lane_stages && tp.precision != 0 && l <= LANE_LMAX;
+    // staged kernel work items of a node: slices of its pairs of about
+    // NODE_ITEM_TESTS tests each (at least one pair per slice)
+    auto items = [&](int dg, ull T) -> ull {
+        if (!small || !T || !node_staged(tp, l, dg)) return 0ull;
+        const ull w = sat_mul(T, (ull)dg), k = (w + NODE_ITEM_TESTS - 1) / NODE_ITEM_TESTS;
+        return k < (ull)dg ? k : (ull)dg;
+    };
+    ull v[4] = {0ull, 0ull, 0ull, 0ull}, mxT = 0;        // direct, complement, proposal rows, staged items
     bool sat = false;
     for (int u = s0; u < s1; ++u) {
         const int dg = g.deg[u], d = dg - 1;
@@ -397,13 +412,14 @@ __global__ void __launch_bounds__(1024) head_kernel(GraphDev g, TestParams tp, d
         if (comp) v[1] = sat_add(v[1], tot);
         else {
             v[0] = sat_add(v[0], tot);
-            mxT = T > mxT ? T : mxT;
+            if (!items(dg, T)) mxT = T > mxT ? T : mxT;   // the lane kernel's pairs only
             v[2] = sat_add(v[2], prows(dg, T));           // complement-path pairs keep the plain order
+            v[3] += items(dg, T);
         }
     }
     const int ssat = __syncthreads_or(sat);
-    ull ex[3], tot[3];
-    block_scan_sat<3>(v, ex, tot, sh);
+    ull ex[4], tot[4];
+    block_scan_sat<4>(v, ex, tot, sh);
     // else: plain order this stage (too many rows, or too few tests for the order to matter)
     // score rows are one per candidate; the order pays off only when a pair has
     // many more sets than candidates (l >= 2 and large neighbourhoods)
@@ -413,17 +429,19 @@ __global__ void __launch_bounds__(1024) head_kernel(GraphDev g, TestParams tp, d
     const ull rows_total = tot[2];
     if (t == 0 && g.scored) g.scored[l] = rows_fit && rows_total > 0;
     {
-        ull rd = ex[0], rc = ex[1], rr = ex[2];
+        ull rd = ex[0], rc = ex[1], rr = ex[2], ri = ex[3];
         for (int u = s0; u < s1; ++u) {
             const int dg = g.deg[u];
             const ull T = Tn[u - s0], tt = sat_mul(T, (ull)dg);
             g.tn_off[u] = rd;
             g.cn_off[u] = rc;
+            g.it_off[u] = ri;
             if (g.row_off) g.row_off[u] = rows_fit ? rr : 0ull;
             if (cm[u - s0]) rc = sat_add(rc, tt);
             else {
                 rd = sat_add(rd, tt);
                 rr = sat_add(rr, prows(dg, T));
+                ri += items(dg, T);
             }
         }
     }
@@ -432,7 +450,6 @@ __global__ void __launch_bounds__(1024) head_kernel(GraphDev g, TestParams tp, d
         const long long b = g.ooff[u];
         for (int jj = 0, dg = g.deg[u]; jj < dg; ++jj) g.opu[b + jj] = u;
     }
-    const bool small = tp.lane_stages && tp.precision != 0 && l <= LANE_LMAX;
     int rounds = 0;
     if (small && tot[0] > 0) {
         // rank-major rounds of the lane kernel: at most tp.lane_rounds chunks of
@@ -452,7 +469,7 @@ __global__ void __launch_bounds__(1024) head_kernel(GraphDev g, TestParams tp, d
         ull v2[1] = {0ull};
         for (int u = s0; u < s1; ++u) {
             const ull T = Tn[u - s0];
-            if (!cm[u - s0] && T > skip) v2[0] = sat_add(v2[0], sat_mul(T - skip, (ull)g.deg[u]));
+            if (!cm[u - s0] && T > skip && !items(g.deg[u], T)) v2[0] = sat_add(v2[0], sat_mul(T - skip, (ull)g.deg[u]));
         }
         ull ex2[1], tot2[1];
         block_scan_sat<1>(v2, ex2, tot2, sh);
@@ -460,7 +477,7 @@ __global__ void __launch_bounds__(1024) head_kernel(GraphDev g, TestParams tp, d
         for (int u = s0; u < s1; ++u) {
             const ull T = Tn[u - s0];
             g.rn_off[u] = rr2;
-            if (!cm[u - s0] && T > skip) rr2 = sat_add(rr2, sat_mul(T - skip, (ull)g.deg[u]));
+            if (!cm[u - s0] && T > skip && !items(g.deg[u], T)) rr2 = sat_add(rr2, sat_mul(T - skip, (ull)g.deg[u]));
         }
         if (t == 0) g.rn_off[p] = tot2[0];
     }
@@ -468,9 +485,11 @@ __global__ void __launch_bounds__(1024) head_kernel(GraphDev g, TestParams tp, d
     if (t == 0) {
         I->lane_rounds = rounds;
         I->lane_overflow = 0;
+        I->node_next = 0;
         const ull td = tot[0], tc = tot[1];
         g.tn_off[p] = td;
         g.cn_off[p] = tc;
+        g.it_off[p] = tot[3];
         if (g.row_off) g.row_off[p] = rows_fit ? rows_total : 0ull;
         I->total_direct = td;
         I->total_comp = tc;
@@ -487,7 +506,7 @@ __global__ void __launch_bounds__(1024) head_kernel(GraphDev g, TestParams tp, d
             set_stage_conds(conds, I, run && small && td > 0 ? lane_range_of_dev(l) : LANE_RANGES,
                             run && td > 0 && !small, run && tc > 0,
                             run && g.row_off && rows_fit && rows_total > 0,
-                            tp.lazy && tp.c64_list && tp.pair_seen ? 5 : 3);
+                            (tp.lazy && tp.c64_list && tp.pair_seen ? 5 : 3) + (tp.node_dmax > 0 ? 1 : 0));
         }
     }
 }
@@ -797,12 +816,12 @@ __device__ __forceinline__ void flush_acc(const WarpAcc &acc, DevCounters *ctr)
 // Candidate position x of the ordered pair (u, j) (d candidates) -> node id:
 // position x of adj(u)\{v} in ascending order (v sits at index j of nbr[u]), or
 // the x-th candidate of the proposal order when the stage has one (perm holds
-// the candidates' node ids in that order).
+// the candidates' indices into nbr[u] in that order).
 __device__ __forceinline__ int cand_node(const GraphDev &g, bool prop, int u, int j, int d, int x)
 {
     if (prop) {
         const ull b = g.row_off[u];
-        if (g.row_off[u + 1] > b) return g.perm[b + (ull)j * d + x];
+        if (g.row_off[u + 1] > b) return g.nbr[nidx(g, u) + g.perm[b + (ull)j * d + x]];
     }
     return g.nbr[nidx(g, u) + x + (x >= j)];
 }
@@ -939,6 +958,41 @@ __device__ __forceinline__ bool lane_decide(const TestParams &tp, float sqf, flo
     return ind;
 }
 
+// Where the small-stage tests read corr.  A member is named by its index into
+// the frozen neighbour list nbr[u]; a handle is what row() and get() take.
+//   GlobalSrc: rows of the FP32 matrix in L2 (handles are node ids);
+//   StagedSrc: the block corr[adj(u), adj(u)] and the row corr[u, adj(u)] that
+//              a CTA staged in shared memory (handles are neighbour indices).
+// corr is exactly symmetric (the GEMMs mirror one triangle), so corr(s, u) is
+// read as corr(u, s) from u's row: the same value either way.
+struct GlobalSrc {
+    const float *C;
+    const long long *prow;
+    int ldc;
+    const int *nb;
+    const float *Cu, *Cv;      // rows of u and v
+    int v;
+    __device__ __forceinline__ int handle(int idx) const { return nb[idx]; }
+    __device__ __forceinline__ const float *row(int h) const { return C + cidx(prow, ldc, h, 0); }
+    __device__ __forceinline__ float get(const float *r, int h) const { return __ldg(r + h); }
+    __device__ __forceinline__ float cu(int h) const { return __ldg(Cu + h); }
+    __device__ __forceinline__ float cv(int h) const { return __ldg(Cv + h); }
+    __device__ __forceinline__ float cuv() const { return __ldg(Cu + v); }
+};
+
+struct StagedSrc {
+    const float *B;            // deg x deg, row stride ld: corr[nbr[u][a], nbr[u][b]]
+    const float *cus;          // deg: corr[u, nbr[u][a]]
+    int ld;
+    int j;                     // v = nbr[u][j]
+    __device__ __forceinline__ int handle(int idx) const { return idx; }
+    __device__ __forceinline__ const float *row(int h) const { return B + h * ld; }
+    __device__ __forceinline__ float get(const float *r, int h) const { return r[h]; }
+    __device__ __forceinline__ float cu(int h) const { return cus[h]; }
+    __device__ __forceinline__ float cv(int h) const { return B[j * ld + h]; }
+    __device__ __forceinline__ float cuv() const { return cus[j]; }
+};
+
 // lexicographic successor of pos (L of d); returns the first position that changed
 template <int L>
 __device__ __forceinline__ int lex_next(int *pos, int d)
@@ -961,26 +1015,23 @@ __device__ __forceinline__ int lex_next(int *pos, int d)
 //   x = 1 - |l_s|^2,  c_u = corr_us - lu.l_s,  c_v = corr_vs - lv.l_s,
 //   H = H_P - [c_u c_v]^T [c_u c_v] / x
 // -- the same Cholesky of the S block (Sec. 4) in bordered form, O(L^2) work.
-template <int L, bool PROP>
-__device__ __forceinline__ void lane_tests_lex(const GraphDev &g, const TestParams &tp, const float *C32, int ldc,
-                                               int u, int j, int d, ull T, ull rank, ull rank_end, ull *queue,
+template <int L, bool PROP, class Src>
+__device__ __forceinline__ void lane_tests_lex(const GraphDev &g, const TestParams &tp, const Src &src, int u,
+                                               int v, int j, int d, ull T, ull rank, ull rank_end, ull *queue,
                                                ull qcap, ull *qlen, LaneAcc &acc)
 {
     constexpr int K = L > 0 ? L - 1 : 0;                 // prefix length
     constexpr int KA = K > 0 ? K : 1;
     const float sqf = sqrtf((float)(n_of(tp, u) - L - 3));
     const float rq = tanhf(tp.qf / sqf);                 // |r| threshold of this stage
-    const int *nb = g.nbr + nidx(g, u);
-    const int v = nb[j];
-    // proposal order: position x of the enumeration is the node perm[x]
+    // proposal order: position x of the enumeration is neighbour index perm[x]
     const short *pr = nullptr;
     if (PROP && stage_prop(g, L) && g.row_off[u + 1] > g.row_off[u]) pr = g.perm + g.row_off[u] + (ull)j * d;
-    auto member = [&](int x) -> int { return (PROP && pr) ? (int)pr[x] : nb[x + (x >= j)]; };
+    auto member = [&](int x) -> int { return src.handle((PROP && pr) ? (int)pr[x] : x + (x >= j)); };
     const int side = u > v;
     ull *bp = g.best + pidx(g, min(u, v), max(u, v));
     const ull tbase = g.tn_off[u] + (ull)j * T;
-    const float *Cu = C32 + cidx(tp.prow, ldc, u, 0), *Cv = C32 + cidx(tp.prow, ldc, v, 0);
-    const float cuv = __ldg(Cu + v);
+    const float cuv = src.cuv();
     int pos[L > 0 ? L : 1];
     unrank_lex(rank, d, L, g.binom, g.ldb, pos);
     int sp[KA];
@@ -1006,11 +1057,11 @@ __device__ __forceinline__ void lane_tests_lex(const GraphDev &g, const TestPara
             for (int i = 0; i < K; ++i) sp[i] = member(pos[i]);
 #pragma unroll
             for (int i = 0; i < K; ++i) {
-                const float *Ci = C32 + cidx(tp.prow, ldc, sp[i], 0);
+                const float *Ci = src.row(sp[i]);
                 float dd = 1.f;
 #pragma unroll
                 for (int c = 0; c < i; ++c) {
-                    float t = __ldg(Ci + sp[c]);
+                    float t = src.get(Ci, sp[c]);
 #pragma unroll
                     for (int c2 = 0; c2 < c; ++c2) t -= Lp[i * (i + 1) / 2 + c2] * Lp[c * (c + 1) / 2 + c2];
                     t *= rd[c];
@@ -1022,7 +1073,7 @@ __device__ __forceinline__ void lane_tests_lex(const GraphDev &g, const TestPara
                 const float rl = rsqrtf(fmaxf(dd, 1e-30f));
                 Lp[i * (i + 1) / 2 + i] = dd * rl;
                 rd[i] = rl;
-                float tu = __ldg(Cu + sp[i]), tv = __ldg(Cv + sp[i]);
+                float tu = src.cu(sp[i]), tv = src.cv(sp[i]);
 #pragma unroll
                 for (int c = 0; c < i; ++c) {
                     tu -= lu[c] * Lp[i * (i + 1) / 2 + c];
@@ -1086,19 +1137,19 @@ __device__ __forceinline__ void lane_tests_lex(const GraphDev &g, const TestPara
         bool bad = pbad;
         if (L > 0) {
             const int s = member(pos[L - 1]);
-            const float *Cs = C32 + cidx(tp.prow, ldc, s, 0);
+            const float *Cs = src.row(s);
             float ls[KA];
             float x = 1.f;
 #pragma unroll
             for (int i = 0; i < K; ++i) {
-                float t = __ldg(Cs + sp[i]);
+                float t = src.get(Cs, sp[i]);
 #pragma unroll
                 for (int c = 0; c < i; ++c) t -= ls[c] * Lp[i * (i + 1) / 2 + c];
                 t *= rd[i];
                 ls[i] = t;
                 x -= t * t;
             }
-            float cu = __ldg(Cs + u), cv = __ldg(Cs + v);
+            float cu = src.cu(s), cv = src.cv(s);
 #pragma unroll
             for (int i = 0; i < K; ++i) {
                 cu -= lu[i] * ls[i];
@@ -1131,7 +1182,10 @@ __device__ __forceinline__ void lane_chunk(const GraphDev &g, const TestParams &
                                            int u, int j, int d, ull T, ull rank, ull rank_end, ull *queue,
                                            ull qcap, ull *qlen, LaneAcc &acc)
 {
-    lane_tests_lex<L, PROP>(g, tp, C32, ldc, u, j, d, T, rank, rank_end, queue, qcap, qlen, acc);
+    const int *nb = g.nbr + nidx(g, u);
+    const int v = nb[j];
+    const GlobalSrc src{C32, tp.prow, ldc, nb, C32 + cidx(tp.prow, ldc, u, 0), C32 + cidx(tp.prow, ldc, v, 0), v};
+    lane_tests_lex<L, PROP>(g, tp, src, u, v, j, d, T, rank, rank_end, queue, qcap, qlen, acc);
 }
 
 // Phase A, rank-major: item g = (round r, ordered pair o), r = g / NP -- a wave
@@ -1162,6 +1216,7 @@ __device__ __forceinline__ void lane_dispatch(const GraphDev &g, const TestParam
             }
             const int u = g.opu[o];                     // owner of ordered pair o
             if (g.tn_off[u + 1] == g.tn_off[u]) continue;   // not a direct node this stage
+            if (g.it_off[u + 1] != g.it_off[u]) continue;   // its pairs run on the staged kernel
             const int d = g.deg[u] - 1;
             const ull T = g.binom[(long long)d * g.ldb + L];
             const ull r0 = (ull)r * chunk;
@@ -1215,7 +1270,7 @@ __device__ __forceinline__ void lane_switch(int l, const GraphDev &g, const Test
 // Stages LO <= l <= HI (one instantiation per range keeps the register count of
 // small l low: the launch sequence runs every range, all but one return at once).
 template <int LO, int HI, bool PROP>
-__global__ void __launch_bounds__(256, HI <= 2 ? 3 : (HI <= 4 ? 2 : (HI <= 8 ? 2 : 1)))
+__global__ void __launch_bounds__(256, HI <= 2 ? 4 : (HI <= 4 ? 3 : (HI <= 8 ? 2 : 1)))
     ci_lane_kernel(GraphDev g, TestParams tp, const float *C32, int ldc,
                                                       ull *queue, ull qcap, ull *qlen)
 {
@@ -1224,6 +1279,93 @@ __global__ void __launch_bounds__(256, HI <= 2 ? 3 : (HI <= 4 ? 2 : (HI <= 8 ? 2
     const ull total = g.info->total_direct;
     if (tp.precision == 0 || l < LO || l > HI || total == 0) return;
     lane_switch<LO, HI, PROP>(l, g, tp, C32, ldc, queue, qcap, qlen);
+}
+
+// ---------------------------------------------------------------- staged small stages
+// Every ordered pair (u, v) of a node u has the same candidate count d and the
+// same C(d, l) sets, and every set it tests lies in adj(u): the block
+// corr[adj(u), adj(u)] and the row corr[u, adj(u)] hold every entry the
+// node's tests read.  A CTA takes a work item (a slice of the pairs of one
+// node, from the per-stage counter), stages that block in shared memory once,
+// and its threads run the slice's chunks rank-major (chunk r of every pair of
+// the slice before chunk r+1), each chunk by the bordered tests of
+// lane_tests_lex reading the staged block.  The arithmetic, the keys and the
+// FP64 queue are those of the lane kernel, so the results are the same.
+template <int L, bool PROP>
+__device__ __forceinline__ void node_dispatch(const GraphDev &g, const TestParams &tp, const float *C32, int ldc,
+                                              ull *queue, ull qcap, ull *qlen)
+{
+    extern __shared__ __align__(16) float node_smem[];
+    __shared__ ull item_s;
+    float *cus = node_smem;                              // NODE_DMAX floats
+    float *B = node_smem + NODE_DMAX;                    // deg x deg
+    LaneAcc acc = {0u, 0u, 0u};
+    const int p = g.p;
+    const ull nitems = g.it_off[p];
+    for (;;) {
+        __syncthreads();                                 // the last item's tests are done with the block
+        if (threadIdx.x == 0) item_s = atomicAdd(&g.info->node_next, 1ull);
+        __syncthreads();
+        const ull it = item_s;
+        if (it >= nitems) break;
+        const int u = (int)(upper_bound_dev(g.it_off, (long long)p + 1, it) - 1);
+        const int dg = g.deg[u], d = dg - 1;
+        const ull T = g.binom[(long long)d * g.ldb + L];
+        const int nsl = (int)(g.it_off[u + 1] - g.it_off[u]), sl = (int)(it - g.it_off[u]);
+        const int j0 = (int)((long long)dg * sl / nsl), j1 = (int)((long long)dg * (sl + 1) / nsl);
+        const int *nb = g.nbr + nidx(g, u);
+        for (int e = threadIdx.x; e < dg * dg; e += blockDim.x) {
+            const int a = e / dg, b = e - a * dg;
+            B[e] = C32[cidx(tp.prow, ldc, nb[a], nb[b])];
+        }
+        for (int e = threadIdx.x; e < dg; e += blockDim.x) cus[e] = C32[cidx(tp.prow, ldc, u, nb[e])];
+        __syncthreads();
+        // chunks of at most lane_chunk sets, fewer when the slice has few tests, so
+        // that every thread of the CTA has work
+        const unsigned np = (unsigned)(j1 - j0);
+        const ull fair = (ull)np * T / blockDim.x;
+        const ull chunk = fair < (ull)tp.lane_chunk ? (fair > 0 ? fair : 1ull) : (ull)tp.lane_chunk;
+        const ull total = (T + chunk - 1) / chunk * np;
+        for (ull c = threadIdx.x; c < total; c += blockDim.x) {
+            const ull r = c / np;
+            const int j = j0 + (int)(c - r * np);
+            const ull r0 = r * chunk, r1 = r0 + chunk < T ? r0 + chunk : T;
+            const StagedSrc src{B, cus, dg, j};
+            lane_tests_lex<L, PROP>(g, tp, src, u, nb[j], j, d, T, r0, r1, queue, qcap, qlen, acc);
+        }
+    }
+    ull tests = acc.tests, band = acc.band, guard = acc.guard;
+    for (int off = 16; off > 0; off >>= 1) {
+        tests += __shfl_xor_sync(0xffffffffu, tests, off);
+        band += __shfl_xor_sync(0xffffffffu, band, off);
+        guard += __shfl_xor_sync(0xffffffffu, guard, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        WarpAcc w = {tests, 0, band, guard, 0, tests * flops_direct(L), 0, 0.f};
+        flush_acc(w, g.ctr);
+    }
+}
+
+template <int L, int HI, bool PROP>
+__device__ __forceinline__ void node_switch(int l, const GraphDev &g, const TestParams &tp, const float *C32, int ldc,
+                                            ull *queue, ull qcap, ull *qlen)
+{
+    if constexpr (L <= HI) {
+        if (l == L) node_dispatch<L, PROP>(g, tp, C32, ldc, queue, qcap, qlen);
+        else node_switch<L + 1, HI, PROP>(l, g, tp, C32, ldc, queue, qcap, qlen);
+    }
+}
+
+// Stages max(LO, 1) <= l <= HI, the nodes of the staged layout (it_off); the
+// other nodes of those stages run on ci_lane_kernel.
+template <int LO, int HI, bool PROP>
+__global__ void __launch_bounds__(NODE_THREADS, HI <= 2 ? 3 : (HI <= 4 ? 3 : (HI <= 8 ? 2 : 1)))
+    ci_node_kernel(GraphDev g, TestParams tp, const float *C32, int ldc, ull *queue, ull qcap, ull *qlen)
+{
+    if (stopped(g.info)) return;
+    const int l = g.info->l;
+    if (tp.precision == 0 || l < LO || l > HI || l < 1 || g.it_off[g.p] == 0) return;
+    node_switch<(LO > 1 ? LO : 1), HI, PROP>(l, g, tp, C32, ldc, queue, qcap, qlen);
 }
 
 // FP64 pass over the queued tests of the lane kernel (one warp per test).
@@ -2132,15 +2274,49 @@ cudaError_t launch_ci_direct(GraphDev g, TestParams tp, int mmax, const float *C
     return cudaGetLastError();
 }
 
+// shared memory of the staged kernel: the row corr[u, adj(u)] and the block
+size_t node_smem_bytes(int dmax) { return (size_t)(NODE_DMAX + dmax * dmax) * sizeof(float); }
+
+// resident CTAs per SM of the staged kernel instantiation (registers and shared
+// memory), looked up once per instantiation and shared-memory size
+template <int LO, int HI, bool PROP>
+static int node_blocks_per_sm(size_t smem)
+{
+    static size_t cached_smem = 0;
+    static int cached = 0;
+    if (cached_smem != smem) {
+        int nb = 0;
+        cudaFuncSetAttribute(ci_node_kernel<LO, HI, PROP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, ci_node_kernel<LO, HI, PROP>, NODE_THREADS, smem) !=
+                cudaSuccess || nb < 1)
+            nb = 1;
+        cached = nb;
+        cached_smem = smem;
+    }
+    return cached;
+}
+
+template <int LO, int HI, bool PROP>
+static void lane_launch_p(GraphDev g, TestParams tp, const float *C32, int ldc, ull *queue, ull qcap, ull *qlen,
+                          cudaStream_t s)
+{
+    ci_lane_kernel<LO, HI, PROP><<<num_sms() * tp.lane_blocks, 256, 0, s>>>(g, tp, C32, ldc, queue, qcap, qlen);
+    note_launch();
+    if (HI >= 1 && tp.node_dmax > 0) {
+        const size_t smem = node_smem_bytes(tp.node_dmax);
+        const int per_sm = node_blocks_per_sm<LO, HI, PROP>(smem);
+        ci_node_kernel<LO, HI, PROP><<<num_sms() * per_sm, NODE_THREADS, smem, s>>>(g, tp, C32, ldc, queue, qcap,
+                                                                                   qlen);
+        note_launch();
+    }
+}
+
 template <int LO, int HI>
 static void lane_launch(GraphDev g, TestParams tp, const float *C32, int ldc, ull *queue, ull qcap, ull *qlen,
                         bool prop, cudaStream_t s)
 {
-    if (prop)
-        ci_lane_kernel<LO, HI, true><<<num_sms() * tp.lane_blocks, 256, 0, s>>>(g, tp, C32, ldc, queue, qcap, qlen);
-    else
-        ci_lane_kernel<LO, HI, false><<<num_sms() * tp.lane_blocks, 256, 0, s>>>(g, tp, C32, ldc, queue, qcap, qlen);
-    note_launch();
+    if (prop) lane_launch_p<LO, HI, true>(g, tp, C32, ldc, queue, qcap, qlen, s);
+    else lane_launch_p<LO, HI, false>(g, tp, C32, ldc, queue, qcap, qlen, s);
 }
 
 cudaError_t launch_ci_lane(GraphDev g, TestParams tp, const float *C32, const double *C64, int ldc,

@@ -397,7 +397,7 @@ __global__ void perm_kernel(GraphDev g, const unsigned long long *row_off, const
                 const float sy = scores[base + y];
                 rank += (sy > sx) || (sy == sx && y < x);
             }
-            perm[base + rank] = (short)g.nbr[nidx(g, u) + x + (x >= j)];   // node id
+            perm[base + rank] = (short)(x + (x >= j));   // index into nbr[u]
         }
     }
 }

@@ -36,10 +36,10 @@ def _sem_case(seed, p, n, prob, dtype=np.float32):
     return np.ascontiguousarray(X)
 
 
-def _run_gpu(fp, X, alpha, max_level, order, precision, complement=1, device_input=True):
+def _run_gpu(fp, X, alpha, max_level, order, precision, complement=1, device_input=True, **opts):
     n, p = X.shape
     with fp.PC(n, p, alpha, max_level, order=order, precision=precision,
-               complement=complement) as pc:
+               complement=complement, **opts) as pc:
         pc.corr(torch.from_numpy(X).cuda() if device_input else X)
         adj, st = pc.skeleton()
         seps = pc.sepsets()
@@ -47,11 +47,11 @@ def _run_gpu(fp, X, alpha, max_level, order, precision, complement=1, device_inp
 
 
 def _check_skeleton(fp, X, alpha=0.01, max_level=-1, order=1, precision=2, complement=1,
-                    device_input=True):
+                    device_input=True, **opts):
     n, p = X.shape
     C = oracle.pearson(X)
     R = oracle.skeleton(C, n, alpha, max_level, reversed_order=bool(order))
-    adj, st, seps = _run_gpu(fp, X, alpha, max_level, order, precision, complement, device_input)
+    adj, st, seps = _run_gpu(fp, X, alpha, max_level, order, precision, complement, device_input, **opts)
     np.testing.assert_array_equal(adj, R["adj"])
     assert seps == R["sepsets"]
     assert st["tests_canonical"] == R["tests_total"]
@@ -237,6 +237,42 @@ def test_skeleton_deep_stages_proposal_order(fp):
     for (a, b), (lv, side, rank, nodes) in seps.items():
         assert lv == R["sepsets"][(a, b)][0]
         assert oracle.ci_test(C, n, 0.01, a, b, list(nodes))[0]
+
+
+@pytest.mark.parametrize("node_dmax", [0, 5, 12, 128])
+@pytest.mark.parametrize("case", ["p95_conventional", "hub", "p95_reversed"])
+def test_skeleton_staged_and_global_small_stages(fp, case, node_dmax):
+    """The small stages split between the staged kernel (nodes of degree <=
+    node_dmax: corr block in shared memory) and the kernel reading corr from L2
+    (the rest); every split gives the oracle's skeleton, sets and counts."""
+    if case == "hub":
+        X, order = _hub_case(), 0
+    else:
+        X, order = sem.make(2).X, (1 if case == "p95_reversed" else 0)
+    for precision in (1, 2):
+        _check_skeleton(fp, X, order=order, precision=precision, node_dmax=node_dmax)
+
+
+def test_staged_kernel_proposal_order(fp):
+    """The staged kernel in the proposal order: the sets of a pair are enumerated
+    over its permuted candidate list (neighbour indices into the staged block)."""
+    X = _hub_case()
+    n, p = X.shape
+    C = oracle.pearson(X)
+    R = oracle.skeleton(C, n, 0.01, -1, reversed_order=False)
+    theta = np.random.default_rng(9).standard_normal(fp.pc_mlp_nparam()).astype(np.float32) * 0.2
+    for node_dmax in (0, 10, 128):
+        with fp.PC(n, p, 0.01, -1, order=0, node_dmax=node_dmax) as pc:
+            pc.corr(torch.from_numpy(X).cuda())
+            fp.pc_mlp_set_params(pc.h, theta)
+            pc.set(learned=1, learned_min_tests=0, learned_min_ratio=0, learned_max_level=12)
+            adj, st = pc.skeleton()
+            seps = pc.sepsets()
+        np.testing.assert_array_equal(adj, R["adj"])
+        assert set(seps) == set(R["sepsets"])
+        for (a, b), (lv, side, rank, nodes) in seps.items():
+            assert lv == R["sepsets"][(a, b)][0]
+            assert oracle.ci_test(C, n, 0.01, a, b, list(nodes))[0]
 
 
 @pytest.mark.parametrize("seed", range(6))
