@@ -123,6 +123,13 @@ void pc_destroy(pc_handle *h);
  *   "lane_blocks" CTAs of 256 threads per SM of that kernel (1..32, default 8)
  *   "direct_warps" at most this many warps per CTA of the warp-per-test kernel
  *                 (1, 2, 4 or 8; default 8)
+ *   "pair_warp"   1 = at stages 1 and 2, the ordered pairs of nodes of degree
+ *                 above "pair_warp_dmin" (default 32) run one warp per pair, the
+ *                 32 lanes on 32 consecutive sets of the pair (default); 0 = off
+ *   "node_dmax"   the other small-stage nodes of degree <= node_dmax (0..128,
+ *                 default 128) run on the staged kernel, which holds
+ *                 corr[adj(u), adj(u)] in shared memory; the rest read corr
+ *                 from L2 (0 = staged kernel off)
  * Unknown keys return PC_ERR_ARG. */
 pc_status pc_set_opt(pc_handle *h, const char *key, double val);
 pc_status pc_get_opt(pc_handle *h, const char *key, double *val);

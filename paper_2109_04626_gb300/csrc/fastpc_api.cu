@@ -52,6 +52,8 @@ struct pc_handle {
     // launch shape of the test kernels (pc_autotune)
     int lane_chunk = 8, lane_rounds = 32, lane_blocks = 8, direct_warps = 8;
     int node_dmax = fpc::NODE_DMAX;   // staged small-stage kernel: largest node degree (0: off)
+    int pair_warp = 1;                // stages 1-2: warp-per-pair kernel for the larger nodes
+    int pair_warp_dmin = fpc::PAIRWARP_DMIN;
     int stage_conds = 1;                 // conditional nodes in the captured stage body
     int lane_stages = 1;                 // small stages on the rank-major small-stage kernel
     cudaStream_t stream = 0;
@@ -249,6 +251,8 @@ static TestParams make_tp(const pc_handle *h)
     tp.lane_rounds = h->lane_rounds;
     tp.lane_blocks = h->lane_blocks;
     tp.node_dmax = h->node_dmax;
+    tp.pair_warp = h->pair_warp;
+    tp.pair_warp_dmin = h->pair_warp_dmin;
     tp.direct_warps = h->direct_warps;
     tp.lane_stages = h->lane_stages;
     tp.precision = h->precision;
@@ -304,7 +308,9 @@ static pc_status create_impl(int64_t n, int32_t p, double alpha, int32_t max_lev
     A(dalloc(h, &g.tn_off, (size_t)(p + 2) * sizeof(ull)));
     A(dalloc(h, &g.cn_off, (size_t)(p + 2) * sizeof(ull)));
     A(dalloc(h, &g.rn_off, (size_t)(p + 2) * sizeof(ull)));
+    A(dalloc(h, &g.ia_off, (size_t)(p + 2) * sizeof(ull)));
     A(dalloc(h, &g.it_off, (size_t)(p + 2) * sizeof(ull)));
+    A(dalloc(h, &g.wo_off, (size_t)(p + 2) * sizeof(ull)));
     A(dalloc(h, &g.best, pp * sizeof(ull)));
     A(dalloc(h, &h->binom, (size_t)(pmax + 1) * (pmax + 1) * sizeof(ull)));
     A(dalloc(h, &g.sep_level, pp * sizeof(int)));
@@ -552,6 +558,12 @@ extern "C" pc_status pc_set_opt(pc_handle *h, const char *key, double val)
     } else if (k == "lane_blocks") {
         if (!(val >= 1 && val <= 32)) return fail(h, PC_ERR_ARG, "lane_blocks must be in [1, 32]");
         h->lane_blocks = (int)val;
+    } else if (k == "pair_warp") {
+        if (!(val == 0 || val == 1)) return fail(h, PC_ERR_ARG, "pair_warp must be 0 or 1");
+        h->pair_warp = (int)val;
+    } else if (k == "pair_warp_dmin") {
+        if (!(val >= 0 && val <= 16384)) return fail(h, PC_ERR_ARG, "pair_warp_dmin must be in [0, 16384]");
+        h->pair_warp_dmin = (int)val;
     } else if (k == "node_dmax") {
         if (!(val >= 0 && val <= fpc::NODE_DMAX))
             return fail(h, PC_ERR_ARG, "node_dmax must be in [0, " + std::to_string(fpc::NODE_DMAX) + "]");
@@ -587,6 +599,8 @@ extern "C" pc_status pc_get_opt(pc_handle *h, const char *key, double *val)
     else if (k == "lane_rounds") *val = h->lane_rounds;
     else if (k == "lane_blocks") *val = h->lane_blocks;
     else if (k == "node_dmax") *val = h->node_dmax;
+    else if (k == "pair_warp") *val = h->pair_warp;
+    else if (k == "pair_warp_dmin") *val = h->pair_warp_dmin;
     else if (k == "direct_warps") *val = h->direct_warps;
     else if (k == "tensor_core_gemm") *val = h->used_tc ? 1.0 : 0.0;
     else return fail(h, PC_ERR_ARG, "unknown option: " + k);
@@ -1065,7 +1079,7 @@ static std::vector<double> graph_key(const pc_handle *h)
             h->budget, (double)level_cap(h), (double)(uintptr_t)h->g.pool, (double)h->g.pool_cap,
             (double)(uintptr_t)h->C32, (double)(uintptr_t)h->C64, (double)h->lane_chunk,
             (double)h->lane_rounds, (double)h->lane_blocks, (double)h->direct_warps, (double)h->stage_conds,
-            (double)h->node_dmax, (double)h->learned_lmax,
+            (double)h->node_dmax, (double)h->pair_warp, (double)h->pair_warp_dmin, (double)h->learned_lmax,
             (double)h->lane_stages};
 }
 

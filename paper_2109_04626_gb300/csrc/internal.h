@@ -62,6 +62,7 @@ struct LevelInfo {
     int kernels_run;                    // kernels the captured stage loop executed
     unsigned deg_ticket;                // CTAs of the stage's degrees kernel done (last one runs the tail)
     unsigned long long node_next;       // next work item of the staged small-stage kernel
+    unsigned long long pair_next;       // next ordered pair of the warp-per-pair kernel
 };
 
 // Conditional nodes of the captured stage body: the head kernel picks one branch
@@ -78,7 +79,13 @@ constexpr int LANE_LMAX = 12;           // stages the lane-per-test kernel runs 
 // its pairs; larger neighbourhoods stay on the kernel that reads corr from L2.
 constexpr int NODE_DMAX = 128;
 constexpr int NODE_THREADS = 256;
-constexpr unsigned long long NODE_ITEM_TESTS = 16384;   // tests per work item (a slice of a node's pairs)
+constexpr unsigned long long NODE_ITEM_CHUNKS = 512;    // chunks per work item (two per thread)
+constexpr int NODE_ROUNDS_MAX = (int)NODE_ITEM_CHUNKS / 2 + 1;   // rank rounds an item spans (degree >= 2)
+// Stages 1 <= l <= PAIRWARP_LMAX: the pairs of nodes of degree above
+// pair_warp_dmin (default PAIRWARP_DMIN) run one warp per ordered pair, the
+// lanes on consecutive sets of the pair.
+constexpr int PAIRWARP_LMAX = 2;
+constexpr int PAIRWARP_DMIN = 32;
 constexpr int LANE_RANGES = 6;          // small-stage kernel instantiations: l 0-2, 3-4, 5-6, 7-8, 9-10, 11-12
 
 // Branches of the stage's switch node.  kind: 0 .. LANE_RANGES-1 a small-stage
@@ -120,7 +127,9 @@ struct GraphDev {
     unsigned long long *tn_off; // p+1: first direct test of each node (exclusive scan)
     unsigned long long *cn_off; // p+1: first complement test of each node
     unsigned long long *rn_off; // p+1: first remainder test of each node (small-stage kernel)
-    unsigned long long *it_off; // p+1: first work item of each node on the staged small-stage kernel
+    unsigned long long *ia_off; // p+1: staged small-stage kernel, first items: one per staged node
+    unsigned long long *it_off; // p+1: staged small-stage kernel, the nodes' further items
+    unsigned long long *wo_off; // p+1: warp-per-pair kernel, first ordered pair of each of its nodes
     unsigned long long *best;   // p x p, best (side<<62 | rank) per unordered pair (a<b at a*p+b)
     const unsigned long long *binom;   // ldb x ldb saturating binomials
     int ldb;                    // p+1 (batched problems: largest instance p + 1)
@@ -176,6 +185,9 @@ struct TestParams {
                         // 0: every stage on the warp-per-test kernel
     int node_dmax;      // stages 1 <= l <= LANE_LMAX: nodes of degree <= node_dmax run on the
                         // staged kernel (corr block in shared memory); 0: none
+    int pair_warp;      // stages 1 <= l <= PAIRWARP_LMAX: the pairs of nodes of degree above
+                        // pair_warp_dmin one warp per pair (0: off)
+    int pair_warp_dmin;
     int precision;      // 0 fp64, 1/2 fp32 tests with FP64 re-decision
     int reversed;
     int complement;

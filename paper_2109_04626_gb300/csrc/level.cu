@@ -153,11 +153,28 @@ __global__ void __launch_bounds__(256) degrees_tail_kernel(GraphDev g, TestParam
     tail_body(g, tp, cap, 0, nullptr, 0, hc, use_cond, sc, true);
 }
 
+// Stages 1 and 2: the pairs of a node of degree above pair_warp_dmin run one
+// warp per pair.
+__device__ __forceinline__ bool pair_warped(const TestParams &tp, int l, int dg)
+{
+    return tp.pair_warp && l >= 1 && l <= PAIRWARP_LMAX && dg > tp.pair_warp_dmin;
+}
+
 // The small-stage tests of a node of degree dg at stage l >= 1 run on the staged
-// kernel when its neighbourhood block fits the shared-memory layout.
+// kernel when its neighbourhood block fits the shared-memory layout (and the
+// node is not one of the warp-per-pair kernel).
 __device__ __forceinline__ bool node_staged(const TestParams &tp, int l, int dg)
 {
-    return l >= 1 && dg <= tp.node_dmax;
+    return l >= 1 && dg <= tp.node_dmax && !pair_warped(tp, l, dg);
+}
+
+// Chunk of the staged kernel for a node with T sets per pair and dg pairs: the
+// lane chunk, smaller when the node has too few tests to give every thread of
+// a CTA one chunk.
+__device__ __forceinline__ ull node_chunk(const TestParams &tp, ull T, int dg)
+{
+    const ull fair = T * (ull)dg / NODE_THREADS;       // T * dg < 2^64: T <= C(127, 12), dg <= 128
+    return fair < (ull)tp.lane_chunk ? (fair > 0 ? fair : 1ull) : (ull)tp.lane_chunk;
 }
 
 __device__ __forceinline__ bool comp_eligible(int d, int l, const TestParams &tp)
@@ -378,7 +395,7 @@ __global__ void __launch_bounds__(1024) head_kernel(GraphDev g, TestParams tp, d
         if (conds.use && threadIdx.x == 0) set_stage_conds(conds, I, LANE_RANGES, 0, 0, 0, 0);
         return;
     }
-    __shared__ ull sh[4 * 32];
+    __shared__ ull sh[6 * 32];                           // scratch of block_scan_sat<6>
     const int p = g.p, l = I->l, t = threadIdx.x;
     const int per = (p + (int)blockDim.x - 1) / (int)blockDim.x;   // <= HEAD_PER_MAX
     const int s0 = min(p, t * per), s1 = min(p, s0 + per);
@@ -392,14 +409,19 @@ __global__ void __launch_bounds__(1024) head_kernel(GraphDev g, TestParams tp, d
         return (g.row_off && l >= 1 && l <= tp.learned_lmax && T >= 2) ? (ull)dg * (ull)(dg - 1) : 0ull;
     };
     const bool small = tp.lane_stages && tp.precision != 0 && l <= LANE_LMAX;
-    // staged kernel work items of a node: slices of its pairs of about
-    // NODE_ITEM_TESTS tests each (at least one pair per slice)
+    // staged kernel work items of a node: consecutive ranges of NODE_ITEM_CHUNKS
+    // chunks of its rank-major chunk space (chunk r of every pair before r+1)
     auto items = [&](int dg, ull T) -> ull {
         if (!small || !T || !node_staged(tp, l, dg)) return 0ull;
-        const ull w = sat_mul(T, (ull)dg), k = (w + NODE_ITEM_TESTS - 1) / NODE_ITEM_TESTS;
-        return k < (ull)dg ? k : (ull)dg;
+        const ull ch = node_chunk(tp, T, dg);
+        const ull nc = sat_mul((T + ch - 1) / ch, (ull)dg);
+        return nc == KEY_NONE ? KEY_NONE : (nc + NODE_ITEM_CHUNKS - 1) / NODE_ITEM_CHUNKS;
     };
-    ull v[4] = {0ull, 0ull, 0ull, 0ull}, mxT = 0;        // direct, complement, proposal rows, staged items
+    // warp-per-pair kernel: the pairs of the larger direct nodes of stages 1-2
+    auto warp_mode = [&](int dg, ull T) -> bool { return small && T && pair_warped(tp, l, dg); };
+    // direct, complement, proposal rows, staged nodes (their first items), the
+    // staged nodes' further items, warp-per-pair ordered pairs
+    ull v[6] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull}, mxT = 0;
     bool sat = false;
     for (int u = s0; u < s1; ++u) {
         const int dg = g.deg[u], d = dg - 1;
@@ -412,14 +434,17 @@ __global__ void __launch_bounds__(1024) head_kernel(GraphDev g, TestParams tp, d
         if (comp) v[1] = sat_add(v[1], tot);
         else {
             v[0] = sat_add(v[0], tot);
-            if (!items(dg, T)) mxT = T > mxT ? T : mxT;   // the lane kernel's pairs only
+            if (!items(dg, T) && !warp_mode(dg, T)) mxT = T > mxT ? T : mxT;   // the lane kernel's pairs only
             v[2] = sat_add(v[2], prows(dg, T));           // complement-path pairs keep the plain order
-            v[3] += items(dg, T);
+            const ull k = items(dg, T);
+            v[3] += k ? 1ull : 0ull;
+            v[4] = sat_add(v[4], k ? k - 1 : 0ull);
+            v[5] += warp_mode(dg, T) ? (ull)dg : 0ull;
         }
     }
     const int ssat = __syncthreads_or(sat);
-    ull ex[4], tot[4];
-    block_scan_sat<4>(v, ex, tot, sh);
+    ull ex[6], tot[6];
+    block_scan_sat<6>(v, ex, tot, sh);
     // else: plain order this stage (too many rows, or too few tests for the order to matter)
     // score rows are one per candidate; the order pays off only when a pair has
     // many more sets than candidates (l >= 2 and large neighbourhoods)
@@ -429,19 +454,24 @@ __global__ void __launch_bounds__(1024) head_kernel(GraphDev g, TestParams tp, d
     const ull rows_total = tot[2];
     if (t == 0 && g.scored) g.scored[l] = rows_fit && rows_total > 0;
     {
-        ull rd = ex[0], rc = ex[1], rr = ex[2], ri = ex[3];
+        ull rd = ex[0], rc = ex[1], rr = ex[2], ra = ex[3], ri = ex[4], rw = ex[5];
         for (int u = s0; u < s1; ++u) {
             const int dg = g.deg[u];
             const ull T = Tn[u - s0], tt = sat_mul(T, (ull)dg);
             g.tn_off[u] = rd;
             g.cn_off[u] = rc;
+            g.ia_off[u] = ra;
             g.it_off[u] = ri;
+            g.wo_off[u] = rw;
             if (g.row_off) g.row_off[u] = rows_fit ? rr : 0ull;
             if (cm[u - s0]) rc = sat_add(rc, tt);
             else {
                 rd = sat_add(rd, tt);
                 rr = sat_add(rr, prows(dg, T));
-                ri += items(dg, T);
+                const ull k = items(dg, T);
+                ra += k ? 1ull : 0ull;
+                ri = sat_add(ri, k ? k - 1 : 0ull);
+                rw += (!cm[u - s0] && warp_mode(dg, T)) ? (ull)dg : 0ull;
             }
         }
     }
@@ -469,7 +499,8 @@ __global__ void __launch_bounds__(1024) head_kernel(GraphDev g, TestParams tp, d
         ull v2[1] = {0ull};
         for (int u = s0; u < s1; ++u) {
             const ull T = Tn[u - s0];
-            if (!cm[u - s0] && T > skip && !items(g.deg[u], T)) v2[0] = sat_add(v2[0], sat_mul(T - skip, (ull)g.deg[u]));
+            if (!cm[u - s0] && T > skip && !items(g.deg[u], T) && !warp_mode(g.deg[u], T))
+                v2[0] = sat_add(v2[0], sat_mul(T - skip, (ull)g.deg[u]));
         }
         ull ex2[1], tot2[1];
         block_scan_sat<1>(v2, ex2, tot2, sh);
@@ -477,7 +508,8 @@ __global__ void __launch_bounds__(1024) head_kernel(GraphDev g, TestParams tp, d
         for (int u = s0; u < s1; ++u) {
             const ull T = Tn[u - s0];
             g.rn_off[u] = rr2;
-            if (!cm[u - s0] && T > skip && !items(g.deg[u], T)) rr2 = sat_add(rr2, sat_mul(T - skip, (ull)g.deg[u]));
+            if (!cm[u - s0] && T > skip && !items(g.deg[u], T) && !warp_mode(g.deg[u], T))
+                rr2 = sat_add(rr2, sat_mul(T - skip, (ull)g.deg[u]));
         }
         if (t == 0) g.rn_off[p] = tot2[0];
     }
@@ -486,10 +518,17 @@ __global__ void __launch_bounds__(1024) head_kernel(GraphDev g, TestParams tp, d
         I->lane_rounds = rounds;
         I->lane_overflow = 0;
         I->node_next = 0;
+        I->pair_next = 0;
+        g.wo_off[p] = tot[5];
         const ull td = tot[0], tc = tot[1];
         g.tn_off[p] = td;
         g.cn_off[p] = tc;
-        g.it_off[p] = tot[3];
+        g.ia_off[p] = tot[3];
+        g.it_off[p] = tot[4];
+        if (tot[4] == KEY_NONE) {                       // staged items saturated: treat as over budget
+            I->error = 6;
+            I->halt = 1;
+        }
         if (g.row_off) g.row_off[p] = rows_fit ? rows_total : 0ull;
         I->total_direct = td;
         I->total_comp = tc;
@@ -506,7 +545,8 @@ __global__ void __launch_bounds__(1024) head_kernel(GraphDev g, TestParams tp, d
             set_stage_conds(conds, I, run && small && td > 0 ? lane_range_of_dev(l) : LANE_RANGES,
                             run && td > 0 && !small, run && tc > 0,
                             run && g.row_off && rows_fit && rows_total > 0,
-                            (tp.lazy && tp.c64_list && tp.pair_seen ? 5 : 3) + (tp.node_dmax > 0 ? 1 : 0));
+                            (tp.lazy && tp.c64_list && tp.pair_seen ? 5 : 3) + (tp.node_dmax > 0 ? 1 : 0) +
+                                (tp.pair_warp && l <= PAIRWARP_LMAX ? 1 : 0));
         }
     }
 }
@@ -1015,15 +1055,19 @@ __device__ __forceinline__ int lex_next(int *pos, int d)
 //   x = 1 - |l_s|^2,  c_u = corr_us - lu.l_s,  c_v = corr_vs - lv.l_s,
 //   H = H_P - [c_u c_v]^T [c_u c_v] / x
 // -- the same Cholesky of the S block (Sec. 4) in bordered form, O(L^2) work.
-template <int L, bool PROP, class Src>
-__device__ __forceinline__ void lane_tests_lex(const GraphDev &g, const TestParams &tp, const Src &src, int u,
+// sqf = sqrt(n - L - 3) and rq = tanh(q / sqf), the stage's |r| threshold, come
+// from the caller; pos0: the positions of the set at `rank` when the caller has
+// unranked it (nullptr: unranked here).  CHECK: re-read the pair's key every
+// fourth test (the callers that run one test per call check it themselves).
+// Returns true when a test of the range separated (its key is recorded).
+template <int L, bool PROP, class Src, bool CHECK = true, class PosT = short>
+__device__ __forceinline__ bool lane_tests_lex(const GraphDev &g, const TestParams &tp, const Src &src, int u,
                                                int v, int j, int d, ull T, ull rank, ull rank_end, ull *queue,
-                                               ull qcap, ull *qlen, LaneAcc &acc)
+                                               ull qcap, ull *qlen, LaneAcc &acc, float sqf, float rq,
+                                               const PosT *pos0 = nullptr)
 {
     constexpr int K = L > 0 ? L - 1 : 0;                 // prefix length
     constexpr int KA = K > 0 ? K : 1;
-    const float sqf = sqrtf((float)(n_of(tp, u) - L - 3));
-    const float rq = tanhf(tp.qf / sqf);                 // |r| threshold of this stage
     // proposal order: position x of the enumeration is neighbour index perm[x]
     const short *pr = nullptr;
     if (PROP && stage_prop(g, L) && g.row_off[u + 1] > g.row_off[u]) pr = g.perm + g.row_off[u] + (ull)j * d;
@@ -1033,7 +1077,12 @@ __device__ __forceinline__ void lane_tests_lex(const GraphDev &g, const TestPara
     const ull tbase = g.tn_off[u] + (ull)j * T;
     const float cuv = src.cuv();
     int pos[L > 0 ? L : 1];
-    unrank_lex(rank, d, L, g.binom, g.ldb, pos);
+    if (pos0) {
+#pragma unroll
+        for (int i = 0; i < L; ++i) pos[i] = pos0[i];
+    } else {
+        unrank_lex(rank, d, L, g.binom, g.ldb, pos);
+    }
     int sp[KA];
     float Lp[KA * (KA + 1) / 2], rd[KA], lu[KA], lv[KA];
     float huu = 1.f, hvv = 1.f, huv = cuv, ppmin = 1e30f;
@@ -1047,7 +1096,7 @@ __device__ __forceinline__ void lane_tests_lex(const GraphDev &g, const TestPara
         const ull key = ((ull)side << 62) | rank;
         // an earlier set of this pair already separates: checked every fourth test
         // (the read goes to L2; at most three tests are wasted)
-        if (since == 0 && *(volatile ull *)bp < key) return;
+        if (CHECK && since == 0 && *(volatile ull *)bp < key) return false;
         since = (since + 1) & 3;
         if (K > 0 && fresh) {
             // factor the prefix and eliminate the rows of u and v by it
@@ -1169,10 +1218,11 @@ __device__ __forceinline__ void lane_tests_lex(const GraphDev &g, const TestPara
         if (lane_decide<L>(tp, sqf, rq, h11, h12, h22, pmin, bad, xs, bsu, bsv, gs, kapP, A0u, A0v, tbase + rank,
                            queue, qcap, qlen, acc)) {
             atomicMin(bp, key);
-            return;
+            return true;
         }
         if (rank + 1 < rank_end && lex_next<L>(pos, d) < L - 1) fresh = true;
     }
+    return false;
 }
 
 // one chunk of a pair (PROP: the kernel variant of handles with a proposal
@@ -1185,7 +1235,9 @@ __device__ __forceinline__ void lane_chunk(const GraphDev &g, const TestParams &
     const int *nb = g.nbr + nidx(g, u);
     const int v = nb[j];
     const GlobalSrc src{C32, tp.prow, ldc, nb, C32 + cidx(tp.prow, ldc, u, 0), C32 + cidx(tp.prow, ldc, v, 0), v};
-    lane_tests_lex<L, PROP>(g, tp, src, u, v, j, d, T, rank, rank_end, queue, qcap, qlen, acc);
+    const float sqf = sqrtf((float)(n_of(tp, u) - L - 3));
+    lane_tests_lex<L, PROP>(g, tp, src, u, v, j, d, T, rank, rank_end, queue, qcap, qlen, acc, sqf,
+                            tanhf(tp.qf / sqf));
 }
 
 // Phase A, rank-major: item g = (round r, ordered pair o), r = g / NP -- a wave
@@ -1216,7 +1268,8 @@ __device__ __forceinline__ void lane_dispatch(const GraphDev &g, const TestParam
             }
             const int u = g.opu[o];                     // owner of ordered pair o
             if (g.tn_off[u + 1] == g.tn_off[u]) continue;   // not a direct node this stage
-            if (g.it_off[u + 1] != g.it_off[u]) continue;   // its pairs run on the staged kernel
+            if (g.ia_off[u + 1] != g.ia_off[u]) continue;   // its pairs run on the staged kernel
+            if (g.wo_off[u + 1] != g.wo_off[u]) continue;   // ... or on the warp-per-pair kernel
             const int d = g.deg[u] - 1;
             const ull T = g.binom[(long long)d * g.ldb + L];
             const ull r0 = (ull)r * chunk;
@@ -1285,53 +1338,78 @@ __global__ void __launch_bounds__(256, HI <= 2 ? 4 : (HI <= 4 ? 3 : (HI <= 8 ? 2
 // Every ordered pair (u, v) of a node u has the same candidate count d and the
 // same C(d, l) sets, and every set it tests lies in adj(u): the block
 // corr[adj(u), adj(u)] and the row corr[u, adj(u)] hold every entry the
-// node's tests read.  A CTA takes a work item (a slice of the pairs of one
-// node, from the per-stage counter), stages that block in shared memory once,
-// and its threads run the slice's chunks rank-major (chunk r of every pair of
-// the slice before chunk r+1), each chunk by the bordered tests of
-// lane_tests_lex reading the staged block.  The arithmetic, the keys and the
-// FP64 queue are those of the lane kernel, so the results are the same.
+// node's tests read.  The node's chunks are ordered rank-major (chunk r of
+// every pair before chunk r+1) and cut into work items of NODE_ITEM_CHUNKS
+// chunks; a CTA takes items from the per-stage counter, stages the node's block
+// in shared memory (once for consecutive items of one node), and its threads
+// run the item's chunks by the bordered tests of lane_tests_lex reading the
+// staged block.  The arithmetic, the keys and the FP64 queue are those of the
+// lane kernel, so the results are the same.
 template <int L, bool PROP>
 __device__ __forceinline__ void node_dispatch(const GraphDev &g, const TestParams &tp, const float *C32, int ldc,
                                               ull *queue, ull qcap, ull *qlen)
 {
     extern __shared__ __align__(16) float node_smem[];
     __shared__ ull item_s;
+    constexpr int LP = L > 0 ? L : 1;
     float *cus = node_smem;                              // NODE_DMAX floats
-    float *B = node_smem + NODE_DMAX;                    // deg x deg
+    short *pos_s = (short *)(node_smem + NODE_DMAX);     // NODE_ROUNDS_MAX x L start positions
+    float *B = node_smem + NODE_DMAX + (NODE_ROUNDS_MAX * LP + 1) / 2;   // deg x deg
     LaneAcc acc = {0u, 0u, 0u};
     const int p = g.p;
-    const ull nitems = g.it_off[p];
+    const ull na = g.ia_off[p], nitems = na + g.it_off[p];
+    int staged = -1;                                     // node whose block is in shared memory
     for (;;) {
         __syncthreads();                                 // the last item's tests are done with the block
         if (threadIdx.x == 0) item_s = atomicAdd(&g.info->node_next, 1ull);
         __syncthreads();
         const ull it = item_s;
         if (it >= nitems) break;
-        const int u = (int)(upper_bound_dev(g.it_off, (long long)p + 1, it) - 1);
+        // the first item of every staged node comes first, then the further
+        // items node by node: early chunks of all pairs run before late ones
+        int u;
+        ull loc;
+        if (it < na) {
+            u = (int)(upper_bound_dev(g.ia_off, (long long)p + 1, it) - 1);
+            loc = 0;
+        } else {
+            u = (int)(upper_bound_dev(g.it_off, (long long)p + 1, it - na) - 1);
+            loc = 1 + (it - na - g.it_off[u]);
+        }
         const int dg = g.deg[u], d = dg - 1;
         const ull T = g.binom[(long long)d * g.ldb + L];
-        const int nsl = (int)(g.it_off[u + 1] - g.it_off[u]), sl = (int)(it - g.it_off[u]);
-        const int j0 = (int)((long long)dg * sl / nsl), j1 = (int)((long long)dg * (sl + 1) / nsl);
+        const ull chunk = node_chunk(tp, T, dg);
+        const ull nc = (T + chunk - 1) / chunk * (ull)dg;
+        const ull c0 = loc * NODE_ITEM_CHUNKS;
+        const ull c1 = c0 + NODE_ITEM_CHUNKS < nc ? c0 + NODE_ITEM_CHUNKS : nc;
         const int *nb = g.nbr + nidx(g, u);
-        for (int e = threadIdx.x; e < dg * dg; e += blockDim.x) {
-            const int a = e / dg, b = e - a * dg;
-            B[e] = C32[cidx(tp.prow, ldc, nb[a], nb[b])];
+        if (u != staged) {
+            for (int e = threadIdx.x; e < dg * dg; e += blockDim.x) {
+                const int a = e / dg, b = e - a * dg;
+                B[e] = C32[cidx(tp.prow, ldc, nb[a], nb[b])];
+            }
+            for (int e = threadIdx.x; e < dg; e += blockDim.x) cus[e] = C32[cidx(tp.prow, ldc, u, nb[e])];
+            staged = u;
         }
-        for (int e = threadIdx.x; e < dg; e += blockDim.x) cus[e] = C32[cidx(tp.prow, ldc, u, nb[e])];
+        // the item's chunks span the rank rounds r0 .. r1 (a round: chunk r of every
+        // pair); every pair of the node has the same d, so each round's first set is
+        // unranked once for the CTA
+        const ull rb = c0 / (unsigned)dg, re = (c1 - 1) / (unsigned)dg;
+        for (int q = threadIdx.x; q <= (int)(re - rb); q += blockDim.x) {
+            int pq[LP];
+            unrank_lex((rb + q) * chunk, d, L, g.binom, g.ldb, pq);
+#pragma unroll
+            for (int i = 0; i < L; ++i) pos_s[q * LP + i] = (short)pq[i];
+        }
         __syncthreads();
-        // chunks of at most lane_chunk sets, fewer when the slice has few tests, so
-        // that every thread of the CTA has work
-        const unsigned np = (unsigned)(j1 - j0);
-        const ull fair = (ull)np * T / blockDim.x;
-        const ull chunk = fair < (ull)tp.lane_chunk ? (fair > 0 ? fair : 1ull) : (ull)tp.lane_chunk;
-        const ull total = (T + chunk - 1) / chunk * np;
-        for (ull c = threadIdx.x; c < total; c += blockDim.x) {
-            const ull r = c / np;
-            const int j = j0 + (int)(c - r * np);
+        const float sqf = sqrtf((float)(n_of(tp, u) - L - 3)), rq = tanhf(tp.qf / sqf);
+        for (ull c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+            const ull r = c / (unsigned)dg;
+            const int j = (int)(c - r * (unsigned)dg);
             const ull r0 = r * chunk, r1 = r0 + chunk < T ? r0 + chunk : T;
             const StagedSrc src{B, cus, dg, j};
-            lane_tests_lex<L, PROP>(g, tp, src, u, nb[j], j, d, T, r0, r1, queue, qcap, qlen, acc);
+            lane_tests_lex<L, PROP>(g, tp, src, u, nb[j], j, d, T, r0, r1, queue, qcap, qlen, acc, sqf, rq,
+                                    pos_s + (r - rb) * LP);
         }
     }
     ull tests = acc.tests, band = acc.band, guard = acc.guard;
@@ -1364,8 +1442,97 @@ __global__ void __launch_bounds__(NODE_THREADS, HI <= 2 ? 3 : (HI <= 4 ? 3 : (HI
 {
     if (stopped(g.info)) return;
     const int l = g.info->l;
-    if (tp.precision == 0 || l < LO || l > HI || l < 1 || g.it_off[g.p] == 0) return;
+    if (tp.precision == 0 || l < LO || l > HI || l < 1 || g.ia_off[g.p] == 0) return;
     node_switch<(LO > 1 ? LO : 1), HI, PROP>(l, g, tp, C32, ldc, queue, qcap, qlen);
+}
+
+// ---------------------------------------------------------------- one warp per pair (stages 1-2)
+// At stages 1 and 2 the nodes too large for the staged layout have hundreds of
+// neighbours.  A warp takes one of their ordered pairs (u, v) from the stage
+// counter and walks its sets in lexicographic order, 32 at a time: lane i tests
+// the set of rank base + i (the bordered test of lane_tests_lex, one set), so
+// the rows corr[u, .], corr[v, .] and the prefix member's row are the same for
+// the whole warp and the index arithmetic is shared.  The pair stops at the
+// first block in which a test separates (keys by atomicMin: the lowest rank
+// wins), or when the pair's key shows an earlier separation.
+// Advance the lexicographic position (q0 < q1 < d) by k sets; positions past the
+// last set stop at q0 = d - 1.
+__device__ __forceinline__ void lex2_advance(int &q0, int &q1, int k, int d)
+{
+    q1 += k;
+    while (q1 >= d && q0 < d - 1) {
+        ++q0;
+        q1 = q1 - d + q0 + 1;
+    }
+}
+
+template <int L, bool PROP>
+__device__ __forceinline__ void pairwarp_dispatch(const GraphDev &g, const TestParams &tp, const float *C32, int ldc,
+                                                  ull *queue, ull qcap, ull *qlen)
+{
+    static_assert(L == 1 || L == 2, "the warp-per-pair kernel runs stages 1 and 2");
+    const int lane = threadIdx.x & 31;
+    LaneAcc acc = {0u, 0u, 0u};
+    const int p = g.p;
+    const ull npairs = g.wo_off[p];
+    for (;;) {
+        ull o = 0;
+        if (lane == 0) o = atomicAdd(&g.info->pair_next, 1ull);
+        o = __shfl_sync(0xffffffffu, o, 0);
+        if (o >= npairs) break;
+        const int u = (int)(upper_bound_dev(g.wo_off, (long long)p + 1, o) - 1);
+        const int j = (int)(o - g.wo_off[u]);
+        const int d = g.deg[u] - 1;
+        const ull T = g.binom[(long long)d * g.ldb + L];
+        const int *nb = g.nbr + nidx(g, u);
+        const int v = nb[j];
+        const GlobalSrc src{C32, tp.prow, ldc, nb, C32 + cidx(tp.prow, ldc, u, 0), C32 + cidx(tp.prow, ldc, v, 0),
+                            v};
+        const float sqf = sqrtf((float)(n_of(tp, u) - L - 3)), rq = tanhf(tp.qf / sqf);
+        const ull *bp = g.best + pidx(g, min(u, v), max(u, v));
+        const ull side = (ull)(u > v) << 62;
+        int b0 = 0, b1 = 1;                               // positions of the block's first set (L = 2)
+        for (ull base = 0; base < T; base += 32) {
+            if (*(volatile const ull *)bp < (side | base)) break;   // an earlier set separates
+            const ull rank = base + (ull)lane;
+            int pos[L];
+            if (L == 1) {
+                pos[0] = (int)rank;
+            } else {
+                int q0 = b0, q1 = b1;
+                lex2_advance(q0, q1, lane, d);
+                pos[0] = q0;
+                pos[L - 1] = q1;
+            }
+            bool found = false;
+            if (rank < T)
+                found = lane_tests_lex<L, PROP, GlobalSrc, false, int>(g, tp, src, u, v, j, d, T, rank, rank + 1,
+                                                                       queue, qcap, qlen, acc, sqf, rq, pos);
+            if (__any_sync(0xffffffffu, found)) break;
+            if (L == 2) lex2_advance(b0, b1, 32, d);
+        }
+    }
+    ull tests = acc.tests, band = acc.band, guard = acc.guard;
+    for (int off = 16; off > 0; off >>= 1) {
+        tests += __shfl_xor_sync(0xffffffffu, tests, off);
+        band += __shfl_xor_sync(0xffffffffu, band, off);
+        guard += __shfl_xor_sync(0xffffffffu, guard, off);
+    }
+    if (lane == 0) {
+        WarpAcc w = {tests, 0, band, guard, 0, tests * flops_direct(L), 0, 0.f};
+        flush_acc(w, g.ctr);
+    }
+}
+
+template <bool PROP>
+__global__ void __launch_bounds__(256, 4) ci_pairwarp_kernel(GraphDev g, TestParams tp, const float *C32, int ldc,
+                                                             ull *queue, ull qcap, ull *qlen)
+{
+    if (stopped(g.info)) return;
+    const int l = g.info->l;
+    if (tp.precision == 0 || l < 1 || l > PAIRWARP_LMAX || g.wo_off[g.p] == 0) return;
+    if (l == 1) pairwarp_dispatch<1, PROP>(g, tp, C32, ldc, queue, qcap, qlen);
+    else pairwarp_dispatch<2, PROP>(g, tp, C32, ldc, queue, qcap, qlen);
 }
 
 // FP64 pass over the queued tests of the lane kernel (one warp per test).
@@ -2274,8 +2441,12 @@ cudaError_t launch_ci_direct(GraphDev g, TestParams tp, int mmax, const float *C
     return cudaGetLastError();
 }
 
-// shared memory of the staged kernel: the row corr[u, adj(u)] and the block
-size_t node_smem_bytes(int dmax) { return (size_t)(NODE_DMAX + dmax * dmax) * sizeof(float); }
+// shared memory of the staged kernel: the row corr[u, adj(u)], the start
+// positions of an item's rank rounds (shorts, L <= LANE_LMAX) and the block
+size_t node_smem_bytes(int dmax)
+{
+    return (size_t)(NODE_DMAX + (NODE_ROUNDS_MAX * LANE_LMAX + 1) / 2 + dmax * dmax) * sizeof(float);
+}
 
 // resident CTAs per SM of the staged kernel instantiation (registers and shared
 // memory), looked up once per instantiation and shared-memory size
@@ -2302,6 +2473,10 @@ static void lane_launch_p(GraphDev g, TestParams tp, const float *C32, int ldc, 
 {
     ci_lane_kernel<LO, HI, PROP><<<num_sms() * tp.lane_blocks, 256, 0, s>>>(g, tp, C32, ldc, queue, qcap, qlen);
     note_launch();
+    if (LO <= PAIRWARP_LMAX && tp.pair_warp) {
+        ci_pairwarp_kernel<PROP><<<num_sms() * 4, 256, 0, s>>>(g, tp, C32, ldc, queue, qcap, qlen);
+        note_launch();
+    }
     if (HI >= 1 && tp.node_dmax > 0) {
         const size_t smem = node_smem_bytes(tp.node_dmax);
         const int per_sm = node_blocks_per_sm<LO, HI, PROP>(smem);

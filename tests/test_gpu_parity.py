@@ -239,18 +239,24 @@ def test_skeleton_deep_stages_proposal_order(fp):
         assert oracle.ci_test(C, n, 0.01, a, b, list(nodes))[0]
 
 
+@pytest.mark.parametrize("pair_warp", [0, 1])
 @pytest.mark.parametrize("node_dmax", [0, 5, 12, 128])
 @pytest.mark.parametrize("case", ["p95_conventional", "hub", "p95_reversed"])
-def test_skeleton_staged_and_global_small_stages(fp, case, node_dmax):
+def test_skeleton_staged_and_global_small_stages(fp, case, node_dmax, pair_warp):
+    # pair_warp_dmin 4: the warp-per-pair kernel takes every node of degree > 4 at
+    # stages 1 and 2 (the default 32 leaves the small ones to the staged kernel)
     """The small stages split between the staged kernel (nodes of degree <=
-    node_dmax: corr block in shared memory) and the kernel reading corr from L2
-    (the rest); every split gives the oracle's skeleton, sets and counts."""
+    node_dmax: corr block in shared memory), the warp-per-pair kernel (stages 1
+    and 2, the other nodes) and the kernel reading corr from L2 (the rest); every
+    split gives the oracle's skeleton, sets and counts."""
     if case == "hub":
         X, order = _hub_case(), 0
     else:
         X, order = sem.make(2).X, (1 if case == "p95_reversed" else 0)
     for precision in (1, 2):
-        _check_skeleton(fp, X, order=order, precision=precision, node_dmax=node_dmax)
+        for dmin in (4, 32):
+            _check_skeleton(fp, X, order=order, precision=precision, node_dmax=node_dmax, pair_warp=pair_warp,
+                            pair_warp_dmin=dmin)
 
 
 def test_staged_kernel_proposal_order(fp):
@@ -261,8 +267,8 @@ def test_staged_kernel_proposal_order(fp):
     C = oracle.pearson(X)
     R = oracle.skeleton(C, n, 0.01, -1, reversed_order=False)
     theta = np.random.default_rng(9).standard_normal(fp.pc_mlp_nparam()).astype(np.float32) * 0.2
-    for node_dmax in (0, 10, 128):
-        with fp.PC(n, p, 0.01, -1, order=0, node_dmax=node_dmax) as pc:
+    for node_dmax, pair_warp in ((0, 0), (0, 1), (10, 1), (128, 0), (128, 1)):
+        with fp.PC(n, p, 0.01, -1, order=0, node_dmax=node_dmax, pair_warp=pair_warp) as pc:
             pc.corr(torch.from_numpy(X).cuda())
             fp.pc_mlp_set_params(pc.h, theta)
             pc.set(learned=1, learned_min_tests=0, learned_min_ratio=0, learned_max_level=12)
