@@ -123,6 +123,15 @@ void pc_destroy(pc_handle *h);
  *   "lane_blocks" CTAs of 256 threads per SM of that kernel (1..32, default 8)
  *   "direct_warps" at most this many warps per CTA of the warp-per-test kernel
  *                 (1, 2, 4 or 8; default 8)
+ *   "path_pool"   1 = search the path-restricted pools adj(G,i,j) n path(G,i,j)
+ *                 of Algorithms 1 and 2 (Sec. 2.1 notation): the neighbours of
+ *                 i or j, other than i and j, that lie on some simple i-j path of
+ *                 the stage's frozen graph; one pool per unordered pair, searched
+ *                 once, sets in lexicographic order of the ascending pool (side
+ *                 0), FP64 tests, PC-stable, a host-driven stage loop; the
+ *                 schedule runs on the largest pool.  0 = the neighbour sets
+ *                 adj(u)\{v} of both endpoints (default).  Not with "learned" or
+ *                 a batched handle.
  *   "pair_warp"   1 = at stages 1 and 2, the ordered pairs of nodes of degree
  *                 above "pair_warp_dmin" (default 32) run one warp per pair, the
  *                 32 lanes on 32 consecutive sets of the pair (default); 0 = off

@@ -54,6 +54,10 @@ struct pc_handle {
     int node_dmax = fpc::NODE_DMAX;   // staged small-stage kernel: largest node degree (0: off)
     int pair_warp = 1;                // stages 1-2: warp-per-pair kernel for the larger nodes
     int pair_warp_dmin = fpc::PAIRWARP_DMIN;
+    // path-restricted pools (option "path_pool"): component labels of the graph
+    // without each node, the largest pool
+    int path_pool = 0;
+    int *pp_comp = nullptr, *pp_max = nullptr;
     int stage_conds = 1;                 // conditional nodes in the captured stage body
     int lane_stages = 1;                 // small stages on the rank-major small-stage kernel
     cudaStream_t stream = 0;
@@ -558,6 +562,10 @@ extern "C" pc_status pc_set_opt(pc_handle *h, const char *key, double val)
     } else if (k == "lane_blocks") {
         if (!(val >= 1 && val <= 32)) return fail(h, PC_ERR_ARG, "lane_blocks must be in [1, 32]");
         h->lane_blocks = (int)val;
+    } else if (k == "path_pool") {
+        if (!(val == 0 || val == 1)) return fail(h, PC_ERR_ARG, "path_pool must be 0 or 1");
+        if (val == 1 && h->nblk) return fail(h, PC_ERR_ARG, "path_pool: a batched handle is not supported");
+        h->path_pool = (int)val;
     } else if (k == "pair_warp") {
         if (!(val == 0 || val == 1)) return fail(h, PC_ERR_ARG, "pair_warp must be 0 or 1");
         h->pair_warp = (int)val;
@@ -600,6 +608,7 @@ extern "C" pc_status pc_get_opt(pc_handle *h, const char *key, double *val)
     else if (k == "lane_blocks") *val = h->lane_blocks;
     else if (k == "node_dmax") *val = h->node_dmax;
     else if (k == "pair_warp") *val = h->pair_warp;
+    else if (k == "path_pool") *val = h->path_pool;
     else if (k == "pair_warp_dmin") *val = h->pair_warp_dmin;
     else if (k == "direct_warps") *val = h->direct_warps;
     else if (k == "tensor_core_gemm") *val = h->used_tc ? 1.0 : 0.0;
@@ -968,7 +977,7 @@ static pc_status enqueue_level(pc_handle *h, cudaStream_t s, int mmax, bool use_
         CK(cudaStreamGetCaptureInfo(s, &cst, nullptr, &cg, nullptr, nullptr, nullptr));
         sc.use = 1;
         sc.has_comp = use_prec;
-        sc.has_score = h->learned;
+        sc.has_score = h->learned && h->learned_lmax >= 1;
         sc.has_prec = use_prec;
         CK(cudaGraphConditionalHandleCreate(&sc.tests, cg, (unsigned)fpc::stage_branches(sc.has_comp, sc.has_score),
                                             0));
@@ -988,7 +997,10 @@ static pc_status enqueue_level(pc_handle *h, cudaStream_t s, int mmax, bool use_
     // small stages: one lane-kernel range, the FP64 pass over its queue, and the
     // warp-per-test kernel that re-runs the stage if that queue overflowed
     auto lane = [&](int range, cudaStream_t st) -> pc_status {
-        CK(fpc::launch_ci_lane(g, tp, h->C32, h->C64, h->ldc, h->rq, h->rq_cap, h->rq_len, range, h->learned, st));
+        // the proposal-order variants only where a stage can be scored (the scoring
+        // gate at 0 leaves every stage in the plain order)
+        CK(fpc::launch_ci_lane(g, tp, h->C32, h->C64, h->ldc, h->rq, h->rq_cap, h->rq_len, range,
+                               h->learned && h->learned_lmax >= 1, st));
         CK(fpc::launch_ci_direct(g, tp, fpc::LANE_LMAX + 2, h->C32, h->C64, h->ldc, st));
         return PC_OK;
     };
@@ -1030,7 +1042,7 @@ static pc_status enqueue_level(pc_handle *h, cudaStream_t s, int mmax, bool use_
                                     (unsigned)fpc::stage_branches(sc.has_comp, sc.has_score), branch))
             return r;
     } else {
-        if (h->learned) {
+        if (h->learned && h->learned_lmax >= 1) {
             auto t = T(6);
             if (pc_status r = score(0, s)) return r;
         }
@@ -1283,7 +1295,7 @@ static pc_status skeleton_complete(pc_handle *h, pc_stats *st, bool *overflow)
         }
     }
     CK(cudaEventRecord(h->ev1, s));
-    if (h->learned) {
+    if (h->learned && h->learned_lmax >= 1) {
         // largest stage run: the first one in the reversed order, the last one conventionally
         Timed tm(h, h->timing ? 6 : -1);
         const int lmax = h->order == 1 ? h->info_h->first_level : h->info_h->l - 1;
@@ -1455,13 +1467,144 @@ extern "C" pc_status pc_autotune(pc_handle *h, int32_t reps, pc_tune_result *out
     return PC_OK;
 }
 
+// The search over the path-restricted pools adj(G,i,j) n path(G,i,j) of
+// Algorithms 1 and 2 (Sec. 2.1 notation, option "path_pool"): PC-stable, one
+// pool per unordered pair searched once (side 0), FP64 tests, driven from the
+// host stage by stage.  Schedule as for the neighbour sets: Algorithm 1 runs
+// l = 0, 1, ... while some pair's pool has at least l members; Algorithm 2 runs
+// the closed-form stage l = p-2, then l = min(cap, p-3, largest pool) and
+// l <- min(l-1, largest pool) down to 0.  The pools and the largest pool come
+// from the graph as it is at the start of the stage.
+static pc_status skeleton_pathpool_once(pc_handle *h, pc_stats *st, bool *overflow)
+{
+    GraphDev &g = h->g;
+    cudaStream_t s = h->stream;
+    const int p = h->p;
+    const long long n = h->n;
+    const size_t pp = h->pair_elems;
+    *overflow = false;
+    if (h->learned) return fail(h, PC_ERR_ARG, "path_pool: the proposal order does not apply to pair pools");
+    if (!h->c64_full) {
+        if (pc_status r = materialize_c64(h)) return r;
+    }
+    if (!h->pp_comp) {
+        CK(dalloc(h, &h->pp_comp, (size_t)p * p * sizeof(int)));
+        CK(dalloc(h, &h->pp_max, sizeof(int)));
+    }
+    TestParams tp = make_tp(h);
+    tp.lazy = 0;                                         // the full FP64 matrix
+    std::memset(st, 0, sizeof(*st));
+    CK(cudaEventRecord(h->ev0, s));
+    CK(fpc::launch_init_adj(g, s));
+    CK(cudaMemsetAsync(g.best, 0xff, pp * sizeof(ull), s));
+    CK(cudaMemsetAsync(g.sep_level, 0xff, pp * sizeof(int), s));
+    CK(cudaMemsetAsync(g.sep_off, 0xff, pp * sizeof(long long), s));
+    CK(cudaMemsetAsync(g.ctr, 0, sizeof(DevCounters), s));
+    CK(cudaMemsetAsync(g.info, 0, sizeof(LevelInfo), s));
+    CK(cudaMemsetAsync(h->singular, 0, sizeof(int), s));
+    const int cap = level_cap(h);
+    int levels = 0, first = -1, stage_a_ran = 0;
+    auto largest_pool = [&](int *out) -> pc_status {
+        CK(fpc::launch_pp_components(g, h->pp_comp, s));
+        CK(cudaMemsetAsync(h->pp_max, 0xff, sizeof(int), s));
+        CK(fpc::launch_pp_search(g, tp, h->C64, h->ldc, h->pp_comp, 0, 0, h->pp_max, h->budget, s));
+        CK(cudaMemcpyAsync(out, h->pp_max, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        return PC_OK;
+    };
+    auto stage = [&](int l) -> pc_status {
+        if (l + 2 > fpc::DIRECT_MMAX) return fail(h, PC_ERR_BUDGET, "path_pool: a stage beyond l = 158");
+        int status = 0;
+        CK(cudaMemcpyAsync(&status, &g.ctr->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (status) return fail(h, (pc_status)status, "path_pool: a stage would exceed the test budget");
+        CK(cudaMemsetAsync(&g.info->total_direct, 0, sizeof(unsigned long long), s));   // scheduled tests
+        CK(fpc::launch_pp_search(g, tp, h->C64, h->ldc, h->pp_comp, l, 1, h->pp_max, h->budget, s));
+        CK(fpc::launch_pp_commit(g, s));
+        ++levels;
+        if (first < 0) first = l;
+        return PC_OK;
+    };
+    int mp = -1;
+    if (h->order == 0) {
+        for (int l = 0; l <= cap; ++l) {
+            if (pc_status r = largest_pool(&mp)) return r;
+            if (mp < l) break;
+            if (pc_status r = stage(l)) return r;
+        }
+    } else {
+        if (h->stage_a && n - p - 1 > 0) {
+            // the closed-form stage l = p-2 on the complete graph (its only set is V\{u,v})
+            CK(fpc::launch_level_degrees(g, s));
+            CK(fpc::launch_tail(g, tp, cap, 2, h->singular, 0, h->hcond, 0, fpc::StageConds{}, s));
+            CK(cudaMemcpyAsync(h->Pbuf, h->C64, (size_t)p * h->ldc * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            CK(fpc::launch_inverse_spd(h->Pbuf, p, h->ldc, h->work, h->singular, s));
+            CK(fpc::launch_stage_a_decide(h->Pbuf, p, h->ldc, h->singular, g, tp, s));
+            CK(fpc::launch_commit(g, h->opair_cap, p - 2, 0, s));
+            int sing = 0;
+            CK(cudaMemcpyAsync(&sing, h->singular, sizeof(int), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            stage_a_ran = sing ? 0 : 1;
+            levels += stage_a_ran;
+        }
+        int l = cap;
+        if (stage_a_ran && l > p - 3) l = p - 3;
+        if (pc_status r = largest_pool(&mp)) return r;
+        if (mp < l) l = mp;
+        while (l >= 0) {
+            if (pc_status r = stage(l)) return r;
+            if (pc_status r = largest_pool(&mp)) return r;
+            l = std::min(l - 1, mp);
+        }
+    }
+    CK(cudaEventRecord(h->ev1, s));
+    DevCounters c;
+    CK(cudaMemcpyAsync(&c, g.ctr, sizeof(c), cudaMemcpyDeviceToHost, s));
+    if (pc_status r = read_info(h)) return r;
+    if (h->info_h->pool_overflow) {
+        *overflow = true;
+        return PC_OK;
+    }
+    if (c.status) return fail(h, (pc_status)c.status, "device-side error in the path-pool search");
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+    st->tests_executed = c.tests_executed;
+    st->tests_canonical = c.tests_canonical;
+    st->degenerate = c.degenerate;
+    st->tests_redecided = 0;
+    st->edges_removed = c.edges_removed;
+    st->edges_kept = (uint64_t)p * (p - 1) / 2 - c.edges_removed;
+    st->levels_run = levels;
+    st->first_level = first;
+    st->stage_a_ran = stage_a_ran;
+    st->t_skeleton_ms = ms;
+    return PC_OK;
+}
+
+static pc_status skeleton_pathpool(pc_handle *h, pc_stats *st)
+{
+    for (int attempt = 0; attempt < 6; ++attempt) {
+        bool overflow = false;
+        if (pc_status r = skeleton_pathpool_once(h, st, &overflow)) return r;
+        if (!overflow) return PC_OK;
+        // the sepset pool was too small: enlarge it and run again (deterministic)
+        int *np = nullptr;
+        const long long cap = h->g.pool_cap * 4;
+        CK(dalloc(h, &np, (size_t)cap * sizeof(int)));
+        dfree(h, h->g.pool);
+        h->g.pool = np;
+        h->g.pool_cap = cap;
+    }
+    return fail(h, PC_ERR_INTERNAL, "sepset pool could not be sized");
+}
+
 extern "C" pc_status pc_skeleton(pc_handle *h, uint8_t *adj_out, pc_stats *stats)
 {
     if (!h) return PC_ERR_ARG;
     if (!h->have_corr) return fail(h, PC_ERR_STATE, "pc_skeleton before pc_corr");
     if (pc_status r = check_tc(h)) return r;
     pc_stats st;
-    pc_status r = skeleton_run(h, &st);
+    pc_status r = h->path_pool ? skeleton_pathpool(h, &st) : skeleton_run(h, &st);
     if (r != PC_OK) return r;
     h->last = st;
     h->have_skel = true;

@@ -262,6 +262,11 @@ cudaError_t launch_ci_direct(GraphDev g, TestParams tp, int mmax, const float *C
 cudaError_t launch_ci_complement(GraphDev g, TestParams tp, cudaStream_t s);
 // range: one instantiation (0 .. LANE_RANGES-1) or -1 for all; prop: the
 // variant for handles with a proposal network
+// ---- path-restricted candidate pools (level.cu)
+cudaError_t launch_pp_components(GraphDev g, int *comp, cudaStream_t s);
+cudaError_t launch_pp_search(GraphDev g, TestParams tp, const double *C64, int ldc, const int *comp, int l,
+                             int mode, int *maxpool, double budget, cudaStream_t s);
+cudaError_t launch_pp_commit(GraphDev g, cudaStream_t s);
 cudaError_t launch_ci_lane(GraphDev g, TestParams tp, const float *C32, const double *C64, int ldc,
                            unsigned long long *queue, unsigned long long qcap, unsigned long long *qlen,
                            int range, bool prop, cudaStream_t s);

@@ -475,10 +475,11 @@ __global__ void __launch_bounds__(1024) head_kernel(GraphDev g, TestParams tp, d
             }
         }
     }
-    // owner node of every ordered pair (the small-stage kernel's work items; the commit)
-    for (int u = s0; u < s1; ++u) {
+    // owner node of every ordered pair (the small-stage kernel's work items; the commit):
+    // one warp per node, consecutive entries per lane group (coalesced stores)
+    for (int u = t >> 5; u < p; u += (int)blockDim.x >> 5) {
         const long long b = g.ooff[u];
-        for (int jj = 0, dg = g.deg[u]; jj < dg; ++jj) g.opu[b + jj] = u;
+        for (int jj = t & 31, dg = g.deg[u]; jj < dg; jj += 32) g.opu[b + jj] = u;
     }
     int rounds = 0;
     if (small && tot[0] > 0) {
@@ -946,13 +947,13 @@ __global__ void __launch_bounds__(256) ci_direct_kernel(GraphDev g, TestParams t
 // (l <= LANE_LMAX): one unranking, then lexicographic successors; the
 // (l+2)x(l+2) lower triangle (order S..., u, v) lives in registers and is
 // factored with compile-time indices.  A chunk stops at the first set its pair
-// already beats.  Tests the FP32 error model cannot trust go to a queue that a
+// already beats.  Tests the FP32 trust rule cannot trust go to a queue that a
 // warp-per-test FP64 pass drains before the commit; when the queue is full the
 // direct kernel re-runs the stage.
 
 // Decision of one FP32 test of the small-stage kernel from the trailing 2x2
 // (h11, h12, h22) and the smallest pivot: true = independent (the caller
-// records the key and stops); a test the FP32 error model cannot trust goes
+// records the key and stops); a test the FP32 trust rule cannot trust goes
 // to the FP64 queue.
 // x: pivot of the border member given the prefix (1 without a prefix), bsu/bsv:
 // |its regression coefficients| c_u/x, c_v/x; gs bounds the l1 norm of the
@@ -1044,6 +1045,17 @@ __device__ __forceinline__ int lex_next(int *pos, int d)
         for (int k2 = i + 1; k2 < L; ++k2) pos[k2] = pos[k2 - 1] + 1;
     }
     return i;
+}
+
+// lexicographic successor of pos (l of d positions, l known at run time)
+__device__ __forceinline__ void lex_next_dyn(int *pos, int l, int d)
+{
+    int i = l - 1;
+    while (i >= 0 && pos[i] == d - l + i) --i;
+    if (i >= 0) {
+        ++pos[i];
+        for (int k2 = i + 1; k2 < l; ++k2) pos[k2] = pos[k2 - 1] + 1;
+    }
 }
 
 // Lexicographic order over the candidate list (ascending ids, or the proposal's
@@ -2148,8 +2160,8 @@ __global__ void commit_kernel(GraphDev g, int l_fixed, int explicit_sets, int co
     for (long long base = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); base < nop;
          base += (long long)gridDim.x * blockDim.x) {
         const long long o = base + lane;
-        bool expand = false;
-        int su = 0, jj = 0, dd = 0;
+        bool expand = false, cut = false;                 // cut: this lane removes the edge (u, v)
+        int su = 0, jj = 0, dd = 0, cu_ = 0, cv_ = 0;
         ull rank = 0, off = 0;
         if (o < nop) {
             // owner node: the head kernel's table inside the stage loop, else a search
@@ -2172,8 +2184,9 @@ __global__ void commit_kernel(GraphDev g, int l_fixed, int explicit_sets, int co
                     canon = sat_add(canon, c);
                 }
                 if (key != KEY_NONE) {
-                    atomicAnd(g.adj + (long long)u * g.W + (v >> 5), ~(1u << (v & 31)));
-                    atomicAnd(g.adj + (long long)v * g.W + (u >> 5), ~(1u << (u & 31)));
+                    cut = true;
+                    cu_ = u;
+                    cv_ = v;
                     const int side = (int)(key >> 62);
                     rank = key & ((1ull << 62) - 1);
                     g.sep_level[e] = l;
@@ -2197,6 +2210,16 @@ __global__ void commit_kernel(GraphDev g, int l_fixed, int explicit_sets, int co
                     }
                 }
             }
+        }
+        // adjacency bits of the removed edges: the lanes of a warp hold consecutive
+        // neighbours v of one node u, so their bits in row u share words -- one atomic
+        // per word with the lanes' bits combined; row v's bit u per lane
+        {
+            const long long wu = cut ? (long long)cu_ * g.W + (cv_ >> 5) : -1ll - lane;
+            const unsigned peers = __match_any_sync(0xffffffffu, wu);
+            const unsigned bits = __reduce_or_sync(peers, cut ? 1u << (cv_ & 31) : 0u);
+            if (cut && (int)(__ffs(peers) - 1) == lane) atomicAnd(g.adj + wu, ~bits);
+            if (cut) atomicAnd(g.adj + (long long)cv_ * g.W + (cu_ >> 5), ~(1u << (cu_ & 31)));
         }
         // each lane expands its own removed pair (the pairs of a warp are consecutive
         // neighbours of one node, so removals cluster; one pair at a time per warp
@@ -2262,31 +2285,50 @@ __global__ void __launch_bounds__(256) reverify_kernel(GraphDev g, TestParams tp
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     WarpAcc acc = {0, 0, 0, 0, 0, 0, 0, 0.f};
     ull fails = 0;
-    // pair (a, b), a < b within a's instance: row a of the pair arrays
+    // nothing to re-test when no stage ran in the proposed order
+    if (g.scored) {
+        bool any = false;
+        for (int l = lane; l <= mmax - 2 && l < p; l += 32) any |= g.scored[l] != 0;
+        if (!__any_sync(0xffffffffu, any)) return;
+    }
+    // pair (a, b), a < b within a's instance: row a of the pair arrays, scanned 32
+    // entries at a time by the lanes; the pairs to re-test are taken one by one
     for (long long a_ = gw; a_ < p; a_ += nw)
-    for (int b = (int)a_ + 1, a = (int)a_, bend = g.blk_hi ? g.blk_hi[a] : p; b < bend; ++b) {
-        const long long e = pidx(g, a, b);
-        const int l = g.sep_level[e];
-        const long long off = g.sep_off[e];
-        if (l < 0 || off < 0 || l + 2 > mmax) continue;
-        if (g.scored && !g.scored[l]) continue;        // a plain-order stage: its sepset is canonical
-        if (lane == 0) {
-            for (int i = 0; i < l; ++i) nd[i] = g.pool[off + i];
-            nd[l] = a;
-            nd[l + 1] = b;
+    for (int b0 = (int)a_ + 1, a = (int)a_, bend = g.blk_hi ? g.blk_hi[a] : p; b0 < bend; b0 += 32) {
+        int lb = -1;
+        long long ob = -1;
+        bool need = false;
+        if (b0 + lane < bend) {
+            const long long e = pidx(g, a, b0 + lane);
+            lb = g.sep_level[e];
+            ob = g.sep_off[e];
+            // an explicit set of a stage that ran in the proposed order (a plain-order
+            // stage's set is the canonical one)
+            need = lb >= 0 && ob >= 0 && lb + 2 <= mmax && !(g.scored && !g.scored[lb]);
         }
-        __syncwarp();
-        const double sq = sqrt((double)(n_of(tp, a) - l - 3));
-        double r;
-        float z;
-        // FP32 with the error model's guard and band, FP64 where they require it
-        // (FP64 throughout in the FP64 mode): the warp-per-test evaluation, members
-        // in ascending order, independent of the kernel that found the set
-        const bool ind = tp.precision == 0
-                             ? warp_test<true>(nd, l + 2, l, nullptr, C64, ldc, tp, sq, (float)sq, Mbuf, ms, acc, r, z)
-                             : warp_test<false>(nd, l + 2, l, C32, C64, ldc, tp, sq, (float)sq, Mbuf, ms, acc, r, z);
-        if (!ind) ++fails;
-        __syncwarp();
+        for (unsigned m = __ballot_sync(0xffffffffu, need); m; m &= m - 1) {
+            const int src = __ffs(m) - 1;
+            const int b = b0 + src;
+            const int l = __shfl_sync(0xffffffffu, lb, src);
+            const long long off = __shfl_sync(0xffffffffu, ob, src);
+            if (lane == 0) {
+                for (int i = 0; i < l; ++i) nd[i] = g.pool[off + i];
+                nd[l] = a;
+                nd[l + 1] = b;
+            }
+            __syncwarp();
+            const double sq = sqrt((double)(n_of(tp, a) - l - 3));
+            double r;
+            float z;
+            // FP32 under the trust rule (guard, bound, band), FP64 where it requires it
+            // (FP64 throughout in the FP64 mode): the warp-per-test evaluation, members
+            // in ascending order, independent of the kernel that found the set
+            const bool ind = tp.precision == 0
+                                 ? warp_test<true>(nd, l + 2, l, nullptr, C64, ldc, tp, sq, (float)sq, Mbuf, ms, acc, r, z)
+                                 : warp_test<false>(nd, l + 2, l, C32, C64, ldc, tp, sq, (float)sq, Mbuf, ms, acc, r, z);
+            if (!ind) ++fails;
+            __syncwarp();
+        }
     }
     if (lane == 0 && fails) g.ctr->status = 8;
 }
@@ -2358,6 +2400,262 @@ static int num_sms()
         if (g_num_sms <= 0) g_num_sms = 148;
     }
     return g_num_sms;
+}
+
+// ---------------------------------------------------------------- path-restricted pools
+// The candidate pool adj(G,i,j) intersected with path(G,i,j) of Algorithms 1 and 2
+// (Sec. 2.1 notation): the neighbours of i or of j, other than i and j, that lie
+// on some simple i-j path of the frozen graph.  A neighbour k of i lies on one iff
+// k reaches j in the graph without i (then i, k, ..., j is such a path), a
+// neighbour of j iff it reaches i without j.  comp[x * p + k] labels the
+// connected component of k in the frozen graph without node x (-1 at k = x); one
+// CTA per x, by frontier expansion over the adjacency bitset in shared memory.
+// The labels' values do not matter, only their equality.
+__global__ void __launch_bounds__(256) pp_components_kernel(GraphDev g, int *comp)
+{
+    extern __shared__ unsigned pp_bits[];
+    const int p = g.p, W = g.W, x = blockIdx.x;
+    unsigned *vis = pp_bits, *front = pp_bits + W, *nxt = pp_bits + 2 * W;
+    __shared__ int start_s;
+    int *cx = comp + (long long)x * p;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int w = threadIdx.x; w < W; w += blockDim.x) {
+        // nodes >= p and x itself count as visited
+        unsigned v = 0;
+        for (int b = 0; b < 32; ++b)
+            if (w * 32 + b >= p || w * 32 + b == x) v |= 1u << b;
+        vis[w] = v;
+    }
+    if (threadIdx.x == 0) cx[x] = -1;
+    __syncthreads();
+    for (int id = 0;; ++id) {
+        // the lowest node not yet labelled starts the next component
+        if (threadIdx.x == 0) {
+            int st = -1;
+            for (int w = 0; w < W && st < 0; ++w)
+                if (~vis[w]) st = w * 32 + __ffs(~vis[w]) - 1;
+            start_s = st;
+        }
+        __syncthreads();
+        const int st = start_s;
+        if (st < 0) break;
+        for (int w = threadIdx.x; w < W; w += blockDim.x) front[w] = w == (st >> 5) ? 1u << (st & 31) : 0u;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            vis[st >> 5] |= 1u << (st & 31);
+            cx[st] = id;
+        }
+        __syncthreads();
+        for (;;) {
+            for (int w = threadIdx.x; w < W; w += blockDim.x) nxt[w] = 0u;
+            __syncthreads();
+            // every frontier node y: OR its adjacency row into nxt (a warp per word of front)
+            for (int fw = warp; fw < W; fw += nwarps) {
+                unsigned f = front[fw];
+                while (f) {
+                    const int y = fw * 32 + __ffs(f) - 1;
+                    f &= f - 1;
+                    const uint32_t *row = g.adj + (long long)y * W;
+                    for (int w = lane; w < W; w += 32) {
+                        const unsigned a = row[w];
+                        if (a) atomicOr(&nxt[w], a);
+                    }
+                }
+            }
+            __syncthreads();
+            int more = 0;
+            for (int w = threadIdx.x; w < W; w += blockDim.x) {
+                const unsigned nw = nxt[w] & ~vis[w];
+                front[w] = nw;
+                vis[w] |= nw;
+                more |= nw != 0;
+                for (unsigned m = nw; m; m &= m - 1) cx[w * 32 + __ffs(m) - 1] = id;
+            }
+            if (!__syncthreads_or(more)) break;
+        }
+    }
+}
+
+// The pool of the adjacent pair (a, b), ascending, into pool (one warp); returns its size.
+__device__ __forceinline__ int pp_pool(const GraphDev &g, const int *comp, int a, int b, int *pool)
+{
+    const int p = g.p, lane = threadIdx.x & 31;
+    const int *ca = comp + (long long)a * p, *cb = comp + (long long)b * p;
+    const int la = ca[b], lb = cb[a];
+    int dp = 0;
+    for (int k0 = 0; k0 < p; k0 += 32) {
+        const int k = k0 + lane;
+        bool on = false;
+        if (k < p && k != a && k != b) {
+            const bool adj_a = (g.adj[(long long)a * g.W + (k >> 5)] >> (k & 31)) & 1u;
+            const bool adj_b = (g.adj[(long long)b * g.W + (k >> 5)] >> (k & 31)) & 1u;
+            on = (adj_a && ca[k] == la) || (adj_b && cb[k] == lb);
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, on);
+        if (on) pool[dp + __popc(m & ((1u << lane) - 1))] = k;
+        dp += __popc(m);
+    }
+    __syncwarp();
+    return dp;
+}
+
+// The adjacent pairs (a, b), a < b, one warp each: node a of the warp by a
+// grid-stride over the nodes, then a's neighbours b > a in turn.
+//   mode 0: the largest pool into *maxpool (the schedule's L*)
+//   mode 1: stage l -- the pool's l-subsets in lexicographic order of positions in
+//           the ascending pool (side 0), each an FP64 test by the warp; the first
+//           independent one is the pair's separating set: key best[e] = rank,
+//           level, side, rank and the explicit set recorded (the deletion waits for
+//           the end of the stage, PC-stable).
+// A stage whose scheduled tests (the sum of C(|pool|, l) over the pairs reached)
+// pass `budget` stops with PC_ERR_BUDGET: pairs not yet started are skipped.
+__global__ void __launch_bounds__(256) pp_search_kernel(GraphDev g, TestParams tp, const double *C64, int ldc,
+                                                        const int *comp, int l, int mode, int *maxpool, int mmax,
+                                                        int ms, int per_warp_bytes, double budget)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    unsigned char *mine = smem_raw + (size_t)wib * per_warp_bytes;
+    double *Mbuf = (double *)mine;
+    int *nd = (int *)(mine + (size_t)mmax * ms * sizeof(double));
+    int *pos = nd + mmax;
+    int *pool = pos + mmax;                              // p entries
+    const int p = g.p, W = g.W;
+    const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const double sq = sqrt((double)(tp.n - l - 3));
+    WarpAcc acc = {0, 0, 0, 0, 0, 0, 0, 0.f};
+    int best_dp = -1;
+    for (long long a_ = gw; a_ < p; a_ += nw) {
+        const int a = (int)a_;
+        for (int w = (a + 1) >> 5; w < W; ++w) {
+            unsigned bits = g.adj[(long long)a * W + w];
+            if (w == ((a + 1) >> 5)) bits &= ~0u << ((a + 1) & 31);
+            while (bits) {
+                const int b = w * 32 + __ffs(bits) - 1;
+                bits &= bits - 1;
+                const int dp = pp_pool(g, comp, a, b, pool);
+                if (mode == 0) {
+                    best_dp = max(best_dp, dp);
+                    continue;
+                }
+                if (dp < l || l + 2 > mmax) continue;
+                const ull T = g.binom[(long long)dp * g.ldb + l];
+                ull sched = 0;
+                if (lane == 0) sched = atomicAdd(&g.info->total_direct, T) + T;
+                sched = __shfl_sync(0xffffffffu, sched, 0);
+                if (T == KEY_NONE || (double)sched > budget || g.ctr->status) {
+                    if (lane == 0) atomicExch(&g.ctr->status, 6);   // PC_ERR_BUDGET
+                    continue;
+                }
+                if (lane == 0)
+                    for (int i = 0; i < l; ++i) pos[i] = i;
+                __syncwarp();
+                const long long e = pidx(g, a, b);
+                for (ull rank = 0; rank < T; ++rank) {
+                    if (lane == 0) {
+                        for (int i = 0; i < l; ++i) nd[i] = pool[pos[i]];
+                        nd[l] = a;
+                        nd[l + 1] = b;
+                    }
+                    __syncwarp();
+                    double r;
+                    float z;
+                    ++acc.tests;
+                    const bool ind = warp_test<true>(nd, l + 2, l, nullptr, C64, ldc, tp, sq, (float)sq, Mbuf, ms,
+                                                     acc, r, z);
+                    if (ind) {
+                        if (lane == 0) {
+                            const ull off = atomicAdd(&g.ctr->pool_len, (ull)l);
+                            g.best[e] = rank;
+                            g.sep_level[e] = l;
+                            g.sep_side[e] = 0;
+                            g.sep_rank[e] = (long long)rank;
+                            g.sep_off[e] = (long long)off;
+                            if ((long long)(off + l) > g.pool_cap) {
+                                g.info->pool_overflow = 1;   // the host enlarges the pool and reruns
+                            } else {
+                                for (int i = 0; i < l; ++i) g.pool[off + i] = nd[i];
+                            }
+                        }
+                        __syncwarp();
+                        break;
+                    }
+                    if (lane == 0) lex_next_dyn(pos, l, dp);
+                    __syncwarp();
+                }
+            }
+        }
+    }
+    if (mode == 0) {
+        for (int off = 16; off > 0; off >>= 1) best_dp = max(best_dp, __shfl_xor_sync(0xffffffffu, best_dp, off));
+        if (lane == 0 && best_dp >= 0) atomicMax(maxpool, best_dp);
+        return;
+    }
+    if (lane == 0) {
+        flush_acc(acc, g.ctr);
+        if (acc.tests) atomicAdd(&g.ctr->tests_canonical, acc.tests);
+    }
+}
+
+// End of a path-pool stage: every pair with a recorded key loses its edge.
+__global__ void pp_commit_kernel(GraphDev g)
+{
+    const int p = g.p;
+    ull removed = 0;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)p * p;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int a = (int)(t / p), b = (int)(t - (long long)a * p);
+        if (b <= a) continue;
+        const long long e = pidx(g, a, b);
+        if (g.best[e] == KEY_NONE) continue;
+        g.best[e] = KEY_NONE;
+        atomicAnd(g.adj + (long long)a * g.W + (b >> 5), ~(1u << (b & 31)));
+        atomicAnd(g.adj + (long long)b * g.W + (a >> 5), ~(1u << (a & 31)));
+        ++removed;
+    }
+    if (removed) atomicAdd(&g.ctr->edges_removed, removed);
+}
+
+cudaError_t launch_pp_components(GraphDev g, int *comp, cudaStream_t s)
+{
+    pp_components_kernel<<<g.p, 256, (size_t)3 * g.W * sizeof(unsigned), s>>>(g, comp);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// per-warp shared memory of the search: the (l+2) x (l+2) FP64 matrix, the test's
+// node ids, the set positions and the pool (p ids)
+static size_t pp_per_warp(int mmax, int p, int &ms)
+{
+    ms = mmax + 1;
+    return ((size_t)mmax * ms * sizeof(double) + (2 * (size_t)mmax + (size_t)p) * sizeof(int) + 15) / 16 * 16;
+}
+
+cudaError_t launch_pp_search(GraphDev g, TestParams tp, const double *C64, int ldc, const int *comp, int l,
+                             int mode, int *maxpool, double budget, cudaStream_t s)
+{
+    const int mmax = std::max(2, std::min(DIRECT_MMAX, l + 2));
+    int ms;
+    const size_t per = pp_per_warp(mmax, g.p, ms);
+    int wpc = 8;
+    while (wpc > 1 && (size_t)wpc * per > 96 * 1024) wpc >>= 1;
+    const size_t smem = (size_t)wpc * per;
+    if (smem > 200 * 1024) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(pp_search_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int blocks = std::max(1, std::min((g.p + wpc - 1) / wpc, num_sms() * 4));
+    pp_search_kernel<<<blocks, wpc * 32, smem, s>>>(g, tp, C64, ldc, comp, l, mode, maxpool, mmax, ms, (int)per,
+                                                    budget);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pp_commit(GraphDev g, cudaStream_t s)
+{
+    pp_commit_kernel<<<num_sms() * 4, 256, 0, s>>>(g);
+    note_launch();
+    return cudaGetLastError();
 }
 
 cudaError_t launch_init_adj(GraphDev g, cudaStream_t s)

@@ -42,10 +42,9 @@ __device__ __forceinline__ int sw128_off(int row, int col_bf16)
 // the FP32 correlation matrix: marginal correlations, first-order partial
 // correlations, the first-order test statistic relative to the threshold,
 // and the stage shape.
-__device__ __forceinline__ void member_features(const float *C, int ldc, const long long *prow, int u, int v, int k,
-                                                int l, int d, float sqn_over_q, float *f)
+__device__ __forceinline__ void member_features_of(float cuv, float cuk, float cvk, int l, int d, float sqn_over_q,
+                                                   float *f)
 {
-    const float cuv = C[cidx(prow, ldc, u, v)], cuk = C[cidx(prow, ldc, u, k)], cvk = C[cidx(prow, ldc, v, k)];
     const float e = 1e-6f;
     const float ruv_k = (cuv - cuk * cvk) * rsqrtf(fmaxf((1.f - cuk * cuk) * (1.f - cvk * cvk), e));
     const float ruk_v = (cuk - cuv * cvk) * rsqrtf(fmaxf((1.f - cuv * cuv) * (1.f - cvk * cvk), e));
@@ -66,6 +65,13 @@ __device__ __forceinline__ void member_features(const float *C, int ldc, const l
     f[13] = (cuv * cuk * cvk > 0.f) ? 1.f : 0.f;
     f[14] = 1.f;
     f[15] = 0.f;
+}
+
+__device__ __forceinline__ void member_features(const float *C, int ldc, const long long *prow, int u, int v, int k,
+                                                int l, int d, float sqn_over_q, float *f)
+{
+    member_features_of(C[cidx(prow, ldc, u, v)], C[cidx(prow, ldc, u, k)], C[cidx(prow, ldc, v, k)], l, d,
+                       sqn_over_q, f);
 }
 
 // Packs the FP32 master parameters into the swizzled BF16 B-operand tiles of
@@ -100,25 +106,53 @@ struct MlpRows {
     float inv_q;
 };
 
-__device__ __forceinline__ void row_features(const MlpRows &R, const GraphDev &g, long long row, float *f)
+// A candidate row of the current stage: node u (tracked by the caller, which
+// walks it forward over consecutive rows), the pair's v, the candidate k.
+struct RowRef {
+    int u, v, k, d;
+    bool ok;
+};
+
+__device__ __forceinline__ RowRef locate_row(const MlpRows &R, const GraphDev &g, long long row, long long nrows,
+                                             int &ucur)
 {
-    if (R.feats) {
-#pragma unroll
-        for (int i = 0; i < NF; ++i) f[i] = R.feats[row * NF + i];
-        return;
-    }
-    const int p = g.p, l = g.info->l;
-    const int u = (int)(upper_bound_dev(R.row_off, (long long)p + 1, (unsigned long long)row) - 1);
-    const int dg = g.deg[u], d = dg - 1;
+    RowRef r{0, 0, 0, 0, row < nrows};
+    if (!r.ok) return r;
+    while ((long long)R.row_off[ucur + 1] <= row) ++ucur;
+    const int u = ucur, d = g.deg[u] - 1;
     const long long w = row - (long long)R.row_off[u];
     const int j = (int)(w / d), x = (int)(w - (long long)j * d);
-    const int v = g.nbr[nidx(g, u) + j];
-    const int k = g.nbr[nidx(g, u) + x + (x >= j)];
-    const float sq = R.nvec ? sqrtf((float)R.nvec[u]) * R.inv_q : R.sqn_over_q;
-    member_features(R.C32, R.ldc, g.prow, u, v, k, l, d, sq, f);
+    const int *nb = g.nbr + nidx(g, u);
+    r.u = u;
+    r.d = d;
+    r.v = nb[j];
+    r.k = nb[x + (x >= j)];
+    return r;
+}
+
+// The correlations a row's features need (loaded one tile ahead of use).
+struct RowVals {
+    float cuv, cuk, cvk, sq;
+    int d;
+    bool ok;
+};
+
+__device__ __forceinline__ RowVals fetch_row(const MlpRows &R, const GraphDev &g, const RowRef &r)
+{
+    RowVals x{0.f, 0.f, 0.f, 0.f, r.d, r.ok};
+    if (!r.ok) return x;
+    x.cuv = R.C32[cidx(g.prow, R.ldc, r.u, r.v)];
+    x.cuk = R.C32[cidx(g.prow, R.ldc, r.u, r.k)];
+    x.cvk = R.C32[cidx(g.prow, R.ldc, r.v, r.k)];
+    x.sq = R.nvec ? sqrtf((float)R.nvec[r.u]) * R.inv_q : R.sqn_over_q;
+    return x;
 }
 
 // Forward pass over rows [0, R): scores s, and for training h1 (BF16), h2 (FP32).
+// Each CTA takes a contiguous range of 128-row tiles.  For the rows of the
+// current stage the next tile's indices are located while the first product
+// runs and its correlations are requested before the second product's wait,
+// so the gathers overlap the tensor-core work and the epilogues.
 __global__ void __launch_bounds__(128, 2) mlp_forward_kernel(MlpRows rows, GraphDev g, const uint8_t *wpack,
                                                              const float *theta, float *scores,
                                                              __nv_bfloat16 *h1_out, float *h2_out, int *err)
@@ -130,16 +164,17 @@ __global__ void __launch_bounds__(128, 2) mlp_forward_kernel(MlpRows rows, Graph
     __shared__ uint32_t tmem_base;
     __shared__ float b1[NH], b2[NH], w3[NH];
     __shared__ float b3;
-    __shared__ long long nrows;
     const int tid = threadIdx.x, warp = tid >> 5;
     if (!rows.feats && (g.info->done || g.info->halt)) return;
-    // a stage without proposal rows (or a CTA past the last tile) leaves before
+    const long long R = rows.feats ? rows.R : (long long)rows.row_off[g.p];
+    const long long ntiles = (R + T_ROWS - 1) / T_ROWS;
+    const long long tb = ntiles * blockIdx.x / gridDim.x, te = ntiles * (blockIdx.x + 1) / gridDim.x;
+    // a stage without proposal rows (or a CTA without tiles) leaves before
     // loading the weights and allocating tensor memory
-    if (!rows.feats && (long long)blockIdx.x * T_ROWS >= (long long)rows.row_off[g.p]) return;
+    if (tb >= te) return;
     if (tid == 0) {
         mbar_init(&bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        nrows = rows.feats ? rows.R : (long long)rows.row_off[g.p];
     }
     // weights (pre-swizzled) and vectors into shared memory; A1 zero-filled once
     for (int i = tid; i < (W1_TILE + 2 * W2_TILE) / 16; i += blockDim.x)
@@ -158,16 +193,33 @@ __global__ void __launch_bounds__(128, 2) mlp_forward_kernel(MlpRows rows, Graph
     const uint32_t tmem = tmem_base, d1 = tmem, d2 = tmem + 128;
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
     constexpr uint32_t idesc = idesc_bf16_f32(128, 128);
-    const long long R = nrows;
+    const int l = rows.feats ? 0 : g.info->l;
     unsigned phase = 0;
     bool ok = true;
-    for (long long t0 = (long long)blockIdx.x * T_ROWS; t0 < R && ok; t0 += (long long)gridDim.x * T_ROWS) {
-        const long long row = t0 + tid;
+    // the row this thread feeds into the first tile, located and fetched
+    int ucur = 0;
+    RowVals cur{};
+    if (!rows.feats) {
+        const long long r0 = tb * T_ROWS + tid;
+        if (r0 < R) ucur = (int)(upper_bound_dev(rows.row_off, (long long)g.p + 1, (unsigned long long)r0) - 1);
+        cur = fetch_row(rows, g, locate_row(rows, g, r0, R, ucur));
+    }
+    for (long long t = tb; t < te && ok; ++t) {
+        const long long row = t * T_ROWS + tid;
         float f[NF];
-        if (row < R) row_features(rows, g, row, f);
-        else
+        if (rows.feats) {
+            if (row < R)
+#pragma unroll
+                for (int i = 0; i < NF; ++i) f[i] = rows.feats[row * NF + i];
+            else
+#pragma unroll
+                for (int i = 0; i < NF; ++i) f[i] = 0.f;
+        } else if (cur.ok) {
+            member_features_of(cur.cuv, cur.cuk, cur.cvk, l, cur.d, cur.sq, f);
+        } else {
 #pragma unroll
             for (int i = 0; i < NF; ++i) f[i] = 0.f;
+        }
 #pragma unroll
         for (int i = 0; i < NF; ++i) *(__nv_bfloat16 *)(sA1 + sw128_off(tid, i)) = __float2bfloat16_rn(f[i]);
         fence_proxy_async_smem();
@@ -178,6 +230,9 @@ __global__ void __launch_bounds__(128, 2) mlp_forward_kernel(MlpRows rows, Graph
             tc_commit(&bar);
         }
         __syncwarp();
+        // the next tile's row: indices now, correlations before the second wait
+        RowRef nxt{0, 0, 0, 0, false};
+        if (!rows.feats && t + 1 < te) nxt = locate_row(rows, g, row + T_ROWS, R, ucur);
         ok = mbar_wait(&bar, phase);
         phase ^= 1u;
         tc_fence_after();
@@ -202,13 +257,14 @@ __global__ void __launch_bounds__(128, 2) mlp_forward_kernel(MlpRows rows, Graph
         __syncthreads();
         if (tid == 0) {
             tc_fence_after();
-            for (int t = 0; t < 2; ++t)
+            for (int tt = 0; tt < 2; ++tt)
                 for (int ks = 0; ks < 4; ++ks)
-                    tc_mma(d2, sw128_desc(smem_u32(sA2 + t * 128 * 128) + ks * 32),
-                           sw128_desc(smem_u32(sW2 + t * W2_TILE) + ks * 32), idesc, (t | ks) ? 1u : 0u);
+                    tc_mma(d2, sw128_desc(smem_u32(sA2 + tt * 128 * 128) + ks * 32),
+                           sw128_desc(smem_u32(sW2 + tt * W2_TILE) + ks * 32), idesc, (tt | ks) ? 1u : 0u);
             tc_commit(&bar);
         }
         __syncwarp();
+        if (!rows.feats && t + 1 < te) cur = fetch_row(rows, g, nxt);
         ok = ok && mbar_wait(&bar, phase);
         phase ^= 1u;
         tc_fence_after();
@@ -374,30 +430,37 @@ __global__ void adam_kernel(float *theta, const float *grad, float *m, float *v,
 }
 
 // Per ordered pair (u, j) of a node with scored candidates: the permutation of
-// its d candidate positions in descending score (ties: ascending position),
-// by counting ranks (O(d^2 / 32) per lane).  One warp per pair.
+// its d candidate positions in descending score (ties: ascending position), as
+// indices into nbr[u].  One warp per pair (its node from the stage's owner
+// table): each lane holds the scores of positions lane, lane + 32, ... and
+// counts, for each of them, the larger scores broadcast from the other lanes.
 __global__ void perm_kernel(GraphDev g, const unsigned long long *row_off, const float *scores, short *perm)
 {
     if (g.info->done || g.info->halt) return;
     if (row_off[g.p] == 0) return;                     // this stage runs in plain order
-    const int p = g.p;
     const long long npairs = g.info->n_opairs;
     const int lane = threadIdx.x & 31;
     for (long long o = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; o < npairs;
          o += ((long long)gridDim.x * blockDim.x) >> 5) {
-        const int u = (int)(upper_bound_dev(g.ooff, (long long)p + 1, o) - 1);
+        const int u = g.opu[o];
         if (row_off[u + 1] == row_off[u]) continue;
         const int j = (int)(o - g.ooff[u]);
         const int d = g.deg[u] - 1;
         const long long base = (long long)row_off[u] + (long long)j * d;
-        for (int x = lane; x < d; x += 32) {
-            const float sx = scores[base + x];
+        for (int x0 = 0; x0 < d; x0 += 32) {
+            const int x = x0 + lane;
+            const float sx = x < d ? scores[base + x] : 0.f;
             int rank = 0;
-            for (int y = 0; y < d; ++y) {
-                const float sy = scores[base + y];
-                rank += (sy > sx) || (sy == sx && y < x);
+            for (int y0 = 0; y0 < d; y0 += 32) {
+                const float sl = y0 + lane < d ? scores[base + y0 + lane] : 0.f;
+                const int ny = d - y0 < 32 ? d - y0 : 32;
+                for (int t = 0; t < ny; ++t) {
+                    const float sy = __shfl_sync(0xffffffffu, sl, t);
+                    const int y = y0 + t;
+                    rank += (sy > sx) || (sy == sx && y < x);
+                }
             }
-            perm[base + rank] = (short)(x + (x >= j));   // index into nbr[u]
+            if (x < d) perm[base + rank] = (short)(x + (x >= j));   // index into nbr[u]
         }
     }
 }
