@@ -330,7 +330,12 @@ pc_status pc_corr_noalloc(const void *X, int32_t dtype, int64_t n, int32_t p, in
  *   s = w3 . h2 + b3; training loss mean BCE(sigmoid(s), y).
  * Parameters: one FP32 vector W1 (128x16 row-major), b1, W2 (128x128), b2, w3,
  * b3 -- pc_mlp_nparam() values.  Forward on the tensor cores in BF16 with FP32
- * accumulation; backward and Adam in FP32. */
+ * accumulation.  Backward (option "mlp_backward" 1, default): the products
+ * dL/dh1 = dL/da2 W2, dW2 = (dL/da2)^T h1 and dW1 = (dL/da1)^T x on the tensor
+ * cores with BF16 operands (the back-propagated signals rounded to BF16) and
+ * FP32 accumulation; db1, db2 sum those BF16 signals; dw3, db3 and the loss in
+ * FP32; "mlp_backward" 0: the whole backward in FP32 on the CUDA cores.  Adam
+ * updates FP32 master parameters. */
 int32_t pc_mlp_nparam(void);
 /* theta: host or device, pc_mlp_nparam() floats; resets the Adam state. */
 pc_status pc_mlp_set_params(pc_handle *h, const float *theta, int64_t count);

@@ -63,9 +63,12 @@ def loss(theta, X, y, h1_store=None):
     return float(np.mean(softplus(s) - np.asarray(y, dtype=np.float64) * s))
 
 
-def grad(theta, X, y, h1_store=None) -> np.ndarray:
+def grad(theta, X, y, h1_store=None, dh_store=None) -> np.ndarray:
     """Gradient of loss() by the chain rule written out layer by layer (h1_store as
-    in forward(): the second layer and its weight gradient use the stored h1)."""
+    in forward(): the second layer and its weight gradient use the stored h1).
+    dh_store: optional map applied to the back-propagated signals dL/da2 and
+    dL/da1 (after the ReLU masks) before anything reads them -- the precision a
+    network stores them in for its gradient products (identity if None)."""
     P = unpack(theta)
     X = np.asarray(X, dtype=np.float64)
     y = np.asarray(y, dtype=np.float64)
@@ -76,9 +79,13 @@ def grad(theta, X, y, h1_store=None) -> np.ndarray:
     g["w3"] = h2.T @ ds
     g["b3"] = np.array([ds.sum()])
     dh2 = np.outer(ds, P["w3"]) * (a2 > 0)
+    if dh_store is not None:
+        dh2 = np.asarray(dh_store(dh2), dtype=np.float64)
     g["W2"] = dh2.T @ h1
     g["b2"] = dh2.sum(0)
     dh1 = (dh2 @ P["W2"]) * (a1 > 0)
+    if dh_store is not None:
+        dh1 = np.asarray(dh_store(dh1), dtype=np.float64)
     g["W1"] = dh1.T @ X
     g["b1"] = dh1.sum(0)
     return pack(g)

@@ -129,6 +129,7 @@ struct pc_handle {
     double learned_min = 1.0e6;
     double learned_ratio = 8.0;
     int learned_lmax = 8;
+    int mlp_bwd_tc = 1;    // backward products on the tensor cores (BF16 operands); 0: FP32 CUDA cores
     // per-kernel-class timing
     int timing = 0;
     std::vector<TimedPair> pending;
@@ -562,6 +563,9 @@ extern "C" pc_status pc_set_opt(pc_handle *h, const char *key, double val)
     } else if (k == "lane_blocks") {
         if (!(val >= 1 && val <= 32)) return fail(h, PC_ERR_ARG, "lane_blocks must be in [1, 32]");
         h->lane_blocks = (int)val;
+    } else if (k == "mlp_backward") {
+        if (!(val == 0 || val == 1)) return fail(h, PC_ERR_ARG, "mlp_backward must be 0 or 1");
+        h->mlp_bwd_tc = (int)val;
     } else if (k == "path_pool") {
         if (!(val == 0 || val == 1)) return fail(h, PC_ERR_ARG, "path_pool must be 0 or 1");
         if (val == 1 && h->nblk) return fail(h, PC_ERR_ARG, "path_pool: a batched handle is not supported");
@@ -609,6 +613,7 @@ extern "C" pc_status pc_get_opt(pc_handle *h, const char *key, double *val)
     else if (k == "node_dmax") *val = h->node_dmax;
     else if (k == "pair_warp") *val = h->pair_warp;
     else if (k == "path_pool") *val = h->path_pool;
+    else if (k == "mlp_backward") *val = h->mlp_bwd_tc;
     else if (k == "pair_warp_dmin") *val = h->pair_warp_dmin;
     else if (k == "direct_warps") *val = h->direct_warps;
     else if (k == "tensor_core_gemm") *val = h->used_tc ? 1.0 : 0.0;
@@ -1913,8 +1918,11 @@ extern "C" pc_status pc_mlp_grad(pc_handle *h, const float *feats, const float *
     if (st == PC_OK) {
         cudaError_t e = cudaMemsetAsync(h->mlp_loss, 0, sizeof(double), h->stream);
         if (e == cudaSuccess)
-            e = fpc::launch_mlp_backward(feats, labels, w.scores, w.h1, w.h2, R, 1.0f / (float)R, h->theta, h->grad,
-                                         h->mlp_loss, h->stream);
+            e = h->mlp_bwd_tc
+                    ? fpc::launch_mlp_backward_tc(feats, labels, w.scores, w.h1, w.h2, R, 1.0f / (float)R, h->theta,
+                                                  h->wpack, h->grad, h->mlp_loss, h->mlp_err, h->stream)
+                    : fpc::launch_mlp_backward(feats, labels, w.scores, w.h1, w.h2, R, 1.0f / (float)R, h->theta,
+                                               h->grad, h->mlp_loss, h->stream);
         if (e != cudaSuccess) st = cuda_fail(h, e, "pc_mlp_grad");
     }
     if (st == PC_OK) st = mlp_check_err(h);
@@ -1949,8 +1957,12 @@ extern "C" pc_status pc_mlp_train(pc_handle *h, const float *feats, const float 
             const long long nb = std::min<long long>(B, R - b0);
             st = mlp_forward(h, feats + b0 * 16, nb, w.scores, w.h1, w.h2);
             if (st != PC_OK) break;
-            e = fpc::launch_mlp_backward(feats + b0 * 16, labels + b0, w.scores, w.h1, w.h2, nb, 1.0f / (float)nb,
-                                         h->theta, h->grad, h->mlp_loss, s);
+            e = h->mlp_bwd_tc
+                    ? fpc::launch_mlp_backward_tc(feats + b0 * 16, labels + b0, w.scores, w.h1, w.h2, nb,
+                                                  1.0f / (float)nb, h->theta, h->wpack, h->grad, h->mlp_loss,
+                                                  h->mlp_err, s)
+                    : fpc::launch_mlp_backward(feats + b0 * 16, labels + b0, w.scores, w.h1, w.h2, nb,
+                                               1.0f / (float)nb, h->theta, h->grad, h->mlp_loss, s);
             if (e == cudaSuccess) e = fpc::launch_adam(h->theta, h->grad, h->adam_m, h->adam_v, (float)lr, ++h->adam_step, s);
             if (e == cudaSuccess) e = fpc::launch_mlp_pack(h->theta, h->wpack, s);
         }

@@ -294,6 +294,10 @@ cudaError_t launch_mlp_forward_feats(const float *feats, long long R, const uint
 cudaError_t launch_mlp_score_stage(GraphDev g, const unsigned long long *row_off, long long rows_cap,
                                    const float *C32, int ldc, float sqn_over_q, float inv_q, const uint8_t *wpack,
                                    const float *theta, float *scores, short *perm, int *err, cudaStream_t s);
+cudaError_t launch_mlp_backward_tc(const float *feats, const float *labels, const float *scores,
+                                   const __nv_bfloat16 *h1, const float *h2, long long R, float inv_b,
+                                   const float *theta, const uint8_t *wpack, float *grad, double *loss, int *err,
+                                   cudaStream_t s);
 cudaError_t launch_mlp_backward(const float *feats, const float *labels, const float *scores,
                                 const __nv_bfloat16 *h1, const float *h2, long long R, float inv_b,
                                 const float *theta, float *grad, double *loss, cudaStream_t s);

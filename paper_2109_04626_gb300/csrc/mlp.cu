@@ -76,6 +76,8 @@ __device__ __forceinline__ void member_features(const float *C, int ldc, const l
 
 // Packs the FP32 master parameters into the swizzled BF16 B-operand tiles of
 // W1 (128 x 64, features zero-padded) and W2 (two 128 x 64 K tiles).
+// ... and W2 transposed (rows i, K = o) as the B operand of the backward
+// product dL/dh1 = dL/da2 W2, after the forward's tiles.
 __global__ void mlp_pack_kernel(const float *theta, uint8_t *wpack)
 {
     const int o = blockIdx.x;            // output unit (row of the B operand)
@@ -85,8 +87,10 @@ __global__ void mlp_pack_kernel(const float *theta, uint8_t *wpack)
     }
     for (int c = threadIdx.x; c < NH; c += blockDim.x) {
         const int t = c >> 6;
-        *(__nv_bfloat16 *)(wpack + W1_TILE + t * W2_TILE + sw128_off(o, c & 63)) =
-            __float2bfloat16_rn(theta[OFF_W2 + o * NH + c]);
+        const __nv_bfloat16 w = __float2bfloat16_rn(theta[OFF_W2 + o * NH + c]);
+        *(__nv_bfloat16 *)(wpack + W1_TILE + t * W2_TILE + sw128_off(o, c & 63)) = w;
+        // element (i = c, K = o) of W2^T
+        *(__nv_bfloat16 *)(wpack + W1_TILE + 2 * W2_TILE + (o >> 6) * W2_TILE + sw128_off(c, o & 63)) = w;
     }
 }
 
@@ -415,6 +419,210 @@ __global__ void __launch_bounds__(256) mlp_backward_kernel(const float *feats, c
     }
 }
 
+// Backward pass on the tensor cores: BF16 operands, FP32 accumulators in TMEM.
+// Per 128-row tile of the batch (thread t owns row t):
+//   ds = (sigmoid(s) - y) / B,  dL/da2 = ds w3 (h2 > 0)            (FP32, then BF16)
+//   dL/dh1 = dL/da2 W2  -> masked by h1 > 0                         (tensor core, then BF16)
+//   dW2 += (dL/da2)^T h1,  dW1 += (dL/da1)^T x                      (tensor core, over the tiles)
+// The products contract over the batch rows for the weight gradients, so their
+// operands are written transposed (unit-major, rows along K) into K-major tiles.
+// db2, db1 sum the BF16 signals the products read; dw3, db3 and the loss stay in
+// FP32 from the saved h2.  dW2 and dW1 accumulate in TMEM across the CTA's tiles
+// and are added into grad once per CTA.
+constexpr int BWD_SMEM = 2 * W2_TILE + 4 * 2 * W2_TILE + 2 * 16 * 128 + 1024;
+
+__global__ void __launch_bounds__(128, 1) mlp_backward_tc_kernel(const float *feats, const float *labels,
+                                                                 const float *scores, const __nv_bfloat16 *h1,
+                                                                 const float *h2, long long R, float inv_b,
+                                                                 const float *theta, const uint8_t *wpack,
+                                                                 float *grad, double *loss, int *err)
+{
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *sW2T = smem;                              // B of dh1: rows i, K = o (two K chunks)
+    uint8_t *sAdh2 = sW2T + 2 * W2_TILE;               // A of dh1: rows = batch rows, K = o
+    uint8_t *sTdh2 = sAdh2 + 2 * W2_TILE;              // A of dW2: rows o, K = batch rows
+    uint8_t *sTh1 = sTdh2 + 2 * W2_TILE;               // B of dW2: rows i, K = batch rows
+    uint8_t *sTdh1 = sTh1 + 2 * W2_TILE;               // A of dW1: rows i, K = batch rows
+    uint8_t *sTx = sTdh1 + 2 * W2_TILE;                // B of dW1: rows f (16), K = batch rows
+    constexpr int XCH = 16 * 128;                      // bytes of one K chunk of sTx
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tmem_base;
+    __shared__ float w3s[NH];
+    __shared__ double red[128];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long ntiles = (R + T_ROWS - 1) / T_ROWS;
+    if ((long long)blockIdx.x >= ntiles) return;
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int i = tid; i < 2 * W2_TILE / 16; i += blockDim.x)
+        ((uint4 *)sW2T)[i] = ((const uint4 *)(wpack + W1_TILE + 2 * W2_TILE))[i];
+    for (int i = tid; i < NH; i += blockDim.x) w3s[i] = theta[OFF_W3 + i];
+    if (warp == 0) tc_alloc(&tmem_base, 512);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base, d_dh1 = tmem, d_dW2 = tmem + 128, d_dW1 = tmem + 256;
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    constexpr uint32_t idesc128 = idesc_bf16_f32(128, 128), idesc16 = idesc_bf16_f32(128, 16);
+    unsigned phase = 0;
+    bool ok = true, first = true;
+    float gb1 = 0.f, gb2 = 0.f, gw3[4] = {0.f, 0.f, 0.f, 0.f}, gb3 = 0.f;
+    double lsum = 0.0;
+    for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        const long long r = tile * T_ROWS + tid;
+        const bool valid = r < R;
+        // the output signal and dL/da2 of this thread's row
+        float ds = 0.f;
+        if (valid) {
+            const float sc = scores[r], y = labels[r];
+            ds = (1.f / (1.f + __expf(-sc)) - y) * inv_b;
+            lsum += (double)(fmaxf(sc, 0.f) + log1pf(__expf(-fabsf(sc))) - y * sc);
+        }
+        gb3 += ds;
+#pragma unroll 1
+        for (int c0 = 0; c0 < NH; c0 += 8) {
+            float hv[8];
+            if (valid) {
+                const float4 a = *(const float4 *)(h2 + r * NH + c0), b = *(const float4 *)(h2 + r * NH + c0 + 4);
+                hv[0] = a.x, hv[1] = a.y, hv[2] = a.z, hv[3] = a.w, hv[4] = b.x, hv[5] = b.y, hv[6] = b.z, hv[7] = b.w;
+            } else {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) hv[j] = 0.f;
+            }
+            __align__(16) __nv_bfloat16 db[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int o = c0 + j;
+                db[j] = __float2bfloat16_rn(hv[j] > 0.f ? ds * w3s[o] : 0.f);
+                *(__nv_bfloat16 *)(sTdh2 + (tid >> 6) * W2_TILE + sw128_off(o, tid & 63)) = db[j];
+                // dw3[o] = sum over rows of ds h2[o]: warp sum, kept by lane o mod 32
+                float v = ds * hv[j];
+                for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+                if (lane == (o & 31)) gw3[o >> 5] += v;
+            }
+            *(uint4 *)(sAdh2 + (c0 >> 6) * W2_TILE + sw128_off(tid, c0 & 63)) = *(const uint4 *)db;
+        }
+        // h1 (BF16 as saved) and x (rounded to BF16 as the forward read it), transposed
+#pragma unroll 1
+        for (int c0 = 0; c0 < NH; c0 += 8) {
+            uint4 q = make_uint4(0, 0, 0, 0);
+            if (valid) q = *(const uint4 *)(h1 + r * NH + c0);
+            const __nv_bfloat16 *hb = (const __nv_bfloat16 *)&q;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) *(__nv_bfloat16 *)(sTh1 + (tid >> 6) * W2_TILE + sw128_off(c0 + j, tid & 63)) = hb[j];
+        }
+#pragma unroll
+        for (int f = 0; f < NF; ++f)
+            *(__nv_bfloat16 *)(sTx + (tid >> 6) * XCH + sw128_off(f, tid & 63)) =
+                __float2bfloat16_rn(valid ? feats[r * NF + f] : 0.f);
+        fence_proxy_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            for (int c = 0; c < 2; ++c)
+                for (int ks = 0; ks < 4; ++ks) {
+                    tc_mma(d_dh1, sw128_desc(smem_u32(sAdh2 + c * W2_TILE) + ks * 32),
+                           sw128_desc(smem_u32(sW2T + c * W2_TILE) + ks * 32), idesc128, (c | ks) ? 1u : 0u);
+                    tc_mma(d_dW2, sw128_desc(smem_u32(sTdh2 + c * W2_TILE) + ks * 32),
+                           sw128_desc(smem_u32(sTh1 + c * W2_TILE) + ks * 32), idesc128,
+                           (first && c == 0 && ks == 0) ? 0u : 1u);
+                }
+            tc_commit(&bar);
+        }
+        __syncwarp();
+        ok = mbar_wait(&bar, phase);
+        phase ^= 1u;
+        tc_fence_after();
+        // db2[o = tid]: the BF16 signals of the tile, from the transposed tile
+        {
+            float a = 0.f;
+            for (int k = 0; k < T_ROWS; ++k)
+                a += __bfloat162float(*(const __nv_bfloat16 *)(sTdh2 + (k >> 6) * W2_TILE + sw128_off(tid, k & 63)));
+            gb2 += a;
+        }
+        // dL/da1 = (dL/dh1) masked by h1 > 0, BF16, transposed into the A tile of dW1
+#pragma unroll 1
+        for (int c0 = 0; c0 < NH; c0 += 32) {
+            float v[32];
+            tc_ld_32cols(d_dh1 + lane_base + (uint32_t)c0, v);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int i = c0 + j;
+                const float h = __bfloat162float(*(const __nv_bfloat16 *)(sTh1 + (tid >> 6) * W2_TILE +
+                                                                         sw128_off(i, tid & 63)));
+                *(__nv_bfloat16 *)(sTdh1 + (tid >> 6) * W2_TILE + sw128_off(i, tid & 63)) =
+                    __float2bfloat16_rn(h > 0.f ? v[j] : 0.f);
+            }
+        }
+        fence_proxy_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            for (int c = 0; c < 2; ++c)
+                for (int ks = 0; ks < 4; ++ks)
+                    tc_mma(d_dW1, sw128_desc(smem_u32(sTdh1 + c * W2_TILE) + ks * 32),
+                           sw128_desc(smem_u32(sTx + c * XCH) + ks * 32), idesc16,
+                           (first && c == 0 && ks == 0) ? 0u : 1u);
+            tc_commit(&bar);
+        }
+        __syncwarp();
+        ok = ok && mbar_wait(&bar, phase);
+        phase ^= 1u;
+        tc_fence_after();
+        // db1[i = tid] from the transposed BF16 tile
+        {
+            float a = 0.f;
+            for (int k = 0; k < T_ROWS; ++k)
+                a += __bfloat162float(*(const __nv_bfloat16 *)(sTdh1 + (k >> 6) * W2_TILE + sw128_off(tid, k & 63)));
+            gb1 += a;
+        }
+        first = false;
+        tc_fence_before();
+        __syncthreads();
+    }
+    tc_fence_after();
+    if (ok && !first) {
+        // dW2[o = lane of TMEM][i = column], dW1[i][f]
+#pragma unroll 1
+        for (int c0 = 0; c0 < NH; c0 += 32) {
+            float v[32];
+            tc_ld_32cols(d_dW2 + lane_base + (uint32_t)c0, v);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) atomicAdd(&grad[OFF_W2 + tid * NH + c0 + j], v[j]);
+        }
+        {
+            float v[32];
+            tc_ld_32cols(d_dW1 + lane_base, v);
+#pragma unroll
+            for (int f = 0; f < NF; ++f) atomicAdd(&grad[OFF_W1 + tid * NF + f], v[f]);
+        }
+        atomicAdd(&grad[OFF_B1 + tid], gb1);
+        atomicAdd(&grad[OFF_B2 + tid], gb2);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) atomicAdd(&grad[OFF_W3 + k * 32 + lane], gw3[k]);
+    }
+    for (int off = 16; off > 0; off >>= 1) gb3 += __shfl_xor_sync(0xffffffffu, gb3, off);
+    if (lane == 0) atomicAdd(&grad[OFF_B3], gb3);
+    if (loss) {
+        red[tid] = lsum;
+        __syncthreads();
+        for (int s2 = 64; s2 > 0; s2 >>= 1) {
+            if (tid < s2) red[tid] += red[tid + s2];
+            __syncthreads();
+        }
+        if (tid == 0) atomicAdd(loss, red[0]);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tc_dealloc(tmem, 512);
+    if (!ok && tid == 0) atomicExch(err, 7);   // a bounded wait expired
+}
+
 // Adam (Kingma & Ba): m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
 // theta -= lr * mhat / (sqrt(vhat) + eps).
 __global__ void adam_kernel(float *theta, const float *grad, float *m, float *v, int n, float lr, float bc1,
@@ -467,7 +675,7 @@ __global__ void perm_kernel(GraphDev g, const unsigned long long *row_off, const
 
 // ---------------------------------------------------------------- host side
 int mlp_nparam() { return NPARAM; }
-size_t mlp_pack_bytes() { return (size_t)W1_TILE + 2 * W2_TILE; }
+size_t mlp_pack_bytes() { return (size_t)W1_TILE + 4 * W2_TILE; }
 
 cudaError_t launch_mlp_pack(const float *theta, uint8_t *wpack, cudaStream_t s)
 {
@@ -531,6 +739,21 @@ cudaError_t launch_mlp_score_stage(GraphDev g, const unsigned long long *row_off
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     perm_kernel<<<sms * 4, 256, 0, s>>>(g, row_off, scores, perm);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_backward_tc(const float *feats, const float *labels, const float *scores,
+                                   const __nv_bfloat16 *h1, const float *h2, long long R, float inv_b,
+                                   const float *theta, const uint8_t *wpack, float *grad, double *loss, int *err,
+                                   cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(grad, 0, NPARAM * sizeof(float), s);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(mlp_backward_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, BWD_SMEM);
+    if (e != cudaSuccess) return e;
+    mlp_backward_tc_kernel<<<mlp_ctas(R), 128, BWD_SMEM, s>>>(feats, labels, scores, h1, h2, R, inv_b, theta, wpack,
+                                                              grad, loss, err);
     note_launch();
     return cudaGetLastError();
 }

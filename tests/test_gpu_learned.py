@@ -61,9 +61,11 @@ def test_forward_matches_reference(fp, R):
     pc.close()
 
 
-@pytest.mark.parametrize("R", [1, 300, 3001])
-def test_gradient_matches_reference_elementwise(fp, R):
+@pytest.mark.parametrize("backward", [0, 1], ids=["fp32_cuda_cores", "bf16_tensor_cores"])
+@pytest.mark.parametrize("R", [1, 300, 3001, 20000])
+def test_gradient_matches_reference_elementwise(fp, R, backward):
     pc = _handle(fp)
+    fp.pc_set_opt(pc.h, "mlp_backward", backward)
     theta = (mlp.init(12) * 0.5).astype(np.float32)
     fp.pc_mlp_set_params(pc.h, theta)
     rng = np.random.default_rng(4 + R)
@@ -71,22 +73,45 @@ def test_gradient_matches_reference_elementwise(fp, R):
     y = (rng.random(R) < 0.3).astype(np.float32)
     g, loss = fp.pc_mlp_grad(pc.h, torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda())
     # FP64 reference at the parameters and roundings the GPU uses: BF16 inputs,
-    # BF16 W1 and W2, and h1 stored in BF16 (the second layer's operand)
+    # BF16 W1 and W2, h1 stored in BF16 (the second layer's operand) and, on the
+    # tensor-core backward, the back-propagated signals stored in BF16 (the
+    # operands of its products, formed in FP32 first)
     P = mlp.unpack(theta.astype(np.float64))
     P["W1"], P["W2"] = bf16(P["W1"]), bf16(P["W2"])
-    gr = mlp.grad(mlp.pack(P), bf16(X), y, h1_store=bf16)
+    dh_store = (lambda a: bf16(np.asarray(a, np.float32))) if backward else None
+    gr = mlp.grad(mlp.pack(P), bf16(X), y, h1_store=bf16, dh_store=dh_store)
     lr = mlp.loss(mlp.pack(P), bf16(X), y, h1_store=bf16)
     assert abs(loss - lr) <= 1e-5 * abs(lr) + 1e-7
     # element by element, per parameter block: the GPU accumulates in FP32 (in
-    # another order) where the reference accumulates in FP64
+    # another order) where the reference accumulates in FP64; with BF16 signals an
+    # element whose FP32 and FP64 values round to neighbouring BF16 numbers moves
+    # its products by one BF16 step (2^-8), hence the wider band there
+    rtol, atol = (1e-3, 1e-4) if backward == 0 else (4e-3, 4e-4)
     o = 0
     for name, shape in mlp.SIZES:
         k = int(np.prod(shape))
         gb, rb = g[o:o + k].astype(np.float64), gr[o:o + k]
         scale = float(np.abs(rb).max())
-        np.testing.assert_allclose(gb, rb, rtol=1e-3, atol=1e-4 * scale + 1e-9, err_msg=name)
+        np.testing.assert_allclose(gb, rb, rtol=rtol, atol=atol * scale + 1e-9, err_msg=name)
         o += k
     pc.close()
+
+
+def test_tensor_core_and_fp32_backward_train_alike(fp):
+    # the two backward paths give the same training curve to BF16 accuracy
+    rng = np.random.default_rng(21)
+    X = rng.uniform(0, 1, (30000, 16)).astype(np.float32)
+    y = ((X[:, 2] - 0.5 * X[:, 5] + 0.3 * X[:, 9]) > 0.3).astype(np.float32)
+    Xt, yt = torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda()
+    losses = []
+    for backward in (0, 1):
+        pc = _handle(fp)
+        fp.pc_set_opt(pc.h, "mlp_backward", backward)
+        fp.pc_mlp_set_params(pc.h, proposal.initial_params(2))
+        fp.pc_mlp_train(pc.h, Xt, yt, 4, 2048, 3e-3)
+        losses.append(fp.pc_mlp_grad(pc.h, Xt, yt)[1])
+        pc.close()
+    assert losses[1] < 0.3 and abs(losses[1] - losses[0]) <= 0.1 * losses[0], losses
 
 
 def test_training_reduces_loss(fp):

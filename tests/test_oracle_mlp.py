@@ -1,6 +1,7 @@
 """Pins for the FP64 reference of the proposal network: the hand-written
 backward pass agrees with central finite differences of the loss."""
 import numpy as np
+import pytest
 
 from oracle import mlp
 
@@ -56,3 +57,31 @@ def test_stored_h1_gradient_matches_finite_differences():
         tm[i] -= h
         fd = (mlp.loss(tp, X, y, h1_store=store) - mlp.loss(tm, X, y, h1_store=store)) / (2 * h)
         assert abs(fd - g[i]) <= 1e-6 + 1e-5 * abs(fd), (i, fd, g[i])
+
+
+def test_stored_signals_identity_map_is_the_gradient():
+    # the backward-signal storage map at the identity gives the exact gradient
+    # (pinned above by finite differences); any other map is applied as stated
+    rng = np.random.default_rng(7)
+    theta = mlp.init(5) * 0.5
+    X = rng.standard_normal((25, mlp.NF))
+    y = (rng.random(25) < 0.5).astype(float)
+    np.testing.assert_array_equal(mlp.grad(theta, X, y, dh_store=lambda a: a), mlp.grad(theta, X, y))
+    g0 = mlp.grad(theta, X, y, dh_store=lambda a: np.zeros_like(a))
+    P = mlp.unpack(g0)
+    assert not P["W2"].any() and not P["W1"].any() and not P["b1"].any()   # nothing flows past a2
+    assert P["w3"].any()                                                     # the last layer does not read them
+
+
+def test_bf16_rounding_of_the_tests_equals_torch():
+    # the BF16 rounding the GPU tests apply to their references (nearest, ties to
+    # even) is torch's own conversion
+    torch = pytest.importorskip("torch")
+    import sys, os
+    sys.path.insert(0, os.path.dirname(__file__))
+    from test_gpu_learned import bf16
+    rng = np.random.default_rng(8)
+    x = np.concatenate([rng.standard_normal(5000) * 10.0 ** rng.integers(-6, 6, 5000),
+                        np.array([1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, -(1.0 + 2 ** -8), 0.0])]).astype(np.float32)
+    ref = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(bf16(x), ref)
