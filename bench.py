@@ -79,7 +79,7 @@ def measured_peaks():
 # capture of the current kernels (the profile summary of that workload and
 # kernel gives the command and the per-launch figures); absent: not captured
 # since the kernels last changed (the roofline's traffic is then null)
-DRAM_BYTES_PER_LAUNCH = {}
+DRAM_BYTES_PER_LAUNCH = {("p1000_er", "ci_direct"): 1.677e7}
 
 
 def parse():
@@ -107,6 +107,9 @@ def parse():
                     help="time only pc_corr (standardise + tensor-core correlation GEMM) on the workload")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch shape of the test kernels (no pc_autotune)")
+    ap.add_argument("--opt", action="append", default=[], metavar="KEY=VALUE",
+                    help="a handle option (pc_set_opt) for the timed handle, e.g. pair_warp=0 or node_dmax=0; "
+                         "repeatable")
     ap.add_argument("--graph", type=int, default=1,
                     help="1: stage loop as one CUDA graph (default); 0: host-driven launches "
                          "(for ncu launch lists, which do not enter conditional graph bodies)")
@@ -382,6 +385,9 @@ def run_ours(args):
 
     mixed_prec = 0 if w["cfg"] == 1 else 2
     pc = make(mixed_prec, 1, graph=args.graph)
+    for kv in args.opt:
+        key, val = kv.split("=", 1)
+        fp.pc_set_opt(pc.h, key.strip(), float(val))
     adj_d = torch.empty((p, p), dtype=torch.uint8, device=dev)
 
     def step(pcx):
@@ -607,7 +613,8 @@ def run_ours(args):
                            "tensor_core_gemm": bool(fp.pc_get_opt(pc.h, "tensor_core_gemm")),
                            "learned_order": learned is not None,
                            "parallelism": f"replicas x{world}",
-                           "l2": "flushed before every step (512 MB write)"},
+                           "l2": "flushed before every step (512 MB write)",
+                           "options": list(args.opt)},
                 "tests_canonical_per_step": tests_unit,
                 "tests_executed_per_step": stats[-1]["tests_executed"],
                 "skeleton_ms": float(np.mean([x["t_skeleton_ms"] for x in stats])),
