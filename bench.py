@@ -647,11 +647,13 @@ MANY = {"name": "many64", "count": 64, "alpha": 0.01, "max_level": -1, "order": 
 
 
 def run_many(args):
-    """64 independent problems: every handle's pc_corr on its own stream, then all
-    skeleton searches concurrently (pc_skeleton_many); beside it the same problems
-    in one batched handle (pc_create_batch: one launch sequence per stage)."""
+    """64 independent problems in one batched handle (pc_create_batch: block-diagonal
+    layout, every stage one launch sequence over all instances' tests), mixed
+    precision, the proposal order behind the autotuned scoring gate -- the timed
+    configuration; beside it the same problems as 64 handles searched concurrently
+    on 16 streams (pc_skeleton_many)."""
     import torch
-    from paper_2109_04626_gb300 import fastpc as fp, sem
+    from paper_2109_04626_gb300 import fastpc as fp, proposal, sem
     rank, world, local = dist_setup(args)
     fp.load()
     inst = sem.make_many(MANY["count"])
@@ -661,29 +663,6 @@ def run_many(args):
     Xd = [torch.from_numpy(s_.X).to(dev) for s_ in inst]
     main_s = torch.cuda.current_stream()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    streams = [torch.cuda.Stream() for _ in range(MANY["streams"])]
-    pcs = []
-    for i in range(len(inst)):
-        pc = fp.PC(ns[i], ps[i], MANY["alpha"], MANY["max_level"], order=0, precision=2)
-        fp.pc_set_stream(pc.h, streams[i % len(streams)])
-        pcs.append(pc)
-    hs = [pc.h for pc in pcs]
-
-    def step(Xs, adj=False):
-        ev = torch.cuda.Event()
-        ev.record(main_s)
-        for st in streams:
-            st.wait_event(ev)
-        for i, pc in enumerate(pcs):
-            pc.corr(Xs[i])
-        adjs, stats, status = fp.pc_skeleton_many(hs, ps, adj_out=adj)
-        if any(status):
-            raise RuntimeError(f"pc_skeleton_many: statuses {status}")
-        for st in streams:
-            e2 = torch.cuda.Event()
-            e2.record(st)
-            main_s.wait_event(e2)
-        return adjs, stats
 
     def timed(fn, k):
         ms, out = [], None
@@ -697,43 +676,64 @@ def run_many(args):
             ms.append(a.elapsed_time(b))
         return ms, out
 
-    adjs_ref, stats0 = step(Xd, adj=True)
-    tests_unit = sum(x["tests_canonical"] for x in stats0)
+    # the batched handle: every instance's correlation block, then one search
+    pb = fp.PCBatch(ns, ps, MANY["alpha"], MANY["max_level"], precision=2)
+    for kv in args.opt:
+        key, val = kv.split("=", 1)
+        fp.pc_set_opt(pb.h, key.strip(), float(val))
+    fp.pc_set_stream(pb.h, main_s)
+    adj_b = torch.empty((pb.p, pb.p), dtype=torch.uint8, device=dev)
+
+    def step_b(Xs=Xd, adj=adj_b):
+        for i in range(len(inst)):
+            pb.corr_block(i, Xs[i])
+        _, st = pb.skeleton(adj)
+        return st
+
+    # lexicographic order first: its canonical count is the oracle's, the unit of the metric
+    st_lex = step_b()
+    tests_unit = st_lex["tests_canonical"]
+    adjs_lex = pb.split(adj_b.cpu().numpy())
+    learned = None
+    if not args.no_learned:
+        t0 = time.perf_counter()
+        train = sem.make_many(24, base_seed=9000)          # other seeds of the same recipe
+        feats, labels = proposal.collect(lambda i: train[i].X, range(len(train)), MANY["alpha"], 0,
+                                         MANY["max_level"], 2, max_rows_per_seed=50_000)
+        loss = proposal.train(pb.h, feats, labels, epochs=4, batch=8192, lr=2e-3, seed=2)
+        fp.pc_set_opt(pb.h, "learned", 1)
+        learned = {"train_rows": int(labels.shape[0]), "train_sems": "24 instances of the recipe (other seeds)",
+                   "final_loss": loss, "train_s": time.perf_counter() - t0}
     for _ in range(args.warmup):
-        step(Xd)
+        step_b()
+    torch.cuda.synchronize()
+    tune = fp.pc_autotune(pb.h, 2) if not args.no_autotune else None
+    for _ in range(args.warmup):
+        step_b()
     torch.cuda.synchronize()
     barrier(world)
     l0 = fp.pc_kernel_launches()
     with ClockSampler(local if world > 1 else torch.cuda.current_device()) as clk:
         torch.cuda.nvtx.range_push("bench_timed")
-        ms, (_, stats) = timed(lambda: step(Xd), args.steps)
+        ms, st_b = timed(step_b, args.steps)
         torch.cuda.nvtx.range_pop()
     launches = fp.pc_kernel_launches() - l0
     barrier(world)
     t_max = max_over_ranks(sum(ms) / 1000.0, world)
     value = sum_over_ranks(float(tests_unit * args.steps), world) / t_max
-
-    # the same problems in one batched handle
-    pb = fp.PCBatch(ns, ps, MANY["alpha"], MANY["max_level"], precision=2)
-    fp.pc_set_stream(pb.h, main_s)
-    adj_b = torch.empty((pb.p, pb.p), dtype=torch.uint8, device=dev)
-
-    def step_b():
-        for i in range(len(inst)):
-            pb.corr_block(i, Xd[i])
-        _, st = pb.skeleton(adj_b)
-        return st
-    step_b()
-    ms_b, st_b = timed(step_b, max(2, min(args.steps, 3)))
     blocks = pb.split(adj_b.cpu().numpy())
-    batched = {"ms_per_step": float(np.mean(ms_b)), "value": st_b["tests_canonical"] / (np.mean(ms_b) / 1e3),
-               "tests_executed": st_b["tests_executed"], "levels_run": st_b["levels_run"],
-               "identical_skeletons": all(np.array_equal(blocks[i], adjs_ref[i]) for i in range(len(inst)))}
+    identical = all(np.array_equal(blocks[i], adjs_lex[i]) for i in range(len(inst)))
+    if learned is not None:
+        learned.update({"tests_canonical": st_b["tests_canonical"], "tests_executed": st_b["tests_executed"],
+                        "max_level": int(fp.pc_get_opt(pb.h, "learned_max_level")),
+                        "identical_skeletons": identical})
+
     # per-kernel-class device time of the batched search (roofline of its dominant class)
     fp.pc_set_opt(pb.h, "timing", 1)
     fp.pc_timing(pb.h, reset=True)
     st_t = step_b()
     tim = fp.pc_timing(pb.h, reset=True)
+    fp.pc_set_opt(pb.h, "timing", 0)
     cls = fp.TIMING_CLASSES
     dom = dominant_class(tim)
     di = cls.index(dom)
@@ -742,18 +742,51 @@ def run_many(args):
     peak = FP64_PEAK_TFLOPS if dom in ("stage_a", "prec", "ci_complement") else FP32_PEAK_TFLOPS
     achieved = dom_flops / (tim[dom][0] * 1e-3) / 1e12 if tim[dom][0] > 0 else 0.0
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": dom, "measured_on": "batched handle, timing step",
+                "traffic": None, "kernel": dom, "kernels": CLASS_KERNELS.get(dom, dom),
+                "measured_on": "batched handle, timing step",
                 "peak_source": "nominal FP64 1.25 TFLOP/s" if peak == FP64_PEAK_TFLOPS else
                 "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz", "class_ms": {c: tim[c][0] for c in cls},
-                "largest_class": max(cls, key=lambda c: tim[c][0])}
+                "launch_groups": tim[dom][1], "largest_class": max(cls, key=lambda c: tim[c][0])}
+
+    # end to end with host buffers: every instance's X from pinned host memory, the
+    # block-diagonal skeleton back to the host
+    Xh = [torch.from_numpy(s_.X).pin_memory() for s_ in inst]
+    adj_h = np.empty((pb.p, pb.p), dtype=np.uint8)
+    e2e_ms, _ = timed(lambda: step_b(Xh, adj_h), max(2, min(args.steps, 3)))
+    e2e = {"value": tests_unit / (np.mean(e2e_ms) / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": int(sum(s_.X.nbytes for s_ in inst)), "d2h_bytes_per_step": int(adj_h.nbytes)}
     pb.close()
 
-    # end to end with host buffers: X from pinned host memory, adjacencies back to the host
-    Xh = [torch.from_numpy(s_.X).pin_memory() for s_ in inst]
-    e2e_ms, _ = timed(lambda: step(Xh, adj=True), max(2, min(args.steps, 3)))
-    e2e = {"value": tests_unit / (np.mean(e2e_ms) / 1e3), "unit": UNIT,
-           "h2d_bytes_per_step": int(sum(s_.X.nbytes for s_ in inst)),
-           "d2h_bytes_per_step": int(sum(p_ * p_ for p_ in ps))}
+    # the same problems as 64 handles on 16 streams, searched concurrently
+    streams = [torch.cuda.Stream() for _ in range(MANY["streams"])]
+    pcs = []
+    for i in range(len(inst)):
+        pc = fp.PC(ns[i], ps[i], MANY["alpha"], MANY["max_level"], order=0, precision=2)
+        fp.pc_set_stream(pc.h, streams[i % len(streams)])
+        pcs.append(pc)
+    hs = [pc.h for pc in pcs]
+
+    def step_s():
+        ev = torch.cuda.Event()
+        ev.record(main_s)
+        for st in streams:
+            st.wait_event(ev)
+        for i, pc in enumerate(pcs):
+            pc.corr(Xd[i])
+        _, stats, status = fp.pc_skeleton_many(hs, ps, adj_out=False)
+        if any(status):
+            raise RuntimeError(f"pc_skeleton_many: statuses {status}")
+        for st in streams:
+            e2 = torch.cuda.Event()
+            e2.record(st)
+            main_s.wait_event(e2)
+        return stats
+    step_s()
+    ms_s, stats_s = timed(step_s, max(2, min(args.steps, 5)))
+    streams_obj = {"ms_per_step": float(np.mean(ms_s)), "value": tests_unit / (np.mean(ms_s) / 1e3),
+                   "streams": MANY["streams"], "tests_executed": int(sum(x["tests_executed"] for x in stats_s))}
+    for pc in pcs:
+        pc.close()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -774,15 +807,19 @@ def run_many(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
                 "config": {"workload": "many64", "instances": len(inst), "p_total": int(sum(ps)),
                            "alpha": MANY["alpha"], "order": "conventional",
-                           "precision": "bf16x3-gemm+fp32-tests", "streams": MANY["streams"],
+                           "precision": "bf16x3-gemm+fp32-tests",
+                           "form": "one batched handle (block-diagonal, one launch sequence per stage)",
+                           "learned_order": learned is not None, "options": list(args.opt),
                            "parallelism": f"replicas x{world}", "l2": "flushed before every step (512 MB write)"},
                 "tests_canonical_per_step": tests_unit,
-                "tests_executed_per_step": int(sum(x["tests_executed"] for x in stats)),
-                "roofline": roofline, "cpu_baseline": cpu, "batched_handle": batched, "e2e": e2e,
+                "tests_executed_per_step": st_b["tests_executed"],
+                "skeleton_ms": float(st_b["t_skeleton_ms"]),
+                "roofline": roofline, "autotune": tune, "learned": learned,
+                "lexicographic": {"tests_canonical": st_lex["tests_canonical"],
+                                  "tests_executed": st_lex["tests_executed"]},
+                "streams_16": streams_obj, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
-    for pc in pcs:
-        pc.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -57,6 +57,8 @@ struct pc_handle {
     // path-restricted pools (option "path_pool"): component labels of the graph
     // without each node, the largest pool
     int path_pool = 0;
+    uint8_t *adj_stage = nullptr;     // the expanded skeleton for host outputs
+    size_t adj_stage_bytes = 0;
     int *pp_comp = nullptr, *pp_max = nullptr;
     int stage_conds = 1;                 // conditional nodes in the captured stage body
     int lane_stages = 1;                 // small stages on the rank-major small-stage kernel
@@ -1618,15 +1620,25 @@ extern "C" pc_status pc_skeleton(pc_handle *h, uint8_t *adj_out, pc_stats *stats
     return PC_OK;
 }
 
+// The skeleton as a p x p 0/1 matrix: expanded from the bitset on the device, into
+// adj_out directly when it is device memory, else through a device staging buffer.
 static pc_status copy_adj(pc_handle *h, uint8_t *adj_out)
 {
-    const int p = h->p, W = h->g.W;
-    std::vector<uint32_t> bits((size_t)p * W);
-    CK(cudaMemcpy(bits.data(), h->g.adj, bits.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost));
-    std::vector<uint8_t> A((size_t)p * p);
-    for (int u = 0; u < p; ++u)
-        for (int v = 0; v < p; ++v) A[(size_t)u * p + v] = (bits[(size_t)u * W + (v >> 5)] >> (v & 31)) & 1u;
-    CK(cudaMemcpy(adj_out, A.data(), A.size(), cudaMemcpyDefault));
+    const size_t bytes = (size_t)h->p * h->p;
+    cudaStream_t s = h->stream;
+    if (is_device_ptr(adj_out)) {
+        CK(fpc::launch_expand_adj(h->g, adj_out, s));
+    } else {
+        if (h->adj_stage_bytes < bytes) {
+            dfree(h, h->adj_stage);
+            h->adj_stage = nullptr;
+            CK(dalloc(h, &h->adj_stage, bytes));
+            h->adj_stage_bytes = bytes;
+        }
+        CK(fpc::launch_expand_adj(h->g, h->adj_stage, s));
+        CK(cudaMemcpyAsync(adj_out, h->adj_stage, bytes, cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaStreamSynchronize(s));
     return PC_OK;
 }
 

@@ -262,6 +262,7 @@ cudaError_t launch_ci_direct(GraphDev g, TestParams tp, int mmax, const float *C
 cudaError_t launch_ci_complement(GraphDev g, TestParams tp, cudaStream_t s);
 // range: one instantiation (0 .. LANE_RANGES-1) or -1 for all; prop: the
 // variant for handles with a proposal network
+cudaError_t launch_expand_adj(GraphDev g, uint8_t *out, cudaStream_t s);
 // ---- path-restricted candidate pools (level.cu)
 cudaError_t launch_pp_components(GraphDev g, int *comp, cudaStream_t s);
 cudaError_t launch_pp_search(GraphDev g, TestParams tp, const double *C64, int ldc, const int *comp, int l,

@@ -2658,6 +2658,31 @@ cudaError_t launch_pp_commit(GraphDev g, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// The adjacency bitset as a p x p 0/1 byte matrix (row-major), four bytes per thread.
+__global__ void expand_adj_kernel(const uint32_t *adj, int p, int W, uint8_t *out)
+{
+    const long long total = (long long)p * p;
+    for (long long q = (blockIdx.x * (long long)blockDim.x + threadIdx.x) * 4; q < total;
+         q += (long long)gridDim.x * blockDim.x * 4) {
+        uint32_t word = 0;
+        for (int k = 0; k < 4 && q + k < total; ++k) {
+            const long long e = q + k;
+            const int u = (int)(e / p), v = (int)(e - (long long)u * p);
+            word |= ((adj[(long long)u * W + (v >> 5)] >> (v & 31)) & 1u) << (8 * k);
+        }
+        if (q + 4 <= total && ((uintptr_t)(out + q) & 3) == 0) *(uint32_t *)(out + q) = word;
+        else
+            for (int k = 0; k < 4 && q + k < total; ++k) out[q + k] = (uint8_t)(word >> (8 * k));
+    }
+}
+
+cudaError_t launch_expand_adj(GraphDev g, uint8_t *out, cudaStream_t s)
+{
+    expand_adj_kernel<<<num_sms() * 8, 256, 0, s>>>(g.adj, g.p, g.W, out);
+    note_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_init_adj(GraphDev g, cudaStream_t s)
 {
     long long tot = (long long)g.p * g.W;
