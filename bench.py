@@ -54,8 +54,9 @@ def dominant_class(tim):
 
 # the kernels behind each timing class that the roofline names
 CLASS_KERNELS = {
-    "ci_direct": "ci_lane_kernel (stages l <= 12, one thread per chunk of sets) + ci_direct_kernel "
-                 "(one warp per test) + ci_redecide_kernel (FP64 pass)",
+    "ci_direct": "ci_pairwarp_kernel (l = 1, 2, degree > 32: a warp per ordered pair) + ci_node_kernel "
+                 "(degree <= 128: corr block in shared memory) + ci_lane_kernel (other stages l <= 12) + "
+                 "ci_direct_kernel (one warp per test) + ci_redecide_kernel (FP64 pass)",
     "ci_complement": "ci_complement_kernel (FP64, from neighbourhood precision blocks)",
     "prec": "prec_update_kernel (neighbourhood precision blocks, FP64)",
     "stage_a": "stage_a sweep inverse (FP64)",
@@ -676,7 +677,7 @@ def run_many(args):
             ms.append(a.elapsed_time(b))
         return ms, out
 
-    # the batched handle: every instance's correlation block, then one search
+    # the batched handle: every instance's correlation block (concurrently), then one search
     pb = fp.PCBatch(ns, ps, MANY["alpha"], MANY["max_level"], precision=2)
     for kv in args.opt:
         key, val = kv.split("=", 1)
@@ -685,8 +686,7 @@ def run_many(args):
     adj_b = torch.empty((pb.p, pb.p), dtype=torch.uint8, device=dev)
 
     def step_b(Xs=Xd, adj=adj_b):
-        for i in range(len(inst)):
-            pb.corr_block(i, Xs[i])
+        pb.corr_blocks(Xs)                  # the instances' correlation steps on the handle's side streams
         _, st = pb.skeleton(adj)
         return st
 

@@ -228,6 +228,21 @@ pc_status pc_create_batch(int32_t k, const int64_t *n, const int32_t *p, double 
  * PC_ERR_STATE on a handle from pc_create, PC_ERR_ARG on a bad index. */
 pc_status pc_corr_block(pc_handle *h, int32_t i, const void *X, int32_t dtype, int64_t ld);
 
+/* pc_corr_blocks -- pc_corr_block for every instance of a batched handle in one
+ * call: X[i], dtype[i], ld[i] (host arrays of k entries) as pc_corr_block's
+ * arguments for instance i.  The instances' standardisation and correlation
+ * GEMMs are independent (disjoint planes, disjoint diagonal blocks of corr),
+ * so they run concurrently on up to 8 internal streams of the handle, each with
+ * its own staging and split-K workspaces, forked from and joined back into the
+ * handle's stream: the call is ordered on that stream like one pc_corr_block
+ * per instance, and gives the same results.  With "precision" 0 (FP64 Gram,
+ * one shared workspace) the instances run one after the other on the handle's
+ * stream.  Timing class "corr" covers the whole fork and join; "corr_gemm" is
+ * not recorded.  PC_ERR_STATE on a handle from pc_create, PC_ERR_ARG (nothing
+ * issued) on a null array or a bad entry.  Not in the paper: it runs one
+ * problem at a time. */
+pc_status pc_corr_blocks(pc_handle *h, const void *const *X, const int32_t *dtype, const int64_t *ld);
+
 /* pc_batch_layout -- the number of instances (1 for a pc_create handle) into
  * *k and, if offsets is not NULL, their first node ids plus the total
  * (k + 1 entries, host). */

@@ -29,6 +29,18 @@ struct TimedPair {
     cudaEvent_t a, b;
 };
 
+// A stream and the workspaces of one correlation step (statistics partials,
+// host-input staging, the tensor-core GEMM's split-K partials).
+struct CorrLane {
+    cudaStream_t s = nullptr;
+    void *Xstage = nullptr;
+    size_t Xstage_bytes = 0;
+    double *stats_ws = nullptr;
+    size_t stats_ws_bytes = 0;
+    float *tc_ws = nullptr;
+    size_t tc_ws_bytes = 0;
+};
+
 struct pc_handle {
     long long n = 0;
     int p = 0;
@@ -57,6 +69,10 @@ struct pc_handle {
     // path-restricted pools (option "path_pool"): component labels of the graph
     // without each node, the largest pool
     int path_pool = 0;
+    // pc_corr_blocks: side streams with their own workspaces for the instances'
+    // correlation steps (their planes and blocks are disjoint)
+    std::vector<CorrLane> lanes;
+    std::vector<cudaEvent_t> lane_ev;
     uint8_t *adj_stage = nullptr;     // the expanded skeleton for host outputs
     size_t adj_stage_bytes = 0;
     int *pp_comp = nullptr, *pp_max = nullptr;
@@ -489,6 +505,8 @@ extern "C" pc_status pc_batch_layout(pc_handle *h, int32_t *k, int32_t *offsets)
 extern "C" void pc_destroy(pc_handle *h)
 {
     if (!h) return;
+    for (auto &cl : h->lanes)
+        if (cl.s) cudaStreamSynchronize(cl.s);
     for (void *p : h->allocs) cudaFree(p);
     h->allocs.clear();
     if (h->info_h) cudaFreeHost(h->info_h);
@@ -503,6 +521,9 @@ extern "C" void pc_destroy(pc_handle *h)
     for (auto e : h->evpool) cudaEventDestroy(e);
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     if (h->graph) cudaGraphDestroy(h->graph);
+    for (auto &cl : h->lanes)
+        if (cl.s) cudaStreamDestroy(cl.s);
+    for (auto e : h->lane_ev) cudaEventDestroy(e);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->br_stream) cudaStreamDestroy(h->br_stream);
     delete h;
@@ -734,9 +755,17 @@ static pc_status alloc_c64_list(pc_handle *h)
 // Standardisation and correlation GEMM of one problem, or of instance blk of a
 // batched handle (its columns are rows [o, o+p) of the planes, its block of
 // corr the diagonal block there).
-static pc_status corr_impl(pc_handle *h, const void *X, int32_t dtype, int64_t ld, int blk)
+// lane: run on a side stream with its own workspaces (pc_corr_blocks, which has
+// allocated the handle's planes and flags and cleared the GEMM's error flag first)
+static pc_status corr_impl(pc_handle *h, const void *X, int32_t dtype, int64_t ld, int blk, CorrLane *lane = nullptr)
 {
-    cudaStream_t s = h->stream;
+    cudaStream_t s = lane ? lane->s : h->stream;
+    void *&Xstage = lane ? lane->Xstage : h->Xstage;
+    size_t &Xstage_bytes = lane ? lane->Xstage_bytes : h->Xstage_bytes;
+    double *&stats_ws = lane ? lane->stats_ws : h->stats_ws;
+    size_t &stats_ws_bytes = lane ? lane->stats_ws_bytes : h->stats_ws_bytes;
+    float *&tc_ws = lane ? lane->tc_ws : h->tc_ws;
+    size_t &tc_ws_bytes = lane ? lane->tc_ws_bytes : h->tc_ws_bytes;
     const int o = blk < 0 ? 0 : h->boff[blk];
     const int p = blk < 0 ? h->p : h->boff[blk + 1] - o;
     const long long n = blk < 0 ? h->n : h->bn[blk];
@@ -746,15 +775,15 @@ static pc_status corr_impl(pc_handle *h, const void *X, int32_t dtype, int64_t l
     const void *Xd = X;
     if (!is_device_ptr(X)) {
         size_t bytes = (size_t)n * ld * esz;
-        if (bytes > h->Xstage_bytes) {
-            dfree(h, h->Xstage);
-            h->Xstage = nullptr;
-            h->Xstage_bytes = 0;
-            CK(dalloc(h, &h->Xstage, bytes));
-            h->Xstage_bytes = bytes;
+        if (bytes > Xstage_bytes) {
+            dfree(h, Xstage);
+            Xstage = nullptr;
+            Xstage_bytes = 0;
+            CK(dalloc(h, &Xstage, bytes));
+            Xstage_bytes = bytes;
         }
-        CK(cudaMemcpyAsync(h->Xstage, X, bytes, cudaMemcpyHostToDevice, s));
-        Xd = h->Xstage;
+        CK(cudaMemcpyAsync(Xstage, X, bytes, cudaMemcpyHostToDevice, s));
+        Xd = Xstage;
     }
     const size_t plane = (size_t)h->p * h->ldk;
     if (!h->Xs64) {
@@ -767,18 +796,18 @@ static pc_status corr_impl(pc_handle *h, const void *X, int32_t dtype, int64_t l
         CK(cudaMemsetAsync(h->Xhi, 0, plane * sizeof(uint16_t), s));
         CK(cudaMemsetAsync(h->Xlo, 0, plane * sizeof(uint16_t), s));
     }
-    Timed tm(h, 0);
+    Timed tm(h, lane ? -1 : 0);
     const size_t sws = fpc::col_stats_ws_bytes(n, p);
-    if (sws > h->stats_ws_bytes) {
-        dfree(h, h->stats_ws);
-        h->stats_ws = nullptr;
-        CK(dalloc(h, &h->stats_ws, sws));
-        h->stats_ws_bytes = sws;
+    if (sws > stats_ws_bytes) {
+        dfree(h, stats_ws);
+        stats_ws = nullptr;
+        CK(dalloc(h, &stats_ws, sws));
+        stats_ws_bytes = sws;
     }
     const size_t po = (size_t)o * h->ldk;                  // first plane row of this problem
-    CK(fpc::launch_col_stats_split(Xd, dtype, n, p, ld, h->mean + o, h->rsd + o, h->stats_ws, s));
+    CK(fpc::launch_col_stats_split(Xd, dtype, n, p, ld, h->mean + o, h->rsd + o, stats_ws, s));
     const bool want_bf16 = h->precision == 2 && fpc::tc_gemm_available();
-    CK(fpc::launch_standardize(Xd, dtype, n, p, ld, h->mean + o, h->rsd + o, h->stats_ws, h->Xs64 + po,
+    CK(fpc::launch_standardize(Xd, dtype, n, p, ld, h->mean + o, h->rsd + o, stats_ws, h->Xs64 + po,
                                h->precision == 1 ? h->Xs32 + po : nullptr,
                                want_bf16 ? h->Xhi + po : nullptr, want_bf16 ? h->Xlo + po : nullptr, h->ldk,
                                s));
@@ -819,23 +848,23 @@ static pc_status corr_impl(pc_handle *h, const void *X, int32_t dtype, int64_t l
     } else if (h->precision == 1 || !want_bf16) {
         if (h->precision == 2) {
             // tensor-core path not available on this device: FP32 operands on the CUDA cores
-            CK(fpc::launch_standardize(Xd, dtype, n, p, ld, h->mean + o, h->rsd + o, h->stats_ws, nullptr, h->Xs32 + po,
+            CK(fpc::launch_standardize(Xd, dtype, n, p, ld, h->mean + o, h->rsd + o, stats_ws, nullptr, h->Xs32 + po,
                                        nullptr, nullptr, h->ldk, s));
         }
-        Timed tg(h, 7);
+        Timed tg(h, lane ? -1 : 7);
         CK(fpc::launch_syrk_f32(h->Xs32 + po, n, h->ldk, p, C32b, ldb, s));
     } else {
         const size_t need = fpc::corr_bf16x3_ws_bytes(n, p);
-        if (need > h->tc_ws_bytes) {
-            dfree(h, h->tc_ws);
-            h->tc_ws = nullptr;
-            CK(dalloc(h, &h->tc_ws, need));
-            h->tc_ws_bytes = need;
+        if (need > tc_ws_bytes) {
+            dfree(h, tc_ws);
+            tc_ws = nullptr;
+            CK(dalloc(h, &tc_ws, need));
+            tc_ws_bytes = need;
         }
-        if (blk <= 0) CK(cudaMemsetAsync(h->tc_err, 0, sizeof(int), s));
-        Timed tg(h, 7);
-        CK(fpc::launch_corr_bf16x3(h->Xhi + po, h->Xlo + po, n, h->ldk, p, C32b, ldb, h->tc_ws,
-                                   h->tc_ws_bytes, h->tc_err, s));
+        if (blk <= 0 && !lane) CK(cudaMemsetAsync(h->tc_err, 0, sizeof(int), s));
+        Timed tg(h, lane ? -1 : 7);
+        CK(fpc::launch_corr_bf16x3(h->Xhi + po, h->Xlo + po, n, h->ldk, p, C32b, ldb, tc_ws, tc_ws_bytes,
+                                   h->tc_err, s));
         tc = true;
     }
     if (blk < 0) {
@@ -869,6 +898,76 @@ extern "C" pc_status pc_corr_block(pc_handle *h, int32_t i, const void *X, int32
     if (!h->nblk) return fail(h, PC_ERR_STATE, "pc_corr_block needs a batched handle (pc_create_batch)");
     if (i < 0 || i >= h->nblk) return fail(h, PC_ERR_ARG, "pc_corr_block: instance index out of range");
     return corr_impl(h, X, dtype, ld, i);
+}
+
+extern "C" pc_status pc_corr_blocks(pc_handle *h, const void *const *X, const int32_t *dtype, const int64_t *ld)
+{
+    if (!h) return PC_ERR_ARG;
+    if (!h->nblk) return fail(h, PC_ERR_STATE, "pc_corr_blocks needs a batched handle (pc_create_batch)");
+    if (!X || !dtype || !ld) return fail(h, PC_ERR_ARG, "pc_corr_blocks: null array");
+    const int k = h->nblk;
+    for (int i = 0; i < k; ++i)
+        if (!X[i] || (dtype[i] != PC_F32 && dtype[i] != PC_F64) || ld[i] < h->boff[i + 1] - h->boff[i])
+            return fail(h, PC_ERR_ARG, "pc_corr_blocks: bad X, dtype or ld of instance " + std::to_string(i));
+    if (h->precision == 0) {
+        // the FP64 Gram shares one split-K workspace: one instance after the other
+        for (int i = 0; i < k; ++i)
+            if (pc_status r = corr_impl(h, X[i], dtype[i], ld[i], i)) return r;
+        return PC_OK;
+    }
+    cudaStream_t s = h->stream;
+    Timed tm(h, 0);
+    // what the instances share, on the handle's stream before the fork: the
+    // standardised planes, the FP64-validity flags, the GEMM's error flag
+    const size_t plane = (size_t)h->p * h->ldk;
+    if (!h->Xs64) {
+        CK(dalloc(h, &h->Xs64, plane * sizeof(double)));
+        CK(dalloc(h, &h->Xs32, plane * sizeof(float)));
+        CK(dalloc(h, &h->Xhi, plane * sizeof(uint16_t)));
+        CK(dalloc(h, &h->Xlo, plane * sizeof(uint16_t)));
+        CK(cudaMemsetAsync(h->Xs64, 0, plane * sizeof(double), s));
+        CK(cudaMemsetAsync(h->Xs32, 0, plane * sizeof(float), s));
+        CK(cudaMemsetAsync(h->Xhi, 0, plane * sizeof(uint16_t), s));
+        CK(cudaMemsetAsync(h->Xlo, 0, plane * sizeof(uint16_t), s));
+    }
+    if (!h->c64_valid) {
+        CK(dalloc(h, &h->c64_valid, (h->pair_elems + 7) / 4 * 4));
+        CK(cudaMemsetAsync(h->c64_valid, 0, (h->pair_elems + 7) / 4 * 4, s));
+        if (pc_status r = alloc_c64_list(h)) return r;
+    }
+    CK(cudaMemsetAsync(h->tc_err, 0, sizeof(int), s));
+    const int nl = std::min(k, 8);
+    while ((int)h->lanes.size() < nl) {
+        CorrLane cl;
+        CK(cudaStreamCreateWithFlags(&cl.s, cudaStreamNonBlocking));
+        cudaEvent_t ev = nullptr;
+        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        h->lanes.push_back(cl);
+        h->lane_ev.push_back(ev);
+    }
+    if (h->lane_ev.size() < (size_t)nl + 1) {
+        cudaEvent_t ev = nullptr;
+        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        h->lane_ev.push_back(ev);
+    }
+    cudaEvent_t fork = h->lane_ev[nl];
+    CK(cudaEventRecord(fork, s));
+    for (int j = 0; j < nl; ++j) CK(cudaStreamWaitEvent(h->lanes[j].s, fork, 0));
+    // the larger instances first, spread over the lanes
+    std::vector<int> order(k);
+    for (int i = 0; i < k; ++i) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](int a, int b) {
+        return (double)h->bn[a] * (h->boff[a + 1] - h->boff[a]) > (double)h->bn[b] * (h->boff[b + 1] - h->boff[b]);
+    });
+    for (int t = 0; t < k; ++t) {
+        const int i = order[t];
+        if (pc_status r = corr_impl(h, X[i], dtype[i], ld[i], i, &h->lanes[t % nl])) return r;
+    }
+    for (int j = 0; j < nl; ++j) {
+        CK(cudaEventRecord(h->lane_ev[j], h->lanes[j].s));
+        CK(cudaStreamWaitEvent(s, h->lane_ev[j], 0));
+    }
+    return PC_OK;
 }
 
 extern "C" pc_status pc_corr_get(pc_handle *h, float *C32, double *C64)

@@ -93,6 +93,7 @@ def load():
         "pc_autotune": (i32, [vp, i32, ctypes.POINTER(pc_tune_result)]),
         "pc_create_batch": (i32, [i32, vp, vp, dbl, i32, ctypes.POINTER(vp)]),
         "pc_corr_block": (i32, [vp, i32, vp, i32, i64]),
+        "pc_corr_blocks": (i32, [vp, ctypes.POINTER(vp), vp, vp]),
         "pc_batch_layout": (i32, [vp, ctypes.POINTER(i32), vp]),
         "pc_mlp_nparam": (i32, []),
         "pc_mlp_set_params": (i32, [vp, vp, i64]),
@@ -183,6 +184,16 @@ def pc_corr_block(h, i: int, X):
     """Instance i's data (n_i x p_i row-major, numpy host or torch CUDA tensor)."""
     X, dt, ld = _x_args(X)
     _check(h, load().pc_corr_block(h, int(i), ctypes.c_void_p(_ptr(X)), dt, int(ld)))
+
+
+def pc_corr_blocks(h, Xs):
+    """Every instance's data in one call (Xs[i] as pc_corr_block's X for instance i);
+    the instances' correlation steps run concurrently on the handle's side streams."""
+    args = [_x_args(X) for X in Xs]
+    ptrs = (ctypes.c_void_p * len(args))(*[_ptr(a[0]) for a in args])
+    dts = np.ascontiguousarray([a[1] for a in args], dtype=np.int32)
+    lds = np.ascontiguousarray([a[2] for a in args], dtype=np.int64)
+    _check(h, load().pc_corr_blocks(h, ptrs, dts.ctypes.data, lds.ctypes.data))
 
 
 def pc_batch_layout(h):
@@ -488,6 +499,12 @@ class PCBatch(PC):
 
     def corr_block(self, i, X):
         pc_corr_block(self.h, i, X)
+        return self
+
+    def corr_blocks(self, Xs):
+        if len(Xs) != len(self.ps):
+            raise ValueError("corr_blocks: one array per instance")
+        pc_corr_blocks(self.h, Xs)
         return self
 
     def split(self, adj, sepsets=None):

@@ -158,3 +158,55 @@ def test_many64_full_size_equals_oracle(fp):
         assert seps_many[i] == R["sepsets"], i
         assert seps_b[i] == R["sepsets"], i
         assert stats[i]["tests_canonical"] == R["tests_total"], i
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_corr_blocks_equals_per_instance_calls(fp, precision):
+    """pc_corr_blocks (the instances' correlation steps on the handle's side
+    streams) gives bit for bit the correlations of one pc_corr_block per
+    instance, and the skeleton of every instance equals the oracle's.  Twelve
+    instances of mixed sizes: more than the side streams, so a stream's
+    workspaces serve several instances and grow between them."""
+    inst = _instances(12, 1010 + precision, p_range=(8, 70), n_range=(150, 5000))
+    ns = [s.X.shape[0] for s in inst]
+    ps = [s.X.shape[1] for s in inst]
+    Xs = [torch.from_numpy(s.X).cuda() if i % 3 else s.X for i, s in enumerate(inst)]   # host and device
+    with fp.PCBatch(ns, ps, 0.01, -1, precision=precision) as pa:
+        for i, X in enumerate(Xs):
+            pa.corr_block(i, X)
+        C32a, C64a = pa.corr_get()
+        adj_a, st_a = pa.skeleton()
+    with fp.PCBatch(ns, ps, 0.01, -1, precision=precision) as pb:
+        pb.corr_blocks(Xs)
+        C32b, C64b = pb.corr_get()
+        adj_b, st_b = pb.skeleton()
+        adjs, seps = pb.split(adj_b, pb.sepsets())
+        pb.corr_blocks(Xs)                               # again, on the same side streams
+        C32c, _ = pb.corr_get()
+    np.testing.assert_array_equal(C32a, C32b)
+    np.testing.assert_array_equal(C64a, C64b)
+    np.testing.assert_array_equal(C32b, C32c)
+    np.testing.assert_array_equal(adj_a, adj_b)
+    assert st_a["tests_canonical"] == st_b["tests_canonical"]
+    for i, s in enumerate(inst):
+        R = _oracle(s.X, 0.01, -1)
+        np.testing.assert_array_equal(adjs[i], R["adj"])
+        assert seps[i] == R["sepsets"], i
+
+
+def test_corr_blocks_errors(fp):
+    inst = _instances(3, 1030, p_range=(10, 16), n_range=(300, 600))
+    ns = [s.X.shape[0] for s in inst]
+    ps = [s.X.shape[1] for s in inst]
+    with fp.PCBatch(ns, ps, 0.01, -1) as pb:
+        with pytest.raises(ValueError):
+            pb.corr_blocks([s.X for s in inst[:2]])                 # one array per instance
+        with pytest.raises(fp.PCError):
+            fp.pc_corr_blocks(pb.h, [s.X for s in inst[:2]] + [inst[2].X[:, :5]])  # ld < p_2
+        with pytest.raises(fp.PCError):
+            pb.skeleton()                                           # nothing was issued
+        pb.corr_blocks([s.X for s in inst])
+        adj, _ = pb.skeleton()
+    with fp.PC(ns[0], ps[0], 0.01, -1) as pc:
+        with pytest.raises(fp.PCError):
+            fp.pc_corr_blocks(pc.h, [inst[0].X])                    # not a batched handle
