@@ -139,6 +139,12 @@ void pc_destroy(pc_handle *h);
  *                 default 128) run on the staged kernel, which holds
  *                 corr[adj(u), adj(u)] in shared memory; the rest read corr
  *                 from L2 (0 = staged kernel off)
+ *   "comp_fp32"   1 = complement tests (reversed order) in FP32 first from the
+ *                 FP64 precision blocks, decided there when a first-order
+ *                 error bound with validity checks shows the FP64 decision is
+ *                 the same and the statistic lies at least "band" from q, else
+ *                 in FP64 (default; counted in tests_redecided, band_hits,
+ *                 guard_hits); 0 = FP64 only.  Not used with "precision" 0.
  * Unknown keys return PC_ERR_ARG. */
 pc_status pc_set_opt(pc_handle *h, const char *key, double val);
 pc_status pc_get_opt(pc_handle *h, const char *key, double *val);

@@ -64,6 +64,7 @@ struct pc_handle {
     // launch shape of the test kernels (pc_autotune)
     int lane_chunk = 8, lane_rounds = 32, lane_blocks = 8, direct_warps = 8;
     int node_dmax = fpc::NODE_DMAX;   // staged small-stage kernel: largest node degree (0: off)
+    int comp_fp32 = 1;                // complement tests in FP32 first (FP32 modes)
     int pair_warp = 1;                // stages 1-2: warp-per-pair kernel for the larger nodes
     int pair_warp_dmin = fpc::PAIRWARP_DMIN;
     // path-restricted pools (option "path_pool"): component labels of the graph
@@ -274,6 +275,7 @@ static TestParams make_tp(const pc_handle *h)
     tp.lane_rounds = h->lane_rounds;
     tp.lane_blocks = h->lane_blocks;
     tp.node_dmax = h->node_dmax;
+    tp.comp_fp32 = h->comp_fp32 && h->precision != 0;
     tp.pair_warp = h->pair_warp;
     tp.pair_warp_dmin = h->pair_warp_dmin;
     tp.direct_warps = h->direct_warps;
@@ -603,6 +605,9 @@ extern "C" pc_status pc_set_opt(pc_handle *h, const char *key, double val)
         if (!(val >= 0 && val <= fpc::NODE_DMAX))
             return fail(h, PC_ERR_ARG, "node_dmax must be in [0, " + std::to_string(fpc::NODE_DMAX) + "]");
         h->node_dmax = (int)val;
+    } else if (k == "comp_fp32") {
+        if (!(val == 0 || val == 1)) return fail(h, PC_ERR_ARG, "comp_fp32 must be 0 or 1");
+        h->comp_fp32 = (int)val;
     } else if (k == "direct_warps") {
         if (val != 1 && val != 2 && val != 4 && val != 8) return fail(h, PC_ERR_ARG, "direct_warps must be 1, 2, 4 or 8");
         h->direct_warps = (int)val;
@@ -634,6 +639,7 @@ extern "C" pc_status pc_get_opt(pc_handle *h, const char *key, double *val)
     else if (k == "lane_rounds") *val = h->lane_rounds;
     else if (k == "lane_blocks") *val = h->lane_blocks;
     else if (k == "node_dmax") *val = h->node_dmax;
+    else if (k == "comp_fp32") *val = h->comp_fp32;
     else if (k == "pair_warp") *val = h->pair_warp;
     else if (k == "path_pool") *val = h->path_pool;
     else if (k == "mlp_backward") *val = h->mlp_bwd_tc;
@@ -1198,6 +1204,7 @@ static std::vector<double> graph_key(const pc_handle *h)
             (double)(uintptr_t)h->C32, (double)(uintptr_t)h->C64, (double)h->lane_chunk,
             (double)h->lane_rounds, (double)h->lane_blocks, (double)h->direct_warps, (double)h->stage_conds,
             (double)h->node_dmax, (double)h->pair_warp, (double)h->pair_warp_dmin, (double)h->learned_lmax,
+            (double)h->comp_fp32,
             (double)h->lane_stages};
 }
 

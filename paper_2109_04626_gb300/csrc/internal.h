@@ -189,6 +189,7 @@ struct TestParams {
                         // pair_warp_dmin one warp per pair (0: off)
     int pair_warp_dmin;
     int precision;      // 0 fp64, 1/2 fp32 tests with FP64 re-decision
+    int comp_fp32;      // complement tests in FP32 first, FP64 where the bound does not decide
     int reversed;
     int complement;
     // lazily filled FP64 correlations: entry (a,b) of C64 is valid once

@@ -234,9 +234,16 @@ __device__ void tail_body(GraphDev g, TestParams tp, int cap, int mode, const in
         __syncthreads();
     }
     long long run = part[t] - sum;
-    for (int i = s0; i < s1; ++i) {
-        g.ooff[i] = run;
-        run += __ldcg(g.deg + i);
+    for (int i0 = s0; i0 < s1; i0 += 8) {              // batches of independent loads, then the stores
+        int dv[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) dv[k] = i0 + k < s1 ? __ldcg(g.deg + i0 + k) : 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (i0 + k < s1) {
+                g.ooff[i0 + k] = run;
+                run += dv[k];
+            }
     }
     if (t == 0) {
         const long long tot = part[nth - 1];
@@ -456,7 +463,7 @@ __global__ void __launch_bounds__(1024) head_kernel(GraphDev g, TestParams tp, d
     {
         ull rd = ex[0], rc = ex[1], rr = ex[2], ra = ex[3], ri = ex[4], rw = ex[5];
         for (int u = s0; u < s1; ++u) {
-            const int dg = g.deg[u];
+            const int dg = __ldg(g.deg + u);             // read-only here: not held behind the stores
             const ull T = Tn[u - s0], tt = sat_mul(T, (ull)dg);
             g.tn_off[u] = rd;
             g.cn_off[u] = rc;
@@ -476,10 +483,19 @@ __global__ void __launch_bounds__(1024) head_kernel(GraphDev g, TestParams tp, d
         }
     }
     // owner node of every ordered pair (the small-stage kernel's work items; the commit):
-    // one warp per node, consecutive entries per lane group (coalesced stores)
-    for (int u = t >> 5; u < p; u += (int)blockDim.x >> 5) {
-        const long long b = g.ooff[u];
-        for (int jj = t & 31, dg = g.deg[u]; jj < dg; jj += 32) g.opu[b + jj] = u;
+    // a warp takes 32 consecutive nodes, each lane loading one node's offset and degree
+    // (one round of loads instead of one per node), then writes the nodes' runs in turn
+    // with consecutive entries per lane group (coalesced stores)
+    for (int u0 = (t >> 5) * 32; u0 < p; u0 += (int)blockDim.x) {
+        const int ul = u0 + (t & 31);
+        const long long bl = ul < p ? g.ooff[ul] : 0;
+        const int dl = ul < p ? g.deg[ul] : 0;
+        const int nk = min(32, p - u0);
+        for (int k = 0; k < nk; ++k) {
+            const long long b = __shfl_sync(0xffffffffu, bl, k);
+            const int dg = __shfl_sync(0xffffffffu, dl, k);
+            for (int jj = t & 31; jj < dg; jj += 32) g.opu[b + jj] = u0 + k;
+        }
     }
     int rounds = 0;
     if (small && tot[0] > 0) {
@@ -500,17 +516,19 @@ __global__ void __launch_bounds__(1024) head_kernel(GraphDev g, TestParams tp, d
         ull v2[1] = {0ull};
         for (int u = s0; u < s1; ++u) {
             const ull T = Tn[u - s0];
-            if (!cm[u - s0] && T > skip && !items(g.deg[u], T) && !warp_mode(g.deg[u], T))
-                v2[0] = sat_add(v2[0], sat_mul(T - skip, (ull)g.deg[u]));
+            const int dg = __ldg(g.deg + u);
+            if (!cm[u - s0] && T > skip && !items(dg, T) && !warp_mode(dg, T))
+                v2[0] = sat_add(v2[0], sat_mul(T - skip, (ull)dg));
         }
         ull ex2[1], tot2[1];
         block_scan_sat<1>(v2, ex2, tot2, sh);
         ull rr2 = ex2[0];
         for (int u = s0; u < s1; ++u) {
             const ull T = Tn[u - s0];
+            const int dg = __ldg(g.deg + u);
             g.rn_off[u] = rr2;
-            if (!cm[u - s0] && T > skip && !items(g.deg[u], T) && !warp_mode(g.deg[u], T))
-                rr2 = sat_add(rr2, sat_mul(T - skip, (ull)g.deg[u]));
+            if (!cm[u - s0] && T > skip && !items(dg, T) && !warp_mode(dg, T))
+                rr2 = sat_add(rr2, sat_mul(T - skip, (ull)dg));
         }
         if (t == 0) g.rn_off[p] = tot2[0];
     }
@@ -1748,6 +1766,139 @@ __device__ __forceinline__ void load_small_binom(const GraphDev &g, ull *sb)
 // T = S u {u,v}, is Q = P_TT - P_TR P_RR^{-1} P_RT restricted to {u,v}
 // (inverse of a principal submatrix); r = -Q_uv / sqrt(Q_uu Q_vv), and the
 // Schur complement H of Sec. 4 is Q^{-1}: h11 = Q_vv/det, h22 = Q_uu/det.
+// FP32 evaluation of one complement test with the proof that its decision is the
+// FP64 one.  The test reads P_RR, P_Ru, P_Rv and the {u,v} block of P (FP64,
+// rounded to FP32 on load).  Computed by Cholesky, the result is the exact
+// Q = P_TT - P_TR P_RR^{-1} P_RT ({u,v} block) of P + dP with, to first order,
+// |dP_ij| <= eps s_i s_j, s_i = sqrt(P_ii), eps = (4k + 8) eps32: the rounding
+// of P, the backward errors of the factorisation, the two solves and the final
+// dot products (rows of the factor and the solves have norms s_i, s_u, s_v).
+// With X_a = P_RR^{-1} P_Ra (a in {u, v}) the change of Q is
+//   dQ_ab = dP_ab - dP_aR X_b - X_a^T dP_Rb + X_a^T dP_RR X_b,
+// so |dQ_ab| <= eps W_a W_b with W_a = s_a + sum_r s_r |X_ra|, and for
+// r = -Q_uv / sqrt(Q_uu Q_vv)
+//   |dr| <= eps (W_u W_v / sqrt(Q_uu Q_vv) + |r|/2 (W_u^2/Q_uu + W_v^2/Q_vv)).
+// The expansion is used while eps W_a^2 / Q_aa and kap = k eps tr(D P_RR^{-1} D)
+// (D = diag s_r; tr bounds the norm of the scaled inverse, hence the size of
+// the higher-order terms relative to the first) stay below 0.05; the bound is
+// doubled for those terms and 8 eps32 added for the final ratio and the FP32
+// threshold.  Trusted: the |r| threshold r_q is cleared by more than that, the
+// statistic lies at least `band` from q (as for the direct tests), and the
+// test is far from the FP64 degeneracy rule (h11 = 1/(Q_uu (1 - r^2)) and h22
+// at least 1000 times the floor).  Returns 0 trusted (indep set), 1 band,
+// 2 guard; the FP64 evaluation decides the others.
+__device__ __forceinline__ int comp_test_fp32(const double *P, const int (&sr)[KC_MAX], int su, int sv, int k,
+                                              const TestParams &tp, float sqf, float rq, bool &indep)
+{
+    float L[KC_MAX][KC_MAX], yu[KC_MAX], yv[KC_MAX], sd[KC_MAX], ri[KC_MAX];
+#pragma unroll
+    for (int i = 0; i < KC_MAX; ++i) {
+        yu[i] = yv[i] = sd[i] = ri[i] = 0.f;
+#pragma unroll
+        for (int c = 0; c < KC_MAX; ++c) L[i][c] = 0.f;
+        if (i < k) {
+            const double *Pi = P + (long long)sr[i] * PREC_MAX;
+#pragma unroll
+            for (int c = 0; c <= i; ++c) L[i][c] = (float)Pi[sr[c]];
+            yu[i] = (float)Pi[su];
+            yv[i] = (float)Pi[sv];
+        }
+    }
+    const float Puu = (float)P[su * PREC_MAX + su], Pvv = (float)P[sv * PREC_MAX + sv];
+    float Quv = (float)P[su * PREC_MAX + sv];
+#pragma unroll
+    for (int i = 0; i < KC_MAX; ++i) sd[i] = i < k ? sqrtf(fmaxf(L[i][i], 0.f)) : 0.f;
+    bool bad = false;
+#pragma unroll
+    for (int i = 0; i < KC_MAX; ++i) {
+        if (i >= k || bad) continue;
+#pragma unroll
+        for (int c = 0; c < i; ++c) {
+            float t = L[i][c];
+#pragma unroll
+            for (int q = 0; q < c; ++q) t = fmaf(-L[i][q], L[c][q], t);
+            L[i][c] = t * ri[c];
+        }
+        float t = L[i][i];
+#pragma unroll
+        for (int q = 0; q < i; ++q) t = fmaf(-L[i][q], L[i][q], t);
+        if (!(t > 0.f)) {
+            bad = true;
+            continue;
+        }
+        ri[i] = rsqrtf(t);
+        float a = yu[i], b = yv[i];
+#pragma unroll
+        for (int q = 0; q < i; ++q) {
+            a = fmaf(-L[i][q], yu[q], a);
+            b = fmaf(-L[i][q], yv[q], b);
+        }
+        yu[i] = a * ri[i];
+        yv[i] = b * ri[i];
+    }
+    if (bad) return 2;
+    float Quu = Puu, Qvv = Pvv;
+#pragma unroll
+    for (int i = 0; i < KC_MAX; ++i) {
+        Quu = fmaf(-yu[i], yu[i], Quu);
+        Qvv = fmaf(-yv[i], yv[i], Qvv);
+        Quv = fmaf(-yu[i], yv[i], Quv);
+    }
+    if (!(Quu > 0.f) || !(Qvv > 0.f)) return 2;
+    // X_a = L^{-T} y_a in place (back substitution); W_a
+    float Wu = sqrtf(Puu), Wv = sqrtf(Pvv);
+#pragma unroll
+    for (int i = KC_MAX - 1; i >= 0; --i) {
+        if (i >= k) continue;
+        float a = yu[i], b = yv[i];
+#pragma unroll
+        for (int q = i + 1; q < KC_MAX; ++q)
+            if (q < k) {
+                a = fmaf(-L[q][i], yu[q], a);
+                b = fmaf(-L[q][i], yv[q], b);
+            }
+        yu[i] = a * ri[i];
+        yv[i] = b * ri[i];
+        Wu = fmaf(sd[i], fabsf(yu[i]), Wu);
+        Wv = fmaf(sd[i], fabsf(yv[i]), Wv);
+    }
+    // tr(D P_RR^{-1} D) = sum_j s_j^2 |column j of L^{-1}|^2 (forward substitution per column)
+    float tr = 0.f;
+#pragma unroll
+    for (int j = 0; j < KC_MAX; ++j) {
+        if (j >= k) continue;
+        float m[KC_MAX];
+        float nj = 0.f;
+#pragma unroll
+        for (int i = 0; i < KC_MAX; ++i) {
+            m[i] = 0.f;
+            if (i < j || i >= k) continue;
+            float t = i == j ? 1.f : 0.f;
+#pragma unroll
+            for (int q = 0; q < i; ++q)
+                if (q >= j) t = fmaf(-L[i][q], m[q], t);
+            m[i] = t * ri[i];
+            nj = fmaf(m[i], m[i], nj);
+        }
+        tr = fmaf(sd[j] * sd[j], nj, tr);
+    }
+    const float eps = (4.0f * (float)k + 8.0f) * EPS32;
+    const float kap = (float)k * eps * tr;
+    const float iu = __frcp_rn(Quu), iv = __frcp_rn(Qvv);
+    const float qu = eps * Wu * Wu * iu, qv = eps * Wv * Wv * iv;
+    if (!(fmaxf(fmaxf(qu, qv), kap) <= 0.05f)) return 2;
+    const float ih = rsqrtf(Quu * Qvv);
+    const float a = fabsf(Quv * ih);
+    const float dr = 2.0f * eps * (Wu * Wv * ih + 0.5f * a * (Wu * Wu * iu + Wv * Wv * iv)) + 8.0f * EPS32;
+    if (!(dr <= tp.dr_max)) return 2;
+    const float om = 1.0f - a * a;
+    if (!(om > 8.0f * dr) || Quu * om > 1e9f || Qvv * om > 1e9f) return 2;
+    const float gap = fabsf(a - rq), mn = fminf(a, rq);
+    if (gap <= dr || sqf * gap < (float)tp.band * (1.0f - mn * mn)) return 1;
+    indep = a <= rq;
+    return 0;
+}
+
 constexpr int COMP_OFF_MAX = 2048;    // per-node offsets staged in shared memory up to this p
 __global__ void __launch_bounds__(128) ci_complement_kernel(GraphDev g, TestParams tp)
 {
@@ -1770,7 +1921,10 @@ __global__ void __launch_bounds__(128) ci_complement_kernel(GraphDev g, TestPara
     // |r| threshold of the stage: z <= q  <=>  |r| <= tanh(q / sqrt(n - l - 3)); tests within a
     // relative 1e-12 of it are decided by z itself, exactly as the z form would
     const double rq = tanh(tp.q / sq);
-    ull nt = 0, ndg = 0, nfl = 0;
+    // FP32 first (one problem; a batched handle's nodes differ in n): rq rounded to FP32
+    const bool f32 = tp.comp_fp32 && !tp.nvec;
+    const float sqf = (float)sq, rqf = (float)rq;
+    ull nt = 0, ndg = 0, nfl = 0, nband = 0, nguard = 0;
     const ull nthr = (ull)gridDim.x * blockDim.x;
     // tests are dealt CTA-first, so that a stage with a few thousand tests still
     // spreads its FP64 work (the bound of a test) over every SM
@@ -1796,6 +1950,18 @@ __global__ void __launch_bounds__(128) ci_complement_kernel(GraphDev g, TestPara
         for (int i = 0; i < KC_MAX; ++i) sr[i] = i < k ? ps[cand_node(g, prop, u, j, d, posR[i])] : 0x7fffffff;
         if (prop) sort_fixed<KC_MAX>(sr);                   // ascending slots (ids); unused entries last
         if (best0 < key) continue;                          // an earlier set of this pair separates
+        nfl += (ull)(k * k * k) / 3 + 2ull * k * k + 6ull * k + 20;
+        if (f32) {
+            bool ind32 = false;
+            const int tr32 = comp_test_fp32(P, sr, su, sv, k, tp, sqf, rqf, ind32);
+            if (tr32 == 0) {
+                ++nt;
+                if (ind32) atomicMin(bp, key);
+                continue;
+            }
+            if (tr32 == 1) ++nband;
+            else ++nguard;
+        }
         // every entry of P the test reads (P_RR lower triangle, P_Ru, P_Rv and the {u,v}
         // block) is loaded before the factorisation starts: one round of independent
         // loads instead of one per row
@@ -1868,7 +2034,6 @@ __global__ void __launch_bounds__(128) ci_complement_kernel(GraphDev g, TestPara
             }
         }
         ++nt;
-        nfl += (ull)(k * k * k) / 3 + 2ull * k * k + 6ull * k + 20;
         if (ind) atomicMin(bp, key);
     }
     if (nt) {
@@ -1877,6 +2042,9 @@ __global__ void __launch_bounds__(128) ci_complement_kernel(GraphDev g, TestPara
         atomicAdd(&g.ctr->flops_comp, nfl);
     }
     if (ndg) atomicAdd(&g.ctr->degenerate, ndg);
+    if (nband + nguard) atomicAdd(&g.ctr->redecided, nband + nguard);
+    if (nband) atomicAdd(&g.ctr->band_hits, nband);
+    if (nguard) atomicAdd(&g.ctr->guard_hits, nguard);
 }
 
 // ---------------------------------------------------------------- neighbourhood precision blocks
@@ -1884,6 +2052,19 @@ __global__ void __launch_bounds__(128) ci_complement_kernel(GraphDev g, TestPara
 // deleted (P <- P - P[:,w] P[w,:] / P_ww: the inverse of a principal
 // submatrix); a requested block is built by a symmetric sweep of corr[F,F],
 // F = adj(u) u {u} (ascending ids).
+// 1/v for a pivot v of the block downdate (v > 0 in FP32 range once it passes the
+// DEGEN floor) by two Newton-Raphson steps x <- x + x (1 - v x) from the FP32
+// reciprocal: each step squares the relative error (2^-23 -> 2^-46 -> below the
+// FP64 rounding), so x is within two units in the last place of 1/v, without the
+// IEEE division's slow path on the chain of the factorisation's pivots.
+__device__ __forceinline__ double rcp_newton(double v)
+{
+    double x = (double)__frcp_rn((float)v);
+    x = fma(x, fma(-v, x, 1.0), x);
+    x = fma(x, fma(-v, x, 1.0), x);
+    return x;
+}
+
 constexpr int PREC_CHUNKS = 8;        // CTAs sharing one node's block downdate
 constexpr int PREC_RMAX = 64;         // removals applied in one block downdate (two per lane)
 constexpr int PREC_SHARE_MIN = 16;    // from this many removals one CTA of the cluster factors P_RR
@@ -1997,7 +2178,7 @@ __global__ void __cluster_dims__(1, PREC_CHUNKS, 1) __launch_bounds__(512)
         if (threadIdx.x == 0) {
             const double d = A[0];
             badv[0] = !(d > DEGEN);
-            rdv[0] = 1.0 / d;
+            rdv[0] = rcp_newton(d);
         }
         for (int k = 0; k < nr; ++k) {
             __syncthreads();                     // column k and 1/D_k final
@@ -2021,7 +2202,7 @@ __global__ void __cluster_dims__(1, PREC_CHUNKS, 1) __launch_bounds__(512)
                 A[i * nr + c] = v;
                 if (e == 0) {                                // thread 0: the next pivot
                     badv[(k + 1) & 1] = !(v > DEGEN);
-                    rdv[k + 1] = 1.0 / v;
+                    rdv[k + 1] = rcp_newton(v);
                 }
             }
         }
@@ -2047,6 +2228,14 @@ __global__ void __cluster_dims__(1, PREC_CHUNKS, 1) __launch_bounds__(512)
             return;
         }
         if (t0 >= t1) return;                          // no kept rows in this chunk
+        // the entries P[rem[q]][keep[j]] every row of the update reads (rows of R are
+        // never written here): staged once per CTA, all loads in flight together
+        double *Sg = rdv + nr;                   // nr x nt
+        for (int e = threadIdx.x; e < nr * nt; e += blockDim.x) {
+            const int q = e / nt, j = e - q * nt;
+            Sg[e] = P[(long long)rem[q] * PREC_MAX + keep[j]];
+        }
+        __syncthreads();
         const bool two = nr > 32;                // lanes hold y_q for q = lane, lane + 32
         for (int t = t0 + w; t < t1; t += nw) {
             double *Pi = P + (long long)keep[t] * PREC_MAX;
@@ -2071,13 +2260,13 @@ __global__ void __cluster_dims__(1, PREC_CHUNKS, 1) __launch_bounds__(512)
                 acc[x] = jj < nt ? Pi[keep[jj]] : 0.0;
             }
 #pragma unroll 4
-            for (int q = 0; q < nr; ++q) {                // unrolled: four rows of R in flight
+            for (int q = 0; q < nr; ++q) {
                 const double yq = __shfl_sync(0xffffffffu, q < 32 ? b0 : b1, q & 31);
-                const double *Pq = P + (long long)rem[q] * PREC_MAX;
+                const double *Sq = Sg + q * nt;
 #pragma unroll
                 for (int x = 0; x < PREC_JPL; ++x) {
                     const int jj = lane + 32 * x;
-                    if (jj < nt) acc[x] = fma(-yq, Pq[keep[jj]], acc[x]);
+                    if (jj < nt) acc[x] = fma(-yq, Sq[jj], acc[x]);
                 }
             }
 #pragma unroll
@@ -2144,21 +2333,19 @@ __global__ void __cluster_dims__(1, PREC_CHUNKS, 1) __launch_bounds__(512)
 // first separating set (side, rank, and the expanded node list), reset the
 // key, and count the tests of the sequential canonical order:
 // key (0, rank) -> rank+1; key (1, rank) -> C(d_u,l) + rank+1; none -> both sides.
-__global__ void commit_kernel(GraphDev g, int l_fixed, int explicit_sets, int count_canonical)
+// The commit of CTA `cta` of `ncta` (sb: the small binomial table, loaded).
+__device__ __forceinline__ void commit_body(const GraphDev &g, int l_fixed, int explicit_sets, int count_canonical,
+                                            const ull *sb, int cta, int ncta)
 {
-    if (stopped(g.info)) return;
     const int l = l_fixed >= 0 ? l_fixed : g.info->l;
     const bool prop = stage_prop(g, l);
     const long long nop = g.info->n_opairs;
     const int p = g.p;
     const int lane = threadIdx.x & 31;
     ull removed = 0, canon = 0;
-    __shared__ ull sb[SB_ROWS * SB_COLS];
-    load_small_binom(g, sb);
-    __syncthreads();
     // one ordered pair per thread (grid-stride in warp-aligned steps)
-    for (long long base = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); base < nop;
-         base += (long long)gridDim.x * blockDim.x) {
+    for (long long base = cta * (long long)blockDim.x + (threadIdx.x & ~31); base < nop;
+         base += (long long)ncta * blockDim.x) {
         const long long o = base + lane;
         bool expand = false, cut = false;                 // cut: this lane removes the edge (u, v)
         int su = 0, jj = 0, dd = 0, cu_ = 0, cv_ = 0;
@@ -2170,13 +2357,15 @@ __global__ void commit_kernel(GraphDev g, int l_fixed, int explicit_sets, int co
             const int v = g.nbr[nidx(g, u) + j];
             if (u < v) {
                 const long long e = pidx(g, u, v);
+                // every load of the pair before its first store (the compiler keeps
+                // loads behind stores it cannot prove apart)
                 const ull key = g.best[e];
+                const int du = g.deg[u] - 1, dv = g.deg[v] - 1;
+                const bool dof = !g.nvec || g.nvec[u] - l - 3 > 0;   // u and v share their instance
+                const ull T0 = count_canonical && du >= l && dof ? g.binom[(long long)du * g.ldb + l] : 0ull;
+                const ull T1 = count_canonical && dv >= l && dof ? g.binom[(long long)dv * g.ldb + l] : 0ull;
                 g.best[e] = KEY_NONE;                     // ready for the next stage
                 if (count_canonical) {
-                    const int du = g.deg[u] - 1, dv = g.deg[v] - 1;
-                    const bool dof = !g.nvec || g.nvec[u] - l - 3 > 0;   // u and v share their instance
-                    const ull T0 = du >= l && dof ? g.binom[(long long)du * g.ldb + l] : 0ull;
-                    const ull T1 = dv >= l && dof ? g.binom[(long long)dv * g.ldb + l] : 0ull;
                     ull c;
                     if (key == KEY_NONE) c = sat_add(T0, T1);
                     else if ((key >> 62) == 0) c = key + 1;
@@ -2201,8 +2390,8 @@ __global__ void commit_kernel(GraphDev g, int l_fixed, int explicit_sets, int co
                             g.info->halt = 1;
                         } else {
                             su = side ? v : u;
-                            jj = side ? lower_bound_int(g.nbr + nidx(g, v), g.deg[v], u) : j;
-                            dd = g.deg[su] - 1;
+                            jj = side ? lower_bound_int(g.nbr + nidx(g, v), dv + 1, u) : j;
+                            dd = side ? dv : du;
                             expand = true;
                         }
                     } else {
@@ -2237,21 +2426,32 @@ __global__ void commit_kernel(GraphDev g, int l_fixed, int explicit_sets, int co
                                          posR);
 #pragma unroll
                 for (int i = 0; i < KC_MAX; ++i) nodeR[i] = i < kd ? cand_node(g, prop, su, jj, dd, posR[i]) : -1;
+                // the neighbour list in batches of 8 independent read-only loads (one
+                // round trip per batch, not per neighbour: the pool stores follow them)
                 int o2 = 0;
-                for (int y = 0; y <= dd; ++y) {
-                    if (y == jj) continue;
-                    const int w = nb[y];
-                    bool keep = true;
+                for (int y0 = 0; y0 <= dd; y0 += 8) {
+                    int wv[8];
 #pragma unroll
-                    for (int i = 0; i < KC_MAX; ++i) keep &= nodeR[i] != w;
-                    if (keep) g.pool[off + o2++] = w;
+                    for (int k = 0; k < 8; ++k) wv[k] = y0 + k <= dd ? __ldg(nb + y0 + k) : -1;
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const int y = y0 + k;
+                        if (y > dd || y == jj) continue;
+                        bool keep = true;
+#pragma unroll
+                        for (int i = 0; i < KC_MAX; ++i) keep &= nodeR[i] != wv[k];
+                        if (keep) g.pool[off + o2++] = wv[k];
+                    }
                 }
             } else {
                 ull r = rank;
                 int x = 0;
+                // C(x, r) from the shared table where it covers the walk (x < SB_ROWS, r < SB_COLS)
+                const bool sbl = dd < SB_ROWS && l <= SB_COLS;
                 for (int i = 0; i < l; ++i) {
                     while (x < dd - (l - i)) {
-                        ull c = g.binom[(long long)(dd - x - 1) * g.ldb + (l - i - 1)];
+                        ull c = sbl ? sb[(dd - x - 1) * SB_COLS + (l - i - 1)]
+                                    : g.binom[(long long)(dd - x - 1) * g.ldb + (l - i - 1)];
                         if (r < c) break;
                         r -= c;
                         ++x;
@@ -2266,6 +2466,16 @@ __global__ void commit_kernel(GraphDev g, int l_fixed, int explicit_sets, int co
     if (removed) atomicAdd(&g.ctr->edges_removed, removed);
     if (canon) atomicAdd(&g.ctr->tests_canonical, canon);
 }
+
+__global__ void commit_kernel(GraphDev g, int l_fixed, int explicit_sets, int count_canonical)
+{
+    if (stopped(g.info)) return;
+    __shared__ ull sb[SB_ROWS * SB_COLS];
+    load_small_binom(g, sb);
+    __syncthreads();
+    commit_body(g, l_fixed, explicit_sets, count_canonical, sb, blockIdx.x, gridDim.x);
+}
+
 
 // ---------------------------------------------------------------- re-verification
 // Every explicit separating set recorded in the sepset store is tested again in
@@ -2856,7 +3066,9 @@ cudaError_t launch_prec_update(GraphDev g, TestParams tp, const double *C64, int
 {
     const int mmax = std::min(g.p + 1, PREC_MAX);
     const size_t build = ((size_t)mmax * mmax + (size_t)mmax) * sizeof(double);
-    const size_t down = ((size_t)PREC_RMAX * PREC_RMAX + (size_t)PREC_RMAX) * sizeof(double);
+    // downdate: L (nr x nr), 1/D (nr) and the staged rows of R at the kept columns (nr x nt)
+    const size_t down = ((size_t)PREC_RMAX * PREC_RMAX + (size_t)PREC_RMAX + (size_t)PREC_RMAX * mmax) *
+                        sizeof(double);
     const size_t smem = std::max(build, down);
     cudaError_t e = cudaFuncSetAttribute(prec_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);

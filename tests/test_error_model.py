@@ -336,3 +336,174 @@ def test_bf16x3_entry_errors_stay_below_the_allowance(shape):
     np.fill_diagonal(E, 0.0)
     assert E.max() < 5e-7                     # half the allowance
     assert np.median(E[np.triu_indices(p, 1)]) < 1e-7
+
+
+# --------------------------------------------------------------------------- complement tests
+# The reversed order's high stages test (u, v | S) with S = F \ {u, v} \ R, |R| = k
+# small, from the FP64 precision block P = corr[F,F]^{-1}:  Q = P_TT - P_TR P_RR^{-1}
+# P_RT on {u, v} is the inverse of corr[T,T] there (T = F \ R), r = -Q_uv /
+# sqrt(Q_uu Q_vv).  In FP32 (P rounded on load) the result is that of P + dP,
+# |dP_ij| <= eps s_i s_j (s_i = sqrt(P_ii), eps = (4k + 8) eps32), and to first order
+#   |dr| <= eps (W_u W_v / sqrt(Q_uu Q_vv) + |r|/2 (W_u^2/Q_uu + W_v^2/Q_vv)),
+#   W_a = s_a + sum_r s_r |X_ra|,  X_a = P_RR^{-1} P_Ra,
+# used while eps W_a^2/Q_aa and k eps tr(D P_RR^{-1} D) stay below 0.05, doubled,
+# plus 8 eps32.
+
+def comp_test_fp32(P, R, u, v, sqf, rq, dr_max=1.0):
+    """The complement kernel's FP32 evaluation in its order of operations (R: the
+    dropped slots in ascending order, u and v: slots of the pair)."""
+    k = len(R)
+    L = np.zeros((k, k), f32)
+    yu = np.array([P[r, u] for r in R], dtype=f32)
+    yv = np.array([P[r, v] for r in R], dtype=f32)
+    for i in range(k):
+        for c in range(i + 1):
+            L[i, c] = f32(P[R[i], R[c]])
+    sd = np.array([np.sqrt(max(L[i, i], f32(0)), dtype=f32) for i in range(k)], dtype=f32)
+    ri = np.zeros(k, f32)
+    for i in range(k):
+        for c in range(i):
+            t = L[i, c]
+            for q in range(c):
+                t = f32(t - f32(L[i, q] * L[c, q]))
+            L[i, c] = f32(t * ri[c])
+        t = L[i, i]
+        for q in range(i):
+            t = f32(t - f32(L[i, q] * L[i, q]))
+        if not t > 0:
+            return "queued", None, None, None
+        ri[i] = _rsqrt(t)
+        a, b = yu[i], yv[i]
+        for q in range(i):
+            a = f32(a - f32(L[i, q] * yu[q]))
+            b = f32(b - f32(L[i, q] * yv[q]))
+        yu[i], yv[i] = f32(a * ri[i]), f32(b * ri[i])
+    Quu, Qvv, Quv = f32(P[u, u]), f32(P[v, v]), f32(P[u, v])
+    for i in range(k):
+        Quu = f32(Quu - f32(yu[i] * yu[i]))
+        Qvv = f32(Qvv - f32(yv[i] * yv[i]))
+        Quv = f32(Quv - f32(yu[i] * yv[i]))
+    if not (Quu > 0 and Qvv > 0):
+        return "queued", None, None, None
+    Wu, Wv = np.sqrt(f32(P[u, u]), dtype=f32), np.sqrt(f32(P[v, v]), dtype=f32)
+    for i in range(k - 1, -1, -1):
+        a, b = yu[i], yv[i]
+        for q in range(i + 1, k):
+            a = f32(a - f32(L[q, i] * yu[q]))
+            b = f32(b - f32(L[q, i] * yv[q]))
+        yu[i], yv[i] = f32(a * ri[i]), f32(b * ri[i])
+        Wu = f32(Wu + f32(sd[i] * abs(yu[i])))
+        Wv = f32(Wv + f32(sd[i] * abs(yv[i])))
+    tr = f32(0)
+    for j in range(k):
+        m = np.zeros(k, f32)
+        nj = f32(0)
+        for i in range(j, k):
+            t = f32(1) if i == j else f32(0)
+            for q in range(j, i):
+                t = f32(t - f32(L[i, q] * m[q]))
+            m[i] = f32(t * ri[i])
+            nj = f32(nj + f32(m[i] * m[i]))
+        tr = f32(tr + f32(f32(sd[j] * sd[j]) * nj))
+    eps = f32((4.0 * k + 8.0) * E32)
+    kap = f32(f32(k) * eps * tr)
+    iu, iv = f32(1) / Quu, f32(1) / Qvv
+    if not max(eps * Wu * Wu * iu, eps * Wv * Wv * iv, kap) <= 0.05:
+        return "queued", None, None, None
+    ih = _rsqrt(f32(Quu * Qvv))
+    a = abs(f32(Quv * ih))
+    dr = f32(2) * eps * (Wu * Wv * ih + f32(0.5) * a * (Wu * Wu * iu + Wv * Wv * iv)) + f32(8 * E32)
+    if not dr <= dr_max:
+        return "queued", a, None, dr
+    om = f32(1) - a * a
+    if not om > 8 * dr or Quu * om > 1e9 or Qvv * om > 1e9:
+        return "queued", a, None, dr
+    gap, mn = abs(a - rq), min(a, rq)
+    if gap <= dr or sqf * gap < f32(BAND) * (f32(1) - mn * mn):
+        return "queued", a, None, dr
+    return "trusted", a, bool(a <= rq), dr
+
+
+def _comp_case(rng):
+    """A neighbourhood block F (slot 0 = u, slot 1 = v), a dropped set R of k slots
+    and the FP64 r of (u, v | F \\ {u, v} \\ R) from corr directly."""
+    k = int(rng.integers(1, 9))
+    m = k + 2 + int(rng.integers(0, 30))
+    C = _block(rng, m, (1, 60))
+    P = np.linalg.inv(C)
+    R = sorted(int(x) for x in rng.choice(np.arange(2, m), size=k, replace=False))
+    T = [i for i in range(m) if i not in R]
+    Q = np.linalg.inv(C[np.ix_(T, T)])
+    r64 = -Q[0, 1] / math.sqrt(Q[0, 0] * Q[1, 1])
+    return C, P, R, r64, len(T) - 2
+
+
+def test_trusted_fp32_complement_decisions_equal_fp64():
+    rng = np.random.default_rng(23)
+    q = -statistics.NormalDist().inv_cdf(0.005)
+    rows = []
+    while len(rows) < 700:
+        C, P, R, r64, L = _comp_case(rng)
+        if abs(r64) < 1e-6 or abs(r64) > 0.999:
+            continue
+        n = int(round((q / math.atanh(abs(r64))) ** 2 * (1 + rng.uniform(-0.01, 0.01)) + L + 3))
+        if n - L - 3 <= 0:
+            continue
+        sq = math.sqrt(n - L - 3)
+        z64 = sq * abs(math.atanh(r64))
+        kind, a, ind, dr = comp_test_fp32(P, R, 0, 1, f32(sq), f32(math.tanh(q / sq)))
+        rows.append((kind, a, ind, z64 <= q, abs(r64), dr))
+    trusted = [x for x in rows if x[0] == "trusted"]
+    assert len(trusted) > 0.2 * len(rows)            # within 1 % of the threshold many are still decided
+    assert any(x[0] == "queued" for x in rows)        # and others go to FP64
+    for kind, a, ind, ind64, r64, dr in trusted:
+        assert ind == ind64
+        assert abs(float(a) - r64) <= float(dr)
+
+
+def test_trusted_fp32_complement_far_from_threshold():
+    # at the workloads' sizes most complement tests are far from the threshold:
+    # there nearly all are decided in FP32, and the decisions are the FP64 ones
+    rng = np.random.default_rng(29)
+    q = -statistics.NormalDist().inv_cdf(0.005)
+    n_trusted = n_all = 0
+    while n_all < 400:
+        C, P, R, r64, L = _comp_case(rng)
+        n = int(rng.integers(500, 20000))
+        sq = math.sqrt(n - L - 3)
+        kind, a, ind, dr = comp_test_fp32(P, R, 0, 1, f32(sq), f32(math.tanh(q / sq)))
+        n_all += 1
+        if kind == "trusted":
+            n_trusted += 1
+            assert ind == (sq * abs(math.atanh(r64)) <= q)
+            assert abs(float(a) - abs(r64)) <= float(dr)
+    assert n_trusted > 0.6 * n_all
+
+
+def test_complement_bound_holds_for_exact_perturbations():
+    # the first-order bound (no rounding terms) against exact FP64 arithmetic:
+    # perturbing P by symmetric dP with |dP_ij| <= eps s_i s_j moves r by at most
+    # eps (W_u W_v / sqrt(Q_uu Q_vv) + |r|/2 (W_u^2/Q_uu + W_v^2/Q_vv))
+    rng = np.random.default_rng(31)
+    worst = 0.0
+    for _ in range(300):
+        C, P, R, r64, L = _comp_case(rng)
+        m = P.shape[0]
+        X = np.linalg.solve(P[np.ix_(R, R)], P[np.ix_(R, [0, 1])])
+        Q = P[np.ix_([0, 1], [0, 1])] - P[np.ix_([0, 1], R)] @ X
+        r = -Q[0, 1] / math.sqrt(Q[0, 0] * Q[1, 1])
+        s = np.sqrt(np.diag(P))
+        Wu = s[0] + s[R] @ np.abs(X[:, 0])
+        Wv = s[1] + s[R] @ np.abs(X[:, 1])
+        eps = 1e-9 * min(1.0, Q[0, 0] / Wu ** 2, Q[1, 1] / Wv ** 2)
+        bound = eps * (Wu * Wv / math.sqrt(Q[0, 0] * Q[1, 1]) + abs(r) / 2 * (Wu ** 2 / Q[0, 0] + Wv ** 2 / Q[1, 1]))
+        for _ in range(3):
+            E = np.triu(rng.uniform(-eps, eps, (m, m)), 1)
+            E = E + E.T + np.diag(rng.uniform(-eps, eps, m))
+            P2 = P + E * np.outer(s, s)
+            X2 = np.linalg.solve(P2[np.ix_(R, R)], P2[np.ix_(R, [0, 1])])
+            Q2 = P2[np.ix_([0, 1], [0, 1])] - P2[np.ix_([0, 1], R)] @ X2
+            r2 = -Q2[0, 1] / math.sqrt(Q2[0, 0] * Q2[1, 1])
+            worst = max(worst, abs(r2 - r) / bound)
+        assert abs(r - r64) <= 1e-9 * max(1.0, abs(r64))   # the complement identity itself
+    assert worst <= 1.02

@@ -259,6 +259,20 @@ def test_skeleton_staged_and_global_small_stages(fp, case, node_dmax, pair_warp)
                             pair_warp_dmin=dmin)
 
 
+def test_complement_fp32_first_equals_fp64(fp):
+    """The complement tests of the reversed order in FP32 first (decided there
+    only under the error bound) or in FP64 only: the oracle's skeleton, sets and
+    counts either way; with FP32 first most complement tests are decided in FP32
+    (the FP64 re-decisions they add are few)."""
+    cases = [sem.make(2).X, _sem_case(91, 60, 4000, 0.4), _sem_case(92, 120, 2000, 0.3),
+             _sem_case(93, 80, 800, 0.5)]
+    for X in cases:
+        _, st0 = _check_skeleton(fp, X, order=1, comp_fp32=0)
+        _, st1 = _check_skeleton(fp, X, order=1, comp_fp32=1)
+        assert st1["complement_tests"] == st0["complement_tests"]
+        assert st1["tests_redecided"] - st0["tests_redecided"] <= 0.5 * st1["complement_tests"]
+
+
 def test_staged_kernel_proposal_order(fp):
     """The staged kernel in the proposal order: the sets of a pair are enumerated
     over its permuted candidate list (neighbour indices into the staged block)."""
