@@ -139,6 +139,14 @@ void pc_destroy(pc_handle *h);
  *                 default 128) run on the staged kernel, which holds
  *                 corr[adj(u), adj(u)] in shared memory; the rest read corr
  *                 from L2 (0 = staged kernel off)
+ *   "stage_loop"  1 = in the reversed order with the complement path, problems of
+ *                 p <= 128 run the stages whose tests all take the complement
+ *                 path in one cooperative kernel, a grid-wide barrier where the
+ *                 captured loop has a kernel boundary (head, tests, commit,
+ *                 degrees, next stage, precision blocks); from the first stage
+ *                 with direct tests on, the captured loop (default; skipped on a
+ *                 device without cooperative launches).  0 = the captured loop
+ *                 throughout.  The results are the same either way.
  *   "comp_fp32"   1 = complement tests (reversed order) in FP32 first from the
  *                 FP64 precision blocks, decided there when a first-order
  *                 error bound with validity checks shows the FP64 decision is
@@ -312,9 +320,11 @@ int64_t pc_kernel_launches(void);
  * lists, counts, scans, commit), 6 proposal scoring, ordering and the FP64
  * re-test of the sepsets found in the proposal order, 7 the correlation GEMM
  * kernels alone (the tensor-core product and its split-K reduce, or the SIMT
- * Gram kernel; a part of class 0).  Writes per-class device milliseconds and
- * launch-group counts accumulated since the last reset (reset != 0 clears them
- * afterwards).  ms and count have 8 entries; either may be NULL. */
+ * Gram kernel; a part of class 0), 8 the stage loop in one kernel (option
+ * "stage_loop": every class of work of the stages it runs).  Writes per-class
+ * device milliseconds and launch-group counts accumulated since the last reset
+ * (reset != 0 clears them afterwards).  ms and count have 9 entries; either may
+ * be NULL. */
 pc_status pc_timing(pc_handle *h, double *ms, int64_t *count, int32_t reset);
 
 /* pc_corr_noalloc -- the correlation matrix without any allocation, for

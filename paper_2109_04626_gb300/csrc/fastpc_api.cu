@@ -23,7 +23,7 @@ namespace fpc {
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 }
 
-constexpr int NCLS = 8;   // class 7 (the correlation GEMM kernels) lies inside class 0
+constexpr int NCLS = 9;   // class 7 (the correlation GEMM kernels) lies inside class 0
 struct TimedPair {
     int cls;
     cudaEvent_t a, b;
@@ -65,6 +65,8 @@ struct pc_handle {
     int lane_chunk = 8, lane_rounds = 32, lane_blocks = 8, direct_warps = 8;
     int node_dmax = fpc::NODE_DMAX;   // staged small-stage kernel: largest node degree (0: off)
     int comp_fp32 = 1;                // complement tests in FP32 first (FP32 modes)
+    int stage_loop = 1;               // reversed order, p <= LOOP_PMAX: complement-only stages in one kernel
+    int coop = -1;                    // device supports cooperative launches (-1: not asked yet)
     int pair_warp = 1;                // stages 1-2: warp-per-pair kernel for the larger nodes
     int pair_warp_dmin = fpc::PAIRWARP_DMIN;
     // path-restricted pools (option "path_pool"): component labels of the graph
@@ -100,6 +102,7 @@ struct pc_handle {
     // graph state
     GraphDev g{};
     ull *binom = nullptr;
+    double *rq_tab = nullptr;         // per stage l: tanh(q / sqrt(n - l - 3)), the |r| threshold
     long long opair_cap = 0;
     LevelInfo *info_h = nullptr;     // pinned mirror
     DevCounters *ctr_h = nullptr;    // pinned mirror
@@ -153,8 +156,8 @@ struct pc_handle {
     int timing = 0;
     std::vector<TimedPair> pending;
     std::vector<cudaEvent_t> evpool;
-    double cls_ms[NCLS] = {0, 0, 0, 0, 0, 0, 0, 0};
-    long long cls_n[NCLS] = {0, 0, 0, 0, 0, 0, 0, 0};
+    double cls_ms[NCLS] = {};
+    long long cls_n[NCLS] = {};
 };
 
 // Brackets the launches of one kernel class with events on the handle's stream.
@@ -267,6 +270,7 @@ static TestParams make_tp(const pc_handle *h)
     tp.prow = h->g.prow;
     tp.q = h->q;
     tp.qf = (float)h->q;
+    tp.rq_tab = h->rq_tab;
     tp.band = h->band;
     tp.guard = h->guard;
     tp.eps_c = h->used_tc ? 1.0e-6f : 1.2e-7f;
@@ -338,6 +342,7 @@ static pc_status create_impl(int64_t n, int32_t p, double alpha, int32_t max_lev
     A(dalloc(h, &g.wo_off, (size_t)(p + 2) * sizeof(ull)));
     A(dalloc(h, &g.best, pp * sizeof(ull)));
     A(dalloc(h, &h->binom, (size_t)(pmax + 1) * (pmax + 1) * sizeof(ull)));
+    A(dalloc(h, &h->rq_tab, (size_t)(pmax + 1) * sizeof(double)));
     A(dalloc(h, &g.sep_level, pp * sizeof(int)));
     A(dalloc(h, &g.sep_side, pp * sizeof(int)));
     A(dalloc(h, &g.sep_rank, pp * sizeof(long long)));
@@ -395,6 +400,17 @@ static pc_status create_impl(int64_t n, int32_t p, double alpha, int32_t max_lev
         }
     }
     e = cudaMemcpy(h->binom, B.data(), B.size() * sizeof(ull), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        pc_destroy(h);
+        return PC_ERR_CUDA;
+    }
+    // the stage thresholds, formed once here (an FP64 tanh in every thread of a
+    // stage's kernel costs microseconds on this GPU's FP64 pipe); stages past n - 4
+    // have no tests
+    std::vector<double> rq(pmax + 1, 0.0);
+    for (int l = 0; l <= pmax; ++l)
+        if (n - l - 3 > 0) rq[l] = std::tanh(h->q / std::sqrt((double)(n - l - 3)));
+    e = cudaMemcpy(h->rq_tab, rq.data(), rq.size() * sizeof(double), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         pc_destroy(h);
         return PC_ERR_CUDA;
@@ -605,6 +621,9 @@ extern "C" pc_status pc_set_opt(pc_handle *h, const char *key, double val)
         if (!(val >= 0 && val <= fpc::NODE_DMAX))
             return fail(h, PC_ERR_ARG, "node_dmax must be in [0, " + std::to_string(fpc::NODE_DMAX) + "]");
         h->node_dmax = (int)val;
+    } else if (k == "stage_loop") {
+        if (!(val == 0 || val == 1)) return fail(h, PC_ERR_ARG, "stage_loop must be 0 or 1");
+        h->stage_loop = (int)val;
     } else if (k == "comp_fp32") {
         if (!(val == 0 || val == 1)) return fail(h, PC_ERR_ARG, "comp_fp32 must be 0 or 1");
         h->comp_fp32 = (int)val;
@@ -640,6 +659,7 @@ extern "C" pc_status pc_get_opt(pc_handle *h, const char *key, double *val)
     else if (k == "lane_blocks") *val = h->lane_blocks;
     else if (k == "node_dmax") *val = h->node_dmax;
     else if (k == "comp_fp32") *val = h->comp_fp32;
+    else if (k == "stage_loop") *val = h->stage_loop;
     else if (k == "pair_warp") *val = h->pair_warp;
     else if (k == "path_pool") *val = h->path_pool;
     else if (k == "mlp_backward") *val = h->mlp_bwd_tc;
@@ -1347,6 +1367,22 @@ static pc_status skeleton_enqueue(pc_handle *h)
     if (h->order == 1 && h->complement) {
         Timed t(h, 2);
         CK(fpc::launch_prec_update(g, tp, h->C64, h->ldc, s));
+    }
+    if (h->stage_loop && h->order == 1 && h->complement && p <= fpc::LOOP_PMAX && !h->nblk) {
+        if (h->coop < 0) {
+            int dev = 0, v = 0;
+            CK(cudaGetDevice(&dev));
+            CK(cudaDeviceGetAttribute(&v, cudaDevAttrCooperativeLaunch, dev));
+            h->coop = v;
+        }
+        if (h->coop) {
+            // the complement-only stages in one cooperative kernel; the captured loop
+            // (or the host loop) goes on from the first stage with direct tests
+            Timed t(h, 8);
+            cudaError_t e = fpc::launch_stage_loop(g, tp, h->C64, h->ldc, h->budget, level_cap(h), s);
+            if (e == cudaErrorCooperativeLaunchTooLarge) cudaGetLastError();   // not resident: the loop runs it all
+            else CK(e);
+        }
     }
 
     if (graph) CK(cudaGraphLaunch(h->gexec, s));

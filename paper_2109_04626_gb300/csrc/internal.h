@@ -114,6 +114,9 @@ __host__ __device__ inline int stage_branch(int kind, int comp, int score, int h
 }
 // kernels of a stage outside conditional nodes: head, commit, degrees + tail (one kernel)
 constexpr int STAGE_FIXED_KERNELS = 3;
+// the stage loop in one cooperative kernel (reversed order, complement-only stages)
+constexpr int LOOP_THREADS = 256;
+constexpr int LOOP_PMAX = 128;          // largest p it runs (its shared memory holds a p+1 block)
 
 // Everything the stage kernels need, by value.
 struct GraphDev {
@@ -171,6 +174,7 @@ struct TestParams {
     const long long *prow;  // batched problems: packed row bases of the correlation blocks
     double q;           // threshold Phi^{-1}(1-alpha/2)
     float qf;
+    const double *rq_tab;   // stage l -> tanh(q / sqrt(n - l - 3)) (one problem's n), formed on the host
     double band;        // |z - q| band for FP64 re-decision
     double guard;       // pivot guard
     float eps_c;        // bound on |C32 - corr| (FP32 GEMM or cast: 2^-23; BF16x3 tensor cores: 1e-6)
@@ -282,6 +286,11 @@ cudaError_t launch_orient_codes(GraphDev g, const uint32_t *ah, const uint32_t *
 // degrees of the frozen graph, then (last CTA) the stage tail of mode 0 in the same kernel
 cudaError_t launch_degrees_tail(GraphDev g, TestParams tp, int cap, cudaGraphConditionalHandle hc, int use_cond,
                                 StageConds sc, cudaStream_t s);
+// the reversed order's complement-only stages of a problem of p <= LOOP_PMAX nodes in
+// one cooperative kernel, from the stage the tail scheduled; returns at the first
+// stage with direct tests (cudaErrorCooperativeLaunchTooLarge when it cannot be resident)
+cudaError_t launch_stage_loop(GraphDev g, TestParams tp, const double *C64, int ldc, double budget, int cap,
+                              cudaStream_t s);
 cudaError_t launch_commit(GraphDev g, long long n_opairs_cap, int l_fixed, int explicit_sets,
                           cudaStream_t s);
 size_t scan_ws_bytes(long long n);

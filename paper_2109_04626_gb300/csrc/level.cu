@@ -81,16 +81,16 @@ __global__ void init_adj_kernel(GraphDev g)
 }
 
 // Degrees and ascending neighbour lists of the current graph, one warp per node.
-__global__ void degrees_kernel(GraphDev g)
+// Frozen neighbour list (ascending) and degree of node u from its adjacency row, by
+// the calling warp.  l2: read the row through L2 (words other CTAs of the running
+// kernel cleared with atomics).
+__device__ __forceinline__ void node_degree(const GraphDev &g, int u, int lane, bool l2)
 {
-    const int lane = threadIdx.x & 31;
-    const int u = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
-    if (u >= g.p || stopped(g.info)) return;
     const uint32_t *row = g.adj + (long long)u * g.W;
     int base = 0;
     for (int w0 = 0; w0 < g.W; w0 += 32) {
         const int w = w0 + lane;
-        uint32_t bits = (w < g.W) ? row[w] : 0u;
+        uint32_t bits = (w < g.W) ? (l2 ? __ldcg(row + w) : row[w]) : 0u;
         const int c = __popc(bits);
         int incl = c;
         for (int off = 1; off < 32; off <<= 1) {
@@ -108,6 +108,14 @@ __global__ void degrees_kernel(GraphDev g)
     if (lane == 0) g.deg[u] = base;
 }
 
+__global__ void degrees_kernel(GraphDev g)
+{
+    const int lane = threadIdx.x & 31;
+    const int u = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+    if (u >= g.p || stopped(g.info)) return;
+    node_degree(g, u, lane, false);
+}
+
 __device__ void tail_body(GraphDev g, TestParams tp, int cap, int mode, const int *stagea_singular,
                           int stagea_launched, cudaGraphConditionalHandle hc, int use_cond, StageConds sc,
                           bool fused);
@@ -120,28 +128,7 @@ __global__ void __launch_bounds__(256) degrees_tail_kernel(GraphDev g, TestParam
 {
     const int lane = threadIdx.x & 31;
     const int u = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
-    if (u < g.p && !stopped(g.info)) {
-        const uint32_t *row = g.adj + (long long)u * g.W;
-        int base = 0;
-        for (int w0 = 0; w0 < g.W; w0 += 32) {
-            const int w = w0 + lane;
-            uint32_t bits = (w < g.W) ? row[w] : 0u;
-            const int c = __popc(bits);
-            int incl = c;
-            for (int off = 1; off < 32; off <<= 1) {
-                int t = __shfl_up_sync(0xffffffffu, incl, off);
-                if (lane >= off) incl += t;
-            }
-            int pos = base + incl - c;
-            while (bits) {
-                int t = __ffs(bits) - 1;
-                g.nbr[nidx(g, u) + pos++] = w * 32 + t;
-                bits &= bits - 1;
-            }
-            base += __shfl_sync(0xffffffffu, incl, 31);
-        }
-        if (lane == 0) g.deg[u] = base;
-    }
+    if (u < g.p && !stopped(g.info)) node_degree(g, u, lane, false);
     __shared__ int last;
     __threadfence();
     __syncthreads();
@@ -394,8 +381,8 @@ __device__ __forceinline__ void block_scan_sat(const ull (&v)[NV], ull (&ex)[NV]
 // the direct kernel's shared-memory layout (the host runs that stage).  In the
 // stages of the small-stage kernel it also lays out its rank-major rounds.
 constexpr int HEAD_PER_MAX = MAXP_BATCH / 1024;           // nodes per thread at most
-__global__ void __launch_bounds__(1024) head_kernel(GraphDev g, TestParams tp, double budget,
-                                                    int mmax_direct, StageConds conds)
+__device__ __forceinline__ void head_body(const GraphDev &g, const TestParams &tp, double budget, int mmax_direct,
+                                          const StageConds &conds)
 {
     LevelInfo *I = g.info;
     if (stopped(I)) {
@@ -568,6 +555,12 @@ __global__ void __launch_bounds__(1024) head_kernel(GraphDev g, TestParams tp, d
                                 (tp.pair_warp && l <= PAIRWARP_LMAX ? 1 : 0));
         }
     }
+}
+
+__global__ void __launch_bounds__(1024) head_kernel(GraphDev g, TestParams tp, double budget,
+                                                    int mmax_direct, StageConds conds)
+{
+    head_body(g, tp, budget, mmax_direct, conds);
 }
 
 // test index t of the stage -> (u, j, rank): node by the per-node offsets,
@@ -1900,35 +1893,34 @@ __device__ __forceinline__ int comp_test_fp32(const double *P, const int (&sr)[K
 }
 
 constexpr int COMP_OFF_MAX = 2048;    // per-node offsets staged in shared memory up to this p
-__global__ void __launch_bounds__(128) ci_complement_kernel(GraphDev g, TestParams tp)
+// The complement tests of CTA `cta` of `ncta`.  sb: the unranking table (loaded by
+// the caller); soff: shared room for soff_cap per-node test offsets, used when they
+// fit (the searches in both are chains of dependent loads).
+__device__ __forceinline__ void complement_body(const GraphDev &g, const TestParams &tp, const ull *sb, ull *soff,
+                                                int soff_cap, int cta, int ncta)
 {
     if (stopped(g.info)) return;
     const int l = g.info->l;
     const bool prop = stage_prop(g, l);
     const ull total = g.info->total_comp;
-    if ((ull)blockIdx.x >= total) return;                // no test reaches this CTA
-    // the unranking table and, when they fit, the per-node test offsets in shared
-    // memory: the searches in both are chains of dependent loads
-    __shared__ ull sb[SB_ROWS * SB_COLS];
-    __shared__ ull soff[COMP_OFF_MAX];
-    load_small_binom(g, sb);
-    const bool off_sm = g.p < COMP_OFF_MAX;
+    if ((ull)cta >= total) return;                       // no test reaches this CTA
+    const bool off_sm = g.p < soff_cap;
     if (off_sm)
         for (int i = threadIdx.x; i <= g.p; i += blockDim.x) soff[i] = g.cn_off[i];
     __syncthreads();
     const ull *noff = off_sm ? soff : g.cn_off;
-    const double sq = sqrt((double)(tp.n - l - 3));
-    // |r| threshold of the stage: z <= q  <=>  |r| <= tanh(q / sqrt(n - l - 3)); tests within a
-    // relative 1e-12 of it are decided by z itself, exactly as the z form would
-    const double rq = tanh(tp.q / sq);
+    // |r| threshold of the stage: z <= q  <=>  |r| <= tanh(q / sqrt(n - l - 3)) (from the
+    // host's table); tests within a relative 1e-12 of it are decided by z itself, exactly
+    // as the z form would
+    const double rq = tp.rq_tab[l];
     // FP32 first (one problem; a batched handle's nodes differ in n): rq rounded to FP32
     const bool f32 = tp.comp_fp32 && !tp.nvec;
-    const float sqf = (float)sq, rqf = (float)rq;
+    const float sqf = sqrtf((float)(tp.n - l - 3)), rqf = (float)rq;
     ull nt = 0, ndg = 0, nfl = 0, nband = 0, nguard = 0;
-    const ull nthr = (ull)gridDim.x * blockDim.x;
+    const ull nthr = (ull)ncta * blockDim.x;
     // tests are dealt CTA-first, so that a stage with a few thousand tests still
     // spreads its FP64 work (the bound of a test) over every SM
-    for (ull t = (ull)threadIdx.x * gridDim.x + blockIdx.x; t < total; t += nthr) {
+    for (ull t = (ull)threadIdx.x * ncta + cta; t < total; t += nthr) {
         int u, j, d;
         ull rank;
         locate_test(g, noff, l, t, u, j, d, rank);
@@ -2028,7 +2020,7 @@ __global__ void __launch_bounds__(128) ci_complement_kernel(GraphDev g, TestPara
             if (!tp.nvec && fabs(ar - rq) > 1e-12 * rq) {
                 ind = ar < rq;
             } else {
-                const double squ = tp.nvec ? sqrt((double)(n_of(tp, u) - l - 3)) : sq;
+                const double squ = sqrt((double)(n_of(tp, u) - l - 3));
                 const double z = ar < 1.0 ? squ * fabs(atanh(r)) : INFINITY;
                 ind = z <= tp.q;
             }
@@ -2045,6 +2037,15 @@ __global__ void __launch_bounds__(128) ci_complement_kernel(GraphDev g, TestPara
     if (nband + nguard) atomicAdd(&g.ctr->redecided, nband + nguard);
     if (nband) atomicAdd(&g.ctr->band_hits, nband);
     if (nguard) atomicAdd(&g.ctr->guard_hits, nguard);
+}
+
+__global__ void __launch_bounds__(128) ci_complement_kernel(GraphDev g, TestParams tp)
+{
+    __shared__ ull sb[SB_ROWS * SB_COLS];
+    __shared__ ull soff[COMP_OFF_MAX];
+    if (stopped(g.info) || (ull)blockIdx.x >= g.info->total_comp) return;
+    load_small_binom(g, sb);                             // the body's first barrier covers it
+    complement_body(g, tp, sb, soff, COMP_OFF_MAX, blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------- neighbourhood precision blocks
@@ -2068,7 +2069,6 @@ __device__ __forceinline__ double rcp_newton(double v)
 constexpr int PREC_CHUNKS = 8;        // CTAs sharing one node's block downdate
 constexpr int PREC_RMAX = 64;         // removals applied in one block downdate (two per lane)
 constexpr int PREC_SHARE_MIN = 16;    // from this many removals one CTA of the cluster factors P_RR
-constexpr int PREC_JPL = (PREC_MAX + 31) / 32;   // kept columns per lane
 
 // One node per blockIdx.x, its kept rows split over blockIdx.y.  A maintained
 // block drops the members the last commit deleted, R, all at once (the inverse
@@ -2082,12 +2082,16 @@ constexpr int PREC_JPL = (PREC_MAX + 31) / 32;   // kept columns per lane
 // slot map, so that chunk 0 can retire R (slot map entry -1) at once; members
 // retired earlier are skipped.  A requested block (chunk 0) is built by a
 // symmetric sweep of corr[F,F], F = adj(u) u {u}.
-__global__ void __cluster_dims__(1, PREC_CHUNKS, 1) __launch_bounds__(512)
-    prec_update_kernel(GraphDev g, TestParams tp, const double *C64, int ldc)
+// Node u, chunk `chunk` of `nchunks` (smd: the dynamic shared memory).  CL: the
+// chunks of a node are one thread-block cluster (the kernel below), which shares
+// a large factor through distributed shared memory and retires R in place; else
+// every chunk with rows factors P_RR itself and prec_retire retires R after all
+// chunks are done.
+template <bool CL>
+__device__ __forceinline__ void prec_body(const GraphDev &g, const TestParams &tp, const double *C64, int ldc, int u,
+                                          int chunk, int nchunks, double *smd)
 {
-    const int u = blockIdx.x;
     if (stopped(g.info)) return;
-    extern __shared__ double smd[];
     __shared__ int mem[PREC_MAX];
     __shared__ int bad, nrem;
     const int p = g.p;
@@ -2112,7 +2116,7 @@ __global__ void __cluster_dims__(1, PREC_CHUNKS, 1) __launch_bounds__(512)
                 if (w == u) {
                     kept = true;
                 } else if (pos[w] >= 0) {
-                    kept = (row[w >> 5] >> (w & 31)) & 1u;
+                    kept = (__ldcg(row + (w >> 5)) >> (w & 31)) & 1u;
                     gone = !kept;
                 }
             }
@@ -2142,22 +2146,24 @@ __global__ void __cluster_dims__(1, PREC_CHUNKS, 1) __launch_bounds__(512)
         __syncthreads();
         const int nr = nrem, nt = nkeep;
         if (nr == 0) return;
-        if (blockIdx.y == 0 && threadIdx.x == 0) atomicAdd(&g.ctr->prec_downdates, 1ull);
+        if (chunk == 0 && threadIdx.x == 0) atomicAdd(&g.ctr->prec_downdates, 1ull);
         if (nr > PREC_RMAX) {
             // too many at once: drop the block; it is rebuilt if the node needs it again
-            if (blockIdx.y == 0 && threadIdx.x == 0) g.prec_m[u] = -2;
+            if (chunk == 0 && threadIdx.x == 0) g.prec_m[u] = -2;
             return;
         }
-        // every chunk of the node's cluster has read the slot map (the exits above are
-        // the same in all of them): chunk 0 retires R while the others go on
-        cg::this_cluster().sync();
-        if (blockIdx.y == 0)
-            for (int i = threadIdx.x; i < nr; i += blockDim.x) g.prec_pos[pidx(g, u, pm[rem[i]])] = -1;
-        const int per = (nt + PREC_CHUNKS - 1) / PREC_CHUNKS;
-        const int t0 = blockIdx.y * per, t1 = min(nt, t0 + per);
-        // many removals: cluster rank 0 factors P_RR and the others copy the factor
-        // (distributed shared memory); few: every chunk with rows factors it itself
-        const bool share = nr >= PREC_SHARE_MIN;       // the same in every chunk
+        if constexpr (CL) {
+            // every chunk of the node's cluster has read the slot map (the exits above are
+            // the same in all of them): chunk 0 retires R while the others go on
+            cg::this_cluster().sync();
+            if (chunk == 0)
+                for (int i = threadIdx.x; i < nr; i += blockDim.x) g.prec_pos[pidx(g, u, pm[rem[i]])] = -1;
+        }
+        const int per = (nt + nchunks - 1) / nchunks;
+        const int t0 = chunk * per, t1 = min(nt, t0 + per);
+        // many removals in a cluster: rank 0 factors P_RR and the others copy the factor
+        // (distributed shared memory); else every chunk with rows factors it itself
+        const bool share = CL && nr >= PREC_SHARE_MIN;   // the same in every chunk
         if (!share && t0 >= t1) return;                // no kept rows in this chunk
         // P_RR = L D L^T, right-looking with one barrier per pivot: the trailing update of
         // pivot k reads the unscaled column k (times 1/D_k); column k-1 is scaled to L in
@@ -2166,7 +2172,7 @@ __global__ void __cluster_dims__(1, PREC_CHUNKS, 1) __launch_bounds__(512)
         double *rdv = A + nr * nr;               // 1/D
         const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
         bool brk = false;
-        if (!share || blockIdx.y == 0) {
+        if (!share || chunk == 0) {
         for (int e = threadIdx.x; e < nr * nr; e += blockDim.x) {
             const int a2 = e / nr, b2 = e - a2 * nr;
             if (b2 <= a2) A[e] = P[rem[a2] * PREC_MAX + rem[b2]];
@@ -2208,23 +2214,25 @@ __global__ void __cluster_dims__(1, PREC_CHUNKS, 1) __launch_bounds__(512)
         }
         __syncthreads();
         }
-        if (share) {
-            __shared__ int fac_bad;
-            if (blockIdx.y == 0 && threadIdx.x == 0) fac_bad = brk;
-            cg::cluster_group cl = cg::this_cluster();
-            cl.sync();                                 // rank 0's factor and flag are ready
-            if (blockIdx.y != 0) {
-                brk = *cl.map_shared_rank(&fac_bad, 0) != 0;
-                const double *A0 = cl.map_shared_rank(smd, 0);
-                if (!brk)
-                    for (int e = threadIdx.x; e < nr * nr + nr; e += blockDim.x) smd[e] = A0[e];   // L, then 1/D
+        if constexpr (CL) {
+            if (share) {
+                __shared__ int fac_bad;
+                if (chunk == 0 && threadIdx.x == 0) fac_bad = brk;
+                cg::cluster_group cl = cg::this_cluster();
+                cl.sync();                                 // rank 0's factor and flag are ready
+                if (chunk != 0) {
+                    brk = *cl.map_shared_rank(&fac_bad, 0) != 0;
+                    const double *A0 = cl.map_shared_rank(smd, 0);
+                    if (!brk)
+                        for (int e = threadIdx.x; e < nr * nr + nr; e += blockDim.x) smd[e] = A0[e];   // L, then 1/D
+                }
+                cl.sync();                                 // rank 0 keeps its shared memory until every copy is done
             }
-            cl.sync();                                 // rank 0 keeps its shared memory until every copy is done
         }
         if (brk) {
             // P_RR is a principal block of an SPD inverse; a pivot at the floor means the
             // block has lost accuracy: drop it (rebuilt from corr if the node needs it)
-            if (blockIdx.y == 0 && threadIdx.x == 0) g.prec_m[u] = -2;
+            if (chunk == 0 && threadIdx.x == 0) g.prec_m[u] = -2;
             return;
         }
         if (t0 >= t1) return;                          // no kept rows in this chunk
@@ -2253,33 +2261,29 @@ __global__ void __cluster_dims__(1, PREC_CHUNKS, 1) __launch_bounds__(512)
                 if (lane < k) b0 = fma(-A[k * nr + lane], yk, b0);
                 if (two && lane + 32 < k) b1 = fma(-A[k * nr + lane + 32], yk, b1);
             }
-            double acc[PREC_JPL];
-#pragma unroll
-            for (int x = 0; x < PREC_JPL; ++x) {
-                const int jj = lane + 32 * x;
-                acc[x] = jj < nt ? Pi[keep[jj]] : 0.0;
-            }
+            // the kept columns in groups of 32 (lanes), two groups per pass; only the
+            // groups the row has are issued (the FP64 pipe is the scarce one)
+            for (int x0 = 0; 32 * x0 < nt; x0 += 2) {
+                const int j0 = lane + 32 * x0, j1 = j0 + 32;
+                const bool h1 = 32 * (x0 + 1) < nt;        // warp-uniform: a second group exists
+                double a0 = j0 < nt ? Pi[keep[j0]] : 0.0;
+                double a1 = h1 && j1 < nt ? Pi[keep[j1]] : 0.0;
 #pragma unroll 4
-            for (int q = 0; q < nr; ++q) {
-                const double yq = __shfl_sync(0xffffffffu, q < 32 ? b0 : b1, q & 31);
-                const double *Sq = Sg + q * nt;
-#pragma unroll
-                for (int x = 0; x < PREC_JPL; ++x) {
-                    const int jj = lane + 32 * x;
-                    if (jj < nt) acc[x] = fma(-yq, Sq[jj], acc[x]);
+                for (int q = 0; q < nr; ++q) {
+                    const double yq = __shfl_sync(0xffffffffu, q < 32 ? b0 : b1, q & 31);
+                    const double *Sq = Sg + q * nt;
+                    if (j0 < nt) a0 = fma(-yq, Sq[j0], a0);
+                    if (h1 && j1 < nt) a1 = fma(-yq, Sq[j1], a1);
                 }
-            }
-#pragma unroll
-            for (int x = 0; x < PREC_JPL; ++x) {
-                const int jj = lane + 32 * x;
-                if (jj < nt) Pi[keep[jj]] = acc[x];
+                if (j0 < nt) Pi[keep[j0]] = a0;
+                if (h1 && j1 < nt) Pi[keep[j1]] = a1;
             }
         }
-        if (blockIdx.y == 0 && threadIdx.x == 0)
+        if (chunk == 0 && threadIdx.x == 0)
             atomicAdd(&g.ctr->flops_prec, (ull)nr * nr * nr / 3 + 2ull * nt * nr * (nr + nt));
         return;
     }
-    if (blockIdx.y != 0 || !g.prec_need[u]) return;
+    if (chunk != 0 || !g.prec_need[u]) return;
     const int m = g.deg[u] + 1;
     if (threadIdx.x == 0) {
         bad = 0;
@@ -2325,6 +2329,29 @@ __global__ void __cluster_dims__(1, PREC_CHUNKS, 1) __launch_bounds__(512)
         g.prec_need[u] = 0;
         atomicAdd(&g.ctr->flops_prec, (ull)m * m * m);
         atomicAdd(&g.ctr->prec_builds, 1ull);
+    }
+}
+
+__global__ void __cluster_dims__(1, PREC_CHUNKS, 1) __launch_bounds__(512)
+    prec_update_kernel(GraphDev g, TestParams tp, const double *C64, int ldc)
+{
+    extern __shared__ double smd[];
+    prec_body<true>(g, tp, C64, ldc, blockIdx.x, blockIdx.y, PREC_CHUNKS, smd);
+}
+
+// After prec_body<false> of every chunk: the slots of node u's maintained block
+// whose members the commit deleted leave the slot map (entry -1).  A dropped
+// block (prec_m <= 0) keeps its stale map until it is rebuilt.
+__device__ __forceinline__ void prec_retire(const GraphDev &g, int u)
+{
+    const int m0 = g.prec_m[u];
+    if (m0 <= 0) return;
+    const int *pm = g.prec_mem + (long long)u * PREC_MAX;
+    short *pos = g.prec_pos + pidx(g, u, 0);
+    const uint32_t *row = g.adj + (long long)u * g.W;
+    for (int sl = threadIdx.x; sl < m0; sl += blockDim.x) {
+        const int w = pm[sl];
+        if (w != u && pos[w] >= 0 && !((row[w >> 5] >> (w & 31)) & 1u)) pos[w] = -1;
     }
 }
 
@@ -2474,6 +2501,59 @@ __global__ void commit_kernel(GraphDev g, int l_fixed, int explicit_sets, int co
     load_small_binom(g, sb);
     __syncthreads();
     commit_body(g, l_fixed, explicit_sets, count_canonical, sb, blockIdx.x, gridDim.x);
+}
+
+// ---------------------------------------------------------------- stage loop in one kernel
+// Small problems in the reversed order (Algorithm 2) spend most of a stage on the
+// latency of its launches, not on its tests.  This cooperative kernel runs the
+// stages whose tests all take the complement path, one after the other, with a
+// grid-wide barrier where the captured loop has a kernel boundary:
+//   head (CTA 0) and the previous stage's retirement of deleted members |
+//   complement tests | commit | degrees | tail (CTA 0) | precision downdates and builds.
+// It returns at the first stage with direct tests (the captured loop, whose head
+// recomputes that stage, runs it and the rest), or when the search ends or halts.
+// The one exit is taken by all CTAs together: it reads the loop state right after
+// the head's barrier, and nothing writes that state (done, halt, the stage's direct
+// count) before the next barrier (the head returns at once once the search has
+// ended or halted; commit, tail and head write it in phases of their own).
+__global__ void __launch_bounds__(LOOP_THREADS, 1) stage_loop_kernel(GraphDev g, TestParams tp, const double *C64,
+                                                                     int ldc, double budget, int cap, int chunks)
+{
+    cg::grid_group grid = cg::this_grid();
+    extern __shared__ double lsm[];
+    __shared__ ull sb[SB_ROWS * SB_COLS];
+    __shared__ ull soff[LOOP_PMAX + 1];
+    LevelInfo *I = g.info;
+    load_small_binom(g, sb);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), nwg = (int)((gridDim.x * blockDim.x) >> 5);
+    for (int it = 0; it <= g.p; ++it) {                 // one pass per stage, at most p stages
+        if (blockIdx.x == 0) head_body(g, tp, budget, 1 << 30, StageConds{});
+        // beside the head (which reads no slot map): the previous stage's deleted
+        // members leave the slot maps (no barrier inside; repeating it is harmless)
+        if (it > 0)
+            for (int u = blockIdx.x; u < g.p; u += gridDim.x) prec_retire(g, u);
+        grid.sync();
+        if (stopped(I) || I->total_direct > 0) break;
+        complement_body(g, tp, sb, soff, LOOP_PMAX + 1, blockIdx.x, gridDim.x);
+        grid.sync();
+        if (!stopped(I)) commit_body(g, -1, 1, 1, sb, blockIdx.x, gridDim.x);
+        grid.sync();
+        if (!stopped(I))
+            for (int u = gw; u < g.p; u += nwg) node_degree(g, u, lane, true);
+        grid.sync();
+        if (blockIdx.x == 0) tail_body(g, tp, cap, 0, nullptr, 0, 0, 0, StageConds{}, true);
+        grid.sync();
+        for (int item = blockIdx.x; item < g.p * chunks; item += gridDim.x) {
+            prec_body<false>(g, tp, C64, ldc, item / chunks, item % chunks, chunks, lsm);
+            __syncthreads();                            // the body's shared arrays are reused
+        }
+        grid.sync();
+    }
+    // the last stage's deletions, also when the loop ran out of passes (no barrier
+    // needed: nothing else runs in the kernel any more)
+    for (int u = blockIdx.x; u < g.p; u += gridDim.x) prec_retire(g, u);
 }
 
 
@@ -3062,19 +3142,47 @@ cudaError_t launch_ci_complement(GraphDev g, TestParams tp, cudaStream_t s)
     return cudaGetLastError();
 }
 
+static size_t prec_smem_bytes(int p);
+
 cudaError_t launch_prec_update(GraphDev g, TestParams tp, const double *C64, int ldc, cudaStream_t s)
 {
-    const int mmax = std::min(g.p + 1, PREC_MAX);
-    const size_t build = ((size_t)mmax * mmax + (size_t)mmax) * sizeof(double);
-    // downdate: L (nr x nr), 1/D (nr) and the staged rows of R at the kept columns (nr x nt)
-    const size_t down = ((size_t)PREC_RMAX * PREC_RMAX + (size_t)PREC_RMAX + (size_t)PREC_RMAX * mmax) *
-                        sizeof(double);
-    const size_t smem = std::max(build, down);
+    const size_t smem = prec_smem_bytes(g.p);
     cudaError_t e = cudaFuncSetAttribute(prec_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     prec_update_kernel<<<dim3(g.p, PREC_CHUNKS), 512, smem, s>>>(g, tp, C64, ldc); note_launch();
     return cudaGetLastError();
+}
+
+static size_t prec_smem_bytes(int p)
+{
+    const int mmax = std::min(p + 1, PREC_MAX);
+    const size_t build = ((size_t)mmax * mmax + (size_t)mmax) * sizeof(double);
+    // downdate: L (nr x nr), 1/D (nr) and the staged rows of R at the kept columns (nr x nt)
+    const size_t down = ((size_t)PREC_RMAX * PREC_RMAX + (size_t)PREC_RMAX + (size_t)PREC_RMAX * mmax) *
+                        sizeof(double);
+    return std::max(build, down);
+}
+
+cudaError_t launch_stage_loop(GraphDev g, TestParams tp, const double *C64, int ldc, double budget, int cap,
+                              cudaStream_t s)
+{
+    if (g.p > LOOP_PMAX) return cudaErrorInvalidValue;
+    const size_t smem = prec_smem_bytes(g.p);
+    cudaError_t e = cudaFuncSetAttribute(stage_loop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_loop_kernel, LOOP_THREADS, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+    const int grid = num_sms() * std::min(per_sm, 2);   // every CTA resident (cooperative launch)
+    // a node's kept rows over PREC_CHUNKS CTAs (consecutive items: different SMs), so
+    // that the FP64 work of a large downdate is spread
+    int chunks = PREC_CHUNKS;
+    void *args[] = {&g, &tp, (void *)&C64, &ldc, &budget, &cap, &chunks};
+    e = cudaLaunchCooperativeKernel((const void *)stage_loop_kernel, dim3(grid), dim3(LOOP_THREADS), args, smem, s);
+    note_launch();
+    return e;
 }
 
 cudaError_t launch_commit(GraphDev g, long long n_opairs_cap, int l_fixed, int explicit_sets,

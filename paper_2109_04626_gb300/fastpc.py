@@ -344,7 +344,8 @@ def pc_kernel_launches() -> int:
 
 
 # class "corr_gemm" (the correlation GEMM kernels alone) is a part of class "corr"
-TIMING_CLASSES = ["corr", "stage_a", "prec", "ci_direct", "ci_complement", "bookkeeping", "scoring", "corr_gemm"]
+TIMING_CLASSES = ["corr", "stage_a", "prec", "ci_direct", "ci_complement", "bookkeeping", "scoring", "corr_gemm",
+                  "stage_loop"]
 
 
 def pc_timing(h, reset: bool = False) -> dict:

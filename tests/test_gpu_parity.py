@@ -259,6 +259,28 @@ def test_skeleton_staged_and_global_small_stages(fp, case, node_dmax, pair_warp)
                             pair_warp_dmin=dmin)
 
 
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_stage_loop_in_one_kernel_equals_captured_loop(fp, precision):
+    """The reversed order's complement-only stages in one cooperative kernel
+    (option stage_loop) or in the captured stage loop: the oracle's skeleton,
+    sets, counts and stages either way -- dense and sparse problems, a problem
+    whose later stages have direct tests (the kernel hands over to the captured
+    loop), a level cap, p at the kernel's limit, host-driven and timed loops."""
+    cases = [(sem.make(2).X, -1), (_sem_case(91, 60, 4000, 0.4), -1), (_sem_case(94, 128, 3000, 0.3), -1),
+             (_sem_case(95, 40, 600, 0.6), -1), (_sem_case(95, 40, 600, 0.6), 25), (sem.make(1).X, -1)]
+    for X, ml in cases:
+        for opts in ({"stage_loop": 1}, {"stage_loop": 0}, {"stage_loop": 1, "graph": 0}):
+            R, st = _check_skeleton(fp, X, max_level=ml, order=1, precision=precision, **opts)
+            assert st["levels_run"] == len(R["levels"])
+    X = sem.make(2).X
+    n, p = X.shape
+    with fp.PC(n, p, 0.01, -1, order=1, timing=1) as pc:
+        pc.corr(torch.from_numpy(X).cuda())
+        pc.skeleton()
+        tm = fp.pc_timing(pc.h)
+        assert tm["stage_loop"][1] == 1 and tm["stage_loop"][0] > 0
+
+
 def test_complement_fp32_first_equals_fp64(fp):
     """The complement tests of the reversed order in FP32 first (decided there
     only under the error bound) or in FP64 only: the oracle's skeleton, sets and
