@@ -330,6 +330,7 @@ static pc_status create_impl(int64_t n, int32_t p, double alpha, int32_t max_lev
     auto A = [&](cudaError_t ee) { if (e == cudaSuccess) e = ee; };
     A(dalloc(h, &g.adj, (size_t)p * W * sizeof(uint32_t)));
     A(dalloc(h, &g.deg, (size_t)p * sizeof(int)));
+    A(dalloc(h, &g.dchg, (size_t)p * sizeof(int)));
     A(dalloc(h, &g.nbr, pp * sizeof(int)));
     A(dalloc(h, &g.ooff, (size_t)(p + 1) * sizeof(long long)));
     A(dalloc(h, &g.opu, (size_t)p * pmax * sizeof(int)));   // ordered pairs <= p * (largest p)
@@ -1366,6 +1367,8 @@ static pc_status skeleton_enqueue(pc_handle *h)
     }
     if (h->order == 1 && h->complement) {
         Timed t(h, 2);
+        // after the closed-form stage: blocks from its inverse, then one downdate each
+        if (stage_a_launched && p <= fpc::PREC_MAX) CK(fpc::launch_prec_seed(g, h->Pbuf, h->ldc, s));
         CK(fpc::launch_prec_update(g, tp, h->C64, h->ldc, s));
     }
     if (h->stage_loop && h->order == 1 && h->complement && p <= fpc::LOOP_PMAX && !h->nblk) {

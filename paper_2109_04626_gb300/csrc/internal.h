@@ -124,6 +124,7 @@ struct GraphDev {
     int W;                      // 32-bit words per adjacency row
     uint32_t *adj;              // p x W bitset
     int *deg;                   // p
+    int *dchg;                  // p: neighbours the last degree pass found deleted (old - new degree)
     int *nbr;                   // p x p, ascending neighbour ids of the frozen graph
     long long *ooff;            // p+1, exclusive scan of deg (ordered-pair offsets)
     int *opu;                   // per ordered pair: its node u (stages of the small-stage kernel)
@@ -286,6 +287,9 @@ cudaError_t launch_orient_codes(GraphDev g, const uint32_t *ah, const uint32_t *
 // degrees of the frozen graph, then (last CTA) the stage tail of mode 0 in the same kernel
 cudaError_t launch_degrees_tail(GraphDev g, TestParams tp, int cap, cudaGraphConditionalHandle hc, int use_cond,
                                 StageConds sc, cudaStream_t s);
+// the first stage's precision blocks seeded from the closed-form stage's inverse P
+// (the downdate that follows drops the non-neighbours)
+cudaError_t launch_prec_seed(GraphDev g, const double *P, int ldp, cudaStream_t s);
 // the reversed order's complement-only stages of a problem of p <= LOOP_PMAX nodes in
 // one cooperative kernel, from the stage the tail scheduled; returns at the first
 // stage with direct tests (cudaErrorCooperativeLaunchTooLarge when it cannot be resident)

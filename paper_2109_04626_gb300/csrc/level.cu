@@ -86,6 +86,7 @@ __global__ void init_adj_kernel(GraphDev g)
 // kernel cleared with atomics).
 __device__ __forceinline__ void node_degree(const GraphDev &g, int u, int lane, bool l2)
 {
+    const int old = lane == 0 ? (l2 ? __ldcg(g.deg + u) : g.deg[u]) : 0;
     const uint32_t *row = g.adj + (long long)u * g.W;
     int base = 0;
     for (int w0 = 0; w0 < g.W; w0 += 32) {
@@ -105,7 +106,10 @@ __device__ __forceinline__ void node_degree(const GraphDev &g, int u, int lane, 
         }
         base += __shfl_sync(0xffffffffu, incl, 31);
     }
-    if (lane == 0) g.deg[u] = base;
+    if (lane == 0) {
+        g.deg[u] = base;
+        g.dchg[u] = old - base;
+    }
 }
 
 __global__ void degrees_kernel(GraphDev g)
@@ -2096,6 +2100,9 @@ __device__ __forceinline__ void prec_body(const GraphDev &g, const TestParams &t
     __shared__ int bad, nrem;
     const int p = g.p;
     const int m0 = g.prec_m[u];
+    // a maintained block loses exactly the neighbours the last degree pass found
+    // deleted (its live members are the neighbours of the previous stage): none, no work
+    if (m0 > 0 && g.dchg[u] == 0) return;
     if (m0 > 0) {
         int *rem = mem;
         __shared__ int keep[PREC_MAX];
@@ -2337,6 +2344,35 @@ __global__ void __cluster_dims__(1, PREC_CHUNKS, 1) __launch_bounds__(512)
 {
     extern __shared__ double smd[];
     prec_body<true>(g, tp, C64, ldc, blockIdx.x, blockIdx.y, PREC_CHUNKS, smd);
+}
+
+// The first stage's blocks from the closed-form stage's inverse P = corr^{-1}: node
+// u's block starts as all of P (every node a member, slot = id), and the downdate
+// that follows drops the non-neighbours R = V \ F, which leaves corr[F,F]^{-1}
+// (the inverse of a principal submatrix, as for every later deletion), F = adj(u)
+// u {u}: a downdate of |R| members instead of a sweep of the whole neighbourhood.
+// Nodes with more than PREC_RMAX non-neighbours keep the sweep build.
+__global__ void __launch_bounds__(256) prec_seed_kernel(GraphDev g, const double *P, int ldp)
+{
+    const int u = blockIdx.x;
+    const LevelInfo *I = g.info;
+    const int p = g.p;
+    if (stopped(I) || !I->stage_a_ran || !g.prec_need[u] || p - 1 - g.deg[u] > PREC_RMAX) return;
+    double *B = g.prec + (long long)u * PREC_MAX * PREC_MAX;
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+        const int i = e / p, j = e - i * p;
+        B[(long long)i * PREC_MAX + j] = P[(long long)i * ldp + j];
+    }
+    for (int w = threadIdx.x; w < p; w += blockDim.x) {
+        g.prec_mem[(long long)u * PREC_MAX + w] = w;
+        g.prec_pos[pidx(g, u, w)] = (short)w;
+    }
+    if (threadIdx.x == 0) {
+        g.prec_m[u] = p;
+        g.prec_need[u] = 0;
+        g.dchg[u] = p - 1 - g.deg[u];                  // the downdate's removals
+        atomicAdd(&g.ctr->prec_builds, 1ull);
+    }
 }
 
 // After prec_body<false> of every chunk: the slots of node u's maintained block
@@ -3162,6 +3198,13 @@ static size_t prec_smem_bytes(int p)
     const size_t down = ((size_t)PREC_RMAX * PREC_RMAX + (size_t)PREC_RMAX + (size_t)PREC_RMAX * mmax) *
                         sizeof(double);
     return std::max(build, down);
+}
+
+cudaError_t launch_prec_seed(GraphDev g, const double *P, int ldp, cudaStream_t s)
+{
+    if (g.p > PREC_MAX) return cudaErrorInvalidValue;
+    prec_seed_kernel<<<g.p, 256, 0, s>>>(g, P, ldp); note_launch();
+    return cudaGetLastError();
 }
 
 cudaError_t launch_stage_loop(GraphDev g, TestParams tp, const double *C64, int ldc, double budget, int cap,
