@@ -385,7 +385,7 @@ __device__ __forceinline__ void block_scan_sat(const ull (&v)[NV], ull (&ex)[NV]
 // the direct kernel's shared-memory layout (the host runs that stage).  In the
 // stages of the small-stage kernel it also lays out its rank-major rounds.
 constexpr int HEAD_PER_MAX = MAXP_BATCH / 1024;           // nodes per thread at most
-__device__ __forceinline__ void head_body(const GraphDev &g, const TestParams &tp, double budget, int mmax_direct,
+__device__ __noinline__ void head_body(const GraphDev &g, const TestParams &tp, double budget, int mmax_direct,
                                           const StageConds &conds)
 {
     LevelInfo *I = g.info;
@@ -1900,18 +1900,22 @@ constexpr int COMP_OFF_MAX = 2048;    // per-node offsets staged in shared memor
 // The complement tests of CTA `cta` of `ncta`.  sb: the unranking table (loaded by
 // the caller); soff: shared room for soff_cap per-node test offsets, used when they
 // fit (the searches in both are chains of dependent loads).
-__device__ __forceinline__ void complement_body(const GraphDev &g, const TestParams &tp, const ull *sb, ull *soff,
-                                                int soff_cap, int cta, int ncta)
+// planned: soff already holds this CTA's own copy of the stage's offsets (soff[p] =
+// the total) and the stage is unscored (the stage loop's stages have no direct tests).
+__device__ __noinline__ void complement_body(const GraphDev &g, const TestParams &tp, const ull *sb, ull *soff,
+                                                int soff_cap, int cta, int ncta, bool planned = false)
 {
-    if (stopped(g.info)) return;
+    if (!planned && stopped(g.info)) return;
     const int l = g.info->l;
-    const bool prop = stage_prop(g, l);
-    const ull total = g.info->total_comp;
+    const bool prop = !planned && stage_prop(g, l);
+    const ull total = planned ? soff[g.p] : g.info->total_comp;
     if ((ull)cta >= total) return;                       // no test reaches this CTA
-    const bool off_sm = g.p < soff_cap;
-    if (off_sm)
-        for (int i = threadIdx.x; i <= g.p; i += blockDim.x) soff[i] = g.cn_off[i];
-    __syncthreads();
+    const bool off_sm = planned || g.p < soff_cap;
+    if (!planned) {
+        if (off_sm)
+            for (int i = threadIdx.x; i <= g.p; i += blockDim.x) soff[i] = g.cn_off[i];
+        __syncthreads();
+    }
     const ull *noff = off_sm ? soff : g.cn_off;
     // |r| threshold of the stage: z <= q  <=>  |r| <= tanh(q / sqrt(n - l - 3)) (from the
     // host's table); tests within a relative 1e-12 of it are decided by z itself, exactly
@@ -2089,8 +2093,8 @@ constexpr int PREC_SHARE_MIN = 16;    // from this many removals one CTA of the 
 // Node u, chunk `chunk` of `nchunks` (smd: the dynamic shared memory).  CL: the
 // chunks of a node are one thread-block cluster (the kernel below), which shares
 // a large factor through distributed shared memory and retires R in place; else
-// every chunk with rows factors P_RR itself and prec_retire retires R after all
-// chunks are done.
+// every chunk with rows factors P_RR itself and prec_retire retires R once every
+// chunk is done.
 template <bool CL>
 __device__ __forceinline__ void prec_body(const GraphDev &g, const TestParams &tp, const double *C64, int ldc, int u,
                                           int chunk, int nchunks, double *smd)
@@ -2346,6 +2350,22 @@ __global__ void __cluster_dims__(1, PREC_CHUNKS, 1) __launch_bounds__(512)
     prec_body<true>(g, tp, C64, ldc, blockIdx.x, blockIdx.y, PREC_CHUNKS, smd);
 }
 
+// After prec_body<false> of every chunk: the slots of node u's maintained block
+// whose members the commit deleted leave the slot map (entry -1).  A dropped
+// block (prec_m <= 0) keeps its stale map until it is rebuilt.
+__device__ __forceinline__ void prec_retire(const GraphDev &g, int u)
+{
+    const int m0 = g.prec_m[u];
+    if (m0 <= 0) return;
+    const int *pm = g.prec_mem + (long long)u * PREC_MAX;
+    short *pos = g.prec_pos + pidx(g, u, 0);
+    const uint32_t *row = g.adj + (long long)u * g.W;
+    for (int sl = threadIdx.x; sl < m0; sl += blockDim.x) {
+        const int w = pm[sl];
+        if (w != u && pos[w] >= 0 && !((row[w >> 5] >> (w & 31)) & 1u)) pos[w] = -1;
+    }
+}
+
 // The first stage's blocks from the closed-form stage's inverse P = corr^{-1}: node
 // u's block starts as all of P (every node a member, slot = id), and the downdate
 // that follows drops the non-neighbours R = V \ F, which leaves corr[F,F]^{-1}
@@ -2375,30 +2395,16 @@ __global__ void __launch_bounds__(256) prec_seed_kernel(GraphDev g, const double
     }
 }
 
-// After prec_body<false> of every chunk: the slots of node u's maintained block
-// whose members the commit deleted leave the slot map (entry -1).  A dropped
-// block (prec_m <= 0) keeps its stale map until it is rebuilt.
-__device__ __forceinline__ void prec_retire(const GraphDev &g, int u)
-{
-    const int m0 = g.prec_m[u];
-    if (m0 <= 0) return;
-    const int *pm = g.prec_mem + (long long)u * PREC_MAX;
-    short *pos = g.prec_pos + pidx(g, u, 0);
-    const uint32_t *row = g.adj + (long long)u * g.W;
-    for (int sl = threadIdx.x; sl < m0; sl += blockDim.x) {
-        const int w = pm[sl];
-        if (w != u && pos[w] >= 0 && !((row[w >> 5] >> (w & 31)) & 1u)) pos[w] = -1;
-    }
-}
-
 // ---------------------------------------------------------------- commit
 // End of stage l (PC-stable): delete every pair with a recorded key, store its
 // first separating set (side, rank, and the expanded node list), reset the
 // key, and count the tests of the sequential canonical order:
 // key (0, rank) -> rank+1; key (1, rank) -> C(d_u,l) + rank+1; none -> both sides.
 // The commit of CTA `cta` of `ncta` (sb: the small binomial table, loaded).
+// soo: when given, a shared copy of the ordered-pair offsets (p+1 entries): the
+// owner of a pair is found there instead of in the head's owner table.
 __device__ __forceinline__ void commit_body(const GraphDev &g, int l_fixed, int explicit_sets, int count_canonical,
-                                            const ull *sb, int cta, int ncta)
+                                            const ull *sb, int cta, int ncta, const long long *soo = nullptr)
 {
     const int l = l_fixed >= 0 ? l_fixed : g.info->l;
     const bool prop = stage_prop(g, l);
@@ -2415,7 +2421,8 @@ __device__ __forceinline__ void commit_body(const GraphDev &g, int l_fixed, int 
         ull rank = 0, off = 0;
         if (o < nop) {
             // owner node: the head kernel's table inside the stage loop, else a search
-            const int u = l_fixed < 0 ? g.opu[o] : (int)(upper_bound_dev(g.ooff, (long long)p + 1, o) - 1);
+            const int u = soo ? (int)(upper_bound_dev(soo, (long long)p + 1, o) - 1)
+                              : l_fixed < 0 ? g.opu[o] : (int)(upper_bound_dev(g.ooff, (long long)p + 1, o) - 1);
             const int j = (int)(o - g.ooff[u]);
             const int v = g.nbr[nidx(g, u) + j];
             if (u < v) {
@@ -2540,18 +2547,46 @@ __global__ void commit_kernel(GraphDev g, int l_fixed, int explicit_sets, int co
 }
 
 // ---------------------------------------------------------------- stage loop in one kernel
+// Every CTA of the stage loop plans stage l itself, as the head does: the
+// complement tests' per-node offsets in shared memory (soff[p] = their total) and
+// the direct-test total.  True when the stage is one for the loop: no direct
+// tests, nothing saturated, within the budget (the captured loop's head reports
+// the others).  sh: 64 words of scratch.
+__device__ __forceinline__ bool loop_stage_plan(const GraphDev &g, const TestParams &tp, int l, double budget,
+                                                ull *soff, ull *sh)
+{
+    const int t = threadIdx.x, p = g.p;                // p <= LOOP_PMAX < blockDim.x
+    ull v[2] = {0ull, 0ull};
+    bool sat = false;
+    if (t < p) {
+        const int dg = g.deg[t], d = dg - 1;
+        const ull T = (dg > 0 && d >= l && dof_ok(tp, t, l)) ? g.binom[(long long)d * g.ldb + l] : 0ull;
+        const ull tot = sat_mul(T, (ull)dg);
+        sat = tot == KEY_NONE;
+        if (T && comp_eligible(d, l, tp) && g.prec_m[t] > 0) v[0] = tot;
+        else v[1] = tot;
+    }
+    const int ssat = __syncthreads_or(sat);
+    ull ex[2], tot[2];
+    block_scan_sat<2>(v, ex, tot, sh);
+    if (t < p) soff[t] = ex[0];
+    if (t == 0) soff[p] = tot[0];
+    __syncthreads();
+    return !ssat && tot[0] != KEY_NONE && tot[1] == 0 && (double)tot[0] <= budget;
+}
+
 // Small problems in the reversed order (Algorithm 2) spend most of a stage on the
 // latency of its launches, not on its tests.  This cooperative kernel runs the
 // stages whose tests all take the complement path, one after the other, with a
 // grid-wide barrier where the captured loop has a kernel boundary:
-//   head (CTA 0) and the previous stage's retirement of deleted members |
-//   complement tests | commit | degrees | tail (CTA 0) | precision downdates and builds.
+//   plan (every CTA: the head's offsets, in its shared memory), the previous
+//   stage's retirement of deleted block members, complement tests | commit (the
+//   owner of a pair found in a shared copy of the pair offsets) | degrees |
+//   tail (CTA 0) | precision downdates and builds.
 // It returns at the first stage with direct tests (the captured loop, whose head
 // recomputes that stage, runs it and the rest), or when the search ends or halts.
-// The one exit is taken by all CTAs together: it reads the loop state right after
-// the head's barrier, and nothing writes that state (done, halt, the stage's direct
-// count) before the next barrier (the head returns at once once the search has
-// ended or halted; commit, tail and head write it in phases of their own).
+// The exits are taken by all CTAs together: `done` and `halt` are written only in
+// the tail and commit phases, and every CTA plans the stage from the same data.
 __global__ void __launch_bounds__(LOOP_THREADS, 1) stage_loop_kernel(GraphDev g, TestParams tp, const double *C64,
                                                                      int ldc, double budget, int cap, int chunks)
 {
@@ -2559,22 +2594,27 @@ __global__ void __launch_bounds__(LOOP_THREADS, 1) stage_loop_kernel(GraphDev g,
     extern __shared__ double lsm[];
     __shared__ ull sb[SB_ROWS * SB_COLS];
     __shared__ ull soff[LOOP_PMAX + 1];
+    __shared__ ull sh[2 * 32];
+    __shared__ long long soo[LOOP_PMAX + 1];
     LevelInfo *I = g.info;
     load_small_binom(g, sb);
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), nwg = (int)((gridDim.x * blockDim.x) >> 5);
     for (int it = 0; it <= g.p; ++it) {                 // one pass per stage, at most p stages
-        if (blockIdx.x == 0) head_body(g, tp, budget, 1 << 30, StageConds{});
-        // beside the head (which reads no slot map): the previous stage's deleted
-        // members leave the slot maps (no barrier inside; repeating it is harmless)
+        if (stopped(I)) break;
+        if (!loop_stage_plan(g, tp, I->l, budget, soff, sh)) break;
+        // the previous stage's deletions leave the slot maps (the complement tests
+        // read only the slots of current neighbours; repeating it is harmless)
         if (it > 0)
             for (int u = blockIdx.x; u < g.p; u += gridDim.x) prec_retire(g, u);
+        complement_body(g, tp, sb, soff, LOOP_PMAX + 1, blockIdx.x, gridDim.x, true);
         grid.sync();
-        if (stopped(I) || I->total_direct > 0) break;
-        complement_body(g, tp, sb, soff, LOOP_PMAX + 1, blockIdx.x, gridDim.x);
-        grid.sync();
-        if (!stopped(I)) commit_body(g, -1, 1, 1, sb, blockIdx.x, gridDim.x);
+        if (!stopped(I)) {
+            for (int i = threadIdx.x; i <= g.p; i += blockDim.x) soo[i] = g.ooff[i];
+            __syncthreads();
+            commit_body(g, -1, 1, 1, sb, blockIdx.x, gridDim.x, soo);
+        }
         grid.sync();
         if (!stopped(I))
             for (int u = gw; u < g.p; u += nwg) node_degree(g, u, lane, true);
@@ -2591,7 +2631,6 @@ __global__ void __launch_bounds__(LOOP_THREADS, 1) stage_loop_kernel(GraphDev g,
     // needed: nothing else runs in the kernel any more)
     for (int u = blockIdx.x; u < g.p; u += gridDim.x) prec_retire(g, u);
 }
-
 
 // ---------------------------------------------------------------- re-verification
 // Every explicit separating set recorded in the sepset store is tested again in

@@ -291,7 +291,8 @@ def test_complement_fp32_first_equals_fp64(fp):
     for X in cases:
         _, st0 = _check_skeleton(fp, X, order=1, comp_fp32=0)
         _, st1 = _check_skeleton(fp, X, order=1, comp_fp32=1)
-        assert st1["complement_tests"] == st0["complement_tests"]
+        # executed counts are speculative (a test is skipped once an earlier set of its
+        # pair is recorded, which depends on timing); the canonical counts are checked above
         assert st1["tests_redecided"] - st0["tests_redecided"] <= 0.5 * st1["complement_tests"]
 
 
