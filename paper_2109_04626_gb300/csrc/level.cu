@@ -1902,8 +1902,11 @@ constexpr int COMP_OFF_MAX = 2048;    // per-node offsets staged in shared memor
 // fit (the searches in both are chains of dependent loads).
 // planned: soff already holds this CTA's own copy of the stage's offsets (soff[p] =
 // the total) and the stage is unscored (the stage loop's stages have no direct tests).
+// sdeg, sT: with planned, the degree and C(d, l) of every node (shared), so that a
+// test is located without global loads.
 __device__ __noinline__ void complement_body(const GraphDev &g, const TestParams &tp, const ull *sb, ull *soff,
-                                                int soff_cap, int cta, int ncta, bool planned = false)
+                                                int soff_cap, int cta, int ncta, bool planned = false,
+                                                const int *sdeg = nullptr, const ull *sT = nullptr)
 {
     if (!planned && stopped(g.info)) return;
     const int l = g.info->l;
@@ -1930,8 +1933,18 @@ __device__ __noinline__ void complement_body(const GraphDev &g, const TestParams
     // spreads its FP64 work (the bound of a test) over every SM
     for (ull t = (ull)threadIdx.x * ncta + cta; t < total; t += nthr) {
         int u, j, d;
-        ull rank;
-        locate_test(g, noff, l, t, u, j, d, rank);
+        ull rank, T;
+        if (sdeg) {
+            u = (int)(upper_bound_dev(noff, (long long)g.p + 1, t) - 1);
+            d = sdeg[u] - 1;
+            T = sT[u];
+            const ull w = t - noff[u], jj = w / T;
+            j = (int)jj;
+            rank = w - jj * T;
+        } else {
+            locate_test(g, noff, l, t, u, j, d, rank);
+            T = g.binom[(long long)d * g.ldb + l];
+        }
         const int v = g.nbr[nidx(g, u) + j];
         const int k = d - l;
         const int side = u > v;
@@ -1939,7 +1952,6 @@ __device__ __noinline__ void complement_body(const GraphDev &g, const TestParams
         const ull key = ((ull)side << 62) | rank;
         ull *bp = g.best + pidx(g, a, b);
         const ull best0 = *(volatile ull *)bp;            // checked below, once the candidates are known
-        const ull T = g.binom[(long long)d * g.ldb + l];
         int posR[KC_MAX];
         unrank_lex_fixed<KC_MAX>(T - 1 - rank, d, k, sb, SB_COLS, posR);   // complement of lex is reverse lex
         const double *P = g.prec + (long long)u * PREC_MAX * PREC_MAX;
@@ -2096,8 +2108,9 @@ constexpr int PREC_SHARE_MIN = 16;    // from this many removals one CTA of the 
 // every chunk with rows factors P_RR itself and prec_retire retires R once every
 // chunk is done.
 template <bool CL>
+// need: the node's build request (-1: read it from the tail's flags in memory).
 __device__ __forceinline__ void prec_body(const GraphDev &g, const TestParams &tp, const double *C64, int ldc, int u,
-                                          int chunk, int nchunks, double *smd)
+                                          int chunk, int nchunks, double *smd, int need = -1)
 {
     if (stopped(g.info)) return;
     __shared__ int mem[PREC_MAX];
@@ -2294,7 +2307,7 @@ __device__ __forceinline__ void prec_body(const GraphDev &g, const TestParams &t
             atomicAdd(&g.ctr->flops_prec, (ull)nr * nr * nr / 3 + 2ull * nt * nr * (nr + nt));
         return;
     }
-    if (chunk != 0 || !g.prec_need[u]) return;
+    if (chunk != 0 || !(need < 0 ? g.prec_need[u] : need)) return;
     const int m = g.deg[u] + 1;
     if (threadIdx.x == 0) {
         bad = 0;
@@ -2551,9 +2564,10 @@ __global__ void commit_kernel(GraphDev g, int l_fixed, int explicit_sets, int co
 // complement tests' per-node offsets in shared memory (soff[p] = their total) and
 // the direct-test total.  True when the stage is one for the loop: no direct
 // tests, nothing saturated, within the budget (the captured loop's head reports
-// the others).  sh: 64 words of scratch.
+// the others).  sh: 64 words of scratch; sdeg, sT receive every node's degree and
+// C(d, l).
 __device__ __forceinline__ bool loop_stage_plan(const GraphDev &g, const TestParams &tp, int l, double budget,
-                                                ull *soff, ull *sh)
+                                                ull *soff, ull *sh, int *sdeg, ull *sT)
 {
     const int t = threadIdx.x, p = g.p;                // p <= LOOP_PMAX < blockDim.x
     ull v[2] = {0ull, 0ull};
@@ -2561,6 +2575,8 @@ __device__ __forceinline__ bool loop_stage_plan(const GraphDev &g, const TestPar
     if (t < p) {
         const int dg = g.deg[t], d = dg - 1;
         const ull T = (dg > 0 && d >= l && dof_ok(tp, t, l)) ? g.binom[(long long)d * g.ldb + l] : 0ull;
+        sdeg[t] = dg;
+        sT[t] = T;
         const ull tot = sat_mul(T, (ull)dg);
         sat = tot == KEY_NONE;
         if (T && comp_eligible(d, l, tp) && g.prec_m[t] > 0) v[0] = tot;
@@ -2575,18 +2591,50 @@ __device__ __forceinline__ bool loop_stage_plan(const GraphDev &g, const TestPar
     return !ssat && tot[0] != KEY_NONE && tot[1] == 0 && (double)tot[0] <= budget;
 }
 
+// Every CTA of the stage loop forms the tail's results it needs from the degrees
+// of the new frozen graph (stage l just committed): the ordered-pair offsets
+// (soo[p] = their total), and per node the precision-block request for the next
+// stage min(l - 1, L*) (reversed order), as the tail does.  CTA 0's tail writes
+// the same into memory for the captured loop.  sh: 32 words of scratch.
+__device__ __forceinline__ void loop_tail_plan(const GraphDev &g, const TestParams &tp, int l, long long *soo,
+                                               int *sneed, ull *sh)
+{
+    __shared__ int smx[32];
+    const int t = threadIdx.x, p = g.p, lane = t & 31, w = t >> 5;
+    const int dg = t < p ? __ldcg(g.deg + t) : 0;
+    ull v[1] = {(ull)dg}, ex[1], tot[1];
+    block_scan_sat<1>(v, ex, tot, sh);
+    int mx = dg;
+    for (int off = 16; off > 0; off >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if (lane == 0) smx[w] = mx;
+    if (t < p) soo[t] = (long long)ex[0];
+    if (t == 0) soo[p] = (long long)tot[0];
+    __syncthreads();
+    int lmax = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) lmax = max(lmax, smx[i]);
+    const int nl = min(l - 1, lmax - 1);
+    if (t < p) {
+        const int pm = g.prec_m[t];
+        sneed[t] = nl >= 0 && dg > 0 && comp_eligible(dg - 1, nl, tp) && (pm == 0 || pm == -2);
+    }
+    __syncthreads();
+}
+
 // Small problems in the reversed order (Algorithm 2) spend most of a stage on the
 // latency of its launches, not on its tests.  This cooperative kernel runs the
 // stages whose tests all take the complement path, one after the other, with a
 // grid-wide barrier where the captured loop has a kernel boundary:
-//   plan (every CTA: the head's offsets, in its shared memory), the previous
-//   stage's retirement of deleted block members, complement tests | commit (the
+//   plan (every CTA: the head's offsets, in its shared memory), complement tests,
+//   the previous stage's retirement of deleted block members | commit (the
 //   owner of a pair found in a shared copy of the pair offsets) | degrees |
-//   tail (CTA 0) | precision downdates and builds.
+//   tail (CTA 0 into memory; every CTA forms the offsets and block requests it
+//   needs itself) and precision downdates and builds.
 // It returns at the first stage with direct tests (the captured loop, whose head
 // recomputes that stage, runs it and the rest), or when the search ends or halts.
 // The exits are taken by all CTAs together: `done` and `halt` are written only in
-// the tail and commit phases, and every CTA plans the stage from the same data.
+// the commit and the last phase (the tail), each followed by a barrier, and every
+// CTA plans the stage from the same data.  The stage l is read once per pass, at
+// its start: the tail moves it on in the last phase.
 __global__ void __launch_bounds__(LOOP_THREADS, 1) stage_loop_kernel(GraphDev g, TestParams tp, const double *C64,
                                                                      int ldc, double budget, int cap, int chunks)
 {
@@ -2596,33 +2644,37 @@ __global__ void __launch_bounds__(LOOP_THREADS, 1) stage_loop_kernel(GraphDev g,
     __shared__ ull soff[LOOP_PMAX + 1];
     __shared__ ull sh[2 * 32];
     __shared__ long long soo[LOOP_PMAX + 1];
+    __shared__ int sdeg[LOOP_PMAX];
+    __shared__ ull sT[LOOP_PMAX];
+    __shared__ int sneed[LOOP_PMAX];
     LevelInfo *I = g.info;
     load_small_binom(g, sb);
+    for (int i = threadIdx.x; i <= g.p; i += blockDim.x) soo[i] = g.ooff[i];   // the first stage's, from the tail
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), nwg = (int)((gridDim.x * blockDim.x) >> 5);
     for (int it = 0; it <= g.p; ++it) {                 // one pass per stage, at most p stages
         if (stopped(I)) break;
-        if (!loop_stage_plan(g, tp, I->l, budget, soff, sh)) break;
-        // the previous stage's deletions leave the slot maps (the complement tests
+        const int lcur = I->l;                          // moved on only by the tail below
+        if (!loop_stage_plan(g, tp, lcur, budget, soff, sh, sdeg, sT)) break;
+        complement_body(g, tp, sb, soff, LOOP_PMAX + 1, blockIdx.x, gridDim.x, true, sdeg, sT);
+        // then the previous stage's deletions leave the slot maps (the complement tests
         // read only the slots of current neighbours; repeating it is harmless)
         if (it > 0)
             for (int u = blockIdx.x; u < g.p; u += gridDim.x) prec_retire(g, u);
-        complement_body(g, tp, sb, soff, LOOP_PMAX + 1, blockIdx.x, gridDim.x, true);
         grid.sync();
-        if (!stopped(I)) {
-            for (int i = threadIdx.x; i <= g.p; i += blockDim.x) soo[i] = g.ooff[i];
-            __syncthreads();
-            commit_body(g, -1, 1, 1, sb, blockIdx.x, gridDim.x, soo);
-        }
+        if (!stopped(I)) commit_body(g, -1, 1, 1, sb, blockIdx.x, gridDim.x, soo);
         grid.sync();
         if (!stopped(I))
             for (int u = gw; u < g.p; u += nwg) node_degree(g, u, lane, true);
         grid.sync();
+        // the tail: CTA 0 in memory (next stage, loop end, offsets, requests), every
+        // CTA for itself what the downdates and the next commit need
         if (blockIdx.x == 0) tail_body(g, tp, cap, 0, nullptr, 0, 0, 0, StageConds{}, true);
-        grid.sync();
+        loop_tail_plan(g, tp, lcur, soo, sneed, sh);
         for (int item = blockIdx.x; item < g.p * chunks; item += gridDim.x) {
-            prec_body<false>(g, tp, C64, ldc, item / chunks, item % chunks, chunks, lsm);
+            const int u = item / chunks;
+            prec_body<false>(g, tp, C64, ldc, u, item % chunks, chunks, lsm, sneed[u]);
             __syncthreads();                            // the body's shared arrays are reused
         }
         grid.sync();
