@@ -544,14 +544,18 @@ __global__ void __launch_bounds__(256) syrk_kernel(const T *__restrict__ Xs, lon
 }
 
 // Split-K FP64 Gram: CTA (tile, split) accumulates K range
-// [split*kchunk, min(n, (split+1)*kchunk)) of an upper-triangle 64x64 tile into
-// ws[(split*ntiles + tile)][64][64]; syrk_reduce_kernel then adds the splits
+// [split*kchunk, min(n, (split+1)*kchunk)) of an upper-triangle BT x BT tile into
+// ws[(split*ntiles + tile)][BT][BT]; syrk_reduce_kernel then adds the splits
 // in a fixed order (deterministic), scales by 1/n, mirrors, sets the diagonal.
+// BT 64 (4 x 4 outputs per thread) for large p; BT 32 (2 x 2) for p <= 128, where
+// 64-wide tiles would pad the matrix to 128 and nearly double the FP64 work (the
+// FP64 pipe is what bounds this kernel on GB300).
+template <int BT>
 __global__ void __launch_bounds__(256) syrk_f64_split_kernel(const double *__restrict__ Xs, long long n,
                                                              long long ldk, int p, long long kchunk,
                                                              double *ws)
 {
-    constexpr int BT = 64, BK = 32;
+    constexpr int BK = 32, RT = BT / 16;                 // RT x RT outputs per thread
     __shared__ double As[BK][BT + 1];
     __shared__ double Bs[BK][BT + 1];
     const int tile = blockIdx.x, nt = (p + BT - 1) / BT;
@@ -562,11 +566,11 @@ __global__ void __launch_bounds__(256) syrk_f64_split_kernel(const double *__res
     const int a0 = bi * BT, b0 = bj * BT;
     const long long kb = (long long)blockIdx.y * kchunk;
     const long long ke = kb + kchunk < n ? kb + kchunk : n;
-    double acc[4][4];
+    double acc[RT][RT];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < RT; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+        for (int j = 0; j < RT; ++j) acc[i][j] = 0.0;
     for (long long k0 = kb; k0 < ke; k0 += BK) {
         for (int e = threadIdx.x; e < BT * BK; e += 256) {
             int r = e / BK, k = e % BK;
@@ -578,29 +582,29 @@ __global__ void __launch_bounds__(256) syrk_f64_split_kernel(const double *__res
         __syncthreads();
 #pragma unroll 8
         for (int k = 0; k < BK; ++k) {
-            double av[4], bv[4];
+            double av[RT], bv[RT];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) av[i] = As[k][ty * 4 + i];
+            for (int i = 0; i < RT; ++i) av[i] = As[k][ty * RT + i];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) bv[j] = Bs[k][tx * 4 + j];
+            for (int j = 0; j < RT; ++j) bv[j] = Bs[k][tx * RT + j];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < RT; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+                for (int j = 0; j < RT; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
         }
         __syncthreads();
     }
     double *out = ws + ((size_t)blockIdx.y * gridDim.x + tile) * (BT * BT);
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < RT; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) out[(ty * 4 + i) * BT + tx * 4 + j] = acc[i][j];
+        for (int j = 0; j < RT; ++j) out[(ty * RT + i) * BT + tx * RT + j] = acc[i][j];
 }
 
+template <int BT>
 __global__ void __launch_bounds__(256) syrk_reduce_kernel(const double *ws, int p, int ntiles_total,
                                                           int splits, long long n, double *C, int ldc)
 {
-    constexpr int BT = 64;
     const int tile = blockIdx.x, nt = (p + BT - 1) / BT;
     const int e0 = blockIdx.y * (BT * BT / 8), e1 = e0 + BT * BT / 8;
     int t = tile, bi = 0;
@@ -631,9 +635,12 @@ static int sm_count()
     return g_sms;
 }
 
+static int syrk_tile(int p) { return p <= 128 ? 32 : 64; }
+
 static void syrk_split_shape(long long n, int p, int &ntiles, int &splits, long long &kchunk)
 {
-    const int nt = (p + 63) / 64;
+    const int bt = syrk_tile(p);
+    const int nt = (p + bt - 1) / bt;
     ntiles = nt * (nt + 1) / 2;
     const long long kt = (n + 31) / 32;                   // 32-wide K steps
     long long sp = (2LL * sm_count() + ntiles - 1) / ntiles;
@@ -648,7 +655,8 @@ size_t syrk_f64_ws_bytes(long long n, int p)
     int ntiles, splits;
     long long kchunk;
     syrk_split_shape(n, p, ntiles, splits, kchunk);
-    return (size_t)ntiles * splits * 64 * 64 * sizeof(double);
+    const int bt = syrk_tile(p);
+    return (size_t)ntiles * splits * bt * bt * sizeof(double);
 }
 
 // Lazy FP64 correlations: unit diagonal, no entry valid yet.
@@ -809,9 +817,15 @@ cudaError_t launch_syrk_f64(const double *Xs, long long n, long long ldk, int p,
     int ntiles, splits;
     long long kchunk;
     syrk_split_shape(n, p, ntiles, splits, kchunk);
-    if (ws_bytes < (size_t)ntiles * splits * 64 * 64 * sizeof(double)) return cudaErrorInvalidValue;
-    syrk_f64_split_kernel<<<dim3(ntiles, splits), 256, 0, s>>>(Xs, n, ldk, p, kchunk, ws); note_launch();
-    syrk_reduce_kernel<<<dim3(ntiles, 8), 256, 0, s>>>(ws, p, ntiles, splits, n, C64, ldc); note_launch();
+    const int bt = syrk_tile(p);
+    if (ws_bytes < (size_t)ntiles * splits * bt * bt * sizeof(double)) return cudaErrorInvalidValue;
+    if (bt == 32) {
+        syrk_f64_split_kernel<32><<<dim3(ntiles, splits), 256, 0, s>>>(Xs, n, ldk, p, kchunk, ws); note_launch();
+        syrk_reduce_kernel<32><<<dim3(ntiles, 8), 256, 0, s>>>(ws, p, ntiles, splits, n, C64, ldc); note_launch();
+    } else {
+        syrk_f64_split_kernel<64><<<dim3(ntiles, splits), 256, 0, s>>>(Xs, n, ldk, p, kchunk, ws); note_launch();
+        syrk_reduce_kernel<64><<<dim3(ntiles, 8), 256, 0, s>>>(ws, p, ntiles, splits, n, C64, ldc); note_launch();
+    }
     return cudaGetLastError();
 }
 

@@ -19,6 +19,19 @@ __device__ __forceinline__ long long cidx(const long long *prow, int ldc, int a,
     return prow ? __ldg(prow + a) + c : (long long)a * ldc + c;
 }
 
+// 1/v for a pivot v (v > 0 in FP32 range once it passes the DEGEN floor) by two
+// Newton-Raphson steps x <- x + x (1 - v x) from the FP32 reciprocal: each step
+// squares the relative error (2^-23 -> 2^-46 -> below the FP64 rounding), so x is
+// within two units in the last place of 1/v, without the IEEE division's slow
+// path (a long FP64 sequence, and GB300's FP64 pipe is narrow) on a pivot chain.
+__device__ __forceinline__ double rcp_newton(double v)
+{
+    double x = (double)__frcp_rn((float)v);
+    x = fma(x, fma(-v, x, 1.0), x);
+    x = fma(x, fma(-v, x, 1.0), x);
+    return x;
+}
+
 // Symmetric sweep of every pivot of an SPD matrix in shared memory:
 // A <- -A^{-1}.  Pivot k is used without row exchanges, so it equals the
 // conditional variance of k given 0..k-1 (the degeneracy test of the oracle's
@@ -37,7 +50,7 @@ __device__ __forceinline__ void sweep_inverse_block(double *A, int m, int lda, d
         }
         for (int i = threadIdx.x; i < m; i += blockDim.x) colk[i] = A[i * lda + k];
         __syncthreads();
-        const double iD = 1.0 / D;
+        const double iD = rcp_newton(D);
         for (int i = ty; i < m; i += ny) {
             const double ci = colk[i] * iD;
             for (int j = i + tx; j < m; j += 32) {

@@ -2073,19 +2073,6 @@ __global__ void __launch_bounds__(128) ci_complement_kernel(GraphDev g, TestPara
 // deleted (P <- P - P[:,w] P[w,:] / P_ww: the inverse of a principal
 // submatrix); a requested block is built by a symmetric sweep of corr[F,F],
 // F = adj(u) u {u} (ascending ids).
-// 1/v for a pivot v of the block downdate (v > 0 in FP32 range once it passes the
-// DEGEN floor) by two Newton-Raphson steps x <- x + x (1 - v x) from the FP32
-// reciprocal: each step squares the relative error (2^-23 -> 2^-46 -> below the
-// FP64 rounding), so x is within two units in the last place of 1/v, without the
-// IEEE division's slow path on the chain of the factorisation's pivots.
-__device__ __forceinline__ double rcp_newton(double v)
-{
-    double x = (double)__frcp_rn((float)v);
-    x = fma(x, fma(-v, x, 1.0), x);
-    x = fma(x, fma(-v, x, 1.0), x);
-    return x;
-}
-
 constexpr int PREC_CHUNKS = 8;        // CTAs sharing one node's block downdate
 constexpr int PREC_RMAX = 64;         // removals applied in one block downdate (two per lane)
 constexpr int PREC_SHARE_MIN = 16;    // from this many removals one CTA of the cluster factors P_RR

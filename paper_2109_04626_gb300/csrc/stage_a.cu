@@ -14,11 +14,14 @@ namespace cg = cooperative_groups;
 
 // The same symmetric sweep (A <- -A^{-1}, pivots in order, no exchanges) on a
 // cluster of SA_CLUSTER CTAs: CTA r holds rows [r*rpc, (r+1)*rpc) in shared
-// memory; at pivot k every CTA copies row k (= column k, A stays symmetric) from
-// its owner through distributed shared memory, then updates its own rows.  Each
-// entry (i, j) is computed with the operands the one-CTA sweep uses for the
-// pair {i, j}, so the result is bit-identical to it; GB300's FP64 rate (about
-// 2 FMA per clock per SM) is what the cluster multiplies.
+// memory.  At pivot k every CTA copies row k (= column k, A stays symmetric) from
+// its owner's broadcast buffer through distributed shared memory and updates its
+// own rows; the owner of row k+1 then publishes that row into the other of its two
+// buffers, and one cluster barrier ends the pivot (a reader of buffer k%2 is done
+// with it before the barrier; it is written again only after the next one).  Each
+// entry (i, j) is computed with the operands the one-CTA sweep uses for the pair
+// {i, j}, so the result is bit-identical to it; GB300's FP64 rate (about 2 FMA per
+// clock per SM) is what the cluster multiplies.
 constexpr int SA_CLUSTER = 8;
 __global__ void __cluster_dims__(SA_CLUSTER, 1, 1) __launch_bounds__(256)
     inverse_cluster_kernel(double *A, int m, int lda, int *singular)
@@ -29,21 +32,25 @@ __global__ void __cluster_dims__(SA_CLUSTER, 1, 1) __launch_bounds__(256)
     const int rpc = (m + SA_CLUSTER - 1) / SA_CLUSTER;
     const int i0 = min(m, r * rpc), i1 = min(m, i0 + rpc), nr = i1 - i0;
     double *R = smc;                                   // own rows, row-major, m per row
-    double *colk = smc + (size_t)rpc * m;
+    double *colk = smc + (size_t)rpc * m;              // this CTA's copy of row k
+    double *bc = colk + m;                             // two broadcast rows (the owner's)
     for (int e = threadIdx.x; e < nr * m; e += blockDim.x) R[e] = A[(long long)(i0 + e / m) * lda + e % m];
+    __syncthreads();
+    if (i0 == 0 && nr > 0)
+        for (int j = threadIdx.x; j < m; j += blockDim.x) bc[j] = R[j];
     bool bad = false;
     cl.sync();
     for (int k = 0; k < m; ++k) {
         const int owner = k / rpc;
-        const double *rowk = cl.map_shared_rank(R, owner) + (size_t)(k - owner * rpc) * m;
+        const double *rowk = cl.map_shared_rank(bc, owner) + (size_t)(k & 1) * m;
         for (int j = threadIdx.x; j < m; j += blockDim.x) colk[j] = rowk[j];
-        cl.sync();                                     // row k copied everywhere: its owner may update it
+        __syncthreads();
         const double D = colk[k];
         if (!(D > DEGEN)) {                            // the same pivot in every CTA: a uniform exit
             bad = true;
             break;
         }
-        const double iD = 1.0 / D;
+        const double iD = rcp_newton(D);
         for (int e = threadIdx.x; e < nr * m; e += blockDim.x) {
             const int i = i0 + e / m, j = e - (e / m) * m;
             double v;
@@ -53,8 +60,13 @@ __global__ void __cluster_dims__(SA_CLUSTER, 1, 1) __launch_bounds__(256)
             else v = fma(-(colk[j] * iD), colk[i], R[e]);
             R[e] = v;
         }
-        cl.sync();                                     // pivot k applied before row k+1 is read
+        __syncthreads();
+        if (k + 1 < m && k + 1 >= i0 && k + 1 < i1)      // publish row k+1, as updated by pivot k
+            for (int j = threadIdx.x; j < m; j += blockDim.x)
+                bc[(size_t)((k + 1) & 1) * m + j] = R[(size_t)(k + 1 - i0) * m + j];
+        cl.sync();
     }
+    cl.sync();                                         // no CTA leaves while another reads its buffers
     if (bad) {
         if (r == 0 && threadIdx.x == 0) *singular = 1;
         return;
@@ -99,7 +111,7 @@ __global__ void gj_update_kernel(double *A, int m, int lda, int k, const double 
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y;
     if (j >= m) return;
-    const double ip = 1.0 / rowk[k];
+    const double ip = rcp_newton(rowk[k]);
     double v;
     if (i == k) v = (j == k) ? ip : rowk[j] * ip;
     else if (j == k) v = -colk[i] * ip;
@@ -113,7 +125,7 @@ cudaError_t launch_inverse_spd(double *A, int m, int lda, double *work, int *sin
     cudaError_t e = cudaMemsetAsync(singular, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     // a cluster of SA_CLUSTER CTAs when the rows fit their shared memory
-    const size_t smem_c = ((size_t)((m + SA_CLUSTER - 1) / SA_CLUSTER) * m + (size_t)m) * sizeof(double);
+    const size_t smem_c = ((size_t)((m + SA_CLUSTER - 1) / SA_CLUSTER) * m + 3 * (size_t)m) * sizeof(double);
     if (m >= 32 && smem_c <= 200 * 1024) {
         e = cudaFuncSetAttribute(inverse_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c);
         if (e != cudaSuccess) return e;

@@ -1,4 +1,5 @@
-"""The reciprocal the precision-block downdate uses for its pivots (no GPU
+"""The reciprocal the FP64 pivot chains use (the precision-block downdate, the
+symmetric sweeps of the closed-form stage and of the block builds; no GPU
 needed): two Newton-Raphson steps x <- x + x (1 - v x) from the FP32
 reciprocal.  Each step squares the relative error, 2^-23 -> 2^-46 -> below the
 FP64 rounding, so the result lies within two units in the last place of 1/v
