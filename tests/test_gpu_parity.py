@@ -377,8 +377,8 @@ def test_skeleton_degenerate_duplicate_column(fp):
 
 @pytest.mark.parametrize("precision", [0, 2])
 def test_stage_a_singular_cluster_sweep(fp, precision):
-    # p >= 32: the closed-form stage inverts corr on a CTA cluster; an exactly
-    # collinear pair makes corr singular, so the stage is skipped as in the oracle
+    # an exactly collinear pair makes corr singular, so the closed-form stage is
+    # skipped as in the oracle
     X = _sem_case(73, 48, 4000, 0.2, np.float64)
     X[:, 30] = X[:, 7]
     R, st = _check_skeleton(fp, X, order=1, precision=precision)
@@ -386,10 +386,24 @@ def test_stage_a_singular_cluster_sweep(fp, precision):
     assert st["stage_a_ran"] == 0
 
 
-@pytest.mark.parametrize("p", [32, 57, 130])
+def test_stage_a_singular_on_the_cluster(fp):
+    # on the cluster a singular corr ends the sweep at the same pivot in every CTA
+    # (the stage is skipped as in the oracle); the cap keeps the enumerated stages
+    # of the complete graph small
+    rng = np.random.Generator(np.random.PCG64(7300))
+    dag, W, order = sem.er_dag(200, 0.02, rng)
+    X = np.ascontiguousarray(sem.sample(W, order, 4000, rng))
+    X[:, 150] = X[:, 7]
+    for ml in (0, 1):
+        R, st = _check_skeleton(fp, X, max_level=ml, order=1, precision=2)
+        assert st["stage_a_ran"] == 0 and not R["stageA_ran"]
+
+
+@pytest.mark.parametrize("p", [32, 57, 130, 200, 330])
 def test_stage_a_cluster_sizes(fp, p):
-    # the cluster sweep over 8 CTAs with ragged row blocks (p not a multiple of 8)
-    X = _sem_case(90 + p, p, max(2000, 4 * p), 0.15 if p < 100 else 0.04)
+    # the closed-form stage's inverse: the sweep over a cluster of 8 CTAs with ragged
+    # row blocks (p not a multiple of 8)
+    X = _sem_case(90 + p, p, max(2000, 4 * p), 0.15 if p < 100 else (0.04 if p < 150 else 0.015))
     R, st = _check_skeleton(fp, X, order=1, precision=2)
     assert st["stage_a_ran"] == int(bool(R["stageA_ran"]))
 
