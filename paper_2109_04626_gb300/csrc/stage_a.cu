@@ -13,18 +13,23 @@ namespace fpc {
 namespace cg = cooperative_groups;
 
 // The same symmetric sweep (A <- -A^{-1}, pivots in order, no exchanges) on a
-// cluster of SA_CLUSTER CTAs: CTA r holds rows [r*rpc, (r+1)*rpc) in shared
-// memory.  At pivot k every CTA copies row k (= column k, A stays symmetric) from
-// its owner's broadcast buffer through distributed shared memory and updates its
-// own rows; the owner of row k+1 then publishes that row into the other of its two
-// buffers, and one cluster barrier ends the pivot (a reader of buffer k%2 is done
-// with it before the barrier; it is written again only after the next one).  Each
-// entry (i, j) is computed with the operands the one-CTA sweep uses for the pair
-// {i, j}, so the result is bit-identical to it; GB300's FP64 rate (about 2 FMA per
-// clock per SM) is what the cluster multiplies.
+// cluster of SA_CLUSTER CTAs, with one cluster barrier per sb pivots.  CTA r
+// holds rows [r*rpc, (r+1)*rpc) in shared memory.  At the start of a group of
+// pivots k0..k0+b-1 every CTA copies those rows (= columns, A stays symmetric), as
+// their owners published them, through distributed shared memory; it then applies
+// the group's pivots one after the other to its own rows and to its copies of
+// the group's later rows -- the same operations on the same operands as their
+// owners, so every copy of row k is the owner's row k when pivot k uses it.  The
+// owners of the next group's rows publish them into the other of two buffers, and
+// one cluster barrier ends the group (a reader of buffer g%2 is done with it
+// before the barrier; it is written again only after the next one).  Each entry
+// (i, j) is computed with the operands the one-CTA sweep uses for the pair {i, j},
+// so the result is bit-identical to it; GB300's FP64 rate (about 2 FMA per clock
+// per SM) is what the cluster multiplies, and the groups cut the barriers.
 constexpr int SA_CLUSTER = 8;
+constexpr int SA_SB_MAX = 8;
 __global__ void __cluster_dims__(SA_CLUSTER, 1, 1) __launch_bounds__(256)
-    inverse_cluster_kernel(double *A, int m, int lda, int *singular)
+    inverse_cluster_kernel(double *A, int m, int lda, int sb, int *singular)
 {
     extern __shared__ double smc[];
     cg::cluster_group cl = cg::this_cluster();
@@ -32,38 +37,60 @@ __global__ void __cluster_dims__(SA_CLUSTER, 1, 1) __launch_bounds__(256)
     const int rpc = (m + SA_CLUSTER - 1) / SA_CLUSTER;
     const int i0 = min(m, r * rpc), i1 = min(m, i0 + rpc), nr = i1 - i0;
     double *R = smc;                                   // own rows, row-major, m per row
-    double *colk = smc + (size_t)rpc * m;              // this CTA's copy of row k
-    double *bc = colk + m;                             // two broadcast rows (the owner's)
+    double *Pn = R + (size_t)rpc * m;                  // the group's rows, sb x m
+    double *bc = Pn + (size_t)sb * m;                  // two broadcast buffers of sb rows (own rows only)
     for (int e = threadIdx.x; e < nr * m; e += blockDim.x) R[e] = A[(long long)(i0 + e / m) * lda + e % m];
     __syncthreads();
-    if (i0 == 0 && nr > 0)
-        for (int j = threadIdx.x; j < m; j += blockDim.x) bc[j] = R[j];
+    for (int e = threadIdx.x; e < sb * m; e += blockDim.x) {       // own rows of group 0
+        const int row = e / m;
+        if (row < m && row >= i0 && row < i1) bc[e] = R[(size_t)(row - i0) * m + e % m];
+    }
     bool bad = false;
     cl.sync();
-    for (int k = 0; k < m; ++k) {
-        const int owner = k / rpc;
-        const double *rowk = cl.map_shared_rank(bc, owner) + (size_t)(k & 1) * m;
-        for (int j = threadIdx.x; j < m; j += blockDim.x) colk[j] = rowk[j];
+    const int ng = (m + sb - 1) / sb;
+    for (int gi = 0; gi < ng && !bad; ++gi) {
+        const int k0 = gi * sb, b = min(sb, m - k0);
+        const size_t buf = (size_t)(gi & 1) * sb * m;
+        for (int e = threadIdx.x; e < b * m; e += blockDim.x)
+            Pn[e] = cl.map_shared_rank(bc, (k0 + e / m) / rpc)[buf + e];
         __syncthreads();
-        const double D = colk[k];
-        if (!(D > DEGEN)) {                            // the same pivot in every CTA: a uniform exit
-            bad = true;
-            break;
+        for (int q = 0; q < b; ++q) {
+            const int k = k0 + q;
+            const double *colk = Pn + (size_t)q * m;   // row k after pivots < k
+            const double D = colk[k];
+            if (!(D > DEGEN)) {                        // the same pivot in every CTA: a uniform exit
+                bad = true;
+                break;
+            }
+            const double iD = rcp_newton(D);
+            // own rows, then the copies of the group's later rows, by the same formula:
+            // a warp per row, lanes over its columns (no index division per entry)
+            const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+            const int nrows = nr + (b - 1 - q);
+            for (int rr = threadIdx.x >> 5; rr < nrows; rr += nw) {
+                const bool own = rr < nr;
+                const int i = own ? i0 + rr : k + 1 + (rr - nr);
+                double *row = own ? R + (size_t)rr * m : Pn + (size_t)(q + 1 + rr - nr) * m;
+                const double ci = colk[i] * iD;
+                for (int j = lane; j < m; j += 32) {
+                    double v;
+                    if (i == k) v = (j == k) ? -iD : colk[j] * iD;
+                    else if (j == k) v = ci;
+                    else if (i <= j) v = fma(-ci, colk[j], row[j]);
+                    else v = fma(-(colk[j] * iD), colk[i], row[j]);
+                    row[j] = v;
+                }
+            }
+            __syncthreads();
         }
-        const double iD = rcp_newton(D);
-        for (int e = threadIdx.x; e < nr * m; e += blockDim.x) {
-            const int i = i0 + e / m, j = e - (e / m) * m;
-            double v;
-            if (i == k) v = (j == k) ? -iD : colk[j] * iD;
-            else if (j == k) v = colk[i] * iD;
-            else if (i <= j) v = fma(-(colk[i] * iD), colk[j], R[e]);
-            else v = fma(-(colk[j] * iD), colk[i], R[e]);
-            R[e] = v;
+        if (!bad && gi + 1 < ng) {                     // publish own rows of the next group
+            const int n0 = k0 + sb, nb2 = min(sb, m - n0);
+            const size_t nbuf = (size_t)((gi + 1) & 1) * sb * m;
+            for (int e = threadIdx.x; e < nb2 * m; e += blockDim.x) {
+                const int row = n0 + e / m;
+                if (row >= i0 && row < i1) bc[nbuf + e] = R[(size_t)(row - i0) * m + e % m];
+            }
         }
-        __syncthreads();
-        if (k + 1 < m && k + 1 >= i0 && k + 1 < i1)      // publish row k+1, as updated by pivot k
-            for (int j = threadIdx.x; j < m; j += blockDim.x)
-                bc[(size_t)((k + 1) & 1) * m + j] = R[(size_t)(k + 1 - i0) * m + j];
         cl.sync();
     }
     cl.sync();                                         // no CTA leaves while another reads its buffers
@@ -124,13 +151,17 @@ cudaError_t launch_inverse_spd(double *A, int m, int lda, double *work, int *sin
 {
     cudaError_t e = cudaMemsetAsync(singular, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
-    // a cluster of SA_CLUSTER CTAs when the rows fit their shared memory (at m = 95 it
-    // takes 0.29 ms against 0.46 ms for the one-CTA sweep)
-    const size_t smem_c = ((size_t)((m + SA_CLUSTER - 1) / SA_CLUSTER) * m + 3 * (size_t)m) * sizeof(double);
+    // a cluster of SA_CLUSTER CTAs when the rows fit their shared memory, with the
+    // largest block of pivots per barrier that fits beside them
+    const size_t rpc = (size_t)(m + SA_CLUSTER - 1) / SA_CLUSTER;
+    int sb = SA_SB_MAX;
+    auto smem_of = [&](int b) { return (rpc * m + 3 * (size_t)b * m) * sizeof(double); };
+    while (sb > 1 && smem_of(sb) > 200 * 1024) sb >>= 1;
+    const size_t smem_c = smem_of(sb);
     if (m >= 32 && smem_c <= 200 * 1024) {
         e = cudaFuncSetAttribute(inverse_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c);
         if (e != cudaSuccess) return e;
-        inverse_cluster_kernel<<<SA_CLUSTER, 256, smem_c, s>>>(A, m, lda, singular); note_launch();
+        inverse_cluster_kernel<<<SA_CLUSTER, 256, smem_c, s>>>(A, m, lda, sb, singular); note_launch();
         return cudaGetLastError();
     }
     size_t smem = ((size_t)m * m + (size_t)m) * sizeof(double);
