@@ -2583,8 +2583,10 @@ __device__ __forceinline__ bool loop_stage_plan(const GraphDev &g, const TestPar
 // (soo[p] = their total), and per node the precision-block request for the next
 // stage min(l - 1, L*) (reversed order), as the tail does.  CTA 0's tail writes
 // the same into memory for the captured loop.  sh: 32 words of scratch.
+// Also the list of nodes whose blocks have work this stage (a maintained block whose
+// node lost neighbours, or a build request): sact[0..*nact).
 __device__ __forceinline__ void loop_tail_plan(const GraphDev &g, const TestParams &tp, int l, long long *soo,
-                                               int *sneed, ull *sh)
+                                               int *sneed, ull *sh, int *sact, int *nact)
 {
     __shared__ int smx[32];
     const int t = threadIdx.x, p = g.p, lane = t & 31, w = t >> 5;
@@ -2600,10 +2602,18 @@ __device__ __forceinline__ void loop_tail_plan(const GraphDev &g, const TestPara
     int lmax = 0;
     for (int i = 0; i < (int)(blockDim.x >> 5); ++i) lmax = max(lmax, smx[i]);
     const int nl = min(l - 1, lmax - 1);
+    bool act = false;
     if (t < p) {
         const int pm = g.prec_m[t];
-        sneed[t] = nl >= 0 && dg > 0 && comp_eligible(dg - 1, nl, tp) && (pm == 0 || pm == -2);
+        const int nd = nl >= 0 && dg > 0 && comp_eligible(dg - 1, nl, tp) && (pm == 0 || pm == -2);
+        sneed[t] = nd;
+        act = nd || (pm > 0 && __ldcg(g.dchg + t) != 0);
     }
+    __syncthreads();                                    // sh free again
+    ull va[1] = {act ? 1ull : 0ull}, exa[1], tota[1];
+    block_scan_sat<1>(va, exa, tota, sh);
+    if (act) sact[exa[0]] = t;
+    if (t == 0) *nact = (int)tota[0];
     __syncthreads();
 }
 
@@ -2634,6 +2644,8 @@ __global__ void __launch_bounds__(LOOP_THREADS, 1) stage_loop_kernel(GraphDev g,
     __shared__ int sdeg[LOOP_PMAX];
     __shared__ ull sT[LOOP_PMAX];
     __shared__ int sneed[LOOP_PMAX];
+    __shared__ int sact[LOOP_PMAX];
+    __shared__ int nact;
     LevelInfo *I = g.info;
     load_small_binom(g, sb);
     for (int i = threadIdx.x; i <= g.p; i += blockDim.x) soo[i] = g.ooff[i];   // the first stage's, from the tail
@@ -2658,9 +2670,9 @@ __global__ void __launch_bounds__(LOOP_THREADS, 1) stage_loop_kernel(GraphDev g,
         // the tail: CTA 0 in memory (next stage, loop end, offsets, requests), every
         // CTA for itself what the downdates and the next commit need
         if (blockIdx.x == 0) tail_body(g, tp, cap, 0, nullptr, 0, 0, 0, StageConds{}, true);
-        loop_tail_plan(g, tp, lcur, soo, sneed, sh);
-        for (int item = blockIdx.x; item < g.p * chunks; item += gridDim.x) {
-            const int u = item / chunks;
+        loop_tail_plan(g, tp, lcur, soo, sneed, sh, sact, &nact);
+        for (int item = blockIdx.x; item < nact * chunks; item += gridDim.x) {   // the nodes with work only
+            const int u = sact[item / chunks];
             prec_body<false>(g, tp, C64, ldc, u, item % chunks, chunks, lsm, sneed[u]);
             __syncthreads();                            // the body's shared arrays are reused
         }
