@@ -2671,9 +2671,12 @@ __global__ void __launch_bounds__(LOOP_THREADS, 1) stage_loop_kernel(GraphDev g,
         // CTA for itself what the downdates and the next commit need
         if (blockIdx.x == 0) tail_body(g, tp, cap, 0, nullptr, 0, 0, 0, StageConds{}, true);
         loop_tail_plan(g, tp, lcur, soo, sneed, sh, sact, &nact);
-        for (int item = blockIdx.x; item < nact * chunks; item += gridDim.x) {   // the nodes with work only
-            const int u = sact[item / chunks];
-            prec_body<false>(g, tp, C64, ldc, u, item % chunks, chunks, lsm, sneed[u]);
+        // the nodes with work only, each node's kept rows over as many CTAs as leave one
+        // item per CTA (up to `chunks`): a CTA's items run one after the other
+        const int ch = max(1, min(chunks, (int)gridDim.x / max(1, nact)));
+        for (int item = blockIdx.x; item < nact * ch; item += gridDim.x) {
+            const int u = sact[item / ch];
+            prec_body<false>(g, tp, C64, ldc, u, item % ch, ch, lsm, sneed[u]);
             __syncthreads();                            // the body's shared arrays are reused
         }
         grid.sync();
