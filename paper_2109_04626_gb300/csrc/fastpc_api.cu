@@ -1365,26 +1365,31 @@ static pc_status skeleton_enqueue(pc_handle *h)
         CK(fpc::launch_tail(g, tp, level_cap(h), 1, h->singular, stage_a_launched, h->hcond, 0, fpc::StageConds{},
                             s));
     }
+    bool loop = h->stage_loop && h->order == 1 && h->complement && p <= fpc::LOOP_PMAX && !h->nblk;
+    if (loop && h->coop < 0) {
+        int dev = 0, v = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&v, cudaDevAttrCooperativeLaunch, dev));
+        h->coop = v;
+    }
+    loop = loop && h->coop;
     if (h->order == 1 && h->complement) {
         Timed t(h, 2);
         // after the closed-form stage: blocks from its inverse, then one downdate each
+        // (in the stage loop kernel when it runs)
         if (stage_a_launched && p <= fpc::PREC_MAX) CK(fpc::launch_prec_seed(g, h->Pbuf, h->ldc, s));
-        CK(fpc::launch_prec_update(g, tp, h->C64, h->ldc, s));
+        if (!loop) CK(fpc::launch_prec_update(g, tp, h->C64, h->ldc, s));
     }
-    if (h->stage_loop && h->order == 1 && h->complement && p <= fpc::LOOP_PMAX && !h->nblk) {
-        if (h->coop < 0) {
-            int dev = 0, v = 0;
-            CK(cudaGetDevice(&dev));
-            CK(cudaDeviceGetAttribute(&v, cudaDevAttrCooperativeLaunch, dev));
-            h->coop = v;
-        }
-        if (h->coop) {
-            // the complement-only stages in one cooperative kernel; the captured loop
-            // (or the host loop) goes on from the first stage with direct tests
-            Timed t(h, 8);
-            cudaError_t e = fpc::launch_stage_loop(g, tp, h->C64, h->ldc, h->budget, level_cap(h), s);
-            if (e == cudaErrorCooperativeLaunchTooLarge) cudaGetLastError();   // not resident: the loop runs it all
-            else CK(e);
+    if (loop) {
+        // the first blocks and the complement-only stages in one cooperative kernel; the
+        // captured loop (or the host loop) goes on from the first stage with direct tests
+        Timed t(h, 8);
+        cudaError_t e = fpc::launch_stage_loop(g, tp, h->C64, h->ldc, h->budget, level_cap(h), 1, s);
+        if (e == cudaErrorCooperativeLaunchTooLarge) {
+            cudaGetLastError();                        // not resident: the captured loop runs it all
+            CK(fpc::launch_prec_update(g, tp, h->C64, h->ldc, s));
+        } else {
+            CK(e);
         }
     }
 

@@ -292,9 +292,10 @@ cudaError_t launch_degrees_tail(GraphDev g, TestParams tp, int cap, cudaGraphCon
 cudaError_t launch_prec_seed(GraphDev g, const double *P, int ldp, cudaStream_t s);
 // the reversed order's complement-only stages of a problem of p <= LOOP_PMAX nodes in
 // one cooperative kernel, from the stage the tail scheduled; returns at the first
-// stage with direct tests (cudaErrorCooperativeLaunchTooLarge when it cannot be resident)
+// stage with direct tests (cudaErrorCooperativeLaunchTooLarge when it cannot be
+// resident).  pre: it first applies the first stage's block builds and downdates.
 cudaError_t launch_stage_loop(GraphDev g, TestParams tp, const double *C64, int ldc, double budget, int cap,
-                              cudaStream_t s);
+                              int pre, cudaStream_t s);
 cudaError_t launch_commit(GraphDev g, long long n_opairs_cap, int l_fixed, int explicit_sets,
                           cudaStream_t s);
 size_t scan_ws_bytes(long long n);

@@ -2632,8 +2632,11 @@ __device__ __forceinline__ void loop_tail_plan(const GraphDev &g, const TestPara
 // the commit and the last phase (the tail), each followed by a barrier, and every
 // CTA plans the stage from the same data.  The stage l is read once per pass, at
 // its start: the tail moves it on in the last phase.
+// pre: first the first stage's block builds and downdates (the seeded blocks drop
+// their non-neighbours), in place of the cluster kernel.
 __global__ void __launch_bounds__(LOOP_THREADS, 1) stage_loop_kernel(GraphDev g, TestParams tp, const double *C64,
-                                                                     int ldc, double budget, int cap, int chunks)
+                                                                     int ldc, double budget, int cap, int chunks,
+                                                                     int pre)
 {
     cg::grid_group grid = cg::this_grid();
     extern __shared__ double lsm[];
@@ -2652,15 +2655,36 @@ __global__ void __launch_bounds__(LOOP_THREADS, 1) stage_loop_kernel(GraphDev g,
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), nwg = (int)((gridDim.x * blockDim.x) >> 5);
+    if (pre) {
+        // the tail scheduled the requests; every CTA lists the nodes with block work
+        const int t = threadIdx.x;
+        bool act = false;
+        if (t < g.p) {
+            const int nd = g.prec_need[t], pm = g.prec_m[t];
+            sneed[t] = nd;
+            act = nd || (pm > 0 && g.dchg[t] != 0);
+        }
+        ull va[1] = {act ? 1ull : 0ull}, exa[1], tota[1];
+        block_scan_sat<1>(va, exa, tota, sh);
+        if (act) sact[exa[0]] = t;
+        if (t == 0) nact = (int)tota[0];
+        __syncthreads();
+        const int ch = max(1, min(chunks, (int)gridDim.x / max(1, nact)));
+        for (int item = blockIdx.x; item < nact * ch; item += gridDim.x) {
+            const int u = sact[item / ch];
+            prec_body<false>(g, tp, C64, ldc, u, item % ch, ch, lsm, sneed[u]);
+            __syncthreads();
+        }
+        grid.sync();
+    }
     for (int it = 0; it <= g.p; ++it) {                 // one pass per stage, at most p stages
         if (stopped(I)) break;
         const int lcur = I->l;                          // moved on only by the tail below
         if (!loop_stage_plan(g, tp, lcur, budget, soff, sh, sdeg, sT)) break;
         complement_body(g, tp, sb, soff, LOOP_PMAX + 1, blockIdx.x, gridDim.x, true, sdeg, sT);
-        // then the previous stage's deletions leave the slot maps (the complement tests
+        // then the previous downdates' deletions leave the slot maps (the complement tests
         // read only the slots of current neighbours; repeating it is harmless)
-        if (it > 0)
-            for (int u = blockIdx.x; u < g.p; u += gridDim.x) prec_retire(g, u);
+        for (int u = blockIdx.x; u < g.p; u += gridDim.x) prec_retire(g, u);
         grid.sync();
         if (!stopped(I)) commit_body(g, -1, 1, 1, sb, blockIdx.x, gridDim.x, soo);
         grid.sync();
@@ -3301,7 +3325,7 @@ cudaError_t launch_prec_seed(GraphDev g, const double *P, int ldp, cudaStream_t 
 }
 
 cudaError_t launch_stage_loop(GraphDev g, TestParams tp, const double *C64, int ldc, double budget, int cap,
-                              cudaStream_t s)
+                              int pre, cudaStream_t s)
 {
     if (g.p > LOOP_PMAX) return cudaErrorInvalidValue;
     const size_t smem = prec_smem_bytes(g.p);
@@ -3315,7 +3339,7 @@ cudaError_t launch_stage_loop(GraphDev g, TestParams tp, const double *C64, int 
     // a node's kept rows over PREC_CHUNKS CTAs (consecutive items: different SMs), so
     // that the FP64 work of a large downdate is spread
     int chunks = PREC_CHUNKS;
-    void *args[] = {&g, &tp, (void *)&C64, &ldc, &budget, &cap, &chunks};
+    void *args[] = {&g, &tp, (void *)&C64, &ldc, &budget, &cap, &chunks, &pre};
     e = cudaLaunchCooperativeKernel((const void *)stage_loop_kernel, dim3(grid), dim3(LOOP_THREADS), args, smem, s);
     note_launch();
     return e;
