@@ -140,11 +140,13 @@ void pc_destroy(pc_handle *h);
  *                 corr[adj(u), adj(u)] in shared memory; the rest read corr
  *                 from L2 (0 = staged kernel off)
  *   "stage_loop"  1 = in the reversed order with the complement path, problems of
- *                 p <= 128 run the stages whose tests all take the complement
- *                 path in one cooperative kernel, a grid-wide barrier where the
- *                 captured loop has a kernel boundary (head, tests, commit,
- *                 degrees, next stage, precision blocks); from the first stage
- *                 with direct tests on, the captured loop (default; skipped on a
+ *                 p <= 128 run the stage loop in one cooperative kernel, a
+ *                 grid-wide barrier where the captured loop has a kernel
+ *                 boundary (tests, commit, degrees, next stage and precision
+ *                 blocks), the direct tests of stages with at most 12
+ *                 conditioning members a warp each; from the first stage it
+ *                 does not take (larger direct tests, or a stage the proposal
+ *                 may score) on, the captured loop (default; skipped on a
  *                 device without cooperative launches).  0 = the captured loop
  *                 throughout.  The results are the same either way.
  *   "comp_fp32"   1 = complement tests (reversed order) in FP32 first from the

@@ -1384,7 +1384,7 @@ static pc_status skeleton_enqueue(pc_handle *h)
         // the first blocks and the complement-only stages in one cooperative kernel; the
         // captured loop (or the host loop) goes on from the first stage with direct tests
         Timed t(h, 8);
-        cudaError_t e = fpc::launch_stage_loop(g, tp, h->C64, h->ldc, h->budget, level_cap(h), 1, s);
+        cudaError_t e = fpc::launch_stage_loop(g, tp, h->C32, h->C64, h->ldc, h->budget, level_cap(h), 1, s);
         if (e == cudaErrorCooperativeLaunchTooLarge) {
             cudaGetLastError();                        // not resident: the captured loop runs it all
             CK(fpc::launch_prec_update(g, tp, h->C64, h->ldc, s));

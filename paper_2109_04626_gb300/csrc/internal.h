@@ -117,6 +117,7 @@ constexpr int STAGE_FIXED_KERNELS = 3;
 // the stage loop in one cooperative kernel (reversed order, complement-only stages)
 constexpr int LOOP_THREADS = 256;
 constexpr int LOOP_PMAX = 128;          // largest p it runs (its shared memory holds a p+1 block)
+constexpr int LOOP_MMAX = 14;           // direct tests it runs: l + 2 <= LOOP_MMAX
 
 // Everything the stage kernels need, by value.
 struct GraphDev {
@@ -290,12 +291,13 @@ cudaError_t launch_degrees_tail(GraphDev g, TestParams tp, int cap, cudaGraphCon
 // the first stage's precision blocks seeded from the closed-form stage's inverse P
 // (the downdate that follows drops the non-neighbours)
 cudaError_t launch_prec_seed(GraphDev g, const double *P, int ldp, cudaStream_t s);
-// the reversed order's complement-only stages of a problem of p <= LOOP_PMAX nodes in
-// one cooperative kernel, from the stage the tail scheduled; returns at the first
-// stage with direct tests (cudaErrorCooperativeLaunchTooLarge when it cannot be
+// the reversed order's stages of a problem of p <= LOOP_PMAX nodes in one
+// cooperative kernel, from the stage the tail scheduled; returns at the first stage
+// with direct tests of more than LOOP_MMAX - 2 members or that the proposal may
+// score (cudaErrorCooperativeLaunchTooLarge when it cannot be
 // resident).  pre: it first applies the first stage's block builds and downdates.
-cudaError_t launch_stage_loop(GraphDev g, TestParams tp, const double *C64, int ldc, double budget, int cap,
-                              int pre, cudaStream_t s);
+cudaError_t launch_stage_loop(GraphDev g, TestParams tp, const float *C32, const double *C64, int ldc,
+                              double budget, int cap, int pre, cudaStream_t s);
 cudaError_t launch_commit(GraphDev g, long long n_opairs_cap, int l_fixed, int explicit_sets,
                           cudaStream_t s);
 size_t scan_ws_bytes(long long n);

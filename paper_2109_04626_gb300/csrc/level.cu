@@ -957,6 +957,57 @@ __global__ void __launch_bounds__(256) ci_direct_kernel(GraphDev g, TestParams t
 }
 
 
+// bytes of one warp's buffer in the stage loop's direct tests: the FP64 matrix of
+// LOOP_MMAX x (LOOP_MMAX + 1) and the member and position lists
+__host__ __device__ constexpr size_t loop_direct_bytes()
+{
+    return ((size_t)LOOP_MMAX * (LOOP_MMAX + 1) * sizeof(double) + 2 * LOOP_MMAX * sizeof(int) + 15) / 16 * 16;
+}
+
+// The stage loop's direct tests of a small stage (l + 2 <= LOOP_MMAX): one warp per
+// test as ci_direct_kernel, located by the CTA's own plan (doff: per-node offsets in
+// shared memory, doff[p] = their total); mine: the warp's buffer of loop_direct_bytes.
+template <bool F64>
+__device__ __noinline__ void loop_direct_body(const GraphDev &g, const TestParams &tp, int l, const ull *doff,
+                                              const float *C32, const double *C64, int ldc, unsigned char *mine)
+{
+    const int lane = threadIdx.x & 31;
+    const int m = l + 2, ms = LOOP_MMAX + 1;
+    double *Mbuf = (double *)mine;
+    int *nd = (int *)(mine + (size_t)LOOP_MMAX * ms * sizeof(double));
+    int *pos = nd + LOOP_MMAX;
+    const ull total = doff[g.p];
+    const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const double sq = sqrt((double)(tp.n - l - 3));
+    const float sqf = (float)sq;
+    WarpAcc acc = {0, 0, 0, 0, 0, 0, 0, 0.f};
+    for (ull t = gw; t < total; t += nw) {
+        int u, j, d;
+        ull rank;
+        locate_test(g, doff, l, t, u, j, d, rank);
+        const int v = g.nbr[nidx(g, u) + j];
+        const int side = u > v;
+        const ull key = ((ull)side << 62) | rank;
+        ull *bp = g.best + pidx(g, min(u, v), max(u, v));
+        if (*(volatile ull *)bp < key) continue;   // an earlier set already separates
+        if (lane == 0) {
+            unrank_lex(rank, d, l, g.binom, g.ldb, pos);
+            for (int i = 0; i < l; ++i) nd[i] = g.nbr[nidx(g, u) + pos[i] + (pos[i] >= j)];
+            nd[l] = u;
+            nd[l + 1] = v;
+        }
+        __syncwarp();
+        double r;
+        float z;
+        ++acc.tests;
+        const bool ind = warp_test<F64>(nd, m, l, C32, C64, ldc, tp, sq, sqf, Mbuf, ms, acc, r, z);
+        if (ind && lane == 0) atomicMin(bp, key);
+        __syncwarp();
+    }
+    if (lane == 0) flush_acc(acc, g.ctr);
+}
+
 // ---------------------------------------------------------------- direct path, small stages
 // One thread per chunk of tp.lane_chunk consecutive sets of one ordered pair
 // (l <= LANE_LMAX): one unranking, then lexicographic successors; the
@@ -2548,13 +2599,13 @@ __global__ void commit_kernel(GraphDev g, int l_fixed, int explicit_sets, int co
 
 // ---------------------------------------------------------------- stage loop in one kernel
 // Every CTA of the stage loop plans stage l itself, as the head does: the
-// complement tests' per-node offsets in shared memory (soff[p] = their total) and
-// the direct-test total.  True when the stage is one for the loop: no direct
-// tests, nothing saturated, within the budget (the captured loop's head reports
-// the others).  sh: 64 words of scratch; sdeg, sT receive every node's degree and
-// C(d, l).
+// complement and direct tests' per-node offsets in shared memory (soff, sdoff;
+// entry p holds the total).  True when the stage is one for the loop: direct tests
+// only of at most LOOP_MMAX - 2 members and outside the proposal's stages, nothing
+// saturated, within the budget (the captured loop's head reports the others).
+// sh: 64 words of scratch; sdeg, sT receive every node's degree and C(d, l).
 __device__ __forceinline__ bool loop_stage_plan(const GraphDev &g, const TestParams &tp, int l, double budget,
-                                                ull *soff, ull *sh, int *sdeg, ull *sT)
+                                                ull *soff, ull *sh, int *sdeg, ull *sT, ull *sdoff)
 {
     const int t = threadIdx.x, p = g.p;                // p <= LOOP_PMAX < blockDim.x
     ull v[2] = {0ull, 0ull};
@@ -2572,10 +2623,20 @@ __device__ __forceinline__ bool loop_stage_plan(const GraphDev &g, const TestPar
     const int ssat = __syncthreads_or(sat);
     ull ex[2], tot[2];
     block_scan_sat<2>(v, ex, tot, sh);
-    if (t < p) soff[t] = ex[0];
-    if (t == 0) soff[p] = tot[0];
+    if (t < p) {
+        soff[t] = ex[0];
+        sdoff[t] = ex[1];
+    }
+    if (t == 0) {
+        soff[p] = tot[0];
+        sdoff[p] = tot[1];
+    }
     __syncthreads();
-    return !ssat && tot[0] != KEY_NONE && tot[1] == 0 && (double)tot[0] <= budget;
+    // direct tests only where the warp buffer holds them and no proposal order could
+    // apply (the captured loop scores such stages)
+    const bool direct_ok = tot[1] == 0 || (l + 2 <= LOOP_MMAX && !(g.row_off && l >= 1 && l <= tp.learned_lmax));
+    return !ssat && tot[0] != KEY_NONE && tot[1] != KEY_NONE && direct_ok &&
+           (double)tot[0] + (double)tot[1] <= budget;
 }
 
 // Every CTA of the stage loop forms the tail's results it needs from the degrees
@@ -2626,17 +2687,19 @@ __device__ __forceinline__ void loop_tail_plan(const GraphDev &g, const TestPara
 //   owner of a pair found in a shared copy of the pair offsets) | degrees |
 //   tail (CTA 0 into memory; every CTA forms the offsets and block requests it
 //   needs itself) and precision downdates and builds.
-// It returns at the first stage with direct tests (the captured loop, whose head
-// recomputes that stage, runs it and the rest), or when the search ends or halts.
+// Stages with direct tests of at most LOOP_MMAX - 2 members run them too, a warp per
+// test beside the complement tests.  It returns at the first stage it does not take
+// (larger direct tests, or stages the proposal may score: the captured loop, whose
+// head recomputes that stage, runs it and the rest), or when the search ends or halts.
 // The exits are taken by all CTAs together: `done` and `halt` are written only in
 // the commit and the last phase (the tail), each followed by a barrier, and every
 // CTA plans the stage from the same data.  The stage l is read once per pass, at
 // its start: the tail moves it on in the last phase.
 // pre: first the first stage's block builds and downdates (the seeded blocks drop
 // their non-neighbours), in place of the cluster kernel.
-__global__ void __launch_bounds__(LOOP_THREADS, 1) stage_loop_kernel(GraphDev g, TestParams tp, const double *C64,
-                                                                     int ldc, double budget, int cap, int chunks,
-                                                                     int pre)
+__global__ void __launch_bounds__(LOOP_THREADS, 1) stage_loop_kernel(GraphDev g, TestParams tp, const float *C32,
+                                                                     const double *C64, int ldc, double budget,
+                                                                     int cap, int chunks, int pre)
 {
     cg::grid_group grid = cg::this_grid();
     extern __shared__ double lsm[];
@@ -2646,6 +2709,7 @@ __global__ void __launch_bounds__(LOOP_THREADS, 1) stage_loop_kernel(GraphDev g,
     __shared__ long long soo[LOOP_PMAX + 1];
     __shared__ int sdeg[LOOP_PMAX];
     __shared__ ull sT[LOOP_PMAX];
+    __shared__ ull sdoff[LOOP_PMAX + 1];
     __shared__ int sneed[LOOP_PMAX];
     __shared__ int sact[LOOP_PMAX];
     __shared__ int nact;
@@ -2680,7 +2744,12 @@ __global__ void __launch_bounds__(LOOP_THREADS, 1) stage_loop_kernel(GraphDev g,
     for (int it = 0; it <= g.p; ++it) {                 // one pass per stage, at most p stages
         if (stopped(I)) break;
         const int lcur = I->l;                          // moved on only by the tail below
-        if (!loop_stage_plan(g, tp, lcur, budget, soff, sh, sdeg, sT)) break;
+        if (!loop_stage_plan(g, tp, lcur, budget, soff, sh, sdeg, sT, sdoff)) break;
+        if (sdoff[g.p] > 0) {                           // the stage's direct tests, a warp each
+            unsigned char *mine = (unsigned char *)lsm + (size_t)(threadIdx.x >> 5) * loop_direct_bytes();
+            if (tp.precision == 0) loop_direct_body<true>(g, tp, lcur, sdoff, C32, C64, ldc, mine);
+            else loop_direct_body<false>(g, tp, lcur, sdoff, C32, C64, ldc, mine);
+        }
         complement_body(g, tp, sb, soff, LOOP_PMAX + 1, blockIdx.x, gridDim.x, true, sdeg, sT);
         // then the previous downdates' deletions leave the slot maps (the complement tests
         // read only the slots of current neighbours; repeating it is harmless)
@@ -3324,11 +3393,12 @@ cudaError_t launch_prec_seed(GraphDev g, const double *P, int ldp, cudaStream_t 
     return cudaGetLastError();
 }
 
-cudaError_t launch_stage_loop(GraphDev g, TestParams tp, const double *C64, int ldc, double budget, int cap,
-                              int pre, cudaStream_t s)
+cudaError_t launch_stage_loop(GraphDev g, TestParams tp, const float *C32, const double *C64, int ldc,
+                              double budget, int cap, int pre, cudaStream_t s)
 {
     if (g.p > LOOP_PMAX) return cudaErrorInvalidValue;
-    const size_t smem = prec_smem_bytes(g.p);
+    // the downdates' and builds' block, or the direct tests' warp buffers
+    const size_t smem = std::max(prec_smem_bytes(g.p), (size_t)(LOOP_THREADS / 32) * loop_direct_bytes());
     cudaError_t e = cudaFuncSetAttribute(stage_loop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -3339,7 +3409,7 @@ cudaError_t launch_stage_loop(GraphDev g, TestParams tp, const double *C64, int 
     // a node's kept rows over PREC_CHUNKS CTAs (consecutive items: different SMs), so
     // that the FP64 work of a large downdate is spread
     int chunks = PREC_CHUNKS;
-    void *args[] = {&g, &tp, (void *)&C64, &ldc, &budget, &cap, &chunks, &pre};
+    void *args[] = {&g, &tp, (void *)&C32, (void *)&C64, &ldc, &budget, &cap, &chunks, &pre};
     e = cudaLaunchCooperativeKernel((const void *)stage_loop_kernel, dim3(grid), dim3(LOOP_THREADS), args, smem, s);
     note_launch();
     return e;
