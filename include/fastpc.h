@@ -139,16 +139,17 @@ void pc_destroy(pc_handle *h);
  *                 default 128) run on the staged kernel, which holds
  *                 corr[adj(u), adj(u)] in shared memory; the rest read corr
  *                 from L2 (0 = staged kernel off)
- *   "stage_loop"  1 = in the reversed order with the complement path, problems of
- *                 p <= 128 run the stage loop in one cooperative kernel, a
- *                 grid-wide barrier where the captured loop has a kernel
- *                 boundary (tests, commit, degrees, next stage and precision
- *                 blocks), the direct tests of stages with at most 12
- *                 conditioning members a warp each; from the first stage it
- *                 does not take (larger direct tests, or a stage the proposal
- *                 may score) on, the captured loop (default; skipped on a
- *                 device without cooperative launches).  0 = the captured loop
- *                 throughout.  The results are the same either way.
+ *   "stage_loop"  1 = problems of p <= 128 (not batched) run the stage loop in
+ *                 one cooperative kernel, a grid-wide barrier where the captured
+ *                 loop has a kernel boundary (tests, commit, degrees, next stage,
+ *                 and in the reversed order the precision blocks); it runs the
+ *                 complement tests and the direct tests of stages with at most
+ *                 12 conditioning members and at most 16 tests per warp of its
+ *                 grid, a warp each; from the first stage it does not take
+ *                 (larger direct stages, or a stage the proposal may score) on,
+ *                 the captured loop (default; skipped on a device without
+ *                 cooperative launches).  0 = the captured loop throughout.
+ *                 The results are the same either way.
  *   "comp_fp32"   1 = complement tests (reversed order) in FP32 first from the
  *                 FP64 precision blocks, decided there when a first-order
  *                 error bound with validity checks shows the FP64 decision is

@@ -1365,7 +1365,9 @@ static pc_status skeleton_enqueue(pc_handle *h)
         CK(fpc::launch_tail(g, tp, level_cap(h), 1, h->singular, stage_a_launched, h->hcond, 0, fpc::StageConds{},
                             s));
     }
-    bool loop = h->stage_loop && h->order == 1 && h->complement && p <= fpc::LOOP_PMAX && !h->nblk;
+    // the stage loop in one kernel for small problems (the reversed order's precision
+    // blocks, when it has them, included)
+    bool loop = h->stage_loop && p <= fpc::LOOP_PMAX && !h->nblk;
     if (loop && h->coop < 0) {
         int dev = 0, v = 0;
         CK(cudaGetDevice(&dev));
@@ -1381,13 +1383,15 @@ static pc_status skeleton_enqueue(pc_handle *h)
         if (!loop) CK(fpc::launch_prec_update(g, tp, h->C64, h->ldc, s));
     }
     if (loop) {
-        // the first blocks and the complement-only stages in one cooperative kernel; the
-        // captured loop (or the host loop) goes on from the first stage with direct tests
+        // the first blocks and the stages in one cooperative kernel; the captured loop (or
+        // the host loop) goes on from the first stage the kernel does not take
+        const bool blocks = h->order == 1 && h->complement;
         Timed t(h, 8);
-        cudaError_t e = fpc::launch_stage_loop(g, tp, h->C32, h->C64, h->ldc, h->budget, level_cap(h), 1, s);
+        cudaError_t e = fpc::launch_stage_loop(g, tp, h->C32, h->C64, h->ldc, h->budget, level_cap(h),
+                                               blocks ? 1 : 0, s);
         if (e == cudaErrorCooperativeLaunchTooLarge) {
             cudaGetLastError();                        // not resident: the captured loop runs it all
-            CK(fpc::launch_prec_update(g, tp, h->C64, h->ldc, s));
+            if (blocks) CK(fpc::launch_prec_update(g, tp, h->C64, h->ldc, s));
         } else {
             CK(e);
         }

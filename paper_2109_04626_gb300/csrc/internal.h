@@ -118,6 +118,7 @@ constexpr int STAGE_FIXED_KERNELS = 3;
 constexpr int LOOP_THREADS = 256;
 constexpr int LOOP_PMAX = 128;          // largest p it runs (its shared memory holds a p+1 block)
 constexpr int LOOP_MMAX = 14;           // direct tests it runs: l + 2 <= LOOP_MMAX
+constexpr unsigned long long LOOP_DIRECT_ROUNDS = 16;   // ... and at most this many per warp of its grid
 
 // Everything the stage kernels need, by value.
 struct GraphDev {

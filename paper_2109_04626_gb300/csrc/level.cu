@@ -2567,18 +2567,40 @@ __device__ __forceinline__ void commit_body(const GraphDev &g, int l_fixed, int 
             } else {
                 ull r = rank;
                 int x = 0;
-                // C(x, r) from the shared table where it covers the walk (x < SB_ROWS, r < SB_COLS)
-                const bool sbl = dd < SB_ROWS && l <= SB_COLS;
-                for (int i = 0; i < l; ++i) {
-                    while (x < dd - (l - i)) {
-                        ull c = sbl ? sb[(dd - x - 1) * SB_COLS + (l - i - 1)]
-                                    : g.binom[(long long)(dd - x - 1) * g.ldb + (l - i - 1)];
-                        if (r < c) break;
-                        r -= c;
+                // C(a, b) from the shared table where it covers them (a < SB_ROWS, b < SB_COLS)
+                auto bin = [&](int a, int b) -> ull {
+                    return (a < SB_ROWS && b < SB_COLS) ? sb[a * SB_COLS + b] : g.binom[(long long)a * g.ldb + b];
+                };
+                int lg = 0;
+                while ((1 << lg) < dd + 1) ++lg;
+                if (l * lg < dd) {
+                    // each position by a binary search (the walk below takes up to dd dependent
+                    // loads): the sets whose i-th position lies in [x, y) number
+                    // C(dd - x, l - i) - C(dd - y, l - i)
+                    for (int i = 0; i < l; ++i) {
+                        const int r1 = l - i;
+                        const ull base = bin(dd - x, r1), target = base - r;
+                        int lo = x, hi = dd - r1;
+                        while (lo < hi) {
+                            const int mid = (lo + hi + 1) >> 1;
+                            if (bin(dd - mid, r1) >= target) lo = mid;
+                            else hi = mid - 1;
+                        }
+                        r -= base - bin(dd - lo, r1);
+                        g.pool[off + i] = cand_node(g, prop, su, jj, dd, lo);
+                        x = lo + 1;
+                    }
+                } else {
+                    for (int i = 0; i < l; ++i) {
+                        while (x < dd - (l - i)) {
+                            const ull c = bin(dd - x - 1, l - i - 1);
+                            if (r < c) break;
+                            r -= c;
+                            ++x;
+                        }
+                        g.pool[off + i] = cand_node(g, prop, su, jj, dd, x);
                         ++x;
                     }
-                    g.pool[off + i] = cand_node(g, prop, su, jj, dd, x);
-                    ++x;
                 }
                 if (prop) sort_small(g.pool + off, l);
             }
@@ -2632,9 +2654,12 @@ __device__ __forceinline__ bool loop_stage_plan(const GraphDev &g, const TestPar
         sdoff[p] = tot[1];
     }
     __syncthreads();
-    // direct tests only where the warp buffer holds them and no proposal order could
-    // apply (the captured loop scores such stages)
-    const bool direct_ok = tot[1] == 0 || (l + 2 <= LOOP_MMAX && !(g.row_off && l >= 1 && l <= tp.learned_lmax));
+    // direct tests only where the warp buffer holds them, where no proposal order could
+    // apply (the captured loop scores such stages), and at most LOOP_DIRECT_ROUNDS per
+    // warp of the grid (larger stages run faster on the small-stage kernels)
+    const ull nwarps = (ull)gridDim.x * (blockDim.x >> 5);
+    const bool direct_ok = tot[1] == 0 || (l + 2 <= LOOP_MMAX && tot[1] <= LOOP_DIRECT_ROUNDS * nwarps &&
+                                           !(g.row_off && l >= 1 && l <= tp.learned_lmax));
     return !ssat && tot[0] != KEY_NONE && tot[1] != KEY_NONE && direct_ok &&
            (double)tot[0] + (double)tot[1] <= budget;
 }
