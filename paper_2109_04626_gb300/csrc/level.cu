@@ -400,6 +400,9 @@ __device__ __noinline__ void head_body(const GraphDev &g, const TestParams &tp, 
     // tests per pair of each of this thread's nodes; 0 for complement-path nodes' direct count
     ull Tn[HEAD_PER_MAX];
     bool cm[HEAD_PER_MAX];
+    // each node's staged work items and degree, formed once (64-bit divisions)
+    ull Ik[HEAD_PER_MAX];
+    int Dg[HEAD_PER_MAX];
     // proposal rows: a direct-path node whose pairs have at least two sets to order
     // gets deg*(deg-1) score rows (pair j, candidate position x); the complement path
     // (dropped sets of at most KC_MAX members, reverse-lexicographic) keeps the plain order
@@ -429,12 +432,14 @@ __device__ __noinline__ void head_body(const GraphDev &g, const TestParams &tp, 
         const bool comp = T && comp_eligible(d, l, tp) && g.prec_m[u] > 0;
         Tn[u - s0] = T;
         cm[u - s0] = comp;
+        Dg[u - s0] = dg;
+        const ull k = comp ? 0ull : items(dg, T);
+        Ik[u - s0] = k;
         if (comp) v[1] = sat_add(v[1], tot);
         else {
             v[0] = sat_add(v[0], tot);
-            if (!items(dg, T) && !warp_mode(dg, T)) mxT = T > mxT ? T : mxT;   // the lane kernel's pairs only
+            if (!k && !warp_mode(dg, T)) mxT = T > mxT ? T : mxT;   // the lane kernel's pairs only
             v[2] = sat_add(v[2], prows(dg, T));           // complement-path pairs keep the plain order
-            const ull k = items(dg, T);
             v[3] += k ? 1ull : 0ull;
             v[4] = sat_add(v[4], k ? k - 1 : 0ull);
             v[5] += warp_mode(dg, T) ? (ull)dg : 0ull;
@@ -454,7 +459,7 @@ __device__ __noinline__ void head_body(const GraphDev &g, const TestParams &tp, 
     {
         ull rd = ex[0], rc = ex[1], rr = ex[2], ra = ex[3], ri = ex[4], rw = ex[5];
         for (int u = s0; u < s1; ++u) {
-            const int dg = __ldg(g.deg + u);             // read-only here: not held behind the stores
+            const int dg = Dg[u - s0];
             const ull T = Tn[u - s0], tt = sat_mul(T, (ull)dg);
             g.tn_off[u] = rd;
             g.cn_off[u] = rc;
@@ -466,7 +471,7 @@ __device__ __noinline__ void head_body(const GraphDev &g, const TestParams &tp, 
             else {
                 rd = sat_add(rd, tt);
                 rr = sat_add(rr, prows(dg, T));
-                const ull k = items(dg, T);
+                const ull k = Ik[u - s0];
                 ra += k ? 1ull : 0ull;
                 ri = sat_add(ri, k ? k - 1 : 0ull);
                 rw += (!cm[u - s0] && warp_mode(dg, T)) ? (ull)dg : 0ull;
@@ -507,8 +512,8 @@ __device__ __noinline__ void head_body(const GraphDev &g, const TestParams &tp, 
         ull v2[1] = {0ull};
         for (int u = s0; u < s1; ++u) {
             const ull T = Tn[u - s0];
-            const int dg = __ldg(g.deg + u);
-            if (!cm[u - s0] && T > skip && !items(dg, T) && !warp_mode(dg, T))
+            const int dg = Dg[u - s0];
+            if (!cm[u - s0] && T > skip && !Ik[u - s0] && !warp_mode(dg, T))
                 v2[0] = sat_add(v2[0], sat_mul(T - skip, (ull)dg));
         }
         ull ex2[1], tot2[1];
@@ -516,9 +521,9 @@ __device__ __noinline__ void head_body(const GraphDev &g, const TestParams &tp, 
         ull rr2 = ex2[0];
         for (int u = s0; u < s1; ++u) {
             const ull T = Tn[u - s0];
-            const int dg = __ldg(g.deg + u);
+            const int dg = Dg[u - s0];
             g.rn_off[u] = rr2;
-            if (!cm[u - s0] && T > skip && !items(dg, T) && !warp_mode(dg, T))
+            if (!cm[u - s0] && T > skip && !Ik[u - s0] && !warp_mode(dg, T))
                 rr2 = sat_add(rr2, sat_mul(T - skip, (ull)dg));
         }
         if (t == 0) g.rn_off[p] = tot2[0];
@@ -2468,7 +2473,8 @@ __device__ __forceinline__ void commit_body(const GraphDev &g, int l_fixed, int 
          base += (long long)ncta * blockDim.x) {
         const long long o = base + lane;
         bool expand = false, cut = false;                 // cut: this lane removes the edge (u, v)
-        int su = 0, jj = 0, dd = 0, cu_ = 0, cv_ = 0;
+        int su = 0, jj = 0, dd = 0, cu_ = 0, cv_ = 0, side_ = 0, j_ = 0, du_ = 0, dv_ = 0;
+        long long e_ = 0;
         ull rank = 0, off = 0;
         if (o < nop) {
             // owner node: the head kernel's table inside the stage loop, else a search
@@ -2503,21 +2509,40 @@ __device__ __forceinline__ void commit_body(const GraphDev &g, int l_fixed, int 
                     g.sep_side[e] = side;
                     g.sep_rank[e] = (long long)rank;
                     ++removed;
-                    if (explicit_sets) {
-                        off = atomicAdd(&g.ctr->pool_len, (ull)l);
-                        g.sep_off[e] = (long long)off;
-                        if ((long long)(off + l) > g.pool_cap) {
-                            g.info->pool_overflow = 1;   // the host enlarges the pool and reruns
-                            g.info->halt = 1;
-                        } else {
-                            su = side ? v : u;
-                            jj = side ? lower_bound_int(g.nbr + nidx(g, v), dv + 1, u) : j;
-                            dd = side ? dv : du;
-                            expand = true;
-                        }
-                    } else {
-                        g.sep_off[e] = -1;
-                    }
+                    side_ = side;
+                    e_ = e;
+                    j_ = j;
+                    du_ = du;
+                    dv_ = dv;
+                }
+            }
+        }
+        // room for the explicit sets in the sepset pool: one atomic per warp, each cutting
+        // lane's offset from a scan of the lanes' set sizes
+        if (cut && !explicit_sets) g.sep_off[e_] = -1;
+        {
+            const bool alloc = cut && explicit_sets;   // also at l = 0: an empty set, not V \ {u, v}
+            const ull want = alloc ? (ull)l : 0ull;
+            ull incl = want;
+            for (int k = 1; k < 32; k <<= 1) {
+                const ull y = __shfl_up_sync(0xffffffffu, incl, k);
+                if (lane >= k) incl += y;
+            }
+            const ull wtot = __shfl_sync(0xffffffffu, incl, 31);
+            ull wbase = 0;
+            if (lane == 31 && wtot) wbase = atomicAdd(&g.ctr->pool_len, wtot);
+            wbase = __shfl_sync(0xffffffffu, wbase, 31);
+            if (alloc) {
+                off = wbase + incl - want;
+                g.sep_off[e_] = (long long)off;
+                if ((long long)(off + l) > g.pool_cap) {
+                    g.info->pool_overflow = 1;           // the host enlarges the pool and reruns
+                    g.info->halt = 1;
+                } else {
+                    su = side_ ? cv_ : cu_;
+                    jj = side_ ? lower_bound_int(g.nbr + nidx(g, cv_), dv_ + 1, cu_) : j_;
+                    dd = side_ ? dv_ : du_;
+                    expand = true;
                 }
             }
         }
@@ -2606,8 +2631,15 @@ __device__ __forceinline__ void commit_body(const GraphDev &g, int l_fixed, int 
             }
         }
     }
-    if (removed) atomicAdd(&g.ctr->edges_removed, removed);
-    if (canon) atomicAdd(&g.ctr->tests_canonical, canon);
+    // the counters: one atomic per warp (a stage's commit has up to p(p-1) threads)
+    for (int k = 16; k > 0; k >>= 1) {
+        removed += __shfl_xor_sync(0xffffffffu, removed, k);
+        canon = sat_add(canon, __shfl_xor_sync(0xffffffffu, canon, k));
+    }
+    if (lane == 0) {
+        if (removed) atomicAdd(&g.ctr->edges_removed, removed);
+        if (canon) atomicAdd(&g.ctr->tests_canonical, canon);
+    }
 }
 
 __global__ void commit_kernel(GraphDev g, int l_fixed, int explicit_sets, int count_canonical)
